@@ -1,0 +1,203 @@
+"""FP64 CPU oracle of the column microphysics step -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  It wraps ``casim_oracle.c`` (plain C, compiled
+with ``-ffp-contract=off``) through ctypes and shares no code with the CUDA
+path.  See ``casim_oracle.c`` for the scheme and the parameterisation each
+function follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "casim_oracle.c")
+_LIB = os.path.join(_HERE, "libcasim_oracle.so")
+
+NFIELDS = 16
+NPROG = 13
+NPROC = 14
+SPECIES = {"c": 0, "r": 1, "i": 2, "s": 3, "g": 4}
+PROCS = ("aut", "acc", "scc", "scr", "evr", "nuc", "depi", "deps", "depg",
+         "rims", "rimg", "mlti", "mlts", "mltg")
+ERR_NONFINITE = 1
+ERR_CFL = 2
+NSUB_MAX = 64
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "casim_oracle.h"))):
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+               "-shared", "-std=c11", "-o", _LIB, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        d, pd, i, u = ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_uint
+        for name in ("orc_es_liq", "orc_es_ice", "orc_arg_sm"):
+            getattr(L, name).restype = d
+            getattr(L, name).argtypes = [d]
+        L.orc_qsat.restype = d
+        L.orc_qsat.argtypes = [d, d]
+        L.orc_dqsat_liq_dT.restype = d
+        L.orc_dqsat_liq_dT.argtypes = [d, d]
+        L.orc_satadj.restype = None
+        L.orc_satadj.argtypes = [d, pd, pd, pd]
+        for name in ("orc_arg_smax", "orc_arg_nact"):
+            getattr(L, name).restype = d
+            getattr(L, name).argtypes = [d, d, d, d]
+        L.orc_lambda.restype = d
+        L.orc_lambda.argtypes = [i, d, d]
+        L.orc_moment.restype = d
+        L.orc_moment.argtypes = [i, d, d, d, d]
+        L.orc_vent_integral.restype = d
+        L.orc_vent_integral.argtypes = [i, d, d, d]
+        for name in ("orc_vq", "orc_vn"):
+            getattr(L, name).restype = d
+            getattr(L, name).argtypes = [i, d, d]
+        L.orc_rates.restype = None
+        L.orc_rates.argtypes = [pd, d, pd]
+        L.orc_point.restype = None
+        L.orc_point.argtypes = [pd, d, pd]
+        L.orc_sediment_column.restype = u
+        L.orc_sediment_column.argtypes = [pd, pd, pd, pd, i, d, pd, ctypes.POINTER(ctypes.c_int)]
+        L.orc_step.restype = u
+        L.orc_step.argtypes = [pd, ctypes.c_long, i, i, pd, pd, ctypes.POINTER(ctypes.c_int), d, i]
+        L.orc_param.restype = d
+        L.orc_param.argtypes = [ctypes.c_char_p]
+        L.orc_max_threads.restype = i
+        L.orc_max_threads.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def param(name: str) -> float:
+    return lib().orc_param(name.encode())
+
+
+def es_liq(T: float) -> float:
+    return lib().orc_es_liq(T)
+
+
+def es_ice(T: float) -> float:
+    return lib().orc_es_ice(T)
+
+
+def qsat(es: float, p: float) -> float:
+    return lib().orc_qsat(es, p)
+
+
+def dqsat_liq_dT(T: float, p: float) -> float:
+    return lib().orc_dqsat_liq_dT(T, p)
+
+
+def satadj(p: float, T: float, qv: float, qc: float):
+    t, v, c = ctypes.c_double(T), ctypes.c_double(qv), ctypes.c_double(qc)
+    lib().orc_satadj(p, ctypes.byref(t), ctypes.byref(v), ctypes.byref(c))
+    return t.value, v.value, c.value
+
+
+def arg_sm(T: float) -> float:
+    return lib().orc_arg_sm(T)
+
+
+def arg_smax(N: float, w: float, T: float, p: float) -> float:
+    return lib().orc_arg_smax(N, w, T, p)
+
+
+def arg_nact(N: float, w: float, T: float, p: float) -> float:
+    return lib().orc_arg_nact(N, w, T, p)
+
+
+def lam(sp: str, q: float, n: float) -> float:
+    return lib().orc_lambda(SPECIES[sp], q, n)
+
+
+def moment(sp: str, rho: float, q: float, lam_: float, k: float) -> float:
+    return lib().orc_moment(SPECIES[sp], rho, q, lam_, k)
+
+
+def vent_integral(sp: str, rho: float, q: float, lam_: float) -> float:
+    return lib().orc_vent_integral(SPECIES[sp], rho, q, lam_)
+
+
+def vq(sp: str, rho: float, lam_: float) -> float:
+    return lib().orc_vq(SPECIES[sp], rho, lam_)
+
+
+def vn(sp: str, rho: float, lam_: float) -> float:
+    return lib().orc_vn(SPECIES[sp], rho, lam_)
+
+
+def rates(state: np.ndarray, dt: float) -> dict:
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    assert st.shape == (NFIELDS,)
+    out = np.zeros(NPROC)
+    lib().orc_rates(_dp(st), dt, _dp(out))
+    return dict(zip(PROCS, out.tolist()))
+
+
+def point(state: np.ndarray, dt: float) -> np.ndarray:
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    assert st.shape == (NFIELDS,)
+    out = np.zeros(NPROG)
+    lib().orc_point(_dp(st), dt, _dp(out))
+    return out
+
+
+def sediment_column(q: np.ndarray, n: np.ndarray, rho: np.ndarray, dz: np.ndarray, dt: float):
+    """q, n: [4][nlev] for r, i, s, g (copied); returns (q, n, precip[4], nsub[4], err)."""
+    q = np.array(q, dtype=np.float64, order="C")
+    n = np.array(n, dtype=np.float64, order="C")
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    nlev = rho.shape[0]
+    assert q.shape == (4, nlev) and n.shape == (4, nlev) and dz.shape == (nlev,)
+    pr = np.zeros(4)
+    ns = np.zeros(4, dtype=np.int32)
+    err = lib().orc_sediment_column(_dp(q), _dp(n), _dp(rho), _dp(dz), nlev, dt, _dp(pr),
+                                    ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return q, n, pr, ns, err
+
+
+def step(fld: np.ndarray, ncols: int, dz: np.ndarray, dt: float, precip: np.ndarray | None = None,
+         nthreads: int = 0, want_nsub: bool = False):
+    """One step over a domain, in place on ``fld`` [16][nlev][pitch].
+
+    Returns (precip [4][pitch] accumulated, nsub [4][pitch] or None, err bits).
+    """
+    assert fld.dtype == np.float64 and fld.flags["C_CONTIGUOUS"] and fld.shape[0] == NFIELDS
+    nlev, pitch = fld.shape[1], fld.shape[2]
+    assert ncols <= pitch
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    assert dz.shape == (nlev,)
+    if precip is None:
+        precip = np.zeros((4, pitch))
+    assert precip.shape == (4, pitch) and precip.dtype == np.float64 and precip.flags["C_CONTIGUOUS"]
+    nsub = np.zeros((4, pitch), dtype=np.int32) if want_nsub else None
+    nsp = nsub.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if want_nsub else None
+    err = lib().orc_step(_dp(fld), pitch, ncols, nlev, _dp(dz), _dp(precip), nsp, dt, nthreads)
+    return precip, nsub, err
+
+
+def max_threads() -> int:
+    return lib().orc_max_threads()

@@ -1,0 +1,562 @@
+/*
+ * FP64 CPU oracle of the column microphysics step -- TEST INFRASTRUCTURE.
+ *
+ * Plain, slow, sequential-per-column C, compiled with -ffp-contract=off so
+ * every product and sum is rounded as written.  Only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg load it.  Nothing here is shared
+ * with the CUDA path.
+ *
+ * The paper (Section 2) describes CASIM as a bulk scheme in which each
+ * species carries a gamma-type size distribution described by a diameter D,
+ * a shape mu, a slope lambda and an intercept N0, with columns independent
+ * and processes (accretion, autoconversion, sedimentation, activation)
+ * acting in the vertical only.  It prints no rate laws, so each process
+ * below follows a named published parameterisation:
+ *   saturation vapour pressure   Bolton (1980) over liquid; Murray (1967)
+ *                                Tetens form over ice
+ *   saturation adjustment        Newton iteration on the isobaric enthalpy
+ *                                balance, 4 fixed iterations
+ *   activation                   Abdul-Razzak & Ghan (2000), one lognormal mode
+ *   autoconversion, accretion    Khairoutdinov & Kogan (2000)
+ *   self-collection              Seifert & Beheng (2001) cloud, (2006) rain
+ *   evaporation, deposition,     ventilated diffusional growth integrated
+ *   melting                      over the gamma distribution (Pruppacher &
+ *                                Klett ventilation 0.78 + 0.31 Sc^1/3 Re^1/2)
+ *   ice nucleation               Meyers, DeMott & Cotton (1992)
+ *   riming                       continuous collection, E = 1
+ *   sedimentation                mass/number-weighted fall speeds, upwind
+ *                                flux form, CFL substeps
+ * Parity of the whole step with CASIM itself is unpinned: CASIM's source is
+ * not available; this file defines the scheme the GPU path must reproduce.
+ */
+#include "casim_oracle.h"
+
+#include <math.h>
+#include <string.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- constants */
+static const double T0 = 273.15;       /* melting point, K */
+static const double CP = 1005.0;       /* J kg^-1 K^-1 */
+static const double LV = 2.5e6;        /* J kg^-1 */
+static const double LF = 3.34e5;       /* J kg^-1 */
+#define LS (LV + LF)
+static const double RD = 287.04;
+static const double RV = 461.5;
+#define EPS (RD / RV)
+static const double GRAV = 9.81;
+static const double RHOW = 1000.0;
+static const double RHO0 = 1.2;        /* fall-speed reference density */
+static const double KA = 2.4e-2;       /* thermal conductivity of air */
+static const double DV = 2.26e-5;      /* vapour diffusivity */
+static const double MUAIR = 1.72e-5;   /* dynamic viscosity of air */
+static const double QMIN = 1e-14;      /* species present iff q > QMIN */
+static const double TNUC = 268.15;     /* ice nucleation below this, K */
+static const double MI0 = 1e-12;       /* mass of a nucleated crystal, kg */
+static const double RR0 = 25e-6;       /* radius of a new raindrop, m */
+static const double KK_AUT = 1350.0, KK_AUT_QC = 2.47, KK_AUT_NC = -1.79;
+static const double NC_MIN_CM3 = 1.0;  /* floor on N_c in the KK formula */
+static const double KK_ACC = 67.0, KK_ACC_EXP = 1.15;
+static const double KC_SB = 9.44e9, NU_C = 1.0;   /* cloud self-collection */
+static const double KR_SB = 5.78;                 /* rain self-collection */
+static const double MEY_A = 1e3, MEY_B = -0.639, MEY_C = 12.96;
+static const double ARG_RM = 0.05e-6, ARG_SIGMA = 1.5, ARG_KAPPA = 0.61;
+static const double SURFT = 0.0761, MW = 0.018015, MA = 0.028965, RGAS = 8.314;
+static const double E_RIM = 1.0;
+static const double CMAX = 1.0;        /* Courant limit per substep */
+static const double ES_L0 = 611.2, ES_LA = 17.67, ES_LB = 243.5;      /* Bolton */
+static const double ES_I0 = 610.78, ES_IA = 21.875, ES_IT = 273.16, ES_IB = 7.66;
+
+typedef struct {
+  double a, b;        /* m(D) = a D^b */
+  double mu;          /* gamma shape */
+  double cv, dv;      /* V(D) = cv D^dv (rho0/rho)^0.4 */
+  double vmax;        /* fall-speed cap, m/s */
+  double dmin, dmax;  /* bounds on the mean diameter (mu+1)/lambda */
+  double ccap;        /* capacitance C = ccap * D */
+} orc_species;
+
+#define PI 3.14159265358979323846
+static const orc_species SP[ORC_NSPECIES] = {
+  /* cloud   */ {PI / 6.0 * 1000.0, 3.0, 2.0, 0.0, 0.0, 0.0, 1e-6, 1e-4, 0.5},
+  /* rain    */ {PI / 6.0 * 1000.0, 3.0, 0.0, 130.0, 0.5, 10.0, 50e-6, 5e-3, 0.5},
+  /* ice     */ {PI / 6.0 * 500.0, 3.0, 0.0, 700.0, 1.0, 2.0, 1e-6, 500e-6, 0.5},
+  /* snow    */ {PI / 6.0 * 100.0, 3.0, 0.0, 11.72, 0.41, 4.0, 10e-6, 5e-3, 1.0 / PI},
+  /* graupel */ {PI / 6.0 * 400.0, 3.0, 0.5, 19.3, 0.37, 10.0, 10e-6, 5e-3, 0.5},
+};
+
+/* ------------------------------------------------------ c1 thermodynamics */
+double orc_es_liq(double T) {
+  /* Bolton (1980): e_s = 611.2 exp(17.67 Tc / (Tc + 243.5)), Tc in deg C */
+  double tc = T - T0;
+  return ES_L0 * exp(ES_LA * tc / (tc + ES_LB));
+}
+
+double orc_es_ice(double T) {
+  /* Murray (1967) Tetens form over ice */
+  return ES_I0 * exp(ES_IA * (T - ES_IT) / (T - ES_IB));
+}
+
+double orc_qsat(double es, double p) {
+  /* saturation mixing ratio of vapour over the given saturation pressure */
+  return EPS * es / (p - (1.0 - EPS) * es);
+}
+
+double orc_dqsat_liq_dT(double T, double p) {
+  double tc = T - T0;
+  double es = orc_es_liq(T);
+  double des = es * ES_LA * ES_LB / ((tc + ES_LB) * (tc + ES_LB));
+  double den = p - (1.0 - EPS) * es;
+  return EPS * p / (den * den) * des;
+}
+
+/* ------------------------------------------------ a2 saturation adjustment */
+void orc_satadj(double p, double *T, double *qv, double *qc) {
+  /* Isobaric adjustment to liquid saturation: find T* with
+       cp (T* - T) = Lv (qv - qs(T*))
+     by Newton's method, 4 fixed iterations from T (no convergence test, so
+     every implementation takes the same path).  The condensed amount
+     dq = (cp/Lv)(T* - T) is limited below by -qc (evaporation cannot exceed
+     the cloud present); T then follows from dq so that cp dT = Lv dq. */
+  double T0v = *T, qv0 = *qv, qc0 = *qc;
+  double qs0 = orc_qsat(orc_es_liq(T0v), p);
+  if (!(qv0 > qs0 || qc0 > QMIN)) return;
+  double Tn = T0v;
+  for (int it = 0; it < 4; ++it) {
+    double qs = orc_qsat(orc_es_liq(Tn), p);
+    double f = (Tn - T0v) - (LV / CP) * (qv0 - qs);
+    double fp = 1.0 + (LV / CP) * orc_dqsat_liq_dT(Tn, p);
+    Tn = Tn - f / fp;
+  }
+  double dq = (CP / LV) * (Tn - T0v);
+  if (dq < -qc0) dq = -qc0;
+  *T = T0v + (LV / CP) * dq;
+  *qv = qv0 - dq;
+  *qc = qc0 + dq;
+}
+
+/* ---------------------------------------------------------- a3 activation */
+double orc_arg_sm(double T) {
+  /* Critical supersaturation of a particle at the mode radius (Koehler
+     theory, kappa form): S_m = (2/sqrt(B)) (A / (3 r_m))^(3/2),
+     A = 2 sigma_w M_w / (rho_w R T). */
+  double A = 2.0 * SURFT * MW / (RHOW * RGAS * T);
+  return 2.0 / sqrt(ARG_KAPPA) * pow(A / (3.0 * ARG_RM), 1.5);
+}
+
+double orc_arg_smax(double N, double w, double T, double p) {
+  /* Abdul-Razzak & Ghan (2000) maximum supersaturation of a parcel rising at
+     w through one lognormal mode of N particles per m^3. */
+  double es = orc_es_liq(T);
+  double alpha = GRAV * MW * LV / (CP * RGAS * T * T) - GRAV * MA / (RGAS * T);
+  double gam = RGAS * T / (es * MW) + MW * LV * LV / (CP * p * MA * T);
+  double G = 1.0 / (RHOW * RGAS * T / (es * DV * MW) +
+                    LV * RHOW / (KA * T) * (LV * MW / (RGAS * T) - 1.0));
+  double A = 2.0 * SURFT * MW / (RHOW * RGAS * T);
+  double sm = orc_arg_sm(T);
+  double awg = alpha * w / G;
+  double zeta = 2.0 * A / 3.0 * sqrt(awg);
+  double eta = pow(awg, 1.5) / (2.0 * PI * RHOW * gam * N);
+  double lns = log(ARG_SIGMA);
+  double f1 = 0.5 * exp(2.5 * lns * lns);
+  double f2 = 1.0 + 0.25 * lns;
+  double sum = (1.0 / (sm * sm)) * (f1 * pow(zeta / eta, 1.5) + f2 * pow(sm * sm / (eta + 3.0 * zeta), 0.75));
+  return 1.0 / sqrt(sum);
+}
+
+double orc_arg_nact(double N, double w, double T, double p) {
+  /* Number activated (per m^3): the part of the lognormal mode whose
+     critical supersaturation lies below S_max. */
+  if (!(w > 0.0) || !(N > 0.0)) return 0.0;
+  double smax = orc_arg_smax(N, w, T, p);
+  double sm = orc_arg_sm(T);
+  double u = 2.0 * log(sm / smax) / (3.0 * sqrt(2.0) * log(ARG_SIGMA));
+  return 0.5 * N * erfc(u);
+}
+
+/* ------------------------------------------------ gamma-distribution algebra */
+double orc_lambda(int sp, double q, double n) {
+  /* n(D) = N0 D^mu exp(-lambda D) with m(D) = a D^b:
+       q / n = a Gamma(mu+b+1) / (Gamma(mu+1) lambda^b)
+     lambda is clamped so the mean diameter (mu+1)/lambda stays inside
+     [dmin, dmax]; a non-positive number gives the largest particles. */
+  const orc_species *s = &SP[sp];
+  double nn = n > 0.0 ? n : 0.0;
+  double lam = pow(s->a * tgamma(s->mu + s->b + 1.0) / tgamma(s->mu + 1.0) * nn / q, 1.0 / s->b);
+  double lo = (s->mu + 1.0) / s->dmax, hi = (s->mu + 1.0) / s->dmin;
+  if (lam < lo) lam = lo;
+  if (lam > hi) lam = hi;
+  return lam;
+}
+
+double orc_moment(int sp, double rho, double q, double lam, double k) {
+  /* M_k = int D^k n(D) dD per m^3, with N0 fixed by the mass content
+     rho q = a N0 Gamma(mu+b+1) / lambda^(mu+b+1):
+       M_k = (rho q / a) Gamma(mu+k+1) / Gamma(mu+b+1) * lambda^(b-k) */
+  const orc_species *s = &SP[sp];
+  return rho * q / s->a * tgamma(s->mu + k + 1.0) / tgamma(s->mu + s->b + 1.0) * pow(lam, s->b - k);
+}
+
+double orc_vent_integral(int sp, double rho, double q, double lam) {
+  /* int D f_v(D) n(D) dD with f_v = 0.78 + 0.31 Sc^(1/3) Re^(1/2),
+     Re = V(D) D / nu, V(D) = cv D^dv (rho0/rho)^0.4, Sc = nu / Dv. */
+  const orc_species *s = &SP[sp];
+  double nu = MUAIR / rho;
+  double sc = nu / DV;
+  double vfac = s->cv * pow(RHO0 / rho, 0.4);
+  return 0.78 * orc_moment(sp, rho, q, lam, 1.0) +
+         0.31 * cbrt(sc) * sqrt(vfac / nu) * orc_moment(sp, rho, q, lam, 0.5 * (s->dv + 3.0));
+}
+
+double orc_vq(int sp, double rho, double lam) {
+  /* mass-weighted fall speed, capped */
+  const orc_species *s = &SP[sp];
+  double v = s->cv * pow(RHO0 / rho, 0.4) * tgamma(s->mu + s->b + s->dv + 1.0) /
+             tgamma(s->mu + s->b + 1.0) * pow(lam, -s->dv);
+  return v < s->vmax ? v : s->vmax;
+}
+
+double orc_vn(int sp, double rho, double lam) {
+  /* number-weighted fall speed, capped */
+  const orc_species *s = &SP[sp];
+  double v = s->cv * pow(RHO0 / rho, 0.4) * tgamma(s->mu + s->dv + 1.0) / tgamma(s->mu + 1.0) *
+             pow(lam, -s->dv);
+  return v < s->vmax ? v : s->vmax;
+}
+
+/* --------------------------------------------------------- a4..a9 rates */
+void orc_rates(const double *st, double dt, double *R) {
+  /* Rates in kg kg^-1 s^-1 (masses) except SCC, SCR (number kg^-1 s^-1) and
+     NUC (new crystals kg^-1 s^-1).  All are >= 0 except DEPx, which is
+     positive for deposition and negative for sublimation.  MLTx is the
+     melted mass rate. */
+  double T = st[ORC_T], qv = st[ORC_QV], qc = st[ORC_QC], qr = st[ORC_QR];
+  double nc = st[ORC_NC], nr = st[ORC_NR], ni = st[ORC_NI];
+  double p = st[ORC_P], rho = st[ORC_RHO];
+  for (int j = 0; j < ORC_NPROC; ++j) R[j] = 0.0;
+
+  double esl = orc_es_liq(T), esi = orc_es_ice(T);
+  double qsl = orc_qsat(esl, p), qsi = orc_qsat(esi, p);
+  double Sw = qv / qsl, Si = qv / qsi;
+  double Aw = LV * LV / (KA * RV * T * T), Bw = RV * T / (esl * DV);
+  double Ai = LS * LS / (KA * RV * T * T), Bi = RV * T / (esi * DV);
+
+  int hc = qc > QMIN, hr = qr > QMIN;
+
+  /* a4 warm rain: Khairoutdinov & Kogan (2000), N_c in cm^-3 */
+  if (hc) {
+    double ncc = rho * nc * 1e-6;
+    if (ncc < NC_MIN_CM3) ncc = NC_MIN_CM3;
+    R[ORC_AUT] = KK_AUT * pow(qc, KK_AUT_QC) * pow(ncc, KK_AUT_NC);
+    /* Seifert & Beheng (2001) cloud self-collection, number only:
+       dN/dt = -k_c (nu+2)/(nu+1) L_c^2, L_c = rho q_c */
+    R[ORC_SCC] = KC_SB * (NU_C + 2.0) / (NU_C + 1.0) * rho * qc * qc;
+  }
+  if (hc && hr) R[ORC_ACC] = KK_ACC * pow(qc * qr, KK_ACC_EXP);
+  if (hr) {
+    /* Seifert & Beheng (2006) rain self-collection: dN/dt = -k_r N_r L_r */
+    R[ORC_SCR] = KR_SB * rho * (nr > 0.0 ? nr : 0.0) * qr;
+    /* a5 rain evaporation in subsaturated air: capacitance D/2 */
+    if (Sw < 1.0) {
+      double lam = orc_lambda(ORC_R, qr, nr);
+      R[ORC_EVR] = 2.0 * PI * (1.0 - Sw) * orc_vent_integral(ORC_R, rho, qr, lam) / (rho * (Aw + Bw));
+    }
+  }
+  /* a6 ice nucleation: Meyers et al. (1992), N_in in m^-3 */
+  if (T < TNUC && Si > 1.0) {
+    double nin = MEY_A * exp(MEY_B + MEY_C * (Si - 1.0));
+    double dn = nin / rho - ni;
+    if (dn > 0.0) R[ORC_NUC] = dn / dt;
+  }
+  /* a7 deposition / sublimation, a8 riming, a9 melting for i, s, g */
+  static const int spx[3] = {ORC_I, ORC_S, ORC_G};
+  static const int qx[3] = {ORC_QI, ORC_QS, ORC_QG};
+  static const int nx[3] = {ORC_NI, ORC_NS, ORC_NG};
+  static const int depj[3] = {ORC_DEPI, ORC_DEPS, ORC_DEPG};
+  static const int mltj[3] = {ORC_MLTI, ORC_MLTS, ORC_MLTG};
+  for (int m = 0; m < 3; ++m) {
+    int sp = spx[m];
+    double q = st[qx[m]];
+    if (!(q > QMIN)) continue;
+    double lam = orc_lambda(sp, q, st[nx[m]]);
+    if (T < T0) {
+      double iv = orc_vent_integral(sp, rho, q, lam);
+      R[depj[m]] = 4.0 * PI * SP[sp].ccap * (Si - 1.0) * iv / (rho * (Ai + Bi));
+      if (sp != ORC_I && hc) {
+        /* collection of cloud: (pi/4) E q_c int D^2 V(D) n(D) dD */
+        double vfac = SP[sp].cv * pow(RHO0 / rho, 0.4);
+        double r = 0.25 * PI * E_RIM * qc * vfac * orc_moment(sp, rho, q, lam, 2.0 + SP[sp].dv);
+        R[sp == ORC_S ? ORC_RIMS : ORC_RIMG] = r;
+      }
+    } else if (T > T0) {
+      double iv = orc_vent_integral(sp, rho, q, lam);
+      R[mltj[m]] = 4.0 * PI * SP[sp].ccap * KA * (T - T0) * iv / (rho * LF);
+    }
+  }
+}
+
+/* --------------------------------------------- a10 limiter and update */
+typedef struct {
+  double rate;    /* mass moved per second (kg/kg/s), >= 0 */
+  int msrc, mdst; /* mass pools (state index) or -1 */
+  int nsrc;       /* number pool drawn from, or -1 */
+  double nsink;   /* number removed per second */
+  int ndst;       /* number pool fed, or -1 */
+  double nsource; /* number added per second */
+  double heat;    /* latent heat released per kg moved (J/kg) */
+} orc_transfer;
+
+static double ratio(double n, double q) { return (n > 0.0 ? n : 0.0) / q; }
+
+void orc_point(const double *in, double dt, double *out) {
+  double st[ORC_NFIELDS];
+  memcpy(st, in, sizeof(st));
+  double p = st[ORC_P], rho = st[ORC_RHO], w = st[ORC_W];
+
+  /* a2 */
+  orc_satadj(p, &st[ORC_T], &st[ORC_QV], &st[ORC_QC]);
+
+  /* a3: aerosol activated from the population carried as n_a + n_c; the
+     cloud number is raised to N_act, taking the difference from n_a. */
+  if (w > 0.0 && st[ORC_QC] > QMIN) {
+    double N = rho * (st[ORC_NA] + st[ORC_NC]);
+    double nact = orc_arg_nact(N, w, st[ORC_T], p);
+    double dn = nact / rho - st[ORC_NC];
+    if (dn < 0.0) dn = 0.0;
+    if (dn > st[ORC_NA]) dn = st[ORC_NA];
+    st[ORC_NC] += dn;
+    st[ORC_NA] -= dn;
+  }
+
+  /* a4..a9 from the post-activation state */
+  double R[ORC_NPROC];
+  orc_rates(st, dt, R);
+
+  double qc = st[ORC_QC], qr = st[ORC_QR];
+  orc_transfer tr[ORC_NPROC];
+  int nt = 0;
+#define ADD(rt, ms, md, ns, nsk, nd, nso, ht) \
+  do { tr[nt].rate = (rt); tr[nt].msrc = (ms); tr[nt].mdst = (md); tr[nt].nsrc = (ns); \
+       tr[nt].nsink = (nsk); tr[nt].ndst = (nd); tr[nt].nsource = (nso); tr[nt].heat = (ht); ++nt; } while (0)
+  double rc = qc > QMIN ? ratio(st[ORC_NC], qc) : 0.0;
+  double rr = qr > QMIN ? ratio(st[ORC_NR], qr) : 0.0;
+  double mr0 = 4.0 / 3.0 * PI * RHOW * RR0 * RR0 * RR0;
+  ADD(R[ORC_AUT], ORC_QC, ORC_QR, ORC_NC, R[ORC_AUT] * rc, ORC_NR, R[ORC_AUT] / mr0, 0.0);
+  ADD(R[ORC_ACC], ORC_QC, ORC_QR, ORC_NC, R[ORC_ACC] * rc, -1, 0.0, 0.0);
+  ADD(0.0, -1, -1, ORC_NC, R[ORC_SCC], -1, 0.0, 0.0);
+  ADD(0.0, -1, -1, ORC_NR, R[ORC_SCR], -1, 0.0, 0.0);
+  ADD(R[ORC_EVR], ORC_QR, ORC_QV, ORC_NR, R[ORC_EVR] * rr, -1, 0.0, -LV);
+  ADD(R[ORC_NUC] * MI0, ORC_QV, ORC_QI, -1, 0.0, ORC_NI, R[ORC_NUC], LS);
+  static const int qx[3] = {ORC_QI, ORC_QS, ORC_QG};
+  static const int nx[3] = {ORC_NI, ORC_NS, ORC_NG};
+  for (int m = 0; m < 3; ++m) {
+    double d = R[ORC_DEPI + m];
+    if (d >= 0.0) {
+      ADD(d, ORC_QV, qx[m], -1, 0.0, -1, 0.0, LS);
+    } else {
+      double q = st[qx[m]];
+      ADD(-d, qx[m], ORC_QV, nx[m], -d * ratio(st[nx[m]], q), -1, 0.0, -LS);
+    }
+  }
+  ADD(R[ORC_RIMS], ORC_QC, ORC_QG, ORC_NC, R[ORC_RIMS] * rc, -1, 0.0, LF);
+  ADD(R[ORC_RIMG], ORC_QC, ORC_QG, ORC_NC, R[ORC_RIMG] * rc, -1, 0.0, LF);
+  for (int m = 0; m < 3; ++m) {
+    double r = R[ORC_MLTI + m];
+    double q = st[qx[m]];
+    double nq = r > 0.0 ? r * ratio(st[nx[m]], q) : 0.0;
+    ADD(r, qx[m], ORC_QR, nx[m], nq, ORC_NR, nq, -LF);
+  }
+#undef ADD
+
+  /* Sinks per pool; f_X = min(1, X / (S_X dt)); each transfer is scaled by
+     the smallest f over the pools it draws from, then applied once: taken
+     from its source and given to its destination. */
+  double S[ORC_NPROG], f[ORC_NPROG];
+  for (int x = 0; x < ORC_NPROG; ++x) S[x] = 0.0;
+  for (int j = 0; j < nt; ++j) {
+    if (tr[j].rate > 0.0) S[tr[j].msrc] += tr[j].rate;
+    if (tr[j].nsink > 0.0) S[tr[j].nsrc] += tr[j].nsink;
+  }
+  for (int x = 0; x < ORC_NPROG; ++x) {
+    double X = st[x];
+    f[x] = 1.0;
+    if (S[x] * dt > X) f[x] = (X > 0.0 ? X : 0.0) / (S[x] * dt);
+  }
+  for (int j = 0; j < nt; ++j) {
+    double g = 1.0;
+    if (tr[j].rate > 0.0 && f[tr[j].msrc] < g) g = f[tr[j].msrc];
+    if (tr[j].nsink > 0.0 && f[tr[j].nsrc] < g) g = f[tr[j].nsrc];
+    if (tr[j].rate > 0.0) {
+      double tau = g * tr[j].rate * dt;
+      st[tr[j].msrc] -= tau;
+      st[tr[j].mdst] += tau;
+      st[ORC_T] += tau * tr[j].heat / CP;
+    }
+    if (tr[j].nsink > 0.0) st[tr[j].nsrc] -= g * tr[j].nsink * dt;
+    if (tr[j].ndst >= 0 && tr[j].nsource > 0.0) st[tr[j].ndst] += g * tr[j].nsource * dt;
+  }
+  memcpy(out, st, ORC_NPROG * sizeof(double));
+}
+
+/* ------------------------------------------------------ a12 sedimentation */
+unsigned orc_sediment_column(double *q, double *n, const double *rho, const double *dz,
+                             int nlev, double dt, double *precip, int *nsub) {
+  /* For x in r, i, s, g: F_k = rho_k q_k Vq_k (mass), G_k = rho_k n_k Vn_k
+     (number), fluxes downward.  Per substep of length dt/n_sub, with all
+     fluxes taken from the substep's starting state:
+        X_k += dts (F_{k+1} - F_k) / (rho_k dz_k),  F_nlev = 0,
+        precip += F_0 dts.
+     n_sub = max(1, ceil(max_k Vq_k dt / dz_k / C_max)) from the state
+     entering sedimentation; capped at ORC_NSUB_MAX (error bit).  Speeds are
+     recomputed from the updated q, n at every substep, and limited to
+     dz_k / dts so that no level can be emptied below zero. */
+  static const int spx[4] = {ORC_R, ORC_I, ORC_S, ORC_G};
+  unsigned err = 0;
+  double *F = (double *)malloc(sizeof(double) * (size_t)(nlev + 1));
+  double *G = (double *)malloc(sizeof(double) * (size_t)(nlev + 1));
+  for (int m = 0; m < 4; ++m) {
+    int sp = spx[m];
+    double *qq = q + (size_t)m * nlev, *nn = n + (size_t)m * nlev;
+    double cmax = 0.0;
+    for (int k = 0; k < nlev; ++k) {
+      if (!(qq[k] > QMIN)) continue;
+      double lam = orc_lambda(sp, qq[k], nn[k]);
+      double c = orc_vq(sp, rho[k], lam) * dt / dz[k];
+      if (c > cmax) cmax = c;
+    }
+    int ns = (int)ceil(cmax / CMAX);
+    if (ns < 1) ns = 1;
+    if (ns > ORC_NSUB_MAX) { ns = ORC_NSUB_MAX; err |= ORC_ERR_CFL; }
+    if (nsub) nsub[m] = ns;
+    double dts = dt / ns;
+    for (int s = 0; s < ns; ++s) {
+      for (int k = 0; k < nlev; ++k) {
+        F[k] = 0.0;
+        G[k] = 0.0;
+        if (qq[k] > QMIN) {
+          double lam = orc_lambda(sp, qq[k], nn[k]);
+          /* a level never loses more than it holds within one substep: the
+             speed is limited to dz_k / dts (binds only when a later substep's
+             speeds exceed the maximum that set n_sub) */
+          double vlim = dz[k] / dts;
+          double vq = orc_vq(sp, rho[k], lam), vn = orc_vn(sp, rho[k], lam);
+          if (vq > vlim) vq = vlim;
+          if (vn > vlim) vn = vlim;
+          F[k] = rho[k] * qq[k] * vq;
+          G[k] = rho[k] * (nn[k] > 0.0 ? nn[k] : 0.0) * vn;
+        }
+      }
+      F[nlev] = 0.0;
+      G[nlev] = 0.0;
+      for (int k = 0; k < nlev; ++k) {
+        qq[k] += dts * (F[k + 1] - F[k]) / (rho[k] * dz[k]);
+        nn[k] += dts * (G[k + 1] - G[k]) / (rho[k] * dz[k]);
+      }
+      precip[m] += F[0] * dts;
+    }
+  }
+  free(F);
+  free(G);
+  return err;
+}
+
+/* ----------------------------------------------------------- full step */
+static unsigned step_column(double *fld, long pitch, int nlev, int c, const double *dz,
+                            double *precip, int *nsub, double dt) {
+  unsigned err = 0;
+  long fs = (long)nlev * pitch; /* field stride */
+  double in[ORC_NFIELDS], out[ORC_NPROG];
+  for (int k = 0; k < nlev; ++k) {
+    for (int f = 0; f < ORC_NFIELDS; ++f) in[f] = fld[f * fs + (long)k * pitch + c];
+    orc_point(in, dt, out);
+    for (int f = 0; f < ORC_NPROG; ++f) fld[f * fs + (long)k * pitch + c] = out[f];
+  }
+  double *buf = (double *)malloc(sizeof(double) * (size_t)(9 * nlev));
+  double *q = buf, *n = buf + 4 * nlev, *rho = buf + 8 * nlev;
+  static const int qf[4] = {ORC_QR, ORC_QI, ORC_QS, ORC_QG};
+  static const int nf[4] = {ORC_NR, ORC_NI, ORC_NS, ORC_NG};
+  for (int k = 0; k < nlev; ++k) {
+    rho[k] = fld[ORC_RHO * fs + (long)k * pitch + c];
+    for (int m = 0; m < 4; ++m) {
+      q[m * nlev + k] = fld[qf[m] * fs + (long)k * pitch + c];
+      n[m * nlev + k] = fld[nf[m] * fs + (long)k * pitch + c];
+    }
+  }
+  double pr[4] = {0.0, 0.0, 0.0, 0.0};
+  int ns[4];
+  err |= orc_sediment_column(q, n, rho, dz, nlev, dt, pr, ns);
+  for (int k = 0; k < nlev; ++k)
+    for (int m = 0; m < 4; ++m) {
+      fld[qf[m] * fs + (long)k * pitch + c] = q[m * nlev + k];
+      fld[nf[m] * fs + (long)k * pitch + c] = n[m * nlev + k];
+    }
+  for (int m = 0; m < 4; ++m) {
+    precip[m * pitch + c] += pr[m];
+    if (nsub) nsub[m * pitch + c] = ns[m];
+  }
+  free(buf);
+  for (int k = 0; k < nlev; ++k)
+    for (int f = 0; f < ORC_NPROG; ++f)
+      if (!isfinite(fld[f * fs + (long)k * pitch + c])) err |= ORC_ERR_NONFINITE;
+  return err;
+}
+
+unsigned orc_step(double *fld, long pitch, int ncols, int nlev, const double *dz,
+                  double *precip, int *nsub, double dt, int nthreads) {
+  unsigned err = 0;
+  if (nlev <= 0 || ncols <= 0) return 0;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(guided) num_threads(nthreads) reduction(| : err)
+#endif
+  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, nsub, dt);
+  (void)nthreads;
+  return err;
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* -------------------------------------------------------- parameter table */
+double orc_param(const char *name) {
+  const struct { const char *n; double v; } tab[] = {
+    {"T0", T0}, {"cp", CP}, {"Lv", LV}, {"Lf", LF}, {"Rd", RD}, {"Rv", RV},
+    {"g", GRAV}, {"rho_w", RHOW}, {"rho0", RHO0}, {"Ka", KA}, {"Dv", DV},
+    {"mu_air", MUAIR}, {"q_min", QMIN}, {"T_nuc", TNUC}, {"m_i0", MI0}, {"r_r0", RR0},
+    {"kk_aut", KK_AUT}, {"kk_aut_qc", KK_AUT_QC}, {"kk_aut_nc", KK_AUT_NC}, {"nc_min_cm3", NC_MIN_CM3},
+    {"kk_acc", KK_ACC}, {"kk_acc_exp", KK_ACC_EXP}, {"kc_sb", KC_SB}, {"nu_c", NU_C}, {"kr_sb", KR_SB},
+    {"mey_a", MEY_A}, {"mey_b", MEY_B}, {"mey_c", MEY_C}, {"arg_rm", ARG_RM},
+    {"arg_sigma", ARG_SIGMA}, {"arg_kappa", ARG_KAPPA}, {"surft", SURFT}, {"Mw", MW},
+    {"Ma", MA}, {"Rgas", RGAS}, {"e_rim", E_RIM}, {"c_max", CMAX},
+    {"es_l0", ES_L0}, {"es_la", ES_LA}, {"es_lb", ES_LB},
+    {"es_i0", ES_I0}, {"es_ia", ES_IA}, {"es_it", ES_IT}, {"es_ib", ES_IB},
+  };
+
+  for (size_t i = 0; i < sizeof(tab) / sizeof(tab[0]); ++i)
+    if (strcmp(tab[i].n, name) == 0) return tab[i].v;
+  /* species parameters: "<field>_<c|r|i|s|g>" */
+  static const char *fn[] = {"a", "b", "mu", "cv", "dv", "vmax", "dmin", "dmax", "ccap"};
+  static const char sc[] = "crisg";
+  for (int s = 0; s < ORC_NSPECIES; ++s)
+    for (int f = 0; f < 9; ++f) {
+      char buf[16];
+      size_t l = strlen(fn[f]);
+      memcpy(buf, fn[f], l);
+      buf[l] = '_';
+      buf[l + 1] = sc[s];
+      buf[l + 2] = 0;
+      if (strcmp(buf, name) == 0) {
+        const double *v = &SP[s].a;
+        return v[f];
+      }
+    }
+  return NAN;
+}

@@ -1,0 +1,80 @@
+/*
+ * FP64 CPU oracle of the column microphysics step -- TEST INFRASTRUCTURE.
+ *
+ * Only the tests, the package's smoke check and the benchmark's CPU-baseline
+ * leg may load this library.  It shares no code with the CUDA path: it has
+ * its own constants, its own formulas and its own layout handling.
+ *
+ * The step it defines (Section 2: independent columns, processes limited to
+ * the vertical; Section 3.2: one column handled sequentially per call):
+ *   a2 saturation adjustment -> a3 aerosol activation -> a4..a9 process rates
+ *   -> a10 positivity/conservation limiter and forward-Euler update
+ *   -> a12 CFL-substepped flux-form sedimentation.
+ * The paper names these processes but prints no equations; every rate law
+ * below follows a named published parameterisation, listed in casim_oracle.c.
+ */
+#ifndef CASIM_ORACLE_H
+#define CASIM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Field order of the state (identical meaning to the product's state). */
+enum {
+  ORC_T = 0, ORC_QV, ORC_QC, ORC_QR, ORC_QI, ORC_QS, ORC_QG,
+  ORC_NC, ORC_NR, ORC_NI, ORC_NS, ORC_NG, ORC_NA,
+  ORC_P, ORC_RHO, ORC_W, ORC_NFIELDS
+};
+#define ORC_NPROG 13
+
+/* Hydrometeor species index. */
+enum { ORC_C = 0, ORC_R, ORC_I, ORC_S, ORC_G, ORC_NSPECIES };
+
+/* Process index (a4..a9). */
+enum {
+  ORC_AUT = 0, ORC_ACC, ORC_SCC, ORC_SCR, ORC_EVR, ORC_NUC,
+  ORC_DEPI, ORC_DEPS, ORC_DEPG, ORC_RIMS, ORC_RIMG,
+  ORC_MLTI, ORC_MLTS, ORC_MLTG, ORC_NPROC
+};
+
+/* Error bits returned by orc_step. */
+#define ORC_ERR_NONFINITE 1u
+#define ORC_ERR_CFL 2u
+#define ORC_NSUB_MAX 64
+
+double orc_es_liq(double T);
+double orc_es_ice(double T);
+double orc_qsat(double es, double p);
+double orc_dqsat_liq_dT(double T, double p);
+void   orc_satadj(double p, double *T, double *qv, double *qc);
+double orc_arg_sm(double T);
+double orc_arg_smax(double N, double w, double T, double p);
+double orc_arg_nact(double N, double w, double T, double p);
+double orc_lambda(int sp, double q, double n);
+double orc_moment(int sp, double rho, double q, double lam, double k);
+double orc_vent_integral(int sp, double rho, double q, double lam);
+double orc_vq(int sp, double rho, double lam);
+double orc_vn(int sp, double rho, double lam);
+/* Raw process rates (before the limiter) at one point, from its state after
+   adjustment and activation.  rates[ORC_NPROC]; see casim_oracle.c for signs. */
+void   orc_rates(const double *st, double dt, double *rates);
+/* a2..a10 at one point: in[ORC_NFIELDS] -> out[ORC_NPROG]. */
+void   orc_point(const double *in, double dt, double *out);
+/* a12 for one column: q,n are [4][nlev] (r,i,s,g), updated in place;
+   precip[4] accumulates (kg m^-2); nsub[4] receives the substep counts. */
+unsigned orc_sediment_column(double *q, double *n, const double *rho, const double *dz,
+                             int nlev, double dt, double *precip, int *nsub);
+/* One full step over a domain.  fld is [ORC_NFIELDS][nlev][pitch] (column
+   fastest), updated in place; precip is [4][pitch], accumulated; nsub (may be
+   NULL) is [4][pitch].  nthreads <= 0 uses the OpenMP default. */
+unsigned orc_step(double *fld, long pitch, int ncols, int nlev, const double *dz,
+                  double *precip, int *nsub, double dt, int nthreads);
+/* Parameter lookup by name for the tests (returns NaN for an unknown name). */
+double orc_param(const char *name);
+int    orc_max_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
