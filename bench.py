@@ -1,0 +1,302 @@
+"""Throughput of the column-microphysics step on GB300.
+
+Default workload: deep convection, 512x512 columns x 150 stretched levels
+(39.3 M grid points), dt = 1 s, mixed FP32/FP64 form; the plain FP64 form is
+timed on the same workload for the mixed-vs-FP64 comparison.  One bench step
+is one model timestep over the whole domain (one launch of the step kernel),
+with the state resident in HBM.  The state (5 GB) is far larger than L2, so
+no flush is needed between steps.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point updates/s: mixed-precision vs plain FP64, same GB300, at stated error"
+UNIT = "grid-point updates/s"
+WORKLOAD = "deep_512x512x150"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(recipe_fld, dz, ncols_total, dt, target_s=10.0, max_cols=None):
+    """Time the FP64 oracle (as it stands) on host cores over a bounded sample
+    of columns of the same workload; returns (points/s, cores, sample text)."""
+    import oracle
+    nthreads = os.cpu_count() or 1
+    fld, nlev = recipe_fld, recipe_fld.shape[1]
+    cols = 256
+    while True:
+        cols = min(cols, ncols_total if max_cols is None else min(ncols_total, max_cols))
+        sub = np.ascontiguousarray(fld[:, :, :cols])
+        pitch = cols
+        if pitch % 32:
+            pad = np.zeros((16, nlev, (pitch + 31) // 32 * 32))
+            pad[:, :, :cols] = sub
+            sub = pad
+        t0 = time.perf_counter()
+        oracle.step(sub, cols, dz, dt, nthreads=nthreads)
+        el = time.perf_counter() - t0
+        if el >= target_s * 0.5 or cols >= ncols_total or (max_cols and cols >= max_cols):
+            return cols * nlev / el, nthreads, f"{cols} columns x {nlev} levels, 1 step, {el:.1f} s", el
+        cols = int(cols * min(16.0, max(2.0, target_s / max(el, 1e-3))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--ncols", type=int, default=None, help="override the workload's column count")
+    ap.add_argument("--forms", default="mixed,fp64", help="forms to time: mixed and/or fp64")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2010_14823_gb300 import synth
+    base_fld, dz, ncols, nlev, dt, _ = synth.workload(args.workload, ncols=args.ncols, seed=1236 + rank)
+    forms = set(args.forms.split(","))
+    npts = ncols * nlev
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        rates = []
+        sample = ""
+        cores = os.cpu_count()
+        for i in range(args.warmup + args.steps):
+            r, cores, sample, el = cpu_oracle_rate(base_fld, dz, ncols, dt, target_s=2.0, max_cols=4096)
+            if i >= args.warmup:
+                rates.append(r)
+        v = float(np.mean(rates))
+        line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": npts / v * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "impl": "reference",
+                "config": {"workload": args.workload, "ncols": ncols, "nlev": nlev, "dt_s": dt,
+                           "form": "FP64 CPU oracle, OpenMP over columns (schedule guided)"},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    from paper_2010_14823_gb300 import casim
+    casim.lib()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream()
+    dom = casim.Domain(base_fld, dz, ncols)
+    fld0 = dom.fld.clone()
+
+    def time_form(precision, steps, warmup):
+        ctx = casim.casim_init(precision=precision)
+        dom.fld.copy_(fld0)
+        dom.precip.zero_()
+        for _ in range(warmup):
+            casim.casim_step(ctx, dom.state, ncols, nlev, dt, stream)
+        rc, fl = casim.casim_get_error(ctx, stream)
+        assert rc == 0, (rc, fl)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        n0 = casim.casim_launch_count(ctx)
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(steps):
+            evs[i][0].record(stream)
+            casim.casim_step(ctx, dom.state, ncols, nlev, dt, stream)
+            evs[i][1].record(stream)
+        t_end.record(stream)
+        barrier()
+        launches = casim.casim_launch_count(ctx) - n0
+        total_ms = t_start.elapsed_time(t_end)
+        per = [a.elapsed_time(b) for a, b in evs]
+        rc, fl = casim.casim_get_error(ctx, stream)
+        assert rc == 0, (rc, fl)
+        casim.casim_free(ctx)
+        return total_ms, per, launches
+
+    # algorithmic bytes: 16 fields read per point; 13 written per point the step changes
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED)
+    before = dom.fld[:13].clone()
+    casim.casim_step(ctx, dom.state, ncols, nlev, dt, stream)
+    torch.cuda.synchronize()
+    changed = int((dom.fld[:13] != before).any(dim=0)[:, :ncols].sum().item())
+    del before
+    casim.casim_free(ctx)
+
+    value = fp64_value = None
+    mix_ms = fp_ms = None
+    launches = 0
+    clocks = None
+    mix_per = [float("nan")]
+    if "mixed" in forms:
+        sampler = ClockSampler(local)
+        sampler.start()
+        mix_ms, mix_per, launches = time_form(casim.CASIM_MIXED, args.steps, args.warmup)
+        clocks = sampler.stop()
+        mix_ms = max_over_ranks(mix_ms)
+        value = world * npts * args.steps / (mix_ms * 1e-3)
+    if "fp64" in forms and args.fp64_steps > 0:
+        fp_ms, fp_per, fp_launches = time_form(casim.CASIM_FP64, args.fp64_steps, 1)
+        fp_ms = max_over_ranks(fp_ms)
+        fp64_value = world * npts * args.fp64_steps / (fp_ms * 1e-3)
+        if value is None:
+            value, launches, mix_ms, args.steps = fp64_value, fp_launches, fp_ms, args.fp64_steps
+
+    # end to end through the host entry point: pinned host state, copies inside the timed region
+    e2e = None
+    if args.e2e_steps > 0:
+        pitch = dom.pitch
+        hfld = torch.from_numpy(base_fld).pin_memory()
+        hdz = torch.from_numpy(dz).pin_memory()
+        hpr = torch.zeros((4, pitch), dtype=torch.float64).pin_memory()
+        hstate = casim.make_state(hfld.data_ptr(), pitch, hdz.data_ptr(), hpr.data_ptr())
+        ctx = casim.casim_init(precision=casim.CASIM_MIXED if "mixed" in forms else casim.CASIM_FP64)
+        casim.casim_step_host(ctx, hstate, ncols, nlev, dt, stream)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            casim.casim_step_host(ctx, hstate, ncols, nlev, dt, stream)
+        barrier()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        casim.casim_free(ctx)
+        h2d = hfld.numel() * 8 + hdz.numel() * 8 + hpr.numel() * 8
+        d2h = 13 * nlev * pitch * 8 + hpr.numel() * 8
+        e2e = {"value": world * npts * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+               "path": "casim_step_host: pinned host state, H2D + step + D2H per step"}
+
+    peaks = _peaks()
+    peak = peaks.get("hbm_gbs")
+    alg_bytes = 128.0 * npts + 104.0 * changed
+    kern_ms = float(np.mean(mix_per))
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "kernel": "k_step<PolicyMix>", "algorithmic_bytes_per_launch": alg_bytes,
+                "changed_points_frac": changed / npts, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, cores, sample, _ = cpu_oracle_rate(base_fld, dz, ncols, dt, target_s=12.0)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        cfg = {"workload": args.workload, "ncols": ncols, "nlev": nlev, "dt_s": dt,
+               "form": "mixed FP32 rates / FP64 state and transfers" if "mixed" in forms else "FP64",
+               "l2": "state 5 GB > L2, no flush needed",
+               "parallelism": f"{world} independent domain(s), one per GPU"}
+        if fp64_value is not None:
+            cfg.update({"fp64_value": fp64_value, "fp64_ms_per_step": fp_ms / args.fp64_steps,
+                        "speedup_mixed_vs_fp64": value / fp64_value})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": mix_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if "mixed" in forms else "f64", "data": "synthetic",
+                "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

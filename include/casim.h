@@ -1,0 +1,156 @@
+/*
+ * casim.h -- C ABI of the GB300 column-microphysics step.
+ *
+ * The step advances independent atmospheric columns through one model
+ * timestep of a bulk, double-moment cloud-microphysics scheme: saturation
+ * adjustment, aerosol activation, warm-rain and ice process rates, a
+ * positivity/conservation limiter, and CFL-substepped flux-form
+ * sedimentation.  The paper (Brown et al., "Porting the microphysics model
+ * CASIM to GPU and KNL Cray machines", Section 2) defines the structure:
+ * columns are independent, every process acts in the vertical only, and each
+ * hydrometeor carries a gamma-type size distribution.  Its Section 3.2 gives
+ * the host protocol mirrored here: set-up once (initialise_micromain), one
+ * call per timestep that runs the whole scheme for every column
+ * (shipway_microphysics around CASIM()), tear-down (finalise_micromain).
+ *
+ * Conventions for every entry point:
+ *  - All functions return CASIM_OK (0) or a negative CASIM_ERR_* code; they
+ *    never abort the process and no kernel traps.  Device-side problems
+ *    (non-finite results, substep cap reached) set bits in an error word kept
+ *    by the context and read with casim_get_error().
+ *  - Device pointers are plain CUDA device addresses (e.g. from a PyTorch
+ *    tensor); the caller owns them.  `stream` is a cudaStream_t passed as
+ *    void* (NULL = the legacy default stream).  Work is enqueued
+ *    asynchronously on that stream.
+ *  - State layout (level-major structure of arrays, column fastest):
+ *      fld[f * nlev * pitch + k * pitch + c]
+ *    f in [0, CASIM_NFIELDS) in the order of enum casim_field, k = 0 is the
+ *    lowest level, c in [0, ncols).  pitch >= ncols and a multiple of 32;
+ *    fld must be 256-byte aligned.  Columns ncols..pitch-1 are padding: they
+ *    are never written and their contents are ignored.
+ *  - Units: T in K; q* specific contents in kg/kg of moist air; n* numbers
+ *    per kg of air; p in Pa; rho in kg/m^3; w in m/s; dz in m; dt in s;
+ *    precipitation in kg/m^2.
+ */
+#ifndef CASIM_H
+#define CASIM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CASIM_ABI_VERSION 1
+
+enum casim_field {
+  CASIM_T = 0, CASIM_QV, CASIM_QC, CASIM_QR, CASIM_QI, CASIM_QS, CASIM_QG,
+  CASIM_NC, CASIM_NR, CASIM_NI, CASIM_NS, CASIM_NG, CASIM_NA,
+  CASIM_P, CASIM_RHO, CASIM_W,
+  CASIM_NFIELDS
+};
+#define CASIM_NPROG 13      /* fields T..NA are updated in place; p, rho, w are read only */
+#define CASIM_NPRECIP 4     /* surface accumulators: rain, ice, snow, graupel */
+#define CASIM_NSUB_MAX 64   /* sedimentation substep cap per column and species */
+
+/* precision forms */
+enum casim_precision {
+  CASIM_FP64 = 0,   /* every operation in FP64 */
+  CASIM_MIXED = 1   /* rates, fall speeds, special functions in FP32; FP64 for the
+                       state, the vapour difference of saturation adjustment and
+                       every mass transfer applied by the limiter */
+};
+
+/* return codes */
+enum casim_status {
+  CASIM_OK = 0,
+  CASIM_ERR_ARG = -1,        /* invalid argument (null pointer, size, alignment) */
+  CASIM_ERR_OOM = -2,        /* device allocation failed */
+  CASIM_ERR_CUDA = -3,       /* a CUDA call failed (see casim_last_cuda_error) */
+  CASIM_ERR_NONFINITE = -4,  /* casim_get_error: a non-finite value was produced */
+  CASIM_ERR_CFL = -5         /* casim_get_error: substep cap reached in sedimentation */
+};
+
+/* device error-word bits (casim_get_error) */
+#define CASIM_EFLAG_NONFINITE 1u
+#define CASIM_EFLAG_CFL 2u
+
+/* Scheme parameters.  casim_default_params() fills the published values the
+   scheme is defined with; callers may change them before casim_init(). */
+typedef struct {
+  double T0, cp, Lv, Lf, Rd, Rv, g, rho_w, rho0, Ka, Dv, mu_air;
+  double q_min;              /* species present iff q > q_min */
+  double T_nuc, m_i0, r_r0;  /* nucleation threshold (K), crystal mass (kg), new-drop radius (m) */
+  double kk_aut, kk_aut_qc, kk_aut_nc, nc_min_cm3, kk_acc, kk_acc_exp;
+  double kc_sb, nu_c, kr_sb;
+  double mey_a, mey_b, mey_c;
+  double arg_rm, arg_sigma, arg_kappa, surft, Mw, Ma, Rgas;
+  double e_rim, c_max;
+  double es_l0, es_la, es_lb, es_i0, es_ia, es_it, es_ib;
+  /* per species c, r, i, s, g: m(D) = a D^b; gamma shape mu; V(D) = cv D^dv
+     (rho0/rho)^0.4 capped at vmax; mean diameter kept in [dmin, dmax];
+     capacitance ccap * D */
+  double a[5], b[5], mu[5], cv[5], dv[5], vmax[5], dmin[5], dmax[5], ccap[5];
+} casim_params;
+
+/* Caller-owned device state of one domain. */
+typedef struct {
+  double *fld;          /* [CASIM_NFIELDS][nlev][pitch], 256-byte aligned */
+  long long pitch;      /* >= ncols, multiple of 32 */
+  const double *dz;     /* [nlev] layer thickness, k = 0 lowest */
+  double *precip;       /* [CASIM_NPRECIP][pitch] accumulated surface precipitation */
+} casim_state;
+
+typedef struct casim_ctx casim_ctx;
+
+/* Fill *p with the default scheme parameters.  Returns CASIM_ERR_ARG if p is NULL. */
+int casim_default_params(casim_params *p);
+
+/* Create a context on the current CUDA device (Section 3.2: the one-off
+   set-up that copies constants and allocates device memory).  `params` may be
+   NULL for the defaults; `precision` is a casim_precision; `flags` must be 0.
+   Allocates a small device error word.  On failure *ctx is set to NULL. */
+int casim_init(casim_ctx **ctx, const casim_params *params, int precision, int flags);
+
+/* Advance every column of one domain by one timestep dt, in place
+   (Section 3.2: the per-timestep call running the whole scheme on the GPU).
+   ncols >= 0 (0 is a no-op), 1 <= nlev, dt > 0.  Updates the 13 prognostic
+   fields and adds the step's surface precipitation to s->precip.  Reads
+   s->dz on the device.  Asynchronous on `stream`. */
+int casim_step(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream);
+
+/* Same step for a domain held in HOST memory (any host allocation; pinned
+   memory copies faster): copies fld, dz and precip to device buffers owned by
+   the context, runs casim_step, copies the 13 prognostic fields and precip
+   back, and waits for the stream.  The state layout is the device one, with
+   host pointers.  Device buffers grow to the largest domain seen and are
+   freed by casim_free. */
+int casim_step_host(casim_ctx *ctx, const casim_state *host, int ncols, int nlev, double dt,
+                    void *stream);
+
+/* Per-column FP64 budget sums, written to out[2][ncols] (device):
+   out[0][c] = sum_k rho dz (qv+qc+qr+qi+qs+qg)   (kg/m^2)
+   out[1][c] = sum_k rho dz (nc + na)              (aerosol + droplets, m^-2)
+   Asynchronous on `stream`. */
+int casim_budget(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double *out, void *stream);
+
+/* Wait for `stream`, read and clear the device error word.  *flags receives the
+   CASIM_EFLAG_* bits (may be NULL).  Returns CASIM_OK, CASIM_ERR_NONFINITE or
+   CASIM_ERR_CFL (the first set, in that order of precedence), or CASIM_ERR_CUDA. */
+int casim_get_error(casim_ctx *ctx, unsigned *flags, void *stream);
+
+/* Number of kernel launches this context has enqueued since casim_init. */
+long long casim_launch_count(const casim_ctx *ctx);
+
+/* The last CUDA error string seen by this library (static storage). */
+const char *casim_last_cuda_error(void);
+
+/* Release the context and its device memory (waits for the device). NULL is a no-op. */
+void casim_free(casim_ctx *ctx);
+
+int casim_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

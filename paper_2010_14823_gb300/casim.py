@@ -1,0 +1,197 @@
+"""Python binding of the C ABI in include/casim.h (ctypes; marshalling only).
+
+Each function has the C entry point's name and forwards its arguments: torch
+CUDA tensors are passed as device pointers, torch streams as cudaStream_t.
+Every step of the computation runs in libcasim.so; there is no fallback.  If
+the library has not been built, loading fails with an error naming the
+build command.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from .build import LIB, INCLUDE
+
+CASIM_FP64 = 0
+CASIM_MIXED = 1
+NFIELDS = 16
+NPROG = 13
+NPRECIP = 4
+NSUB_MAX = 64
+EFLAG_NONFINITE = 1
+EFLAG_CFL = 2
+_ERRORS = {-1: "CASIM_ERR_ARG", -2: "CASIM_ERR_OOM", -3: "CASIM_ERR_CUDA",
+           -4: "CASIM_ERR_NONFINITE", -5: "CASIM_ERR_CFL"}
+
+
+class CasimError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {_ERRORS.get(code, code)}{(' (' + detail + ')') if detail else ''}")
+
+
+_D = ctypes.c_double
+_SCALARS = ("T0 cp Lv Lf Rd Rv g rho_w rho0 Ka Dv mu_air q_min T_nuc m_i0 r_r0 kk_aut kk_aut_qc kk_aut_nc "
+            "nc_min_cm3 kk_acc kk_acc_exp kc_sb nu_c kr_sb mey_a mey_b mey_c arg_rm arg_sigma arg_kappa surft "
+            "Mw Ma Rgas e_rim c_max es_l0 es_la es_lb es_i0 es_ia es_it es_ib").split()
+_ARRAYS = "a b mu cv dv vmax dmin dmax ccap".split()
+
+
+class casim_params(ctypes.Structure):
+    _fields_ = [(n, _D) for n in _SCALARS] + [(n, _D * 5) for n in _ARRAYS]
+
+    def as_dict(self) -> dict:
+        d = {n: getattr(self, n) for n in _SCALARS}
+        for n in _ARRAYS:
+            d[n] = list(getattr(self, n))
+        return d
+
+
+class casim_state(ctypes.Structure):
+    _fields_ = [("fld", ctypes.c_void_p), ("pitch", ctypes.c_longlong),
+                ("dz", ctypes.c_void_p), ("precip", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libcasim.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB)
+        vp, i, d, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint
+        ps = ctypes.POINTER(casim_state)
+        L.casim_default_params.argtypes = [ctypes.POINTER(casim_params)]
+        L.casim_default_params.restype = i
+        L.casim_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(casim_params), i, i]
+        L.casim_init.restype = i
+        L.casim_step.argtypes = [vp, ps, i, i, d, vp]
+        L.casim_step.restype = i
+        L.casim_step_host.argtypes = [vp, ps, i, i, d, vp]
+        L.casim_step_host.restype = i
+        L.casim_budget.argtypes = [vp, ps, i, i, vp, vp]
+        L.casim_budget.restype = i
+        L.casim_get_error.argtypes = [vp, ctypes.POINTER(u), vp]
+        L.casim_get_error.restype = i
+        L.casim_launch_count.argtypes = [vp]
+        L.casim_launch_count.restype = ctypes.c_longlong
+        L.casim_last_cuda_error.argtypes = []
+        L.casim_last_cuda_error.restype = ctypes.c_char_p
+        L.casim_free.argtypes = [vp]
+        L.casim_free.restype = None
+        L.casim_abi_version.argtypes = []
+        L.casim_abi_version.restype = i
+        _lib = L
+    return _lib
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions declared in include/*.h."""
+    names = []
+    for f in sorted(os.listdir(INCLUDE)):
+        if f.endswith(".h"):
+            text = open(os.path.join(INCLUDE, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w \*]*?\b(casim_\w+)\s*\(", text, flags=re.M)
+    return names
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        detail = lib().casim_last_cuda_error().decode() if rc == -3 else ""
+        raise CasimError(rc, where, detail)
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()   # torch tensor
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def casim_default_params() -> casim_params:
+    p = casim_params()
+    _check(lib().casim_default_params(ctypes.byref(p)), "casim_default_params")
+    return p
+
+
+def casim_init(params: casim_params | None = None, precision: int = CASIM_FP64, flags: int = 0):
+    ctx = ctypes.c_void_p()
+    _check(lib().casim_init(ctypes.byref(ctx), ctypes.byref(params) if params is not None else None,
+                            precision, flags), "casim_init")
+    return ctx
+
+
+def make_state(fld, pitch: int, dz, precip) -> casim_state:
+    return casim_state(_ptr(fld), int(pitch), _ptr(dz), _ptr(precip))
+
+
+def casim_step(ctx, state: casim_state, ncols: int, nlev: int, dt: float, stream=None):
+    _check(lib().casim_step(ctx, ctypes.byref(state), ncols, nlev, dt, _stream(stream)), "casim_step")
+
+
+def casim_step_host(ctx, state: casim_state, ncols: int, nlev: int, dt: float, stream=None):
+    _check(lib().casim_step_host(ctx, ctypes.byref(state), ncols, nlev, dt, _stream(stream)), "casim_step_host")
+
+
+def casim_budget(ctx, state: casim_state, ncols: int, nlev: int, out, stream=None):
+    _check(lib().casim_budget(ctx, ctypes.byref(state), ncols, nlev, _ptr(out), _stream(stream)), "casim_budget")
+
+
+def casim_get_error(ctx, stream=None) -> tuple[int, int]:
+    """Returns (status, flags); status is 0 or a negative CASIM_ERR_* code."""
+    f = ctypes.c_uint(0)
+    rc = lib().casim_get_error(ctx, ctypes.byref(f), _stream(stream))
+    if rc == -3:
+        _check(rc, "casim_get_error")
+    return rc, f.value
+
+
+def casim_launch_count(ctx) -> int:
+    return lib().casim_launch_count(ctx)
+
+
+def casim_free(ctx):
+    lib().casim_free(ctx)
+
+
+def casim_abi_version() -> int:
+    return lib().casim_abi_version()
+
+
+class Domain:
+    """A domain's device state as torch tensors, in the layout of include/casim.h."""
+
+    def __init__(self, fld: np.ndarray, dz: np.ndarray, ncols: int, device="cuda"):
+        import torch
+        nf, nlev, pitch = fld.shape
+        assert nf == NFIELDS and pitch % 32 == 0 and pitch >= ncols
+        self.ncols, self.nlev, self.pitch = ncols, nlev, pitch
+        self.fld = torch.from_numpy(np.ascontiguousarray(fld)).to(device)
+        assert self.fld.data_ptr() % 256 == 0
+        self.dz = torch.from_numpy(np.ascontiguousarray(dz, dtype=np.float64)).to(device)
+        self.precip = torch.zeros((NPRECIP, pitch), dtype=torch.float64, device=device)
+        self.state = make_state(self.fld, pitch, self.dz, self.precip)
+
+    def numpy(self):
+        return self.fld.cpu().numpy(), self.precip.cpu().numpy()

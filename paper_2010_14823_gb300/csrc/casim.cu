@@ -1,0 +1,304 @@
+// Host side of the C ABI declared in include/casim.h.
+//
+// The library owns no state memory: the caller passes device pointers (for
+// instance PyTorch tensors) and a stream.  A context carries the derived
+// scheme constants, the precision form, a device error word and, for
+// casim_step_host only, staging buffers.  Mirrors the paper's host protocol
+// (Section 3.2): one-off set-up, one asynchronous call per timestep running
+// the whole scheme for every column, tear-down.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <cstdint>
+
+#include "casim.h"
+#include "casim_device.cuh"
+
+using namespace casim_dev;
+
+struct casim_ctx {
+  int precision = CASIM_FP64;
+  int device = 0;
+  KParams kp;
+  unsigned *d_err = nullptr;
+  long long launches = 0;
+  // staging for casim_step_host
+  double *h2d_fld = nullptr, *h2d_dz = nullptr, *h2d_precip = nullptr;
+  size_t cap_fld = 0, cap_dz = 0, cap_precip = 0;
+};
+
+static thread_local char g_last_error[256] = "";
+
+static int cuda_fail(cudaError_t e, const char *what) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+  return CASIM_ERR_CUDA;
+}
+#define CUDA_TRY(x)                                   \
+  do {                                                \
+    cudaError_t e_ = (x);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x);  \
+  } while (0)
+
+extern "C" int casim_abi_version(void) { return CASIM_ABI_VERSION; }
+
+extern "C" const char *casim_last_cuda_error(void) { return g_last_error; }
+
+extern "C" int casim_default_params(casim_params *p) {
+  if (!p) return CASIM_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  // thermodynamic constants
+  p->T0 = 273.15; p->cp = 1005.0; p->Lv = 2.5e6; p->Lf = 3.34e5; p->Rd = 287.04; p->Rv = 461.5;
+  p->g = 9.81; p->rho_w = 1000.0; p->rho0 = 1.2; p->Ka = 2.4e-2; p->Dv = 2.26e-5; p->mu_air = 1.72e-5;
+  p->q_min = 1e-14; p->T_nuc = 268.15; p->m_i0 = 1e-12; p->r_r0 = 25e-6;
+  // Khairoutdinov & Kogan (2000)
+  p->kk_aut = 1350.0; p->kk_aut_qc = 2.47; p->kk_aut_nc = -1.79; p->nc_min_cm3 = 1.0;
+  p->kk_acc = 67.0; p->kk_acc_exp = 1.15;
+  // Seifert & Beheng (2001, 2006)
+  p->kc_sb = 9.44e9; p->nu_c = 1.0; p->kr_sb = 5.78;
+  // Meyers et al. (1992)
+  p->mey_a = 1e3; p->mey_b = -0.639; p->mey_c = 12.96;
+  // Abdul-Razzak & Ghan (2000), one ammonium-sulphate-like mode
+  p->arg_rm = 0.05e-6; p->arg_sigma = 1.5; p->arg_kappa = 0.61; p->surft = 0.0761;
+  p->Mw = 0.018015; p->Ma = 0.028965; p->Rgas = 8.314;
+  p->e_rim = 1.0; p->c_max = 1.0;
+  // Bolton (1980) over liquid, Murray (1967) over ice
+  p->es_l0 = 611.2; p->es_la = 17.67; p->es_lb = 243.5;
+  p->es_i0 = 610.78; p->es_ia = 21.875; p->es_it = 273.16; p->es_ib = 7.66;
+  const double pi = 3.14159265358979323846;
+  //                  cloud             rain              ice              snow             graupel
+  const double a[5] = {pi / 6 * 1000.0, pi / 6 * 1000.0, pi / 6 * 500.0, pi / 6 * 100.0, pi / 6 * 400.0};
+  const double mu[5] = {2.0, 0.0, 0.0, 0.0, 0.5};
+  const double cv[5] = {0.0, 130.0, 700.0, 11.72, 19.3};
+  const double dv[5] = {0.0, 0.5, 1.0, 0.41, 0.37};
+  const double vmax[5] = {0.0, 10.0, 2.0, 4.0, 10.0};
+  const double dmin[5] = {1e-6, 50e-6, 1e-6, 10e-6, 10e-6};
+  const double dmax[5] = {1e-4, 5e-3, 500e-6, 5e-3, 5e-3};
+  const double ccap[5] = {0.5, 0.5, 0.5, 1.0 / pi, 0.5};
+  for (int x = 0; x < 5; ++x) {
+    p->a[x] = a[x]; p->b[x] = 3.0; p->mu[x] = mu[x]; p->cv[x] = cv[x]; p->dv[x] = dv[x];
+    p->vmax[x] = vmax[x]; p->dmin[x] = dmin[x]; p->dmax[x] = dmax[x]; p->ccap[x] = ccap[x];
+  }
+  return CASIM_OK;
+}
+
+// Derived constants.  `l` is the logarithm the policy works in (natural log
+// for FP64, log2 for the mixed form, whose special functions run on ex2/lg2).
+template <class R>
+static void derive(const casim_params &p, ConstK<R> &K, double (*l)(double)) {
+  const double pi = 3.14159265358979323846;
+  const double Ls = p.Lv + p.Lf;
+  const double eps = p.Rd / p.Rv;
+  K.T0 = (R)p.T0; K.Tnuc = (R)p.T_nuc; K.qmin = (R)p.q_min;
+  K.t0_esit = (R)(p.T0 - p.es_it); K.t0_esib = (R)(p.T0 - p.es_ib);
+  K.lv_cp = (R)(p.Lv / p.cp); K.cp_lv = (R)(p.cp / p.Lv); K.cp = (R)p.cp; K.inv_cp = (R)(1.0 / p.cp);
+  K.lv = (R)p.Lv; K.ls = (R)Ls; K.lf = (R)p.Lf;
+  K.eps = (R)eps; K.ome = (R)(1.0 - eps);
+  K.esl0 = (R)p.es_l0; K.esla = (R)p.es_la; K.eslb = (R)p.es_lb; K.eslab = (R)(p.es_la * p.es_lb);
+  K.esi0 = (R)p.es_i0; K.esia = (R)p.es_ia; K.esit = (R)p.es_it; K.esib = (R)p.es_ib;
+  K.awc = (R)(p.Lv * p.Lv / (p.Ka * p.Rv));
+  K.aic = (R)(Ls * Ls / (p.Ka * p.Rv));
+  K.rv_dv = (R)(p.Rv / p.Dv);
+  K.akel = (R)(2.0 * p.surft * p.Mw / (p.rho_w * p.Rgas));
+  K.smc = (R)(2.0 / std::sqrt(p.arg_kappa) * std::pow(1.0 / (3.0 * p.arg_rm), 1.5));
+  K.al1 = (R)(p.g * p.Mw * p.Lv / (p.cp * p.Rgas));
+  K.al2 = (R)(p.g * p.Ma / p.Rgas);
+  K.ga1 = (R)(p.Rgas / p.Mw);
+  K.ga2 = (R)(p.Mw * p.Lv * p.Lv / (p.cp * p.Ma));
+  K.gg1 = (R)(p.rho_w * p.Rgas / (p.Dv * p.Mw));
+  K.gg2 = (R)(p.Lv * p.rho_w / p.Ka);
+  K.gg3 = (R)(p.Lv * p.Mw / p.Rgas);
+  const double lns = std::log(p.arg_sigma);
+  K.twopirhow = (R)(2.0 * pi * p.rho_w);
+  K.f1 = (R)(0.5 * std::exp(2.5 * lns * lns));
+  K.f2 = (R)(1.0 + 0.25 * lns);
+  K.uc = (R)(2.0 / (3.0 * std::sqrt(2.0) * lns));
+  K.kk_aut = (R)p.kk_aut; K.kk_aut_qc = (R)p.kk_aut_qc; K.kk_aut_nc = (R)p.kk_aut_nc;
+  K.nc_min = (R)p.nc_min_cm3; K.kk_acc = (R)p.kk_acc; K.kk_acc_exp = (R)p.kk_acc_exp;
+  K.kcf = (R)(p.kc_sb * (p.nu_c + 2.0) / (p.nu_c + 1.0));
+  K.kr = (R)p.kr_sb;
+  K.inv_mr0 = (R)(1.0 / (4.0 / 3.0 * pi * p.rho_w * p.r_r0 * p.r_r0 * p.r_r0));
+  K.mey_a = (R)p.mey_a; K.mey_b = (R)p.mey_b; K.mey_c = (R)p.mey_c; K.mi0 = (R)p.m_i0;
+  K.mu_air = (R)p.mu_air; K.inv_dv = (R)(1.0 / p.Dv); K.lgrho0 = (R)l(p.rho0); K.twopi = (R)(2.0 * pi);
+  for (int x = 0; x < 5; ++x) {
+    const double a = p.a[x], b = p.b[x], mu = p.mu[x], cv = p.cv[x], dv = p.dv[x];
+    const double gb = std::tgamma(mu + b + 1.0);
+    SpeciesK<R> &S = K.sp[x];
+    S.lglamfac = (R)l(a * gb / std::tgamma(mu + 1.0));
+    S.invb = (R)(1.0 / b);
+    S.lglo = (R)l((mu + 1.0) / p.dmax[x]);
+    S.lghi = (R)l((mu + 1.0) / p.dmin[x]);
+    S.ev1 = (R)(0.78 * std::tgamma(mu + 2.0) / gb / a);
+    S.ex1 = (R)(b - 1.0);
+    const double k2 = 0.5 * (dv + 3.0);
+    S.ev2 = (R)(0.31 * std::sqrt(cv) * std::tgamma(mu + k2 + 1.0) / gb / a);
+    S.ex2 = (R)(b - k2);
+    S.rim = (R)(0.25 * pi * p.e_rim * cv * std::tgamma(mu + dv + 3.0) / gb / a);
+    S.exr = (R)(b - 2.0 - dv);
+    S.vq = (R)(cv * std::tgamma(mu + b + dv + 1.0) / gb);
+    S.vn = (R)(cv * std::tgamma(mu + dv + 1.0) / std::tgamma(mu + 1.0));
+    S.exv = (R)(-dv);
+    S.vmax = (R)p.vmax[x];
+    S.dep = (R)(4.0 * pi * p.ccap[x]);
+    S.mlt = (R)(4.0 * pi * p.ccap[x] * p.Ka / p.Lf);
+  }
+}
+
+static double ln_(double x) { return std::log(x); }
+static double log2_(double x) { return std::log2(x); }
+
+static bool params_ok(const casim_params &p) {
+  if (!(p.cp > 0 && p.Lv > 0 && p.Lf >= 0 && p.Rd > 0 && p.Rv > 0 && p.rho0 > 0 && p.Ka > 0 && p.Dv > 0 &&
+        p.mu_air > 0 && p.q_min > 0 && p.m_i0 > 0 && p.r_r0 > 0 && p.c_max > 0 && p.arg_sigma > 1 &&
+        p.arg_kappa > 0 && p.arg_rm > 0))
+    return false;
+  for (int x = 0; x < 5; ++x)
+    if (!(p.a[x] > 0 && p.b[x] > 0 && p.mu[x] > -1 && p.dmin[x] > 0 && p.dmax[x] > p.dmin[x] && p.cv[x] >= 0 &&
+          p.vmax[x] >= 0))
+      return false;
+  return true;
+}
+
+extern "C" int casim_init(casim_ctx **out, const casim_params *params, int precision, int flags) {
+  if (!out) return CASIM_ERR_ARG;
+  *out = nullptr;
+  if (precision != CASIM_FP64 && precision != CASIM_MIXED) return CASIM_ERR_ARG;
+  if (flags != 0) return CASIM_ERR_ARG;
+  casim_params p;
+  if (params) p = *params;
+  else casim_default_params(&p);
+  if (!params_ok(p)) return CASIM_ERR_ARG;
+  casim_ctx *ctx = new casim_ctx();
+  ctx->precision = precision;
+  derive<double>(p, ctx->kp.d, ln_);
+  derive<float>(p, ctx->kp.f, log2_);
+  ctx->kp.c_max = p.c_max;
+  for (int x = 0; x < 5; ++x) ctx->kp.vmax[x] = p.vmax[x];
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    int rc = e == cudaErrorMemoryAllocation ? CASIM_ERR_OOM : cuda_fail(e, "casim_init");
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return CASIM_OK;
+}
+
+static int check_state(const casim_state *s, int ncols, int nlev, double dt) {
+  if (!s || ncols < 0 || nlev < 1 || nlev > kMaxLev || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
+  if (ncols == 0) return CASIM_OK;
+  if (!s->fld || !s->dz || !s->precip) return CASIM_ERR_ARG;
+  if (s->pitch < ncols || s->pitch % 32 != 0) return CASIM_ERR_ARG;
+  if (((uintptr_t)s->fld) % 256 != 0) return CASIM_ERR_ARG;
+  return CASIM_OK;
+}
+
+static KArgs make_args(const casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt) {
+  KArgs a;
+  a.fld = s->fld;
+  a.pitch = s->pitch;
+  a.dz = s->dz;
+  a.precip = s->precip;
+  a.err = ctx->d_err;
+  a.ncols = ncols;
+  a.nlev = nlev;
+  a.dt = dt;
+  return a;
+}
+
+extern "C" int casim_step(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream) {
+  if (!ctx) return CASIM_ERR_ARG;
+  int rc = check_state(s, ncols, nlev, dt);
+  if (rc != CASIM_OK || ncols == 0) return rc;
+  const KArgs a = make_args(ctx, s, ncols, nlev, dt);
+  const dim3 grid((unsigned)((ncols + kBlock - 1) / kBlock));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ctx->precision == CASIM_MIXED)
+    k_step<PolicyMix><<<grid, kBlock, 0, st>>>(a, ctx->kp);
+  else
+    k_step<PolicyF64><<<grid, kBlock, 0, st>>>(a, ctx->kp);
+  ctx->launches++;
+  CUDA_TRY(cudaGetLastError());
+  return CASIM_OK;
+}
+
+static int grow(double **buf, size_t *cap, size_t n) {
+  if (*cap >= n) return CASIM_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc(buf, n * sizeof(double));
+  if (e != cudaSuccess) {
+    *buf = nullptr;
+    return e == cudaErrorMemoryAllocation ? CASIM_ERR_OOM : cuda_fail(e, "cudaMalloc");
+  }
+  *cap = n;
+  return CASIM_OK;
+}
+
+extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, int nlev, double dt,
+                               void *stream) {
+  if (!ctx) return CASIM_ERR_ARG;
+  if (!h || ncols < 0 || nlev < 1 || nlev > kMaxLev || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
+  if (ncols == 0) return CASIM_OK;
+  if (!h->fld || !h->dz || !h->precip || h->pitch < ncols || h->pitch % 32 != 0) return CASIM_ERR_ARG;
+  const size_t nf = (size_t)CASIM_NFIELDS * nlev * h->pitch;
+  const size_t np = (size_t)CASIM_NPRECIP * h->pitch;
+  int rc;
+  if ((rc = grow(&ctx->h2d_fld, &ctx->cap_fld, nf)) != CASIM_OK) return rc;
+  if ((rc = grow(&ctx->h2d_dz, &ctx->cap_dz, (size_t)nlev)) != CASIM_OK) return rc;
+  if ((rc = grow(&ctx->h2d_precip, &ctx->cap_precip, np)) != CASIM_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(ctx->h2d_fld, h->fld, nf * sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(ctx->h2d_dz, h->dz, (size_t)nlev * sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(ctx->h2d_precip, h->precip, np * sizeof(double), cudaMemcpyHostToDevice, st));
+  casim_state d;
+  d.fld = ctx->h2d_fld;
+  d.pitch = h->pitch;
+  d.dz = ctx->h2d_dz;
+  d.precip = ctx->h2d_precip;
+  if ((rc = casim_step(ctx, &d, ncols, nlev, dt, stream)) != CASIM_OK) return rc;
+  const size_t nprog = (size_t)CASIM_NPROG * nlev * h->pitch;
+  CUDA_TRY(cudaMemcpyAsync(h->fld, ctx->h2d_fld, nprog * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(h->precip, ctx->h2d_precip, np * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return CASIM_OK;
+}
+
+extern "C" int casim_budget(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double *out, void *stream) {
+  if (!ctx || !out) return CASIM_ERR_ARG;
+  int rc = check_state(s, ncols, nlev, 1.0);
+  if (rc != CASIM_OK || ncols == 0) return rc;
+  const KArgs a = make_args(ctx, s, ncols, nlev, 1.0);
+  k_budget<<<(unsigned)((ncols + 255) / 256), 256, 0, (cudaStream_t)stream>>>(a, out);
+  ctx->launches++;
+  CUDA_TRY(cudaGetLastError());
+  return CASIM_OK;
+}
+
+extern "C" int casim_get_error(casim_ctx *ctx, unsigned *flags, void *stream) {
+  if (!ctx) return CASIM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned h = 0;
+  CUDA_TRY(cudaStreamSynchronize(st));
+  CUDA_TRY(cudaMemcpy(&h, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+  if (flags) *flags = h;
+  if (h & CASIM_EFLAG_NONFINITE) return CASIM_ERR_NONFINITE;
+  if (h & CASIM_EFLAG_CFL) return CASIM_ERR_CFL;
+  return CASIM_OK;
+}
+
+extern "C" long long casim_launch_count(const casim_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+extern "C" void casim_free(casim_ctx *ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->h2d_fld) cudaFree(ctx->h2d_fld);
+  if (ctx->h2d_dz) cudaFree(ctx->h2d_dz);
+  if (ctx->h2d_precip) cudaFree(ctx->h2d_precip);
+  delete ctx;
+}

@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads and exports every declared entry point (no GPU needed)."""
+import ctypes
+
+import pytest
+
+from paper_2010_14823_gb300 import build, casim
+
+import oracle as O
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return casim.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = casim.declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_abi_version(L):
+    assert casim.casim_abi_version() == 1
+
+
+def test_default_params_match_the_oracle(L):
+    p = casim.casim_default_params().as_dict()
+    for k, v in p.items():
+        if isinstance(v, list):
+            for s, x in zip("crisg", v):
+                assert x == O.param(f"{k}_{s}"), (k, s)
+        else:
+            assert v == O.param(k), k
+
+
+def test_argument_errors_without_touching_the_device(L):
+    ctx = ctypes.c_void_p()
+    assert L.casim_init(ctypes.byref(ctx), None, 7, 0) == -1          # bad precision
+    assert L.casim_init(ctypes.byref(ctx), None, 0, 1) == -1          # unknown flag
+    assert not ctx.value
+    st = casim.casim_state(None, 32, None, None)
+    assert L.casim_step(None, ctypes.byref(st), 1, 1, 1.0, None) == -1
+    assert L.casim_get_error(None, None, None) == -1
+    assert L.casim_launch_count(None) == -1
+    L.casim_free(None)
+    bad = casim.casim_default_params()
+    bad.q_min = -1.0
+    assert L.casim_init(ctypes.byref(ctx), ctypes.byref(bad), 0, 0) == -1
+    assert L.casim_default_params(None) == -1

@@ -1,0 +1,238 @@
+"""GPU step vs the FP64 oracle, element by element, through the C ABI.
+
+FP64 form: every prognostic field within 1e-12 relative of the oracle, with
+absolute floors of 1e-20 kg/kg (masses), 1e-6 per kg (numbers), 1e-10 K (T).
+Mixed form: the bound derived from its FP32 arithmetic (see mixed_bound).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2010_14823_gb300 import casim, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F = synth.FIDX
+RTOL64 = 1e-12
+ATOL = np.array([1e-10] + [1e-20] * 6 + [1e-6] * 6)   # T, 6 masses, 6 numbers (incl. n_a)
+
+
+def run_gpu(fld, dz, ncols, dt, nsteps=1, precision=casim.CASIM_FP64, check_err=True):
+    ctx = casim.casim_init(precision=precision)
+    try:
+        d = casim.Domain(fld, dz, ncols)
+        for _ in range(nsteps):
+            casim.casim_step(ctx, d.state, ncols, d.nlev, dt)
+        rc, flags = casim.casim_get_error(ctx)
+        if check_err:
+            assert rc == 0, (rc, flags)
+        out, pr = d.numpy()
+        return out, pr, (rc, flags)
+    finally:
+        casim.casim_free(ctx)
+
+
+def run_oracle(fld, dz, ncols, dt, nsteps=1):
+    ref = fld.copy()
+    pr = np.zeros((4, fld.shape[2]))
+    for _ in range(nsteps):
+        _, _, err = O.step(ref, ncols, dz, dt, precip=pr)
+        assert err == 0
+    return ref, pr
+
+
+def assert_fp64_close(out, pr, ref, pr_ref, ncols, rtol=RTOL64):
+    for f in range(13):
+        a, b = out[f, :, :ncols], ref[f, :, :ncols]
+        err = np.abs(a - b)
+        bad = err > rtol * np.abs(b) + ATOL[f]
+        assert not bad.any(), (synth.FIELDS[f], int(bad.sum()), float(err.max()),
+                               np.argwhere(bad)[:3].tolist())
+    e = np.abs(pr[:, :ncols] - pr_ref[:, :ncols])
+    assert np.all(e <= rtol * np.abs(pr_ref[:, :ncols]) + 1e-20), float(e.max())
+
+
+def test_stratus_16x16x50_fp64():
+    fld, dz, ncols, nlev, dt, nsteps = synth.workload("stratus_16x16x50")
+    out, pr, _ = run_gpu(fld, dz, ncols, dt)
+    ref, pr_ref = run_oracle(fld, dz, ncols, dt)
+    assert_fp64_close(out, pr, ref, pr_ref, ncols)
+    # inputs untouched, padding untouched
+    assert np.array_equal(out[13:], fld[13:])
+
+
+@pytest.mark.parametrize("ncols,nlev", [(1, 50), (33, 17), (200, 1), (97, 150)])
+def test_ragged_sizes_fp64(ncols, nlev):
+    dz = synth.dz_stretched(nlev)
+    fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=100 + ncols)
+    out, pr, _ = run_gpu(fld, dz, ncols, 1.0)
+    ref, pr_ref = run_oracle(fld, dz, ncols, 1.0)
+    assert_fp64_close(out, pr, ref, pr_ref, ncols)
+    assert np.array_equal(out[:, :, ncols:], fld[:, :, ncols:])
+
+
+def test_multistep_deep_convective_fp64():
+    dz = synth.dz_stretched(150)
+    fld = synth.make_state("deep_convective", 256, 150, dz, seed=7)
+    out, pr, _ = run_gpu(fld, dz, 256, 1.0, nsteps=5)
+    ref, pr_ref = run_oracle(fld, dz, 256, 1.0, nsteps=5)
+    assert_fp64_close(out, pr, ref, pr_ref, 256, rtol=1e-11)
+
+
+@pytest.mark.parametrize("dt", [5.0, 30.0])
+def test_substepped_sedimentation_fp64(dt):
+    # dz down to 20 m with dt >= 5 s: capped speeds exceed one level per step,
+    # so columns take the multi-substep path
+    dz = synth.dz_stretched(100)
+    fld = synth.make_state("deep_convective", 160, 100, dz, seed=int(dt))
+    out, pr, _ = run_gpu(fld, dz, 160, dt)
+    ref, pr_ref = run_oracle(fld, dz, 160, dt)
+    assert_fp64_close(out, pr, ref, pr_ref, 160)
+
+
+def test_stratus_256x256x100_sampled_columns_fp64():
+    # full-size GPU run (10 steps); the oracle follows 32 sampled columns
+    fld, dz, ncols, nlev, dt, nsteps = synth.workload("stratus_256x256x100")
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, nsteps=nsteps)
+    cols = np.sort(np.random.default_rng(0).choice(ncols, 32, replace=False))
+    sub = np.zeros((16, nlev, 32))
+    sub[:] = fld[:, :, cols]
+    ref, pr_ref = run_oracle(sub, dz, 32, dt, nsteps=nsteps)
+    assert_fp64_close(out[:, :, cols], pr[:, cols], ref, pr_ref, 32, rtol=1e-11)
+
+
+def test_clear_columns_are_bitwise_unchanged():
+    dz = synth.dz_uniform(40)
+    rc = synth.Recipe(cloud_frac=0.0, T_sfc=300.0, rh_clear=(0.5, 0.8))
+    fld = synth.make_state(rc, 64, 40, dz, seed=3)
+    for prec in (casim.CASIM_FP64, casim.CASIM_MIXED):
+        out, pr, _ = run_gpu(fld, dz, 64, 1.0, precision=prec)
+        assert np.array_equal(out, fld)
+        assert np.all(pr == 0.0)
+
+
+def test_zero_columns_is_a_noop():
+    dz = synth.dz_uniform(10)
+    fld = synth.make_state("stratus", 32, 10, dz, seed=1)
+    ctx = casim.casim_init()
+    try:
+        d = casim.Domain(fld, dz, 32)
+        n0 = casim.casim_launch_count(ctx)
+        casim.casim_step(ctx, d.state, 0, 10, 1.0)
+        assert casim.casim_launch_count(ctx) == n0
+        assert np.array_equal(d.numpy()[0], fld)
+        with pytest.raises(casim.CasimError):
+            casim.casim_step(ctx, d.state, 33, 10, 1.0)      # pitch 32 < ncols
+        with pytest.raises(casim.CasimError):
+            casim.casim_step(ctx, d.state, 32, 10, -1.0)
+        with pytest.raises(casim.CasimError):
+            casim.casim_step(ctx, d.state, 32, 2000, 1.0)    # more levels than supported
+    finally:
+        casim.casim_free(ctx)
+
+
+def test_nonfinite_input_sets_error_flag():
+    dz = synth.dz_uniform(10)
+    fld = synth.make_state("stratus", 32, 10, dz, seed=2)
+    fld[F["qc"], 5, 7] = np.nan
+    for prec in (casim.CASIM_FP64, casim.CASIM_MIXED):
+        _, _, (rc, flags) = run_gpu(fld, dz, 32, 1.0, precision=prec, check_err=False)
+        assert rc == -4 and flags & casim.EFLAG_NONFINITE
+
+
+def test_cfl_cap_sets_error_flag():
+    dz = np.full(20, 1.0)
+    fld = synth.make_state("deep_convective", 32, 20, dz, seed=4)
+    fld[F["qr"], 10, :32] = 1e-3
+    fld[F["nr"], 10, :32] = 1.0       # huge drops at the speed cap: 1000 m in 100 s on 1-m levels
+    _, _, (rc, flags) = run_gpu(fld, dz, 32, 100.0, check_err=False)
+    assert rc == -5 and flags & casim.EFLAG_CFL
+
+
+def test_host_entry_point_matches_device_entry_point():
+    fld, dz, ncols, nlev, dt, _ = synth.workload("stratus_16x16x50")
+    out, pr, _ = run_gpu(fld, dz, ncols, dt)
+    ctx = casim.casim_init()
+    try:
+        h = np.ascontiguousarray(fld.copy())
+        hdz = np.ascontiguousarray(dz)
+        hpr = np.zeros((4, fld.shape[2]))
+        st = casim.make_state(h, fld.shape[2], hdz, hpr)
+        casim.casim_step_host(ctx, st, ncols, nlev, dt, stream=0)
+        assert np.array_equal(h, out)
+        assert np.array_equal(hpr, pr)
+    finally:
+        casim.casim_free(ctx)
+
+
+def test_budget_sums():
+    fld, dz, ncols, nlev, dt, _ = synth.workload("stratus_16x16x50")
+    ctx = casim.casim_init()
+    try:
+        d = casim.Domain(fld, dz, ncols)
+        out = torch.zeros((2, ncols), dtype=torch.float64, device="cuda")
+        casim.casim_budget(ctx, d.state, ncols, nlev, out)
+        got = out.cpu().numpy()
+    finally:
+        casim.casim_free(ctx)
+    m = fld[F["rho"], :, :ncols] * dz[:, None]
+    w = (m * sum(fld[F[x], :, :ncols] for x in ("qv", "qc", "qr", "qi", "qs", "qg"))).sum(0)
+    n = (m * (fld[F["nc"], :, :ncols] + fld[F["na"], :, :ncols])).sum(0)
+    assert np.allclose(got[0], w, rtol=1e-13) and np.allclose(got[1], n, rtol=1e-13)
+
+
+# ------------------------------------------------------------------ mixed
+def mixed_bound(ref, inp, f, qv_ref):
+    """Bound of the mixed form's error against the FP64 oracle for field f.
+
+    Rates and fall speeds run in FP32 with MUFU ex2/lg2 (relative error about
+    2^-22 per call, up to ~10 chained calls) and truncating conversions
+    (2^-23): each increment carries a relative error below ~1e-5.  Saturation
+    adjustment evaluates q_s in FP32 (relative ~1e-6 of q_s), which moves
+    ~1e-6 q_v of vapour between q_v and q_c, and Lv/cp times that in T.  The
+    bound gives a factor of 10-100 over these estimates.
+    """
+    inc = np.abs(ref - inp)
+    if f == 0:
+        return 1e-3 * inc + 2.5e3 * 1e-5 * qv_ref + 1e-6
+    if f in (1, 2):
+        return 1e-3 * inc + 1e-5 * qv_ref + 1e-14
+    if f <= 6:
+        return 1e-3 * inc + 1e-5 * np.abs(ref) + 1e-14
+    # numbers: ice nucleation sets n_i to exp(12.96 (S_i - 1)) scaled; S_i in
+    # FP32 carries ~4e-7 relative error, i.e. ~1e-5 relative in n_i
+    return 1e-3 * inc + 1e-4 * np.abs(ref) + 1e-3
+
+
+@pytest.mark.parametrize("name", ["stratus_16x16x50", "deep"])
+def test_mixed_within_derived_bound(name):
+    if name == "deep":
+        dz = synth.dz_stretched(150)
+        fld = synth.make_state("deep_convective", 512, 150, dz, seed=11)
+        ncols, dt = 512, 1.0
+    else:
+        fld, dz, ncols, nlev, dt, _ = synth.workload(name)
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, precision=casim.CASIM_MIXED)
+    ref, pr_ref = run_oracle(fld, dz, ncols, dt)
+    worst = {}
+    for f in range(13):
+        a, b, i = out[f, :, :ncols], ref[f, :, :ncols], fld[f, :, :ncols]
+        err = np.abs(a - b)
+        bound = mixed_bound(b, i, f, ref[1, :, :ncols])
+        worst[synth.FIELDS[f]] = float((err / np.maximum(bound, 1e-300)).max())
+        assert (err <= bound).all(), (synth.FIELDS[f], float(err.max()), np.argwhere(err > bound)[:3].tolist())
+    print("mixed worst error / bound:", worst)
+
+
+def test_mixed_conserves_water():
+    dz = synth.dz_stretched(150)
+    fld = synth.make_state("deep_convective", 512, 150, dz, seed=12)
+    out, pr, _ = run_gpu(fld, dz, 512, 1.0, nsteps=3, precision=casim.CASIM_MIXED)
+    rho = fld[F["rho"], :, :512]
+    names = ("qv", "qc", "qr", "qi", "qs", "qg")
+    w0 = sum((fld[F[x], :, :512] * rho * dz[:, None]).sum(0) for x in names)
+    w1 = sum((out[F[x], :, :512] * rho * dz[:, None]).sum(0) for x in names)
+    drift = np.abs(w1 + pr[:, :512].sum(0) - w0) / w0
+    # processes conserve to FP64 rounding; sedimentation increments carry FP32 rounding
+    assert drift.max() < 1e-9, drift.max()
