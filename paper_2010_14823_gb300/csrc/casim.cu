@@ -172,6 +172,7 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   derive<double>(p, ctx->kp.d, ln_);
   derive<float>(p, ctx->kp.f, log2_);
   ctx->kp.c_max = p.c_max;
+  ctx->kp.T0 = p.T0;
   for (int x = 0; x < 5; ++x) ctx->kp.vmax[x] = p.vmax[x];
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));

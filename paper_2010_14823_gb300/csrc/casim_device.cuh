@@ -6,10 +6,13 @@
 // are level-major, so the 32 threads of a warp touch 32 consecutive columns of
 // one level: every access is a coalesced 256-byte row.
 //
-// Two precision policies share the code:
-//   PolicyF64  every operation in FP64;
+// Two precision policies share the process formulas:
+//   PolicyF64  every operation in FP64, transfers applied in the order of the
+//              scheme's transfer list;
 //   PolicyMix  rates, fall speeds and special functions in FP32 on the MUFU
-//              pipe (ex2/lg2), state and every applied transfer in FP64.
+//              pipe (ex2/lg2); the FP64 state is touched once per changed field
+//              (and once per mass transfer pair, which keeps water conserved to
+//              FP64 rounding).
 // GB300 issues FP64 (and FP32<->FP64 conversions) at about 1/70 of the FP32
 // rate, so the mixed policy converts between the two with integer bit
 // operations and keeps FP64 to the additions that carry conservation.
@@ -66,6 +69,7 @@ struct ConstK {
 struct KParams {
   ConstK<double> d;
   ConstK<float> f;
+  double T0;
   double c_max;
   double vmax[5];
 };
@@ -176,13 +180,35 @@ struct Pt {
   double T, qv, qc, qr, qi, qs, qg, nc, nr, ni, ns, ng, na, p, rho, w;
 };
 
-enum { F_T = 0, F_QV, F_QC, F_QR, F_QI, F_QS, F_QG, F_NC, F_NR, F_NI, F_NS, F_NG, F_NA, F_P, F_RHO, F_W };
+// Working values of a point in the compute precision (after adjustment and
+// activation, as the rates see them).
+template <class R>
+struct W {
+  double Td;   // FP64 temperature (FP64 form only: ice saturation as the oracle writes it)
+  R T, tc, p, rho, qv, qc, qr, qx[3], nc, nr, nx[3];
+  unsigned hmax;   // mixed form: largest |high word| of the FP64 inputs read (non-finite check)
+};
+
+// |high word| of a double: >= 0x7ff00000 exactly when it is not finite
+__device__ __forceinline__ unsigned hiabs(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
+
+// raw process rates (kg/kg/s; number rates for scc, scr, nucn)
+template <class R>
+struct Rt {
+  R aut, acc, scc, scr, evr, nucn, dep[3], rim[2], mlt[3];
+};
+
+// limiter factors per transfer and the number-to-mass ratios they use
+template <class R>
+struct Gt {
+  R rc, rr, rx[3], nucm, depp[3], sub[3], nmlt[3];
+  R aut, acc, scc, scr, evr, nuc, dep[3], mlt[3], rs, rg;
+};
 
 template <class M>
-struct Chain {
+struct Phys {
   using R = typename M::R;
 
-  // saturation specific humidity over liquid and its temperature derivative
   static __device__ __forceinline__ R es_liq(const ConstK<R> &K, R tc) {
     return K.esl0 * M::exp(M::div(K.esla * tc, tc + K.eslb));
   }
@@ -196,82 +222,6 @@ struct Chain {
       return K.esi0 * ::exp(K.esia * (T - K.esit) / (T - K.esib));
     } else {
       return K.esi0 * M::exp(M::div(K.esia * (tc + K.t0_esit), tc + K.t0_esib));
-    }
-  }
-
-  // Activity test: true unless the whole chain would leave the point
-  // unchanged (no hydrometeor present, not supersaturated over liquid, no
-  // ice nucleation possible).  Also returns qs over liquid at the initial
-  // temperature, which saturation adjustment reuses.
-  static __device__ __forceinline__ bool active(const ConstK<R> &K, const Pt &s, R &tc0, R &es0, R &qs0) {
-    tc0 = M::toR(s.T - (double)K.T0);
-    const R p = M::toR(s.p);
-    es0 = es_liq(K, tc0);
-    qs0 = qsat(K, es0, p);
-    const R qmin = K.qmin;
-    bool act = M::toR(s.qc) > qmin || M::toR(s.qr) > qmin || M::toR(s.qi) > qmin ||
-               M::toR(s.qs) > qmin || M::toR(s.qg) > qmin || M::toR(s.qv) > qs0;
-    if (!act && M::toR(s.T) < K.Tnuc) act = M::div(M::toR(s.qv), qsat(K, es_ice(K, s.T, tc0), p)) > (R)1;
-    return act;
-  }
-
-  // a2: isobaric saturation adjustment, 4 Newton iterations on
-  // cp (T* - T) = Lv (qv - qs(T*)), condensate limited by the cloud present.
-  static __device__ __forceinline__ void satadj(const ConstK<R> &K, Pt &s, R tc0, R es0, R qs0) {
-    const R p = M::toR(s.p);
-    if (!(M::toR(s.qv) > qs0 || M::toR(s.qc) > K.qmin)) return;
-    if constexpr (!M::kMixed) {
-      const double T0v = s.T, qv0 = s.qv, qc0 = s.qc;
-      double Tn = T0v, es = es0, qs = qs0;
-      for (int it = 0; it < 4; ++it) {
-        if (it > 0) {
-          es = es_liq(K, Tn - K.T0);
-          qs = qsat(K, es, p);
-        }
-        const double tc = Tn - K.T0;
-        const double f = (Tn - T0v) - K.lv_cp * (qv0 - qs);
-        const double des = es * K.esla * K.eslb / ((tc + K.eslb) * (tc + K.eslb));
-        const double den = p - K.ome * es;
-        const double fp = 1.0 + K.lv_cp * (K.eps * p / (den * den) * des);
-        Tn = Tn - f / fp;
-      }
-      double dq = K.cp_lv * (Tn - T0v);
-      if (dq < -qc0) dq = -qc0;
-      s.T = T0v + K.lv_cp * dq;
-      s.qv = qv0 - dq;
-      s.qc = qc0 + dq;
-    } else {
-      // FP32 Newton on the temperature increment; the vapour difference
-      // qv - qs is formed in FP64 each iteration.
-      R dT = 0.f, es = es0, qs = qs0;
-      for (int it = 0; it < 4; ++it) {
-        const R tc = tc0 + dT;
-        if (it > 0) {
-          es = es_liq(K, tc);
-          qs = qsat(K, es, p);
-        }
-        const R d = M::toR(s.qv - M::toD(qs));
-        const R f = dT - K.lv_cp * d;
-        const R e1 = tc + K.eslb;
-        const R des = es * K.eslab * rcpa(e1 * e1);
-        const R den = p - K.ome * es;
-        const R fp = 1.f + K.lv_cp * K.eps * p * des * rcpa(den * den);
-        dT = dT - M::div(f, fp);
-      }
-      const R dq = K.cp_lv * dT;
-      const R qc0 = M::toR(s.qc);
-      double dqd;
-      R dqr;
-      if (dq <= -qc0) {
-        dqd = -s.qc;
-        dqr = -qc0;
-      } else {
-        dqd = M::toD(dq);
-        dqr = dq;
-      }
-      s.T += M::toD(K.lv_cp * dqr);
-      s.qv -= dqd;
-      s.qc += dqd;
     }
   }
 
@@ -297,33 +247,7 @@ struct Chain {
     return (R)0.5 * N * M::erfc(u);
   }
 
-  static __device__ __forceinline__ void activate(const ConstK<R> &K, Pt &s) {
-    if (!(s.w > 0.0) || !(M::toR(s.qc) > K.qmin)) return;
-    const R rho = M::toR(s.rho);
-    const R N = rho * M::toR(s.na + s.nc);
-    if (!(N > (R)0)) return;
-    const R T = M::toR(s.T);
-    const R es = es_liq(K, M::toR(s.T - (double)K.T0));
-    const R nact = arg_nact(K, N, M::toR(s.w), T, M::toR(s.p), es);
-    if constexpr (!M::kMixed) {
-      double dn = nact / s.rho - s.nc;
-      if (dn < 0.0) dn = 0.0;
-      if (dn > s.na) dn = s.na;
-      s.nc += dn;
-      s.na -= dn;
-    } else {
-      R dn = M::div(nact, rho) - M::toR(s.nc);
-      dn = M::mx(dn, (R)0);
-      dn = M::mn(dn, M::toR(s.na));
-      if (dn > (R)0) {
-        const double dnd = M::toD(dn);
-        s.nc += dnd;
-        s.na -= dnd;
-      }
-    }
-  }
-
-  // log of the gamma slope of species x from (q, n), clamped
+  // log of the gamma slope of a species from (log q, n), clamped
   static __device__ __forceinline__ R lglam(const SpeciesK<R> &X, R lgq, R n) {
     const R lgn = M::lg(M::mx(n, (R)0));
     R l = (X.lglamfac + lgn - lgq) * X.invb;
@@ -331,15 +255,11 @@ struct Chain {
     return M::mn(l, X.lghi);
   }
 
-  // a4..a10 on an adjusted, activated point
-  static __device__ __forceinline__ void rates_and_limit(const ConstK<R> &K, Pt &s, double dt) {
-    const R T = M::toR(s.T), p = M::toR(s.p), rho = M::toR(s.rho);
-    const R qv = M::toR(s.qv), qc = M::toR(s.qc), qr = M::toR(s.qr);
-    const R qx[3] = {M::toR(s.qi), M::toR(s.qs), M::toR(s.qg)};
-    const R nc = M::toR(s.nc), nr = M::toR(s.nr);
-    const R nx[3] = {M::toR(s.ni), M::toR(s.ns), M::toR(s.ng)};
+  // a4..a9: process rates from the post-activation state
+  static __device__ __forceinline__ void rates(const ConstK<R> &K, const W<R> &w, double dt, Rt<R> &r) {
+    const R T = w.T, p = w.p, rho = w.rho, qv = w.qv, qc = w.qc, qr = w.qr, nc = w.nc, nr = w.nr;
+    const R tc = w.tc;
     const R dtr = M::toR(dt);
-    const R tc = M::toR(s.T - (double)K.T0);
     const R esl = es_liq(K, tc);
     const R qsl = qsat(K, esl, p);
     const R iT2 = M::div((R)1, T * T);
@@ -353,99 +273,84 @@ struct Chain {
     const R nu = M::div(K.mu_air, rho);
     const R V0 = M::cbrt(nu * K.inv_dv) * M::sqrt(M::div(dfac, nu));
 
-    R aut = 0, acc = 0, scc = 0, scr = 0, evr = 0, nucn = 0;
-    R dep[3] = {0, 0, 0}, rim[2] = {0, 0}, mlt[3] = {0, 0, 0};
+    r.aut = r.acc = r.scc = r.scr = r.evr = r.nucn = (R)0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) r.dep[m] = r.mlt[m] = (R)0;
+    r.rim[0] = r.rim[1] = (R)0;
 
     const R lgqc = hc ? M::lg(qc) : (R)0;
     const R lgqr = hr ? M::lg(qr) : (R)0;
     if (hc) {
       const R ncc = M::mx(rho * nc * (R)1e-6, K.nc_min);
-      aut = K.kk_aut * M::ex(K.kk_aut_qc * lgqc + K.kk_aut_nc * M::lg(ncc));
-      scc = K.kcf * rho * qc * qc;
+      r.aut = K.kk_aut * M::ex(K.kk_aut_qc * lgqc + K.kk_aut_nc * M::lg(ncc));
+      r.scc = K.kcf * rho * qc * qc;
     }
-    if (hc && hr) acc = K.kk_acc * M::ex(K.kk_acc_exp * (lgqc + lgqr));
+    if (hc && hr) r.acc = K.kk_acc * M::ex(K.kk_acc_exp * (lgqc + lgqr));
     if (hr) {
-      scr = K.kr * rho * M::mx(nr, (R)0) * qr;
+      r.scr = K.kr * rho * M::mx(nr, (R)0) * qr;
       if (Sw < (R)1) {
         const SpeciesK<R> &X = K.sp[1];
         const R l = lglam(X, lgqr, nr);
         const R iv = rho * qr * (X.ev1 * M::ex(X.ex1 * l) + V0 * X.ev2 * M::ex(X.ex2 * l));
         const R Aw = K.awc * iT2, Bw = M::div(K.rv_dv * T, esl);
-        evr = M::div(K.twopi * ((R)1 - Sw) * iv, rho * (Aw + Bw));
+        r.evr = M::div(K.twopi * ((R)1 - Sw) * iv, rho * (Aw + Bw));
       }
     }
-    if (cold || T < K.Tnuc) {
-      const R esi = es_ice(K, s.T, tc);
+    if (cold) {
+      const R esi = es_ice(K, w.Td, tc);
       const R qsi = qsat(K, esi, p);
       const R Si = M::div(qv, qsi);
       if (T < K.Tnuc && Si > (R)1) {
         const R nin = K.mey_a * M::exp(K.mey_b + K.mey_c * (Si - (R)1));
-        const R dn = M::div(nin, rho) - nx[0];
-        if (dn > (R)0) nucn = M::div(dn, dtr);
+        const R dn = M::div(nin, rho) - w.nx[0];
+        if (dn > (R)0) r.nucn = M::div(dn, dtr);
       }
-      if (cold) {
-        const R Ai = K.aic * iT2, Bi = M::div(K.rv_dv * T, esi);
-        const R dfa = M::div(Si - (R)1, rho * (Ai + Bi));
+      const R Ai = K.aic * iT2, Bi = M::div(K.rv_dv * T, esi);
+      const R dfa = M::div(Si - (R)1, rho * (Ai + Bi));
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          if (!(qx[m] > K.qmin)) continue;
-          const SpeciesK<R> &X = K.sp[2 + m];
-          const R lq = M::lg(qx[m]);
-          const R l = lglam(X, lq, nx[m]);
-          const R iv = rho * qx[m] * (X.ev1 * M::ex(X.ex1 * l) + V0 * X.ev2 * M::ex(X.ex2 * l));
-          dep[m] = X.dep * dfa * iv;
-          if (m > 0 && hc) rim[m - 1] = X.rim * qc * dfac * rho * qx[m] * M::ex(X.exr * l);
-        }
+      for (int m = 0; m < 3; ++m) {
+        if (!(w.qx[m] > K.qmin)) continue;
+        const SpeciesK<R> &X = K.sp[2 + m];
+        const R l = lglam(X, M::lg(w.qx[m]), w.nx[m]);
+        const R iv = rho * w.qx[m] * (X.ev1 * M::ex(X.ex1 * l) + V0 * X.ev2 * M::ex(X.ex2 * l));
+        r.dep[m] = X.dep * dfa * iv;
+        if (m > 0 && hc) r.rim[m - 1] = X.rim * qc * dfac * rho * w.qx[m] * M::ex(X.exr * l);
       }
     }
     if (warm) {
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        if (!(qx[m] > K.qmin)) continue;
+        if (!(w.qx[m] > K.qmin)) continue;
         const SpeciesK<R> &X = K.sp[2 + m];
-        const R lq = M::lg(qx[m]);
-        const R l = lglam(X, lq, nx[m]);
-        const R iv = rho * qx[m] * (X.ev1 * M::ex(X.ex1 * l) + V0 * X.ev2 * M::ex(X.ex2 * l));
-        mlt[m] = M::div(X.mlt * tc * iv, rho);
+        const R l = lglam(X, M::lg(w.qx[m]), w.nx[m]);
+        const R iv = rho * w.qx[m] * (X.ev1 * M::ex(X.ex1 * l) + V0 * X.ev2 * M::ex(X.ex2 * l));
+        r.mlt[m] = M::div(X.mlt * tc * iv, rho);
       }
     }
-
-    limit_apply(K, s, dt, qv, qc, qr, qx, nc, nr, nx, aut, acc, scc, scr, evr, nucn, dep, rim, mlt);
   }
 
-  // a10: per-pool limiting factors, each transfer scaled by the smallest
-  // factor of the pools it draws from, applied once to source and sink.
-  static __device__ __forceinline__ void limit_apply(const ConstK<R> &K, Pt &s, double dt, R qv, R qc, R qr,
-                                                     const R qx[3], R nc, R nr, const R nx[3], R aut, R acc,
-                                                     R scc, R scr, R evr, R nucn, const R dep[3], const R rim[2],
-                                                     const R mlt[3]) {
+  // a10: per-pool limiting factors f_X = min(1, X / (S_X dt)); each transfer
+  // takes the smallest factor of the pools it draws from.
+  static __device__ __forceinline__ void limits(const ConstK<R> &K, const W<R> &w, double dt, const Rt<R> &r,
+                                                Gt<R> &g) {
     const R dtr = M::toR(dt);
-    const R rc = qc > K.qmin ? M::div(M::mx(nc, (R)0), qc) : (R)0;
-    const R rr = qr > K.qmin ? M::div(M::mx(nr, (R)0), qr) : (R)0;
-    R rx[3];
+    g.rc = w.qc > K.qmin ? M::div(M::mx(w.nc, (R)0), w.qc) : (R)0;
+    g.rr = w.qr > K.qmin ? M::div(M::mx(w.nr, (R)0), w.qr) : (R)0;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) rx[m] = qx[m] > K.qmin ? M::div(M::mx(nx[m], (R)0), qx[m]) : (R)0;
-    const R nucm = nucn * K.mi0;
-    R sub[3], depp[3];
+    for (int m = 0; m < 3; ++m) g.rx[m] = w.qx[m] > K.qmin ? M::div(M::mx(w.nx[m], (R)0), w.qx[m]) : (R)0;
+    g.nucm = r.nucn * K.mi0;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      depp[m] = dep[m] >= (R)0 ? dep[m] : (R)0;
-      sub[m] = dep[m] >= (R)0 ? (R)0 : -dep[m];
+      g.depp[m] = r.dep[m] >= (R)0 ? r.dep[m] : (R)0;
+      g.sub[m] = r.dep[m] >= (R)0 ? (R)0 : -r.dep[m];
+      g.nmlt[m] = r.mlt[m] > (R)0 ? r.mlt[m] * g.rx[m] : (R)0;
     }
-    // sinks per pool (same summation order as the transfer list)
-    const R S_qv = ((nucm + depp[0]) + depp[1]) + depp[2];
-    const R S_qc = ((aut + acc) + rim[0]) + rim[1];
-    const R S_qr = evr;
-    R S_qx[3], S_nx[3], nmlt[3];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      S_qx[m] = sub[m] + mlt[m];
-      nmlt[m] = mlt[m] > (R)0 ? mlt[m] * rx[m] : (R)0;
-      S_nx[m] = sub[m] * rx[m] + nmlt[m];
-    }
-    const R S_nc = (((aut * rc + acc * rc) + scc) + rim[0] * rc) + rim[1] * rc;
-    const R S_nr = scr + evr * rr;
-
+    // sinks per pool, summed in the order of the transfer list
+    const R S_qv = ((g.nucm + g.depp[0]) + g.depp[1]) + g.depp[2];
+    const R S_qc = ((r.aut + r.acc) + r.rim[0]) + r.rim[1];
+    const R S_qr = r.evr;
+    const R S_nc = (((r.aut * g.rc + r.acc * g.rc) + r.scc) + r.rim[0] * g.rc) + r.rim[1] * g.rc;
+    const R S_nr = r.scr + r.evr * g.rr;
     auto fac = [&](R S, R X) -> R {
       if constexpr (!M::kMixed) {
         return S * dtr > X ? M::mx(X, (R)0) / (S * dtr) : (R)1;
@@ -456,134 +361,301 @@ struct Chain {
         return Sd > X * 0.99999f ? M::mx(X, (R)0) * 0.999996185f * rcpa(Sd) : (R)1;
       }
     };
-    const R f_qv = fac(S_qv, qv), f_qc = fac(S_qc, qc), f_qr = fac(S_qr, qr);
-    const R f_nc = fac(S_nc, nc), f_nr = fac(S_nr, nr);
-    R f_qx[3], f_nx[3];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      f_qx[m] = fac(S_qx[m], qx[m]);
-      f_nx[m] = fac(S_nx[m], nx[m]);
-    }
+    const R f_qv = fac(S_qv, w.qv), f_qc = fac(S_qc, w.qc), f_qr = fac(S_qr, w.qr);
+    const R f_nc = fac(S_nc, w.nc), f_nr = fac(S_nr, w.nr);
     auto g2 = [&](R rate, R fm, R nsink, R fn) -> R {
-      R g = (R)1;
-      if (rate > (R)0 && fm < g) g = fm;
-      if (nsink > (R)0 && fn < g) g = fn;
-      return g;
+      R x = (R)1;
+      if (rate > (R)0 && fm < x) x = fm;
+      if (nsink > (R)0 && fn < x) x = fn;
+      return x;
     };
-    const R g_aut = g2(aut, f_qc, aut * rc, f_nc);
-    const R g_acc = g2(acc, f_qc, acc * rc, f_nc);
-    const R g_scc = g2(0, 1, scc, f_nc);
-    const R g_scr = g2(0, 1, scr, f_nr);
-    const R g_evr = g2(evr, f_qr, evr * rr, f_nr);
-    const R g_nuc = g2(nucm, f_qv, 0, 1);
-    R g_dep[3], g_mlt[3];
+    g.aut = g2(r.aut, f_qc, r.aut * g.rc, f_nc);
+    g.acc = g2(r.acc, f_qc, r.acc * g.rc, f_nc);
+    g.scc = g2(0, 1, r.scc, f_nc);
+    g.scr = g2(0, 1, r.scr, f_nr);
+    g.evr = g2(r.evr, f_qr, r.evr * g.rr, f_nr);
+    g.nuc = g2(g.nucm, f_qv, 0, 1);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      g_dep[m] = dep[m] >= (R)0 ? g2(depp[m], f_qv, 0, 1) : g2(sub[m], f_qx[m], sub[m] * rx[m], f_nx[m]);
-      g_mlt[m] = g2(mlt[m], f_qx[m], nmlt[m], f_nx[m]);
+      const R f_qx = fac(g.sub[m] + r.mlt[m], w.qx[m]);
+      const R f_nx = fac(g.sub[m] * g.rx[m] + g.nmlt[m], w.nx[m]);
+      g.dep[m] = r.dep[m] >= (R)0 ? g2(g.depp[m], f_qv, 0, 1) : g2(g.sub[m], f_qx, g.sub[m] * g.rx[m], f_nx);
+      g.mlt[m] = g2(r.mlt[m], f_qx, g.nmlt[m], f_nx);
     }
-    const R g_rs = g2(rim[0], f_qc, rim[0] * rc, f_nc);
-    const R g_rg = g2(rim[1], f_qc, rim[1] * rc, f_nc);
-
-    if constexpr (!M::kMixed) {
-      // FP64: transfers applied one by one in list order
-      double qxd[3] = {s.qi, s.qs, s.qg};
-      double nxd[3] = {s.ni, s.ns, s.ng};
-      const double mr0i = K.inv_mr0;
-      double tau;
-      if (aut > 0) { tau = g_aut * aut * dt; s.qc -= tau; s.qr += tau; }
-      if (aut * rc > 0) s.nc -= g_aut * (aut * rc) * dt;
-      if (aut * mr0i > 0) s.nr += g_aut * (aut * mr0i) * dt;
-      if (acc > 0) { tau = g_acc * acc * dt; s.qc -= tau; s.qr += tau; }
-      if (acc * rc > 0) s.nc -= g_acc * (acc * rc) * dt;
-      if (scc > 0) s.nc -= g_scc * scc * dt;
-      if (scr > 0) s.nr -= g_scr * scr * dt;
-      if (evr > 0) { tau = g_evr * evr * dt; s.qr -= tau; s.qv += tau; s.T += tau * (-K.lv) / K.cp; }
-      if (evr * rr > 0) s.nr -= g_evr * (evr * rr) * dt;
-      if (nucm > 0) { tau = g_nuc * nucm * dt; s.qv -= tau; qxd[0] += tau; s.T += tau * K.ls / K.cp; }
-      if (nucn > 0) nxd[0] += g_nuc * nucn * dt;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        if (dep[m] >= 0) {
-          if (depp[m] > 0) { tau = g_dep[m] * depp[m] * dt; s.qv -= tau; qxd[m] += tau; s.T += tau * K.ls / K.cp; }
-        } else {
-          tau = g_dep[m] * sub[m] * dt; qxd[m] -= tau; s.qv += tau; s.T += tau * (-K.ls) / K.cp;
-          if (sub[m] * rx[m] > 0) nxd[m] -= g_dep[m] * (sub[m] * rx[m]) * dt;
-        }
-      }
-      if (rim[0] > 0) { tau = g_rs * rim[0] * dt; s.qc -= tau; qxd[2] += tau; s.T += tau * K.lf / K.cp; }
-      if (rim[0] * rc > 0) s.nc -= g_rs * (rim[0] * rc) * dt;
-      if (rim[1] > 0) { tau = g_rg * rim[1] * dt; s.qc -= tau; qxd[2] += tau; s.T += tau * K.lf / K.cp; }
-      if (rim[1] * rc > 0) s.nc -= g_rg * (rim[1] * rc) * dt;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        if (mlt[m] > 0) { tau = g_mlt[m] * mlt[m] * dt; qxd[m] -= tau; s.qr += tau; s.T += tau * (-K.lf) / K.cp; }
-        if (nmlt[m] > 0) { nxd[m] -= g_mlt[m] * nmlt[m] * dt; s.nr += g_mlt[m] * nmlt[m] * dt; }
-      }
-      s.qi = qxd[0]; s.qs = qxd[1]; s.qg = qxd[2];
-      s.ni = nxd[0]; s.ns = nxd[1]; s.ng = nxd[2];
-    } else {
-      // Mixed: each (source, destination) pair moves one FP32 amount, added
-      // to and subtracted from the FP64 state, so water is conserved to FP64
-      // rounding.  Net number and heat changes are FP32 sums.
-      const R t_cr = g_aut * aut * dtr + g_acc * acc * dtr;
-      const R t_cg = g_rs * rim[0] * dtr + g_rg * rim[1] * dtr;
-      const R t_rv = g_evr * evr * dtr;
-      R t_vx[3], t_xr[3];
-      t_vx[0] = g_nuc * nucm * dtr + g_dep[0] * dep[0] * dtr;  // signed: deposition > 0
-      t_vx[1] = g_dep[1] * dep[1] * dtr;
-      t_vx[2] = g_dep[2] * dep[2] * dtr;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) t_xr[m] = g_mlt[m] * mlt[m] * dtr;
-      if (t_cr != (R)0) { const double d = M::toD(t_cr); s.qc -= d; s.qr += d; }
-      if (t_cg != (R)0) { const double d = M::toD(t_cg); s.qc -= d; s.qg += d; }
-      if (t_rv != (R)0) { const double d = M::toD(t_rv); s.qr -= d; s.qv += d; }
-      if (t_vx[0] != (R)0) { const double d = M::toD(t_vx[0]); s.qv -= d; s.qi += d; }
-      if (t_vx[1] != (R)0) { const double d = M::toD(t_vx[1]); s.qv -= d; s.qs += d; }
-      if (t_vx[2] != (R)0) { const double d = M::toD(t_vx[2]); s.qv -= d; s.qg += d; }
-      if (t_xr[0] != (R)0) { const double d = M::toD(t_xr[0]); s.qi -= d; s.qr += d; }
-      if (t_xr[1] != (R)0) { const double d = M::toD(t_xr[1]); s.qs -= d; s.qr += d; }
-      if (t_xr[2] != (R)0) { const double d = M::toD(t_xr[2]); s.qg -= d; s.qr += d; }
-      const R dnc = -(g_aut * aut * rc + g_acc * acc * rc + g_scc * scc + g_rs * rim[0] * rc + g_rg * rim[1] * rc) * dtr;
-      const R dnr = (g_aut * aut * K.inv_mr0 - g_scr * scr - g_evr * evr * rr +
-                     g_mlt[0] * nmlt[0] + g_mlt[1] * nmlt[1] + g_mlt[2] * nmlt[2]) * dtr;
-      R dnx[3];
-      dnx[0] = g_nuc * nucn * dtr;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const R sn = dep[m] < (R)0 ? g_dep[m] * sub[m] * rx[m] : (R)0;
-        dnx[m] = (m == 0 ? dnx[0] : (R)0) - (sn + g_mlt[m] * nmlt[m]) * dtr;
-      }
-      const R dT = (K.ls * (t_vx[0] + t_vx[1] + t_vx[2]) + K.lf * t_cg - K.lv * t_rv -
-                    K.lf * (t_xr[0] + t_xr[1] + t_xr[2])) * K.inv_cp;
-      if (dnc != (R)0) s.nc += M::toD(dnc);
-      if (dnr != (R)0) s.nr += M::toD(dnr);
-      if (dnx[0] != (R)0) s.ni += M::toD(dnx[0]);
-      if (dnx[1] != (R)0) s.ns += M::toD(dnx[1]);
-      if (dnx[2] != (R)0) s.ng += M::toD(dnx[2]);
-      if (dT != (R)0) s.T += M::toD(dT);
-    }
+    g.rs = g2(r.rim[0], f_qc, r.rim[0] * g.rc, f_nc);
+    g.rg = g2(r.rim[1], f_qc, r.rim[1] * g.rc, f_nc);
   }
 
-  // sedimentation: speeds of species x (0..3 = r,i,s,g) at one point
-  static __device__ __forceinline__ void fall_speeds(const ConstK<R> &K, R guard, R q, R n, R rho, int x, R &vq,
+  // fall speeds of sedimenting species x (0..3 = r, i, s, g) at one point
+  static __device__ __forceinline__ void fall_speeds(const ConstK<R> &K, R guard, R lgq, R n, R dfac, int x, R &vq,
                                                      R &vn) {
     const SpeciesK<R> &X = K.sp[1 + x];
-    const R l = lglam(X, M::lg(q), n);
-    const R dfac = M::ex((R)0.4 * (K.lgrho0 - M::lg(rho)));
+    const R l = lglam(X, lgq, n);
     const R pw = M::ex(X.exv * l);
-    vq = M::mn(X.vq * dfac * pw, X.vmax);
-    vn = M::mn(X.vn * dfac * pw, X.vmax);
-    vq = M::mn(vq, guard);
-    vn = M::mn(vn, guard);
+    vq = M::mn(M::mn(X.vq * dfac * pw, X.vmax), guard);
+    vn = M::mn(M::mn(X.vn * dfac * pw, X.vmax), guard);
+  }
+};
+
+// ------------------------------------------------------- FP64 form
+struct F64 {
+  using M = PolicyF64;
+  using P = Phys<M>;
+
+  // true unless the chain leaves the point unchanged (no hydrometeor, not
+  // supersaturated over liquid, no ice nucleation possible); also returns
+  // q_s over liquid at the initial temperature for the adjustment
+  static __device__ __forceinline__ bool active(const ConstK<double> &K, const Pt &s, double &es0, double &qs0) {
+    const double qmin = K.qmin;
+    es0 = P::es_liq(K, s.T - K.T0);
+    qs0 = P::qsat(K, es0, s.p);
+    bool act = s.qc > qmin || s.qr > qmin || s.qi > qmin || s.qs > qmin || s.qg > qmin || s.qv > qs0;
+    if (!act && s.T < K.Tnuc) act = s.qv / P::qsat(K, P::es_ice(K, s.T, 0.0), s.p) > 1.0;
+    return act;
+  }
+
+  // a2: 4 Newton iterations on cp (T* - T) = Lv (qv - qs(T*))
+  static __device__ __forceinline__ void satadj(const ConstK<double> &K, Pt &s, double es0, double qs0) {
+    const double p = s.p;
+    if (!(s.qv > qs0 || s.qc > K.qmin)) return;
+    const double T0v = s.T, qv0 = s.qv, qc0 = s.qc;
+    double Tn = T0v, es = es0, qs = qs0;
+    for (int it = 0; it < 4; ++it) {
+      if (it > 0) {
+        es = P::es_liq(K, Tn - K.T0);
+        qs = P::qsat(K, es, p);
+      }
+      const double tc = Tn - K.T0;
+      const double f = (Tn - T0v) - K.lv_cp * (qv0 - qs);
+      const double des = es * K.esla * K.eslb / ((tc + K.eslb) * (tc + K.eslb));
+      const double den = p - K.ome * es;
+      const double fp = 1.0 + K.lv_cp * (K.eps * p / (den * den) * des);
+      Tn = Tn - f / fp;
+    }
+    double dq = K.cp_lv * (Tn - T0v);
+    if (dq < -qc0) dq = -qc0;
+    s.T = T0v + K.lv_cp * dq;
+    s.qv = qv0 - dq;
+    s.qc = qc0 + dq;
+  }
+
+  static __device__ __forceinline__ void activate(const ConstK<double> &K, Pt &s) {
+    if (!(s.w > 0.0) || !(s.qc > K.qmin)) return;
+    const double N = s.rho * (s.na + s.nc);
+    if (!(N > 0.0)) return;
+    const double nact = P::arg_nact(K, N, s.w, s.T, s.p, P::es_liq(K, s.T - K.T0));
+    double dn = nact / s.rho - s.nc;
+    if (dn < 0.0) dn = 0.0;
+    if (dn > s.na) dn = s.na;
+    s.nc += dn;
+    s.na -= dn;
+  }
+
+  // a2..a10 on one active point; transfers applied one by one in list order
+  static __device__ __forceinline__ void process(const ConstK<double> &K, Pt &s, double dt, double es0, double qs0) {
+    satadj(K, s, es0, qs0);
+    activate(K, s);
+    W<double> w;
+    w.Td = s.T; w.T = s.T; w.tc = s.T - K.T0; w.p = s.p; w.rho = s.rho;
+    w.qv = s.qv; w.qc = s.qc; w.qr = s.qr; w.qx[0] = s.qi; w.qx[1] = s.qs; w.qx[2] = s.qg;
+    w.nc = s.nc; w.nr = s.nr; w.nx[0] = s.ni; w.nx[1] = s.ns; w.nx[2] = s.ng;
+    Rt<double> r;
+    P::rates(K, w, dt, r);
+    Gt<double> g;
+    P::limits(K, w, dt, r, g);
+    double qxd[3] = {s.qi, s.qs, s.qg};
+    double nxd[3] = {s.ni, s.ns, s.ng};
+    double tau;
+    if (r.aut > 0) { tau = g.aut * r.aut * dt; s.qc -= tau; s.qr += tau; }
+    if (r.aut * g.rc > 0) s.nc -= g.aut * (r.aut * g.rc) * dt;
+    if (r.aut * K.inv_mr0 > 0) s.nr += g.aut * (r.aut * K.inv_mr0) * dt;
+    if (r.acc > 0) { tau = g.acc * r.acc * dt; s.qc -= tau; s.qr += tau; }
+    if (r.acc * g.rc > 0) s.nc -= g.acc * (r.acc * g.rc) * dt;
+    if (r.scc > 0) s.nc -= g.scc * r.scc * dt;
+    if (r.scr > 0) s.nr -= g.scr * r.scr * dt;
+    if (r.evr > 0) { tau = g.evr * r.evr * dt; s.qr -= tau; s.qv += tau; s.T += tau * (-K.lv) / K.cp; }
+    if (r.evr * g.rr > 0) s.nr -= g.evr * (r.evr * g.rr) * dt;
+    if (g.nucm > 0) { tau = g.nuc * g.nucm * dt; s.qv -= tau; qxd[0] += tau; s.T += tau * K.ls / K.cp; }
+    if (r.nucn > 0) nxd[0] += g.nuc * r.nucn * dt;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      if (r.dep[m] >= 0) {
+        if (g.depp[m] > 0) { tau = g.dep[m] * g.depp[m] * dt; s.qv -= tau; qxd[m] += tau; s.T += tau * K.ls / K.cp; }
+      } else {
+        tau = g.dep[m] * g.sub[m] * dt; qxd[m] -= tau; s.qv += tau; s.T += tau * (-K.ls) / K.cp;
+        if (g.sub[m] * g.rx[m] > 0) nxd[m] -= g.dep[m] * (g.sub[m] * g.rx[m]) * dt;
+      }
+    }
+    if (r.rim[0] > 0) { tau = g.rs * r.rim[0] * dt; s.qc -= tau; qxd[2] += tau; s.T += tau * K.lf / K.cp; }
+    if (r.rim[0] * g.rc > 0) s.nc -= g.rs * (r.rim[0] * g.rc) * dt;
+    if (r.rim[1] > 0) { tau = g.rg * r.rim[1] * dt; s.qc -= tau; qxd[2] += tau; s.T += tau * K.lf / K.cp; }
+    if (r.rim[1] * g.rc > 0) s.nc -= g.rg * (r.rim[1] * g.rc) * dt;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      if (r.mlt[m] > 0) { tau = g.mlt[m] * r.mlt[m] * dt; qxd[m] -= tau; s.qr += tau; s.T += tau * (-K.lf) / K.cp; }
+      if (g.nmlt[m] > 0) { nxd[m] -= g.mlt[m] * g.nmlt[m] * dt; s.nr += g.mlt[m] * g.nmlt[m] * dt; }
+    }
+    s.qi = qxd[0]; s.qs = qxd[1]; s.qg = qxd[2];
+    s.ni = nxd[0]; s.ns = nxd[1]; s.ng = nxd[2];
+  }
+};
+
+// ------------------------------------------------------- mixed form
+// Increments of one active point in FP32, applied to the FP64 state once.
+struct MixInc {
+  float vc;        // vapour -> cloud by adjustment (signed)
+  bool evap_all;   // adjustment evaporated all cloud: the FP64 cloud moves to vapour
+  float cr, cg, rv, vx[3], xr[3];   // cloud->rain, cloud->graupel, rain->vapour,
+                                    // vapour->i,s,g (signed), i,s,g->rain
+  float dT;        // temperature
+  float dn[5];     // numbers c, r, i, s, g
+  float dna;       // aerosol number
+};
+
+struct Mix {
+  using M = PolicyMix;
+  using P = Phys<M>;
+
+  // activity flag; fills the FP32 values it needs
+  static __device__ __forceinline__ bool active(const ConstK<float> &K, const Pt &s, double T0d, W<float> &w,
+                                                float &es0, float &qs0) {
+    w.Td = s.T;
+    w.hmax = max(max(max(hiabs(s.T), hiabs(s.p)), max(hiabs(s.qv), hiabs(s.qc))),
+                 max(max(hiabs(s.qr), hiabs(s.qi)), max(hiabs(s.qs), hiabs(s.qg))));
+    w.tc = d2f(s.T - T0d);
+    w.T = d2f(s.T);
+    w.p = d2f(s.p);
+    w.qv = d2f(s.qv);
+    w.qc = d2f(s.qc);
+    w.qr = d2f(s.qr);
+    w.qx[0] = d2f(s.qi);
+    w.qx[1] = d2f(s.qs);
+    w.qx[2] = d2f(s.qg);
+    es0 = P::es_liq(K, w.tc);
+    qs0 = P::qsat(K, es0, w.p);
+    const float qmin = K.qmin;
+    bool act = w.qc > qmin || w.qr > qmin || w.qx[0] > qmin || w.qx[1] > qmin || w.qx[2] > qmin || w.qv > qs0;
+    if (!act && w.T < K.Tnuc) act = __fdividef(w.qv, P::qsat(K, P::es_ice(K, s.T, w.tc), w.p)) > 1.f;
+    return act;
+  }
+
+  // a2..a10 on an active point: FP32 throughout, except the initial vapour
+  // difference of the adjustment, formed in FP64
+  static __device__ __forceinline__ void process(const ConstK<float> &K, const Pt &s, double dt, W<float> &w,
+                                                 float es0, float qs0, MixInc &o) {
+    w.rho = d2f(s.rho);
+    w.nc = d2f(s.nc);
+    w.nr = d2f(s.nr);
+    w.nx[0] = d2f(s.ni);
+    w.nx[1] = d2f(s.ns);
+    w.nx[2] = d2f(s.ng);
+    const float na = d2f(s.na);
+    w.hmax = max(w.hmax, max(max(max(hiabs(s.rho), hiabs(s.w)), max(hiabs(s.nc), hiabs(s.nr))),
+                             max(max(hiabs(s.ni), hiabs(s.ns)), max(hiabs(s.ng), hiabs(s.na)))));
+    o.vc = 0.f;
+    o.evap_all = false;
+    o.dT = 0.f;
+    // a2: Newton on the temperature increment; qv - qs(T + dT) is the FP64
+    // difference at dT = 0 plus the FP32 change of qs
+    if (w.qv > qs0 || w.qc > K.qmin) {
+      const float d0 = d2f(s.qv - f2d(qs0));
+      float dT = 0.f, es = es0, qs = qs0;
+#pragma unroll
+      for (int it = 0; it < 4; ++it) {
+        const float tc = w.tc + dT;
+        if (it > 0) {
+          es = P::es_liq(K, tc);
+          qs = P::qsat(K, es, w.p);
+        }
+        const float d = d0 + (qs0 - qs);
+        const float f = dT - K.lv_cp * d;
+        const float e1 = tc + K.eslb;
+        const float des = es * K.eslab * rcpa(e1 * e1);
+        const float den = w.p - K.ome * es;
+        const float fp = 1.f + K.lv_cp * K.eps * w.p * des * rcpa(den * den);
+        dT = dT - __fdividef(f, fp);
+      }
+      float dq = K.cp_lv * dT;
+      if (dq <= -w.qc) {
+        dq = -w.qc;
+        o.evap_all = true;
+      }
+      o.vc = dq;
+      const float dTs = K.lv_cp * dq;
+      o.dT = dTs;
+      w.T += dTs;
+      w.tc += dTs;
+      w.qv -= dq;
+      w.qc = o.evap_all ? 0.f : w.qc + dq;
+    }
+    // a3
+    o.dna = 0.f;
+    float dnc_act = 0.f;
+    const float wv = d2f(s.w);
+    if (wv > 0.f && w.qc > K.qmin) {
+      const float N = w.rho * (na + w.nc);
+      if (N > 0.f) {
+        const float nact = P::arg_nact(K, N, wv, w.T, w.p, P::es_liq(K, w.tc));
+        float dn = __fdividef(nact, w.rho) - w.nc;
+        dn = fminf(fmaxf(dn, 0.f), na);
+        dnc_act = dn;
+        o.dna = -dn;
+        w.nc += dn;
+      }
+    }
+    // a4..a10
+    Rt<float> r;
+    P::rates(K, w, dt, r);
+    Gt<float> g;
+    P::limits(K, w, dt, r, g);
+    const float dtr = d2f(dt);
+    o.cr = (g.aut * r.aut + g.acc * r.acc) * dtr;
+    o.cg = (g.rs * r.rim[0] + g.rg * r.rim[1]) * dtr;
+    o.rv = g.evr * r.evr * dtr;
+    o.vx[0] = (g.nuc * g.nucm + g.dep[0] * r.dep[0]) * dtr;   // signed: deposition > 0
+    o.vx[1] = g.dep[1] * r.dep[1] * dtr;
+    o.vx[2] = g.dep[2] * r.dep[2] * dtr;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) o.xr[m] = g.mlt[m] * r.mlt[m] * dtr;
+    o.dn[0] = dnc_act - (g.aut * r.aut * g.rc + g.acc * r.acc * g.rc + g.scc * r.scc + g.rs * r.rim[0] * g.rc +
+                         g.rg * r.rim[1] * g.rc) * dtr;
+    o.dn[1] = (g.aut * r.aut * K.inv_mr0 - g.scr * r.scr - g.evr * r.evr * g.rr + g.mlt[0] * g.nmlt[0] +
+               g.mlt[1] * g.nmlt[1] + g.mlt[2] * g.nmlt[2]) * dtr;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const float sn = r.dep[m] < 0.f ? g.dep[m] * g.sub[m] * g.rx[m] : 0.f;
+      o.dn[2 + m] = (m == 0 ? g.nuc * r.nucn : 0.f) * dtr - (sn + g.mlt[m] * g.nmlt[m]) * dtr;
+    }
+    o.dT += (K.ls * (o.vx[0] + o.vx[1] + o.vx[2]) + K.lf * o.cg - K.lv * o.rv - K.lf * (o.xr[0] + o.xr[1] + o.xr[2])) *
+            K.inv_cp;
+  }
+
+  // apply the process increments to the FP64 state: every mass transfer is
+  // one FP32 amount subtracted from its source and added to its destination
+  static __device__ __forceinline__ void apply_masses(Pt &s, const MixInc &o) {
+    if (o.evap_all) {
+      s.qv += s.qc;
+      s.qc = 0.0;
+    } else if (o.vc != 0.f) {
+      const double d = f2d(o.vc);
+      s.qv -= d;
+      s.qc += d;
+    }
+    if (o.cr != 0.f) { const double d = f2d(o.cr); s.qc -= d; s.qr += d; }
+    if (o.cg != 0.f) { const double d = f2d(o.cg); s.qc -= d; s.qg += d; }
+    if (o.rv != 0.f) { const double d = f2d(o.rv); s.qr -= d; s.qv += d; }
+    if (o.vx[0] != 0.f) { const double d = f2d(o.vx[0]); s.qv -= d; s.qi += d; }
+    if (o.vx[1] != 0.f) { const double d = f2d(o.vx[1]); s.qv -= d; s.qs += d; }
+    if (o.vx[2] != 0.f) { const double d = f2d(o.vx[2]); s.qv -= d; s.qg += d; }
+    if (o.xr[0] != 0.f) { const double d = f2d(o.xr[0]); s.qi -= d; s.qr += d; }
+    if (o.xr[1] != 0.f) { const double d = f2d(o.xr[1]); s.qs -= d; s.qr += d; }
+    if (o.xr[2] != 0.f) { const double d = f2d(o.xr[2]); s.qg -= d; s.qr += d; }
+    if (o.dT != 0.f) s.T += f2d(o.dT);
+    if (o.dna != 0.f) s.na += f2d(o.dna);
   }
 };
 
 // ---------------------------------------------------------------- kernels
-__device__ __forceinline__ size_t fidx(const KArgs &a, int f, int k, int c) {
-  return ((size_t)f * (size_t)a.nlev + (size_t)k) * (size_t)a.pitch + (size_t)c;
-}
-
 __device__ __forceinline__ void load_pt(const KArgs &a, int k, int c, Pt &s) {
   const double *b = a.fld + (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
@@ -622,6 +694,109 @@ __device__ __forceinline__ double &nref(Pt &s, int x) {
   return x == 0 ? s.nr : x == 1 ? s.ni : x == 2 ? s.ns : s.ng;
 }
 
+// Block prologue: dz and dz/dt of every level into shared memory, and whether
+// every species' capped speed keeps within one level per step.
+struct Smem {
+  double dz[kMaxLev];
+  double dzdt[kMaxLev];
+  double red[kBlock / 32];
+  int fast;
+};
+
+__device__ __forceinline__ bool prologue(const KArgs &a, const KParams &P, Smem &sm) {
+  double dzmin = 1e300;
+  for (int k = threadIdx.x; k < a.nlev; k += blockDim.x) {
+    const double v = a.dz[k];
+    sm.dz[k] = v;
+    sm.dzdt[k] = v / a.dt;
+    dzmin = fmin(dzmin, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) dzmin = fmin(dzmin, __shfl_xor_sync(0xffffffffu, dzmin, o));
+  if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = dzmin;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = sm.red[0];
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmin(m, sm.red[i]);
+    int fast = 1;
+    for (int x = 1; x < 5; ++x) fast &= ((P.vmax[x] * a.dt) / m) / P.c_max <= 1.0;
+    sm.fast = fast;
+  }
+  __syncthreads();
+  return sm.fast != 0;
+}
+
+// Multi-substep sedimentation of one column after the processes (used when a
+// capped speed could exceed one level per step): per species, n_sub from the
+// largest Courant number, then n_sub top-down sweeps in place.
+template <class M>
+__device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KParams &P, const Smem &sm, int c,
+                                                      double prec[4]) {
+  using R = typename M::R;
+  using Ph = Phys<M>;
+  const ConstK<R> &K = M::K(P);
+  unsigned eflag = 0;
+  const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
+  const double *rhop = a.fld + 14 * fs;
+  for (int x = 0; x < 4; ++x) {
+    double *qp = a.fld + (3 + x) * fs;
+    double *np = a.fld + (8 + x) * fs;
+    R cmax = 0;
+    for (int k = 0; k < a.nlev; ++k) {
+      const size_t o = (size_t)k * a.pitch + c;
+      const R q = M::toR(qp[o]);
+      if (!(q > K.qmin)) continue;
+      const R rho = M::toR(__ldg(rhop + o));
+      const R dfac = M::ex((R)0.4 * (K.lgrho0 - M::lg(rho)));
+      R vq, vn;
+      Ph::fall_speeds(K, (R)1e30, M::lg(q), M::toR(np[o]), dfac, x, vq, vn);
+      cmax = M::mx(cmax, M::div(vq * M::toR(a.dt), M::toR(sm.dz[k])));
+    }
+    int ns = (int)ceil((double)M::div(cmax, M::toR(P.c_max)));
+    if (ns < 1) ns = 1;
+    if (ns > 64) { ns = 64; eflag |= 2u; }
+    const double dts = a.dt / ns;
+    for (int st = 0; st < ns; ++st) {
+      R Fu = 0, Gu = 0;
+      for (int k = a.nlev - 1; k >= 0; --k) {
+        const size_t o = (size_t)k * a.pitch + c;
+        double q = qp[o], n = np[o];
+        const double rhod = __ldg(rhop + o);
+        const R qR = M::toR(q), rho = M::toR(rhod);
+        R F = 0, G = 0;
+        if (qR > K.qmin) {
+          const R dfac = M::ex((R)0.4 * (K.lgrho0 - M::lg(rho)));
+          R vq, vn;
+          Ph::fall_speeds(K, M::toR(sm.dz[k] / dts), M::lg(qR), M::toR(n), dfac, x, vq, vn);
+          if constexpr (!M::kMixed) {
+            F = rhod * q * vq;
+            G = rhod * (n > 0.0 ? n : 0.0) * vn;
+          } else {
+            F = rho * qR * vq;
+            G = rho * M::mx(M::toR(n), (R)0) * vn;
+          }
+        }
+        if (F != (R)0 || Fu != (R)0 || G != (R)0 || Gu != (R)0) {
+          if constexpr (!M::kMixed) {
+            q += dts * (Fu - F) / (rhod * sm.dz[k]);
+            n += dts * (Gu - G) / (rhod * sm.dz[k]);
+          } else {
+            const R sc = M::div(M::toR(dts), rho * M::toR(sm.dz[k]));
+            q += M::toD((Fu - F) * sc);
+            n += M::toD((Gu - G) * sc);
+          }
+          qp[o] = q;
+          np[o] = n;
+          eflag |= nonfinite(q) | nonfinite(n);
+        }
+        Fu = F;
+        Gu = G;
+      }
+      prec[x] += M::toD(Fu) * dts;
+    }
+  }
+  return eflag;
+}
+
 // One timestep for ncols columns.  When every species' capped fall speed
 // satisfies vmax dt / min(dz) <= c_max, each column needs exactly one
 // sedimentation substep and the flux recurrence is fused into the top-down
@@ -629,165 +804,128 @@ __device__ __forceinline__ double &nref(Pt &s, int x) {
 // the processes are applied first and each species is sedimented with its
 // own substep count in further sweeps over the column.
 template <class M>
-__global__ void __launch_bounds__(kBlock) k_step(const KArgs a, const KParams P) {
+__global__ void __launch_bounds__(kBlock, M::kMixed ? 4 : 3) k_step(const KArgs a, const KParams P) {
   using R = typename M::R;
-  using C = Chain<M>;
-  __shared__ double s_dz[kMaxLev];
-  __shared__ int s_fast;
+  using Ph = Phys<M>;
+  __shared__ Smem sm;
   const ConstK<R> &K = M::K(P);
-
-  double dzmin = 1e300;
-  for (int k = threadIdx.x; k < a.nlev; k += blockDim.x) {
-    const double v = a.dz[k];
-    s_dz[k] = v;
-    dzmin = fmin(dzmin, v);
-  }
-  // block-wide minimum of dz
-  for (int o = 16; o > 0; o >>= 1) dzmin = fmin(dzmin, __shfl_xor_sync(0xffffffffu, dzmin, o));
-  __shared__ double s_red[kBlock / 32];
-  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = dzmin;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = s_red[0];
-    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmin(m, s_red[i]);
-    int fast = 1;
-    for (int x = 1; x < 5; ++x) fast &= ((P.vmax[x] * a.dt) / m) / P.c_max <= 1.0;
-    s_fast = fast;
-  }
-  __syncthreads();
-  const bool fast = s_fast != 0;
+  const bool fast = prologue(a, P, sm);
 
   const int c = blockIdx.x * kBlock + threadIdx.x;
   if (c >= a.ncols) return;
 
   unsigned eflag = 0;
   double prec[4] = {0.0, 0.0, 0.0, 0.0};
+  // carried downward fluxes F_{k+1}, G_{k+1} (kg m^-2 s^-1, m^-2 s^-1)
+  R Fq[4] = {0, 0, 0, 0}, Fn[4] = {0, 0, 0, 0};
 
-  if (fast) {
-    // carried downward fluxes F_{k+1}, G_{k+1} (kg m^-2 s^-1, m^-2 s^-1)
-    R Fq[4] = {0, 0, 0, 0}, Fn[4] = {0, 0, 0, 0};
-    for (int k = a.nlev - 1; k >= 0; --k) {
-      Pt s;
-      load_pt(a, k, c, s);
+  for (int k = a.nlev - 1; k >= 0; --k) {
+    Pt s;
+    load_pt(a, k, c, s);
+    bool touched;
+    if constexpr (!M::kMixed) {
       eflag |= nonfinite_in(s);
-      R tc0, es0, qs0;
-      const bool act = C::active(K, s, tc0, es0, qs0);
-      if (act) {
-        C::satadj(K, s, tc0, es0, qs0);
-        C::activate(K, s);
-        C::rates_and_limit(K, s, a.dt);
-      }
-      const double dzk = s_dz[k];
-      const R vguard = M::toR(dzk / a.dt);
-      const R rho = M::toR(s.rho);
-      bool touched = act;
+      double es0, qs0;
+      touched = F64::active(K, s, es0, qs0);
+      if (touched) F64::process(K, s, a.dt, es0, qs0);
+      if (fast) {
+        const double dzk = sm.dz[k];
+        const double dfac = ::exp(0.4 * (K.lgrho0 - ::log(s.rho)));
 #pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        double &q = qref(s, x);
-        double &n = nref(s, x);
-        R F = 0, G = 0;
-        const R qR = M::toR(q);
-        if (qR > K.qmin) {
-          R vq, vn;
-          C::fall_speeds(K, vguard, qR, M::toR(n), rho, x, vq, vn);
-          if constexpr (!M::kMixed) {
+        for (int x = 0; x < 4; ++x) {
+          double &q = qref(s, x);
+          double &n = nref(s, x);
+          double F = 0, G = 0;
+          if (q > K.qmin) {
+            double vq, vn;
+            Ph::fall_speeds(K, sm.dzdt[k], ::log(q), n, dfac, x, vq, vn);
             F = s.rho * q * vq;
             G = s.rho * (n > 0.0 ? n : 0.0) * vn;
-          } else {
-            F = rho * qR * vq;
-            G = rho * M::mx(M::toR(n), (R)0) * vn;
           }
-        }
-        if (F != (R)0 || Fq[x] != (R)0 || G != (R)0 || Fn[x] != (R)0) {
-          if constexpr (!M::kMixed) {
+          if (F != 0.0 || Fq[x] != 0.0 || G != 0.0 || Fn[x] != 0.0) {
             q += a.dt * (Fq[x] - F) / (s.rho * dzk);
             n += a.dt * (Fn[x] - G) / (s.rho * dzk);
-          } else {
-            const R sc = M::div(M::toR(a.dt), rho * M::toR(dzk));
-            q += M::toD((Fq[x] - F) * sc);
-            n += M::toD((Fn[x] - G) * sc);
+            touched = true;
           }
-          touched = true;
+          Fq[x] = F;
+          Fn[x] = G;
         }
-        Fq[x] = F;
-        Fn[x] = G;
       }
-      if (touched) eflag |= store_pt(a, k, c, s);
+    } else {
+      W<float> w;
+      float es0, qs0;
+      const bool act = Mix::active(K, s, P.T0, w, es0, qs0);
+      MixInc o;
+      float dn[4] = {0.f, 0.f, 0.f, 0.f};   // number increments of r, i, s, g
+      float qpost[4], npost[4];
+      if (act) {
+        Mix::process(K, s, a.dt, w, es0, qs0, o);
+        Mix::apply_masses(s, o);
+        if (o.dn[0] != 0.f) s.nc += f2d(o.dn[0]);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) dn[x] = o.dn[1 + x];
+        // post-process FP32 masses and numbers for the fall speeds
+        qpost[0] = w.qr + o.cr - o.rv + o.xr[0] + o.xr[1] + o.xr[2];
+        qpost[1] = w.qx[0] + o.vx[0] - o.xr[0];
+        qpost[2] = w.qx[1] + o.vx[1] - o.xr[1];
+        qpost[3] = w.qx[2] + o.vx[2] + o.cg - o.xr[2];
+        npost[0] = w.nr + dn[0];
+#pragma unroll
+        for (int x = 1; x < 4; ++x) npost[x] = w.nx[x - 1] + dn[x];
+      } else {
+        qpost[0] = w.qr;
+        qpost[1] = w.qx[0];
+        qpost[2] = w.qx[1];
+        qpost[3] = w.qx[2];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) npost[x] = 0.f;   // read only where a species is present
+      }
+      touched = act;
+      if (fast) {
+        bool any = false;
+#pragma unroll
+        for (int x = 0; x < 4; ++x) any |= qpost[x] > K.qmin || Fq[x] != 0.f || Fn[x] != 0.f;
+        if (any) {
+          if (!act) w.hmax = max(w.hmax, hiabs(s.rho));
+          const float rho = act ? w.rho : d2f(s.rho);
+          const float dfac = ex2a(0.4f * (K.lgrho0 - lg2a(rho)));
+          const float sc = __fdividef(d2f(a.dt), rho * d2f(sm.dz[k]));
+          const float guard = d2f(sm.dzdt[k]);
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            float F = 0.f, G = 0.f;
+            if (qpost[x] > K.qmin) {
+              const float n = act ? npost[x] : d2f(nref(s, x));
+              float vq, vn;
+              Ph::fall_speeds(K, guard, lg2a(qpost[x]), n, dfac, x, vq, vn);
+              F = rho * qpost[x] * vq;
+              G = rho * fmaxf(n, 0.f) * vn;
+            }
+            if (F != 0.f || Fq[x] != 0.f) {
+              qref(s, x) += f2d((Fq[x] - F) * sc);
+              touched = true;
+            }
+            if (G != 0.f || Fn[x] != 0.f) {
+              dn[x] += (Fn[x] - G) * sc;
+              touched = true;
+            }
+            Fq[x] = F;
+            Fn[x] = G;
+          }
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+        if (dn[x] != 0.f) nref(s, x) += f2d(dn[x]);
+      eflag |= w.hmax >= 0x7ff00000u;
     }
+    if (touched) eflag |= store_pt(a, k, c, s);
+  }
+  if (fast) {
 #pragma unroll
     for (int x = 0; x < 4; ++x) prec[x] = M::toD(Fq[x]) * a.dt;
   } else {
-    // processes first ...
-    for (int k = a.nlev - 1; k >= 0; --k) {
-      Pt s;
-      load_pt(a, k, c, s);
-      eflag |= nonfinite_in(s);
-      R tc0, es0, qs0;
-      if (C::active(K, s, tc0, es0, qs0)) {
-        C::satadj(K, s, tc0, es0, qs0);
-        C::activate(K, s);
-        C::rates_and_limit(K, s, a.dt);
-        eflag |= store_pt(a, k, c, s);
-      }
-    }
-    // ... then each species with its own substep count
-    const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
-    const double *rhop = a.fld + 14 * fs;
-    for (int x = 0; x < 4; ++x) {
-      double *qp = a.fld + (3 + x) * fs;
-      double *np = a.fld + (8 + x) * fs;
-      R cmax = 0;
-      for (int k = 0; k < a.nlev; ++k) {
-        const size_t o = (size_t)k * a.pitch + c;
-        const R q = M::toR(qp[o]);
-        if (!(q > K.qmin)) continue;
-        R vq, vn;
-        C::fall_speeds(K, (R)1e30, q, M::toR(np[o]), M::toR(__ldg(rhop + o)), x, vq, vn);
-        const R cr = M::div(vq * M::toR(a.dt), M::toR(s_dz[k]));
-        cmax = M::mx(cmax, cr);
-      }
-      int ns = (int)ceil((double)M::div(cmax, M::toR(P.c_max)));
-      if (ns < 1) ns = 1;
-      if (ns > 64) { ns = 64; eflag |= 2u; }
-      const double dts = a.dt / ns;
-      for (int st = 0; st < ns; ++st) {
-        R Fu = 0, Gu = 0;
-        for (int k = a.nlev - 1; k >= 0; --k) {
-          const size_t o = (size_t)k * a.pitch + c;
-          double q = qp[o], n = np[o];
-          const double rhod = __ldg(rhop + o);
-          const R qR = M::toR(q), rho = M::toR(rhod);
-          R F = 0, G = 0;
-          if (qR > K.qmin) {
-            R vq, vn;
-            C::fall_speeds(K, M::toR(s_dz[k] / dts), qR, M::toR(n), rho, x, vq, vn);
-            if constexpr (!M::kMixed) {
-              F = rhod * q * vq;
-              G = rhod * (n > 0.0 ? n : 0.0) * vn;
-            } else {
-              F = rho * qR * vq;
-              G = rho * M::mx(M::toR(n), (R)0) * vn;
-            }
-          }
-          if (F != (R)0 || Fu != (R)0 || G != (R)0 || Gu != (R)0) {
-            if constexpr (!M::kMixed) {
-              q += dts * (Fu - F) / (rhod * s_dz[k]);
-              n += dts * (Gu - G) / (rhod * s_dz[k]);
-            } else {
-              const R sc = M::div(M::toR(dts), rho * M::toR(s_dz[k]));
-              q += M::toD((Fu - F) * sc);
-              n += M::toD((Gu - G) * sc);
-            }
-            qp[o] = q;
-            np[o] = n;
-            eflag |= nonfinite(q) | nonfinite(n);
-          }
-          Fu = F;
-          Gu = G;
-        }
-        prec[x] += M::toD(Fu) * dts;
-      }
-    }
+    eflag |= sediment_substeps<M>(a, P, sm, c, prec);
   }
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
@@ -805,9 +943,9 @@ __global__ void __launch_bounds__(256) k_budget(const KArgs a, double *out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= a.ncols) return;
   double wsum = 0.0, nsum = 0.0;
+  const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
   for (int k = 0; k < a.nlev; ++k) {
     const size_t o = (size_t)k * a.pitch + c;
-    const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
     const double m = a.fld[14 * fs + o] * a.dz[k];
     wsum += m * (((((a.fld[1 * fs + o] + a.fld[2 * fs + o]) + a.fld[3 * fs + o]) + a.fld[4 * fs + o]) +
                   a.fld[5 * fs + o]) + a.fld[6 * fs + o]);
