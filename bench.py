@@ -113,6 +113,98 @@ def cpu_oracle_rate(recipe_fld, dz, ncols_total, dt, target_s=10.0, max_cols=Non
         cols = int(cols * min(16.0, max(2.0, target_s / max(el, 1e-3))))
 
 
+def bench_batch(args, rank, world, local):
+    """64 uneven domains (column counts log-uniform 1k-100k, 40-150 levels,
+    cloud fraction 5-60 %), mixed form, one persistent launch per step over the
+    active-column list, configuration picked by the autotuner, steps replayed
+    from a CUDA graph of 10 steps."""
+    import torch
+    from paper_2010_14823_gb300 import casim, synth
+    casim.lib()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    doms, dt = synth.batch_workload(64, seed=1237 + rank)
+    dev = [casim.Domain(f, dz, nc) for f, dz, nc, nl in doms]
+    del doms
+    npts = sum(d.ncols * d.nlev for d in dev)
+    stream = torch.cuda.current_stream()
+
+    def sync():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED)
+    b = casim.casim_batch_create(ctx, [d.state for d in dev], [d.ncols for d in dev], [d.nlev for d in dev])
+    table = casim.casim_batch_tune(ctx, b, dt, steps=2, stream=stream)
+    cfg = casim.casim_batch_get_config(b)
+    g = 10
+    casim.casim_batch_graph(ctx, b, dt, g, stream)
+    for _ in range(max(1, args.warmup // g)):
+        casim.casim_batch_graph_launch(b, stream)
+    nrep = max(1, args.steps // g)
+    sync()
+    n0 = casim.casim_launch_count(ctx)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nrep):
+        casim.casim_batch_graph_launch(b, stream)
+    e1.record(stream)
+    sync()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = casim.casim_launch_count(ctx) - n0
+    rc, fl = casim.casim_get_error(ctx, stream)
+    assert rc == 0, (rc, fl)
+    steps = nrep * g
+    value = world * npts * steps / (ms * 1e-3)
+    # the same batch stepped eagerly, one launch pair per step, and the FP64 form
+    e0.record(stream)
+    for _ in range(g):
+        casim.casim_batch_step(ctx, b, dt, stream)
+    e1.record(stream)
+    sync()
+    eager_ms = e0.elapsed_time(e1) / g
+    casim.casim_batch_free(b)
+    casim.casim_free(ctx)
+    ctx64 = casim.casim_init(precision=casim.CASIM_FP64)
+    b64 = casim.casim_batch_create(ctx64, [d.state for d in dev], [d.ncols for d in dev], [d.nlev for d in dev])
+    casim.casim_batch_step(ctx64, b64, dt, stream)
+    sync()
+    e0.record(stream)
+    casim.casim_batch_step(ctx64, b64, dt, stream)
+    e1.record(stream)
+    sync()
+    fp64_ms = e0.elapsed_time(e1)
+    casim.casim_batch_free(b64)
+    casim.casim_free(ctx64)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "batch64", "domains": 64, "grid_points": npts,
+                           "columns": int(sum(d.ncols for d in dev)),
+                           "form": "mixed, batched persistent launch, CUDA graph of 10 steps",
+                           "tuned": {"block": cfg[0], "compact": cfg[1], "persistent": cfg[2]},
+                           "tune_table": table, "eager_ms_per_step": eager_ms,
+                           "fp64_ms_per_step": fp64_ms, "fp64_value": world * npts / (fp64_ms * 1e-3),
+                           "l2": "state %.1f GB > L2, no flush needed" % (16 * 8 * sum(d.nlev * d.pitch for d in dev) / 1e9)},
+                "roofline": None, "cpu_baseline": None, "e2e": None,
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -132,6 +224,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     from paper_2010_14823_gb300 import synth
+    if args.workload == "batch64":
+        return bench_batch(args, rank, world, local)
     base_fld, dz, ncols, nlev, dt, _ = synth.workload(args.workload, ncols=args.ncols, seed=1236 + rank)
     forms = set(args.forms.split(","))
     npts = ncols * nlev

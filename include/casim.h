@@ -139,6 +139,62 @@ int casim_budget(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, doub
    CASIM_ERR_CFL (the first set, in that order of precedence), or CASIM_ERR_CUDA. */
 int casim_get_error(casim_ctx *ctx, unsigned *flags, void *stream);
 
+/* ----------------------------------------------------------------------------
+ * Batches: many independent domains advanced by one launch per step.
+ * (Section 2: columns are independent, so domains of different sizes can share
+ * one launch; Section 3.4: the best launch configuration depends on the
+ * column count and must be found by experiment -- casim_batch_tune does so.)
+ * ------------------------------------------------------------------------- */
+typedef struct casim_batch casim_batch;
+
+/* One measured candidate of casim_batch_tune. */
+typedef struct {
+  int block;          /* threads (columns) per block: 64, 128 or 256 */
+  int compact;        /* 1: flag pass + active-column list, 0: every column */
+  int persistent;     /* 1: one resident wave taking items from a counter, 0: one item per block */
+  float ms_per_step;
+} casim_tune_entry;
+
+/* Describe ndom domains (device states as for casim_step; ncols[i] >= 0,
+   1 <= nlev[i] <= 1024).  Reads every domain's dz once (they must not change
+   afterwards), orders work by descending level count and allocates the
+   batch's device scratch: a domain table, an active-column list of
+   sum(ncols) ints, per-domain counts, a work counter.  The default launch
+   configuration is block 128, compaction on, persistent grid. */
+int casim_batch_create(casim_ctx *ctx, const casim_state *domains, const int *ncols, const int *nlev, int ndom,
+                       casim_batch **batch);
+
+/* Advance every domain of the batch by dt (asynchronous on `stream`): an
+   optional flag/compaction launch and one step launch. Results are identical,
+   bit for bit, to casim_step on each domain, for every launch configuration. */
+int casim_batch_step(casim_ctx *ctx, casim_batch *batch, double dt, void *stream);
+
+/* Set / read the launch configuration (invalidates a captured graph). */
+int casim_batch_config(casim_batch *batch, int block, int compact, int persistent);
+int casim_batch_get_config(const casim_batch *batch, int *block, int *compact, int *persistent);
+
+/* Autotuner: times the 12 configurations (block 64/128/256 x compaction x
+   persistent), each for 1 warm-up and `steps` timed steps, and keeps the
+   fastest.  These are REAL timesteps of the batch: the state advances by
+   casim_batch_tune_steps(steps) = 12 (steps + 1) steps.  Fills up to
+   table_len entries of `table` (may be NULL when table_len is 0).
+   Synchronises `stream`. */
+int casim_batch_tune(casim_ctx *ctx, casim_batch *batch, double dt, int steps, void *stream,
+                     casim_tune_entry *table, int table_len);
+int casim_batch_tune_steps(int steps);
+
+/* Capture nsteps steps of the batch (current configuration, this dt) into a
+   CUDA graph held by the batch; casim_batch_graph_launch replays it on
+   `stream`.  A new capture or configuration replaces the graph. */
+int casim_batch_graph(casim_ctx *ctx, casim_batch *batch, double dt, int nsteps, void *stream);
+int casim_batch_graph_launch(casim_batch *batch, void *stream);
+
+/* Total columns of the batch (sum of ncols). */
+long long casim_batch_columns(const casim_batch *batch);
+
+/* Release the batch (waits for the device). NULL is a no-op. */
+void casim_batch_free(casim_batch *batch);
+
 /* Number of kernel launches this context has enqueued since casim_init. */
 long long casim_launch_count(const casim_ctx *ctx);
 

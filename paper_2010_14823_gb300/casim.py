@@ -56,6 +56,11 @@ class casim_state(ctypes.Structure):
                 ("dz", ctypes.c_void_p), ("precip", ctypes.c_void_p)]
 
 
+class casim_tune_entry(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("compact", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("ms_per_step", ctypes.c_float)]
+
+
 _lib = None
 
 
@@ -89,6 +94,27 @@ def lib():
         L.casim_free.restype = None
         L.casim_abi_version.argtypes = []
         L.casim_abi_version.restype = i
+        pi = ctypes.POINTER(i)
+        L.casim_batch_create.argtypes = [vp, ps, pi, pi, i, ctypes.POINTER(vp)]
+        L.casim_batch_create.restype = i
+        L.casim_batch_step.argtypes = [vp, vp, d, vp]
+        L.casim_batch_step.restype = i
+        L.casim_batch_config.argtypes = [vp, i, i, i]
+        L.casim_batch_config.restype = i
+        L.casim_batch_get_config.argtypes = [vp, pi, pi, pi]
+        L.casim_batch_get_config.restype = i
+        L.casim_batch_tune.argtypes = [vp, vp, d, i, vp, ctypes.POINTER(casim_tune_entry), i]
+        L.casim_batch_tune.restype = i
+        L.casim_batch_tune_steps.argtypes = [i]
+        L.casim_batch_tune_steps.restype = i
+        L.casim_batch_graph.argtypes = [vp, vp, d, i, vp]
+        L.casim_batch_graph.restype = i
+        L.casim_batch_graph_launch.argtypes = [vp, vp]
+        L.casim_batch_graph_launch.restype = i
+        L.casim_batch_columns.argtypes = [vp]
+        L.casim_batch_columns.restype = ctypes.c_longlong
+        L.casim_batch_free.argtypes = [vp]
+        L.casim_batch_free.restype = None
         _lib = L
     return _lib
 
@@ -177,6 +203,59 @@ def casim_free(ctx):
 
 def casim_abi_version() -> int:
     return lib().casim_abi_version()
+
+
+def casim_batch_create(ctx, states, ncols, nlev):
+    """states: list of casim_state (device); ncols, nlev: lists of ints."""
+    n = len(states)
+    arr = (casim_state * n)(*states)
+    nc = (ctypes.c_int * n)(*ncols)
+    nl = (ctypes.c_int * n)(*nlev)
+    b = ctypes.c_void_p()
+    _check(lib().casim_batch_create(ctx, arr, nc, nl, n, ctypes.byref(b)), "casim_batch_create")
+    return b
+
+
+def casim_batch_step(ctx, batch, dt: float, stream=None):
+    _check(lib().casim_batch_step(ctx, batch, dt, _stream(stream)), "casim_batch_step")
+
+
+def casim_batch_config(batch, block: int, compact: int, persistent: int):
+    _check(lib().casim_batch_config(batch, block, compact, persistent), "casim_batch_config")
+
+
+def casim_batch_get_config(batch) -> tuple[int, int, int]:
+    b, c, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().casim_batch_get_config(batch, ctypes.byref(b), ctypes.byref(c), ctypes.byref(p)),
+           "casim_batch_get_config")
+    return b.value, c.value, p.value
+
+
+def casim_batch_tune(ctx, batch, dt: float, steps: int = 2, stream=None) -> list[dict]:
+    table = (casim_tune_entry * 12)()
+    _check(lib().casim_batch_tune(ctx, batch, dt, steps, _stream(stream), table, 12), "casim_batch_tune")
+    return [{"block": e.block, "compact": e.compact, "persistent": e.persistent, "ms_per_step": e.ms_per_step}
+            for e in table]
+
+
+def casim_batch_tune_steps(steps: int) -> int:
+    return lib().casim_batch_tune_steps(steps)
+
+
+def casim_batch_graph(ctx, batch, dt: float, nsteps: int, stream=None):
+    _check(lib().casim_batch_graph(ctx, batch, dt, nsteps, _stream(stream)), "casim_batch_graph")
+
+
+def casim_batch_graph_launch(batch, stream=None):
+    _check(lib().casim_batch_graph_launch(batch, _stream(stream)), "casim_batch_graph_launch")
+
+
+def casim_batch_columns(batch) -> int:
+    return lib().casim_batch_columns(batch)
+
+
+def casim_batch_free(batch):
+    lib().casim_batch_free(batch)
 
 
 class Domain:

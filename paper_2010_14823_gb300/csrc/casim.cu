@@ -11,14 +11,19 @@
 #include <cstring>
 #include <cstdint>
 
+#include <algorithm>
+#include <vector>
+
 #include "casim.h"
 #include "casim_device.cuh"
+#include "casim_batch.cuh"
 
 using namespace casim_dev;
 
 struct casim_ctx {
   int precision = CASIM_FP64;
   int device = 0;
+  int nsm = 1;
   KParams kp;
   unsigned *d_err = nullptr;
   long long launches = 0;
@@ -175,6 +180,7 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   ctx->kp.T0 = p.T0;
   for (int x = 0; x < 5; ++x) ctx->kp.vmax[x] = p.vmax[x];
   cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
@@ -291,6 +297,287 @@ extern "C" int casim_get_error(casim_ctx *ctx, unsigned *flags, void *stream) {
   if (h & CASIM_EFLAG_CFL) return CASIM_ERR_CFL;
   return CASIM_OK;
 }
+
+
+// ------------------------------------------------------------------ batches
+struct casim_batch {
+  casim_ctx *ctx = nullptr;
+  int ndom = 0;
+  std::vector<DomDesc> dom;       // host copy of the device table
+  std::vector<int> order;         // domains by descending level count
+  DomDesc *d_dom = nullptr;
+  int *d_list = nullptr, *d_count = nullptr, *d_counter = nullptr;
+  Item *d_tiles = nullptr;
+  int ntiles = 0;
+  Item *d_items = nullptr;
+  int nitems = 0, items_block = 0, items_cap = 0;
+  long long total_cols = 0;
+  int block = 128, compact = 1, persistent = 1;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_steps = 0;
+};
+
+static std::vector<Item> make_items(const casim_batch &b, int width) {
+  std::vector<Item> v;
+  for (int d : b.order) {
+    const int n = (b.dom[d].ncols + width - 1) / width;
+    for (int ch = 0; ch < n; ++ch) v.push_back(Item{d, ch});
+  }
+  return v;
+}
+
+static int set_items(casim_batch *b, int block) {
+  if (b->items_block == block) return CASIM_OK;
+  std::vector<Item> v = make_items(*b, block);
+  if ((int)v.size() > b->items_cap) {
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_items = nullptr;
+    b->items_cap = 0;
+    cudaError_t e = cudaMalloc(&b->d_items, std::max<size_t>(1, v.size()) * sizeof(Item));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CASIM_ERR_OOM : cuda_fail(e, "cudaMalloc");
+    b->items_cap = (int)v.size();
+  }
+  if (!v.empty()) CUDA_TRY(cudaMemcpy(b->d_items, v.data(), v.size() * sizeof(Item), cudaMemcpyHostToDevice));
+  b->nitems = (int)v.size();
+  b->items_block = block;
+  return CASIM_OK;
+}
+
+extern "C" void casim_batch_free(casim_batch *b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  cudaFree(b->d_dom);
+  cudaFree(b->d_list);
+  cudaFree(b->d_count);
+  cudaFree(b->d_counter);
+  cudaFree(b->d_tiles);
+  cudaFree(b->d_items);
+  delete b;
+}
+
+extern "C" int casim_batch_create(casim_ctx *ctx, const casim_state *domains, const int *ncols, const int *nlev,
+                                  int ndom, casim_batch **out) {
+  if (!out) return CASIM_ERR_ARG;
+  *out = nullptr;
+  if (!ctx || ndom < 1 || !domains || !ncols || !nlev) return CASIM_ERR_ARG;
+  casim_batch *b = new casim_batch();
+  b->ctx = ctx;
+  b->ndom = ndom;
+  b->dom.resize(ndom);
+  long long off = 0;
+  std::vector<double> hdz;
+  for (int i = 0; i < ndom; ++i) {
+    const casim_state &s = domains[i];
+    if (ncols[i] < 0 || nlev[i] < 1 || nlev[i] > kMaxLev) { delete b; return CASIM_ERR_ARG; }
+    if (ncols[i] > 0 && (check_state(&s, ncols[i], nlev[i], 1.0) != CASIM_OK)) { delete b; return CASIM_ERR_ARG; }
+    DomDesc &d = b->dom[i];
+    d.fld = s.fld;
+    d.pitch = s.pitch;
+    d.dz = s.dz;
+    d.precip = s.precip;
+    d.ncols = ncols[i];
+    d.nlev = nlev[i];
+    d.list_off = off;
+    d.dzmin = 1e300;
+    if (ncols[i] > 0) {
+      hdz.resize(nlev[i]);
+      cudaError_t e = cudaMemcpy(hdz.data(), s.dz, nlev[i] * sizeof(double), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) { delete b; return cuda_fail(e, "casim_batch_create: dz"); }
+      for (double v : hdz) {
+        if (!(v > 0.0)) { delete b; return CASIM_ERR_ARG; }
+        d.dzmin = std::min(d.dzmin, v);
+      }
+    }
+    off += ncols[i];
+  }
+  b->total_cols = off;
+  b->order.resize(ndom);
+  for (int i = 0; i < ndom; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return b->dom[x].nlev > b->dom[y].nlev; });
+  std::vector<Item> tiles = make_items(*b, kTile);
+  b->ntiles = (int)tiles.size();
+  cudaError_t e = cudaMalloc(&b->d_dom, ndom * sizeof(DomDesc));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_list, std::max<long long>(1, off) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_count, ndom * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(Item));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_dom, b->dom.data(), ndom * sizeof(DomDesc), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !tiles.empty())
+    e = cudaMemcpy(b->d_tiles, tiles.data(), tiles.size() * sizeof(Item), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    int rc = e == cudaErrorMemoryAllocation ? CASIM_ERR_OOM : cuda_fail(e, "casim_batch_create");
+    casim_batch_free(b);
+    return rc;
+  }
+  int rc = set_items(b, b->block);
+  if (rc != CASIM_OK) { casim_batch_free(b); return rc; }
+  *out = b;
+  return CASIM_OK;
+}
+
+static BatchArgs batch_args(const casim_batch *b, double dt) {
+  BatchArgs a;
+  a.dom = b->d_dom;
+  a.items = b->d_items;
+  a.nitems = b->nitems;
+  a.list = b->d_list;
+  a.count = b->d_count;
+  a.counter = b->d_counter;
+  a.err = b->ctx->d_err;
+  a.dt = dt;
+  a.compact = b->compact;
+  a.persistent = b->persistent;
+  return a;
+}
+
+template <class M>
+static int persistent_grid(const casim_batch *b) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch<M>, b->block, 0);
+  return std::max(1, per_sm) * b->ctx->nsm;
+}
+
+// enqueue one step of every domain (no validation; used by step and capture)
+static int enqueue_batch_step(casim_batch *b, double dt, cudaStream_t st) {
+  casim_ctx *ctx = b->ctx;
+  if (b->nitems == 0) return CASIM_OK;
+  const BatchArgs a = batch_args(b, dt);
+  if (b->compact) {
+    CUDA_TRY(cudaMemsetAsync(b->d_count, 0, b->ndom * sizeof(int), st));
+    if (ctx->precision == CASIM_MIXED)
+      k_compact<PolicyMix><<<b->ntiles, kTile, 0, st>>>(a, b->d_tiles, b->ntiles, ctx->kp);
+    else
+      k_compact<PolicyF64><<<b->ntiles, kTile, 0, st>>>(a, b->d_tiles, b->ntiles, ctx->kp);
+    ctx->launches++;
+    CUDA_TRY(cudaGetLastError());
+  }
+  if (b->persistent) CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
+  if (ctx->precision == CASIM_MIXED) {
+    const int grid = b->persistent ? std::min(b->nitems, persistent_grid<PolicyMix>(b)) : b->nitems;
+    k_step_batch<PolicyMix><<<grid, b->block, 0, st>>>(a, ctx->kp);
+  } else {
+    const int grid = b->persistent ? std::min(b->nitems, persistent_grid<PolicyF64>(b)) : b->nitems;
+    k_step_batch<PolicyF64><<<grid, b->block, 0, st>>>(a, ctx->kp);
+  }
+  ctx->launches++;
+  CUDA_TRY(cudaGetLastError());
+  return CASIM_OK;
+}
+
+extern "C" int casim_batch_step(casim_ctx *ctx, casim_batch *b, double dt, void *stream) {
+  if (!ctx || !b || b->ctx != ctx || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
+  return enqueue_batch_step(b, dt, (cudaStream_t)stream);
+}
+
+extern "C" int casim_batch_config(casim_batch *b, int block, int compact, int persistent) {
+  if (!b || (block != 64 && block != 128 && block != 256) || (compact != 0 && compact != 1) ||
+      (persistent != 0 && persistent != 1))
+    return CASIM_ERR_ARG;
+  int rc = set_items(b, block);
+  if (rc != CASIM_OK) return rc;
+  b->block = block;
+  b->compact = compact;
+  b->persistent = persistent;
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->graph_steps = 0;
+  }
+  return CASIM_OK;
+}
+
+extern "C" int casim_batch_get_config(const casim_batch *b, int *block, int *compact, int *persistent) {
+  if (!b) return CASIM_ERR_ARG;
+  if (block) *block = b->block;
+  if (compact) *compact = b->compact;
+  if (persistent) *persistent = b->persistent;
+  return CASIM_OK;
+}
+
+extern "C" int casim_batch_tune(casim_ctx *ctx, casim_batch *b, double dt, int steps, void *stream,
+                                casim_tune_entry *table, int table_len) {
+  if (!ctx || !b || b->ctx != ctx || steps < 1 || !(dt > 0.0) || table_len < 0 || (table_len && !table))
+    return CASIM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  static const int blocks[3] = {64, 128, 256};
+  float best = 1e30f;
+  int bb = b->block, bc = b->compact, bp = b->persistent;
+  int n = 0;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  int rc = CASIM_OK;
+  for (int bi = 0; bi < 3 && rc == CASIM_OK; ++bi)
+    for (int comp = 0; comp < 2 && rc == CASIM_OK; ++comp)
+      for (int pers = 0; pers < 2 && rc == CASIM_OK; ++pers) {
+        if ((rc = casim_batch_config(b, blocks[bi], comp, pers)) != CASIM_OK) break;
+        if ((rc = enqueue_batch_step(b, dt, st)) != CASIM_OK) break;   // warm-up (a real step)
+        cudaEventRecord(e0, st);
+        for (int s = 0; s < steps && rc == CASIM_OK; ++s) rc = enqueue_batch_step(b, dt, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "casim_batch_tune"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= steps;
+        if (n < table_len) {
+          table[n].block = blocks[bi];
+          table[n].compact = comp;
+          table[n].persistent = pers;
+          table[n].ms_per_step = ms;
+        }
+        ++n;
+        if (ms < best) { best = ms; bb = blocks[bi]; bc = comp; bp = pers; }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != CASIM_OK) return rc;
+  return casim_batch_config(b, bb, bc, bp);
+}
+
+extern "C" int casim_batch_tune_steps(int steps) { return 12 * (steps + 1); }
+
+extern "C" int casim_batch_graph(casim_ctx *ctx, casim_batch *b, double dt, int nsteps, void *stream) {
+  if (!ctx || !b || b->ctx != ctx || nsteps < 1 || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->graph_steps = 0;
+  }
+  // capture on a private stream (the legacy default stream cannot capture)
+  cudaStream_t cs;
+  CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  const long long l0 = ctx->launches;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int rc = CASIM_OK;
+  if (e == cudaSuccess) {
+    for (int s = 0; s < nsteps && rc == CASIM_OK; ++s) rc = enqueue_batch_step(b, dt, cs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (rc == CASIM_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "cudaStreamEndCapture");
+  } else {
+    rc = cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  ctx->launches = l0;   // captured, not launched
+  if (rc == CASIM_OK) {
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaGraphInstantiate");
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (rc == CASIM_OK) b->graph_steps = nsteps;
+  (void)stream;
+  return rc;
+}
+
+extern "C" int casim_batch_graph_launch(casim_batch *b, void *stream) {
+  if (!b || !b->gexec) return CASIM_ERR_ARG;
+  CUDA_TRY(cudaGraphLaunch(b->gexec, (cudaStream_t)stream));
+  b->ctx->launches += (long long)b->graph_steps * (b->compact ? 2 : 1);
+  return CASIM_OK;
+}
+
+extern "C" long long casim_batch_columns(const casim_batch *b) { return b ? b->total_cols : -1; }
 
 extern "C" long long casim_launch_count(const casim_ctx *ctx) { return ctx ? ctx->launches : -1; }
 

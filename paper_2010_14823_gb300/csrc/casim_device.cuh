@@ -729,7 +729,7 @@ __device__ __forceinline__ bool prologue(const KArgs &a, const KParams &P, Smem 
 // capped speed could exceed one level per step): per species, n_sub from the
 // largest Courant number, then n_sub top-down sweeps in place.
 template <class M>
-__device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KParams &P, const Smem &sm, int c,
+__device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KParams &P, const double *sdz, int c,
                                                       double prec[4]) {
   using R = typename M::R;
   using Ph = Phys<M>;
@@ -749,7 +749,7 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
       const R dfac = M::ex((R)0.4 * (K.lgrho0 - M::lg(rho)));
       R vq, vn;
       Ph::fall_speeds(K, (R)1e30, M::lg(q), M::toR(np[o]), dfac, x, vq, vn);
-      cmax = M::mx(cmax, M::div(vq * M::toR(a.dt), M::toR(sm.dz[k])));
+      cmax = M::mx(cmax, M::div(vq * M::toR(a.dt), M::toR(sdz[k])));
     }
     int ns = (int)ceil((double)M::div(cmax, M::toR(P.c_max)));
     if (ns < 1) ns = 1;
@@ -766,7 +766,7 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
         if (qR > K.qmin) {
           const R dfac = M::ex((R)0.4 * (K.lgrho0 - M::lg(rho)));
           R vq, vn;
-          Ph::fall_speeds(K, M::toR(sm.dz[k] / dts), M::lg(qR), M::toR(n), dfac, x, vq, vn);
+          Ph::fall_speeds(K, M::toR(sdz[k] / dts), M::lg(qR), M::toR(n), dfac, x, vq, vn);
           if constexpr (!M::kMixed) {
             F = rhod * q * vq;
             G = rhod * (n > 0.0 ? n : 0.0) * vn;
@@ -777,10 +777,10 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
         }
         if (F != (R)0 || Fu != (R)0 || G != (R)0 || Gu != (R)0) {
           if constexpr (!M::kMixed) {
-            q += dts * (Fu - F) / (rhod * sm.dz[k]);
-            n += dts * (Gu - G) / (rhod * sm.dz[k]);
+            q += dts * (Fu - F) / (rhod * sdz[k]);
+            n += dts * (Gu - G) / (rhod * sdz[k]);
           } else {
-            const R sc = M::div(M::toR(dts), rho * M::toR(sm.dz[k]));
+            const R sc = M::div(M::toR(dts), rho * M::toR(sdz[k]));
             q += M::toD((Fu - F) * sc);
             n += M::toD((Gu - G) * sc);
           }
@@ -804,16 +804,11 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
 // the processes are applied first and each species is sedimented with its
 // own substep count in further sweeps over the column.
 template <class M>
-__global__ void __launch_bounds__(kBlock, M::kMixed ? 4 : 3) k_step(const KArgs a, const KParams P) {
+__device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P, const double *sdz,
+                                               const double *sdzdt, bool fast, int c) {
   using R = typename M::R;
   using Ph = Phys<M>;
-  __shared__ Smem sm;
   const ConstK<R> &K = M::K(P);
-  const bool fast = prologue(a, P, sm);
-
-  const int c = blockIdx.x * kBlock + threadIdx.x;
-  if (c >= a.ncols) return;
-
   unsigned eflag = 0;
   double prec[4] = {0.0, 0.0, 0.0, 0.0};
   // carried downward fluxes F_{k+1}, G_{k+1} (kg m^-2 s^-1, m^-2 s^-1)
@@ -829,7 +824,7 @@ __global__ void __launch_bounds__(kBlock, M::kMixed ? 4 : 3) k_step(const KArgs 
       touched = F64::active(K, s, es0, qs0);
       if (touched) F64::process(K, s, a.dt, es0, qs0);
       if (fast) {
-        const double dzk = sm.dz[k];
+        const double dzk = sdz[k];
         const double dfac = ::exp(0.4 * (K.lgrho0 - ::log(s.rho)));
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
@@ -838,7 +833,7 @@ __global__ void __launch_bounds__(kBlock, M::kMixed ? 4 : 3) k_step(const KArgs 
           double F = 0, G = 0;
           if (q > K.qmin) {
             double vq, vn;
-            Ph::fall_speeds(K, sm.dzdt[k], ::log(q), n, dfac, x, vq, vn);
+            Ph::fall_speeds(K, sdzdt[k], ::log(q), n, dfac, x, vq, vn);
             F = s.rho * q * vq;
             G = s.rho * (n > 0.0 ? n : 0.0) * vn;
           }
@@ -889,8 +884,8 @@ __global__ void __launch_bounds__(kBlock, M::kMixed ? 4 : 3) k_step(const KArgs 
           if (!act) w.hmax = max(w.hmax, hiabs(s.rho));
           const float rho = act ? w.rho : d2f(s.rho);
           const float dfac = ex2a(0.4f * (K.lgrho0 - lg2a(rho)));
-          const float sc = __fdividef(d2f(a.dt), rho * d2f(sm.dz[k]));
-          const float guard = d2f(sm.dzdt[k]);
+          const float sc = __fdividef(d2f(a.dt), rho * d2f(sdz[k]));
+          const float guard = d2f(sdzdt[k]);
 #pragma unroll
           for (int x = 0; x < 4; ++x) {
             float F = 0.f, G = 0.f;
@@ -925,7 +920,7 @@ __global__ void __launch_bounds__(kBlock, M::kMixed ? 4 : 3) k_step(const KArgs 
 #pragma unroll
     for (int x = 0; x < 4; ++x) prec[x] = M::toD(Fq[x]) * a.dt;
   } else {
-    eflag |= sediment_substeps<M>(a, P, sm, c, prec);
+    eflag |= sediment_substeps<M>(a, P, sdz, c, prec);
   }
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
@@ -935,6 +930,16 @@ __global__ void __launch_bounds__(kBlock, M::kMixed ? 4 : 3) k_step(const KArgs 
       eflag |= nonfinite(*pp);
     }
   }
+  return eflag;
+}
+
+template <class M>
+__global__ void __launch_bounds__(kBlock, M::kMixed ? 4 : 3) k_step(const KArgs a, const KParams P) {
+  __shared__ Smem sm;
+  const bool fast = prologue(a, P, sm);
+  const int c = blockIdx.x * kBlock + threadIdx.x;
+  if (c >= a.ncols) return;
+  const unsigned eflag = run_column<M>(a, P, sm.dz, sm.dzdt, fast, c);
   if (eflag) atomicOr(a.err, eflag);
 }
 

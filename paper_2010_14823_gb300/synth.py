@@ -187,3 +187,23 @@ def workload(name: str, ncols: int | None = None, nlev: int | None = None, seed:
     dz = dz_uniform(nl) if dzk == "uniform" else dz_stretched(nl)
     fld = make_state(recipe, nc, nl, dz, sd)
     return fld, dz, nc, nl, dt, nsteps
+
+
+def batch_workload(ndom: int = 64, seed: int = 1237, ncols_range=(1_000, 100_000), nlev_range=(40, 150),
+                   cloud_range=(0.05, 0.60), scale: float = 1.0):
+    """Many independent domains of uneven size (config of the batched step):
+    column counts log-uniform in ncols_range (times `scale`), level counts
+    uniform in nlev_range, stretched dz 20-200 m, stratus-type profiles with a
+    cloud fraction uniform in cloud_range.  Returns a list of (fld, dz, ncols,
+    nlev) and dt = 1 s."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(ndom):
+        nc = int(round(math.exp(rng.uniform(math.log(ncols_range[0]), math.log(ncols_range[1]))) * scale))
+        nc = max(nc, 1)
+        nl = int(rng.integers(nlev_range[0], nlev_range[1] + 1))
+        cf = float(rng.uniform(*cloud_range))
+        rc = Recipe(cloud_frac=cf, base_range=(500.0, 2000.0), top_range=(2000.0, 4000.0))
+        dz = dz_stretched(nl)
+        out.append((make_state(rc, nc, nl, dz, seed=int(rng.integers(1 << 30))), dz, nc, nl))
+    return out, 1.0
