@@ -195,6 +195,35 @@ long long casim_batch_columns(const casim_batch *batch);
 /* Release the batch (waits for the device). NULL is a no-op. */
 void casim_batch_free(casim_batch *batch);
 
+/* ----------------------------------------------------------------------------
+ * Allocation-free step.  The paper has no counterpart; this entry point exists
+ * for callers that cannot allocate device memory: a host model whose memory
+ * pool already owns the GPU, a plug-in called while its framework forbids
+ * allocation, or a real-time loop that must never meet a failed allocation.
+ * It needs no context and calls no cudaMalloc or cudaFree (nor any routine
+ * that allocates): its scratch -- the error word, a work counter, the domain
+ * table and the active-column list -- is one fixed array of device memory
+ * that the library holds on every GPU it is loaded on, until the process
+ * exits (about 4.2 MB for the limit below).
+ *  - Runs the compacted step (flag pass, then the step over the active
+ *    columns); results are bit-for-bit those of casim_step with the same
+ *    parameters and precision.
+ *  - ncols above CASIM_NOALLOC_MAX_COLS is rejected with CASIM_ERR_ARG and a
+ *    message in casim_last_cuda_error(); other arguments as for casim_step.
+ *  - The first call on each device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; the call clears what must start at zero.  Two calls whose work
+ *    overlaps on the GPU (different streams, no ordering) race on the array
+ *    and give wrong results: order them on one stream.
+ *  - params may be NULL (defaults).  If flags is non-NULL the call waits for
+ *    `stream`, stores the CASIM_EFLAG_* bits of this step in *flags and
+ *    returns CASIM_ERR_NONFINITE / CASIM_ERR_CFL when they are set; if NULL it
+ *    returns after enqueuing. */
+#define CASIM_NOALLOC_MAX_COLS (1 << 20)
+int casim_step_noalloc(const casim_params *params, int precision, const casim_state *s, int ncols, int nlev,
+                       double dt, void *stream, unsigned *flags);
+
 /* Number of kernel launches this context has enqueued since casim_init. */
 long long casim_launch_count(const casim_ctx *ctx);
 

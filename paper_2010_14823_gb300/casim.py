@@ -24,6 +24,7 @@ NPRECIP = 4
 NSUB_MAX = 64
 EFLAG_NONFINITE = 1
 EFLAG_CFL = 2
+NOALLOC_MAX_COLS = 1 << 20
 _ERRORS = {-1: "CASIM_ERR_ARG", -2: "CASIM_ERR_OOM", -3: "CASIM_ERR_CUDA",
            -4: "CASIM_ERR_NONFINITE", -5: "CASIM_ERR_CFL"}
 
@@ -115,6 +116,8 @@ def lib():
         L.casim_batch_columns.restype = ctypes.c_longlong
         L.casim_batch_free.argtypes = [vp]
         L.casim_batch_free.restype = None
+        L.casim_step_noalloc.argtypes = [ctypes.POINTER(casim_params), i, ps, i, i, d, vp, ctypes.POINTER(u)]
+        L.casim_step_noalloc.restype = i
         _lib = L
     return _lib
 
@@ -274,3 +277,17 @@ class Domain:
 
     def numpy(self):
         return self.fld.cpu().numpy(), self.precip.cpu().numpy()
+
+
+def casim_step_noalloc(params, precision: int, state: casim_state, ncols: int, nlev: int, dt: float,
+                       stream=None, want_flags: bool = True) -> tuple[int, int]:
+    """One step without any device allocation (scratch is a fixed array in the
+    library).  Returns (status, flags); with want_flags the call waits for the
+    stream and reports this step's error bits."""
+    f = ctypes.c_uint(0)
+    rc = lib().casim_step_noalloc(ctypes.byref(params) if params is not None else None, precision,
+                                  ctypes.byref(state), ncols, nlev, dt, _stream(stream),
+                                  ctypes.byref(f) if want_flags else None)
+    if rc in (-1, -3):
+        _check(rc, "casim_step_noalloc")
+    return rc, f.value

@@ -579,6 +579,155 @@ extern "C" int casim_batch_graph_launch(casim_batch *b, void *stream) {
 
 extern "C" long long casim_batch_columns(const casim_batch *b) { return b ? b->total_cols : -1; }
 
+
+// ------------------------------------------------------- allocation-free step
+// Some callers cannot allocate device memory at all: code embedded in a host
+// model whose memory pool owns the whole GPU, a plug-in running under a
+// framework that forbids allocation while it is capturing or replaying work,
+// or a real-time loop that must not risk an allocation failing mid-run.  For
+// them casim_step_noalloc runs the compacted step (flag pass + step over the
+// active-column list) with every piece of scratch memory taken from the
+// fixed array below, which exists once per GPU for as long as the library is
+// loaded.
+constexpr int kNoallocMaxCols = CASIM_NOALLOC_MAX_COLS;
+constexpr int kNoallocMaxTiles = (kNoallocMaxCols + kTile - 1) / kTile;
+
+struct NoallocScratch {
+  unsigned err;          // device error word of the call
+  int counter;           // work counter of the persistent grid
+  int count;             // active columns found by the flag pass
+  int pad;
+  DomDesc dom;           // the one domain
+  Item tiles[kNoallocMaxTiles];
+  int list[kNoallocMaxCols];
+};
+
+static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+// Writes the call's domain table and tiles and clears the words that must
+// start at zero; the column list needs no clearing (the flag pass fills it).
+__global__ void k_noalloc_setup(NoallocScratch *sc, DomDesc d, int ntiles) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    sc->err = 0u;
+    sc->counter = 0;
+    sc->count = 0;
+    sc->dom = d;
+  }
+  if (i < ntiles) sc->tiles[i] = Item{0, i};
+}
+
+
+// smallest layer thickness of the no-alloc call's domain, into its table
+__global__ void k_noalloc_dzmin(NoallocScratch *sc) {
+  __shared__ double red[8];
+  double m = 1e300;
+  for (int k = threadIdx.x; k < sc->dom.nlev; k += blockDim.x) m = fmin(m, sc->dom.dz[k]);
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmin(m, red[i]);
+    sc->dom.dzmin = fmin(m, red[0]);
+  }
+}
+
+static NoallocScratch *noalloc_scratch_ptr(int dev, int *rc) {
+  // set-up once per device, with that device current; host code must not
+  // take the address of the __device__ array directly (that would be the
+  // host-side stand-in, not device memory)
+  static NoallocScratch *ptrs[64] = {nullptr};
+  if (dev < 0 || dev >= 64) { *rc = CASIM_ERR_ARG; return nullptr; }
+  if (!ptrs[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) { *rc = cuda_fail(e, "cudaGetSymbolAddress"); return nullptr; }
+    ptrs[dev] = static_cast<NoallocScratch *>(p);
+  }
+  *rc = CASIM_OK;
+  return ptrs[dev];
+}
+
+extern "C" int casim_step_noalloc(const casim_params *params, int precision, const casim_state *s, int ncols,
+                                  int nlev, double dt, void *stream, unsigned *flags) {
+  if (precision != CASIM_FP64 && precision != CASIM_MIXED) return CASIM_ERR_ARG;
+  int rc = check_state(s, ncols, nlev, dt);
+  if (rc != CASIM_OK) return rc;
+  if (ncols > kNoallocMaxCols) {
+    std::snprintf(g_last_error, sizeof(g_last_error),
+                  "casim_step_noalloc: %d columns exceed the fixed scratch of %d columns", ncols, kNoallocMaxCols);
+    return CASIM_ERR_ARG;
+  }
+  if (flags) *flags = 0u;
+  if (ncols == 0) return CASIM_OK;
+  casim_params p;
+  if (params) p = *params;
+  else casim_default_params(&p);
+  if (!params_ok(p)) return CASIM_ERR_ARG;
+  KParams kp;
+  derive<double>(p, kp.d, ln_);
+  derive<float>(p, kp.f, log2_);
+  kp.c_max = p.c_max;
+  kp.T0 = p.T0;
+  for (int x = 0; x < 5; ++x) kp.vmax[x] = p.vmax[x];
+
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  NoallocScratch *sc = noalloc_scratch_ptr(dev, &rc);
+  if (!sc) return rc;
+  int nsm = 1;
+  CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+
+  // the domain's smallest layer thickness (which decides the fused
+  // sedimentation path) is found on the device, without a host copy
+  DomDesc d;
+  d.fld = s->fld;
+  d.pitch = s->pitch;
+  d.dz = s->dz;
+  d.precip = s->precip;
+  d.ncols = ncols;
+  d.nlev = nlev;
+  d.dzmin = 0.0;   // replaced on the device by k_noalloc_dzmin
+  d.list_off = 0;
+  const int ntiles = (ncols + kTile - 1) / kTile;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_noalloc_setup<<<(ntiles + 255) / 256, 256, 0, st>>>(sc, d, ntiles);
+  k_noalloc_dzmin<<<1, 256, 0, st>>>(sc);
+  CUDA_TRY(cudaGetLastError());
+
+  BatchArgs a;
+  a.dom = &sc->dom;
+  a.items = sc->tiles;
+  a.nitems = ntiles;
+  a.list = sc->list;
+  a.count = &sc->count;
+  a.counter = &sc->counter;
+  a.err = &sc->err;
+  a.dt = dt;
+  a.compact = 1;
+  a.persistent = 1;
+  int per_sm = 1;
+  if (precision == CASIM_MIXED) {
+    k_compact<PolicyMix><<<ntiles, kTile, 0, st>>>(a, sc->tiles, ntiles, kp);
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch<PolicyMix>, kTile, 0));
+    k_step_batch<PolicyMix><<<std::min(ntiles, std::max(1, per_sm) * nsm), kTile, 0, st>>>(a, kp);
+  } else {
+    k_compact<PolicyF64><<<ntiles, kTile, 0, st>>>(a, sc->tiles, ntiles, kp);
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch<PolicyF64>, kTile, 0));
+    k_step_batch<PolicyF64><<<std::min(ntiles, std::max(1, per_sm) * nsm), kTile, 0, st>>>(a, kp);
+  }
+  CUDA_TRY(cudaGetLastError());
+  if (flags) {
+    unsigned h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, &sc->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    *flags = h;
+    if (h & CASIM_EFLAG_NONFINITE) return CASIM_ERR_NONFINITE;
+    if (h & CASIM_EFLAG_CFL) return CASIM_ERR_CFL;
+  }
+  return CASIM_OK;
+}
+
 extern "C" long long casim_launch_count(const casim_ctx *ctx) { return ctx ? ctx->launches : -1; }
 
 extern "C" void casim_free(casim_ctx *ctx) {
