@@ -126,7 +126,8 @@ def bench_batch(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    doms, dt = synth.batch_workload(64, seed=1237 + rank)
+    from paper_2010_14823_gb300 import shard
+    doms, dt = synth.batch_workload(64, seed=shard.rank_seed(1237, rank))
     dev = [casim.Domain(f, dz, nc) for f, dz, nc, nl in doms]
     del doms
     npts = sum(d.ncols * d.nlev for d in dev)
@@ -157,11 +158,7 @@ def bench_batch(args, rank, world, local):
     e1.record(stream)
     sync()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     launches = casim.casim_launch_count(ctx) - n0
     rc, fl = casim.casim_get_error(ctx, stream)
     assert rc == 0, (rc, fl)
@@ -226,7 +223,9 @@ def main():
     from paper_2010_14823_gb300 import synth
     if args.workload == "batch64":
         return bench_batch(args, rank, world, local)
-    base_fld, dz, ncols, nlev, dt, _ = synth.workload(args.workload, ncols=args.ncols, seed=1236 + rank)
+    from paper_2010_14823_gb300 import shard
+    base_fld, dz, ncols, nlev, dt, _ = synth.workload(args.workload, ncols=args.ncols,
+                                                      seed=shard.rank_seed(1236, rank))
     forms = set(args.forms.split(","))
     npts = ncols * nlev
 
@@ -269,11 +268,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return shard.max_over_ranks(x, dist, "cuda")
 
     stream = torch.cuda.current_stream()
     dom = casim.Domain(base_fld, dz, ncols)
