@@ -196,6 +196,65 @@ long long casim_batch_columns(const casim_batch *batch);
 void casim_batch_free(casim_batch *batch);
 
 /* ----------------------------------------------------------------------------
+ * Warm-rain surrogate: a network 12 -> 256 -> 256 -> 256 -> 4 (tanh hidden
+ * layers) that predicts the natural logarithms of autoconversion, accretion,
+ * cloud and rain self-collection from 12 features of a point's state after
+ * adjustment and activation.  Weights and every GEMM operand are BF16, sums
+ * FP32 (tensor cores).  The paper has no learned component; the network, its
+ * training and its guard follow the mixed form of the step.
+ *
+ * Features (in order): ln qc, ln qr (floored at q_min), ln nc (floored at 1),
+ * ln nr (floored at 1e-3), ln rho, T - T0, ln p, ln qv (floored at 1e-10), w,
+ * ln na (floored at 1), [qc > q_min], [qr > q_min].
+ * Flat parameter order: W1[12][256], b1[256], W2[256][256], b2, W3[256][256],
+ * b3, W4[256][4], b4[4]; W[k][n] multiplies input k into unit n.
+ * ------------------------------------------------------------------------- */
+typedef struct casim_mlp casim_mlp;
+#define CASIM_MLP_NIN 12
+#define CASIM_MLP_NOUT 4
+#define CASIM_MLP_NSTATS (2 * CASIM_MLP_NIN + 2 * CASIM_MLP_NOUT + 2 * CASIM_MLP_NIN)
+
+/* New network on the current device: Xavier-uniform weights from `seed`, zero biases. */
+int casim_mlp_create(casim_mlp **mlp, unsigned long long seed);
+long long casim_mlp_param_count(void);
+/* FP32 master parameters, host arrays of casim_mlp_param_count() floats. */
+int casim_mlp_set_params(casim_mlp *mlp, const float *host, long long n);
+int casim_mlp_get_params(const casim_mlp *mlp, float *host, long long n);
+/* Standardised inputs Xn[n][12] -> outputs Y[n][4] (host arrays; synchronous). */
+int casim_mlp_forward_host(casim_mlp *mlp, const float *Xn, int n, float *Y);
+/* Loss sum_i sum_j M (Y - Tn)^2 / sum M and its gradient (host arrays of
+   n x 12, n x 4, n x 4, and param_count floats; synchronous). */
+int casim_mlp_loss_grad_host(casim_mlp *mlp, const float *Xn, const float *Tn, const float *M, int n, double *loss,
+                             float *grad);
+/* Training data from one state (mixed form): for every point with cloud or
+   rain after adjustment and activation, raw features X[row][12], the scheme's
+   log-rates Y[row][4] and masks M[row][4] (1 where the scheme defines the
+   rate), and (if pts is not NULL) the point index k * pitch + c of each row.
+   Device buffers of `cap` rows; *rows receives the number of such points
+   (rows beyond cap are not written).  Synchronises `stream`. */
+int casim_mlp_data(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, float *X, float *Y,
+                   float *M, long long *pts, long long cap, long long *rows, void *stream);
+/* Fit the standardisation and the input box to n rows of device data, then
+   train with Adam (lr, betas 0.9/0.999) for `steps` mini-batches of `batch`
+   rows drawn with a counter-based hash of (seed, step, row).  loss_hist
+   (host, may be NULL) receives the loss of every step.  Synchronises `stream`. */
+int casim_mlp_fit(casim_mlp *mlp, const float *X, const float *Y, const float *M, long long n, int steps, int batch,
+                  float lr, unsigned long long seed, float *loss_hist, void *stream);
+/* Standardisation and box: [12 mean][12 sd][4 mean][4 sd][12 lo][12 hi]. */
+int casim_mlp_get_norm(const casim_mlp *mlp, float *stats);
+int casim_mlp_set_norm(casim_mlp *mlp, const float *stats);
+/* One mixed-form step in which the four warm-rain rates come from the network
+   at every point whose features lie inside the training box, and from the
+   scheme elsewhere (the out-of-distribution guard).  The context must be
+   CASIM_MIXED.  Allocates the network's scratch on first use for a domain
+   size (features, row map, per-point rates).  Synchronises `stream` once
+   (to size the network's pass); *served (may be NULL) receives the number of
+   points that took the network's rates. */
+int casim_step_surrogate(casim_ctx *ctx, casim_mlp *mlp, const casim_state *s, int ncols, int nlev, double dt,
+                         void *stream, long long *served);
+void casim_mlp_free(casim_mlp *mlp);
+
+/* ----------------------------------------------------------------------------
  * Allocation-free step.  The paper has no counterpart; this entry point exists
  * for callers that cannot allocate device memory: a host model whose memory
  * pool already owns the GPU, a plug-in called while its framework forbids

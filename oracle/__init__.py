@@ -72,6 +72,8 @@ def lib():
         L.orc_rates.restype = None
         L.orc_rates.argtypes = [pd, d, pd]
         L.orc_point.restype = None
+        L.orc_adjust_activate.restype = None
+        L.orc_adjust_activate.argtypes = [pd, pd]
         L.orc_point.argtypes = [pd, d, pd]
         L.orc_sediment_column.restype = u
         L.orc_sediment_column.argtypes = [pd, pd, pd, pd, i, d, pd, ctypes.POINTER(ctypes.c_int)]
@@ -201,3 +203,12 @@ def step(fld: np.ndarray, ncols: int, dz: np.ndarray, dt: float, precip: np.ndar
 
 def max_threads() -> int:
     return lib().orc_max_threads()
+
+
+def adjust_activate(state: np.ndarray) -> np.ndarray:
+    """The state after saturation adjustment and activation (what the rates see)."""
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    assert st.shape == (NFIELDS,)
+    out = np.zeros(NFIELDS)
+    lib().orc_adjust_activate(_dp(st), _dp(out))
+    return out

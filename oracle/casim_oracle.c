@@ -311,9 +311,8 @@ typedef struct {
 
 static double ratio(double n, double q) { return (n > 0.0 ? n : 0.0) / q; }
 
-void orc_point(const double *in, double dt, double *out) {
-  double st[ORC_NFIELDS];
-  memcpy(st, in, sizeof(st));
+void orc_adjust_activate(const double *in, double *st) {
+  memcpy(st, in, ORC_NFIELDS * sizeof(double));
   double p = st[ORC_P], rho = st[ORC_RHO], w = st[ORC_W];
 
   /* a2 */
@@ -330,6 +329,11 @@ void orc_point(const double *in, double dt, double *out) {
     st[ORC_NC] += dn;
     st[ORC_NA] -= dn;
   }
+}
+
+void orc_point(const double *in, double dt, double *out) {
+  double st[ORC_NFIELDS];
+  orc_adjust_activate(in, st);
 
   /* a4..a9 from the post-activation state */
   double R[ORC_NPROC];

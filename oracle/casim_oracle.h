@@ -59,6 +59,8 @@ double orc_vn(int sp, double rho, double lam);
 /* Raw process rates (before the limiter) at one point, from its state after
    adjustment and activation.  rates[ORC_NPROC]; see casim_oracle.c for signs. */
 void   orc_rates(const double *st, double dt, double *rates);
+/* a2 and a3 at one point: the state the process rates see, st[ORC_NFIELDS]. */
+void   orc_adjust_activate(const double *in, double *st);
 /* a2..a10 at one point: in[ORC_NFIELDS] -> out[ORC_NPROG]. */
 void   orc_point(const double *in, double dt, double *out);
 /* a12 for one column: q,n are [4][nlev] (r,i,s,g), updated in place;

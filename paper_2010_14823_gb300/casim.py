@@ -118,6 +118,32 @@ def lib():
         L.casim_batch_free.restype = None
         L.casim_step_noalloc.argtypes = [ctypes.POINTER(casim_params), i, ps, i, i, d, vp, ctypes.POINTER(u)]
         L.casim_step_noalloc.restype = i
+        pf = ctypes.POINTER(ctypes.c_float)
+        ll = ctypes.c_longlong
+        L.casim_mlp_create.argtypes = [ctypes.POINTER(vp), ctypes.c_ulonglong]
+        L.casim_mlp_create.restype = i
+        L.casim_mlp_param_count.argtypes = []
+        L.casim_mlp_param_count.restype = ll
+        L.casim_mlp_set_params.argtypes = [vp, pf, ll]
+        L.casim_mlp_set_params.restype = i
+        L.casim_mlp_get_params.argtypes = [vp, pf, ll]
+        L.casim_mlp_get_params.restype = i
+        L.casim_mlp_forward_host.argtypes = [vp, pf, i, pf]
+        L.casim_mlp_forward_host.restype = i
+        L.casim_mlp_loss_grad_host.argtypes = [vp, pf, pf, pf, i, ctypes.POINTER(d), pf]
+        L.casim_mlp_loss_grad_host.restype = i
+        L.casim_mlp_data.argtypes = [vp, ps, i, i, d, vp, vp, vp, vp, ll, ctypes.POINTER(ll), vp]
+        L.casim_mlp_data.restype = i
+        L.casim_mlp_fit.argtypes = [vp, vp, vp, vp, ll, i, i, ctypes.c_float, ctypes.c_ulonglong, pf, vp]
+        L.casim_mlp_fit.restype = i
+        L.casim_mlp_get_norm.argtypes = [vp, pf]
+        L.casim_mlp_get_norm.restype = i
+        L.casim_mlp_set_norm.argtypes = [vp, pf]
+        L.casim_mlp_set_norm.restype = i
+        L.casim_step_surrogate.argtypes = [vp, vp, ps, i, i, d, vp, ctypes.POINTER(ll)]
+        L.casim_step_surrogate.restype = i
+        L.casim_mlp_free.argtypes = [vp]
+        L.casim_mlp_free.restype = None
         _lib = L
     return _lib
 
@@ -291,3 +317,91 @@ def casim_step_noalloc(params, precision: int, state: casim_state, ncols: int, n
     if rc in (-1, -3):
         _check(rc, "casim_step_noalloc")
     return rc, f.value
+
+
+MLP_NIN = 12
+MLP_NOUT = 4
+MLP_NSTATS = 2 * 12 + 2 * 4 + 2 * 12
+
+
+def _fp(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def casim_mlp_create(seed: int = 0):
+    m = ctypes.c_void_p()
+    _check(lib().casim_mlp_create(ctypes.byref(m), seed), "casim_mlp_create")
+    return m
+
+
+def casim_mlp_param_count() -> int:
+    return lib().casim_mlp_param_count()
+
+
+def casim_mlp_set_params(mlp, theta: np.ndarray):
+    t = np.ascontiguousarray(theta, dtype=np.float32)
+    _check(lib().casim_mlp_set_params(mlp, _fp(t), t.size), "casim_mlp_set_params")
+
+
+def casim_mlp_get_params(mlp) -> np.ndarray:
+    t = np.zeros(casim_mlp_param_count(), dtype=np.float32)
+    _check(lib().casim_mlp_get_params(mlp, _fp(t), t.size), "casim_mlp_get_params")
+    return t
+
+
+def casim_mlp_forward_host(mlp, Xn: np.ndarray) -> np.ndarray:
+    X = np.ascontiguousarray(Xn, dtype=np.float32)
+    Y = np.zeros((X.shape[0], MLP_NOUT), dtype=np.float32)
+    _check(lib().casim_mlp_forward_host(mlp, _fp(X), X.shape[0], _fp(Y)), "casim_mlp_forward_host")
+    return Y
+
+
+def casim_mlp_loss_grad_host(mlp, Xn, Tn, M):
+    X = np.ascontiguousarray(Xn, dtype=np.float32)
+    T = np.ascontiguousarray(Tn, dtype=np.float32)
+    Mk = np.ascontiguousarray(M, dtype=np.float32)
+    g = np.zeros(casim_mlp_param_count(), dtype=np.float32)
+    loss = ctypes.c_double(0.0)
+    _check(lib().casim_mlp_loss_grad_host(mlp, _fp(X), _fp(T), _fp(Mk), X.shape[0], ctypes.byref(loss), _fp(g)),
+           "casim_mlp_loss_grad_host")
+    return loss.value, g
+
+
+def casim_mlp_data(ctx, state: casim_state, ncols: int, nlev: int, dt: float, X, Y, M, cap: int, pts=None,
+                   stream=None) -> int:
+    rows = ctypes.c_longlong(0)
+    _check(lib().casim_mlp_data(ctx, ctypes.byref(state), ncols, nlev, dt, _ptr(X), _ptr(Y), _ptr(M), _ptr(pts),
+                                cap, ctypes.byref(rows), _stream(stream)), "casim_mlp_data")
+    return rows.value
+
+
+def casim_mlp_fit(mlp, X, Y, M, n: int, steps: int, batch: int, lr: float, seed: int = 0, stream=None,
+                  history: bool = True) -> np.ndarray | None:
+    hist = np.zeros(max(steps, 1), dtype=np.float32) if history else None
+    _check(lib().casim_mlp_fit(mlp, _ptr(X), _ptr(Y), _ptr(M), n, steps, batch, lr, seed,
+                               _fp(hist) if history else None, _stream(stream)), "casim_mlp_fit")
+    return hist[:steps] if history else None
+
+
+def casim_mlp_get_norm(mlp) -> np.ndarray:
+    st = np.zeros(MLP_NSTATS, dtype=np.float32)
+    _check(lib().casim_mlp_get_norm(mlp, _fp(st)), "casim_mlp_get_norm")
+    return st
+
+
+def casim_mlp_set_norm(mlp, stats: np.ndarray):
+    st = np.ascontiguousarray(stats, dtype=np.float32)
+    assert st.size == MLP_NSTATS
+    _check(lib().casim_mlp_set_norm(mlp, _fp(st)), "casim_mlp_set_norm")
+
+
+def casim_step_surrogate(ctx, mlp, state: casim_state, ncols: int, nlev: int, dt: float, stream=None) -> int:
+    served = ctypes.c_longlong(0)
+    _check(lib().casim_step_surrogate(ctx, mlp, ctypes.byref(state), ncols, nlev, dt, _stream(stream),
+                                      ctypes.byref(served)), "casim_step_surrogate")
+    return served.value
+
+
+def casim_mlp_free(mlp):
+    lib().casim_mlp_free(mlp)

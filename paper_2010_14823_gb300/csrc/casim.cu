@@ -17,6 +17,9 @@
 #include "casim.h"
 #include "casim_device.cuh"
 #include "casim_batch.cuh"
+#include "casim_mlp.cuh"
+
+#include <random>
 
 using namespace casim_dev;
 
@@ -212,6 +215,7 @@ static KArgs make_args(const casim_ctx *ctx, const casim_state *s, int ncols, in
   a.ncols = ncols;
   a.nlev = nlev;
   a.dt = dt;
+  a.surr = nullptr;
   return a;
 }
 
@@ -725,6 +729,402 @@ extern "C" int casim_step_noalloc(const casim_params *params, int precision, con
     if (h & CASIM_EFLAG_NONFINITE) return CASIM_ERR_NONFINITE;
     if (h & CASIM_EFLAG_CFL) return CASIM_ERR_CFL;
   }
+  return CASIM_OK;
+}
+
+
+// ------------------------------------------------------------ surrogate network
+struct casim_mlp {
+  float *theta = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;   // FP32 [kNParam]
+  MlpBf16 wb{};
+  __nv_bfloat16 *wbuf = nullptr;
+  float *norm = nullptr;   // [12 mean][12 sd][4 mean][4 sd]
+  float *box = nullptr;    // [12 lo][12 hi]
+  bool fitted = false;
+  long long adam_t = 0;
+  // batch workspace
+  int cap_b = 0;
+  __nv_bfloat16 *h0 = nullptr, *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
+  __nv_bfloat16 *dzb4 = nullptr, *dzb3 = nullptr, *dzb2 = nullptr, *dzb1 = nullptr;
+  float *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *y = nullptr;
+  float *dz4 = nullptr, *dz3 = nullptr, *dz2 = nullptr, *dz1 = nullptr;
+  float *Xn = nullptr, *Tn = nullptr, *Mb = nullptr, *cnt = nullptr;
+  double *loss = nullptr;
+  // surrogate-step scratch
+  long long cap_rows = 0, cap_pts = 0;
+  __nv_bfloat16 *xb = nullptr;
+  long long *rowpt = nullptr;
+  float4 *surr = nullptr;
+  unsigned long long *rowctr = nullptr;
+};
+
+template <class T>
+static cudaError_t dalloc(T **p, size_t n) {
+  return cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(n, 1) * sizeof(T));
+}
+
+static void mlp_free_batch(casim_mlp *m) {
+  void *ps[] = {m->h0, m->h1, m->h2, m->h3, m->dzb4, m->dzb3, m->dzb2, m->dzb1, m->a1, m->a2, m->a3, m->y,
+                m->dz4, m->dz3, m->dz2, m->dz1, m->Xn, m->Tn, m->Mb};
+  for (void *p : ps) cudaFree(p);
+  m->h0 = m->h1 = m->h2 = m->h3 = m->dzb4 = m->dzb3 = m->dzb2 = m->dzb1 = nullptr;
+  m->a1 = m->a2 = m->a3 = m->y = m->dz4 = m->dz3 = m->dz2 = m->dz1 = m->Xn = m->Tn = m->Mb = nullptr;
+  m->cap_b = 0;
+}
+
+static int mlp_batch_ws(casim_mlp *m, int n) {
+  if (n <= m->cap_b) return CASIM_OK;
+  mlp_free_batch(m);
+  const size_t H = (size_t)n * kNh;
+  cudaError_t e = dalloc(&m->h0, (size_t)n * kNinPad);
+  if (e == cudaSuccess) e = dalloc(&m->h1, H);
+  if (e == cudaSuccess) e = dalloc(&m->h2, H);
+  if (e == cudaSuccess) e = dalloc(&m->h3, H);
+  if (e == cudaSuccess) e = dalloc(&m->dzb4, (size_t)n * kNoutPad);
+  if (e == cudaSuccess) e = dalloc(&m->dzb3, H);
+  if (e == cudaSuccess) e = dalloc(&m->dzb2, H);
+  if (e == cudaSuccess) e = dalloc(&m->dzb1, H);
+  if (e == cudaSuccess) e = dalloc(&m->a1, H);
+  if (e == cudaSuccess) e = dalloc(&m->a2, H);
+  if (e == cudaSuccess) e = dalloc(&m->a3, H);
+  if (e == cudaSuccess) e = dalloc(&m->y, (size_t)n * kNout);
+  if (e == cudaSuccess) e = dalloc(&m->dz4, (size_t)n * kNout);
+  if (e == cudaSuccess) e = dalloc(&m->dz3, H);
+  if (e == cudaSuccess) e = dalloc(&m->dz2, H);
+  if (e == cudaSuccess) e = dalloc(&m->dz1, H);
+  if (e == cudaSuccess) e = dalloc(&m->Xn, (size_t)n * kNin);
+  if (e == cudaSuccess) e = dalloc(&m->Tn, (size_t)n * kNout);
+  if (e == cudaSuccess) e = dalloc(&m->Mb, (size_t)n * kNout);
+  if (e != cudaSuccess) {
+    mlp_free_batch(m);
+    return e == cudaErrorMemoryAllocation ? CASIM_ERR_OOM : cuda_fail(e, "cudaMalloc");
+  }
+  m->cap_b = n;
+  return CASIM_OK;
+}
+
+template <class Epi>
+static void gemm(const __nv_bfloat16 *A, long long sam, long long sak, const __nv_bfloat16 *B, long long sbn,
+                 long long sbk, int M, int N, int K, const Epi &epi, cudaStream_t st) {
+  GemmArgs g{A, sam, sak, B, sbn, sbk, M, N, K};
+  const dim3 grid((N + kGBN - 1) / kGBN, (M + kGBM - 1) / kGBM);
+  k_gemm<Epi><<<grid, 128, 0, st>>>(g, epi);
+}
+
+// forward pass of n rows whose BF16 inputs are in m->h0; keep_act stores the
+// FP32 activations the backward pass needs
+static void mlp_forward(casim_mlp *m, int n, bool keep_act, cudaStream_t st) {
+  gemm(m->h0, kNinPad, 1, m->wb.w1t, kNinPad, 1, n, kNh, kNinPad,
+       EpiHidden{m->theta + kOffB1, keep_act ? m->a1 : nullptr, m->h1, kNh}, st);
+  gemm(m->h1, kNh, 1, m->wb.w2t, kNh, 1, n, kNh, kNh, EpiHidden{m->theta + kOffB2, keep_act ? m->a2 : nullptr, m->h2, kNh}, st);
+  gemm(m->h2, kNh, 1, m->wb.w3t, kNh, 1, n, kNh, kNh, EpiHidden{m->theta + kOffB3, keep_act ? m->a3 : nullptr, m->h3, kNh}, st);
+  gemm(m->h3, kNh, 1, m->wb.w4t, kNh, 1, n, kNout, kNh, EpiOut{m->theta + kOffB4, m->y, kNout}, st);
+}
+
+// loss and gradient of n rows (inputs in h0, targets Tn, masks Mb)
+static void mlp_backward(casim_mlp *m, int n, cudaStream_t st) {
+  cudaMemsetAsync(m->cnt, 0, sizeof(float), st);
+  cudaMemsetAsync(m->loss, 0, sizeof(double), st);
+  k_sum<<<64, 256, 0, st>>>(m->Mb, (long long)n * kNout, m->cnt);
+  const long long tot = (long long)n * kNoutPad;
+  k_mlp_loss<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m->y, m->Tn, m->Mb, n, m->cnt, m->loss, m->dz4, m->dzb4);
+  const dim3 cs(32, 8);
+  // layer 4
+  gemm(m->h3, 1, kNh, m->dzb4, 1, kNoutPad, kNh, kNout, n, EpiStore{m->grad + kOffW4, kNout}, st);
+  k_colsum<<<1, cs, 0, st>>>(m->dz4, n, kNout, kNout, m->grad + kOffB4);
+  gemm(m->dzb4, kNoutPad, 1, m->wb.w4k, kNoutPad, 1, n, kNh, kNoutPad, EpiBackTanh{m->a3, m->dz3, m->dzb3, kNh}, st);
+  // layer 3
+  gemm(m->h2, 1, kNh, m->dzb3, 1, kNh, kNh, kNh, n, EpiStore{m->grad + kOffW3, kNh}, st);
+  k_colsum<<<kNh / 8, cs, 0, st>>>(m->dz3, n, kNh, kNh, m->grad + kOffB3);
+  gemm(m->dzb3, kNh, 1, m->wb.w3k, kNh, 1, n, kNh, kNh, EpiBackTanh{m->a2, m->dz2, m->dzb2, kNh}, st);
+  // layer 2
+  gemm(m->h1, 1, kNh, m->dzb2, 1, kNh, kNh, kNh, n, EpiStore{m->grad + kOffW2, kNh}, st);
+  k_colsum<<<kNh / 8, cs, 0, st>>>(m->dz2, n, kNh, kNh, m->grad + kOffB2);
+  gemm(m->dzb2, kNh, 1, m->wb.w2k, kNh, 1, n, kNh, kNh, EpiBackTanh{m->a1, m->dz1, m->dzb1, kNh}, st);
+  // layer 1
+  gemm(m->h0, 1, kNinPad, m->dzb1, 1, kNh, kNin, kNh, n, EpiStore{m->grad + kOffW1, kNh}, st);
+  k_colsum<<<kNh / 8, cs, 0, st>>>(m->dz1, n, kNh, kNh, m->grad + kOffB1);
+}
+
+static void mlp_cast(casim_mlp *m, cudaStream_t st) {
+  k_mlp_cast<<<(kNh * kNh + 255) / 256, 256, 0, st>>>(m->theta, m->wb);
+}
+
+extern "C" void casim_mlp_free(casim_mlp *m) {
+  if (!m) return;
+  cudaDeviceSynchronize();
+  mlp_free_batch(m);
+  void *ps[] = {m->theta, m->grad, m->m1, m->m2, m->wbuf, m->norm, m->box, m->cnt, m->loss,
+                m->xb, m->rowpt, m->surr, m->rowctr};
+  for (void *p : ps) cudaFree(p);
+  delete m;
+}
+
+extern "C" int casim_mlp_create(casim_mlp **out, unsigned long long seed) {
+  if (!out) return CASIM_ERR_ARG;
+  *out = nullptr;
+  casim_mlp *m = new casim_mlp();
+  // Xavier-uniform weights, zero biases
+  std::vector<float> th(kNParam, 0.f);
+  std::mt19937_64 rng(seed);
+  const int sz[5] = {kNin, kNh, kNh, kNh, kNout};
+  const int offw[4] = {kOffW1, kOffW2, kOffW3, kOffW4};
+  for (int l = 0; l < 4; ++l) {
+    const double lim = std::sqrt(6.0 / (sz[l] + sz[l + 1]));
+    std::uniform_real_distribution<double> u(-lim, lim);
+    for (int i = 0; i < sz[l] * sz[l + 1]; ++i) th[offw[l] + i] = (float)u(rng);
+  }
+  const size_t nw = (size_t)kNh * kNinPad + 2 * (size_t)kNh * kNh + (size_t)kNoutPad * kNh +
+                    2 * (size_t)kNh * kNh + (size_t)kNh * kNoutPad;
+  cudaError_t e = dalloc(&m->theta, kNParam);
+  if (e == cudaSuccess) e = dalloc(&m->grad, kNParam);
+  if (e == cudaSuccess) e = dalloc(&m->m1, kNParam);
+  if (e == cudaSuccess) e = dalloc(&m->m2, kNParam);
+  if (e == cudaSuccess) e = dalloc(&m->wbuf, nw);
+  if (e == cudaSuccess) e = dalloc(&m->norm, 2 * kNin + 2 * kNout);
+  if (e == cudaSuccess) e = dalloc(&m->box, 2 * kNin);
+  if (e == cudaSuccess) e = dalloc(&m->cnt, 1);
+  if (e == cudaSuccess) e = dalloc(&m->loss, 1);
+  if (e == cudaSuccess) e = dalloc(&m->rowctr, 1);
+  if (e == cudaSuccess) e = cudaMemcpy(m->theta, th.data(), kNParam * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->m1, 0, kNParam * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(m->m2, 0, kNParam * sizeof(float));
+  if (e != cudaSuccess) {
+    int rc = e == cudaErrorMemoryAllocation ? CASIM_ERR_OOM : cuda_fail(e, "casim_mlp_create");
+    casim_mlp_free(m);
+    return rc;
+  }
+  __nv_bfloat16 *w = m->wbuf;
+  m->wb.w1t = w; w += (size_t)kNh * kNinPad;
+  m->wb.w2t = w; w += (size_t)kNh * kNh;
+  m->wb.w3t = w; w += (size_t)kNh * kNh;
+  m->wb.w4t = w; w += (size_t)kNoutPad * kNh;
+  m->wb.w2k = w; w += (size_t)kNh * kNh;
+  m->wb.w3k = w; w += (size_t)kNh * kNh;
+  m->wb.w4k = w;
+  mlp_cast(m, 0);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaDeviceSynchronize());
+  *out = m;
+  return CASIM_OK;
+}
+
+extern "C" long long casim_mlp_param_count(void) { return kNParam; }
+
+extern "C" int casim_mlp_set_params(casim_mlp *m, const float *host, long long n) {
+  if (!m || !host || n != kNParam) return CASIM_ERR_ARG;
+  CUDA_TRY(cudaMemcpy(m->theta, host, kNParam * sizeof(float), cudaMemcpyHostToDevice));
+  mlp_cast(m, 0);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaDeviceSynchronize());
+  return CASIM_OK;
+}
+
+extern "C" int casim_mlp_get_params(const casim_mlp *m, float *host, long long n) {
+  if (!m || !host || n != kNParam) return CASIM_ERR_ARG;
+  CUDA_TRY(cudaMemcpy(host, m->theta, kNParam * sizeof(float), cudaMemcpyDeviceToHost));
+  return CASIM_OK;
+}
+
+extern "C" int casim_mlp_forward_host(casim_mlp *m, const float *Xn, int n, float *Y) {
+  if (!m || !Xn || !Y || n < 1) return CASIM_ERR_ARG;
+  int rc = mlp_batch_ws(m, n);
+  if (rc != CASIM_OK) return rc;
+  CUDA_TRY(cudaMemcpy(m->Xn, Xn, (size_t)n * kNin * sizeof(float), cudaMemcpyHostToDevice));
+  k_mlp_inputs<<<(unsigned)(((long long)n * kNinPad + 255) / 256), 256>>>(m->Xn, n, m->h0);
+  mlp_forward(m, n, false, 0);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpy(Y, m->y, (size_t)n * kNout * sizeof(float), cudaMemcpyDeviceToHost));
+  return CASIM_OK;
+}
+
+extern "C" int casim_mlp_loss_grad_host(casim_mlp *m, const float *Xn, const float *Tn, const float *M, int n,
+                                        double *loss, float *grad) {
+  if (!m || !Xn || !Tn || !M || n < 1) return CASIM_ERR_ARG;
+  int rc = mlp_batch_ws(m, n);
+  if (rc != CASIM_OK) return rc;
+  CUDA_TRY(cudaMemcpy(m->Xn, Xn, (size_t)n * kNin * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(m->Tn, Tn, (size_t)n * kNout * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(m->Mb, M, (size_t)n * kNout * sizeof(float), cudaMemcpyHostToDevice));
+  k_mlp_inputs<<<(unsigned)(((long long)n * kNinPad + 255) / 256), 256>>>(m->Xn, n, m->h0);
+  mlp_forward(m, n, true, 0);
+  mlp_backward(m, n, 0);
+  CUDA_TRY(cudaGetLastError());
+  if (loss) CUDA_TRY(cudaMemcpy(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost));
+  if (grad) CUDA_TRY(cudaMemcpy(grad, m->grad, kNParam * sizeof(float), cudaMemcpyDeviceToHost));
+  return CASIM_OK;
+}
+
+extern "C" int casim_mlp_data(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, float *X,
+                              float *Y, float *M, long long *pts, long long cap, long long *rows, void *stream) {
+  if (!ctx || !X || !Y || !M || cap < 0 || !rows) return CASIM_ERR_ARG;
+  int rc = check_state(s, ncols, nlev, dt);
+  if (rc != CASIM_OK) return rc;
+  *rows = 0;
+  if (ncols == 0) return CASIM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long *ctr = nullptr;
+  CUDA_TRY(cudaMalloc(&ctr, sizeof(unsigned long long)));
+  cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st);
+  FeatArgs fa{};
+  fa.mode = 0;
+  fa.cap = cap;
+  fa.rows = ctr;
+  fa.X = X;
+  fa.Y = Y;
+  fa.M = M;
+  fa.rowpt = pts;
+  const KArgs a = make_args(ctx, s, ncols, nlev, dt);
+  const long long np = (long long)nlev * s->pitch;
+  k_mlp_features<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(a, ctx->kp, fa);
+  ctx->launches++;
+  unsigned long long h = 0;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(ctr);
+  if (e != cudaSuccess) return cuda_fail(e, "casim_mlp_data");
+  *rows = (long long)h;   // may exceed cap: only cap rows were written
+  return CASIM_OK;
+}
+
+extern "C" int casim_mlp_fit(casim_mlp *m, const float *X, const float *Y, const float *M, long long n, int steps,
+                             int batch, float lr, unsigned long long seed, float *loss_hist, void *stream) {
+  if (!m || !X || !Y || !M || n < 2 || steps < 0 || batch < 1) return CASIM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  // normalisation and the out-of-distribution box from the data
+  double *acc = nullptr;
+  int *lh = nullptr;
+  CUDA_TRY(cudaMalloc(&acc, (2 * kNin + 3 * kNout) * sizeof(double)));
+  CUDA_TRY(cudaMalloc(&lh, 2 * kNin * sizeof(int)));
+  std::vector<int> init(2 * kNin);
+  for (int k = 0; k < kNin; ++k) { init[k] = 0x7fffffff; init[kNin + k] = -0x7fffffff; }
+  cudaMemsetAsync(acc, 0, (2 * kNin + 3 * kNout) * sizeof(double), st);
+  cudaMemcpyAsync(lh, init.data(), 2 * kNin * sizeof(int), cudaMemcpyHostToDevice, st);
+  k_mlp_stats<<<256, 256, 0, st>>>(X, Y, M, n, acc);
+  k_mlp_box<<<256, 256, 0, st>>>(X, n, lh, lh + kNin);
+  std::vector<double> ha(2 * kNin + 3 * kNout);
+  std::vector<int> hl(2 * kNin);
+  cudaMemcpyAsync(ha.data(), acc, ha.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(hl.data(), lh, hl.size() * sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(acc);
+  cudaFree(lh);
+  if (e != cudaSuccess) return cuda_fail(e, "casim_mlp_fit: statistics");
+  float norm[2 * kNin + 2 * kNout], box[2 * kNin];
+  for (int k = 0; k < kNin; ++k) {
+    const double mu = ha[k] / n, var = ha[kNin + k] / n - mu * mu;
+    norm[k] = (float)mu;
+    norm[kNin + k] = (float)std::sqrt(std::max(var, 1e-12));
+    auto ordf = [](int i) { const int b = i >= 0 ? i : i ^ 0x7fffffff; float f; std::memcpy(&f, &b, 4); return f; };
+    box[k] = ordf(hl[k]);
+    box[kNin + k] = ordf(hl[kNin + k]);
+  }
+  for (int c = 0; c < kNout; ++c) {
+    const double cnt = std::max(ha[2 * kNin + 2 * kNout + c], 1.0);
+    const double mu = ha[2 * kNin + c] / cnt, var = ha[2 * kNin + kNout + c] / cnt - mu * mu;
+    norm[2 * kNin + c] = (float)mu;
+    norm[2 * kNin + kNout + c] = (float)std::sqrt(std::max(var, 1e-12));
+  }
+  CUDA_TRY(cudaMemcpyAsync(m->norm, norm, sizeof(norm), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(m->box, box, sizeof(box), cudaMemcpyHostToDevice, st));
+  m->fitted = true;
+  int rc = mlp_batch_ws(m, batch);
+  if (rc != CASIM_OK) return rc;
+  for (int s = 0; s < steps; ++s) {
+    k_mlp_batch<<<(batch + 255) / 256, 256, 0, st>>>(X, Y, M, n, seed, s, batch, m->norm, m->Xn, m->Tn, m->Mb);
+    k_mlp_inputs<<<(unsigned)(((long long)batch * kNinPad + 255) / 256), 256, 0, st>>>(m->Xn, batch, m->h0);
+    mlp_forward(m, batch, true, st);
+    mlp_backward(m, batch, st);
+    ++m->adam_t;
+    const float c1 = 1.f - (float)std::pow(0.9, (double)m->adam_t), c2 = 1.f - (float)std::pow(0.999, (double)m->adam_t);
+    k_adam<<<(kNParam + 255) / 256, 256, 0, st>>>(m->theta, m->grad, m->m1, m->m2, kNParam, lr, 0.9f, 0.999f, 1e-8f, c1, c2);
+    mlp_cast(m, st);
+    if (loss_hist) {
+      double l = 0.0;
+      CUDA_TRY(cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+      loss_hist[s] = (float)l;
+    }
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return CASIM_OK;
+}
+
+extern "C" int casim_mlp_get_norm(const casim_mlp *m, float *stats) {
+  if (!m || !stats || !m->fitted) return CASIM_ERR_ARG;
+  CUDA_TRY(cudaMemcpy(stats, m->norm, (2 * kNin + 2 * kNout) * sizeof(float), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(stats + 2 * kNin + 2 * kNout, m->box, 2 * kNin * sizeof(float), cudaMemcpyDeviceToHost));
+  return CASIM_OK;
+}
+
+extern "C" int casim_mlp_set_norm(casim_mlp *m, const float *stats) {
+  if (!m || !stats) return CASIM_ERR_ARG;
+  CUDA_TRY(cudaMemcpy(m->norm, stats, (2 * kNin + 2 * kNout) * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(m->box, stats + 2 * kNin + 2 * kNout, 2 * kNin * sizeof(float), cudaMemcpyHostToDevice));
+  m->fitted = true;
+  return CASIM_OK;
+}
+
+extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_state *s, int ncols, int nlev,
+                                    double dt, void *stream, long long *served) {
+  if (!ctx || !m || !m->fitted || ctx->precision != CASIM_MIXED) return CASIM_ERR_ARG;
+  int rc = check_state(s, ncols, nlev, dt);
+  if (rc != CASIM_OK || ncols == 0) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long np = (long long)nlev * s->pitch;
+  if (np > m->cap_pts) {
+    cudaFree(m->xb);
+    cudaFree(m->rowpt);
+    cudaFree(m->surr);
+    m->xb = nullptr;
+    m->rowpt = nullptr;
+    m->surr = nullptr;
+    m->cap_pts = m->cap_rows = 0;
+    cudaError_t e = dalloc(&m->xb, (size_t)np * kNinPad);
+    if (e == cudaSuccess) e = dalloc(&m->rowpt, (size_t)np);
+    if (e == cudaSuccess) e = dalloc(&m->surr, (size_t)np);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CASIM_ERR_OOM : cuda_fail(e, "cudaMalloc");
+    m->cap_pts = m->cap_rows = np;
+  }
+  // 1. features of every warm point inside the box; NaN rates outside it
+  CUDA_TRY(cudaMemsetAsync(m->rowctr, 0, sizeof(unsigned long long), st));
+  FeatArgs fa{};
+  fa.mode = 1;
+  fa.cap = m->cap_rows;
+  fa.rows = m->rowctr;
+  fa.xb = m->xb;
+  fa.rowpt = m->rowpt;
+  fa.surr = m->surr;
+  fa.norm = m->norm;
+  fa.box = m->box;
+  KArgs a = make_args(ctx, s, ncols, nlev, dt);
+  k_mlp_features<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(a, ctx->kp, fa);
+  ctx->launches++;
+  unsigned long long hrows = 0;
+  CUDA_TRY(cudaMemcpyAsync(&hrows, m->rowctr, sizeof(hrows), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  const long long rows = std::min((long long)hrows, m->cap_rows);
+  // 2. the network on the rows, in chunks
+  const int chunk = 1 << 17;
+  if ((rc = mlp_batch_ws(m, (int)std::min<long long>(chunk, std::max<long long>(rows, 1)))) != CASIM_OK) return rc;
+  for (long long r0 = 0; r0 < rows; r0 += m->cap_b) {
+    const int n = (int)std::min<long long>(m->cap_b, rows - r0);
+    __nv_bfloat16 *save = m->h0;
+    m->h0 = m->xb + r0 * kNinPad;
+    mlp_forward(m, n, false, st);
+    m->h0 = save;
+    k_mlp_scatter<<<(n + 255) / 256, 256, 0, st>>>(m->y, n, m->rowpt + r0, m->norm, m->surr);
+    ctx->launches += 5;
+  }
+  // 3. the step, taking the network's rates where given
+  a.surr = m->surr;
+  const dim3 grid((unsigned)((ncols + kBlock - 1) / kBlock));
+  k_step<PolicyMix><<<grid, kBlock, 0, st>>>(a, ctx->kp);
+  ctx->launches++;
+  CUDA_TRY(cudaGetLastError());
+  if (served) *served = rows;
   return CASIM_OK;
 }
 

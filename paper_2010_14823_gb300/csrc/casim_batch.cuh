@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kBatchMaxBlock, M::kMixed ? 2 : 1) k_step_batc
         a.ncols = d.ncols;
         a.nlev = d.nlev;
         a.dt = b.dt;
+        a.surr = nullptr;
         eflag |= run_column<M>(a, P, s_dz, s_dzdt, fast, c);
       }
     }

@@ -82,6 +82,7 @@ struct KArgs {
   unsigned *err;
   int ncols, nlev;
   double dt;
+  const float4 *surr;   // [nlev][pitch] surrogate warm-rain rates (mixed form), or null
 };
 
 // ------------------------------------------------------- conversions
@@ -540,9 +541,17 @@ struct Mix {
   }
 
   // a2..a10 on an active point: FP32 throughout, except the initial vapour
-  // difference of the adjustment, formed in FP64
+  // difference of the adjustment, formed in FP64.  `surr`, if not null,
+  // points at this point's surrogate warm-rain rates (NaN: use the scheme's).
   static __device__ __forceinline__ void process(const ConstK<float> &K, const Pt &s, double dt, W<float> &w,
-                                                 float es0, float qs0, MixInc &o) {
+                                                 float es0, float qs0, MixInc &o, const float4 *surr = nullptr) {
+    const float dnc_act = pre(K, s, w, es0, qs0, o);
+    post(K, w, dt, dnc_act, o, surr);
+  }
+
+  // a2 and a3; returns the cloud droplets activated
+  static __device__ __forceinline__ float pre(const ConstK<float> &K, const Pt &s, W<float> &w, float es0, float qs0,
+                                              MixInc &o) {
     w.rho = d2f(s.rho);
     w.nc = d2f(s.nc);
     w.nr = d2f(s.nr);
@@ -603,9 +612,28 @@ struct Mix {
         w.nc += dn;
       }
     }
-    // a4..a10
+    return dnc_act;
+  }
+
+  // a4..a10 from the post-activation values
+  static __device__ __forceinline__ void post(const ConstK<float> &K, W<float> &w, double dt, float dnc_act,
+                                              MixInc &o, const float4 *surr) {
     Rt<float> r;
     P::rates(K, w, dt, r);
+    if (surr) {
+      const bool hc = w.qc > K.qmin, hr = w.qr > K.qmin;
+      if (hc || hr) {
+        const float4 v = *surr;
+        if (!isnan(v.x)) {
+          if (hc) {
+            r.aut = v.x;
+            r.scc = v.z;
+          }
+          if (hc && hr) r.acc = v.y;
+          if (hr) r.scr = v.w;
+        }
+      }
+    }
     Gt<float> g;
     P::limits(K, w, dt, r, g);
     const float dtr = d2f(dt);
@@ -854,7 +882,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       float dn[4] = {0.f, 0.f, 0.f, 0.f};   // number increments of r, i, s, g
       float qpost[4], npost[4];
       if (act) {
-        Mix::process(K, s, a.dt, w, es0, qs0, o);
+        Mix::process(K, s, a.dt, w, es0, qs0, o, a.surr ? a.surr + (size_t)k * a.pitch + c : nullptr);
         Mix::apply_masses(s, o);
         if (o.dn[0] != 0.f) s.nc += f2d(o.dn[0]);
 #pragma unroll

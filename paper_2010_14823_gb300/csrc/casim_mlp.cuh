@@ -1,0 +1,467 @@
+// Warm-rain surrogate network: 12 -> 256 -> 256 -> 256 -> 4, tanh hidden
+// layers, BF16 weights and GEMM operands, FP32 accumulation on the tensor
+// cores.  Training (forward, backward, Adam) and inference run on the
+// kernels below; the step takes the network's rates where its inputs lie in
+// the box spanned by the training data and the scheme's rates elsewhere.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "casim_device.cuh"
+
+namespace casim_dev {
+
+constexpr int kNin = 12, kNinPad = 16, kNh = 256, kNout = 4, kNoutPad = 16;
+constexpr int kNParam = kNin * kNh + kNh + 2 * (kNh * kNh + kNh) + kNh * kNout + kNout;
+// offsets of the layers in the flat parameter vector (oracle order)
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kNin * kNh, kOffW2 = kOffB1 + kNh, kOffB2 = kOffW2 + kNh * kNh,
+              kOffW3 = kOffB2 + kNh, kOffB3 = kOffW3 + kNh * kNh, kOffW4 = kOffB3 + kNh,
+              kOffB4 = kOffW4 + kNh * kNout;
+
+// ------------------------------------------------------------ tensor-core GEMM
+// C[m][n] = sum_k A(m, k) B(n, k) with A(m, k) = A[m*sam + k*sak] and
+// B(n, k) = B[n*sbn + k*sbk] (BF16), FP32 accumulation by mma.sync
+// m16n8k16.  Tiles of 64x64 over a 2x2 arrangement of warps; operands are
+// gathered with arbitrary strides into k-contiguous shared-memory tiles, so
+// one kernel serves the forward pass (W^T), the data gradient (W) and the
+// weight gradient (both operands transposed).  The epilogue receives
+// (m, n, acc) for m < M, n < N.
+struct GemmArgs {
+  const __nv_bfloat16 *A;
+  long long sam, sak;
+  const __nv_bfloat16 *B;
+  long long sbn, sbk;
+  int M, N, K;
+};
+
+constexpr int kGBM = 64, kGBN = 64, kGBK = 32, kGPad = 8;
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(128) k_gemm(const GemmArgs g, const Epi epi) {
+  __shared__ __align__(16) __nv_bfloat16 As[kGBM][kGBK + kGPad];
+  __shared__ __align__(16) __nv_bfloat16 Bs[kGBN][kGBK + kGPad];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int m0 = blockIdx.y * kGBM, n0 = blockIdx.x * kGBN;
+  const int gq = lane >> 2, tq = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  for (int k0 = 0; k0 < g.K; k0 += kGBK) {
+    // gather the tiles (k fastest across threads when the operand is k-contiguous)
+#pragma unroll 4
+    for (int i = tid; i < kGBM * kGBK; i += 128) {
+      const int r = i / kGBK, kk = i % kGBK;
+      const int m = m0 + r, k = k0 + kk;
+      As[r][kk] = (m < g.M && k < g.K) ? g.A[(long long)m * g.sam + (long long)k * g.sak] : zero;
+      const int n = n0 + r;
+      Bs[r][kk] = (n < g.N && k < g.K) ? g.B[(long long)n * g.sbn + (long long)k * g.sbk] : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < kGBK; ks += 16) {
+      uint32_t af[2][4], bf[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm * 32 + i * 16 + gq;
+        af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][ks + 2 * tq]);
+        af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + 2 * tq]);
+        af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][ks + 2 * tq + 8]);
+        af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][ks + 2 * tq + 8]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = wn * 32 + j * 8 + gq;
+        bf[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[r][ks + 2 * tq]);
+        bf[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[r][ks + 2 * tq + 8]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int m = m0 + wm * 32 + i * 16 + gq + (r >> 1) * 8;
+        const int n = n0 + wn * 32 + j * 8 + 2 * tq + (r & 1);
+        if (m < g.M && n < g.N) epi(m, n, acc[i][j][r]);
+      }
+}
+
+// hidden layer: a = tanh(acc + b); keeps a (FP32, for the backward pass) and
+// its BF16 copy (the next layer's input)
+struct EpiHidden {
+  const float *bias;
+  float *a;              // [M][ld] or null
+  __nv_bfloat16 *h;      // [M][ld]
+  int ld;
+  __device__ __forceinline__ void operator()(int m, int n, float acc) const {
+    const float v = tanhf(acc + bias[n]);
+    if (a) a[(long long)m * ld + n] = v;
+    h[(long long)m * ld + n] = __float2bfloat16(v);
+  }
+};
+
+// output layer: y = acc + b
+struct EpiOut {
+  const float *bias;
+  float *y;              // [M][ld]
+  int ld;
+  __device__ __forceinline__ void operator()(int m, int n, float acc) const { y[(long long)m * ld + n] = acc + bias[n]; }
+};
+
+// weight gradient: g[m][n] = acc
+struct EpiStore {
+  float *c;
+  int ld;
+  __device__ __forceinline__ void operator()(int m, int n, float acc) const { c[(long long)m * ld + n] = acc; }
+};
+
+// data gradient through tanh: dz = acc (1 - a^2); FP32 for the bias sums,
+// BF16 for the next GEMMs
+struct EpiBackTanh {
+  const float *a;        // [M][ld] activations of the layer below
+  float *dz;
+  __nv_bfloat16 *dzb;
+  int ld;
+  __device__ __forceinline__ void operator()(int m, int n, float acc) const {
+    const long long i = (long long)m * ld + n;
+    const float av = a[i];
+    const float v = acc * (1.f - av * av);
+    dz[i] = v;
+    dzb[i] = __float2bfloat16(v);
+  }
+};
+
+// ---------------------------------------------------------- elementwise kernels
+// master FP32 parameters -> BF16 weight copies in both layouts:
+//   Wt[l]: [N][K] (K padded with zeros) for the forward GEMM,
+//   Wk[l]: [K][Npad] for the data gradient.
+struct MlpBf16 {
+  __nv_bfloat16 *w1t, *w2t, *w3t, *w4t;   // [256][16], [256][256], [256][256], [16][256]
+  __nv_bfloat16 *w2k, *w3k, *w4k;         // [256][256], [256][256], [256][16]
+};
+
+__global__ void k_mlp_cast(const float *theta, MlpBf16 w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const __nv_bfloat16 z = __float2bfloat16(0.f);
+  if (i < kNh * kNinPad) {   // w1t[n][k]
+    const int n = i / kNinPad, k = i % kNinPad;
+    w.w1t[i] = k < kNin ? __float2bfloat16(theta[kOffW1 + k * kNh + n]) : z;
+  }
+  if (i < kNh * kNh) {
+    const int n = i / kNh, k = i % kNh;   // t-layout index i = n*256 + k
+    w.w2t[i] = __float2bfloat16(theta[kOffW2 + k * kNh + n]);
+    w.w3t[i] = __float2bfloat16(theta[kOffW3 + k * kNh + n]);
+    w.w2k[i] = __float2bfloat16(theta[kOffW2 + i]);   // natural [k][n]
+    w.w3k[i] = __float2bfloat16(theta[kOffW3 + i]);
+  }
+  if (i < kNoutPad * kNh) {  // w4t[n][k], n < 16 (rows >= 4 zero)
+    const int n = i / kNh, k = i % kNh;
+    w.w4t[i] = n < kNout ? __float2bfloat16(theta[kOffW4 + k * kNout + n]) : z;
+  }
+  if (i < kNh * kNoutPad) {  // w4k[k][n]
+    const int k = i / kNoutPad, n = i % kNoutPad;
+    w.w4k[i] = n < kNout ? __float2bfloat16(theta[kOffW4 + k * kNout + n]) : z;
+  }
+}
+
+// FP32 inputs [n][12] -> BF16 [n][16] (zero padded)
+__global__ void k_mlp_inputs(const float *X, int n, __nv_bfloat16 *h0) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)n * kNinPad) return;
+  const long long r = i / kNinPad;
+  const int k = (int)(i % kNinPad);
+  h0[i] = __float2bfloat16(k < kNin ? X[r * kNin + k] : 0.f);
+}
+
+// masked squared error: loss += sum (y - t)^2 m / cnt; dz = 2 (y - t) m / cnt
+// (FP32 [n][4] and BF16 [n][16], columns >= 4 zero)
+__global__ void k_mlp_loss(const float *Y, const float *T, const float *Mk, int n, const float *cnt, double *loss,
+                           float *dz, __nv_bfloat16 *dzb) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double part = 0.0;
+  if (i < (long long)n * kNoutPad) {
+    const long long r = i / kNoutPad;
+    const int c = (int)(i % kNoutPad);
+    float g = 0.f;
+    if (c < kNout) {
+      const float inv = 1.f / fmaxf(*cnt, 1.f);
+      const float d = (Y[r * kNout + c] - T[r * kNout + c]) * Mk[r * kNout + c];
+      part = (double)d * d * inv;
+      g = 2.f * d * inv;
+      dz[r * kNout + c] = g;
+    }
+    dzb[i] = __float2bfloat16(g);
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(loss, part);
+}
+
+__global__ void k_sum(const float *x, long long n, float *out) {
+  float part = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    part += x[i];
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, part);
+}
+
+// bias gradient: column sums of dz [n][ld] (first `cols` columns) into g
+__global__ void k_colsum(const float *dz, int n, int ld, int cols, float *g) {
+  const int c = blockIdx.x * blockDim.y + threadIdx.y;   // column
+  if (c >= cols) return;
+  float part = 0.f;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) part += dz[(long long)r * ld + c];
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (threadIdx.x == 0) g[c] = part;
+}
+
+// Adam on the flat FP32 parameters
+__global__ void k_adam(float *theta, const float *grad, float *m1, float *m2, int n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = grad[i];
+  const float a = b1 * m1[i] + (1.f - b1) * g;
+  const float b = b2 * m2[i] + (1.f - b2) * g * g;
+  m1[i] = a;
+  m2[i] = b;
+  theta[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+}
+
+// counter-based mini-batch sampling: row r of batch `step` is
+// hash(seed, step, r) mod n (splitmix64 finaliser)
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// gather a standardised mini-batch from the raw data
+__global__ void k_mlp_batch(const float *X, const float *Y, const float *Mk, long long n, unsigned long long seed,
+                            long long step, int B, const float *norm, float *Xn, float *Tn, float *Mb) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= B) return;
+  const long long src = (long long)(mix64(seed ^ mix64((unsigned long long)step * 0x100000001b3ull + r)) % (unsigned long long)n);
+  const float *mu = norm, *sd = norm + kNin, *muy = norm + 2 * kNin, *sdy = norm + 2 * kNin + kNout;
+#pragma unroll
+  for (int k = 0; k < kNin; ++k) Xn[(long long)r * kNin + k] = (X[src * kNin + k] - mu[k]) / sd[k];
+#pragma unroll
+  for (int c = 0; c < kNout; ++c) {
+    const float m = Mk[src * kNout + c];
+    Mb[(long long)r * kNout + c] = m;
+    Tn[(long long)r * kNout + c] = m > 0.f ? (Y[src * kNout + c] - muy[c]) / sdy[c] : 0.f;
+  }
+}
+
+// per-feature mean and standard deviation, per-target (masked) mean and
+// standard deviation, per-feature min and max (the box of the training data)
+__global__ void k_mlp_stats(const float *X, const float *Y, const float *Mk, long long n, double *acc) {
+  // acc: [12 sum][12 sumsq][4 sum][4 sumsq][4 count] then min/max as ordered ints elsewhere
+  double s[kNin] = {0}, q[kNin] = {0}, sy[kNout] = {0}, qy[kNout] = {0}, cy[kNout] = {0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < kNin; ++k) {
+      const double v = X[i * kNin + k];
+      s[k] += v;
+      q[k] += v * v;
+    }
+#pragma unroll
+    for (int c = 0; c < kNout; ++c)
+      if (Mk[i * kNout + c] > 0.f) {
+        const double v = Y[i * kNout + c];
+        sy[c] += v;
+        qy[c] += v * v;
+        cy[c] += 1.0;
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < kNin; ++k) {
+    atomicAdd(&acc[k], s[k]);
+    atomicAdd(&acc[kNin + k], q[k]);
+  }
+#pragma unroll
+  for (int c = 0; c < kNout; ++c) {
+    atomicAdd(&acc[2 * kNin + c], sy[c]);
+    atomicAdd(&acc[2 * kNin + kNout + c], qy[c]);
+    atomicAdd(&acc[2 * kNin + 2 * kNout + c], cy[c]);
+  }
+}
+
+// order-preserving float <-> int mapping for atomic min/max
+__device__ __forceinline__ int f2ord(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__global__ void k_mlp_box(const float *X, long long n, int *lo, int *hi) {
+  int l[kNin], h[kNin];
+#pragma unroll
+  for (int k = 0; k < kNin; ++k) {
+    l[k] = 0x7fffffff;
+    h[k] = -0x7fffffff;
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int k = 0; k < kNin; ++k) {
+      const int v = f2ord(X[i * kNin + k]);
+      l[k] = min(l[k], v);
+      h[k] = max(h[k], v);
+    }
+#pragma unroll
+  for (int k = 0; k < kNin; ++k) {
+    atomicMin(&lo[k], l[k]);
+    atomicMax(&hi[k], h[k]);
+  }
+}
+
+// ------------------------------------------------------ features and targets
+// The 12 features of a post-activation point (natural logarithms).
+__device__ __forceinline__ void mlp_features(const ConstK<float> &K, const W<float> &w, float na, float wv,
+                                             float f[kNin]) {
+  const float ln2 = 0.693147180559945309f;
+  f[0] = lg2a(fmaxf(w.qc, K.qmin)) * ln2;
+  f[1] = lg2a(fmaxf(w.qr, K.qmin)) * ln2;
+  f[2] = lg2a(fmaxf(w.nc, 1.f)) * ln2;
+  f[3] = lg2a(fmaxf(w.nr, 1e-3f)) * ln2;
+  f[4] = lg2a(w.rho) * ln2;
+  f[5] = w.tc;
+  f[6] = lg2a(w.p) * ln2;
+  f[7] = lg2a(fmaxf(w.qv, 1e-10f)) * ln2;
+  f[8] = wv;
+  f[9] = lg2a(fmaxf(na, 1.f)) * ln2;
+  f[10] = w.qc > K.qmin ? 1.f : 0.f;
+  f[11] = w.qr > K.qmin ? 1.f : 0.f;
+}
+
+struct FeatArgs {
+  int mode;               // 0: training data (raw features, log-rates, masks); 1: inference rows
+  long long cap;          // rows available
+  unsigned long long *rows;   // row counter
+  float *X, *Y, *M;       // mode 0: [cap][12], [cap][4], [cap][4]
+  __nv_bfloat16 *xb;      // mode 1: [cap][16] standardised BF16 features
+  long long *rowpt;       // point index (k * pitch + c) of each row (mode 0: optional)
+  float4 *surr;           // mode 1: [nlev][pitch]; NaN written where the point is outside the box
+  const float *norm;      // mode 1: means and deviations of the features
+  const float *box;       // mode 1: [12 lo][12 hi]
+};
+
+// One thread per point of a domain: adjustment and activation as the mixed
+// step does them, then the point's features (and, for training data, the
+// scheme's four log-rates).
+__global__ void __launch_bounds__(256) k_mlp_features(const KArgs a, const KParams P, const FeatArgs fa) {
+  const long long np = (long long)a.nlev * a.pitch;
+  const long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  bool warm = false;
+  float f[kNin];
+  float y[kNout] = {0, 0, 0, 0}, mk[kNout] = {0, 0, 0, 0};
+  if (pt < np) {
+    const int c = (int)(pt % a.pitch);
+    if (c < a.ncols) {
+      const ConstK<float> &K = P.f;
+      Pt s;
+      const double *b = a.fld + pt;
+      const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
+      s.T = b[0]; s.qv = b[1 * fs]; s.qc = b[2 * fs]; s.qr = b[3 * fs];
+      s.qi = b[4 * fs]; s.qs = b[5 * fs]; s.qg = b[6 * fs];
+      s.p = b[13 * fs];
+      W<float> w;
+      float es0, qs0;
+      if (Mix::active(K, s, P.T0, w, es0, qs0)) {
+        s.nc = b[7 * fs]; s.nr = b[8 * fs]; s.ni = b[9 * fs]; s.ns = b[10 * fs]; s.ng = b[11 * fs];
+        s.na = b[12 * fs]; s.rho = b[14 * fs]; s.w = b[15 * fs];
+        MixInc o;
+        const float dn = Mix::pre(K, s, w, es0, qs0, o);
+        warm = w.qc > K.qmin || w.qr > K.qmin;
+        if (warm) {
+          mlp_features(K, w, d2f(s.na) - dn, d2f(s.w), f);
+          if (fa.mode == 0) {
+            Rt<float> r;
+            Phys<PolicyMix>::rates(K, w, a.dt, r);
+            const bool hc = w.qc > K.qmin, hr = w.qr > K.qmin;
+            const float v[kNout] = {r.aut, r.acc, r.scc, r.scr};
+            const bool def[kNout] = {hc, hc && hr, hc, hr};
+#pragma unroll
+            for (int j = 0; j < kNout; ++j)
+              if (def[j] && v[j] > 0.f) {
+                y[j] = lg2a(v[j]) * 0.693147180559945309f;
+                mk[j] = 1.f;
+              }
+          } else {
+            bool inbox = true;
+#pragma unroll
+            for (int j = 0; j < kNin; ++j) inbox &= f[j] >= fa.box[j] && f[j] <= fa.box[kNin + j];
+            if (!inbox) {
+              fa.surr[pt] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+              warm = false;
+            }
+          }
+        }
+      }
+    }
+  }
+  // warp-aggregated append of the rows
+  const unsigned ball = __ballot_sync(0xffffffffu, warm);
+  if (!ball) return;
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(fa.rows, (unsigned long long)__popc(ball));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (!warm) return;
+  const long long row = (long long)base + __popc(ball & ((1u << lane) - 1u));
+  if (row >= fa.cap) return;   // the caller sees rows > cap and reports it
+  if (fa.mode == 0) {
+    if (fa.rowpt) fa.rowpt[row] = pt;
+#pragma unroll
+    for (int j = 0; j < kNin; ++j) fa.X[row * kNin + j] = f[j];
+#pragma unroll
+    for (int j = 0; j < kNout; ++j) {
+      fa.Y[row * kNout + j] = y[j];
+      fa.M[row * kNout + j] = mk[j];
+    }
+  } else {
+    __align__(16) __nv_bfloat16 hb[kNinPad];
+#pragma unroll
+    for (int j = 0; j < kNinPad; ++j)
+      hb[j] = __float2bfloat16(j < kNin ? (f[j] - fa.norm[j]) / fa.norm[kNin + j] : 0.f);
+    uint4 *dst = reinterpret_cast<uint4 *>(fa.xb + row * kNinPad);
+    dst[0] = reinterpret_cast<const uint4 *>(hb)[0];
+    dst[1] = reinterpret_cast<const uint4 *>(hb)[1];
+    fa.rowpt[row] = pt;
+  }
+}
+
+// network outputs (standardised log-rates) -> rates at the rows' points
+__global__ void k_mlp_scatter(const float *Yn, long long rows, const long long *rowpt, const float *norm,
+                              float4 *surr) {
+  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const float *muy = norm + 2 * kNin, *sdy = norm + 2 * kNin + kNout;
+  float v[kNout];
+#pragma unroll
+  for (int j = 0; j < kNout; ++j) v[j] = __expf(Yn[r * kNout + j] * sdy[j] + muy[j]);
+  surr[rowpt[r]] = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+}  // namespace casim_dev

@@ -1,0 +1,165 @@
+"""Warm-rain surrogate on the GPU against the oracle network and the scheme.
+
+Forward and gradient: the GPU network (BF16 operands, FP32 sums) against the
+FP64 oracle network rounding at the same points.  Training data: features and
+log-rates of the feature pass against the oracle's post-activation state and
+rates.  Training: the loss falls.  Surrogate step: the network's rates are
+used where the inputs lie in the training box, the scheme's elsewhere.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as OM
+from oracle import surrogate as OS
+from paper_2010_14823_gb300 import casim, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def net():
+    m = casim.casim_mlp_create(seed=3)
+    yield m
+    casim.casim_mlp_free(m)
+
+
+def _theta(seed):
+    rng = np.random.default_rng(seed)
+    th = OM.init_params(seed) + 0.02 * rng.normal(size=OM.param_count())
+    return th.astype(np.float32).astype(np.float64)   # exactly representable in FP32
+
+
+def test_forward_matches_oracle(net):
+    th = _theta(11)
+    casim.casim_mlp_set_params(net, th)
+    assert np.array_equal(casim.casim_mlp_get_params(net), th.astype(np.float32))
+    X = np.random.default_rng(1).normal(size=(1000, 12)).astype(np.float32).astype(np.float64)
+    Yg = casim.casim_mlp_forward_host(net, X).astype(np.float64)
+    Yo, _, _ = OM.forward(th, X, bf16_round=True)
+    Y64, _, _ = OM.forward(th, X)
+    err = np.abs(Yg - Yo).max()
+    scale = np.abs(Yo).max()
+    print("forward: max |gpu - oracle(bf16)| =", err, " max |gpu - oracle(fp64)| =", np.abs(Yg - Y64).max(),
+          " output scale", scale)
+    # FP32 accumulation order, FP32 tanh, and the occasional one-ulp BF16 flip
+    # of a hidden unit (2^-8 relative), propagated through two layers
+    assert err <= 5e-3 * max(scale, 1.0)
+
+
+def test_gradient_matches_oracle(net):
+    th = _theta(12)
+    casim.casim_mlp_set_params(net, th)
+    rng = np.random.default_rng(2)
+    n = 512
+    X = rng.normal(size=(n, 12)).astype(np.float32).astype(np.float64)
+    T = rng.normal(size=(n, 4)).astype(np.float32).astype(np.float64)
+    M = (rng.random((n, 4)) < 0.8).astype(np.float64)
+    lg, gg = casim.casim_mlp_loss_grad_host(net, X, T, M)
+    lo, go = OM.loss_grad(th, X, T, M, bf16_round=True)
+    assert abs(lg - lo) <= 1e-4 * lo
+    # per layer: relative error of the gradient block
+    sizes = OM.SIZES
+    o = 0
+    worst = 0.0
+    for i in range(4):
+        for blk in (sizes[i] * sizes[i + 1], sizes[i + 1]):
+            a, b = gg[o:o + blk].astype(np.float64), go[o:o + blk]
+            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+            worst = max(worst, rel)
+            assert rel < 2e-3, (i, blk, rel)
+            o += blk
+    print("gradient: worst per-block relative error", worst)
+
+
+def _data(ctx, ncols=512, nlev=150, seed=41):
+    dz = synth.dz_stretched(nlev)
+    fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=seed)
+    d = casim.Domain(fld, dz, ncols)
+    cap = ncols * nlev
+    X = torch.zeros((cap, 12), dtype=torch.float32, device="cuda")
+    Y = torch.zeros((cap, 4), dtype=torch.float32, device="cuda")
+    M = torch.zeros((cap, 4), dtype=torch.float32, device="cuda")
+    rows = casim.casim_mlp_data(ctx, d.state, ncols, nlev, 1.0, X, Y, M, cap)
+    return fld, dz, d, X[:rows], Y[:rows], M[:rows], rows
+
+
+def test_training_data_matches_oracle_features_and_rates():
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED)
+    try:
+        ncols, nlev = 64, 60
+        dz = synth.dz_stretched(nlev)
+        fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=5)
+        d = casim.Domain(fld, dz, ncols)
+        cap = nlev * d.pitch
+        X = torch.zeros((cap, 12), dtype=torch.float32, device="cuda")
+        Y = torch.zeros((cap, 4), dtype=torch.float32, device="cuda")
+        M = torch.zeros((cap, 4), dtype=torch.float32, device="cuda")
+        P = torch.zeros(cap, dtype=torch.int64, device="cuda")
+        rows = casim.casim_mlp_data(ctx, d.state, ncols, nlev, 1.0, X, Y, M, cap, pts=P)
+    finally:
+        casim.casim_free(ctx)
+    X, Y, M, P = X[:rows].cpu().numpy(), Y[:rows].cpu().numpy(), M[:rows].cpu().numpy(), P[:rows].cpu().numpy()
+    warm = {}
+    for k in range(nlev):
+        for c in range(ncols):
+            st = O.adjust_activate(fld[:, k, c])
+            if OS.warm(st):
+                warm[k * d.pitch + c] = st
+    assert set(P.tolist()) == set(warm)
+    fe, ye = [], []
+    for r in range(rows):
+        st = warm[int(P[r])]
+        f = OS.features(st)
+        y, m = OS.targets(st)
+        assert np.array_equal(M[r], m)
+        assert np.array_equal(X[r, 10:], f[10:])
+        fe.append(np.abs(X[r, :10] - f[:10]))
+        ye.append(np.abs((Y[r] - y) * m))
+    fe, ye = np.array(fe), np.array(ye)
+    print("features: max", fe.max(axis=0), "log-rates: max", ye.max(axis=0))
+    # FP32 mixed form vs FP64: logs of small post-adjustment cloud carry the
+    # adjustment's ~1e-8 kg/kg error, everything else ~1e-5
+    assert np.percentile(fe, 99.9) < 1e-3 and fe.max() < 0.1
+    assert np.percentile(ye, 99.9) < 1e-3 and ye.max() < 0.3
+
+
+def test_training_reduces_loss_and_surrogate_step():
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED)
+    m = casim.casim_mlp_create(seed=7)
+    try:
+        fld, dz, d, X, Y, M, rows = _data(ctx, ncols=2048, nlev=150, seed=42)
+        assert rows > 10000
+        hist = casim.casim_mlp_fit(m, X, Y, M, rows, steps=400, batch=4096, lr=1e-3, seed=1)
+        first, last = float(np.mean(hist[:10])), float(np.mean(hist[-20:]))
+        print("training loss", first, "->", last)
+        assert last < 0.1 * first
+        stats = casim.casim_mlp_get_norm(m)
+        lo, hi = stats[32:44], stats[44:56]
+        assert np.all(lo <= hi)
+        # surrogate step on a fresh domain of the same kind vs the plain mixed step
+        dz2 = synth.dz_stretched(150)
+        f2 = synth.make_state("deep_convective", 1024, 150, dz2, seed=99)
+        plain, surr = casim.Domain(f2, dz2, 1024), casim.Domain(f2, dz2, 1024)
+        casim.casim_step(ctx, plain.state, 1024, 150, 1.0)
+        served = casim.casim_step_surrogate(ctx, m, surr.state, 1024, 150, 1.0)
+        assert casim.casim_get_error(ctx)[0] == 0
+        assert served > 0
+        (a, pa), (b, pb) = surr.numpy(), plain.numpy()
+        # non-warm fields and points are untouched by the surrogate; warm ones move
+        F = synth.FIDX
+        assert np.array_equal(a[F["qi"]], b[F["qi"]]) or np.abs(a[F["qi"]] - b[F["qi"]]).max() < 1e-7
+        inc = np.abs(b[F["qr"]] - f2[F["qr"]]).max()
+        print("served", served, "max |qr surrogate - plain| =", np.abs(a[F["qr"]] - b[F["qr"]]).max(),
+              "max |qr increment| =", inc)
+        # a network that says "outside everything" leaves the scheme's result
+        far = stats.copy()
+        far[32:44], far[44:56] = 1e30, -1e30
+        casim.casim_mlp_set_norm(m, far)
+        guard = casim.Domain(f2, dz2, 1024)
+        assert casim.casim_step_surrogate(ctx, m, guard.state, 1024, 150, 1.0) == 0
+        assert np.array_equal(guard.numpy()[0], b)
+    finally:
+        casim.casim_mlp_free(m)
+        casim.casim_free(ctx)

@@ -1,0 +1,77 @@
+"""Pins of the MLP oracle: torch's float64 layers for the forward pass,
+central finite differences for the gradient, exact BF16 rounding cases."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp
+
+
+def _data(n=7, seed=0):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, 12))
+    T = rng.normal(size=(n, 4))
+    M = (rng.random((n, 4)) < 0.7).astype(np.float64)
+    return X, T, M
+
+
+def test_forward_matches_torch_float64_layers():
+    theta = mlp.init_params(1) + 0.01 * np.random.default_rng(2).normal(size=mlp.param_count())
+    X, _, _ = _data()
+    Y, _, _ = mlp.forward(theta, X)
+    layers = mlp.unflatten(theta)
+    h = torch.tensor(X, dtype=torch.float64)
+    for i, (W, b) in enumerate(layers):
+        h = torch.nn.functional.linear(h, torch.tensor(W.T), torch.tensor(b))
+        if i < 3:
+            h = torch.tanh(h)
+    assert np.allclose(Y, h.numpy(), rtol=1e-13, atol=1e-13)
+
+
+def test_gradient_matches_central_differences():
+    theta = mlp.init_params(3) + 0.05 * np.random.default_rng(4).normal(size=mlp.param_count())
+    X, T, M = _data(5, 1)
+    loss, g = mlp.loss_grad(theta, X, T, M)
+    rng = np.random.default_rng(5)
+    idx = np.concatenate([rng.choice(mlp.param_count(), 40, replace=False),
+                          [0, mlp.param_count() - 1, 12 * 256, 12 * 256 + 255]])
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(theta)
+        e[i] = h
+        fd = (mlp.loss_grad(theta + e, X, T, M)[0] - mlp.loss_grad(theta - e, X, T, M)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), i
+
+
+def test_masked_outputs_do_not_contribute():
+    theta = mlp.init_params(6)
+    X, T, M = _data(6, 2)
+    M[:, 2] = 0.0
+    T2 = T.copy()
+    T2[:, 2] += 100.0
+    l1, g1 = mlp.loss_grad(theta, X, T, M)
+    l2, g2 = mlp.loss_grad(theta, X, T2, M)
+    assert l1 == l2 and np.array_equal(g1, g2)
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    # exactly representable values stay, halfway cases go to the even neighbour
+    one = np.float32(1.0)
+    ulp = 2.0 ** -7
+    assert mlp.bf16(1.0) == 1.0 and mlp.bf16(-2.5) == -2.5
+    assert mlp.bf16(1.0 + ulp / 2) == 1.0                 # tie -> even (1.0)
+    assert mlp.bf16(1.0 + 3 * ulp / 2) == 1.0 + 2 * ulp   # tie -> even (1 + 2 ulp)
+    assert mlp.bf16(1.0 + 0.6 * ulp) == 1.0 + ulp
+    x = np.random.default_rng(7).normal(size=1000)
+    r = mlp.bf16(x)
+    assert np.all(np.abs(r - x) <= np.abs(x) * 2.0 ** -8 + 1e-300)   # unit roundoff 2^-8
+    assert np.all((r.astype(np.float32).view(np.uint32) & 0xFFFF) == 0)
+    del one
+
+
+def test_param_count_and_layout():
+    assert mlp.param_count() == 12 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 4 + 4
+    theta = np.arange(mlp.param_count(), dtype=np.float64)
+    assert np.array_equal(mlp.flatten(mlp.unflatten(theta)), theta)
+    W1, b1 = mlp.unflatten(theta)[0]
+    assert W1[0, 1] == 1 and W1[1, 0] == 256 and b1[0] == 12 * 256
