@@ -202,6 +202,101 @@ def bench_batch(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def bench_surrogate(args, rank, world, local):
+    """Learned warm-rain rates on deep convection 512x512x150: training data
+    from mixed-form runs (the scheme's own rates), training on the GPU,
+    inference through the guarded surrogate step; errors judged by the plain
+    mixed step (rates on held-out points, 100-step surface precipitation)."""
+    import torch
+    from paper_2010_14823_gb300 import casim, shard, synth
+    casim.lib()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    fld, dz, ncols, nlev, dt, _ = synth.workload("deep_512x512x150", seed=shard.rank_seed(1240, rank))
+    npts = ncols * nlev
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED)
+    m = casim.casim_mlp_create(seed=5)
+    dom = casim.Domain(fld, dz, ncols)
+    # training data: warm points of successive mixed-form states, up to 10 M rows
+    cap = 10_000_000
+    X = torch.zeros((cap, 12), dtype=torch.float32, device="cuda")
+    Y = torch.zeros((cap, 4), dtype=torch.float32, device="cuda")
+    M = torch.zeros((cap, 4), dtype=torch.float32, device="cuda")
+    have = 0
+    gen_steps = 0
+    while have < cap and gen_steps < 20:
+        rows = casim.casim_mlp_data(ctx, dom.state, ncols, nlev, dt, X[have:], Y[have:], M[have:], cap - have,
+                                    stream=stream)
+        have += min(rows, cap - have)
+        casim.casim_step(ctx, dom.state, ncols, nlev, dt, stream)
+        gen_steps += 1
+    # held-out rows from the state after the training window
+    Xh = torch.zeros((npts, 12), dtype=torch.float32, device="cuda")
+    Yh = torch.zeros((npts, 4), dtype=torch.float32, device="cuda")
+    Mh = torch.zeros((npts, 4), dtype=torch.float32, device="cuda")
+    hold = casim.casim_mlp_data(ctx, dom.state, ncols, nlev, dt, Xh, Yh, Mh, npts, stream=stream)
+    train_steps, batch = 4000, 8192
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = casim.casim_mlp_fit(m, X, Y, M, have, train_steps, batch, 1e-3, seed=3, stream=stream, history=False)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del hist
+    stats = casim.casim_mlp_get_norm(m)
+    # rate error on held-out points inside the box (linear space, relative)
+    sel = np.random.default_rng(0).choice(hold, min(hold, 200_000), replace=False)
+    xs, ys, ms = Xh[sel].cpu().numpy(), Yh[sel].cpu().numpy(), Mh[sel].cpu().numpy()
+    lo, hi = stats[32:44], stats[44:56]
+    inbox = np.all((xs >= lo) & (xs <= hi), axis=1)
+    xn = (xs - stats[0:12]) / stats[12:24]
+    yp = casim.casim_mlp_forward_host(m, xn.astype(np.float32)) * stats[28:32] + stats[24:28]
+    rel = np.abs(np.expm1(yp - ys)) * ms
+    rate_err = {}
+    for j, name in enumerate(("aut", "acc", "scc", "scr")):
+        v = rel[inbox & (ms[:, j] > 0), j]
+        rate_err[name] = {"median": float(np.median(v)), "p99": float(np.percentile(v, 99)), "n": int(v.size)}
+    # 100 steps: plain mixed vs surrogate from the same start, surface precipitation judged by the plain run
+    nsteps = 100
+    plain, surr = casim.Domain(fld, dz, ncols), casim.Domain(fld, dz, ncols)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(nsteps):
+        casim.casim_step(ctx, plain.state, ncols, nlev, dt, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / nsteps
+    served = 0
+    e0.record(stream)
+    for _ in range(nsteps):
+        served += casim.casim_step_surrogate(ctx, m, surr.state, ncols, nlev, dt, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    surr_ms = e0.elapsed_time(e1) / nsteps
+    rc, fl = casim.casim_get_error(ctx, stream)
+    assert rc == 0, (rc, fl)
+    pp, ps = plain.precip[:, :ncols].sum(0).cpu().numpy(), surr.precip[:, :ncols].sum(0).cpu().numpy()
+    tot_p, tot_s = float(pp.sum()), float(ps.sum())
+    wet = pp > 1e-6 * max(pp.max(), 1e-30)
+    col_rel = np.abs(ps[wet] - pp[wet]) / pp[wet]
+    casim.casim_mlp_free(m)
+    casim.casim_free(ctx)
+    if rank == 0:
+        value = world * npts / (surr_ms * 1e-3)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": nsteps, "warmup": 0,
+                "ms_per_step": surr_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16 network + f32/f64 step", "data": "synthetic",
+                "config": {"workload": "surrogate_deep_512x512x150", "train_rows": have, "gen_steps": gen_steps,
+                           "train_steps": train_steps, "batch": batch, "train_s": train_s,
+                           "rate_rel_error_heldout": rate_err, "heldout_inbox_frac": float(inbox.mean()),
+                           "served_points_per_step": served / nsteps, "plain_ms_per_step": plain_ms,
+                           "surrogate_ms_per_step": surr_ms, "precip_total_rel_error": abs(tot_s - tot_p) / tot_p,
+                           "precip_column_rel_error": {"median": float(np.median(col_rel)),
+                                                       "p99": float(np.percentile(col_rel, 99))}},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -223,6 +318,8 @@ def main():
     from paper_2010_14823_gb300 import synth
     if args.workload == "batch64":
         return bench_batch(args, rank, world, local)
+    if args.workload == "surrogate":
+        return bench_surrogate(args, rank, world, local)
     from paper_2010_14823_gb300 import shard
     base_fld, dz, ncols, nlev, dt, _ = synth.workload(args.workload, ncols=args.ncols,
                                                       seed=shard.rank_seed(1236, rank))

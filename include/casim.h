@@ -68,12 +68,15 @@ enum casim_status {
   CASIM_ERR_OOM = -2,        /* device allocation failed */
   CASIM_ERR_CUDA = -3,       /* a CUDA call failed (see casim_last_cuda_error) */
   CASIM_ERR_NONFINITE = -4,  /* casim_get_error: a non-finite value was produced */
-  CASIM_ERR_CFL = -5         /* casim_get_error: substep cap reached in sedimentation */
+  CASIM_ERR_CFL = -5,        /* casim_get_error: substep cap reached in sedimentation */
+  CASIM_ERR_TIMEOUT = -6     /* casim_get_error: a bounded wait inside the surrogate network's
+                                kernel gave up; its rows were left to the scheme's rates */
 };
 
 /* device error-word bits (casim_get_error) */
 #define CASIM_EFLAG_NONFINITE 1u
 #define CASIM_EFLAG_CFL 2u
+#define CASIM_EFLAG_TIMEOUT 4u
 
 /* Scheme parameters.  casim_default_params() fills the published values the
    scheme is defined with; callers may change them before casim_init(). */
@@ -136,7 +139,8 @@ int casim_budget(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, doub
 
 /* Wait for `stream`, read and clear the device error word.  *flags receives the
    CASIM_EFLAG_* bits (may be NULL).  Returns CASIM_OK, CASIM_ERR_NONFINITE or
-   CASIM_ERR_CFL (the first set, in that order of precedence), or CASIM_ERR_CUDA. */
+   CASIM_ERR_CFL (the first set, in that order of precedence, after CASIM_ERR_TIMEOUT),
+   or CASIM_ERR_CUDA. */
 int casim_get_error(casim_ctx *ctx, unsigned *flags, void *stream);
 
 /* ----------------------------------------------------------------------------
@@ -220,7 +224,10 @@ long long casim_mlp_param_count(void);
 /* FP32 master parameters, host arrays of casim_mlp_param_count() floats. */
 int casim_mlp_set_params(casim_mlp *mlp, const float *host, long long n);
 int casim_mlp_get_params(const casim_mlp *mlp, float *host, long long n);
-/* Standardised inputs Xn[n][12] -> outputs Y[n][4] (host arrays; synchronous). */
+/* Inference engine: 1 (default) = tcgen05/TMEM kernel, 0 = mma.sync GEMMs. */
+int casim_mlp_set_engine(casim_mlp *mlp, int engine);
+/* Standardised inputs Xn[n][12] -> outputs Y[n][4] (host arrays; synchronous;
+   runs the selected engine). */
 int casim_mlp_forward_host(casim_mlp *mlp, const float *Xn, int n, float *Y);
 /* Loss sum_i sum_j M (Y - Tn)^2 / sum M and its gradient (host arrays of
    n x 12, n x 4, n x 4, and param_count floats; synchronous). */

@@ -24,9 +24,10 @@ NPRECIP = 4
 NSUB_MAX = 64
 EFLAG_NONFINITE = 1
 EFLAG_CFL = 2
+EFLAG_TIMEOUT = 4
 NOALLOC_MAX_COLS = 1 << 20
 _ERRORS = {-1: "CASIM_ERR_ARG", -2: "CASIM_ERR_OOM", -3: "CASIM_ERR_CUDA",
-           -4: "CASIM_ERR_NONFINITE", -5: "CASIM_ERR_CFL"}
+           -4: "CASIM_ERR_NONFINITE", -5: "CASIM_ERR_CFL", -6: "CASIM_ERR_TIMEOUT"}
 
 
 class CasimError(RuntimeError):
@@ -142,6 +143,8 @@ def lib():
         L.casim_mlp_set_norm.restype = i
         L.casim_step_surrogate.argtypes = [vp, vp, ps, i, i, d, vp, ctypes.POINTER(ll)]
         L.casim_step_surrogate.restype = i
+        L.casim_mlp_set_engine.argtypes = [vp, i]
+        L.casim_mlp_set_engine.restype = i
         L.casim_mlp_free.argtypes = [vp]
         L.casim_mlp_free.restype = None
         _lib = L
@@ -405,3 +408,8 @@ def casim_step_surrogate(ctx, mlp, state: casim_state, ncols: int, nlev: int, dt
 
 def casim_mlp_free(mlp):
     lib().casim_mlp_free(mlp)
+
+
+def casim_mlp_set_engine(mlp, engine: int):
+    """1: tcgen05 inference kernel (default), 0: mma.sync GEMMs."""
+    _check(lib().casim_mlp_set_engine(mlp, engine), "casim_mlp_set_engine")

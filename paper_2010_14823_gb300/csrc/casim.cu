@@ -297,6 +297,7 @@ extern "C" int casim_get_error(casim_ctx *ctx, unsigned *flags, void *stream) {
   CUDA_TRY(cudaMemcpy(&h, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
   if (flags) *flags = h;
+  if (h & CASIM_EFLAG_TIMEOUT) return CASIM_ERR_TIMEOUT;
   if (h & CASIM_EFLAG_NONFINITE) return CASIM_ERR_NONFINITE;
   if (h & CASIM_EFLAG_CFL) return CASIM_ERR_CFL;
   return CASIM_OK;
@@ -738,6 +739,9 @@ struct casim_mlp {
   float *theta = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;   // FP32 [kNParam]
   MlpBf16 wb{};
   __nv_bfloat16 *wbuf = nullptr;
+  unsigned char *img = nullptr;   // weight images for the tcgen05 kernel
+  unsigned *d_err = nullptr;
+  int engine = 1;                 // 1: tcgen05 inference, 0: mma.sync
   float *norm = nullptr;   // [12 mean][12 sd][4 mean][4 sd]
   float *box = nullptr;    // [12 lo][12 hi]
   bool fitted = false;
@@ -848,6 +852,26 @@ static void mlp_backward(casim_mlp *m, int n, cudaStream_t st) {
 
 static void mlp_cast(casim_mlp *m, cudaStream_t st) {
   k_mlp_cast<<<(kNh * kNh + 255) / 256, 256, 0, st>>>(m->theta, m->wb);
+  k_mlp_images<<<(kNh * kNh + 255) / 256, 256, 0, st>>>(m->theta, m->img);
+}
+
+// forward pass of n rows of BF16 inputs on the tcgen05 kernel: rates at the
+// rows' points (rowpt) or standardised outputs in m->y (rowpt null)
+static void mlp_forward_umma(casim_mlp *m, const __nv_bfloat16 *xb, long long n, const long long *rowpt,
+                             float4 *surr, unsigned *err, int nsm, cudaStream_t st) {
+  UmmaArgs u;
+  u.xb = xb;
+  u.rows = n;
+  u.rowpt = rowpt;
+  u.img = m->img;
+  u.theta = m->theta;
+  u.norm = m->norm;
+  u.surr = surr;
+  u.y = m->y;
+  u.err = err;
+  const long long tiles = (n + 127) / 128;
+  const int grid = (int)std::min<long long>(tiles, nsm);
+  if (grid > 0) k_mlp_umma<<<grid, 128, kUmmaSmem, st>>>(u);
 }
 
 extern "C" void casim_mlp_free(casim_mlp *m) {
@@ -855,7 +879,7 @@ extern "C" void casim_mlp_free(casim_mlp *m) {
   cudaDeviceSynchronize();
   mlp_free_batch(m);
   void *ps[] = {m->theta, m->grad, m->m1, m->m2, m->wbuf, m->norm, m->box, m->cnt, m->loss,
-                m->xb, m->rowpt, m->surr, m->rowctr};
+                m->xb, m->rowpt, m->surr, m->rowctr, m->img, m->d_err};
   for (void *p : ps) cudaFree(p);
   delete m;
 }
@@ -886,6 +910,10 @@ extern "C" int casim_mlp_create(casim_mlp **out, unsigned long long seed) {
   if (e == cudaSuccess) e = dalloc(&m->cnt, 1);
   if (e == cudaSuccess) e = dalloc(&m->loss, 1);
   if (e == cudaSuccess) e = dalloc(&m->rowctr, 1);
+  if (e == cudaSuccess) e = dalloc(&m->img, kImgBytes);
+  if (e == cudaSuccess) e = dalloc(&m->d_err, 1);
+  if (e == cudaSuccess) e = cudaMemset(m->d_err, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
   if (e == cudaSuccess) e = cudaMemcpy(m->theta, th.data(), kNParam * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->m1, 0, kNParam * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->m2, 0, kNParam * sizeof(float));
@@ -926,14 +954,34 @@ extern "C" int casim_mlp_get_params(const casim_mlp *m, float *host, long long n
   return CASIM_OK;
 }
 
+extern "C" int casim_mlp_set_engine(casim_mlp *m, int engine) {
+  if (!m || (engine != 0 && engine != 1)) return CASIM_ERR_ARG;
+  m->engine = engine;
+  return CASIM_OK;
+}
+
 extern "C" int casim_mlp_forward_host(casim_mlp *m, const float *Xn, int n, float *Y) {
   if (!m || !Xn || !Y || n < 1) return CASIM_ERR_ARG;
   int rc = mlp_batch_ws(m, n);
   if (rc != CASIM_OK) return rc;
   CUDA_TRY(cudaMemcpy(m->Xn, Xn, (size_t)n * kNin * sizeof(float), cudaMemcpyHostToDevice));
   k_mlp_inputs<<<(unsigned)(((long long)n * kNinPad + 255) / 256), 256>>>(m->Xn, n, m->h0);
-  mlp_forward(m, n, false, 0);
+  if (m->engine == 1) {
+    int dev = 0, nsm = 1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    mlp_forward_umma(m, m->h0, n, nullptr, nullptr, m->d_err, nsm, 0);
+  } else {
+    mlp_forward(m, n, false, 0);
+  }
   CUDA_TRY(cudaGetLastError());
+  unsigned herr = 0;
+  CUDA_TRY(cudaMemcpy(&herr, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (herr) {
+    cudaMemset(m->d_err, 0, sizeof(unsigned));
+    std::snprintf(g_last_error, sizeof(g_last_error), "casim_mlp_forward_host: a bounded wait gave up");
+    return CASIM_ERR_CUDA;
+  }
   CUDA_TRY(cudaMemcpy(Y, m->y, (size_t)n * kNout * sizeof(float), cudaMemcpyDeviceToHost));
   return CASIM_OK;
 }
@@ -1106,17 +1154,22 @@ extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_st
   CUDA_TRY(cudaMemcpyAsync(&hrows, m->rowctr, sizeof(hrows), cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
   const long long rows = std::min((long long)hrows, m->cap_rows);
-  // 2. the network on the rows, in chunks
-  const int chunk = 1 << 17;
-  if ((rc = mlp_batch_ws(m, (int)std::min<long long>(chunk, std::max<long long>(rows, 1)))) != CASIM_OK) return rc;
-  for (long long r0 = 0; r0 < rows; r0 += m->cap_b) {
-    const int n = (int)std::min<long long>(m->cap_b, rows - r0);
-    __nv_bfloat16 *save = m->h0;
-    m->h0 = m->xb + r0 * kNinPad;
-    mlp_forward(m, n, false, st);
-    m->h0 = save;
-    k_mlp_scatter<<<(n + 255) / 256, 256, 0, st>>>(m->y, n, m->rowpt + r0, m->norm, m->surr);
-    ctx->launches += 5;
+  // 2. the network on the rows
+  if (m->engine == 1) {
+    mlp_forward_umma(m, m->xb, rows, m->rowpt, m->surr, ctx->d_err, ctx->nsm, st);
+    ctx->launches++;
+  } else {
+    const int chunk = 1 << 17;
+    if ((rc = mlp_batch_ws(m, (int)std::min<long long>(chunk, std::max<long long>(rows, 1)))) != CASIM_OK) return rc;
+    for (long long r0 = 0; r0 < rows; r0 += m->cap_b) {
+      const int n = (int)std::min<long long>(m->cap_b, rows - r0);
+      __nv_bfloat16 *save = m->h0;
+      m->h0 = m->xb + r0 * kNinPad;
+      mlp_forward(m, n, false, st);
+      m->h0 = save;
+      k_mlp_scatter<<<(n + 255) / 256, 256, 0, st>>>(m->y, n, m->rowpt + r0, m->norm, m->surr);
+      ctx->launches += 5;
+    }
   }
   // 3. the step, taking the network's rates where given
   a.surr = m->surr;

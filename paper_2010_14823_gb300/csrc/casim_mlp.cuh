@@ -465,3 +465,280 @@ __global__ void k_mlp_scatter(const float *Yn, long long rows, const long long *
 }
 
 }  // namespace casim_dev
+
+// ------------------------------------------------ tcgen05 inference kernel
+#include "casim_umma.cuh"
+
+namespace casim_dev {
+
+// Weight images in global memory, already in the swizzled shared-memory
+// layout, so that 1-D bulk copies land them ready for the tensor cores:
+//   W1: [256 rows][64] (k >= 12 zero)                         32 KB
+//   W2, W3: four chunks of 64 output rows x 256 k             4 x 32 KB each
+//   W4: [16 rows][256] (rows >= 4 zero)                        8 KB
+constexpr uint32_t kImgW1 = 256 * 128, kImgChunk = 64 * 4 * 128, kImgW4 = 16 * 4 * 128;
+constexpr uint32_t kImgBytes = kImgW1 + 8 * kImgChunk + kImgW4;
+
+__global__ void k_mlp_images(const float *theta, unsigned char *img) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const __nv_bfloat16 z = __float2bfloat16(0.f);
+  if (i < 256 * 64) {   // W1 (n, k)
+    const int n = i / 64, k = i % 64;
+    *reinterpret_cast<__nv_bfloat16 *>(img + sw128_offset(256, n, k)) =
+        k < kNin ? __float2bfloat16(theta[kOffW1 + k * kNh + n]) : z;
+  }
+  if (i < 256 * 256) {  // W2, W3 (n, k)
+    const int n = i / 256, k = i % 256, q = n / 64, nn = n % 64;
+    const uint32_t off = q * kImgChunk + sw128_offset(64, nn, k);
+    *reinterpret_cast<__nv_bfloat16 *>(img + kImgW1 + off) = __float2bfloat16(theta[kOffW2 + k * kNh + n]);
+    *reinterpret_cast<__nv_bfloat16 *>(img + kImgW1 + 4 * kImgChunk + off) = __float2bfloat16(theta[kOffW3 + k * kNh + n]);
+  }
+  if (i < 16 * 256) {   // W4 (n, k)
+    const int n = i / 256, k = i % 256;
+    *reinterpret_cast<__nv_bfloat16 *>(img + kImgW1 + 8 * kImgChunk + sw128_offset(16, n, k)) =
+        n < kNout ? __float2bfloat16(theta[kOffW4 + k * kNout + n]) : z;
+  }
+}
+
+struct UmmaArgs {
+  const __nv_bfloat16 *xb;     // [rows][16] standardised features
+  long long rows;
+  const long long *rowpt;      // point of each row (null: write Y rows instead)
+  const unsigned char *img;    // weight images
+  const float *theta;          // biases are read from the flat parameters
+  const float *norm;           // output standardisation
+  float4 *surr;                // rates at the points
+  float *y;                    // [rows][4] standardised outputs when rowpt is null
+  unsigned *err;
+};
+
+constexpr unsigned kUmmaSpins = 1u << 22;
+constexpr int kUmmaSmem = 1024 + 65536 + kImgW1 + kImgW4 + 2 * kImgChunk;
+
+// Persistent: one CTA (128 threads) per SM walks 128-row tiles.  Per tile:
+// layer 1 (one MMA, K = 16) -> TMEM -> bias, tanh, BF16 -> swizzled smem ->
+// layer 2 (four N-quarters of 16 MMAs, weights streamed) -> ... -> layer 4
+// (N = 16) -> rates at the rows' points.  Thread 0 issues the MMAs and the
+// weight copies; all four warps run the epilogues on their 32 TMEM lanes.
+__global__ void __launch_bounds__(128, 1) k_mlp_umma(const UmmaArgs u) {
+  extern __shared__ __align__(16) unsigned char sraw[];
+  unsigned char *sm = sraw + ((1024 - (smem_addr(sraw) & 1023)) & 1023);
+  unsigned char *A = sm;                         // 4 slabs x 128 rows x 128 B
+  unsigned char *W1 = A + 65536;
+  unsigned char *W4 = W1 + kImgW1;
+  unsigned char *WB = W4 + kImgW4;               // two chunk buffers
+  __shared__ float s_bias[3 * kNh + kNout];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) unsigned long long s_bar[6];   // 0 weights, 1 mma, 2-3 full, 4-5 free
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long ntiles = (u.rows + 127) / 128;
+
+  for (int i = tid; i < kNh; i += 128) {
+    s_bias[i] = u.theta[kOffB1 + i];
+    s_bias[kNh + i] = u.theta[kOffB2 + i];
+    s_bias[2 * kNh + i] = u.theta[kOffB3 + i];
+  }
+  if (tid < kNout) s_bias[3 * kNh + tid] = u.theta[kOffB4 + tid];
+  if (warp == 0) {
+    tmem_alloc(smem_addr(&s_tmem), 256);
+    tmem_relinquish();
+  }
+  const uint32_t bw = smem_addr(&s_bar[0]), bm = smem_addr(&s_bar[1]);
+  const uint32_t bfull[2] = {smem_addr(&s_bar[2]), smem_addr(&s_bar[3])};
+  const uint32_t bfree[2] = {smem_addr(&s_bar[4]), smem_addr(&s_bar[5])};
+  if (tid == 0) {
+    for (int i = 0; i < 6; ++i) bar_init(smem_addr(&s_bar[i]), 1);
+    bar_fence_init();
+    s_abort = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = s_tmem;
+  const uint32_t trow = taddr + ((uint32_t)(32 * warp) << 16);
+
+  // resident weights of layers 1 and 4, and the first streamed chunk
+  const long long nchunks = ntiles * 8;
+  const long long my_chunks = ((long long)blockIdx.x < ntiles) ? ((ntiles - 1 - blockIdx.x) / gridDim.x + 1) * 8 : 0;
+  int nload[2] = {0, 0}, ncommit[2] = {0, 0};
+  auto chunk_src = [&](long long g) {   // g-th chunk of this CTA: tile-local index g % 8
+    const int c = (int)(g % 8);
+    return u.img + kImgW1 + (uint32_t)c * kImgChunk;   // chunks 0..3 layer 2, 4..7 layer 3
+  };
+  if (tid == 0) {
+    bar_expect_tx(bw, kImgW1 + kImgW4);
+    bulk_load(smem_addr(W1), u.img, kImgW1, bw);
+    bulk_load(smem_addr(W4), u.img + kImgW1 + 8 * kImgChunk, kImgW4, bw);
+    if (my_chunks > 0) {
+      bar_expect_tx(bfull[0], kImgChunk);
+      bulk_load(smem_addr(WB), chunk_src(0), kImgChunk, bfull[0]);
+      nload[0] = 1;
+    }
+    if (!bar_wait(bw, 0, kUmmaSpins)) { s_abort = 1; atomicOr(u.err, 4u); }
+  }
+  (void)nchunks;
+  __syncthreads();
+  int mma_phase = 0;
+  long long g = 0;   // chunks consumed by this CTA
+  const uint32_t id256 = umma_idesc_bf16(128, 256), id64 = umma_idesc_bf16(128, 64), id16 = umma_idesc_bf16(128, 16);
+
+  // epilogue of a hidden layer: TMEM row -> bias, tanh -> BF16 -> A (swizzled)
+  auto hidden_epilogue = [&](const float *bias) {
+    const int r = tid;
+#pragma unroll 1
+    for (int c = 0; c < kNh; c += 32) {
+      float v[32];
+      tmem_ld32(trow + c, v);
+      __align__(16) __nv_bfloat16 hb[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) hb[i] = __float2bfloat16(tanh_approx(v[i] + bias[c + i]));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = c + 8 * j;
+        *reinterpret_cast<uint4 *>(A + sw128_offset(128, r, k)) = reinterpret_cast<const uint4 *>(hb)[j];
+      }
+    }
+  };
+  auto sync_for_mma = [&]() {   // smem writes and TMEM reads done before the next MMAs
+    tc_fence_before();
+    fence_async_smem();
+    __syncthreads();
+    tc_fence_after();
+  };
+  auto wait_mma = [&]() {
+    if (!bar_wait(bm, (uint32_t)(mma_phase & 1), kUmmaSpins)) {
+      s_abort = 1;
+      atomicOr(u.err, 4u);
+    }
+    ++mma_phase;
+    tc_fence_after();
+  };
+  // one streamed layer: 4 chunks of 16 MMAs (N = 64) from the chunk buffers
+  auto streamed_layer = [&]() {
+    for (int q = 0; q < 4; ++q, ++g) {
+      const int b = (int)(g & 1);
+      if (!bar_wait(bfull[b], (uint32_t)((nload[b] - 1) & 1), kUmmaSpins)) {
+        s_abort = 1;
+        atomicOr(u.err, 4u);
+        return;
+      }
+      tc_fence_after();
+      unsigned char *Wc = WB + b * kImgChunk;
+#pragma unroll 1
+      for (int s = 0; s < 16; ++s) {
+        const int slab = s >> 2, sub = s & 3;
+        const uint64_t ad = umma_desc_sw128(smem_addr(A) + slab * 16384 + sub * 32);
+        const uint64_t bd = umma_desc_sw128(smem_addr(Wc) + slab * 8192 + sub * 32);
+        umma_bf16(taddr + q * 64, ad, bd, id64, s > 0 ? 1u : 0u);
+      }
+      umma_commit(bfree[b]);
+      ++ncommit[b];
+      // refill the other buffer once its previous chunk's MMAs are done
+      const long long nxt = g + 1;
+      if (nxt < my_chunks) {
+        const int b2 = (int)(nxt & 1);
+        if (nload[b2] > 0) {
+          if (!bar_wait(bfree[b2], (uint32_t)((ncommit[b2] - 1) & 1), kUmmaSpins)) {
+            s_abort = 1;
+            atomicOr(u.err, 4u);
+            return;
+          }
+        }
+        bar_expect_tx(bfull[b2], kImgChunk);
+        bulk_load(smem_addr(WB + b2 * kImgChunk), chunk_src(nxt), kImgChunk, bfull[b2]);
+        ++nload[b2];
+      }
+    }
+  };
+
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (s_abort) break;
+    const long long r0 = t * 128;
+    const int nrow = (int)min(128LL, u.rows - r0);
+    // features -> A slab 0, chunks 0 and 1 of each row
+    {
+      const int r = tid;
+      uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
+      if (r < nrow) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(u.xb + (r0 + r) * kNinPad);
+        v0 = src[0];
+        v1 = src[1];
+      }
+      *reinterpret_cast<uint4 *>(A + sw128_offset(128, r, 0)) = v0;
+      *reinterpret_cast<uint4 *>(A + sw128_offset(128, r, 8)) = v1;
+    }
+    sync_for_mma();
+    if (tid == 0) {
+      umma_bf16(taddr, umma_desc_sw128(smem_addr(A)), umma_desc_sw128(smem_addr(W1)), id256, 0u);
+      umma_commit(bm);
+    }
+    wait_mma();
+    hidden_epilogue(s_bias);
+    sync_for_mma();
+    if (s_abort) break;
+    if (tid == 0) {
+      streamed_layer();
+      umma_commit(bm);
+    }
+    wait_mma();
+    hidden_epilogue(s_bias + kNh);
+    sync_for_mma();
+    if (s_abort) break;
+    if (tid == 0) {
+      streamed_layer();
+      umma_commit(bm);
+    }
+    wait_mma();
+    hidden_epilogue(s_bias + 2 * kNh);
+    sync_for_mma();
+    if (s_abort) break;
+    if (tid == 0) {
+#pragma unroll 1
+      for (int s = 0; s < 16; ++s) {
+        const int slab = s >> 2, sub = s & 3;
+        const uint64_t ad = umma_desc_sw128(smem_addr(A) + slab * 16384 + sub * 32);
+        const uint64_t bd = umma_desc_sw128(smem_addr(W4) + slab * 2048 + sub * 32);
+        umma_bf16(taddr, ad, bd, id16, s > 0 ? 1u : 0u);
+      }
+      umma_commit(bm);
+    }
+    wait_mma();
+    {
+      float v[32];
+      tmem_ld32(trow, v);
+      const int r = tid;
+      if (r < nrow) {
+        float y[kNout];
+#pragma unroll
+        for (int j = 0; j < kNout; ++j) y[j] = v[j] + s_bias[3 * kNh + j];
+        if (u.rowpt) {
+          const float *muy = u.norm + 2 * kNin, *sdy = u.norm + 2 * kNin + kNout;
+          u.surr[u.rowpt[r0 + r]] = make_float4(__expf(y[0] * sdy[0] + muy[0]), __expf(y[1] * sdy[1] + muy[1]),
+                                                __expf(y[2] * sdy[2] + muy[2]), __expf(y[3] * sdy[3] + muy[3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < kNout; ++j) u.y[(r0 + r) * kNout + j] = y[j];
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  // drain: every tcgen05 operation and bulk copy of this CTA has completed
+  // (bounded waits) before the tensor memory is released
+  __syncthreads();
+  if (tid == 0) {
+    umma_commit(bm);
+    bar_wait(bm, (uint32_t)(mma_phase & 1), kUmmaSpins);
+    for (int b = 0; b < 2; ++b)
+      if (nload[b] > 0) bar_wait(bfull[b], (uint32_t)((nload[b] - 1) & 1), kUmmaSpins);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(taddr, 256);
+}
+
+}  // namespace casim_dev
