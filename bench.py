@@ -217,19 +217,27 @@ def bench_surrogate(args, rank, world, local):
     ctx = casim.casim_init(precision=casim.CASIM_MIXED)
     m = casim.casim_mlp_create(seed=5)
     dom = casim.Domain(fld, dz, ncols)
-    # training data: warm points of successive mixed-form states, up to 10 M rows
-    cap = 10_000_000
+    # training data: 10 M rows sampled evenly from the warm points of 10
+    # successive mixed-form states (1 M per state)
+    cap, gen_steps = 10_000_000, 10
+    per = cap // gen_steps
     X = torch.zeros((cap, 12), dtype=torch.float32, device="cuda")
     Y = torch.zeros((cap, 4), dtype=torch.float32, device="cuda")
     M = torch.zeros((cap, 4), dtype=torch.float32, device="cuda")
+    Xs = torch.zeros((npts, 12), dtype=torch.float32, device="cuda")
+    Ys = torch.zeros((npts, 4), dtype=torch.float32, device="cuda")
+    Ms = torch.zeros((npts, 4), dtype=torch.float32, device="cuda")
     have = 0
-    gen_steps = 0
-    while have < cap and gen_steps < 20:
-        rows = casim.casim_mlp_data(ctx, dom.state, ncols, nlev, dt, X[have:], Y[have:], M[have:], cap - have,
-                                    stream=stream)
-        have += min(rows, cap - have)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(17)
+    for _ in range(gen_steps):
+        rows = casim.casim_mlp_data(ctx, dom.state, ncols, nlev, dt, Xs, Ys, Ms, npts, stream=stream)
+        take = min(per, rows)
+        idx = torch.randperm(rows, device="cuda", generator=gen)[:take]
+        X[have:have + take], Y[have:have + take], M[have:have + take] = Xs[idx], Ys[idx], Ms[idx]
+        have += take
         casim.casim_step(ctx, dom.state, ncols, nlev, dt, stream)
-        gen_steps += 1
+    del Xs, Ys, Ms
     # held-out rows from the state after the training window
     Xh = torch.zeros((npts, 12), dtype=torch.float32, device="cuda")
     Yh = torch.zeros((npts, 4), dtype=torch.float32, device="cuda")

@@ -168,3 +168,70 @@ def test_training_reduces_loss_and_surrogate_step():
     finally:
         casim.casim_mlp_free(m)
         casim.casim_free(ctx)
+
+
+def test_what_the_trained_network_gains_over_the_scheme():
+    """The network is judged by the scheme it replaces.  Training buys
+    accuracy (held-out rate error far below an untrained network's); the
+    surrogate step then follows the plain step closely over many steps.  It
+    buys no speed: the scheme's closed-form rates cost a few MUFU operations
+    per point, the network ~2.7e5 FLOP, so the surrogate step is slower --
+    the measured ratio is reported, not asserted as a gain."""
+    import time
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED)
+    trained, untrained = casim.casim_mlp_create(seed=8), casim.casim_mlp_create(seed=8)
+    try:
+        # data from several successive states
+        ncols, nlev = 2048, 150
+        dz = synth.dz_stretched(nlev)
+        fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=61)
+        d = casim.Domain(fld, dz, ncols)
+        cap = ncols * nlev
+        Xs, Ys, Ms = (torch.zeros((cap, w), dtype=torch.float32, device="cuda") for w in (12, 4, 4))
+        parts = []
+        for _ in range(4):
+            rows = casim.casim_mlp_data(ctx, d.state, ncols, nlev, 1.0, Xs, Ys, Ms, cap)
+            parts.append((Xs[:rows].clone(), Ys[:rows].clone(), Ms[:rows].clone()))
+            casim.casim_step(ctx, d.state, ncols, nlev, 1.0)
+        X, Y, M = (torch.cat([p[i] for p in parts]) for i in range(3))
+        casim.casim_mlp_fit(trained, X, Y, M, X.shape[0], steps=1500, batch=4096, lr=1e-3, seed=2, history=False)
+        casim.casim_mlp_fit(untrained, X, Y, M, X.shape[0], steps=0, batch=4096, lr=1e-3, seed=2, history=False)
+        # held-out state: the one after the training window
+        rows = casim.casim_mlp_data(ctx, d.state, ncols, nlev, 1.0, Xs, Ys, Ms, cap)
+        xh, yh, mh = Xs[:rows].cpu().numpy(), Ys[:rows].cpu().numpy(), Ms[:rows].cpu().numpy()
+        st = casim.casim_mlp_get_norm(trained)
+        inbox = np.all((xh >= st[32:44]) & (xh <= st[44:56]), axis=1)
+        assert inbox.mean() > 0.9
+
+        def rel_err(net):
+            yp = casim.casim_mlp_forward_host(net, ((xh - st[:12]) / st[12:24]).astype(np.float32))
+            yp = yp * st[28:32] + st[24:28]
+            e = np.abs(np.expm1(yp - yh))[inbox] * mh[inbox]
+            return np.array([np.median(e[mh[inbox][:, j] > 0, j]) for j in range(4)])
+
+        et, eu = rel_err(trained), rel_err(untrained)
+        print("held-out median relative rate error: trained", et, "untrained", eu)
+        assert np.all(et < 0.15) and np.all(et < 0.1 * eu)
+        # 20 steps: surrogate vs plain from the same state, judged by the plain step
+        f2 = d.numpy()[0]
+        plain, surr = casim.Domain(f2, dz, ncols), casim.Domain(f2, dz, ncols)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(20):
+            casim.casim_step(ctx, plain.state, ncols, nlev, 1.0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(20):
+            casim.casim_step_surrogate(ctx, trained, surr.state, ncols, nlev, 1.0)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        assert casim.casim_get_error(ctx)[0] == 0
+        pp = plain.precip[:, :ncols].sum().item()
+        ps = surr.precip[:, :ncols].sum().item()
+        print("20-step precipitation: plain %.6e surrogate %.6e (rel %.2e); time per step plain %.3f ms, "
+              "surrogate %.3f ms" % (pp, ps, abs(ps - pp) / pp, (t1 - t0) * 50, (t2 - t1) * 50))
+        assert abs(ps - pp) <= 1e-2 * pp
+    finally:
+        casim.casim_mlp_free(trained)
+        casim.casim_mlp_free(untrained)
+        casim.casim_free(ctx)
