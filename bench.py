@@ -127,7 +127,7 @@ def bench_batch(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2010_14823_gb300 import shard
-    doms, dt = synth.batch_workload(64, seed=shard.rank_seed(1237, rank))
+    doms, dt = synth.batch_workload(64, seed=shard.rank_seed(1237, rank), scale=args.batch_scale)
     dev = [casim.Domain(f, dz, nc) for f, dz, nc, nl in doms]
     del doms
     npts = sum(d.ncols * d.nlev for d in dev)
@@ -212,14 +212,15 @@ def bench_surrogate(args, rank, world, local):
     casim.lib()
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    fld, dz, ncols, nlev, dt, _ = synth.workload("deep_512x512x150", seed=shard.rank_seed(1240, rank))
+    fld, dz, ncols, nlev, dt, _ = synth.workload("deep_512x512x150", ncols=args.ncols, seed=shard.rank_seed(1240, rank))
     npts = ncols * nlev
     ctx = casim.casim_init(precision=casim.CASIM_MIXED)
     m = casim.casim_mlp_create(seed=5)
     dom = casim.Domain(fld, dz, ncols)
     # training data: 10 M rows sampled evenly from the warm points of 10
     # successive mixed-form states (1 M per state)
-    cap, gen_steps = 10_000_000, 10
+    gen_steps = args.gen_steps
+    cap = min(10_000_000, gen_steps * npts)
     per = cap // gen_steps
     X = torch.zeros((cap, 12), dtype=torch.float32, device="cuda")
     Y = torch.zeros((cap, 4), dtype=torch.float32, device="cuda")
@@ -243,7 +244,7 @@ def bench_surrogate(args, rank, world, local):
     Yh = torch.zeros((npts, 4), dtype=torch.float32, device="cuda")
     Mh = torch.zeros((npts, 4), dtype=torch.float32, device="cuda")
     hold = casim.casim_mlp_data(ctx, dom.state, ncols, nlev, dt, Xh, Yh, Mh, npts, stream=stream)
-    train_steps, batch = 4000, 8192
+    train_steps, batch = args.train_steps, 8192
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     hist = casim.casim_mlp_fit(m, X, Y, M, have, train_steps, batch, 1e-3, seed=3, stream=stream, history=False)
@@ -264,7 +265,7 @@ def bench_surrogate(args, rank, world, local):
         v = rel[inbox & (ms[:, j] > 0), j]
         rate_err[name] = {"median": float(np.median(v)), "p99": float(np.percentile(v, 99)), "n": int(v.size)}
     # 100 steps: plain mixed vs surrogate from the same start, surface precipitation judged by the plain run
-    nsteps = 100
+    nsteps = args.surr_steps
     plain, surr = casim.Domain(fld, dz, ncols), casim.Domain(fld, dz, ncols)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -317,6 +318,10 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="batch64: scale of the column counts")
+    ap.add_argument("--surr-steps", type=int, default=100, help="surrogate: steps compared with the plain step")
+    ap.add_argument("--gen-steps", type=int, default=10, help="surrogate: states the training rows come from")
+    ap.add_argument("--train-steps", type=int, default=4000, help="surrogate: Adam steps")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
