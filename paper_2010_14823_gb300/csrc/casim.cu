@@ -742,6 +742,8 @@ struct casim_mlp {
   unsigned char *img = nullptr;   // weight images for the tcgen05 kernel
   unsigned *d_err = nullptr;
   int engine = 1;                 // 1: tcgen05 inference, 0: mma.sync
+  int umma_cluster = 1;           // CTAs per cluster of the tcgen05 kernel (shared weight stream)
+  int umma_max_clusters = 0;      // co-resident clusters of that size (persistent grid)
   float *norm = nullptr;   // [12 mean][12 sd][4 mean][4 sd]
   float *box = nullptr;    // [12 lo][12 hi]
   bool fitted = false;
@@ -855,10 +857,49 @@ static void mlp_cast(casim_mlp *m, cudaStream_t st) {
   k_mlp_images<<<(kNh * kNh + 255) / 256, 256, 0, st>>>(m->theta, m->img);
 }
 
+template <int C>
+static cudaError_t launch_umma_cluster(const UmmaArgs &u, int clusters, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(clusters * C));
+  cfg.blockDim = dim3(kUmmaThreads);
+  cfg.dynamicSmemBytes = kUmmaSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_mlp_umma<C>, u);
+}
+
+// co-resident clusters of C CTAs of the tcgen05 kernel (0: none fit)
+template <int C>
+static int umma_max_clusters() {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kUmmaThreads);
+  cfg.dynamicSmemBytes = kUmmaSmem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_mlp_umma<C>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 // forward pass of n rows of BF16 inputs on the tcgen05 kernel: rates at the
 // rows' points (rowpt) or standardised outputs in m->y (rowpt null)
-static void mlp_forward_umma(casim_mlp *m, const __nv_bfloat16 *xb, long long n, const long long *rowpt,
-                             float4 *surr, unsigned *err, int nsm, cudaStream_t st) {
+static cudaError_t mlp_forward_umma(casim_mlp *m, const __nv_bfloat16 *xb, long long n, const long long *rowpt,
+                                    float4 *surr, unsigned *err, int nsm, cudaStream_t st) {
   UmmaArgs u;
   u.xb = xb;
   u.rows = n;
@@ -870,8 +911,14 @@ static void mlp_forward_umma(casim_mlp *m, const __nv_bfloat16 *xb, long long n,
   u.y = m->y;
   u.err = err;
   const long long tiles = (n + 127) / 128;
+  if (tiles == 0) return cudaSuccess;
+  if (m->umma_cluster == 2) {
+    const int clusters = (int)std::min<long long>((tiles + 1) / 2, m->umma_max_clusters);
+    return launch_umma_cluster<2>(u, clusters, st);
+  }
   const int grid = (int)std::min<long long>(tiles, nsm);
-  if (grid > 0) k_mlp_umma<<<grid, 128, kUmmaSmem, st>>>(u);
+  k_mlp_umma<1><<<grid, kUmmaThreads, kUmmaSmem, st>>>(u);
+  return cudaGetLastError();
 }
 
 extern "C" void casim_mlp_free(casim_mlp *m) {
@@ -913,7 +960,16 @@ extern "C" int casim_mlp_create(casim_mlp **out, unsigned long long seed) {
   if (e == cudaSuccess) e = dalloc(&m->img, kImgBytes);
   if (e == cudaSuccess) e = dalloc(&m->d_err, 1);
   if (e == cudaSuccess) e = cudaMemset(m->d_err, 0, sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_umma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_umma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
+  if (e == cudaSuccess) {
+    // pairs of CTAs share the weight stream when enough pairs fit at once
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    m->umma_max_clusters = umma_max_clusters<2>();
+    m->umma_cluster = 2 * m->umma_max_clusters >= (nsm * 3) / 4 ? 2 : 1;
+  }
   if (e == cudaSuccess) e = cudaMemcpy(m->theta, th.data(), kNParam * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->m1, 0, kNParam * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->m2, 0, kNParam * sizeof(float));
@@ -970,7 +1026,7 @@ extern "C" int casim_mlp_forward_host(casim_mlp *m, const float *Xn, int n, floa
     int dev = 0, nsm = 1;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    mlp_forward_umma(m, m->h0, n, nullptr, nullptr, m->d_err, nsm, 0);
+    CUDA_TRY(mlp_forward_umma(m, m->h0, n, nullptr, nullptr, m->d_err, nsm, 0));
   } else {
     mlp_forward(m, n, false, 0);
   }
@@ -1156,7 +1212,7 @@ extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_st
   const long long rows = std::min((long long)hrows, m->cap_rows);
   // 2. the network on the rows
   if (m->engine == 1) {
-    mlp_forward_umma(m, m->xb, rows, m->rowpt, m->surr, ctx->d_err, ctx->nsm, st);
+    CUDA_TRY(mlp_forward_umma(m, m->xb, rows, m->rowpt, m->surr, ctx->d_err, ctx->nsm, st));
     ctx->launches++;
   } else {
     const int chunk = 1 << 17;

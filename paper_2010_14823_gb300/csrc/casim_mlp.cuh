@@ -473,11 +473,13 @@ namespace casim_dev {
 
 // Weight images in global memory, already in the swizzled shared-memory
 // layout, so that 1-D bulk copies land them ready for the tensor cores:
-//   W1: [256 rows][64] (k >= 12 zero)                         32 KB
-//   W2, W3: four chunks of 64 output rows x 256 k             4 x 32 KB each
-//   W4: [16 rows][256] (rows >= 4 zero)                        8 KB
-constexpr uint32_t kImgW1 = 256 * 128, kImgChunk = 64 * 4 * 128, kImgW4 = 16 * 4 * 128;
-constexpr uint32_t kImgBytes = kImgW1 + 8 * kImgChunk + kImgW4;
+//   W1: [256 rows][64] (k >= 12 zero)                                32 KB
+//   W2, W3: four chunks each, chunk s = all 256 output rows x k = 64s..64s+63
+//           (one K-slab)                                              32 KB each
+//   W4: [16 rows][256] (rows >= 4 zero)                               8 KB
+constexpr uint32_t kImgW1 = 256 * 128, kImgChunk = 256 * 128, kImgW4 = 16 * 4 * 128;
+constexpr int kImgChunks = 8;
+constexpr uint32_t kImgBytes = kImgW1 + kImgChunks * kImgChunk + kImgW4;
 
 __global__ void k_mlp_images(const float *theta, unsigned char *img) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -488,14 +490,14 @@ __global__ void k_mlp_images(const float *theta, unsigned char *img) {
         k < kNin ? __float2bfloat16(theta[kOffW1 + k * kNh + n]) : z;
   }
   if (i < 256 * 256) {  // W2, W3 (n, k)
-    const int n = i / 256, k = i % 256, q = n / 64, nn = n % 64;
-    const uint32_t off = q * kImgChunk + sw128_offset(64, nn, k);
+    const int n = i / 256, k = i % 256, s = k >> 6;
+    const uint32_t off = (uint32_t)s * kImgChunk + sw128_offset(256, n, k & 63);
     *reinterpret_cast<__nv_bfloat16 *>(img + kImgW1 + off) = __float2bfloat16(theta[kOffW2 + k * kNh + n]);
     *reinterpret_cast<__nv_bfloat16 *>(img + kImgW1 + 4 * kImgChunk + off) = __float2bfloat16(theta[kOffW3 + k * kNh + n]);
   }
   if (i < 16 * 256) {   // W4 (n, k)
     const int n = i / 256, k = i % 256;
-    *reinterpret_cast<__nv_bfloat16 *>(img + kImgW1 + 8 * kImgChunk + sw128_offset(16, n, k)) =
+    *reinterpret_cast<__nv_bfloat16 *>(img + kImgW1 + kImgChunks * kImgChunk + sw128_offset(16, n, k)) =
         n < kNout ? __float2bfloat16(theta[kOffW4 + k * kNout + n]) : z;
   }
 }
@@ -513,232 +515,284 @@ struct UmmaArgs {
 };
 
 constexpr unsigned kUmmaSpins = 1u << 22;
-constexpr int kUmmaSmem = 1024 + 65536 + kImgW1 + kImgW4 + 2 * kImgChunk;
+constexpr int kUmmaEpiWarps = 16;                       // 4 per TMEM lane quarter
+constexpr int kUmmaMmaWarp = kUmmaEpiWarps;             // issues the MMAs, owns TMEM
+constexpr int kUmmaProdWarp = kUmmaEpiWarps + 1;        // streams the weight chunks
+constexpr int kUmmaThreads = (kUmmaEpiWarps + 2) * 32;
+constexpr int kUmmaStages = 3;                          // weight-chunk ring
+// dynamic shared memory (1024-byte aligned): the activation tile X (128 rows
+// x 256 BF16, four K-slabs), resident W1 and W4, the chunk ring
+constexpr uint32_t kSmW1 = 65536, kSmW4 = kSmW1 + kImgW1, kSmRing = kSmW4 + kImgW4;
+constexpr int kUmmaSmem = 1024 + kSmRing + kUmmaStages * kImgChunk;
+static_assert(kUmmaSmem + 4096 <= 232448, "shared memory of the tensor-core kernel");
 
-// Persistent: one CTA (128 threads) per SM walks 128-row tiles.  Per tile:
-// layer 1 (one MMA, K = 16) -> TMEM -> bias, tanh, BF16 -> swizzled smem ->
-// layer 2 (four N-quarters of 16 MMAs, weights streamed) -> ... -> layer 4
-// (N = 16) -> rates at the rows' points.  Thread 0 issues the MMAs and the
-// weight copies; all four warps run the epilogues on their 32 TMEM lanes.
-__global__ void __launch_bounds__(128, 1) k_mlp_umma(const UmmaArgs u) {
+// Persistent, one CTA (18 warps) per SM, clusters of C CTAs, 128-row tiles.
+//
+// Tensor memory holds two 256-column FP32 accumulators used by alternate
+// layers (layer 1 -> A0, 2 -> A1, 3 -> A0, 4 -> A1), so the MMAs of layer
+// l+1 run while the epilogue of layer l still reads layer l's sums.  One
+// activation tile X suffices in shared memory: layer l's MMAs have all
+// completed (the accumulator commit) before its epilogue overwrites X slab by
+// slab, and layer l+1's MMAs on slab s wait for that slab:
+//  * epilogue warps (16): warp w reads TMEM lanes 32(w%4).. (its rows) and
+//    columns 16(w/4)..+15 of each 64-column slab; per slab s: bias, tanh,
+//    BF16 pack, swizzled store into slab s of X, then one arrival on act[s];
+//  * MMA warp (one thread): per slab s it waits act[s] and issues that
+//    K-slab's MMAs of the next layer (N = 256, weights from the ring);
+//    after the last slab it commits the accumulator to acc;
+//  * producer warp (one thread): streams the 8 weight chunks of layers 2-3
+//    per tile through the ring (full/free barriers).
+// The C CTAs of a cluster walk tile groups together (CTA r takes tile C*g+r
+// of group g; a tile past the end computes on zero rows and stores nothing),
+// so they consume the same chunk sequence: CTA r copies the chunks i with
+// i % C == r into the ring of every CTA of the cluster (multicast), and every
+// CTA's MMA thread commits each consumed chunk to the free barrier of every
+// CTA, so a stage is refilled only when all C CTAs are done with it.  Weight
+// traffic from L2 is 256 KB per C tiles.  N = 256 MMAs read each A slab once
+// (N = 128 halves would read it twice): shared-memory operand bandwidth, not
+// the tensor pipe, bounds these MMAs.
+// Every wait is bounded and gives up once any thread of the CTA has set the
+// abort flag; before the tensor memory is released and the CTA leaves, all
+// MMAs, copies and arrivals from or to this CTA have completed.
+template <int C>
+__global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) {
   extern __shared__ __align__(16) unsigned char sraw[];
   unsigned char *sm = sraw + ((1024 - (smem_addr(sraw) & 1023)) & 1023);
-  unsigned char *A = sm;                         // 4 slabs x 128 rows x 128 B
-  unsigned char *W1 = A + 65536;
-  unsigned char *W4 = W1 + kImgW1;
-  unsigned char *WB = W4 + kImgW4;               // two chunk buffers
   __shared__ float s_bias[3 * kNh + kNout];
   __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) unsigned long long s_bar[6];   // 0 weights, 1 mma, 2-3 full, 4-5 free
+  __shared__ __align__(8) unsigned long long s_bar[24];
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long ntiles = (u.rows + 127) / 128;
+  const long long ngroups = (ntiles + C - 1) / C;
+  const int rank = C > 1 ? (int)cluster_ctarank() : 0;
+  const long long cluster = blockIdx.x / C, nclusters = gridDim.x / C;
+  const long long my_groups = cluster < ngroups ? (ngroups - 1 - cluster) / nclusters + 1 : 0;
+  const uint16_t all = (uint16_t)((1u << C) - 1u);
+  const uint32_t sb = smem_addr(sm);
+  volatile int *abort = &s_abort;
+  enum { B_W = 0, B_FEAT = 1, B_ACC = 2, B_ACT = 3, B_FULL = 7, B_FREE = 7 + kUmmaStages, B_DRAIN = 7 + 2 * kUmmaStages };
+  const uint32_t bar0 = smem_addr(&s_bar[0]);
+  auto bar = [&](int i) { return bar0 + 8u * (uint32_t)i; };
+  auto fail = [&]() {
+    *abort = 1;
+    atomicOr(u.err, 4u);
+  };
 
-  for (int i = tid; i < kNh; i += 128) {
+  for (int i = tid; i < kNh; i += kUmmaThreads) {
     s_bias[i] = u.theta[kOffB1 + i];
     s_bias[kNh + i] = u.theta[kOffB2 + i];
     s_bias[2 * kNh + i] = u.theta[kOffB3 + i];
   }
   if (tid < kNout) s_bias[3 * kNh + tid] = u.theta[kOffB4 + tid];
-  if (warp == 0) {
-    tmem_alloc(smem_addr(&s_tmem), 256);
+  if (warp == kUmmaMmaWarp) {
+    tmem_alloc(smem_addr(&s_tmem), 512);
     tmem_relinquish();
   }
-  const uint32_t bw = smem_addr(&s_bar[0]), bm = smem_addr(&s_bar[1]);
-  const uint32_t bfull[2] = {smem_addr(&s_bar[2]), smem_addr(&s_bar[3])};
-  const uint32_t bfree[2] = {smem_addr(&s_bar[4]), smem_addr(&s_bar[5])};
   if (tid == 0) {
-    for (int i = 0; i < 6; ++i) bar_init(smem_addr(&s_bar[i]), 1);
+    bar_init(bar(B_W), 1);
+    bar_init(bar(B_FEAT), kUmmaEpiWarps);
+    bar_init(bar(B_ACC), 1);
+    for (int s = 0; s < 4; ++s) bar_init(bar(B_ACT + s), kUmmaEpiWarps);
+    for (int s = 0; s < kUmmaStages; ++s) {
+      bar_init(bar(B_FULL + s), 1);
+      bar_init(bar(B_FREE + s), C);
+    }
+    bar_init(bar(B_DRAIN), 1);
     bar_fence_init();
     s_abort = 0;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // the peers' barriers exist before any copy or commit reaches them
+  if constexpr (C > 1) cluster_sync_all();
   const uint32_t taddr = s_tmem;
-  const uint32_t trow = taddr + ((uint32_t)(32 * warp) << 16);
 
-  // resident weights of layers 1 and 4, and the first streamed chunk
-  const long long nchunks = ntiles * 8;
-  const long long my_chunks = ((long long)blockIdx.x < ntiles) ? ((ntiles - 1 - blockIdx.x) / gridDim.x + 1) * 8 : 0;
-  int nload[2] = {0, 0}, ncommit[2] = {0, 0};
-  auto chunk_src = [&](long long g) {   // g-th chunk of this CTA: tile-local index g % 8
-    const int c = (int)(g % 8);
-    return u.img + kImgW1 + (uint32_t)c * kImgChunk;   // chunks 0..3 layer 2, 4..7 layer 3
-  };
-  if (tid == 0) {
-    bar_expect_tx(bw, kImgW1 + kImgW4);
-    bulk_load(smem_addr(W1), u.img, kImgW1, bw);
-    bulk_load(smem_addr(W4), u.img + kImgW1 + 8 * kImgChunk, kImgW4, bw);
-    if (my_chunks > 0) {
-      bar_expect_tx(bfull[0], kImgChunk);
-      bulk_load(smem_addr(WB), chunk_src(0), kImgChunk, bfull[0]);
-      nload[0] = 1;
+  if (warp == kUmmaProdWarp) {
+    if (lane == 0) {
+      bar_expect_tx(bar(B_W), kImgW1 + kImgW4);
+      bulk_load(sb + kSmW1, u.img, kImgW1, bar(B_W));
+      bulk_load(sb + kSmW4, u.img + kImgW1 + kImgChunks * kImgChunk, kImgW4, bar(B_W));
+      // load i goes to stage i % S as that stage's (i / S)-th fill; from the
+      // second fill on it waits until all C CTAs' MMAs of the previous fill
+      // have completed
+      const long long nch = my_groups * kImgChunks;
+      long long i = 0;
+      for (; i < nch; ++i) {
+        const int st = (int)(i % kUmmaStages);
+        const long long fill = i / kUmmaStages;
+        if (fill > 0 && !bar_wait_or_abort(bar(B_FREE + st), (uint32_t)((fill - 1) & 1), kUmmaSpins, abort)) {
+          fail();
+          break;
+        }
+        bar_expect_tx(bar(B_FULL + st), kImgChunk);
+        const uint32_t dst = sb + kSmRing + (uint32_t)st * kImgChunk;
+        const unsigned char *src = u.img + kImgW1 + (uint32_t)(i % kImgChunks) * kImgChunk;
+        if constexpr (C > 1) {
+          if ((int)(i % C) == rank) bulk_load_multicast(dst, src, kImgChunk, bar(B_FULL + st), all);
+        } else {
+          bulk_load(dst, src, kImgChunk, bar(B_FULL + st));
+        }
+      }
+      // drain: the copies into this CTA have landed (last fill of each
+      // stage), and so have all C CTAs' commits of those fills
+      bar_wait(bar(B_W), 0, kUmmaSpins);
+      for (int st = 0; st < kUmmaStages && st < i; ++st) {
+        const long long fills = (i - st + kUmmaStages - 1) / kUmmaStages;
+        bar_wait(bar(B_FULL + st), (uint32_t)((fills - 1) & 1), kUmmaSpins);
+        bar_wait_or_abort(bar(B_FREE + st), (uint32_t)((fills - 1) & 1), kUmmaSpins, abort);
+      }
     }
-    if (!bar_wait(bw, 0, kUmmaSpins)) { s_abort = 1; atomicOr(u.err, 4u); }
-  }
-  (void)nchunks;
-  __syncthreads();
-  int mma_phase = 0;
-  long long g = 0;   // chunks consumed by this CTA
-  const uint32_t id256 = umma_idesc_bf16(128, 256), id64 = umma_idesc_bf16(128, 64), id16 = umma_idesc_bf16(128, 16);
-
-  // epilogue of a hidden layer: TMEM row -> bias, tanh -> BF16 -> A (swizzled)
-  auto hidden_epilogue = [&](const float *bias) {
-    const int r = tid;
+    __syncwarp();
+  } else if (warp == kUmmaMmaWarp) {
+    if (lane == 0) {
+      const uint32_t id256 = umma_idesc_bf16(128, 256), id16 = umma_idesc_bf16(128, 16);
+      bool ok = bar_wait_or_abort(bar(B_W), 0, kUmmaSpins, abort);
+      int nfeat = 0, nact = 0;
+      long long chunk = 0;
+      for (long long it = 0; ok && it < my_groups; ++it) {
+        ok = bar_wait_or_abort(bar(B_FEAT), (uint32_t)(nfeat++ & 1), kUmmaSpins, abort);
+        if (!ok) break;
+        tc_fence_after();
+        // layer 1: features (X slab 0, k < 16) x W1 -> A0
+        umma_bf16(taddr, umma_desc_sw128(sb), umma_desc_sw128(sb + kSmW1), id256, 0u);
+        umma_commit(bar(B_ACC));
+        // layers 2 (-> A1) and 3 (-> A0), K-slab by K-slab
+        for (int l = 0; ok && l < 2; ++l, ++nact) {
+          const uint32_t dacc = taddr + (l == 0 ? 256u : 0u);
+          for (int s = 0; ok && s < 4; ++s) {
+            ok = bar_wait_or_abort(bar(B_ACT + s), (uint32_t)(nact & 1), kUmmaSpins, abort);
+            if (!ok) break;
+            tc_fence_after();
+            const int st = (int)(chunk % kUmmaStages);
+            ok = bar_wait_or_abort(bar(B_FULL + st), (uint32_t)((chunk / kUmmaStages) & 1), kUmmaSpins, abort);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t wst = sb + kSmRing + (uint32_t)st * kImgChunk;
+#pragma unroll
+            for (int sub = 0; sub < 4; ++sub)
+              umma_bf16(dacc, umma_desc_sw128(sb + 16384u * (uint32_t)s + 32u * (uint32_t)sub),
+                        umma_desc_sw128(wst + 32u * (uint32_t)sub), id256, (s | sub) ? 1u : 0u);
+            if constexpr (C > 1) umma_commit_multicast(bar(B_FREE + st), all);
+            else umma_commit(bar(B_FREE + st));
+            ++chunk;
+          }
+          if (ok) umma_commit(bar(B_ACC));
+        }
+        // layer 4: X x W4 -> A1 columns 0..15
+        for (int s = 0; ok && s < 4; ++s) {
+          ok = bar_wait_or_abort(bar(B_ACT + s), (uint32_t)(nact & 1), kUmmaSpins, abort);
+          if (!ok) break;
+          tc_fence_after();
+#pragma unroll
+          for (int sub = 0; sub < 4; ++sub)
+            umma_bf16(taddr + 256u, umma_desc_sw128(sb + 16384u * (uint32_t)s + 32u * (uint32_t)sub),
+                      umma_desc_sw128(sb + kSmW4 + 2048u * (uint32_t)s + 32u * (uint32_t)sub), id16,
+                      (s | sub) ? 1u : 0u);
+        }
+        ++nact;
+        if (ok) umma_commit(bar(B_ACC));
+      }
+      if (!ok) fail();
+      // drain: every MMA this thread issued has completed
+      umma_commit(bar(B_DRAIN));
+      bar_wait(bar(B_DRAIN), 0, kUmmaSpins);
+    }
+    __syncwarp();
+  } else {
+    // epilogue warps
+    const int q = warp & 3, j = warp >> 2;
+    const int row = 32 * q + lane;
+    const uint32_t tl = taddr + ((uint32_t)(32 * q) << 16);
+    const int sw = row & 7;
+    int nacc = 0;
+    bool ok = true;
+    uint4 f0 = make_uint4(0, 0, 0, 0), f1 = f0;
+    auto load_features = [&](long long g) {
+      f0 = make_uint4(0, 0, 0, 0);
+      f1 = f0;
+      const long long r = (g * C + rank) * 128 + row;
+      if (g < ngroups && r < u.rows) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(u.xb + r * kNinPad);
+        f0 = src[0];
+        f1 = src[1];
+      }
+    };
+    if (j == 0) load_features(cluster);
+    for (long long g = cluster; ok && g < ngroups; g += nclusters) {
+      const long long r0 = (g * C + rank) * 128;
+      // every epilogue warp arrives: the next tile's layer-1 MMA (which
+      // overwrites A0) waits until all of them have seen the previous
+      // tile's last accumulator phase
+      if (j == 0) {
+        unsigned char *rp = sm + row * 128;
+        *reinterpret_cast<uint4 *>(rp + ((0 ^ sw) << 4)) = f0;
+        *reinterpret_cast<uint4 *>(rp + ((1 ^ sw) << 4)) = f1;
+        fence_async_smem();
+      }
+      __syncwarp();
+      if (lane == 0) bar_arrive(bar(B_FEAT));
+      if (j == 0) load_features(g + nclusters);
+      for (int l = 0; l < 3; ++l) {
+        ok = bar_wait_or_abort(bar(B_ACC), (uint32_t)(nacc++ & 1), kUmmaSpins, abort);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t tacc = tl + (l == 1 ? 256u : 0u);
+        unsigned char *xo = sm + row * 128;
+        const float *b = s_bias + l * kNh;
 #pragma unroll 1
-    for (int c = 0; c < kNh; c += 32) {
-      float v[32];
-      tmem_ld32(trow + c, v);
-      __align__(16) __nv_bfloat16 hb[32];
+        for (int s = 0; s < 4; ++s) {
+          const int c0 = 64 * s + 16 * j;
+          float v[16];
+          tmem_ld16(tacc + (uint32_t)c0, v);
+          uint32_t hb[8];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) hb[i] = __float2bfloat16(tanh_approx(v[i] + bias[c + i]));
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int k = c + 8 * j;
-        *reinterpret_cast<uint4 *>(A + sw128_offset(128, r, k)) = reinterpret_cast<const uint4 *>(hb)[j];
+          for (int i = 0; i < 8; ++i) {
+            const __nv_bfloat162 p = __floats2bfloat162_rn(tanh_approx(v[2 * i] + b[c0 + 2 * i]),
+                                                          tanh_approx(v[2 * i + 1] + b[c0 + 2 * i + 1]));
+            hb[i] = *reinterpret_cast<const uint32_t *>(&p);
+          }
+          unsigned char *sp = xo + 16384 * s;
+          *reinterpret_cast<uint4 *>(sp + (((2 * j) ^ sw) << 4)) = make_uint4(hb[0], hb[1], hb[2], hb[3]);
+          *reinterpret_cast<uint4 *>(sp + (((2 * j + 1) ^ sw) << 4)) = make_uint4(hb[4], hb[5], hb[6], hb[7]);
+          fence_async_smem();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) bar_arrive(bar(B_ACT + s));
+        }
       }
-    }
-  };
-  auto sync_for_mma = [&]() {   // smem writes and TMEM reads done before the next MMAs
-    tc_fence_before();
-    fence_async_smem();
-    __syncthreads();
-    tc_fence_after();
-  };
-  auto wait_mma = [&]() {
-    if (!bar_wait(bm, (uint32_t)(mma_phase & 1), kUmmaSpins)) {
-      s_abort = 1;
-      atomicOr(u.err, 4u);
-    }
-    ++mma_phase;
-    tc_fence_after();
-  };
-  // one streamed layer: 4 chunks of 16 MMAs (N = 64) from the chunk buffers
-  auto streamed_layer = [&]() {
-    for (int q = 0; q < 4; ++q, ++g) {
-      const int b = (int)(g & 1);
-      if (!bar_wait(bfull[b], (uint32_t)((nload[b] - 1) & 1), kUmmaSpins)) {
-        s_abort = 1;
-        atomicOr(u.err, 4u);
-        return;
-      }
+      if (!ok) break;
+      ok = bar_wait_or_abort(bar(B_ACC), (uint32_t)(nacc++ & 1), kUmmaSpins, abort);
+      if (!ok) break;
       tc_fence_after();
-      unsigned char *Wc = WB + b * kImgChunk;
-#pragma unroll 1
-      for (int s = 0; s < 16; ++s) {
-        const int slab = s >> 2, sub = s & 3;
-        const uint64_t ad = umma_desc_sw128(smem_addr(A) + slab * 16384 + sub * 32);
-        const uint64_t bd = umma_desc_sw128(smem_addr(Wc) + slab * 8192 + sub * 32);
-        umma_bf16(taddr + q * 64, ad, bd, id64, s > 0 ? 1u : 0u);
-      }
-      umma_commit(bfree[b]);
-      ++ncommit[b];
-      // refill the other buffer once its previous chunk's MMAs are done
-      const long long nxt = g + 1;
-      if (nxt < my_chunks) {
-        const int b2 = (int)(nxt & 1);
-        if (nload[b2] > 0) {
-          if (!bar_wait(bfree[b2], (uint32_t)((ncommit[b2] - 1) & 1), kUmmaSpins)) {
-            s_abort = 1;
-            atomicOr(u.err, 4u);
-            return;
+      if (j == 0) {
+        float v[16];
+        tmem_ld16(tl + 256u, v);
+        tc_fence_before();
+        if (r0 + row < u.rows) {
+          float y[kNout];
+#pragma unroll
+          for (int i = 0; i < kNout; ++i) y[i] = v[i] + s_bias[3 * kNh + i];
+          if (u.rowpt) {
+            const float *muy = u.norm + 2 * kNin, *sdy = u.norm + 2 * kNin + kNout;
+            u.surr[u.rowpt[r0 + row]] = make_float4(__expf(y[0] * sdy[0] + muy[0]), __expf(y[1] * sdy[1] + muy[1]),
+                                                    __expf(y[2] * sdy[2] + muy[2]), __expf(y[3] * sdy[3] + muy[3]));
+          } else {
+#pragma unroll
+            for (int i = 0; i < kNout; ++i) u.y[(r0 + row) * kNout + i] = y[i];
           }
         }
-        bar_expect_tx(bfull[b2], kImgChunk);
-        bulk_load(smem_addr(WB + b2 * kImgChunk), chunk_src(nxt), kImgChunk, bfull[b2]);
-        ++nload[b2];
       }
     }
-  };
-
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    if (s_abort) break;
-    const long long r0 = t * 128;
-    const int nrow = (int)min(128LL, u.rows - r0);
-    // features -> A slab 0, chunks 0 and 1 of each row
-    {
-      const int r = tid;
-      uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
-      if (r < nrow) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(u.xb + (r0 + r) * kNinPad);
-        v0 = src[0];
-        v1 = src[1];
-      }
-      *reinterpret_cast<uint4 *>(A + sw128_offset(128, r, 0)) = v0;
-      *reinterpret_cast<uint4 *>(A + sw128_offset(128, r, 8)) = v1;
-    }
-    sync_for_mma();
-    if (tid == 0) {
-      umma_bf16(taddr, umma_desc_sw128(smem_addr(A)), umma_desc_sw128(smem_addr(W1)), id256, 0u);
-      umma_commit(bm);
-    }
-    wait_mma();
-    hidden_epilogue(s_bias);
-    sync_for_mma();
-    if (s_abort) break;
-    if (tid == 0) {
-      streamed_layer();
-      umma_commit(bm);
-    }
-    wait_mma();
-    hidden_epilogue(s_bias + kNh);
-    sync_for_mma();
-    if (s_abort) break;
-    if (tid == 0) {
-      streamed_layer();
-      umma_commit(bm);
-    }
-    wait_mma();
-    hidden_epilogue(s_bias + 2 * kNh);
-    sync_for_mma();
-    if (s_abort) break;
-    if (tid == 0) {
-#pragma unroll 1
-      for (int s = 0; s < 16; ++s) {
-        const int slab = s >> 2, sub = s & 3;
-        const uint64_t ad = umma_desc_sw128(smem_addr(A) + slab * 16384 + sub * 32);
-        const uint64_t bd = umma_desc_sw128(smem_addr(W4) + slab * 2048 + sub * 32);
-        umma_bf16(taddr, ad, bd, id16, s > 0 ? 1u : 0u);
-      }
-      umma_commit(bm);
-    }
-    wait_mma();
-    {
-      float v[32];
-      tmem_ld32(trow, v);
-      const int r = tid;
-      if (r < nrow) {
-        float y[kNout];
-#pragma unroll
-        for (int j = 0; j < kNout; ++j) y[j] = v[j] + s_bias[3 * kNh + j];
-        if (u.rowpt) {
-          const float *muy = u.norm + 2 * kNin, *sdy = u.norm + 2 * kNin + kNout;
-          u.surr[u.rowpt[r0 + r]] = make_float4(__expf(y[0] * sdy[0] + muy[0]), __expf(y[1] * sdy[1] + muy[1]),
-                                                __expf(y[2] * sdy[2] + muy[2]), __expf(y[3] * sdy[3] + muy[3]));
-        } else {
-#pragma unroll
-          for (int j = 0; j < kNout; ++j) u.y[(r0 + r) * kNout + j] = y[j];
-        }
-      }
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-  }
-  // drain: every tcgen05 operation and bulk copy of this CTA has completed
-  // (bounded waits) before the tensor memory is released
-  __syncthreads();
-  if (tid == 0) {
-    umma_commit(bm);
-    bar_wait(bm, (uint32_t)(mma_phase & 1), kUmmaSpins);
-    for (int b = 0; b < 2; ++b)
-      if (nload[b] > 0) bar_wait(bfull[b], (uint32_t)((nload[b] - 1) & 1), kUmmaSpins);
+    if (!ok) fail();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(taddr, 256);
+  if (warp == kUmmaMmaWarp) tmem_dealloc(taddr, 512);
+  // no CTA leaves while a peer may still copy or arrive into it
+  if constexpr (C > 1) cluster_sync_all();
 }
 
 }  // namespace casim_dev
