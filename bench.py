@@ -306,6 +306,56 @@ def bench_surrogate(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+FIELD_NAMES = ("T", "qv", "qc", "qr", "qi", "qs", "qg", "nc", "nr", "ni", "ns", "ng", "na")
+
+
+def mixed_vs_fp64(casim, torch, fld0, dz, ncols, nlev, dt, nsteps, stream):
+    """The mixed form against the FP64 form on the GPU, both advanced nsteps
+    from the same state: per prognostic field the largest and rms absolute
+    difference, and the largest and rms relative difference over points where
+    the FP64 value exceeds a floor (1e-12 kg/kg for masses, 1 /kg for
+    numbers); per form the drift of total water (vapour + condensate in the
+    air + accumulated surface precipitation) per step, relative."""
+    doms, drift = {}, {}
+    for name, prec in (("mixed", casim.CASIM_MIXED), ("fp64", casim.CASIM_FP64)):
+        ctx = casim.casim_init(precision=prec)
+        d = casim.Domain(fld0, dz, ncols)
+        bud = torch.zeros((2, ncols), dtype=torch.float64, device=d.fld.device)
+        casim.casim_budget(ctx, d.state, ncols, nlev, bud, stream)
+        w0 = float(bud[0].sum().item())
+        for _ in range(nsteps):
+            casim.casim_step(ctx, d.state, ncols, nlev, dt, stream)
+        casim.casim_budget(ctx, d.state, ncols, nlev, bud, stream)
+        rc, fl = casim.casim_get_error(ctx, stream)
+        assert rc == 0, (rc, fl)
+        w1 = float(bud[0].sum().item()) + float(d.precip[:, :ncols].sum().item())
+        drift[name] = abs(w1 - w0) / w0 / nsteps
+        casim.casim_free(ctx)
+        doms[name] = d
+    a, b = doms["mixed"].fld[:13, :, :ncols], doms["fp64"].fld[:13, :, :ncols]
+    out = {"steps": nsteps, "water_drift_per_step": drift, "fields": {}}
+    for f, name in enumerate(FIELD_NAMES):
+        diff = (a[f] - b[f]).abs()
+        rec = {"max_abs": float(diff.max().item()), "rms_abs": float(diff.square().mean().sqrt().item())}
+        # floors: any amount, and a significant amount (1e-6 kg/kg, 1e3 /kg)
+        floors = (0.0, 0.0) if name == "T" else ((1.0, 1e3) if name[0] == "n" else (1e-12, 1e-6))
+        for tag, floor in zip(("", "_significant"), floors):
+            sel = b[f].abs() > floor
+            rel = diff[sel] / b[f].abs()[sel]
+            rec["max_rel" + tag] = float(rel.max().item()) if rel.numel() else 0.0
+            rec["rms_rel" + tag] = float(rel.square().mean().sqrt().item()) if rel.numel() else 0.0
+        if name[0] == "q" and name != "qv":
+            # presence decisions (q > q_min) taken differently by the two forms
+            rec["presence_flips"] = int(((a[f] > 1e-14) != (b[f] > 1e-14)).sum().item())
+        out["fields"][name] = rec
+    pa, pb = doms["mixed"].precip[:, :ncols].sum(0), doms["fp64"].precip[:, :ncols].sum(0)
+    wet = pb > 1e-6 * float(pb.max().item())
+    out["precip_column_max_rel"] = float(((pa - pb).abs()[wet] / pb[wet]).max().item()) if wet.any() else 0.0
+    del doms
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,6 +368,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--acc-steps", type=int, default=100,
+                    help="steps of the mixed-vs-FP64 accuracy comparison (0: skip)")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="batch64: scale of the column counts")
     ap.add_argument("--surr-steps", type=int, default=100, help="surrogate: steps compared with the plain step")
     ap.add_argument("--gen-steps", type=int, default=10, help="surrogate: states the training rows come from")
@@ -463,6 +515,10 @@ def main():
                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
                "path": "casim_step_host: pinned host state, H2D + step + D2H per step"}
 
+    accuracy = None
+    if args.acc_steps > 0 and {"mixed", "fp64"} <= forms:
+        accuracy = mixed_vs_fp64(casim, torch, fld0, dz, ncols, nlev, dt, args.acc_steps, stream)
+
     peaks = _peaks()
     peak = peaks.get("hbm_gbs")
     alg_bytes = 128.0 * npts + 104.0 * changed
@@ -486,6 +542,8 @@ def main():
         if fp64_value is not None:
             cfg.update({"fp64_value": fp64_value, "fp64_ms_per_step": fp_ms / args.fp64_steps,
                         "speedup_mixed_vs_fp64": value / fp64_value})
+        if accuracy is not None:
+            cfg["mixed_vs_fp64"] = accuracy
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": mix_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,

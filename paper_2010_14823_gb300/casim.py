@@ -293,12 +293,18 @@ def casim_batch_free(batch):
 class Domain:
     """A domain's device state as torch tensors, in the layout of include/casim.h."""
 
-    def __init__(self, fld: np.ndarray, dz: np.ndarray, ncols: int, device="cuda"):
+    def __init__(self, fld, dz: np.ndarray, ncols: int, device="cuda"):
+        """fld: host array [16][nlev][pitch] (copied to the device) or a device
+        tensor of that shape (cloned)."""
         import torch
         nf, nlev, pitch = fld.shape
         assert nf == NFIELDS and pitch % 32 == 0 and pitch >= ncols
         self.ncols, self.nlev, self.pitch = ncols, nlev, pitch
-        self.fld = torch.from_numpy(np.ascontiguousarray(fld)).to(device)
+        if isinstance(fld, torch.Tensor):
+            assert fld.dtype == torch.float64
+            self.fld = fld.detach().clone().contiguous()
+        else:
+            self.fld = torch.from_numpy(np.ascontiguousarray(fld)).to(device)
         assert self.fld.data_ptr() % 256 == 0
         self.dz = torch.from_numpy(np.ascontiguousarray(dz, dtype=np.float64)).to(device)
         self.precip = torch.zeros((NPRECIP, pitch), dtype=torch.float64, device=device)

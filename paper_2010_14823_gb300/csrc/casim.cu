@@ -740,6 +740,7 @@ struct casim_mlp {
   MlpBf16 wb{};
   __nv_bfloat16 *wbuf = nullptr;
   unsigned char *img = nullptr;   // weight images for the tcgen05 kernel
+  float *wsplit = nullptr;        // split-K partial weight gradients [kSplitMax][256][256]
   unsigned *d_err = nullptr;
   int engine = 1;                 // 1: tcgen05 inference, 0: mma.sync
   int umma_cluster = 1;           // CTAs per cluster of the tcgen05 kernel (shared weight stream)
@@ -812,9 +813,23 @@ static int mlp_batch_ws(casim_mlp *m, int n) {
 template <class Epi>
 static void gemm(const __nv_bfloat16 *A, long long sam, long long sak, const __nv_bfloat16 *B, long long sbn,
                  long long sbk, int M, int N, int K, const Epi &epi, cudaStream_t st) {
-  GemmArgs g{A, sam, sak, B, sbn, sbk, M, N, K};
+  GemmArgs g{A, sam, sak, B, sbn, sbk, M, N, K, K};
   const dim3 grid((N + kGBN - 1) / kGBN, (M + kGBM - 1) / kGBM);
   k_gemm<Epi><<<grid, 128, 0, st>>>(g, epi);
+}
+
+// weight gradient out[m][n] (ld N) = sum_k A(m, k) B(n, k) over a long K (the
+// batch): K split into chunks of kSplitK rows, partial tiles summed in order
+constexpr int kSplitK = 512, kSplitMax = 64;
+static void gemm_wgrad(casim_mlp *m, const __nv_bfloat16 *A, long long sam, long long sak, const __nv_bfloat16 *B,
+                       long long sbn, long long sbk, int M, int N, int K, float *out, cudaStream_t st) {
+  const int kchunk = std::max(kSplitK, (K + kSplitMax - 1) / kSplitMax + kGBK - 1) / kGBK * kGBK;
+  const int nsplit = (K + kchunk - 1) / kchunk;
+  GemmArgs g{A, sam, sak, B, sbn, sbk, M, N, K, kchunk};
+  const dim3 grid((N + kGBN - 1) / kGBN, (M + kGBM - 1) / kGBM, nsplit);
+  const long long len = (long long)M * N;
+  k_gemm<EpiPartial><<<grid, 128, 0, st>>>(g, EpiPartial{m->wsplit, N, len});
+  k_splitk_sum<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(m->wsplit, nsplit, len, out);
 }
 
 // forward pass of n rows whose BF16 inputs are in m->h0; keep_act stores the
@@ -834,22 +849,22 @@ static void mlp_backward(casim_mlp *m, int n, cudaStream_t st) {
   k_sum<<<64, 256, 0, st>>>(m->Mb, (long long)n * kNout, m->cnt);
   const long long tot = (long long)n * kNoutPad;
   k_mlp_loss<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m->y, m->Tn, m->Mb, n, m->cnt, m->loss, m->dz4, m->dzb4);
-  const dim3 cs(32, 8);
+  const dim3 cs(32, kColsumY);
   // layer 4
-  gemm(m->h3, 1, kNh, m->dzb4, 1, kNoutPad, kNh, kNout, n, EpiStore{m->grad + kOffW4, kNout}, st);
+  gemm_wgrad(m, m->h3, 1, kNh, m->dzb4, 1, kNoutPad, kNh, kNout, n, m->grad + kOffW4, st);
   k_colsum<<<1, cs, 0, st>>>(m->dz4, n, kNout, kNout, m->grad + kOffB4);
   gemm(m->dzb4, kNoutPad, 1, m->wb.w4k, kNoutPad, 1, n, kNh, kNoutPad, EpiBackTanh{m->a3, m->dz3, m->dzb3, kNh}, st);
   // layer 3
-  gemm(m->h2, 1, kNh, m->dzb3, 1, kNh, kNh, kNh, n, EpiStore{m->grad + kOffW3, kNh}, st);
-  k_colsum<<<kNh / 8, cs, 0, st>>>(m->dz3, n, kNh, kNh, m->grad + kOffB3);
+  gemm_wgrad(m, m->h2, 1, kNh, m->dzb3, 1, kNh, kNh, kNh, n, m->grad + kOffW3, st);
+  k_colsum<<<kNh / 32, cs, 0, st>>>(m->dz3, n, kNh, kNh, m->grad + kOffB3);
   gemm(m->dzb3, kNh, 1, m->wb.w3k, kNh, 1, n, kNh, kNh, EpiBackTanh{m->a2, m->dz2, m->dzb2, kNh}, st);
   // layer 2
-  gemm(m->h1, 1, kNh, m->dzb2, 1, kNh, kNh, kNh, n, EpiStore{m->grad + kOffW2, kNh}, st);
-  k_colsum<<<kNh / 8, cs, 0, st>>>(m->dz2, n, kNh, kNh, m->grad + kOffB2);
+  gemm_wgrad(m, m->h1, 1, kNh, m->dzb2, 1, kNh, kNh, kNh, n, m->grad + kOffW2, st);
+  k_colsum<<<kNh / 32, cs, 0, st>>>(m->dz2, n, kNh, kNh, m->grad + kOffB2);
   gemm(m->dzb2, kNh, 1, m->wb.w2k, kNh, 1, n, kNh, kNh, EpiBackTanh{m->a1, m->dz1, m->dzb1, kNh}, st);
   // layer 1
-  gemm(m->h0, 1, kNinPad, m->dzb1, 1, kNh, kNin, kNh, n, EpiStore{m->grad + kOffW1, kNh}, st);
-  k_colsum<<<kNh / 8, cs, 0, st>>>(m->dz1, n, kNh, kNh, m->grad + kOffB1);
+  gemm_wgrad(m, m->h0, 1, kNinPad, m->dzb1, 1, kNh, kNin, kNh, n, m->grad + kOffW1, st);
+  k_colsum<<<kNh / 32, cs, 0, st>>>(m->dz1, n, kNh, kNh, m->grad + kOffB1);
 }
 
 static void mlp_cast(casim_mlp *m, cudaStream_t st) {
@@ -926,7 +941,7 @@ extern "C" void casim_mlp_free(casim_mlp *m) {
   cudaDeviceSynchronize();
   mlp_free_batch(m);
   void *ps[] = {m->theta, m->grad, m->m1, m->m2, m->wbuf, m->norm, m->box, m->cnt, m->loss,
-                m->xb, m->rowpt, m->surr, m->rowctr, m->img, m->d_err};
+                m->xb, m->rowpt, m->surr, m->rowctr, m->img, m->wsplit, m->d_err};
   for (void *p : ps) cudaFree(p);
   delete m;
 }
@@ -958,6 +973,7 @@ extern "C" int casim_mlp_create(casim_mlp **out, unsigned long long seed) {
   if (e == cudaSuccess) e = dalloc(&m->loss, 1);
   if (e == cudaSuccess) e = dalloc(&m->rowctr, 1);
   if (e == cudaSuccess) e = dalloc(&m->img, kImgBytes);
+  if (e == cudaSuccess) e = dalloc(&m->wsplit, (size_t)kSplitMax * kNh * kNh);
   if (e == cudaSuccess) e = dalloc(&m->d_err, 1);
   if (e == cudaSuccess) e = cudaMemset(m->d_err, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_umma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);

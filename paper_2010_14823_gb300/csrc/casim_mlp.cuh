@@ -32,6 +32,7 @@ struct GemmArgs {
   const __nv_bfloat16 *B;
   long long sbn, sbk;
   int M, N, K;
+  int kchunk;            // split K: block z sums k in [z kchunk, (z+1) kchunk)
 };
 
 constexpr int kGBM = 64, kGBN = 64, kGBK = 32, kGPad = 8;
@@ -60,15 +61,21 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g, const Epi epi) {
 #pragma unroll
       for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
   const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (int k0 = 0; k0 < g.K; k0 += kGBK) {
-    // gather the tiles (k fastest across threads when the operand is k-contiguous)
+  const int kb = blockIdx.z * g.kchunk, ke = min(g.K, kb + g.kchunk);
+  // gather order: consecutive threads along the operand's unit-stride index
+  const bool a_rows = g.sam == 1 && g.sak != 1, b_rows = g.sbn == 1 && g.sbk != 1;
+  for (int k0 = kb; k0 < ke; k0 += kGBK) {
 #pragma unroll 4
     for (int i = tid; i < kGBM * kGBK; i += 128) {
-      const int r = i / kGBK, kk = i % kGBK;
+      const int r = a_rows ? i % kGBM : i / kGBK, kk = a_rows ? i / kGBM : i % kGBK;
       const int m = m0 + r, k = k0 + kk;
-      As[r][kk] = (m < g.M && k < g.K) ? g.A[(long long)m * g.sam + (long long)k * g.sak] : zero;
-      const int n = n0 + r;
-      Bs[r][kk] = (n < g.N && k < g.K) ? g.B[(long long)n * g.sbn + (long long)k * g.sbk] : zero;
+      As[r][kk] = (m < g.M && k < ke) ? g.A[(long long)m * g.sam + (long long)k * g.sak] : zero;
+    }
+#pragma unroll 4
+    for (int i = tid; i < kGBN * kGBK; i += 128) {
+      const int r = b_rows ? i % kGBN : i / kGBK, kk = b_rows ? i / kGBN : i % kGBK;
+      const int n = n0 + r, k = k0 + kk;
+      Bs[r][kk] = (n < g.N && k < ke) ? g.B[(long long)n * g.sbn + (long long)k * g.sbk] : zero;
     }
     __syncthreads();
 #pragma unroll
@@ -135,6 +142,25 @@ struct EpiStore {
   int ld;
   __device__ __forceinline__ void operator()(int m, int n, float acc) const { c[(long long)m * ld + n] = acc; }
 };
+
+// split-K partial sums: ws[z][m][n] for block z
+struct EpiPartial {
+  float *ws;
+  int ld;
+  long long zstride;
+  __device__ __forceinline__ void operator()(int m, int n, float acc) const {
+    ws[blockIdx.z * zstride + (long long)m * ld + n] = acc;
+  }
+};
+
+// out[i] = sum over z (in order) of ws[z][i]: deterministic split-K reduction
+__global__ void k_splitk_sum(const float *ws, int nsplit, long long len, float *out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  float s = 0.f;
+  for (int z = 0; z < nsplit; ++z) s += ws[z * len + i];
+  out[i] = s;
+}
 
 // data gradient through tanh: dz = acc (1 - a^2); FP32 for the bias sums,
 // BF16 for the next GEMMs
@@ -225,14 +251,23 @@ __global__ void k_sum(const float *x, long long n, float *out) {
   if ((threadIdx.x & 31) == 0) atomicAdd(out, part);
 }
 
-// bias gradient: column sums of dz [n][ld] (first `cols` columns) into g
-__global__ void k_colsum(const float *dz, int n, int ld, int cols, float *g) {
-  const int c = blockIdx.x * blockDim.y + threadIdx.y;   // column
-  if (c >= cols) return;
+// bias gradient: column sums of dz [n][ld] (first `cols` columns) into g.
+// Block (32, 32): lane x is a column (coalesced rows), y a row phase; the 32
+// phase sums are added in a fixed order.
+constexpr int kColsumY = 32;
+__global__ void __launch_bounds__(32 * kColsumY) k_colsum(const float *dz, int n, int ld, int cols, float *g) {
+  __shared__ float s_part[kColsumY][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
   float part = 0.f;
-  for (int r = threadIdx.x; r < n; r += blockDim.x) part += dz[(long long)r * ld + c];
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if (threadIdx.x == 0) g[c] = part;
+  if (c < cols)
+    for (int r = threadIdx.y; r < n; r += kColsumY) part += dz[(long long)r * ld + c];
+  s_part[threadIdx.y][threadIdx.x] = part;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < cols) {
+    float s = 0.f;
+    for (int y = 0; y < kColsumY; ++y) s += s_part[y][threadIdx.x];
+    g[c] = s;
+  }
 }
 
 // Adam on the flat FP32 parameters
