@@ -962,7 +962,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
 }
 
 template <class M>
-__global__ void __launch_bounds__(kBlock, M::kMixed ? 4 : 3) k_step(const KArgs a, const KParams P) {
+__global__ void __launch_bounds__(kBlock, M::kMixed ? 5 : 3) k_step(const KArgs a, const KParams P) {
   __shared__ Smem sm;
   const bool fast = prologue(a, P, sm);
   const int c = blockIdx.x * kBlock + threadIdx.x;
