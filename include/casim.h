@@ -123,11 +123,17 @@ int casim_init(casim_ctx **ctx, const casim_params *params, int precision, int f
 int casim_step(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream);
 
 /* Same step for a domain held in HOST memory (any host allocation; pinned
-   memory copies faster): copies fld, dz and precip to device buffers owned by
-   the context, runs casim_step, copies the 13 prognostic fields and precip
-   back, and waits for the stream.  The state layout is the device one, with
-   host pointers.  Device buffers grow to the largest domain seen and are
-   freed by casim_free. */
+   memory copies faster and overlaps).  A domain of more than 65 536 columns
+   is processed in column chunks of 65 536 (fewer if 16 fields x nlev of them
+   exceed 2 GB) on three internal streams of the context, so one chunk's copy
+   in (16 fields and precip), another's step and a third's copy out (13
+   prognostic fields and precip) run at once (the paper's per-step transfers,
+   Section 3.3, overlapped with the kernel); a smaller domain is copied whole
+   on `stream`.  Starts after the work already queued on `stream` and returns
+   when every copy back has landed.  Results equal casim_step's on the same
+   state, bit for bit.  The state layout is the device one, with host
+   pointers.  Device buffers grow to the largest size seen and are freed by
+   casim_free. */
 int casim_step_host(casim_ctx *ctx, const casim_state *host, int ncols, int nlev, double dt,
                     void *stream);
 

@@ -30,9 +30,13 @@ struct casim_ctx {
   KParams kp;
   unsigned *d_err = nullptr;
   long long launches = 0;
-  // staging for casim_step_host
-  double *h2d_fld = nullptr, *h2d_dz = nullptr, *h2d_precip = nullptr;
-  size_t cap_fld = 0, cap_dz = 0, cap_precip = 0;
+  // staging for casim_step_host: per pipeline stage a chunk of the state and
+  // of precip, its own stream; dz once
+  static constexpr int kStages = 3;
+  double *h2d_fld[kStages] = {}, *h2d_precip[kStages] = {}, *h2d_dz = nullptr;
+  size_t cap_fld[kStages] = {}, cap_precip[kStages] = {}, cap_dz = 0;
+  cudaStream_t hst[kStages] = {};
+  cudaEvent_t hev_start = nullptr, hev_dz = nullptr;
 };
 
 static thread_local char g_last_error[256] = "";
@@ -249,33 +253,108 @@ static int grow(double **buf, size_t *cap, size_t n) {
   return CASIM_OK;
 }
 
+// Host pipeline chunks: strided host<->device copies run at full speed only
+// with contiguous runs of about 512 KB (measured on GB300: 512 KB rows 205
+// GB/s, 128 KB rows 100 GB/s), so a chunk is at least 65 536 columns wide;
+// at most 2 GB of device state per stage.
+constexpr size_t kHostMinRowBytes = 512ull << 10;
+constexpr size_t kHostChunkBytes = 2ull << 30;
+
+// one column chunk [c0, c0 + wc) of a host state: fields (3-D strided copy:
+// wc columns x nlev levels x nfields) and precip (2-D copy)
+static cudaError_t copy_chunk(double *dev_fld, double *dev_precip, int W, const casim_state *h, int c0, int wc,
+                              int nlev, int nfields, cudaMemcpyKind kind, cudaStream_t st) {
+  cudaMemcpy3DParms p = {};
+  const bool up = kind == cudaMemcpyHostToDevice;
+  cudaPitchedPtr hp = make_cudaPitchedPtr(h->fld + c0, (size_t)h->pitch * sizeof(double), (size_t)wc, (size_t)nlev);
+  cudaPitchedPtr dp = make_cudaPitchedPtr(dev_fld, (size_t)W * sizeof(double), (size_t)wc, (size_t)nlev);
+  p.srcPtr = up ? hp : dp;
+  p.dstPtr = up ? dp : hp;
+  p.extent = make_cudaExtent((size_t)wc * sizeof(double), (size_t)nlev, (size_t)nfields);
+  p.kind = kind;
+  cudaError_t e = cudaMemcpy3DAsync(&p, st);
+  if (e != cudaSuccess) return e;
+  double *hpr = h->precip + c0;
+  const size_t hpitch = (size_t)h->pitch * sizeof(double), dpitch = (size_t)W * sizeof(double);
+  return up ? cudaMemcpy2DAsync(dev_precip, dpitch, hpr, hpitch, (size_t)wc * sizeof(double), CASIM_NPRECIP, kind, st)
+            : cudaMemcpy2DAsync(hpr, hpitch, dev_precip, dpitch, (size_t)wc * sizeof(double), CASIM_NPRECIP, kind, st);
+}
+
 extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, int nlev, double dt,
                                void *stream) {
   if (!ctx) return CASIM_ERR_ARG;
   if (!h || ncols < 0 || nlev < 1 || nlev > kMaxLev || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
   if (ncols == 0) return CASIM_OK;
   if (!h->fld || !h->dz || !h->precip || h->pitch < ncols || h->pitch % 32 != 0) return CASIM_ERR_ARG;
-  const size_t nf = (size_t)CASIM_NFIELDS * nlev * h->pitch;
-  const size_t np = (size_t)CASIM_NPRECIP * h->pitch;
+  // chunk width: a multiple of 32 columns with long contiguous rows, within the byte cap
+  const size_t col_bytes = (size_t)CASIM_NFIELDS * nlev * sizeof(double);
+  const int wcap = (int)std::max<size_t>(32, kHostChunkBytes / col_bytes / 32 * 32);
+  const int W = (int)std::min<size_t>(kHostMinRowBytes / sizeof(double), (size_t)wcap);
+  const int nchunk = (ncols + W - 1) / W;
   int rc;
-  if ((rc = grow(&ctx->h2d_fld, &ctx->cap_fld, nf)) != CASIM_OK) return rc;
+  if (nchunk == 1) {
+    // one chunk: contiguous copies of the whole state at the host pitch
+    const size_t nf = (size_t)CASIM_NFIELDS * nlev * h->pitch, np = (size_t)CASIM_NPRECIP * h->pitch;
+    if ((rc = grow(&ctx->h2d_fld[0], &ctx->cap_fld[0], nf)) != CASIM_OK) return rc;
+    if ((rc = grow(&ctx->h2d_precip[0], &ctx->cap_precip[0], np)) != CASIM_OK) return rc;
+    if ((rc = grow(&ctx->h2d_dz, &ctx->cap_dz, (size_t)nlev)) != CASIM_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(ctx->h2d_fld[0], h->fld, nf * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(ctx->h2d_dz, h->dz, (size_t)nlev * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(ctx->h2d_precip[0], h->precip, np * sizeof(double), cudaMemcpyHostToDevice, st));
+    casim_state d;
+    d.fld = ctx->h2d_fld[0];
+    d.pitch = h->pitch;
+    d.dz = ctx->h2d_dz;
+    d.precip = ctx->h2d_precip[0];
+    if ((rc = casim_step(ctx, &d, ncols, nlev, dt, stream)) != CASIM_OK) return rc;
+    const size_t nprog = (size_t)CASIM_NPROG * nlev * h->pitch;
+    CUDA_TRY(cudaMemcpyAsync(h->fld, ctx->h2d_fld[0], nprog * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(h->precip, ctx->h2d_precip[0], np * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return CASIM_OK;
+  }
+  const int S = std::min(casim_ctx::kStages, nchunk);
+  for (int s = 0; s < S; ++s) {
+    if ((rc = grow(&ctx->h2d_fld[s], &ctx->cap_fld[s], (size_t)CASIM_NFIELDS * nlev * W)) != CASIM_OK) return rc;
+    if ((rc = grow(&ctx->h2d_precip[s], &ctx->cap_precip[s], (size_t)CASIM_NPRECIP * W)) != CASIM_OK) return rc;
+    if (!ctx->hst[s]) CUDA_TRY(cudaStreamCreateWithFlags(&ctx->hst[s], cudaStreamNonBlocking));
+  }
   if ((rc = grow(&ctx->h2d_dz, &ctx->cap_dz, (size_t)nlev)) != CASIM_OK) return rc;
-  if ((rc = grow(&ctx->h2d_precip, &ctx->cap_precip, np)) != CASIM_OK) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
-  CUDA_TRY(cudaMemcpyAsync(ctx->h2d_fld, h->fld, nf * sizeof(double), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(ctx->h2d_dz, h->dz, (size_t)nlev * sizeof(double), cudaMemcpyHostToDevice, st));
-  CUDA_TRY(cudaMemcpyAsync(ctx->h2d_precip, h->precip, np * sizeof(double), cudaMemcpyHostToDevice, st));
-  casim_state d;
-  d.fld = ctx->h2d_fld;
-  d.pitch = h->pitch;
-  d.dz = ctx->h2d_dz;
-  d.precip = ctx->h2d_precip;
-  if ((rc = casim_step(ctx, &d, ncols, nlev, dt, stream)) != CASIM_OK) return rc;
-  const size_t nprog = (size_t)CASIM_NPROG * nlev * h->pitch;
-  CUDA_TRY(cudaMemcpyAsync(h->fld, ctx->h2d_fld, nprog * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaMemcpyAsync(h->precip, ctx->h2d_precip, np * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CUDA_TRY(cudaStreamSynchronize(st));
-  return CASIM_OK;
+  if (!ctx->hev_start) CUDA_TRY(cudaEventCreateWithFlags(&ctx->hev_start, cudaEventDisableTiming));
+  if (!ctx->hev_dz) CUDA_TRY(cudaEventCreateWithFlags(&ctx->hev_dz, cudaEventDisableTiming));
+  // the stages start after the caller's earlier work on `stream`; dz goes up once
+  CUDA_TRY(cudaEventRecord(ctx->hev_start, (cudaStream_t)stream));
+  CUDA_TRY(cudaStreamWaitEvent(ctx->hst[0], ctx->hev_start, 0));
+  CUDA_TRY(cudaMemcpyAsync(ctx->h2d_dz, h->dz, (size_t)nlev * sizeof(double), cudaMemcpyHostToDevice, ctx->hst[0]));
+  CUDA_TRY(cudaEventRecord(ctx->hev_dz, ctx->hst[0]));
+  for (int s = 1; s < S; ++s) CUDA_TRY(cudaStreamWaitEvent(ctx->hst[s], ctx->hev_dz, 0));
+  // chunk i on stage i % S: copy in, step, copy out; the stages overlap
+  // one chunk's copies in, another's step and a third's copies out
+  cudaError_t e = cudaSuccess;
+  rc = CASIM_OK;
+  for (int i = 0; i < nchunk && e == cudaSuccess && rc == CASIM_OK; ++i) {
+    const int s = i % S;
+    const int c0 = i * W, wc = std::min(W, ncols - c0);
+    e = copy_chunk(ctx->h2d_fld[s], ctx->h2d_precip[s], W, h, c0, wc, nlev, CASIM_NFIELDS, cudaMemcpyHostToDevice,
+                   ctx->hst[s]);
+    if (e != cudaSuccess) break;
+    casim_state d;
+    d.fld = ctx->h2d_fld[s];
+    d.pitch = W;
+    d.dz = ctx->h2d_dz;
+    d.precip = ctx->h2d_precip[s];
+    rc = casim_step(ctx, &d, wc, nlev, dt, ctx->hst[s]);
+    if (rc != CASIM_OK) break;
+    e = copy_chunk(ctx->h2d_fld[s], ctx->h2d_precip[s], W, h, c0, wc, nlev, CASIM_NPROG, cudaMemcpyDeviceToHost,
+                   ctx->hst[s]);
+  }
+  for (int s = 0; s < S; ++s) {
+    const cudaError_t es = cudaStreamSynchronize(ctx->hst[s]);
+    if (e == cudaSuccess) e = es;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "casim_step_host");
+  return rc;
 }
 
 extern "C" int casim_budget(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double *out, void *stream) {
@@ -1259,8 +1338,13 @@ extern "C" void casim_free(casim_ctx *ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
   if (ctx->d_err) cudaFree(ctx->d_err);
-  if (ctx->h2d_fld) cudaFree(ctx->h2d_fld);
+  for (int s = 0; s < casim_ctx::kStages; ++s) {
+    if (ctx->h2d_fld[s]) cudaFree(ctx->h2d_fld[s]);
+    if (ctx->h2d_precip[s]) cudaFree(ctx->h2d_precip[s]);
+    if (ctx->hst[s]) cudaStreamDestroy(ctx->hst[s]);
+  }
   if (ctx->h2d_dz) cudaFree(ctx->h2d_dz);
-  if (ctx->h2d_precip) cudaFree(ctx->h2d_precip);
+  if (ctx->hev_start) cudaEventDestroy(ctx->hev_start);
+  if (ctx->hev_dz) cudaEventDestroy(ctx->hev_dz);
   delete ctx;
 }

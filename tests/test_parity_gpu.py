@@ -150,16 +150,32 @@ def test_cfl_cap_sets_error_flag():
     assert rc == -5 and flags & casim.EFLAG_CFL
 
 
-def test_host_entry_point_matches_device_entry_point():
-    fld, dz, ncols, nlev, dt, _ = synth.workload("stratus_16x16x50")
-    out, pr, _ = run_gpu(fld, dz, ncols, dt)
-    ctx = casim.casim_init()
+@pytest.mark.parametrize("case", ["stratus_16x16x50", "deep_1000_of_1056", "deep_mixed_140000_of_140032x6"])
+def test_host_entry_point_matches_device_entry_point(case):
+    """The host-buffer step gives the device step's result bit for bit: one
+    chunk copied whole (pitch = ncols, and pitch > ncols); three column chunks
+    of 65 536, 65 536 and 8 928 pipelined over the internal streams, pitch >
+    ncols, mixed form."""
+    precision = casim.CASIM_FP64
+    if case == "stratus_16x16x50":
+        fld, dz, ncols, nlev, dt, _ = synth.workload(case)
+    else:
+        ncols, pitch, nlev = (1000, 1056, 150) if case.startswith("deep_1000") else (140000, 140032, 6)
+        dz = synth.dz_stretched(nlev)
+        fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=21, pitch=pitch)
+        dt = 1.0
+        if "mixed" in case:
+            precision = casim.CASIM_MIXED
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, precision=precision)
+    ctx = casim.casim_init(precision=precision)
     try:
         h = np.ascontiguousarray(fld.copy())
         hdz = np.ascontiguousarray(dz)
         hpr = np.zeros((4, fld.shape[2]))
         st = casim.make_state(h, fld.shape[2], hdz, hpr)
         casim.casim_step_host(ctx, st, ncols, nlev, dt, stream=0)
+        rc, flags = casim.casim_get_error(ctx)
+        assert rc == 0, (rc, flags)
         assert np.array_equal(h, out)
         assert np.array_equal(hpr, pr)
     finally:
