@@ -122,6 +122,21 @@ int casim_init(casim_ctx **ctx, const casim_params *params, int precision, int f
    s->dz on the device.  Asynchronous on `stream`. */
 int casim_step(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream);
 
+/* Source-term mode: CASIM itself does not update the state but writes a
+   source term per field for the parent model to add (Section 3.2: results go
+   into source-term arguments for each q field; Section 3.1: source terms are
+   copied back and integrated on the host).  The same step as casim_step, but
+   s->fld is left unchanged and tend (device, [13][nlev][s->pitch], owned by
+   the caller, not overlapping s->fld) receives (x_after - x_before) / dt of
+   the 13 prognostic fields at every point of the first ncols columns, where
+   x_after is what casim_step would store (so x_before + tend * dt reproduces
+   it to the rounding of the subtraction and division).  s->precip
+   accumulates the step's surface precipitation as in casim_step.
+   Asynchronous on `stream`; errors as casim_step, and CASIM_ERR_ARG for a
+   NULL, misaligned or overlapping tend. */
+int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, double *tend,
+                        void *stream);
+
 /* Same step for a domain held in HOST memory (any host allocation; pinned
    memory copies faster and overlaps).  A domain of more than 65 536 columns
    is processed in column chunks of 65 536 (fewer if 16 fields x nlev of them

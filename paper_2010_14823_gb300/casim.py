@@ -82,6 +82,8 @@ def lib():
         L.casim_init.restype = i
         L.casim_step.argtypes = [vp, ps, i, i, d, vp]
         L.casim_step.restype = i
+        L.casim_step_tendency.argtypes = [vp, ps, i, i, d, vp, vp]
+        L.casim_step_tendency.restype = i
         L.casim_step_host.argtypes = [vp, ps, i, i, d, vp]
         L.casim_step_host.restype = i
         L.casim_budget.argtypes = [vp, ps, i, i, vp, vp]
@@ -206,6 +208,12 @@ def make_state(fld, pitch: int, dz, precip) -> casim_state:
 
 def casim_step(ctx, state: casim_state, ncols: int, nlev: int, dt: float, stream=None):
     _check(lib().casim_step(ctx, ctypes.byref(state), ncols, nlev, dt, _stream(stream)), "casim_step")
+
+
+def casim_step_tendency(ctx, state: casim_state, ncols: int, nlev: int, dt: float, tend, stream=None):
+    """Source-term mode: state unchanged, tend [13][nlev][pitch] (device) = (x_after - x_before) / dt."""
+    _check(lib().casim_step_tendency(ctx, ctypes.byref(state), ncols, nlev, dt, _ptr(tend), _stream(stream)),
+           "casim_step_tendency")
 
 
 def casim_step_host(ctx, state: casim_state, ncols: int, nlev: int, dt: float, stream=None):

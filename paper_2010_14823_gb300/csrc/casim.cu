@@ -223,20 +223,42 @@ static KArgs make_args(const casim_ctx *ctx, const casim_state *s, int ncols, in
   return a;
 }
 
+// tend null: the in-place step; else the source-term mode
+static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, void *stream) {
+  const dim3 grid((unsigned)((ncols + kBlock - 1) / kBlock));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ctx->precision == CASIM_MIXED) {
+    if (tend) k_step<PolicyMix, true><<<grid, kBlock, 0, st>>>(a, ctx->kp, tend);
+    else k_step<PolicyMix, false><<<grid, kBlock, 0, st>>>(a, ctx->kp, nullptr);
+  } else {
+    if (tend) k_step<PolicyF64, true><<<grid, kBlock, 0, st>>>(a, ctx->kp, tend);
+    else k_step<PolicyF64, false><<<grid, kBlock, 0, st>>>(a, ctx->kp, nullptr);
+  }
+  ctx->launches++;
+  CUDA_TRY(cudaGetLastError());
+  return CASIM_OK;
+}
+
+extern "C" int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, double *tend,
+                                   void *stream) {
+  if (!ctx || !tend) return CASIM_ERR_ARG;
+  int rc = check_state(s, ncols, nlev, dt);
+  if (rc != CASIM_OK || ncols == 0) return rc;
+  const size_t span = (size_t)CASIM_NFIELDS * nlev * s->pitch;
+  const size_t tspan = (size_t)CASIM_NPROG * nlev * s->pitch;
+  if (reinterpret_cast<uintptr_t>(tend) % alignof(double) != 0 ||
+      (tend < s->fld + span && s->fld < tend + tspan))   // must not overlap the state
+    return CASIM_ERR_ARG;
+  const KArgs a = make_args(ctx, s, ncols, nlev, dt);
+  return launch_step(ctx, a, ncols, tend, stream);
+}
+
 extern "C" int casim_step(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream) {
   if (!ctx) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
   const KArgs a = make_args(ctx, s, ncols, nlev, dt);
-  const dim3 grid((unsigned)((ncols + kBlock - 1) / kBlock));
-  cudaStream_t st = (cudaStream_t)stream;
-  if (ctx->precision == CASIM_MIXED)
-    k_step<PolicyMix><<<grid, kBlock, 0, st>>>(a, ctx->kp);
-  else
-    k_step<PolicyF64><<<grid, kBlock, 0, st>>>(a, ctx->kp);
-  ctx->launches++;
-  CUDA_TRY(cudaGetLastError());
-  return CASIM_OK;
+  return launch_step(ctx, a, ncols, nullptr, stream);
 }
 
 static int grow(double **buf, size_t *cap, size_t n) {
@@ -1325,7 +1347,7 @@ extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_st
   // 3. the step, taking the network's rates where given
   a.surr = m->surr;
   const dim3 grid((unsigned)((ncols + kBlock - 1) / kBlock));
-  k_step<PolicyMix><<<grid, kBlock, 0, st>>>(a, ctx->kp);
+  k_step<PolicyMix, false><<<grid, kBlock, 0, st>>>(a, ctx->kp, nullptr);
   ctx->launches++;
   CUDA_TRY(cudaGetLastError());
   if (served) *served = rows;

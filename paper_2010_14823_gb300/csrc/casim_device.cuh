@@ -715,6 +715,21 @@ __device__ __forceinline__ unsigned store_pt(const KArgs &a, int k, int c, const
          nonfinite(s.ns) | nonfinite(s.ng) | nonfinite(s.na);
 }
 
+// Tendency mode (the state is left unchanged): in the single-substep path
+// the source terms (x_new - x_old) / dt go straight to tend (x_old re-read
+// from the state, still in cache); in the multi-substep path the new values
+// go to tend as scratch for the substep sweeps and are converted afterwards.
+__device__ __forceinline__ unsigned store_tend(const KArgs &a, double *tend, int k, int c, const Pt &s, bool fast) {
+  const size_t o = (size_t)k * a.pitch + c;
+  const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
+  const double v[13] = {s.T, s.qv, s.qc, s.qr, s.qi, s.qs, s.qg, s.nc, s.nr, s.ni, s.ns, s.ng, s.na};
+#pragma unroll
+  for (int f = 0; f < 13; ++f) tend[f * fs + o] = fast ? (v[f] - a.fld[f * fs + o]) / a.dt : v[f];
+  return nonfinite(s.T) | nonfinite(s.qv) | nonfinite(s.qc) | nonfinite(s.qr) | nonfinite(s.qi) |
+         nonfinite(s.qs) | nonfinite(s.qg) | nonfinite(s.nc) | nonfinite(s.nr) | nonfinite(s.ni) |
+         nonfinite(s.ns) | nonfinite(s.ng) | nonfinite(s.na);
+}
+
 __device__ __forceinline__ double &qref(Pt &s, int x) {
   return x == 0 ? s.qr : x == 1 ? s.qi : x == 2 ? s.qs : s.qg;
 }
@@ -756,18 +771,19 @@ __device__ __forceinline__ bool prologue(const KArgs &a, const KParams &P, Smem 
 // Multi-substep sedimentation of one column after the processes (used when a
 // capped speed could exceed one level per step): per species, n_sub from the
 // largest Courant number, then n_sub top-down sweeps in place.
-template <class M>
+template <class M, bool kTend>
 __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KParams &P, const double *sdz, int c,
-                                                      double prec[4]) {
+                                                      double prec[4], double *tend) {
   using R = typename M::R;
   using Ph = Phys<M>;
   const ConstK<R> &K = M::K(P);
   unsigned eflag = 0;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
   const double *rhop = a.fld + 14 * fs;
+  double *state = kTend ? tend : a.fld;   // the processed state (tendency mode: scratch)
   for (int x = 0; x < 4; ++x) {
-    double *qp = a.fld + (3 + x) * fs;
-    double *np = a.fld + (8 + x) * fs;
+    double *qp = state + (3 + x) * fs;
+    double *np = state + (8 + x) * fs;
     R cmax = 0;
     for (int k = 0; k < a.nlev; ++k) {
       const size_t o = (size_t)k * a.pitch + c;
@@ -831,9 +847,9 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
 // sweep of the processes (one read and one write of the state).  Otherwise
 // the processes are applied first and each species is sedimented with its
 // own substep count in further sweeps over the column.
-template <class M>
+template <class M, bool kTend = false>
 __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P, const double *sdz,
-                                               const double *sdzdt, bool fast, int c) {
+                                               const double *sdzdt, bool fast, int c, double *tend = nullptr) {
   using R = typename M::R;
   using Ph = Phys<M>;
   const ConstK<R> &K = M::K(P);
@@ -942,13 +958,26 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
         if (dn[x] != 0.f) nref(s, x) += f2d(dn[x]);
       eflag |= w.hmax >= 0x7ff00000u;
     }
-    if (touched) eflag |= store_pt(a, k, c, s);
+    if constexpr (kTend) {
+      eflag |= store_tend(a, tend, k, c, s, fast);
+    } else {
+      if (touched) eflag |= store_pt(a, k, c, s);
+    }
   }
   if (fast) {
 #pragma unroll
     for (int x = 0; x < 4; ++x) prec[x] = M::toD(Fq[x]) * a.dt;
   } else {
-    eflag |= sediment_substeps<M>(a, P, sdz, c, prec);
+    eflag |= sediment_substeps<M, kTend>(a, P, sdz, c, prec, tend);
+    if constexpr (kTend) {
+      // tendency mode: the new state in tend becomes (x_new - x_old) / dt
+      const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
+      for (int k = 0; k < a.nlev; ++k) {
+        const size_t o = (size_t)k * a.pitch + c;
+#pragma unroll
+        for (int f = 0; f < 13; ++f) tend[f * fs + o] = (tend[f * fs + o] - a.fld[f * fs + o]) / a.dt;
+      }
+    }
   }
 #pragma unroll
   for (int x = 0; x < 4; ++x) {
@@ -961,13 +990,14 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
   return eflag;
 }
 
-template <class M>
-__global__ void __launch_bounds__(kBlock, M::kMixed ? 5 : 3) k_step(const KArgs a, const KParams P) {
+// kTend: tendency mode (tend receives the source terms, a.fld unchanged)
+template <class M, bool kTend>
+__global__ void __launch_bounds__(kBlock, M::kMixed ? 5 : 3) k_step(const KArgs a, const KParams P, double *tend) {
   __shared__ Smem sm;
   const bool fast = prologue(a, P, sm);
   const int c = blockIdx.x * kBlock + threadIdx.x;
   if (c >= a.ncols) return;
-  const unsigned eflag = run_column<M>(a, P, sm.dz, sm.dzdt, fast, c);
+  const unsigned eflag = run_column<M, kTend>(a, P, sm.dz, sm.dzdt, fast, c, tend);
   if (eflag) atomicOr(a.err, eflag);
 }
 

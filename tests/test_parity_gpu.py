@@ -182,6 +182,38 @@ def test_host_entry_point_matches_device_entry_point(case):
         casim.casim_free(ctx)
 
 
+@pytest.mark.parametrize("precision", [casim.CASIM_FP64, casim.CASIM_MIXED])
+@pytest.mark.parametrize("dt", [1.0, 30.0])
+def test_tendency_mode_equals_in_place_step(precision, dt):
+    """Source-term mode: the state is untouched and tend is (x_after - x_before)
+    / dt of the in-place step, bit for bit, at every point (also where nothing
+    changes: zero); dt = 30 s takes the multi-substep sedimentation path."""
+    import torch
+    nlev = 150
+    dz = synth.dz_stretched(nlev)
+    ncols, pitch = 333, 352
+    fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=31, pitch=pitch)
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, precision=precision)
+    ctx = casim.casim_init(precision=precision)
+    try:
+        d = casim.Domain(fld, dz, ncols)
+        tend = torch.full((13, nlev, pitch), float("nan"), dtype=torch.float64, device="cuda")
+        casim.casim_step_tendency(ctx, d.state, ncols, nlev, dt, tend)
+        rc, flags = casim.casim_get_error(ctx)
+        assert rc == 0, (rc, flags)
+        f2, p2 = d.numpy()
+        assert np.array_equal(f2, fld)                      # state unchanged
+        assert np.array_equal(p2, pr)                       # precipitation accumulated as in place
+        t = tend.cpu().numpy()[:, :, :ncols]
+        expect = (out[:13, :, :ncols] - fld[:13, :, :ncols]) / dt
+        assert np.array_equal(t, expect)
+        assert np.isnan(tend.cpu().numpy()[:, :, ncols:]).all()   # padding columns not written
+        with pytest.raises(RuntimeError):                   # tend overlapping the state
+            casim.casim_step_tendency(ctx, d.state, ncols, nlev, dt, d.fld)
+    finally:
+        casim.casim_free(ctx)
+
+
 def test_budget_sums():
     fld, dz, ncols, nlev, dt, _ = synth.workload("stratus_16x16x50")
     ctx = casim.casim_init()
