@@ -79,6 +79,12 @@ def lib():
         L.orc_sediment_column.argtypes = [pd, pd, pd, pd, i, d, pd, ctypes.POINTER(ctypes.c_int)]
         L.orc_step.restype = u
         L.orc_step.argtypes = [pd, ctypes.c_long, i, i, pd, pd, ctypes.POINTER(ctypes.c_int), d, i]
+        L.orc_step_cfg.restype = u
+        L.orc_step_cfg.argtypes = [pd, ctypes.c_long, i, i, pd, pd, ctypes.POINTER(ctypes.c_int), d, i, i]
+        L.orc_point_cfg.restype = None
+        L.orc_point_cfg.argtypes = [pd, d, pd, i]
+        L.orc_rates_cfg.restype = None
+        L.orc_rates_cfg.argtypes = [pd, d, pd, i]
         L.orc_param.restype = d
         L.orc_param.argtypes = [ctypes.c_char_p]
         L.orc_max_threads.restype = i
@@ -150,19 +156,19 @@ def vn(sp: str, rho: float, lam_: float) -> float:
     return lib().orc_vn(SPECIES[sp], rho, lam_)
 
 
-def rates(state: np.ndarray, dt: float) -> dict:
+def rates(state: np.ndarray, dt: float, warm: bool = False) -> dict:
     st = np.ascontiguousarray(state, dtype=np.float64)
     assert st.shape == (NFIELDS,)
     out = np.zeros(NPROC)
-    lib().orc_rates(_dp(st), dt, _dp(out))
+    lib().orc_rates_cfg(_dp(st), dt, _dp(out), int(warm))
     return dict(zip(PROCS, out.tolist()))
 
 
-def point(state: np.ndarray, dt: float) -> np.ndarray:
+def point(state: np.ndarray, dt: float, warm: bool = False) -> np.ndarray:
     st = np.ascontiguousarray(state, dtype=np.float64)
     assert st.shape == (NFIELDS,)
     out = np.zeros(NPROG)
-    lib().orc_point(_dp(st), dt, _dp(out))
+    lib().orc_point_cfg(_dp(st), dt, _dp(out), int(warm))
     return out
 
 
@@ -182,10 +188,11 @@ def sediment_column(q: np.ndarray, n: np.ndarray, rho: np.ndarray, dz: np.ndarra
 
 
 def step(fld: np.ndarray, ncols: int, dz: np.ndarray, dt: float, precip: np.ndarray | None = None,
-         nthreads: int = 0, want_nsub: bool = False):
+         nthreads: int = 0, want_nsub: bool = False, warm: bool = False):
     """One step over a domain, in place on ``fld`` [16][nlev][pitch].
 
     Returns (precip [4][pitch] accumulated, nsub [4][pitch] or None, err bits).
+    warm: the warm configuration (liquid water only; ice fields untouched).
     """
     assert fld.dtype == np.float64 and fld.flags["C_CONTIGUOUS"] and fld.shape[0] == NFIELDS
     nlev, pitch = fld.shape[1], fld.shape[2]
@@ -197,7 +204,7 @@ def step(fld: np.ndarray, ncols: int, dz: np.ndarray, dt: float, precip: np.ndar
     assert precip.shape == (4, pitch) and precip.dtype == np.float64 and precip.flags["C_CONTIGUOUS"]
     nsub = np.zeros((4, pitch), dtype=np.int32) if want_nsub else None
     nsp = nsub.ctypes.data_as(ctypes.POINTER(ctypes.c_int)) if want_nsub else None
-    err = lib().orc_step(_dp(fld), pitch, ncols, nlev, _dp(dz), _dp(precip), nsp, dt, nthreads)
+    err = lib().orc_step_cfg(_dp(fld), pitch, ncols, nlev, _dp(dz), _dp(precip), nsp, dt, nthreads, int(warm))
     return precip, nsub, err
 
 

@@ -228,11 +228,12 @@ double orc_vn(int sp, double rho, double lam) {
 }
 
 /* --------------------------------------------------------- a4..a9 rates */
-void orc_rates(const double *st, double dt, double *R) {
+void orc_rates_cfg(const double *st, double dt, double *R, int warm) {
   /* Rates in kg kg^-1 s^-1 (masses) except SCC, SCR (number kg^-1 s^-1) and
      NUC (new crystals kg^-1 s^-1).  All are >= 0 except DEPx, which is
      positive for deposition and negative for sublimation.  MLTx is the
-     melted mass rate. */
+     melted mass rate.  warm != 0: the warm configuration, which considers
+     liquid water only (Section 2.1): a4 and a5; no ice process. */
   double T = st[ORC_T], qv = st[ORC_QV], qc = st[ORC_QC], qr = st[ORC_QR];
   double nc = st[ORC_NC], nr = st[ORC_NR], ni = st[ORC_NI];
   double p = st[ORC_P], rho = st[ORC_RHO];
@@ -265,6 +266,7 @@ void orc_rates(const double *st, double dt, double *R) {
       R[ORC_EVR] = 2.0 * PI * (1.0 - Sw) * orc_vent_integral(ORC_R, rho, qr, lam) / (rho * (Aw + Bw));
     }
   }
+  if (warm) return;
   /* a6 ice nucleation: Meyers et al. (1992), N_in in m^-3 */
   if (T < TNUC && Si > 1.0) {
     double nin = MEY_A * exp(MEY_B + MEY_C * (Si - 1.0));
@@ -331,13 +333,21 @@ void orc_adjust_activate(const double *in, double *st) {
   }
 }
 
-void orc_point(const double *in, double dt, double *out) {
+static const int ICE_FIELDS[6] = {ORC_QI, ORC_QS, ORC_QG, ORC_NI, ORC_NS, ORC_NG};
+
+void orc_point_cfg(const double *in0, double dt, double *out, int warm) {
+  /* warm: the ice fields are not part of the warm state; they are treated as
+     absent and passed through unchanged */
+  double in[ORC_NFIELDS];
+  memcpy(in, in0, sizeof in);
+  if (warm)
+    for (int i = 0; i < 6; ++i) in[ICE_FIELDS[i]] = 0.0;
   double st[ORC_NFIELDS];
   orc_adjust_activate(in, st);
 
   /* a4..a9 from the post-activation state */
   double R[ORC_NPROC];
-  orc_rates(st, dt, R);
+  orc_rates_cfg(st, dt, R, warm);
 
   double qc = st[ORC_QC], qr = st[ORC_QR];
   orc_transfer tr[ORC_NPROC];
@@ -402,12 +412,27 @@ void orc_point(const double *in, double dt, double *out) {
     if (tr[j].nsink > 0.0) st[tr[j].nsrc] -= g * tr[j].nsink * dt;
     if (tr[j].ndst >= 0 && tr[j].nsource > 0.0) st[tr[j].ndst] += g * tr[j].nsource * dt;
   }
+  if (warm)
+    for (int i = 0; i < 6; ++i) st[ICE_FIELDS[i]] = in0[ICE_FIELDS[i]];
   memcpy(out, st, ORC_NPROG * sizeof(double));
 }
 
+void orc_rates(const double *st, double dt, double *R) { orc_rates_cfg(st, dt, R, 0); }
+
+void orc_point(const double *in, double dt, double *out) { orc_point_cfg(in, dt, out, 0); }
+
 /* ------------------------------------------------------ a12 sedimentation */
+static unsigned sediment_species(double *q, double *n, const double *rho, const double *dz, int nlev, double dt,
+                                 double *precip, int *nsub, int nspecies);
+
 unsigned orc_sediment_column(double *q, double *n, const double *rho, const double *dz,
                              int nlev, double dt, double *precip, int *nsub) {
+  return sediment_species(q, n, rho, dz, nlev, dt, precip, nsub, 4);
+}
+
+/* the first nspecies of r, i, s, g (warm configuration: rain only) */
+static unsigned sediment_species(double *q, double *n, const double *rho, const double *dz, int nlev, double dt,
+                                 double *precip, int *nsub, int nspecies) {
   /* For x in r, i, s, g: F_k = rho_k q_k Vq_k (mass), G_k = rho_k n_k Vn_k
      (number), fluxes downward.  Per substep of length dt/n_sub, with all
      fluxes taken from the substep's starting state:
@@ -421,7 +446,7 @@ unsigned orc_sediment_column(double *q, double *n, const double *rho, const doub
   unsigned err = 0;
   double *F = (double *)malloc(sizeof(double) * (size_t)(nlev + 1));
   double *G = (double *)malloc(sizeof(double) * (size_t)(nlev + 1));
-  for (int m = 0; m < 4; ++m) {
+  for (int m = 0; m < nspecies; ++m) {
     int sp = spx[m];
     double *qq = q + (size_t)m * nlev, *nn = n + (size_t)m * nlev;
     double cmax = 0.0;
@@ -469,13 +494,13 @@ unsigned orc_sediment_column(double *q, double *n, const double *rho, const doub
 
 /* ----------------------------------------------------------- full step */
 static unsigned step_column(double *fld, long pitch, int nlev, int c, const double *dz,
-                            double *precip, int *nsub, double dt) {
+                            double *precip, int *nsub, double dt, int warm) {
   unsigned err = 0;
   long fs = (long)nlev * pitch; /* field stride */
   double in[ORC_NFIELDS], out[ORC_NPROG];
   for (int k = 0; k < nlev; ++k) {
     for (int f = 0; f < ORC_NFIELDS; ++f) in[f] = fld[f * fs + (long)k * pitch + c];
-    orc_point(in, dt, out);
+    orc_point_cfg(in, dt, out, warm);
     for (int f = 0; f < ORC_NPROG; ++f) fld[f * fs + (long)k * pitch + c] = out[f];
   }
   double *buf = (double *)malloc(sizeof(double) * (size_t)(9 * nlev));
@@ -490,10 +515,11 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
     }
   }
   double pr[4] = {0.0, 0.0, 0.0, 0.0};
-  int ns[4];
-  err |= orc_sediment_column(q, n, rho, dz, nlev, dt, pr, ns);
+  int ns[4] = {1, 1, 1, 1};
+  const int nsp = warm ? 1 : 4;
+  err |= sediment_species(q, n, rho, dz, nlev, dt, pr, ns, nsp);
   for (int k = 0; k < nlev; ++k)
-    for (int m = 0; m < 4; ++m) {
+    for (int m = 0; m < nsp; ++m) {
       fld[qf[m] * fs + (long)k * pitch + c] = q[m * nlev + k];
       fld[nf[m] * fs + (long)k * pitch + c] = n[m * nlev + k];
     }
@@ -508,17 +534,22 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
   return err;
 }
 
-unsigned orc_step(double *fld, long pitch, int ncols, int nlev, const double *dz,
-                  double *precip, int *nsub, double dt, int nthreads) {
+unsigned orc_step_cfg(double *fld, long pitch, int ncols, int nlev, const double *dz,
+                      double *precip, int *nsub, double dt, int nthreads, int warm) {
   unsigned err = 0;
   if (nlev <= 0 || ncols <= 0) return 0;
 #ifdef _OPENMP
   if (nthreads <= 0) nthreads = omp_get_max_threads();
 #pragma omp parallel for schedule(guided) num_threads(nthreads) reduction(| : err)
 #endif
-  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, nsub, dt);
+  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, nsub, dt, warm);
   (void)nthreads;
   return err;
+}
+
+unsigned orc_step(double *fld, long pitch, int ncols, int nlev, const double *dz,
+                  double *precip, int *nsub, double dt, int nthreads) {
+  return orc_step_cfg(fld, pitch, ncols, nlev, dz, precip, nsub, dt, nthreads, 0);
 }
 
 int orc_max_threads(void) {

@@ -72,6 +72,14 @@ unsigned orc_sediment_column(double *q, double *n, const double *rho, const doub
    NULL) is [4][pitch].  nthreads <= 0 uses the OpenMP default. */
 unsigned orc_step(double *fld, long pitch, int ncols, int nlev, const double *dz,
                   double *precip, int *nsub, double dt, int nthreads);
+/* The warm configuration (warm != 0; Section 2.1: liquid water only): the
+   ice fields are treated as absent and passed through unchanged; no
+   nucleation, deposition, riming or melting; only rain sediments (ice, snow
+   and graupel precipitation stay zero).  warm = 0 is the functions above. */
+void   orc_rates_cfg(const double *st, double dt, double *rates, int warm);
+void   orc_point_cfg(const double *in, double dt, double *out, int warm);
+unsigned orc_step_cfg(double *fld, long pitch, int ncols, int nlev, const double *dz,
+                      double *precip, int *nsub, double dt, int nthreads, int warm);
 /* Parameter lookup by name for the tests (returns NaN for an unknown name). */
 double orc_param(const char *name);
 int    orc_max_threads(void);
