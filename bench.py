@@ -306,6 +306,93 @@ def bench_surrogate(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def bench_warm(args, rank, world, local):
+    """The warm configuration (liquid water only) against the cold one on the
+    same 512x512x150 stratus state, mixed and FP64 forms.  `value` is the warm
+    mixed step; the roofline is the warm kernel's (10 fields read, 7 written
+    where the step changes a point)."""
+    import torch
+    from paper_2010_14823_gb300 import casim, synth, shard
+    casim.lib()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    name = "stratus_512x512x150"
+    fld, dz, ncols, nlev, dt, _ = synth.workload(name, ncols=args.ncols, seed=shard.rank_seed(1238, rank))
+    npts = ncols * nlev
+    stream = torch.cuda.current_stream()
+    dom = casim.Domain(fld, dz, ncols)
+    fld0 = dom.fld.clone()
+
+    def sync():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def run(precision, flags, steps, warmup):
+        ctx = casim.casim_init(precision=precision, flags=flags)
+        dom.fld.copy_(fld0)
+        dom.precip.zero_()
+        for _ in range(warmup):
+            casim.casim_step(ctx, dom.state, ncols, nlev, dt, stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        sync()
+        n0 = casim.casim_launch_count(ctx)
+        for i in range(steps):
+            evs[i][0].record(stream)
+            casim.casim_step(ctx, dom.state, ncols, nlev, dt, stream)
+            evs[i][1].record(stream)
+        sync()
+        rc, fl = casim.casim_get_error(ctx, stream)
+        assert rc == 0, (rc, fl)
+        launches = casim.casim_launch_count(ctx) - n0
+        casim.casim_free(ctx)
+        total = evs[0][0].elapsed_time(evs[-1][1])
+        per = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        return shard.max_over_ranks(total, dist, "cuda") / steps, per, launches
+
+    # points the warm step changes (for the algorithmic bytes)
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM)
+    before = dom.fld[:13].clone()
+    casim.casim_step(ctx, dom.state, ncols, nlev, dt, stream)
+    torch.cuda.synchronize()
+    changed = int((dom.fld[:13] != before).any(dim=0)[:, :ncols].sum().item())
+    del before
+    casim.casim_free(ctx)
+    sampler = ClockSampler(local)
+    sampler.start()
+    warm_ms, warm_per, launches = run(casim.CASIM_MIXED, casim.CASIM_WARM, args.steps, args.warmup)
+    clocks = sampler.stop()
+    cold_ms, _, _ = run(casim.CASIM_MIXED, 0, args.steps, args.warmup)
+    w64_ms, _, _ = run(casim.CASIM_FP64, casim.CASIM_WARM, args.fp64_steps, 1)
+    c64_ms, _, _ = run(casim.CASIM_FP64, 0, args.fp64_steps, 1)
+    peak = _peaks().get("hbm_gbs")
+    alg = 80.0 * npts + 56.0 * changed
+    achieved = alg / (warm_per * 1e-3) / 1e9
+    if rank == 0:
+        v = lambda ms: world * npts / (ms * 1e-3)
+        line = {"metric": METRIC, "value": v(warm_ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": warm_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": name + " warm configuration", "ncols": ncols, "nlev": nlev, "dt_s": dt,
+                           "form": "mixed, warm configuration (liquid water only: 10 fields read, 7 written)",
+                           "l2": "state 5 GB > L2, no flush needed",
+                           "cold_mixed_value": v(cold_ms), "cold_mixed_ms_per_step": cold_ms,
+                           "warm_over_cold": cold_ms / warm_ms,
+                           "warm_fp64_value": v(w64_ms), "cold_fp64_value": v(c64_ms),
+                           "changed_points_frac": changed / npts},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak if peak else None, "traffic": None,
+                             "kernel": "k_step<PolicyMixWarm>", "algorithmic_bytes_per_launch": alg,
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 FIELD_NAMES = ("T", "qv", "qc", "qr", "qi", "qs", "qg", "nc", "nr", "ni", "ns", "ng", "na")
 
 
@@ -385,6 +472,8 @@ def main():
         return bench_batch(args, rank, world, local)
     if args.workload == "surrogate":
         return bench_surrogate(args, rank, world, local)
+    if args.workload == "warm_vs_cold":
+        return bench_warm(args, rank, world, local)
     from paper_2010_14823_gb300 import shard
     base_fld, dz, ncols, nlev, dt, _ = synth.workload(args.workload, ncols=args.ncols,
                                                       seed=shard.rank_seed(1236, rank))

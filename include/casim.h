@@ -109,10 +109,22 @@ typedef struct casim_ctx casim_ctx;
 /* Fill *p with the default scheme parameters.  Returns CASIM_ERR_ARG if p is NULL. */
 int casim_default_params(casim_params *p);
 
+/* casim_init flag: the warm configuration (Section 2.1: liquid water only,
+   5 moisture fields instead of the cold configuration's 18).  Steps read and
+   write only T, qv, qc, qr, nc, nr, na (and read p, rho, w); the ice fields
+   qi, qs, qg, ni, ns, ng are neither read nor written; no nucleation,
+   deposition, riming or melting; only rain sediments.  On a state without
+   ice and warmer than the nucleation threshold it gives the cold
+   configuration's result.  Supported by casim_step, casim_step_host and
+   casim_step_tendency (whose ice source terms are zero); the batched and
+   surrogate entry points reject a warm context (CASIM_ERR_ARG). */
+#define CASIM_WARM 1
+
 /* Create a context on the current CUDA device (Section 3.2: the one-off
    set-up that copies constants and allocates device memory).  `params` may be
-   NULL for the defaults; `precision` is a casim_precision; `flags` must be 0.
-   Allocates a small device error word.  On failure *ctx is set to NULL. */
+   NULL for the defaults; `precision` is a casim_precision; `flags` is 0 or
+   CASIM_WARM.  Allocates a small device error word.  On failure *ctx is set
+   to NULL. */
 int casim_init(casim_ctx **ctx, const casim_params *params, int precision, int flags);
 
 /* Advance every column of one domain by one timestep dt, in place

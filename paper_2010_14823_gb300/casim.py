@@ -18,6 +18,7 @@ from .build import LIB, INCLUDE
 
 CASIM_FP64 = 0
 CASIM_MIXED = 1
+CASIM_WARM = 1          # casim_init flag: the warm configuration
 NFIELDS = 16
 NPROG = 13
 NPRECIP = 4

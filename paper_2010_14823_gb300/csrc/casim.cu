@@ -25,6 +25,7 @@ using namespace casim_dev;
 
 struct casim_ctx {
   int precision = CASIM_FP64;
+  bool warm = false;   // CASIM_WARM: the warm configuration (liquid water only)
   int device = 0;
   int nsm = 1;
   KParams kp;
@@ -174,13 +175,14 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   if (!out) return CASIM_ERR_ARG;
   *out = nullptr;
   if (precision != CASIM_FP64 && precision != CASIM_MIXED) return CASIM_ERR_ARG;
-  if (flags != 0) return CASIM_ERR_ARG;
+  if ((flags & ~CASIM_WARM) != 0) return CASIM_ERR_ARG;
   casim_params p;
   if (params) p = *params;
   else casim_default_params(&p);
   if (!params_ok(p)) return CASIM_ERR_ARG;
   casim_ctx *ctx = new casim_ctx();
   ctx->precision = precision;
+  ctx->warm = (flags & CASIM_WARM) != 0;
   derive<double>(p, ctx->kp.d, ln_);
   derive<float>(p, ctx->kp.f, log2_);
   ctx->kp.c_max = p.c_max;
@@ -227,12 +229,19 @@ static KArgs make_args(const casim_ctx *ctx, const casim_state *s, int ncols, in
 static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, void *stream) {
   const dim3 grid((unsigned)((ncols + kBlock - 1) / kBlock));
   cudaStream_t st = (cudaStream_t)stream;
-  if (ctx->precision == CASIM_MIXED) {
-    if (tend) k_step<PolicyMix, true><<<grid, kBlock, 0, st>>>(a, ctx->kp, tend);
-    else k_step<PolicyMix, false><<<grid, kBlock, 0, st>>>(a, ctx->kp, nullptr);
+  const KParams &kp = ctx->kp;
+  if (ctx->precision == CASIM_MIXED && !ctx->warm) {
+    if (tend) k_step<PolicyMix, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
+    else k_step<PolicyMix, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+  } else if (ctx->precision == CASIM_MIXED) {
+    if (tend) k_step<PolicyMixWarm, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
+    else k_step<PolicyMixWarm, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+  } else if (!ctx->warm) {
+    if (tend) k_step<PolicyF64, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
+    else k_step<PolicyF64, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
   } else {
-    if (tend) k_step<PolicyF64, true><<<grid, kBlock, 0, st>>>(a, ctx->kp, tend);
-    else k_step<PolicyF64, false><<<grid, kBlock, 0, st>>>(a, ctx->kp, nullptr);
+    if (tend) k_step<PolicyF64Warm, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
+    else k_step<PolicyF64Warm, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
   }
   ctx->launches++;
   CUDA_TRY(cudaGetLastError());
@@ -466,7 +475,7 @@ extern "C" int casim_batch_create(casim_ctx *ctx, const casim_state *domains, co
                                   int ndom, casim_batch **out) {
   if (!out) return CASIM_ERR_ARG;
   *out = nullptr;
-  if (!ctx || ndom < 1 || !domains || !ncols || !nlev) return CASIM_ERR_ARG;
+  if (!ctx || ctx->warm || ndom < 1 || !domains || !ncols || !nlev) return CASIM_ERR_ARG;
   casim_batch *b = new casim_batch();
   b->ctx = ctx;
   b->ndom = ndom;
@@ -1178,7 +1187,7 @@ extern "C" int casim_mlp_loss_grad_host(casim_mlp *m, const float *Xn, const flo
 
 extern "C" int casim_mlp_data(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, float *X,
                               float *Y, float *M, long long *pts, long long cap, long long *rows, void *stream) {
-  if (!ctx || !X || !Y || !M || cap < 0 || !rows) return CASIM_ERR_ARG;
+  if (!ctx || ctx->warm || !X || !Y || !M || cap < 0 || !rows) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK) return rc;
   *rows = 0;
@@ -1290,7 +1299,7 @@ extern "C" int casim_mlp_set_norm(casim_mlp *m, const float *stats) {
 
 extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_state *s, int ncols, int nlev,
                                     double dt, void *stream, long long *served) {
-  if (!ctx || !m || !m->fitted || ctx->precision != CASIM_MIXED) return CASIM_ERR_ARG;
+  if (!ctx || ctx->warm || !m || !m->fitted || ctx->precision != CASIM_MIXED) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
   cudaStream_t st = (cudaStream_t)stream;

@@ -143,6 +143,8 @@ __device__ __forceinline__ unsigned nonfinite(double x) {
 struct PolicyF64 {
   using R = double;
   static constexpr bool kMixed = false;
+  static constexpr bool kWarm = false;
+  static constexpr int kMinBlocks = 3;   // resident blocks of kBlock per SM the step kernel is built for
   static __device__ __forceinline__ const ConstK<double> &K(const KParams &p) { return p.d; }
   static __device__ __forceinline__ R toR(double x) { return x; }
   static __device__ __forceinline__ double toD(R x) { return x; }
@@ -161,6 +163,8 @@ struct PolicyF64 {
 struct PolicyMix {
   using R = float;
   static constexpr bool kMixed = true;
+  static constexpr bool kWarm = false;
+  static constexpr int kMinBlocks = 5;   // measured: 4 / 5 / 6 -> 2.95 / 2.73 / 3.06 ms per 512x512x150 step
   static __device__ __forceinline__ const ConstK<float> &K(const KParams &p) { return p.f; }
   static __device__ __forceinline__ R toR(double x) { return d2f(x); }
   static __device__ __forceinline__ double toD(R x) { return f2d(x); }
@@ -297,7 +301,7 @@ struct Phys {
         r.evr = M::div(K.twopi * ((R)1 - Sw) * iv, rho * (Aw + Bw));
       }
     }
-    if (cold) {
+    if (!M::kWarm && cold) {
       const R esi = es_ice(K, w.Td, tc);
       const R qsi = qsat(K, esi, p);
       const R Si = M::div(qv, qsi);
@@ -318,7 +322,7 @@ struct Phys {
         if (m > 0 && hc) r.rim[m - 1] = X.rim * qc * dfac * rho * w.qx[m] * M::ex(X.exr * l);
       }
     }
-    if (warm) {
+    if (!M::kWarm && warm) {
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         if (!(w.qx[m] > K.qmin)) continue;
@@ -399,8 +403,8 @@ struct Phys {
 };
 
 // ------------------------------------------------------- FP64 form
-struct F64 {
-  using M = PolicyF64;
+template <class M>
+struct F64T {
   using P = Phys<M>;
 
   // true unless the chain leaves the point unchanged (no hydrometeor, not
@@ -410,8 +414,11 @@ struct F64 {
     const double qmin = K.qmin;
     es0 = P::es_liq(K, s.T - K.T0);
     qs0 = P::qsat(K, es0, s.p);
-    bool act = s.qc > qmin || s.qr > qmin || s.qi > qmin || s.qs > qmin || s.qg > qmin || s.qv > qs0;
-    if (!act && s.T < K.Tnuc) act = s.qv / P::qsat(K, P::es_ice(K, s.T, 0.0), s.p) > 1.0;
+    bool act = s.qc > qmin || s.qr > qmin || s.qv > qs0;
+    if constexpr (!M::kWarm) {
+      act = act || s.qi > qmin || s.qs > qmin || s.qg > qmin;
+      if (!act && s.T < K.Tnuc) act = s.qv / P::qsat(K, P::es_ice(K, s.T, 0.0), s.p) > 1.0;
+    }
     return act;
   }
 
@@ -501,6 +508,8 @@ struct F64 {
   }
 };
 
+using F64 = F64T<PolicyF64>;
+
 // ------------------------------------------------------- mixed form
 // Increments of one active point in FP32, applied to the FP64 state once.
 struct MixInc {
@@ -513,30 +522,41 @@ struct MixInc {
   float dna;       // aerosol number
 };
 
-struct Mix {
-  using M = PolicyMix;
+template <class M>
+struct MixT {
   using P = Phys<M>;
 
   // activity flag; fills the FP32 values it needs
   static __device__ __forceinline__ bool active(const ConstK<float> &K, const Pt &s, double T0d, W<float> &w,
                                                 float &es0, float &qs0) {
     w.Td = s.T;
-    w.hmax = max(max(max(hiabs(s.T), hiabs(s.p)), max(hiabs(s.qv), hiabs(s.qc))),
-                 max(max(hiabs(s.qr), hiabs(s.qi)), max(hiabs(s.qs), hiabs(s.qg))));
+    if constexpr (!M::kWarm) {
+      w.hmax = max(max(max(hiabs(s.T), hiabs(s.p)), max(hiabs(s.qv), hiabs(s.qc))),
+                   max(max(hiabs(s.qr), hiabs(s.qi)), max(hiabs(s.qs), hiabs(s.qg))));
+    } else {
+      w.hmax = max(max(hiabs(s.T), hiabs(s.p)), max(max(hiabs(s.qv), hiabs(s.qc)), hiabs(s.qr)));
+    }
     w.tc = d2f(s.T - T0d);
     w.T = d2f(s.T);
     w.p = d2f(s.p);
     w.qv = d2f(s.qv);
     w.qc = d2f(s.qc);
     w.qr = d2f(s.qr);
-    w.qx[0] = d2f(s.qi);
-    w.qx[1] = d2f(s.qs);
-    w.qx[2] = d2f(s.qg);
+    if constexpr (!M::kWarm) {
+      w.qx[0] = d2f(s.qi);
+      w.qx[1] = d2f(s.qs);
+      w.qx[2] = d2f(s.qg);
+    } else {
+      w.qx[0] = w.qx[1] = w.qx[2] = 0.f;
+    }
     es0 = P::es_liq(K, w.tc);
     qs0 = P::qsat(K, es0, w.p);
     const float qmin = K.qmin;
-    bool act = w.qc > qmin || w.qr > qmin || w.qx[0] > qmin || w.qx[1] > qmin || w.qx[2] > qmin || w.qv > qs0;
-    if (!act && w.T < K.Tnuc) act = __fdividef(w.qv, P::qsat(K, P::es_ice(K, s.T, w.tc), w.p)) > 1.f;
+    bool act = w.qc > qmin || w.qr > qmin || w.qv > qs0;
+    if constexpr (!M::kWarm) {
+      act = act || w.qx[0] > qmin || w.qx[1] > qmin || w.qx[2] > qmin;
+      if (!act && w.T < K.Tnuc) act = __fdividef(w.qv, P::qsat(K, P::es_ice(K, s.T, w.tc), w.p)) > 1.f;
+    }
     return act;
   }
 
@@ -555,12 +575,17 @@ struct Mix {
     w.rho = d2f(s.rho);
     w.nc = d2f(s.nc);
     w.nr = d2f(s.nr);
-    w.nx[0] = d2f(s.ni);
-    w.nx[1] = d2f(s.ns);
-    w.nx[2] = d2f(s.ng);
     const float na = d2f(s.na);
-    w.hmax = max(w.hmax, max(max(max(hiabs(s.rho), hiabs(s.w)), max(hiabs(s.nc), hiabs(s.nr))),
-                             max(max(hiabs(s.ni), hiabs(s.ns)), max(hiabs(s.ng), hiabs(s.na)))));
+    if constexpr (!M::kWarm) {
+      w.nx[0] = d2f(s.ni);
+      w.nx[1] = d2f(s.ns);
+      w.nx[2] = d2f(s.ng);
+      w.hmax = max(w.hmax, max(max(max(hiabs(s.rho), hiabs(s.w)), max(hiabs(s.nc), hiabs(s.nr))),
+                               max(max(hiabs(s.ni), hiabs(s.ns)), max(hiabs(s.ng), hiabs(s.na)))));
+    } else {
+      w.nx[0] = w.nx[1] = w.nx[2] = 0.f;
+      w.hmax = max(w.hmax, max(max(max(hiabs(s.rho), hiabs(s.w)), max(hiabs(s.nc), hiabs(s.nr))), hiabs(s.na)));
+    }
     o.vc = 0.f;
     o.evap_all = false;
     o.dT = 0.f;
@@ -683,13 +708,37 @@ struct Mix {
   }
 };
 
+using Mix = MixT<PolicyMix>;
+
+// The warm configuration (Section 2.1: liquid water only): ice species are
+// absent from the warm state -- their fields are neither read nor written, no
+// ice process runs and only rain sediments.
+struct PolicyF64Warm : PolicyF64 {
+  static constexpr bool kWarm = true;
+  static constexpr int kMinBlocks = 4;
+};
+struct PolicyMixWarm : PolicyMix {
+  static constexpr bool kWarm = true;
+  static constexpr int kMinBlocks = 6;
+};
+
 // ---------------------------------------------------------------- kernels
+template <bool kWarm = false>
 __device__ __forceinline__ void load_pt(const KArgs &a, int k, int c, Pt &s) {
   const double *b = a.fld + (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
   s.T = b[0 * fs]; s.qv = b[1 * fs]; s.qc = b[2 * fs]; s.qr = b[3 * fs];
-  s.qi = b[4 * fs]; s.qs = b[5 * fs]; s.qg = b[6 * fs];
-  s.nc = b[7 * fs]; s.nr = b[8 * fs]; s.ni = b[9 * fs]; s.ns = b[10 * fs]; s.ng = b[11 * fs];
+  if constexpr (!kWarm) {
+    s.qi = b[4 * fs]; s.qs = b[5 * fs]; s.qg = b[6 * fs];
+  } else {
+    s.qi = s.qs = s.qg = 0.0;
+  }
+  s.nc = b[7 * fs]; s.nr = b[8 * fs];
+  if constexpr (!kWarm) {
+    s.ni = b[9 * fs]; s.ns = b[10 * fs]; s.ng = b[11 * fs];
+  } else {
+    s.ni = s.ns = s.ng = 0.0;
+  }
   s.na = b[12 * fs];
   s.p = __ldg(b + 13 * fs); s.rho = __ldg(b + 14 * fs); s.w = __ldg(b + 15 * fs);
 }
@@ -715,16 +764,35 @@ __device__ __forceinline__ unsigned store_pt(const KArgs &a, int k, int c, const
          nonfinite(s.ns) | nonfinite(s.ng) | nonfinite(s.na);
 }
 
+// the warm configuration's fields only
+__device__ __forceinline__ unsigned store_pt_warm(const KArgs &a, int k, int c, const Pt &s) {
+  double *b = a.fld + (size_t)k * a.pitch + c;
+  const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
+  b[0 * fs] = s.T; b[1 * fs] = s.qv; b[2 * fs] = s.qc; b[3 * fs] = s.qr;
+  b[7 * fs] = s.nc; b[8 * fs] = s.nr; b[12 * fs] = s.na;
+  return nonfinite(s.T) | nonfinite(s.qv) | nonfinite(s.qc) | nonfinite(s.qr) | nonfinite(s.nc) |
+         nonfinite(s.nr) | nonfinite(s.na);
+}
+
 // Tendency mode (the state is left unchanged): in the single-substep path
 // the source terms (x_new - x_old) / dt go straight to tend (x_old re-read
 // from the state, still in cache); in the multi-substep path the new values
 // go to tend as scratch for the substep sweeps and are converted afterwards.
+// (warm configuration: zero source terms for the ice fields)
+template <bool kWarm>
 __device__ __forceinline__ unsigned store_tend(const KArgs &a, double *tend, int k, int c, const Pt &s, bool fast) {
   const size_t o = (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
   const double v[13] = {s.T, s.qv, s.qc, s.qr, s.qi, s.qs, s.qg, s.nc, s.nr, s.ni, s.ns, s.ng, s.na};
 #pragma unroll
-  for (int f = 0; f < 13; ++f) tend[f * fs + o] = fast ? (v[f] - a.fld[f * fs + o]) / a.dt : v[f];
+  for (int f = 0; f < 13; ++f) {
+    const bool ice = (f >= 4 && f <= 6) || (f >= 9 && f <= 11);
+    if (kWarm && ice) {
+      tend[f * fs + o] = 0.0;   // zero source term (the conversion pass skips these)
+    } else {
+      tend[f * fs + o] = fast ? (v[f] - a.fld[f * fs + o]) / a.dt : v[f];
+    }
+  }
   return nonfinite(s.T) | nonfinite(s.qv) | nonfinite(s.qc) | nonfinite(s.qr) | nonfinite(s.qi) |
          nonfinite(s.qs) | nonfinite(s.qg) | nonfinite(s.nc) | nonfinite(s.nr) | nonfinite(s.ni) |
          nonfinite(s.ns) | nonfinite(s.ng) | nonfinite(s.na);
@@ -781,7 +849,8 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
   const double *rhop = a.fld + 14 * fs;
   double *state = kTend ? tend : a.fld;   // the processed state (tendency mode: scratch)
-  for (int x = 0; x < 4; ++x) {
+  constexpr int kSed = M::kWarm ? 1 : 4;   // sedimenting species: r (warm) or r, i, s, g
+  for (int x = 0; x < kSed; ++x) {
     double *qp = state + (3 + x) * fs;
     double *np = state + (8 + x) * fs;
     R cmax = 0;
@@ -854,24 +923,25 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
   using Ph = Phys<M>;
   const ConstK<R> &K = M::K(P);
   unsigned eflag = 0;
+  constexpr int kSed = M::kWarm ? 1 : 4;   // sedimenting species: r (warm) or r, i, s, g
   double prec[4] = {0.0, 0.0, 0.0, 0.0};
   // carried downward fluxes F_{k+1}, G_{k+1} (kg m^-2 s^-1, m^-2 s^-1)
   R Fq[4] = {0, 0, 0, 0}, Fn[4] = {0, 0, 0, 0};
 
   for (int k = a.nlev - 1; k >= 0; --k) {
     Pt s;
-    load_pt(a, k, c, s);
+    load_pt<M::kWarm>(a, k, c, s);
     bool touched;
     if constexpr (!M::kMixed) {
       eflag |= nonfinite_in(s);
       double es0, qs0;
-      touched = F64::active(K, s, es0, qs0);
-      if (touched) F64::process(K, s, a.dt, es0, qs0);
+      touched = F64T<M>::active(K, s, es0, qs0);
+      if (touched) F64T<M>::process(K, s, a.dt, es0, qs0);
       if (fast) {
         const double dzk = sdz[k];
         const double dfac = ::exp(0.4 * (K.lgrho0 - ::log(s.rho)));
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int x = 0; x < kSed; ++x) {
           double &q = qref(s, x);
           double &n = nref(s, x);
           double F = 0, G = 0;
@@ -893,13 +963,13 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
     } else {
       W<float> w;
       float es0, qs0;
-      const bool act = Mix::active(K, s, P.T0, w, es0, qs0);
+      const bool act = MixT<M>::active(K, s, P.T0, w, es0, qs0);
       MixInc o;
       float dn[4] = {0.f, 0.f, 0.f, 0.f};   // number increments of r, i, s, g
       float qpost[4], npost[4];
       if (act) {
-        Mix::process(K, s, a.dt, w, es0, qs0, o, a.surr ? a.surr + (size_t)k * a.pitch + c : nullptr);
-        Mix::apply_masses(s, o);
+        MixT<M>::process(K, s, a.dt, w, es0, qs0, o, a.surr ? a.surr + (size_t)k * a.pitch + c : nullptr);
+        MixT<M>::apply_masses(s, o);
         if (o.dn[0] != 0.f) s.nc += f2d(o.dn[0]);
 #pragma unroll
         for (int x = 0; x < 4; ++x) dn[x] = o.dn[1 + x];
@@ -923,7 +993,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       if (fast) {
         bool any = false;
 #pragma unroll
-        for (int x = 0; x < 4; ++x) any |= qpost[x] > K.qmin || Fq[x] != 0.f || Fn[x] != 0.f;
+        for (int x = 0; x < kSed; ++x) any |= qpost[x] > K.qmin || Fq[x] != 0.f || Fn[x] != 0.f;
         if (any) {
           if (!act) w.hmax = max(w.hmax, hiabs(s.rho));
           const float rho = act ? w.rho : d2f(s.rho);
@@ -931,7 +1001,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
           const float sc = __fdividef(d2f(a.dt), rho * d2f(sdz[k]));
           const float guard = d2f(sdzdt[k]);
 #pragma unroll
-          for (int x = 0; x < 4; ++x) {
+          for (int x = 0; x < kSed; ++x) {
             float F = 0.f, G = 0.f;
             if (qpost[x] > K.qmin) {
               const float n = act ? npost[x] : d2f(nref(s, x));
@@ -954,19 +1024,21 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
         }
       }
 #pragma unroll
-      for (int x = 0; x < 4; ++x)
+      for (int x = 0; x < kSed; ++x)
         if (dn[x] != 0.f) nref(s, x) += f2d(dn[x]);
       eflag |= w.hmax >= 0x7ff00000u;
     }
     if constexpr (kTend) {
-      eflag |= store_tend(a, tend, k, c, s, fast);
+      eflag |= store_tend<M::kWarm>(a, tend, k, c, s, fast);
+    } else if constexpr (M::kWarm) {
+      if (touched) eflag |= store_pt_warm(a, k, c, s);
     } else {
       if (touched) eflag |= store_pt(a, k, c, s);
     }
   }
   if (fast) {
 #pragma unroll
-    for (int x = 0; x < 4; ++x) prec[x] = M::toD(Fq[x]) * a.dt;
+    for (int x = 0; x < kSed; ++x) prec[x] = M::toD(Fq[x]) * a.dt;
   } else {
     eflag |= sediment_substeps<M, kTend>(a, P, sdz, c, prec, tend);
     if constexpr (kTend) {
@@ -975,12 +1047,15 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       for (int k = 0; k < a.nlev; ++k) {
         const size_t o = (size_t)k * a.pitch + c;
 #pragma unroll
-        for (int f = 0; f < 13; ++f) tend[f * fs + o] = (tend[f * fs + o] - a.fld[f * fs + o]) / a.dt;
+        for (int f = 0; f < 13; ++f) {
+          const bool ice = (f >= 4 && f <= 6) || (f >= 9 && f <= 11);
+          if (!(M::kWarm && ice)) tend[f * fs + o] = (tend[f * fs + o] - a.fld[f * fs + o]) / a.dt;
+        }
       }
     }
   }
 #pragma unroll
-  for (int x = 0; x < 4; ++x) {
+  for (int x = 0; x < kSed; ++x) {
     if (prec[x] != 0.0) {
       double *pp = a.precip + (size_t)x * a.pitch + c;
       *pp += prec[x];
@@ -992,7 +1067,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
 
 // kTend: tendency mode (tend receives the source terms, a.fld unchanged)
 template <class M, bool kTend>
-__global__ void __launch_bounds__(kBlock, M::kMixed ? 5 : 3) k_step(const KArgs a, const KParams P, double *tend) {
+__global__ void __launch_bounds__(kBlock, M::kMinBlocks) k_step(const KArgs a, const KParams P, double *tend) {
   __shared__ Smem sm;
   const bool fast = prologue(a, P, sm);
   const int c = blockIdx.x * kBlock + threadIdx.x;

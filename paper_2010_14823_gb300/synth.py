@@ -173,12 +173,14 @@ def workload(name: str, ncols: int | None = None, nlev: int | None = None, seed:
     stratus_16x16x50        16x16 columns x 50 levels, dz = 100 m, dt = 1 s, 1 step
     stratus_256x256x100     256x256 x 100 stretched 20-200 m, 30% cloudy, 10 steps
     deep_512x512x150        512x512 x 150 stretched, deep convection, 100 steps
+    stratus_512x512x150     512x512 x 150 stretched, 30% cloudy stratus (warm vs cold configuration)
     ``ncols`` / ``nlev`` override the sizes (same recipe) for sub-sampled runs.
     """
     table = {
         "stratus_16x16x50": ("stratus", 256, 50, "uniform", 1.0, 1, 1234),
         "stratus_256x256x100": ("stratus_broken", 65536, 100, "stretched", 1.0, 10, 1235),
         "deep_512x512x150": ("deep_convective", 262144, 150, "stretched", 1.0, 100, 1236),
+        "stratus_512x512x150": ("stratus_broken", 262144, 150, "stretched", 1.0, 100, 1238),
     }
     recipe, nc, nl, dzk, dt, nsteps, sd = table[name]
     nc = nc if ncols is None else ncols

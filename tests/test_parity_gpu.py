@@ -18,8 +18,8 @@ RTOL64 = 1e-12
 ATOL = np.array([1e-10] + [1e-20] * 6 + [1e-6] * 6)   # T, 6 masses, 6 numbers (incl. n_a)
 
 
-def run_gpu(fld, dz, ncols, dt, nsteps=1, precision=casim.CASIM_FP64, check_err=True):
-    ctx = casim.casim_init(precision=precision)
+def run_gpu(fld, dz, ncols, dt, nsteps=1, precision=casim.CASIM_FP64, check_err=True, flags=0):
+    ctx = casim.casim_init(precision=precision, flags=flags)
     try:
         d = casim.Domain(fld, dz, ncols)
         for _ in range(nsteps):
@@ -33,11 +33,11 @@ def run_gpu(fld, dz, ncols, dt, nsteps=1, precision=casim.CASIM_FP64, check_err=
         casim.casim_free(ctx)
 
 
-def run_oracle(fld, dz, ncols, dt, nsteps=1):
+def run_oracle(fld, dz, ncols, dt, nsteps=1, warm=False):
     ref = fld.copy()
     pr = np.zeros((4, fld.shape[2]))
     for _ in range(nsteps):
-        _, _, err = O.step(ref, ncols, dz, dt, precip=pr)
+        _, _, err = O.step(ref, ncols, dz, dt, precip=pr, warm=warm)
         assert err == 0
     return ref, pr
 
@@ -284,3 +284,86 @@ def test_mixed_conserves_water():
     drift = np.abs(w1 + pr[:, :512].sum(0) - w0) / w0
     # processes conserve to FP64 rounding; sedimentation increments carry FP32 rounding
     assert drift.max() < 1e-9, drift.max()
+
+
+# ------------------------------------------------------------------ warm configuration
+ICE = [F[x] for x in ("qi", "qs", "qg", "ni", "ns", "ng")]
+
+
+@pytest.mark.parametrize("dt", [1.0, 30.0])
+def test_warm_fp64_matches_oracle_and_leaves_ice(dt):
+    """The warm configuration on a deep-convective state that carries ice:
+    liquid fields within 1e-11 of the oracle's warm mode, ice fields bitwise
+    untouched, no ice, snow or graupel precipitation.  dt = 1 s over three
+    steps; dt = 30 s (the multi-substep path) over one: in its first step the
+    limiter exhausts some cloud-droplet pools, leaving numbers that are the
+    rounding residue of n - n (e.g. 7e-9 /kg from 3.4e8), which FMA rounds
+    differently, and later steps branch on that residue."""
+    nlev = 150
+    dz = synth.dz_stretched(nlev)
+    ncols = 97
+    nsteps = 3 if dt == 1.0 else 1
+    fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=41)
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, nsteps=nsteps, flags=casim.CASIM_WARM)
+    ref, pr_ref = run_oracle(fld, dz, ncols, dt, nsteps=nsteps, warm=True)
+    assert_fp64_close(out, pr, ref, pr_ref, ncols, rtol=1e-11)
+    for f in ICE:
+        assert np.array_equal(out[f], fld[f])
+    assert np.all(pr[1:] == 0.0)
+
+
+def test_warm_mixed_within_derived_bound():
+    nlev = 150
+    dz = synth.dz_stretched(nlev)
+    fld = synth.make_state("deep_convective", 512, nlev, dz, seed=42)
+    out, pr, _ = run_gpu(fld, dz, 512, 1.0, precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM)
+    ref, pr_ref = run_oracle(fld, dz, 512, 1.0, warm=True)
+    for f in range(13):
+        a, b, i = out[f, :, :512], ref[f, :, :512], fld[f, :, :512]
+        bound = mixed_bound(b, i, f, ref[1, :, :512])
+        assert (np.abs(a - b) <= bound).all(), synth.FIELDS[f]
+    for f in ICE:
+        assert np.array_equal(out[f], fld[f])
+
+
+def test_warm_equals_cold_on_an_ice_free_warm_state():
+    """Both configurations against the oracle on a state without ice and
+    warmer than the nucleation threshold, where the two chains coincide."""
+    fld, dz, ncols, nlev, dt, _ = synth.workload("stratus_16x16x50")
+    top = int(np.argmax(fld[F["T"], :, :ncols].min(axis=1) < O.param("T_nuc") + 1.0))
+    sub = np.ascontiguousarray(fld[:, :top, :])
+    sub[ICE] = 0.0
+    dzs = np.ascontiguousarray(dz[:top])
+    cold, pc, _ = run_gpu(sub, dzs, ncols, dt)
+    warm, pw, _ = run_gpu(sub, dzs, ncols, dt, flags=casim.CASIM_WARM)
+    ref, pr_ref = run_oracle(sub, dzs, ncols, dt)
+    assert_fp64_close(cold, pc, ref, pr_ref, ncols)
+    assert_fp64_close(warm, pw, ref, pr_ref, ncols)
+
+
+@pytest.mark.parametrize("dt", [1.0, 30.0])
+def test_warm_tendency_and_host_entry_points(dt):
+    import torch
+    nlev = 150
+    dz = synth.dz_stretched(nlev)
+    ncols, pitch = 200, 224
+    fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=43, pitch=pitch)
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM)
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM)
+    try:
+        d = casim.Domain(fld, dz, ncols)
+        tend = torch.full((13, nlev, pitch), float("nan"), dtype=torch.float64, device="cuda")
+        casim.casim_step_tendency(ctx, d.state, ncols, nlev, dt, tend)
+        assert casim.casim_get_error(ctx)[0] == 0
+        t = tend.cpu().numpy()[:, :, :ncols]
+        assert np.array_equal(t, (out[:13, :, :ncols] - fld[:13, :, :ncols]) / dt)
+        assert np.all(t[ICE] == 0.0)
+        h = np.ascontiguousarray(fld.copy())
+        hpr = np.zeros((4, pitch))
+        casim.casim_step_host(ctx, casim.make_state(h, pitch, np.ascontiguousarray(dz), hpr), ncols, nlev, dt)
+        assert np.array_equal(h, out) and np.array_equal(hpr, pr)
+        # entry points without a warm variant refuse a warm context
+        with pytest.raises(RuntimeError):
+            casim.casim_batch_create(ctx, [d.state], [ncols], [nlev])
+    finally:
+        casim.casim_free(ctx)
