@@ -20,6 +20,8 @@ _LIB = os.path.join(_HERE, "libcasim_oracle.so")
 
 NFIELDS = 16
 NPROG = 13
+NFIELDS_AERO = 19      # + free aerosol mass, aerosol mass in cloud, in rain
+NPROG_AERO = 16
 NPROC = 14
 SPECIES = {"c": 0, "r": 1, "i": 2, "s": 3, "g": 4}
 PROCS = ("aut", "acc", "scc", "scr", "evr", "nuc", "depi", "deps", "depg",
@@ -85,6 +87,10 @@ def lib():
         L.orc_point_cfg.argtypes = [pd, d, pd, i]
         L.orc_rates_cfg.restype = None
         L.orc_rates_cfg.argtypes = [pd, d, pd, i]
+        L.orc_point_aero.restype = None
+        L.orc_point_aero.argtypes = [pd, d, pd]
+        L.orc_step_aero.restype = u
+        L.orc_step_aero.argtypes = [pd, ctypes.c_long, i, i, pd, pd, d, i]
         L.orc_param.restype = d
         L.orc_param.argtypes = [ctypes.c_char_p]
         L.orc_max_threads.restype = i
@@ -219,3 +225,26 @@ def adjust_activate(state: np.ndarray) -> np.ndarray:
     out = np.zeros(NFIELDS)
     lib().orc_adjust_activate(_dp(st), _dp(out))
     return out
+
+
+def point_aero(state: np.ndarray, dt: float) -> np.ndarray:
+    """Warm point with activated-aerosol mass: state[19] -> [13 prognostic, ma, mac, mar]."""
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    assert st.shape == (NFIELDS_AERO,)
+    out = np.zeros(NPROG_AERO)
+    lib().orc_point_aero(_dp(st), dt, _dp(out))
+    return out
+
+
+def step_aero(fld: np.ndarray, ncols: int, dz: np.ndarray, dt: float, precip: np.ndarray | None = None,
+              nthreads: int = 0):
+    """Warm step with activated-aerosol mass, in place on fld [19][nlev][pitch];
+    precip [5][pitch] (r, i, s, g, aerosol) accumulated.  Returns (precip, err)."""
+    assert fld.dtype == np.float64 and fld.flags["C_CONTIGUOUS"] and fld.shape[0] == NFIELDS_AERO
+    nlev, pitch = fld.shape[1], fld.shape[2]
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    if precip is None:
+        precip = np.zeros((5, pitch))
+    assert precip.shape == (5, pitch) and precip.dtype == np.float64 and precip.flags["C_CONTIGUOUS"]
+    err = lib().orc_step_aero(_dp(fld), pitch, ncols, nlev, _dp(dz), _dp(precip), dt, nthreads)
+    return precip, err

@@ -335,7 +335,15 @@ void orc_adjust_activate(const double *in, double *st) {
 
 static const int ICE_FIELDS[6] = {ORC_QI, ORC_QS, ORC_QG, ORC_NI, ORC_NS, ORC_NG};
 
-void orc_point_cfg(const double *in0, double dt, double *out, int warm) {
+/* what the aerosol-mass bookkeeping needs from one point's step */
+typedef struct {
+  double qc0, evap;         /* cloud before adjustment; cloud evaporated by it (>= 0) */
+  double na0, dn_act;       /* free aerosol number before activation; droplets activated */
+  double qc_post, qr_post;  /* cloud and rain after activation (what the rates see) */
+  double tau_cr, tau_rv;    /* cloud -> rain (autoconversion + accretion), rain -> vapour */
+} orc_record;
+
+static void point_core(const double *in0, double dt, double *out, int warm, orc_record *rec) {
   /* warm: the ice fields are not part of the warm state; they are treated as
      absent and passed through unchanged */
   double in[ORC_NFIELDS];
@@ -344,6 +352,18 @@ void orc_point_cfg(const double *in0, double dt, double *out, int warm) {
     for (int i = 0; i < 6; ++i) in[ICE_FIELDS[i]] = 0.0;
   double st[ORC_NFIELDS];
   orc_adjust_activate(in, st);
+  if (rec) {
+    /* the adjustment changes T, qv, qc only; activation nc and na only */
+    double T = in[ORC_T], qv = in[ORC_QV], qc = in[ORC_QC];
+    orc_satadj(in[ORC_P], &T, &qv, &qc);
+    rec->qc0 = in[ORC_QC];
+    rec->evap = in[ORC_QC] > qc ? in[ORC_QC] - qc : 0.0;
+    rec->na0 = in[ORC_NA];
+    rec->dn_act = in[ORC_NA] - st[ORC_NA];
+    rec->qc_post = st[ORC_QC];
+    rec->qr_post = st[ORC_QR];
+    rec->tau_cr = rec->tau_rv = 0.0;
+  }
 
   /* a4..a9 from the post-activation state */
   double R[ORC_NPROC];
@@ -408,6 +428,8 @@ void orc_point_cfg(const double *in0, double dt, double *out, int warm) {
       st[tr[j].msrc] -= tau;
       st[tr[j].mdst] += tau;
       st[ORC_T] += tau * tr[j].heat / CP;
+      if (rec && (j == 0 || j == 1)) rec->tau_cr += tau;   /* autoconversion, accretion */
+      if (rec && j == 4) rec->tau_rv += tau;               /* rain evaporation */
     }
     if (tr[j].nsink > 0.0) st[tr[j].nsrc] -= g * tr[j].nsink * dt;
     if (tr[j].ndst >= 0 && tr[j].nsource > 0.0) st[tr[j].ndst] += g * tr[j].nsource * dt;
@@ -417,22 +439,71 @@ void orc_point_cfg(const double *in0, double dt, double *out, int warm) {
   memcpy(out, st, ORC_NPROG * sizeof(double));
 }
 
+void orc_point_cfg(const double *in, double dt, double *out, int warm) { point_core(in, dt, out, warm, NULL); }
+
 void orc_rates(const double *st, double dt, double *R) { orc_rates_cfg(st, dt, R, 0); }
 
 void orc_point(const double *in, double dt, double *out) { orc_point_cfg(in, dt, out, 0); }
 
+/* Activated-aerosol mass (Section 2: once activated, aerosol mass is carried
+   in the cloud and returned to the air when the water evaporates).  Three
+   mass mixing ratios -- free aerosol ma, aerosol in cloud droplets mac, in
+   rain mac -- move with the water in the warm configuration:
+     a2 the cloud the adjustment evaporates returns its share of mac to ma;
+     a3 activated droplets take the free aerosol's mean particle mass,
+        ma dn / na (na before activation);
+     a4 autoconversion and accretion carry mac into rain in proportion to the
+        cloud water they move (fraction of the post-activation cloud);
+     a5 rain evaporation returns mar to ma in proportion to the rain it
+        evaporates;
+     a12 mar sediments with the rain's mass-weighted fall speed.
+   Water, numbers and temperature are those of the warm step, unchanged.
+   in[ORC_NFIELDS_AERO] -> out[ORC_NPROG_AERO]. */
+void orc_point_aero(const double *in, double dt, double *out) {
+  orc_record r;
+  double o[ORC_NPROG];
+  point_core(in, dt, o, 1, &r);
+  memcpy(out, o, sizeof o);
+  double ma = in[ORC_MA], mac = in[ORC_MAC], mar = in[ORC_MAR], d;
+  if (r.evap > 0.0 && r.qc0 > 0.0) {
+    d = r.evap >= r.qc0 ? mac : mac * (r.evap / r.qc0);
+    mac -= d;
+    ma += d;
+  }
+  if (r.dn_act > 0.0 && r.na0 > 0.0) {
+    d = ma * (r.dn_act / r.na0);
+    ma -= d;
+    mac += d;
+  }
+  if (r.tau_cr > 0.0 && r.qc_post > 0.0) {
+    d = r.tau_cr >= r.qc_post ? mac : mac * (r.tau_cr / r.qc_post);
+    mac -= d;
+    mar += d;
+  }
+  if (r.tau_rv > 0.0 && r.qr_post > 0.0) {
+    d = r.tau_rv >= r.qr_post ? mar : mar * (r.tau_rv / r.qr_post);
+    mar -= d;
+    ma += d;
+  }
+  out[ORC_NPROG + 0] = ma;
+  out[ORC_NPROG + 1] = mac;
+  out[ORC_NPROG + 2] = mar;
+}
+
 /* ------------------------------------------------------ a12 sedimentation */
 static unsigned sediment_species(double *q, double *n, const double *rho, const double *dz, int nlev, double dt,
-                                 double *precip, int *nsub, int nspecies);
+                                 double *precip, int *nsub, int nspecies, double *aer, double *aprecip);
 
 unsigned orc_sediment_column(double *q, double *n, const double *rho, const double *dz,
                              int nlev, double dt, double *precip, int *nsub) {
-  return sediment_species(q, n, rho, dz, nlev, dt, precip, nsub, 4);
+  return sediment_species(q, n, rho, dz, nlev, dt, precip, nsub, 4, NULL, NULL);
 }
 
-/* the first nspecies of r, i, s, g (warm configuration: rain only) */
+/* the first nspecies of r, i, s, g (warm configuration: rain only); aer (may
+   be NULL): aerosol mass in rain, moved with the rain's mass-weighted speed,
+   its surface flux accumulated in *aprecip */
 static unsigned sediment_species(double *q, double *n, const double *rho, const double *dz, int nlev, double dt,
-                                 double *precip, int *nsub, int nspecies) {
+                                 double *precip, int *nsub, int nspecies, double *aer, double *aprecip) {
   /* For x in r, i, s, g: F_k = rho_k q_k Vq_k (mass), G_k = rho_k n_k Vn_k
      (number), fluxes downward.  Per substep of length dt/n_sub, with all
      fluxes taken from the substep's starting state:
@@ -446,6 +517,7 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
   unsigned err = 0;
   double *F = (double *)malloc(sizeof(double) * (size_t)(nlev + 1));
   double *G = (double *)malloc(sizeof(double) * (size_t)(nlev + 1));
+  double *A = (double *)malloc(sizeof(double) * (size_t)(nlev + 1));
   for (int m = 0; m < nspecies; ++m) {
     int sp = spx[m];
     double *qq = q + (size_t)m * nlev, *nn = n + (size_t)m * nlev;
@@ -462,9 +534,11 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
     if (nsub) nsub[m] = ns;
     double dts = dt / ns;
     for (int s = 0; s < ns; ++s) {
+      const int with_aer = aer != NULL && m == 0;
       for (int k = 0; k < nlev; ++k) {
         F[k] = 0.0;
         G[k] = 0.0;
+        A[k] = 0.0;
         if (qq[k] > QMIN) {
           double lam = orc_lambda(sp, qq[k], nn[k]);
           /* a level never loses more than it holds within one substep: the
@@ -476,39 +550,53 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
           if (vn > vlim) vn = vlim;
           F[k] = rho[k] * qq[k] * vq;
           G[k] = rho[k] * (nn[k] > 0.0 ? nn[k] : 0.0) * vn;
+          if (with_aer) A[k] = rho[k] * aer[k] * vq;
         }
       }
       F[nlev] = 0.0;
       G[nlev] = 0.0;
+      A[nlev] = 0.0;
       for (int k = 0; k < nlev; ++k) {
         qq[k] += dts * (F[k + 1] - F[k]) / (rho[k] * dz[k]);
         nn[k] += dts * (G[k + 1] - G[k]) / (rho[k] * dz[k]);
+        if (with_aer) aer[k] += dts * (A[k + 1] - A[k]) / (rho[k] * dz[k]);
       }
       precip[m] += F[0] * dts;
+      if (with_aer) *aprecip += A[0] * dts;
     }
   }
   free(F);
   free(G);
+  free(A);
   return err;
 }
 
 /* ----------------------------------------------------------- full step */
+/* aero: the state has ORC_NFIELDS_AERO fields and precip 5 rows (warm only) */
 static unsigned step_column(double *fld, long pitch, int nlev, int c, const double *dz,
-                            double *precip, int *nsub, double dt, int warm) {
+                            double *precip, int *nsub, double dt, int warm, int aero) {
   unsigned err = 0;
   long fs = (long)nlev * pitch; /* field stride */
-  double in[ORC_NFIELDS], out[ORC_NPROG];
+  const int nfields = aero ? ORC_NFIELDS_AERO : ORC_NFIELDS;
+  double in[ORC_NFIELDS_AERO], out[ORC_NPROG_AERO];
+  const int map[ORC_NPROG_AERO] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, ORC_MA, ORC_MAC, ORC_MAR};
   for (int k = 0; k < nlev; ++k) {
-    for (int f = 0; f < ORC_NFIELDS; ++f) in[f] = fld[f * fs + (long)k * pitch + c];
-    orc_point_cfg(in, dt, out, warm);
-    for (int f = 0; f < ORC_NPROG; ++f) fld[f * fs + (long)k * pitch + c] = out[f];
+    for (int f = 0; f < nfields; ++f) in[f] = fld[f * fs + (long)k * pitch + c];
+    if (aero) {
+      orc_point_aero(in, dt, out);
+      for (int f = 0; f < ORC_NPROG_AERO; ++f) fld[map[f] * fs + (long)k * pitch + c] = out[f];
+    } else {
+      orc_point_cfg(in, dt, out, warm);
+      for (int f = 0; f < ORC_NPROG; ++f) fld[f * fs + (long)k * pitch + c] = out[f];
+    }
   }
-  double *buf = (double *)malloc(sizeof(double) * (size_t)(9 * nlev));
-  double *q = buf, *n = buf + 4 * nlev, *rho = buf + 8 * nlev;
+  double *buf = (double *)malloc(sizeof(double) * (size_t)(10 * nlev));
+  double *q = buf, *n = buf + 4 * nlev, *rho = buf + 8 * nlev, *aer = buf + 9 * nlev;
   static const int qf[4] = {ORC_QR, ORC_QI, ORC_QS, ORC_QG};
   static const int nf[4] = {ORC_NR, ORC_NI, ORC_NS, ORC_NG};
   for (int k = 0; k < nlev; ++k) {
     rho[k] = fld[ORC_RHO * fs + (long)k * pitch + c];
+    aer[k] = aero ? fld[ORC_MAR * fs + (long)k * pitch + c] : 0.0;
     for (int m = 0; m < 4; ++m) {
       q[m * nlev + k] = fld[qf[m] * fs + (long)k * pitch + c];
       n[m * nlev + k] = fld[nf[m] * fs + (long)k * pitch + c];
@@ -517,7 +605,12 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
   double pr[4] = {0.0, 0.0, 0.0, 0.0};
   int ns[4] = {1, 1, 1, 1};
   const int nsp = warm ? 1 : 4;
-  err |= sediment_species(q, n, rho, dz, nlev, dt, pr, ns, nsp);
+  double apr = 0.0;
+  err |= sediment_species(q, n, rho, dz, nlev, dt, pr, ns, nsp, aero ? aer : NULL, &apr);
+  if (aero) {
+    for (int k = 0; k < nlev; ++k) fld[ORC_MAR * fs + (long)k * pitch + c] = aer[k];
+    precip[4 * pitch + c] += apr;
+  }
   for (int k = 0; k < nlev; ++k)
     for (int m = 0; m < nsp; ++m) {
       fld[qf[m] * fs + (long)k * pitch + c] = q[m * nlev + k];
@@ -528,9 +621,13 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
     if (nsub) nsub[m * pitch + c] = ns[m];
   }
   free(buf);
-  for (int k = 0; k < nlev; ++k)
+  for (int k = 0; k < nlev; ++k) {
     for (int f = 0; f < ORC_NPROG; ++f)
       if (!isfinite(fld[f * fs + (long)k * pitch + c])) err |= ORC_ERR_NONFINITE;
+    if (aero)
+      for (int f = ORC_MA; f <= ORC_MAR; ++f)
+        if (!isfinite(fld[f * fs + (long)k * pitch + c])) err |= ORC_ERR_NONFINITE;
+  }
   return err;
 }
 
@@ -542,7 +639,20 @@ unsigned orc_step_cfg(double *fld, long pitch, int ncols, int nlev, const double
   if (nthreads <= 0) nthreads = omp_get_max_threads();
 #pragma omp parallel for schedule(guided) num_threads(nthreads) reduction(| : err)
 #endif
-  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, nsub, dt, warm);
+  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, nsub, dt, warm, 0);
+  (void)nthreads;
+  return err;
+}
+
+unsigned orc_step_aero(double *fld, long pitch, int ncols, int nlev, const double *dz,
+                       double *precip, double dt, int nthreads) {
+  unsigned err = 0;
+  if (nlev <= 0 || ncols <= 0) return 0;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(guided) num_threads(nthreads) reduction(| : err)
+#endif
+  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, NULL, dt, 1, 1);
   (void)nthreads;
   return err;
 }

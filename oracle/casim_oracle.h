@@ -27,6 +27,11 @@ enum {
   ORC_P, ORC_RHO, ORC_W, ORC_NFIELDS
 };
 #define ORC_NPROG 13
+/* Activated-aerosol mass extension (warm configuration): three more fields
+   after the 16 above -- free aerosol mass ma, aerosol mass in cloud mac and in
+   rain mar (kg/kg) -- and a fifth precipitation row (aerosol deposited). */
+enum { ORC_MA = ORC_NFIELDS, ORC_MAC, ORC_MAR, ORC_NFIELDS_AERO };
+#define ORC_NPROG_AERO (ORC_NPROG + 3)
 
 /* Hydrometeor species index. */
 enum { ORC_C = 0, ORC_R, ORC_I, ORC_S, ORC_G, ORC_NSPECIES };
@@ -80,6 +85,14 @@ void   orc_rates_cfg(const double *st, double dt, double *rates, int warm);
 void   orc_point_cfg(const double *in, double dt, double *out, int warm);
 unsigned orc_step_cfg(double *fld, long pitch, int ncols, int nlev, const double *dz,
                       double *precip, int *nsub, double dt, int nthreads, int warm);
+/* The warm configuration with activated-aerosol mass: in[ORC_NFIELDS_AERO]
+   -> out[ORC_NPROG_AERO] (the 13 prognostic fields, then ma, mac, mar); and a
+   step over fld[ORC_NFIELDS_AERO][nlev][pitch] with precip[5][pitch] (r, i,
+   s, g, aerosol).  The first 16 fields and 4 precipitation rows are exactly
+   those of orc_step_cfg(..., warm = 1). */
+void   orc_point_aero(const double *in, double dt, double *out);
+unsigned orc_step_aero(double *fld, long pitch, int ncols, int nlev, const double *dz,
+                       double *precip, double dt, int nthreads);
 /* Parameter lookup by name for the tests (returns NaN for an unknown name). */
 double orc_param(const char *name);
 int    orc_max_threads(void);
