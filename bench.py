@@ -368,6 +368,31 @@ def bench_warm(args, rank, world, local):
     cold_ms, _, _ = run(casim.CASIM_MIXED, 0, args.steps, args.warmup)
     w64_ms, _, _ = run(casim.CASIM_FP64, casim.CASIM_WARM, args.fp64_steps, 1)
     c64_ms, _, _ = run(casim.CASIM_FP64, 0, args.fp64_steps, 1)
+    # the warm step with activated-aerosol mass: 19 fields (free aerosol
+    # ~100 cm^-3 of 0.05 um particles; aerosol in cloud and rain at 1e-5 of
+    # their water)
+    aero = torch.zeros((19, nlev, dom.pitch), dtype=torch.float64, device=dom.fld.device)
+    aero[:16] = fld0
+    aero[16] = 3e-9
+    aero[17] = 1e-5 * fld0[2]
+    aero[18] = 1e-5 * fld0[3]
+    adom = casim.Domain(aero, dz, ncols)
+    del aero
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM | casim.CASIM_AEROSOL)
+    for _ in range(args.warmup):
+        casim.casim_step(ctx, adom.state, ncols, nlev, dt, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sync()
+    e0.record(stream)
+    for _ in range(args.steps):
+        casim.casim_step(ctx, adom.state, ncols, nlev, dt, stream)
+    e1.record(stream)
+    sync()
+    rc, fl = casim.casim_get_error(ctx, stream)
+    assert rc == 0, (rc, fl)
+    casim.casim_free(ctx)
+    aero_ms = e0.elapsed_time(e1) / args.steps
+    del adom
     peak = _peaks().get("hbm_gbs")
     alg = 80.0 * npts + 56.0 * changed
     achieved = alg / (warm_per * 1e-3) / 1e9
@@ -382,6 +407,7 @@ def bench_warm(args, rank, world, local):
                            "cold_mixed_value": v(cold_ms), "cold_mixed_ms_per_step": cold_ms,
                            "warm_over_cold": cold_ms / warm_ms,
                            "warm_fp64_value": v(w64_ms), "cold_fp64_value": v(c64_ms),
+                           "warm_aerosol_mixed_value": v(aero_ms), "warm_aerosol_mixed_ms_per_step": aero_ms,
                            "changed_points_frac": changed / npts},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak if peak else None, "traffic": None,

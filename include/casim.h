@@ -120,6 +120,22 @@ int casim_default_params(casim_params *p);
    surrogate entry points reject a warm context (CASIM_ERR_ARG). */
 #define CASIM_WARM 1
 
+/* casim_init flag, with CASIM_WARM only: activated-aerosol mass (Section 2:
+   CASIM carries the mass of activated aerosol in the cloud and returns it
+   to the air when the water evaporates).  The state then has 19 fields --
+   the 16 above, then ma (free aerosol mass), mac (aerosol mass in cloud
+   droplets), mar (aerosol mass in rain), kg/kg -- and precip 5 rows, the
+   fifth the aerosol mass deposited by rain (kg m^-2).  Aerosol mass moves
+   with the water: the cloud the adjustment evaporates returns its share of
+   mac to ma; activated droplets take the free aerosol's mean particle mass
+   ma * dn / na; autoconversion and accretion carry mac to rain in proportion
+   to the cloud water they move; rain evaporation returns mar to ma in
+   proportion; mar sediments with the rain's mass-weighted fall speed.  The
+   other 16 fields and 4 precipitation rows evolve exactly as in the warm
+   configuration.  Supported by casim_step (both precisions); the other step
+   entry points reject such a context (CASIM_ERR_ARG). */
+#define CASIM_AEROSOL 2
+
 /* Create a context on the current CUDA device (Section 3.2: the one-off
    set-up that copies constants and allocates device memory).  `params` may be
    NULL for the defaults; `precision` is a casim_precision; `flags` is 0 or

@@ -19,6 +19,8 @@ from .build import LIB, INCLUDE
 CASIM_FP64 = 0
 CASIM_MIXED = 1
 CASIM_WARM = 1          # casim_init flag: the warm configuration
+CASIM_AEROSOL = 2       # casim_init flag (with CASIM_WARM): activated-aerosol mass, 19 fields, 5 precip rows
+NFIELDS_AERO = 19
 NFIELDS = 16
 NPROG = 13
 NPRECIP = 4
@@ -304,10 +306,11 @@ class Domain:
 
     def __init__(self, fld, dz: np.ndarray, ncols: int, device="cuda"):
         """fld: host array [16][nlev][pitch] (copied to the device) or a device
-        tensor of that shape (cloned)."""
+        tensor of that shape (cloned); 19 fields for the activated-aerosol
+        state, whose precip then has 5 rows."""
         import torch
         nf, nlev, pitch = fld.shape
-        assert nf == NFIELDS and pitch % 32 == 0 and pitch >= ncols
+        assert nf in (NFIELDS, NFIELDS_AERO) and pitch % 32 == 0 and pitch >= ncols
         self.ncols, self.nlev, self.pitch = ncols, nlev, pitch
         if isinstance(fld, torch.Tensor):
             assert fld.dtype == torch.float64
@@ -316,7 +319,7 @@ class Domain:
             self.fld = torch.from_numpy(np.ascontiguousarray(fld)).to(device)
         assert self.fld.data_ptr() % 256 == 0
         self.dz = torch.from_numpy(np.ascontiguousarray(dz, dtype=np.float64)).to(device)
-        self.precip = torch.zeros((NPRECIP, pitch), dtype=torch.float64, device=device)
+        self.precip = torch.zeros((NPRECIP + (nf == NFIELDS_AERO), pitch), dtype=torch.float64, device=device)
         self.state = make_state(self.fld, pitch, self.dz, self.precip)
 
     def numpy(self):

@@ -26,6 +26,7 @@ using namespace casim_dev;
 struct casim_ctx {
   int precision = CASIM_FP64;
   bool warm = false;   // CASIM_WARM: the warm configuration (liquid water only)
+  bool aero = false;   // CASIM_AEROSOL: with activated-aerosol mass (19-field state, 5 precip rows)
   int device = 0;
   int nsm = 1;
   KParams kp;
@@ -175,7 +176,8 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   if (!out) return CASIM_ERR_ARG;
   *out = nullptr;
   if (precision != CASIM_FP64 && precision != CASIM_MIXED) return CASIM_ERR_ARG;
-  if ((flags & ~CASIM_WARM) != 0) return CASIM_ERR_ARG;
+  if ((flags & ~(CASIM_WARM | CASIM_AEROSOL)) != 0) return CASIM_ERR_ARG;
+  if ((flags & CASIM_AEROSOL) && !(flags & CASIM_WARM)) return CASIM_ERR_ARG;
   casim_params p;
   if (params) p = *params;
   else casim_default_params(&p);
@@ -183,6 +185,7 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   casim_ctx *ctx = new casim_ctx();
   ctx->precision = precision;
   ctx->warm = (flags & CASIM_WARM) != 0;
+  ctx->aero = (flags & CASIM_AEROSOL) != 0;
   derive<double>(p, ctx->kp.d, ln_);
   derive<float>(p, ctx->kp.f, log2_);
   ctx->kp.c_max = p.c_max;
@@ -230,7 +233,11 @@ static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, 
   const dim3 grid((unsigned)((ncols + kBlock - 1) / kBlock));
   cudaStream_t st = (cudaStream_t)stream;
   const KParams &kp = ctx->kp;
-  if (ctx->precision == CASIM_MIXED && !ctx->warm) {
+  if (ctx->aero) {
+    if (tend) return CASIM_ERR_ARG;
+    if (ctx->precision == CASIM_MIXED) k_step<PolicyMixWarmAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+    else k_step<PolicyF64WarmAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+  } else if (ctx->precision == CASIM_MIXED && !ctx->warm) {
     if (tend) k_step<PolicyMix, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
     else k_step<PolicyMix, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
   } else if (ctx->precision == CASIM_MIXED) {
@@ -250,7 +257,7 @@ static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, 
 
 extern "C" int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, double *tend,
                                    void *stream) {
-  if (!ctx || !tend) return CASIM_ERR_ARG;
+  if (!ctx || ctx->aero || !tend) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
   const size_t span = (size_t)CASIM_NFIELDS * nlev * s->pitch;
@@ -313,7 +320,7 @@ static cudaError_t copy_chunk(double *dev_fld, double *dev_precip, int W, const 
 
 extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, int nlev, double dt,
                                void *stream) {
-  if (!ctx) return CASIM_ERR_ARG;
+  if (!ctx || ctx->aero) return CASIM_ERR_ARG;
   if (!h || ncols < 0 || nlev < 1 || nlev > kMaxLev || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
   if (ncols == 0) return CASIM_OK;
   if (!h->fld || !h->dz || !h->precip || h->pitch < ncols || h->pitch % 32 != 0) return CASIM_ERR_ARG;

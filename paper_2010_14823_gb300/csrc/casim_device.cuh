@@ -144,6 +144,7 @@ struct PolicyF64 {
   using R = double;
   static constexpr bool kMixed = false;
   static constexpr bool kWarm = false;
+  static constexpr bool kAero = false;
   static constexpr int kMinBlocks = 3;   // resident blocks of kBlock per SM the step kernel is built for
   static __device__ __forceinline__ const ConstK<double> &K(const KParams &p) { return p.d; }
   static __device__ __forceinline__ R toR(double x) { return x; }
@@ -164,6 +165,7 @@ struct PolicyMix {
   using R = float;
   static constexpr bool kMixed = true;
   static constexpr bool kWarm = false;
+  static constexpr bool kAero = false;
   static constexpr int kMinBlocks = 5;   // measured: 4 / 5 / 6 -> 2.95 / 2.73 / 3.06 ms per 512x512x150 step
   static __device__ __forceinline__ const ConstK<float> &K(const KParams &p) { return p.f; }
   static __device__ __forceinline__ R toR(double x) { return d2f(x); }
@@ -183,6 +185,7 @@ struct PolicyMix {
 // ------------------------------------------------------------ one point
 struct Pt {
   double T, qv, qc, qr, qi, qs, qg, nc, nr, ni, ns, ng, na, p, rho, w;
+  double ma, mac, mar;   // activated-aerosol mass (free, in cloud, in rain): aerosol-mass policies only
 };
 
 // Working values of a point in the compute precision (after adjustment and
@@ -461,8 +464,14 @@ struct F64T {
 
   // a2..a10 on one active point; transfers applied one by one in list order
   static __device__ __forceinline__ void process(const ConstK<double> &K, Pt &s, double dt, double es0, double qs0) {
+    const double qc0 = s.qc;
     satadj(K, s, es0, qs0);
+    const double evap = qc0 > s.qc ? qc0 - s.qc : 0.0;
+    const double na1 = s.na;
     activate(K, s);
+    const double dn_act = na1 - s.na;
+    const double qc_post = s.qc, qr_post = s.qr;
+    double tau_cr = 0.0, tau_rv = 0.0;
     W<double> w;
     w.Td = s.T; w.T = s.T; w.tc = s.T - K.T0; w.p = s.p; w.rho = s.rho;
     w.qv = s.qv; w.qc = s.qc; w.qr = s.qr; w.qx[0] = s.qi; w.qx[1] = s.qs; w.qx[2] = s.qg;
@@ -474,14 +483,14 @@ struct F64T {
     double qxd[3] = {s.qi, s.qs, s.qg};
     double nxd[3] = {s.ni, s.ns, s.ng};
     double tau;
-    if (r.aut > 0) { tau = g.aut * r.aut * dt; s.qc -= tau; s.qr += tau; }
+    if (r.aut > 0) { tau = g.aut * r.aut * dt; s.qc -= tau; s.qr += tau; tau_cr += tau; }
     if (r.aut * g.rc > 0) s.nc -= g.aut * (r.aut * g.rc) * dt;
     if (r.aut * K.inv_mr0 > 0) s.nr += g.aut * (r.aut * K.inv_mr0) * dt;
-    if (r.acc > 0) { tau = g.acc * r.acc * dt; s.qc -= tau; s.qr += tau; }
+    if (r.acc > 0) { tau = g.acc * r.acc * dt; s.qc -= tau; s.qr += tau; tau_cr += tau; }
     if (r.acc * g.rc > 0) s.nc -= g.acc * (r.acc * g.rc) * dt;
     if (r.scc > 0) s.nc -= g.scc * r.scc * dt;
     if (r.scr > 0) s.nr -= g.scr * r.scr * dt;
-    if (r.evr > 0) { tau = g.evr * r.evr * dt; s.qr -= tau; s.qv += tau; s.T += tau * (-K.lv) / K.cp; }
+    if (r.evr > 0) { tau = g.evr * r.evr * dt; s.qr -= tau; s.qv += tau; s.T += tau * (-K.lv) / K.cp; tau_rv = tau; }
     if (r.evr * g.rr > 0) s.nr -= g.evr * (r.evr * g.rr) * dt;
     if (g.nucm > 0) { tau = g.nuc * g.nucm * dt; s.qv -= tau; qxd[0] += tau; s.T += tau * K.ls / K.cp; }
     if (r.nucn > 0) nxd[0] += g.nuc * r.nucn * dt;
@@ -505,6 +514,31 @@ struct F64T {
     }
     s.qi = qxd[0]; s.qs = qxd[1]; s.qg = qxd[2];
     s.ni = nxd[0]; s.ns = nxd[1]; s.ng = nxd[2];
+    if constexpr (M::kAero) {
+      // aerosol mass moves with the water (in the order: adjustment,
+      // activation, cloud -> rain, rain -> vapour)
+      double d;
+      if (evap > 0.0 && qc0 > 0.0) {
+        d = evap >= qc0 ? s.mac : s.mac * (evap / qc0);
+        s.mac -= d;
+        s.ma += d;
+      }
+      if (dn_act > 0.0 && na1 > 0.0) {
+        d = s.ma * (dn_act / na1);
+        s.ma -= d;
+        s.mac += d;
+      }
+      if (tau_cr > 0.0 && qc_post > 0.0) {
+        d = tau_cr >= qc_post ? s.mac : s.mac * (tau_cr / qc_post);
+        s.mac -= d;
+        s.mar += d;
+      }
+      if (tau_rv > 0.0 && qr_post > 0.0) {
+        d = tau_rv >= qr_post ? s.mar : s.mar * (tau_rv / qr_post);
+        s.mar -= d;
+        s.ma += d;
+      }
+    }
   }
 };
 
@@ -520,6 +554,11 @@ struct MixInc {
   float dT;        // temperature
   float dn[5];     // numbers c, r, i, s, g
   float dna;       // aerosol number
+  // aerosol-mass policies: fractions of the source's aerosol mass moved by
+  // the adjustment (cloud -> free), activation (free -> cloud), cloud -> rain
+  // and rain -> free; *_all: the whole pool moves
+  float a_ev, a_act, a_cr, a_rv;
+  bool a_ev_all, a_cr_all, a_rv_all;
 };
 
 template <class M>
@@ -589,6 +628,11 @@ struct MixT {
     o.vc = 0.f;
     o.evap_all = false;
     o.dT = 0.f;
+    const float qc0 = w.qc;
+    if constexpr (M::kAero) {
+      o.a_ev = o.a_act = o.a_cr = o.a_rv = 0.f;
+      o.a_ev_all = o.a_cr_all = o.a_rv_all = false;
+    }
     // a2: Newton on the temperature increment; qv - qs(T + dT) is the FP64
     // difference at dT = 0 plus the FP32 change of qs
     if (w.qv > qs0 || w.qc > K.qmin) {
@@ -615,6 +659,12 @@ struct MixT {
         o.evap_all = true;
       }
       o.vc = dq;
+      if constexpr (M::kAero) {
+        if (dq < 0.f && qc0 > 0.f) {
+          o.a_ev_all = o.evap_all;
+          o.a_ev = __fdividef(-dq, qc0);
+        }
+      }
       const float dTs = K.lv_cp * dq;
       o.dT = dTs;
       w.T += dTs;
@@ -633,6 +683,7 @@ struct MixT {
         float dn = __fdividef(nact, w.rho) - w.nc;
         dn = fminf(fmaxf(dn, 0.f), na);
         dnc_act = dn;
+        if constexpr (M::kAero) o.a_act = na > 0.f ? __fdividef(dn, na) : 0.f;
         o.dna = -dn;
         w.nc += dn;
       }
@@ -665,6 +716,16 @@ struct MixT {
     o.cr = (g.aut * r.aut + g.acc * r.acc) * dtr;
     o.cg = (g.rs * r.rim[0] + g.rg * r.rim[1]) * dtr;
     o.rv = g.evr * r.evr * dtr;
+    if constexpr (M::kAero) {
+      if (o.cr > 0.f && w.qc > 0.f) {
+        o.a_cr_all = o.cr >= w.qc;
+        o.a_cr = __fdividef(o.cr, w.qc);
+      }
+      if (o.rv > 0.f && w.qr > 0.f) {
+        o.a_rv_all = o.rv >= w.qr;
+        o.a_rv = __fdividef(o.rv, w.qr);
+      }
+    }
     o.vx[0] = (g.nuc * g.nucm + g.dep[0] * r.dep[0]) * dtr;   // signed: deposition > 0
     o.vx[1] = g.dep[1] * r.dep[1] * dtr;
     o.vx[2] = g.dep[2] * r.dep[2] * dtr;
@@ -705,6 +766,23 @@ struct MixT {
     if (o.xr[2] != 0.f) { const double d = f2d(o.xr[2]); s.qg -= d; s.qr += d; }
     if (o.dT != 0.f) s.T += f2d(o.dT);
     if (o.dna != 0.f) s.na += f2d(o.dna);
+    if constexpr (M::kAero) apply_aero(s, o);
+  }
+
+  // aerosol masses: each amount is one FP32 product of the source's mass and
+  // the moved fraction, taken from the source (never more than it holds) and
+  // given to the destination
+  static __device__ __forceinline__ void apply_aero(Pt &s, const MixInc &o) {
+    auto move = [](double &from, double &to, float frac, bool all) {
+      if (!all && !(frac > 0.f)) return;
+      const double d = all ? from : fmin(f2d(d2f(from) * frac), from);
+      from -= d;
+      to += d;
+    };
+    move(s.mac, s.ma, o.a_ev, o.a_ev_all);
+    move(s.ma, s.mac, o.a_act, false);
+    move(s.mac, s.mar, o.a_cr, o.a_cr_all);
+    move(s.mar, s.ma, o.a_rv, o.a_rv_all);
   }
 };
 
@@ -721,9 +799,21 @@ struct PolicyMixWarm : PolicyMix {
   static constexpr bool kWarm = true;
   static constexpr int kMinBlocks = 6;
 };
+// The warm configuration with activated-aerosol mass (Section 2: aerosol
+// carried in the cloud once activated and returned when the water
+// evaporates): fields 16, 17, 18 of the state are the free aerosol mass, the
+// aerosol mass in cloud and in rain (kg/kg); precip has a fifth row, the
+// aerosol deposited by rain.  The other fields evolve exactly as in the warm
+// configuration.
+struct PolicyF64WarmAero : PolicyF64Warm {
+  static constexpr bool kAero = true;
+};
+struct PolicyMixWarmAero : PolicyMixWarm {
+  static constexpr bool kAero = true;
+};
 
 // ---------------------------------------------------------------- kernels
-template <bool kWarm = false>
+template <bool kWarm = false, bool kAero = false>
 __device__ __forceinline__ void load_pt(const KArgs &a, int k, int c, Pt &s) {
   const double *b = a.fld + (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
@@ -741,6 +831,9 @@ __device__ __forceinline__ void load_pt(const KArgs &a, int k, int c, Pt &s) {
   }
   s.na = b[12 * fs];
   s.p = __ldg(b + 13 * fs); s.rho = __ldg(b + 14 * fs); s.w = __ldg(b + 15 * fs);
+  if constexpr (kAero) {
+    s.ma = b[16 * fs]; s.mac = b[17 * fs]; s.mar = b[18 * fs];
+  }
 }
 
 // any loaded value non-finite (integer pipe: max of the exponent fields)
@@ -764,14 +857,20 @@ __device__ __forceinline__ unsigned store_pt(const KArgs &a, int k, int c, const
          nonfinite(s.ns) | nonfinite(s.ng) | nonfinite(s.na);
 }
 
-// the warm configuration's fields only
+// the warm configuration's fields only (and the aerosol masses)
+template <bool kAero = false>
 __device__ __forceinline__ unsigned store_pt_warm(const KArgs &a, int k, int c, const Pt &s) {
   double *b = a.fld + (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
   b[0 * fs] = s.T; b[1 * fs] = s.qv; b[2 * fs] = s.qc; b[3 * fs] = s.qr;
   b[7 * fs] = s.nc; b[8 * fs] = s.nr; b[12 * fs] = s.na;
-  return nonfinite(s.T) | nonfinite(s.qv) | nonfinite(s.qc) | nonfinite(s.qr) | nonfinite(s.nc) |
-         nonfinite(s.nr) | nonfinite(s.na);
+  unsigned e = nonfinite(s.T) | nonfinite(s.qv) | nonfinite(s.qc) | nonfinite(s.qr) | nonfinite(s.nc) |
+               nonfinite(s.nr) | nonfinite(s.na);
+  if constexpr (kAero) {
+    b[16 * fs] = s.ma; b[17 * fs] = s.mac; b[18 * fs] = s.mar;
+    e |= nonfinite(s.ma) | nonfinite(s.mac) | nonfinite(s.mar);
+  }
+  return e;
 }
 
 // Tendency mode (the state is left unchanged): in the single-substep path
@@ -841,7 +940,7 @@ __device__ __forceinline__ bool prologue(const KArgs &a, const KParams &P, Smem 
 // largest Courant number, then n_sub top-down sweeps in place.
 template <class M, bool kTend>
 __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KParams &P, const double *sdz, int c,
-                                                      double prec[4], double *tend) {
+                                                      double prec[5], double *tend) {
   using R = typename M::R;
   using Ph = Phys<M>;
   const ConstK<R> &K = M::K(P);
@@ -868,14 +967,19 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
     if (ns < 1) ns = 1;
     if (ns > 64) { ns = 64; eflag |= 2u; }
     const double dts = a.dt / ns;
+    // the rain's aerosol mass moves with the rain (aerosol-mass policies)
+    const bool aer = M::kAero && x == 0;
+    double *ap = a.fld + 18 * fs;
     for (int st = 0; st < ns; ++st) {
-      R Fu = 0, Gu = 0;
+      R Fu = 0, Gu = 0, Au = 0;
       for (int k = a.nlev - 1; k >= 0; --k) {
         const size_t o = (size_t)k * a.pitch + c;
         double q = qp[o], n = np[o];
         const double rhod = __ldg(rhop + o);
         const R qR = M::toR(q), rho = M::toR(rhod);
-        R F = 0, G = 0;
+        R F = 0, G = 0, A = 0;
+        double am = 0.0;
+        if (aer) am = ap[o];
         if (qR > K.qmin) {
           const R dfac = M::ex((R)0.4 * (K.lgrho0 - M::lg(rho)));
           R vq, vn;
@@ -883,11 +987,23 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
           if constexpr (!M::kMixed) {
             F = rhod * q * vq;
             G = rhod * (n > 0.0 ? n : 0.0) * vn;
+            if (aer) A = rhod * am * vq;
           } else {
             F = rho * qR * vq;
             G = rho * M::mx(M::toR(n), (R)0) * vn;
+            if (aer) A = rho * M::toR(am) * vq;
           }
         }
+        if (aer && (A != (R)0 || Au != (R)0)) {
+          if constexpr (!M::kMixed) {
+            am += dts * (Au - A) / (rhod * sdz[k]);
+          } else {
+            am += M::toD((Au - A) * M::div(M::toR(dts), rho * M::toR(sdz[k])));
+          }
+          ap[o] = am;
+          eflag |= nonfinite(am);
+        }
+        Au = A;
         if (F != (R)0 || Fu != (R)0 || G != (R)0 || Gu != (R)0) {
           if constexpr (!M::kMixed) {
             q += dts * (Fu - F) / (rhod * sdz[k]);
@@ -905,6 +1021,7 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
         Gu = G;
       }
       prec[x] += M::toD(Fu) * dts;
+      if (aer) prec[4] += M::toD(Au) * dts;
     }
   }
   return eflag;
@@ -924,13 +1041,15 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
   const ConstK<R> &K = M::K(P);
   unsigned eflag = 0;
   constexpr int kSed = M::kWarm ? 1 : 4;   // sedimenting species: r (warm) or r, i, s, g
-  double prec[4] = {0.0, 0.0, 0.0, 0.0};
-  // carried downward fluxes F_{k+1}, G_{k+1} (kg m^-2 s^-1, m^-2 s^-1)
+  double prec[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // r, i, s, g (and aerosol in rain)
+  // carried downward fluxes F_{k+1}, G_{k+1} (kg m^-2 s^-1, m^-2 s^-1), and
+  // the rain's aerosol-mass flux (aerosol-mass policies)
   R Fq[4] = {0, 0, 0, 0}, Fn[4] = {0, 0, 0, 0};
+  R Fa = 0;
 
   for (int k = a.nlev - 1; k >= 0; --k) {
     Pt s;
-    load_pt<M::kWarm>(a, k, c, s);
+    load_pt<M::kWarm, M::kAero>(a, k, c, s);
     bool touched;
     if constexpr (!M::kMixed) {
       eflag |= nonfinite_in(s);
@@ -944,17 +1063,27 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
         for (int x = 0; x < kSed; ++x) {
           double &q = qref(s, x);
           double &n = nref(s, x);
-          double F = 0, G = 0;
+          double F = 0, G = 0, A = 0;
           if (q > K.qmin) {
             double vq, vn;
             Ph::fall_speeds(K, sdzdt[k], ::log(q), n, dfac, x, vq, vn);
             F = s.rho * q * vq;
             G = s.rho * (n > 0.0 ? n : 0.0) * vn;
+            if (M::kAero && x == 0) A = s.rho * s.mar * vq;
           }
           if (F != 0.0 || Fq[x] != 0.0 || G != 0.0 || Fn[x] != 0.0) {
             q += a.dt * (Fq[x] - F) / (s.rho * dzk);
             n += a.dt * (Fn[x] - G) / (s.rho * dzk);
             touched = true;
+          }
+          if constexpr (M::kAero) {
+            if (x == 0) {
+              if (A != 0.0 || Fa != 0.0) {
+                s.mar += a.dt * (Fa - A) / (s.rho * dzk);
+                touched = true;
+              }
+              Fa = A;
+            }
           }
           Fq[x] = F;
           Fn[x] = G;
@@ -1002,13 +1131,23 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
           const float guard = d2f(sdzdt[k]);
 #pragma unroll
           for (int x = 0; x < kSed; ++x) {
-            float F = 0.f, G = 0.f;
+            float F = 0.f, G = 0.f, A = 0.f;
             if (qpost[x] > K.qmin) {
               const float n = act ? npost[x] : d2f(nref(s, x));
               float vq, vn;
               Ph::fall_speeds(K, guard, lg2a(qpost[x]), n, dfac, x, vq, vn);
               F = rho * qpost[x] * vq;
               G = rho * fmaxf(n, 0.f) * vn;
+              if (M::kAero && x == 0) A = rho * d2f(s.mar) * vq;
+            }
+            if constexpr (M::kAero) {
+              if (x == 0) {
+                if (A != 0.f || Fa != 0.f) {
+                  s.mar += f2d((Fa - A) * sc);
+                  touched = true;
+                }
+                Fa = A;
+              }
             }
             if (F != 0.f || Fq[x] != 0.f) {
               qref(s, x) += f2d((Fq[x] - F) * sc);
@@ -1031,7 +1170,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
     if constexpr (kTend) {
       eflag |= store_tend<M::kWarm>(a, tend, k, c, s, fast);
     } else if constexpr (M::kWarm) {
-      if (touched) eflag |= store_pt_warm(a, k, c, s);
+      if (touched) eflag |= store_pt_warm<M::kAero>(a, k, c, s);
     } else {
       if (touched) eflag |= store_pt(a, k, c, s);
     }
@@ -1039,6 +1178,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
   if (fast) {
 #pragma unroll
     for (int x = 0; x < kSed; ++x) prec[x] = M::toD(Fq[x]) * a.dt;
+    if constexpr (M::kAero) prec[4] = M::toD(Fa) * a.dt;
   } else {
     eflag |= sediment_substeps<M, kTend>(a, P, sdz, c, prec, tend);
     if constexpr (kTend) {
@@ -1055,7 +1195,8 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
     }
   }
 #pragma unroll
-  for (int x = 0; x < kSed; ++x) {
+  for (int x = 0; x < 5; ++x) {
+    if (x >= kSed && !(M::kAero && x == 4)) continue;
     if (prec[x] != 0.0) {
       double *pp = a.precip + (size_t)x * a.pitch + c;
       *pp += prec[x];

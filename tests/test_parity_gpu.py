@@ -367,3 +367,112 @@ def test_warm_tendency_and_host_entry_points(dt):
             casim.casim_batch_create(ctx, [d.state], [ncols], [nlev])
     finally:
         casim.casim_free(ctx)
+
+
+# ------------------------------------------------------------------ activated-aerosol mass (warm)
+MA, MAC, MAR = 16, 17, 18
+
+
+def _aero_state(ncols, nlev, seed, pitch=None):
+    dz = synth.dz_stretched(nlev)
+    base = synth.make_state("deep_convective", ncols, nlev, dz, seed=seed, pitch=pitch)
+    fld = np.zeros((19,) + base.shape[1:])
+    fld[:16] = base
+    rng = np.random.default_rng(seed)
+    fld[MA] = rng.uniform(1e-9, 5e-9, base.shape[1:])
+    fld[MAC] = fld[F["qc"]] * rng.uniform(1e-5, 1e-4, base.shape[1:])
+    fld[MAR] = fld[F["qr"]] * rng.uniform(1e-5, 1e-4, base.shape[1:])
+    return np.ascontiguousarray(fld), dz
+
+
+def _run_gpu_aero(fld, dz, ncols, dt, nsteps, precision):
+    ctx = casim.casim_init(precision=precision, flags=casim.CASIM_WARM | casim.CASIM_AEROSOL)
+    try:
+        d = casim.Domain(fld, dz, ncols)
+        for _ in range(nsteps):
+            casim.casim_step(ctx, d.state, ncols, d.nlev, dt)
+        rc, flags = casim.casim_get_error(ctx)
+        assert rc == 0, (rc, flags)
+        return d.numpy()
+    finally:
+        casim.casim_free(ctx)
+
+
+@pytest.mark.parametrize("dt", [1.0, 30.0])
+def test_aerosol_fp64_matches_oracle(dt):
+    """FP64 form with activated-aerosol mass: all 16 updated fields and the 5
+    precipitation rows within 1e-11 of the oracle; the standard fields equal
+    the warm step's without aerosol, bit for bit (the extension is
+    additive)."""
+    ncols, nlev = 97, 150
+    nsteps = 3 if dt == 1.0 else 1
+    fld, dz = _aero_state(ncols, nlev, seed=51)
+    out, pr = _run_gpu_aero(fld, dz, ncols, dt, nsteps, casim.CASIM_FP64)
+    ref = fld.copy()
+    pref = np.zeros((5, fld.shape[2]))
+    for _ in range(nsteps):
+        _, err = O.step_aero(ref, ncols, dz, dt, precip=pref)
+        assert err == 0
+    assert_fp64_close(out, pr[:4], ref, pref[:4], ncols, rtol=1e-11)
+    # aerosol masses: relative to the point's total aerosol mass -- a pool
+    # that gives most of itself away (e.g. free aerosol almost all
+    # activated) ends as a small difference of large moves, so its error
+    # scales with the aerosol moved, not with what is left
+    scale = (fld[MA] + fld[MAC] + fld[MAR])[:, :ncols]
+    for f in (MA, MAC, MAR):
+        a, b = out[f, :, :ncols], ref[f, :, :ncols]
+        assert (np.abs(a - b) <= 1e-11 * np.maximum(np.abs(b), scale) + 1e-26).all(), \
+            (f, float(np.abs(a - b).max()))
+    assert np.allclose(pr[4, :ncols], pref[4, :ncols], rtol=1e-11, atol=1e-26)
+    assert pref[4, :ncols].max() > 0.0
+    std, pstd, _ = run_gpu(np.ascontiguousarray(fld[:16]), dz, ncols, dt, nsteps=nsteps, flags=casim.CASIM_WARM)
+    assert np.array_equal(out[:16], std) and np.array_equal(pr[:4], pstd)
+
+
+def test_aerosol_mixed_within_bound_and_budget():
+    ncols, nlev = 512, 150
+    fld, dz = _aero_state(ncols, nlev, seed=52)
+    out, pr = _run_gpu_aero(fld, dz, ncols, 1.0, 1, casim.CASIM_MIXED)
+    ref = fld.copy()
+    pref = np.zeros((5, fld.shape[2]))
+    O.step_aero(ref, ncols, dz, 1.0, precip=pref)
+    for f in range(13):
+        a, b, i = out[f, :, :ncols], ref[f, :, :ncols], fld[f, :, :ncols]
+        assert (np.abs(a - b) <= mixed_bound(b, i, f, ref[1, :, :ncols])).all(), synth.FIELDS[f]
+    # aerosol moved in FP32: each amount is an FP32 product of a pool and a
+    # fraction derived from FP32 rates (relative error ~1e-5, see
+    # mixed_bound), and no move exceeds the point's total aerosol, so the
+    # error is below ~1e-5 of that total; the bound gives a factor of 10
+    scale = (fld[MA] + fld[MAC] + fld[MAR])[:, :ncols]
+    for f in (MA, MAC, MAR):
+        a, b = out[f, :, :ncols], ref[f, :, :ncols]
+        bound = 1e-4 * scale + 1e-22
+        assert (np.abs(a - b) <= bound).all(), (f, float((np.abs(a - b) / bound).max()))
+    assert (out[[MA, MAC, MAR], :, :ncols] >= 0).all()
+    # column budget: process moves are exact FP64 pairs; each level's
+    # sedimentation increment of rain aerosol is one FP32 amount (relative
+    # rounding <= 2^-23), so the drift is below 2^-22 of the summed
+    # |change of mar| (an upper proxy for those increments)
+    rho = fld[F["rho"], :, :ncols]
+    w = rho * dz[:, None]
+    m0 = ((fld[MA] + fld[MAC] + fld[MAR])[:, :ncols] * w).sum(0)
+    m1 = ((out[MA] + out[MAC] + out[MAR])[:, :ncols] * w).sum(0)
+    moved = (np.abs(out[MAR] - fld[MAR])[:, :ncols] * w).sum(0) + pr[4, :ncols]
+    assert (np.abs(m1 + pr[4, :ncols] - m0) <= 2.0 ** -22 * moved + 1e-15 * m0).all()
+
+
+def test_aerosol_context_rules():
+    import torch
+    with pytest.raises(RuntimeError):                    # needs the warm configuration
+        casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_AEROSOL)
+    fld, dz = _aero_state(64, 40, seed=53)
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM | casim.CASIM_AEROSOL)
+    try:
+        d = casim.Domain(fld, dz, 64)
+        tend = torch.zeros((16, 40, d.pitch), dtype=torch.float64, device="cuda")
+        with pytest.raises(RuntimeError):
+            casim.casim_step_tendency(ctx, d.state, 64, 40, 1.0, tend)
+        with pytest.raises(RuntimeError):
+            casim.casim_batch_create(ctx, [d.state], [64], [40])
+    finally:
+        casim.casim_free(ctx)
