@@ -554,10 +554,14 @@ constexpr int kUmmaEpiWarps = 16;                       // 4 per TMEM lane quart
 constexpr int kUmmaMmaWarp = kUmmaEpiWarps;             // issues the MMAs, owns TMEM
 constexpr int kUmmaProdWarp = kUmmaEpiWarps + 1;        // streams the weight chunks
 constexpr int kUmmaThreads = (kUmmaEpiWarps + 2) * 32;
-constexpr int kUmmaStages = 3;                          // weight-chunk ring
-// dynamic shared memory (1024-byte aligned): the activation tile X (128 rows
-// x 256 BF16, four K-slabs), resident W1 and W4, the chunk ring
-constexpr uint32_t kSmW1 = 65536, kSmW4 = kSmW1 + kImgW1, kSmRing = kSmW4 + kImgW4;
+constexpr int kUmmaStages = 4;                          // weight-chunk ring
+// dynamic shared memory (1024-byte aligned): resident W1 and W4, the chunk
+// ring.  Activations live in tensor memory.
+constexpr uint32_t kSmW1 = 0, kSmW4 = kSmW1 + kImgW1, kSmRing = kSmW4 + kImgW4;
+// tensor-memory columns: accumulators A0 (layers 1, 3) and A1 (layers 2, 4),
+// each later overwritten in place by its layer's BF16 activations; the next
+// tile's features sit in A1's last 8 columns
+constexpr uint32_t kTmA0 = 0, kTmA1 = 256, kTmFeat = 504;
 constexpr int kUmmaSmem = 1024 + kSmRing + kUmmaStages * kImgChunk;
 static_assert(kUmmaSmem + 4096 <= 232448, "shared memory of the tensor-core kernel");
 
@@ -565,13 +569,16 @@ static_assert(kUmmaSmem + 4096 <= 232448, "shared memory of the tensor-core kern
 //
 // Tensor memory holds two 256-column FP32 accumulators used by alternate
 // layers (layer 1 -> A0, 2 -> A1, 3 -> A0, 4 -> A1), so the MMAs of layer
-// l+1 run while the epilogue of layer l still reads layer l's sums.  One
-// activation tile X suffices in shared memory: layer l's MMAs have all
-// completed (the accumulator commit) before its epilogue overwrites X slab by
-// slab, and layer l+1's MMAs on slab s wait for that slab:
+// l+1 run while the epilogue of layer l still reads layer l's sums.  The
+// activations never touch shared memory: each epilogue warp writes the BF16
+// activations of the 16 sums it has just read back into the first 8 of
+// those 16 columns (two per 32-bit column, even k in the low half), and the
+// next layer's MMAs read their A operand from there (K-step kk of 16 at
+// column 16 kk).  Shared memory only holds weights, and its bandwidth --
+// which bounds these MMAs -- goes to the B operand:
 //  * epilogue warps (16): warp w reads TMEM lanes 32(w%4).. (its rows) and
 //    columns 16(w/4)..+15 of each 64-column slab; per slab s: bias, tanh,
-//    BF16 pack, swizzled store into slab s of X, then one arrival on act[s];
+//    BF16 pack, tcgen05.st in place, then one arrival on act[s];
 //  * MMA warp (one thread): per slab s it waits act[s] and issues that
 //    K-slab's MMAs of the next layer (N = 256, weights from the ring);
 //    after the last slab it commits the accumulator to acc;
@@ -690,12 +697,12 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
         ok = bar_wait_or_abort(bar(B_FEAT), (uint32_t)(nfeat++ & 1), kUmmaSpins, abort);
         if (!ok) break;
         tc_fence_after();
-        // layer 1: features (X slab 0, k < 16) x W1 -> A0
-        umma_bf16(taddr, umma_desc_sw128(sb), umma_desc_sw128(sb + kSmW1), id256, 0u);
+        // layer 1: features (tensor memory, k < 16) x W1 -> A0
+        umma_bf16_ts(taddr + kTmA0, taddr + kTmFeat, umma_desc_sw128(sb + kSmW1), id256, 0u);
         umma_commit(bar(B_ACC));
-        // layers 2 (-> A1) and 3 (-> A0), K-slab by K-slab
+        // layers 2 (A0 -> A1) and 3 (A1 -> A0), K-slab by K-slab
         for (int l = 0; ok && l < 2; ++l, ++nact) {
-          const uint32_t dacc = taddr + (l == 0 ? 256u : 0u);
+          const uint32_t dacc = taddr + (l == 0 ? kTmA1 : kTmA0), ain = taddr + (l == 0 ? kTmA0 : kTmA1);
           for (int s = 0; ok && s < 4; ++s) {
             ok = bar_wait_or_abort(bar(B_ACT + s), (uint32_t)(nact & 1), kUmmaSpins, abort);
             if (!ok) break;
@@ -707,24 +714,24 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
             const uint32_t wst = sb + kSmRing + (uint32_t)st * kImgChunk;
 #pragma unroll
             for (int sub = 0; sub < 4; ++sub)
-              umma_bf16(dacc, umma_desc_sw128(sb + 16384u * (uint32_t)s + 32u * (uint32_t)sub),
-                        umma_desc_sw128(wst + 32u * (uint32_t)sub), id256, (s | sub) ? 1u : 0u);
+              umma_bf16_ts(dacc, ain + 64u * (uint32_t)s + 16u * (uint32_t)sub, umma_desc_sw128(wst + 32u * (uint32_t)sub),
+                           id256, (s | sub) ? 1u : 0u);
             if constexpr (C > 1) umma_commit_multicast(bar(B_FREE + st), all);
             else umma_commit(bar(B_FREE + st));
             ++chunk;
           }
           if (ok) umma_commit(bar(B_ACC));
         }
-        // layer 4: X x W4 -> A1 columns 0..15
+        // layer 4: A0 x W4 -> A1 columns 0..15
         for (int s = 0; ok && s < 4; ++s) {
           ok = bar_wait_or_abort(bar(B_ACT + s), (uint32_t)(nact & 1), kUmmaSpins, abort);
           if (!ok) break;
           tc_fence_after();
 #pragma unroll
           for (int sub = 0; sub < 4; ++sub)
-            umma_bf16(taddr + 256u, umma_desc_sw128(sb + 16384u * (uint32_t)s + 32u * (uint32_t)sub),
-                      umma_desc_sw128(sb + kSmW4 + 2048u * (uint32_t)s + 32u * (uint32_t)sub), id16,
-                      (s | sub) ? 1u : 0u);
+            umma_bf16_ts(taddr + kTmA1, taddr + kTmA0 + 64u * (uint32_t)s + 16u * (uint32_t)sub,
+                         umma_desc_sw128(sb + kSmW4 + 2048u * (uint32_t)s + 32u * (uint32_t)sub), id16,
+                         (s | sub) ? 1u : 0u);
         }
         ++nact;
         if (ok) umma_commit(bar(B_ACC));
@@ -740,7 +747,6 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
     const int q = warp & 3, j = warp >> 2;
     const int row = 32 * q + lane;
     const uint32_t tl = taddr + ((uint32_t)(32 * q) << 16);
-    const int sw = row & 7;
     int nacc = 0;
     bool ok = true;
     uint4 f0 = make_uint4(0, 0, 0, 0), f1 = f0;
@@ -759,12 +765,13 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
       const long long r0 = (g * C + rank) * 128;
       // every epilogue warp arrives: the next tile's layer-1 MMA (which
       // overwrites A0) waits until all of them have seen the previous
-      // tile's last accumulator phase
+      // tile's last accumulator phase; the features go to tensor memory
+      // (A1's last columns: the previous tile's layer-3 MMAs, which read
+      // A1, have completed)
       if (j == 0) {
-        unsigned char *rp = sm + row * 128;
-        *reinterpret_cast<uint4 *>(rp + ((0 ^ sw) << 4)) = f0;
-        *reinterpret_cast<uint4 *>(rp + ((1 ^ sw) << 4)) = f1;
-        fence_async_smem();
+        const uint32_t fv[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+        tmem_st8(tl + kTmFeat, fv);
+        tc_fence_before();
       }
       __syncwarp();
       if (lane == 0) bar_arrive(bar(B_FEAT));
@@ -773,8 +780,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
         ok = bar_wait_or_abort(bar(B_ACC), (uint32_t)(nacc++ & 1), kUmmaSpins, abort);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t tacc = tl + (l == 1 ? 256u : 0u);
-        unsigned char *xo = sm + row * 128;
+        const uint32_t tacc = tl + (l == 1 ? kTmA1 : kTmA0);
         const float *b = s_bias + l * kNh;
 #pragma unroll 1
         for (int s = 0; s < 4; ++s) {
@@ -788,10 +794,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
                                                           tanh_approx(v[2 * i + 1] + b[c0 + 2 * i + 1]));
             hb[i] = *reinterpret_cast<const uint32_t *>(&p);
           }
-          unsigned char *sp = xo + 16384 * s;
-          *reinterpret_cast<uint4 *>(sp + (((2 * j) ^ sw) << 4)) = make_uint4(hb[0], hb[1], hb[2], hb[3]);
-          *reinterpret_cast<uint4 *>(sp + (((2 * j + 1) ^ sw) << 4)) = make_uint4(hb[4], hb[5], hb[6], hb[7]);
-          fence_async_smem();
+          tmem_st8(tacc + (uint32_t)c0, hb);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) bar_arrive(bar(B_ACT + s));
@@ -803,7 +806,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
       tc_fence_after();
       if (j == 0) {
         float v[16];
-        tmem_ld16(tl + 256u, v);
+        tmem_ld16(tl + kTmA1, v);
         tc_fence_before();
         if (r0 + row < u.rows) {
           float y[kNout];
