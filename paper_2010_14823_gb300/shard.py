@@ -30,6 +30,19 @@ def column_range(ncols_total: int, rank: int, world: int) -> tuple[int, int]:
     return start, start + q + (1 if rank < r else 0)
 
 
+def column_range_aligned(ncols_total: int, rank: int, world: int, align: int = 32) -> tuple[int, int]:
+    """Contiguous column range of one part when a domain is split into
+    `world` parts whose starts are multiples of `align` columns (a state view
+    starting at such a column keeps the 256-byte alignment the step needs):
+    whole blocks of `align` columns are shared out as evenly as possible and
+    the last part ends at ncols_total.  Parts may be empty."""
+    nblk = (ncols_total + align - 1) // align
+    q, r = divmod(nblk, world)
+    b0 = rank * q + min(rank, r)
+    b1 = b0 + q + (1 if rank < r else 0)
+    return min(b0 * align, ncols_total), min(b1 * align, ncols_total)
+
+
 def max_over_ranks(value: float, dist=None, device=None) -> float:
     """The largest value over all ranks (the job's time is its slowest rank's)."""
     if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:

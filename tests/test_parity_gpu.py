@@ -214,6 +214,34 @@ def test_tendency_mode_equals_in_place_step(precision, dt):
         casim.casim_free(ctx)
 
 
+@pytest.mark.parametrize("precision", [casim.CASIM_FP64, casim.CASIM_MIXED])
+def test_column_ranges_on_streams_equal_one_launch(precision):
+    """The sharded path on one GPU: the domain split into three 32-aligned
+    column ranges, each stepped on its own stream at the same time, gives the
+    single launch's result bit for bit (columns are independent)."""
+    import torch
+    from paper_2010_14823_gb300 import shard
+    nlev, ncols = 150, 1000
+    dz = synth.dz_stretched(nlev)
+    fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=61)
+    out, pr, _ = run_gpu(fld, dz, ncols, 1.0, precision=precision)
+    ctx = casim.casim_init(precision=precision)
+    try:
+        d = casim.Domain(fld, dz, ncols)
+        streams = [torch.cuda.Stream() for _ in range(3)]
+        torch.cuda.synchronize()
+        for r, st in enumerate(streams):
+            c0, c1 = shard.column_range_aligned(ncols, r, 3)
+            view = casim.make_state(d.fld.data_ptr() + 8 * c0, d.pitch, d.dz, d.precip.data_ptr() + 8 * c0)
+            casim.casim_step(ctx, view, c1 - c0, nlev, 1.0, st)
+        torch.cuda.synchronize()
+        assert casim.casim_get_error(ctx)[0] == 0
+        f2, p2 = d.numpy()
+        assert np.array_equal(f2, out) and np.array_equal(p2, pr)
+    finally:
+        casim.casim_free(ctx)
+
+
 def test_budget_sums():
     fld, dz, ncols, nlev, dt, _ = synth.workload("stratus_16x16x50")
     ctx = casim.casim_init()

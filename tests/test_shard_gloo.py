@@ -67,3 +67,17 @@ def test_column_ranges_cover_exactly():
             assert rs[0][0] == 0 and rs[-1][1] == n
             assert all(a[1] == b[0] for a, b in zip(rs, rs[1:]))
             assert max(b - a for a, b in rs) - min(b - a for a, b in rs) <= 1
+
+
+def test_aligned_column_ranges_cover_exactly():
+    from paper_2010_14823_gb300 import shard
+    for ncols in (1, 31, 32, 33, 1000, 4096, 262144):
+        for world in (1, 2, 3, 7, 8):
+            parts = [shard.column_range_aligned(ncols, r, world) for r in range(world)]
+            assert parts[0][0] == 0 and parts[-1][1] == ncols
+            for (a0, a1), (b0, b1) in zip(parts, parts[1:]):
+                assert a1 == b0
+            for a0, a1 in parts:
+                assert a0 <= a1 and (a0 % 32 == 0 or a0 == a1)
+            sizes = [max(0, (a1 - a0 + 31) // 32) for a0, a1 in parts]
+            assert max(sizes) - min(sizes) <= 1 or ncols < 32 * world
