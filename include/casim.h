@@ -69,8 +69,9 @@ enum casim_status {
   CASIM_ERR_CUDA = -3,       /* a CUDA call failed (see casim_last_cuda_error) */
   CASIM_ERR_NONFINITE = -4,  /* casim_get_error: a non-finite value was produced */
   CASIM_ERR_CFL = -5,        /* casim_get_error: substep cap reached in sedimentation */
-  CASIM_ERR_TIMEOUT = -6     /* casim_get_error: a bounded wait inside the surrogate network's
+  CASIM_ERR_TIMEOUT = -6,    /* casim_get_error: a bounded wait inside the surrogate network's
                                 kernel gave up; its rows were left to the scheme's rates */
+  CASIM_ERR_IO = -7          /* a checkpoint file could not be opened, read or written */
 };
 
 /* device error-word bits (casim_get_error) */
@@ -344,6 +345,23 @@ long long casim_launch_count(const casim_ctx *ctx);
 
 /* The last CUDA error string seen by this library (static storage). */
 const char *casim_last_cuda_error(void);
+
+/* ----------------------------------------------------------------------------
+ * Checkpoint / resume.  The state is plain arrays, so a checkpoint is a
+ * header (format tag, ABI version, nfields, precipitation rows, nlev, pitch,
+ * ncols and a hash of the scheme parameters) followed by dz, the fields and
+ * the precipitation rows as raw FP64 values in host byte order.  A run of N
+ * steps equals, bit for bit, k steps, save, load, N - k steps.
+ * nfields is CASIM_NFIELDS, or CASIM_NFIELDS_AEROSOL for the activated-
+ * aerosol state (whose precip has CASIM_NPRECIP + 1 rows).  Device pointers;
+ * both calls wait for `stream`.  params may be NULL (the defaults).
+ * casim_state_load rejects (CASIM_ERR_ARG) a file whose dimensions or
+ * parameter hash differ from the arguments; file errors give CASIM_ERR_IO. */
+#define CASIM_NFIELDS_AEROSOL 19
+int casim_state_save(const char *path, const casim_params *params, const casim_state *s, int ncols, int nlev,
+                     int nfields, void *stream);
+int casim_state_load(const char *path, const casim_params *params, const casim_state *s, int ncols, int nlev,
+                     int nfields, void *stream);
 
 /* Release the context and its device memory (waits for the device). NULL is a no-op. */
 void casim_free(casim_ctx *ctx);

@@ -14,7 +14,7 @@ DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(
     os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-shared", "-I" + INCLUDE]
+              "-Xcompiler", "-fPIC", "-shared", "-I" + INCLUDE, "-ldl"]
 
 
 def nvcc() -> str:

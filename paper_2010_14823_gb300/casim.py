@@ -30,7 +30,7 @@ EFLAG_CFL = 2
 EFLAG_TIMEOUT = 4
 NOALLOC_MAX_COLS = 1 << 20
 _ERRORS = {-1: "CASIM_ERR_ARG", -2: "CASIM_ERR_OOM", -3: "CASIM_ERR_CUDA",
-           -4: "CASIM_ERR_NONFINITE", -5: "CASIM_ERR_CFL", -6: "CASIM_ERR_TIMEOUT"}
+           -4: "CASIM_ERR_NONFINITE", -5: "CASIM_ERR_CFL", -6: "CASIM_ERR_TIMEOUT", -7: "CASIM_ERR_IO"}
 
 
 class CasimError(RuntimeError):
@@ -90,6 +90,9 @@ def lib():
         L.casim_step_host.argtypes = [vp, ps, i, i, d, vp]
         L.casim_step_host.restype = i
         L.casim_budget.argtypes = [vp, ps, i, i, vp, vp]
+        for name in ("casim_state_save", "casim_state_load"):
+            getattr(L, name).argtypes = [ctypes.c_char_p, ctypes.c_void_p, ps, i, i, i, vp]
+            getattr(L, name).restype = i
         L.casim_budget.restype = i
         L.casim_get_error.argtypes = [vp, ctypes.POINTER(u), vp]
         L.casim_get_error.restype = i
@@ -225,6 +228,20 @@ def casim_step_host(ctx, state: casim_state, ncols: int, nlev: int, dt: float, s
 
 def casim_budget(ctx, state: casim_state, ncols: int, nlev: int, out, stream=None):
     _check(lib().casim_budget(ctx, ctypes.byref(state), ncols, nlev, _ptr(out), _stream(stream)), "casim_budget")
+
+
+def casim_state_save(path: str, state: casim_state, ncols: int, nlev: int, nfields: int = NFIELDS, params=None,
+                     stream=None):
+    """Checkpoint a domain's device state (dz, fields, precip) to a file."""
+    _check(lib().casim_state_save(path.encode(), ctypes.byref(params) if params is not None else None,
+                                  ctypes.byref(state), ncols, nlev, nfields, _stream(stream)), "casim_state_save")
+
+
+def casim_state_load(path: str, state: casim_state, ncols: int, nlev: int, nfields: int = NFIELDS, params=None,
+                     stream=None):
+    """Restore a checkpoint into a domain's device arrays (same sizes and parameters)."""
+    _check(lib().casim_state_load(path.encode(), ctypes.byref(params) if params is not None else None,
+                                  ctypes.byref(state), ncols, nlev, nfields, _stream(stream)), "casim_state_load")
 
 
 def casim_get_error(ctx, stream=None) -> tuple[int, int]:

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "casim.h"
 #include "casim_device.cuh"
 #include "casim_batch.cuh"
@@ -22,6 +24,16 @@
 #include <random>
 
 using namespace casim_dev;
+
+// An NVTX range named after an entry point (or a phase of one) for the
+// duration of the host call: the enqueue of asynchronous work, or the whole
+// work of a synchronous call.  Costs nothing unless a profiler is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct casim_ctx {
   int precision = CASIM_FP64;
@@ -257,6 +269,7 @@ static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, 
 
 extern "C" int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, double *tend,
                                    void *stream) {
+  NvtxRange nvtx_range_("casim_step_tendency");
   if (!ctx || ctx->aero || !tend) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
@@ -270,6 +283,7 @@ extern "C" int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int nco
 }
 
 extern "C" int casim_step(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream) {
+  NvtxRange nvtx_range_("casim_step");
   if (!ctx) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
@@ -320,6 +334,7 @@ static cudaError_t copy_chunk(double *dev_fld, double *dev_precip, int W, const 
 
 extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, int nlev, double dt,
                                void *stream) {
+  NvtxRange nvtx_range_("casim_step_host");
   if (!ctx || ctx->aero) return CASIM_ERR_ARG;
   if (!h || ncols < 0 || nlev < 1 || nlev > kMaxLev || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
   if (ncols == 0) return CASIM_OK;
@@ -396,6 +411,7 @@ extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, 
 }
 
 extern "C" int casim_budget(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double *out, void *stream) {
+  NvtxRange nvtx_range_("casim_budget");
   if (!ctx || !out) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, 1.0);
   if (rc != CASIM_OK || ncols == 0) return rc;
@@ -588,6 +604,7 @@ static int enqueue_batch_step(casim_batch *b, double dt, cudaStream_t st) {
 }
 
 extern "C" int casim_batch_step(casim_ctx *ctx, casim_batch *b, double dt, void *stream) {
+  NvtxRange nvtx_range_("casim_batch_step");
   if (!ctx || !b || b->ctx != ctx || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
   return enqueue_batch_step(b, dt, (cudaStream_t)stream);
 }
@@ -619,6 +636,7 @@ extern "C" int casim_batch_get_config(const casim_batch *b, int *block, int *com
 
 extern "C" int casim_batch_tune(casim_ctx *ctx, casim_batch *b, double dt, int steps, void *stream,
                                 casim_tune_entry *table, int table_len) {
+  NvtxRange nvtx_range_("casim_batch_tune");
   if (!ctx || !b || b->ctx != ctx || steps < 1 || !(dt > 0.0) || table_len < 0 || (table_len && !table))
     return CASIM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
@@ -660,6 +678,7 @@ extern "C" int casim_batch_tune(casim_ctx *ctx, casim_batch *b, double dt, int s
 extern "C" int casim_batch_tune_steps(int steps) { return 12 * (steps + 1); }
 
 extern "C" int casim_batch_graph(casim_ctx *ctx, casim_batch *b, double dt, int nsteps, void *stream) {
+  NvtxRange nvtx_range_("casim_batch_graph");
   if (!ctx || !b || b->ctx != ctx || nsteps < 1 || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
   if (b->gexec) {
     cudaGraphExecDestroy(b->gexec);
@@ -693,6 +712,7 @@ extern "C" int casim_batch_graph(casim_ctx *ctx, casim_batch *b, double dt, int 
 }
 
 extern "C" int casim_batch_graph_launch(casim_batch *b, void *stream) {
+  NvtxRange nvtx_range_("casim_batch_graph_launch");
   if (!b || !b->gexec) return CASIM_ERR_ARG;
   CUDA_TRY(cudaGraphLaunch(b->gexec, (cudaStream_t)stream));
   b->ctx->launches += (long long)b->graph_steps * (b->compact ? 2 : 1);
@@ -772,6 +792,7 @@ static NoallocScratch *noalloc_scratch_ptr(int dev, int *rc) {
 
 extern "C" int casim_step_noalloc(const casim_params *params, int precision, const casim_state *s, int ncols,
                                   int nlev, double dt, void *stream, unsigned *flags) {
+  NvtxRange nvtx_range_("casim_step_noalloc");
   if (precision != CASIM_FP64 && precision != CASIM_MIXED) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK) return rc;
@@ -1150,6 +1171,7 @@ extern "C" int casim_mlp_set_engine(casim_mlp *m, int engine) {
 }
 
 extern "C" int casim_mlp_forward_host(casim_mlp *m, const float *Xn, int n, float *Y) {
+  NvtxRange nvtx_range_("casim_mlp_forward_host");
   if (!m || !Xn || !Y || n < 1) return CASIM_ERR_ARG;
   int rc = mlp_batch_ws(m, n);
   if (rc != CASIM_OK) return rc;
@@ -1194,6 +1216,7 @@ extern "C" int casim_mlp_loss_grad_host(casim_mlp *m, const float *Xn, const flo
 
 extern "C" int casim_mlp_data(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, float *X,
                               float *Y, float *M, long long *pts, long long cap, long long *rows, void *stream) {
+  NvtxRange nvtx_range_("casim_mlp_data");
   if (!ctx || ctx->warm || !X || !Y || !M || cap < 0 || !rows) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK) return rc;
@@ -1227,6 +1250,7 @@ extern "C" int casim_mlp_data(casim_ctx *ctx, const casim_state *s, int ncols, i
 
 extern "C" int casim_mlp_fit(casim_mlp *m, const float *X, const float *Y, const float *M, long long n, int steps,
                              int batch, float lr, unsigned long long seed, float *loss_hist, void *stream) {
+  NvtxRange nvtx_range_("casim_mlp_fit");
   if (!m || !X || !Y || !M || n < 2 || steps < 0 || batch < 1) return CASIM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   // normalisation and the out-of-distribution box from the data
@@ -1306,6 +1330,7 @@ extern "C" int casim_mlp_set_norm(casim_mlp *m, const float *stats) {
 
 extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_state *s, int ncols, int nlev,
                                     double dt, void *stream, long long *served) {
+  NvtxRange nvtx_range_("casim_step_surrogate");
   if (!ctx || ctx->warm || !m || !m->fitted || ctx->precision != CASIM_MIXED) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
@@ -1371,6 +1396,93 @@ extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_st
 }
 
 extern "C" long long casim_launch_count(const casim_ctx *ctx) { return ctx ? ctx->launches : -1; }
+
+// ---------------------------------------------------------------- checkpoints
+namespace {
+struct CkptHeader {
+  char tag[8];                 // "CASIMSV1"
+  int32_t abi, nfields, nprecip, nlev, pitch, ncols;
+  uint64_t params_hash;        // FNV-1a of the parameter block
+};
+
+uint64_t params_hash(const casim_params *params) {
+  casim_params p;
+  if (params) p = *params;
+  else casim_default_params(&p);
+  const unsigned char *b = reinterpret_cast<const unsigned char *>(&p);
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < sizeof(p); ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+int ckpt_check(const casim_state *s, int ncols, int nlev, int nfields) {
+  if (!s || !s->fld || !s->dz || !s->precip || ncols < 0 || nlev < 1 || nlev > kMaxLev) return CASIM_ERR_ARG;
+  if (s->pitch < ncols || s->pitch % 32 != 0) return CASIM_ERR_ARG;
+  if (nfields != CASIM_NFIELDS && nfields != CASIM_NFIELDS_AEROSOL) return CASIM_ERR_ARG;
+  return CASIM_OK;
+}
+}  // namespace
+
+extern "C" int casim_state_save(const char *path, const casim_params *params, const casim_state *s, int ncols,
+                                int nlev, int nfields, void *stream) {
+  NvtxRange nvtx_range_("casim_state_save");
+  if (!path) return CASIM_ERR_ARG;
+  int rc = ckpt_check(s, ncols, nlev, nfields);
+  if (rc != CASIM_OK) return rc;
+  CkptHeader h{};
+  std::memcpy(h.tag, "CASIMSV1", 8);
+  h.abi = CASIM_ABI_VERSION;
+  h.nfields = nfields;
+  h.nprecip = CASIM_NPRECIP + (nfields == CASIM_NFIELDS_AEROSOL);
+  h.nlev = nlev;
+  h.pitch = s->pitch;
+  h.ncols = ncols;
+  h.params_hash = params_hash(params);
+  const size_t nf = (size_t)nfields * nlev * s->pitch, np = (size_t)h.nprecip * s->pitch;
+  std::vector<double> buf(nlev + nf + np);
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(buf.data(), s->dz, (size_t)nlev * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(buf.data() + nlev, s->fld, nf * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(buf.data() + nlev + nf, s->precip, np * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return CASIM_ERR_IO;
+  const bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 && std::fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+  return (std::fclose(f) == 0 && ok) ? CASIM_OK : CASIM_ERR_IO;
+}
+
+extern "C" int casim_state_load(const char *path, const casim_params *params, const casim_state *s, int ncols,
+                                int nlev, int nfields, void *stream) {
+  NvtxRange nvtx_range_("casim_state_load");
+  if (!path) return CASIM_ERR_ARG;
+  int rc = ckpt_check(s, ncols, nlev, nfields);
+  if (rc != CASIM_OK) return rc;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return CASIM_ERR_IO;
+  CkptHeader h{};
+  if (std::fread(&h, sizeof h, 1, f) != 1) {
+    std::fclose(f);
+    return CASIM_ERR_IO;
+  }
+  if (std::memcmp(h.tag, "CASIMSV1", 8) != 0 || h.abi != CASIM_ABI_VERSION || h.nfields != nfields ||
+      h.nprecip != CASIM_NPRECIP + (nfields == CASIM_NFIELDS_AEROSOL) || h.nlev != nlev || h.pitch != s->pitch ||
+      h.ncols != ncols || h.params_hash != params_hash(params)) {
+    std::fclose(f);
+    return CASIM_ERR_ARG;
+  }
+  const size_t nf = (size_t)nfields * nlev * s->pitch, np = (size_t)h.nprecip * s->pitch;
+  std::vector<double> buf(nlev + nf + np);
+  const bool ok = std::fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+  std::fclose(f);
+  if (!ok) return CASIM_ERR_IO;
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(s->dz), buf.data(), (size_t)nlev * sizeof(double),
+                           cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(s->fld, buf.data() + nlev, nf * sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(s->precip, buf.data() + nlev + nf, np * sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return CASIM_OK;
+}
 
 extern "C" void casim_free(casim_ctx *ctx) {
   if (!ctx) return;

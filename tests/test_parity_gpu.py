@@ -504,3 +504,47 @@ def test_aerosol_context_rules():
             casim.casim_batch_create(ctx, [d.state], [64], [40])
     finally:
         casim.casim_free(ctx)
+
+
+
+# ------------------------------------------------------------------ checkpoint / resume
+@pytest.mark.parametrize("aerosol", [False, True])
+def test_checkpoint_resume_is_bitwise(tmp_path, aerosol):
+    """N steps equal k steps, save, load into fresh device memory, N - k steps,
+    bit for bit; a checkpoint of other sizes or parameters is refused."""
+    ncols, nlev = 97, 150
+    if aerosol:
+        fld, dz = _aero_state(ncols, nlev, seed=71)
+        flags, nf = casim.CASIM_WARM | casim.CASIM_AEROSOL, 19
+    else:
+        dz = synth.dz_stretched(nlev)
+        fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=71)
+        flags, nf = 0, 16
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=flags)
+    try:
+        ref = casim.Domain(fld, dz, ncols)
+        for _ in range(6):
+            casim.casim_step(ctx, ref.state, ncols, nlev, 1.0)
+        a = casim.Domain(fld, dz, ncols)
+        for _ in range(3):
+            casim.casim_step(ctx, a.state, ncols, nlev, 1.0)
+        path = str(tmp_path / "state.ckpt")
+        casim.casim_state_save(path, a.state, ncols, nlev, nf)
+        b = casim.Domain(np.zeros_like(fld), np.ones_like(dz), ncols)
+        casim.casim_state_load(path, b.state, ncols, nlev, nf)
+        for _ in range(3):
+            casim.casim_step(ctx, b.state, ncols, nlev, 1.0)
+        assert casim.casim_get_error(ctx)[0] == 0
+        (f1, p1), (f2, p2) = ref.numpy(), b.numpy()
+        assert np.array_equal(f1, f2) and np.array_equal(p1, p2)
+        assert np.array_equal(b.dz.cpu().numpy(), dz)
+        with pytest.raises(RuntimeError):                 # other column count
+            casim.casim_state_load(path, b.state, ncols - 1, nlev, nf)
+        other = casim.casim_default_params()
+        other.c_max = 0.5
+        with pytest.raises(RuntimeError):                 # other parameters
+            casim.casim_state_load(path, b.state, ncols, nlev, nf, params=other)
+        with pytest.raises(RuntimeError):                 # no such file
+            casim.casim_state_load(str(tmp_path / "missing"), b.state, ncols, nlev, nf)
+    finally:
+        casim.casim_free(ctx)
