@@ -22,6 +22,8 @@ NFIELDS = 16
 NPROG = 13
 NFIELDS_AERO = 19      # + free aerosol mass, aerosol mass in cloud, in rain
 NPROG_AERO = 16
+NFIELDS_3M = 17        # + the rain's sixth moment
+NPROG_3M = 14
 NPROC = 14
 SPECIES = {"c": 0, "r": 1, "i": 2, "s": 3, "g": 4}
 PROCS = ("aut", "acc", "scc", "scr", "evr", "nuc", "depi", "deps", "depg",
@@ -87,6 +89,24 @@ def lib():
         L.orc_point_cfg.argtypes = [pd, d, pd, i]
         L.orc_rates_cfg.restype = None
         L.orc_rates_cfg.argtypes = [pd, d, pd, i]
+        for name in ("orc_lambda_mu",):
+            getattr(L, name).restype = d
+            getattr(L, name).argtypes = [i, d, d, d]
+        L.orc_moment_mu.restype = d
+        L.orc_moment_mu.argtypes = [i, d, d, d, d, d]
+        L.orc_vent_integral_mu.restype = d
+        L.orc_vent_integral_mu.argtypes = [i, d, d, d, d]
+        for name in ("orc_vq_mu", "orc_vn_mu", "orc_vz_mu"):
+            getattr(L, name).restype = d
+            getattr(L, name).argtypes = [i, d, d, d]
+        L.orc_rain_mu.restype = d
+        L.orc_rain_mu.argtypes = [d, d, d]
+        L.orc_point_3m.restype = None
+        L.orc_point_3m.argtypes = [pd, d, pd]
+        L.orc_sediment_rain_3m.restype = u
+        L.orc_sediment_rain_3m.argtypes = [pd, pd, pd, pd, pd, i, d, pd, ctypes.POINTER(ctypes.c_int)]
+        L.orc_step_3m.restype = u
+        L.orc_step_3m.argtypes = [pd, ctypes.c_long, i, i, pd, pd, d, i]
         L.orc_point_aero.restype = None
         L.orc_point_aero.argtypes = [pd, d, pd]
         L.orc_step_aero.restype = u
@@ -247,4 +267,68 @@ def step_aero(fld: np.ndarray, ncols: int, dz: np.ndarray, dt: float, precip: np
         precip = np.zeros((5, pitch))
     assert precip.shape == (5, pitch) and precip.dtype == np.float64 and precip.flags["C_CONTIGUOUS"]
     err = lib().orc_step_aero(_dp(fld), pitch, ncols, nlev, _dp(dz), _dp(precip), dt, nthreads)
+    return precip, err
+
+
+# ------------------------------------------------------- triple-moment rain
+def lam_mu(sp: str, q: float, n: float, mu: float) -> float:
+    return lib().orc_lambda_mu(SPECIES[sp], q, n, mu)
+
+
+def moment_mu(sp: str, rho: float, q: float, lam_: float, k: float, mu: float) -> float:
+    return lib().orc_moment_mu(SPECIES[sp], rho, q, lam_, k, mu)
+
+
+def vent_integral_mu(sp: str, rho: float, q: float, lam_: float, mu: float) -> float:
+    return lib().orc_vent_integral_mu(SPECIES[sp], rho, q, lam_, mu)
+
+
+def vq_mu(sp: str, rho: float, lam_: float, mu: float) -> float:
+    return lib().orc_vq_mu(SPECIES[sp], rho, lam_, mu)
+
+
+def vn_mu(sp: str, rho: float, lam_: float, mu: float) -> float:
+    return lib().orc_vn_mu(SPECIES[sp], rho, lam_, mu)
+
+
+def vz_mu(sp: str, rho: float, lam_: float, mu: float) -> float:
+    return lib().orc_vz_mu(SPECIES[sp], rho, lam_, mu)
+
+
+def rain_mu(q: float, n: float, z: float) -> float:
+    """The rain shape parameter diagnosed from its mass, number and sixth moment."""
+    return lib().orc_rain_mu(q, n, z)
+
+
+def point_3m(state: np.ndarray, dt: float) -> np.ndarray:
+    """Warm point with triple-moment rain: state[17] -> [13 prognostic, z]."""
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    assert st.shape == (NFIELDS_3M,)
+    out = np.zeros(NPROG_3M)
+    lib().orc_point_3m(_dp(st), dt, _dp(out))
+    return out
+
+
+def sediment_rain_3m(q, n, z, rho, dz, dt: float):
+    """Rain sedimentation of q, n, z [nlev] (copied); returns (q, n, z, precip, nsub, err)."""
+    q, n, z = (np.array(x, dtype=np.float64, order="C") for x in (q, n, z))
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    pr = np.zeros(1)
+    ns = np.zeros(1, dtype=np.int32)
+    err = lib().orc_sediment_rain_3m(_dp(q), _dp(n), _dp(z), _dp(rho), _dp(dz), rho.shape[0], dt, _dp(pr),
+                                      ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return q, n, z, pr[0], int(ns[0]), err
+
+
+def step_3m(fld: np.ndarray, ncols: int, dz: np.ndarray, dt: float, precip: np.ndarray | None = None,
+            nthreads: int = 0):
+    """Warm step with triple-moment rain, in place on fld [17][nlev][pitch];
+    precip [4][pitch] accumulated.  Returns (precip, err)."""
+    assert fld.dtype == np.float64 and fld.flags["C_CONTIGUOUS"] and fld.shape[0] == NFIELDS_3M
+    nlev, pitch = fld.shape[1], fld.shape[2]
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    if precip is None:
+        precip = np.zeros((4, pitch))
+    err = lib().orc_step_3m(_dp(fld), pitch, ncols, nlev, _dp(dz), _dp(precip), dt, nthreads)
     return precip, err

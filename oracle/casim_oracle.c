@@ -64,6 +64,7 @@ static const double KC_SB = 9.44e9, NU_C = 1.0;   /* cloud self-collection */
 static const double KR_SB = 5.78;                 /* rain self-collection */
 static const double MEY_A = 1e3, MEY_B = -0.639, MEY_C = 12.96;
 static const double ARG_RM = 0.05e-6, ARG_SIGMA = 1.5, ARG_KAPPA = 0.61;
+static const double MU3_MAX = 20.0;     /* largest rain shape parameter of the triple-moment scheme */
 static const double SURFT = 0.0761, MW = 0.018015, MA = 0.028965, RGAS = 8.314;
 static const double E_RIM = 1.0;
 static const double CMAX = 1.0;        /* Courant limit per substep */
@@ -178,57 +179,96 @@ double orc_arg_nact(double N, double w, double T, double p) {
 }
 
 /* ------------------------------------------------ gamma-distribution algebra */
-double orc_lambda(int sp, double q, double n) {
+/* The functions below take the shape parameter mu explicitly; the exported
+   ones without _mu use the species' fixed mu (double-moment scheme). */
+double orc_lambda_mu(int sp, double q, double n, double mu) {
   /* n(D) = N0 D^mu exp(-lambda D) with m(D) = a D^b:
        q / n = a Gamma(mu+b+1) / (Gamma(mu+1) lambda^b)
      lambda is clamped so the mean diameter (mu+1)/lambda stays inside
      [dmin, dmax]; a non-positive number gives the largest particles. */
   const orc_species *s = &SP[sp];
   double nn = n > 0.0 ? n : 0.0;
-  double lam = pow(s->a * tgamma(s->mu + s->b + 1.0) / tgamma(s->mu + 1.0) * nn / q, 1.0 / s->b);
-  double lo = (s->mu + 1.0) / s->dmax, hi = (s->mu + 1.0) / s->dmin;
+  double lam = pow(s->a * tgamma(mu + s->b + 1.0) / tgamma(mu + 1.0) * nn / q, 1.0 / s->b);
+  double lo = (mu + 1.0) / s->dmax, hi = (mu + 1.0) / s->dmin;
   if (lam < lo) lam = lo;
   if (lam > hi) lam = hi;
   return lam;
 }
 
-double orc_moment(int sp, double rho, double q, double lam, double k) {
+double orc_moment_mu(int sp, double rho, double q, double lam, double k, double mu) {
   /* M_k = int D^k n(D) dD per m^3, with N0 fixed by the mass content
      rho q = a N0 Gamma(mu+b+1) / lambda^(mu+b+1):
        M_k = (rho q / a) Gamma(mu+k+1) / Gamma(mu+b+1) * lambda^(b-k) */
   const orc_species *s = &SP[sp];
-  return rho * q / s->a * tgamma(s->mu + k + 1.0) / tgamma(s->mu + s->b + 1.0) * pow(lam, s->b - k);
+  return rho * q / s->a * tgamma(mu + k + 1.0) / tgamma(mu + s->b + 1.0) * pow(lam, s->b - k);
 }
 
-double orc_vent_integral(int sp, double rho, double q, double lam) {
+double orc_vent_integral_mu(int sp, double rho, double q, double lam, double mu) {
   /* int D f_v(D) n(D) dD with f_v = 0.78 + 0.31 Sc^(1/3) Re^(1/2),
      Re = V(D) D / nu, V(D) = cv D^dv (rho0/rho)^0.4, Sc = nu / Dv. */
   const orc_species *s = &SP[sp];
   double nu = MUAIR / rho;
   double sc = nu / DV;
   double vfac = s->cv * pow(RHO0 / rho, 0.4);
-  return 0.78 * orc_moment(sp, rho, q, lam, 1.0) +
-         0.31 * cbrt(sc) * sqrt(vfac / nu) * orc_moment(sp, rho, q, lam, 0.5 * (s->dv + 3.0));
+  return 0.78 * orc_moment_mu(sp, rho, q, lam, 1.0, mu) +
+         0.31 * cbrt(sc) * sqrt(vfac / nu) * orc_moment_mu(sp, rho, q, lam, 0.5 * (s->dv + 3.0), mu);
 }
 
-double orc_vq(int sp, double rho, double lam) {
-  /* mass-weighted fall speed, capped */
+/* fall speed weighted by the k-th moment, int D^k V n dD / int D^k n dD, capped */
+static double vk_mu(int sp, double rho, double lam, double mu, double k) {
   const orc_species *s = &SP[sp];
-  double v = s->cv * pow(RHO0 / rho, 0.4) * tgamma(s->mu + s->b + s->dv + 1.0) /
-             tgamma(s->mu + s->b + 1.0) * pow(lam, -s->dv);
+  double v = s->cv * pow(RHO0 / rho, 0.4) * tgamma(mu + k + s->dv + 1.0) / tgamma(mu + k + 1.0) * pow(lam, -s->dv);
   return v < s->vmax ? v : s->vmax;
 }
 
-double orc_vn(int sp, double rho, double lam) {
-  /* number-weighted fall speed, capped */
-  const orc_species *s = &SP[sp];
-  double v = s->cv * pow(RHO0 / rho, 0.4) * tgamma(s->mu + s->dv + 1.0) / tgamma(s->mu + 1.0) *
-             pow(lam, -s->dv);
-  return v < s->vmax ? v : s->vmax;
+double orc_vq_mu(int sp, double rho, double lam, double mu) { return vk_mu(sp, rho, lam, mu, SP[sp].b); }
+double orc_vn_mu(int sp, double rho, double lam, double mu) { return vk_mu(sp, rho, lam, mu, 0.0); }
+double orc_vz_mu(int sp, double rho, double lam, double mu) { return vk_mu(sp, rho, lam, mu, 2.0 * SP[sp].b); }
+
+double orc_lambda(int sp, double q, double n) { return orc_lambda_mu(sp, q, n, SP[sp].mu); }
+double orc_moment(int sp, double rho, double q, double lam, double k) {
+  return orc_moment_mu(sp, rho, q, lam, k, SP[sp].mu);
+}
+double orc_vent_integral(int sp, double rho, double q, double lam) {
+  return orc_vent_integral_mu(sp, rho, q, lam, SP[sp].mu);
+}
+double orc_vq(int sp, double rho, double lam) { return orc_vq_mu(sp, rho, lam, SP[sp].mu); }
+double orc_vn(int sp, double rho, double lam) { return orc_vn_mu(sp, rho, lam, SP[sp].mu); }
+
+/* Triple-moment rain: the shape parameter from q, n and the sixth moment z
+   (m^6 per kg of air).  With m = a D^3, M3 = q / a per kg and
+     G = z n / M3^2 = (mu+4)(mu+5)(mu+6) / ((mu+1)(mu+2)(mu+3)),
+   decreasing from 20 at mu = 0 to 1 as mu -> inf.  Start from the root of
+   G^(1/3) = (mu+5)/(mu+2), then four Newton steps on ln G(mu) - ln G_obs,
+   every iterate clamped to [0, MU3_MAX].  Rain absent, or n or z not
+   positive: the species' fixed mu. */
+double orc_rain_mu(double q, double n, double z) {
+  if (!(q > QMIN) || !(n > 0.0) || !(z > 0.0)) return SP[ORC_R].mu;
+  double m3 = q / SP[ORC_R].a;
+  double lg = log(z * n / (m3 * m3));
+  double g = cbrt(z * n / (m3 * m3));
+  double mu = g > 1.0 ? (5.0 - 2.0 * g) / (g - 1.0) : MU3_MAX;
+  if (mu < 0.0) mu = 0.0;
+  if (mu > MU3_MAX) mu = MU3_MAX;
+  for (int it = 0; it < 4; ++it) {
+    double f = log((mu + 4.0) * (mu + 5.0) * (mu + 6.0) / ((mu + 1.0) * (mu + 2.0) * (mu + 3.0))) - lg;
+    double fp = 1.0 / (mu + 4.0) + 1.0 / (mu + 5.0) + 1.0 / (mu + 6.0) - 1.0 / (mu + 1.0) - 1.0 / (mu + 2.0) -
+                1.0 / (mu + 3.0);
+    mu -= f / fp;
+    if (mu < 0.0) mu = 0.0;
+    if (mu > MU3_MAX) mu = MU3_MAX;
+  }
+  return mu;
 }
 
 /* --------------------------------------------------------- a4..a9 rates */
-void orc_rates_cfg(const double *st, double dt, double *R, int warm) {
+static void rates_core(const double *st, double dt, double *R, int warm, double mu_r);
+
+void orc_rates_cfg(const double *st, double dt, double *R, int warm) { rates_core(st, dt, R, warm, SP[ORC_R].mu); }
+
+/* mu_r: the rain shape parameter (the species' own, or the triple-moment
+   scheme's diagnosed one) */
+static void rates_core(const double *st, double dt, double *R, int warm, double mu_r) {
   /* Rates in kg kg^-1 s^-1 (masses) except SCC, SCR (number kg^-1 s^-1) and
      NUC (new crystals kg^-1 s^-1).  All are >= 0 except DEPx, which is
      positive for deposition and negative for sublimation.  MLTx is the
@@ -262,8 +302,8 @@ void orc_rates_cfg(const double *st, double dt, double *R, int warm) {
     R[ORC_SCR] = KR_SB * rho * (nr > 0.0 ? nr : 0.0) * qr;
     /* a5 rain evaporation in subsaturated air: capacitance D/2 */
     if (Sw < 1.0) {
-      double lam = orc_lambda(ORC_R, qr, nr);
-      R[ORC_EVR] = 2.0 * PI * (1.0 - Sw) * orc_vent_integral(ORC_R, rho, qr, lam) / (rho * (Aw + Bw));
+      double lam = orc_lambda_mu(ORC_R, qr, nr, mu_r);
+      R[ORC_EVR] = 2.0 * PI * (1.0 - Sw) * orc_vent_integral_mu(ORC_R, rho, qr, lam, mu_r) / (rho * (Aw + Bw));
     }
   }
   if (warm) return;
@@ -341,9 +381,10 @@ typedef struct {
   double na0, dn_act;       /* free aerosol number before activation; droplets activated */
   double qc_post, qr_post;  /* cloud and rain after activation (what the rates see) */
   double tau_cr, tau_rv;    /* cloud -> rain (autoconversion + accretion), rain -> vapour */
+  double tau_aut, nr_aut;   /* autoconversion: rain mass, new drops */
 } orc_record;
 
-static void point_core(const double *in0, double dt, double *out, int warm, orc_record *rec) {
+static void point_core(const double *in0, double dt, double *out, int warm, orc_record *rec, double mu_r) {
   /* warm: the ice fields are not part of the warm state; they are treated as
      absent and passed through unchanged */
   double in[ORC_NFIELDS];
@@ -362,12 +403,12 @@ static void point_core(const double *in0, double dt, double *out, int warm, orc_
     rec->dn_act = in[ORC_NA] - st[ORC_NA];
     rec->qc_post = st[ORC_QC];
     rec->qr_post = st[ORC_QR];
-    rec->tau_cr = rec->tau_rv = 0.0;
+    rec->tau_cr = rec->tau_rv = rec->tau_aut = rec->nr_aut = 0.0;
   }
 
   /* a4..a9 from the post-activation state */
   double R[ORC_NPROC];
-  orc_rates_cfg(st, dt, R, warm);
+  rates_core(st, dt, R, warm, mu_r);
 
   double qc = st[ORC_QC], qr = st[ORC_QR];
   orc_transfer tr[ORC_NPROC];
@@ -429,17 +470,46 @@ static void point_core(const double *in0, double dt, double *out, int warm, orc_
       st[tr[j].mdst] += tau;
       st[ORC_T] += tau * tr[j].heat / CP;
       if (rec && (j == 0 || j == 1)) rec->tau_cr += tau;   /* autoconversion, accretion */
+      if (rec && j == 0) rec->tau_aut = tau;
       if (rec && j == 4) rec->tau_rv += tau;               /* rain evaporation */
     }
     if (tr[j].nsink > 0.0) st[tr[j].nsrc] -= g * tr[j].nsink * dt;
-    if (tr[j].ndst >= 0 && tr[j].nsource > 0.0) st[tr[j].ndst] += g * tr[j].nsource * dt;
+    if (tr[j].ndst >= 0 && tr[j].nsource > 0.0) {
+      st[tr[j].ndst] += g * tr[j].nsource * dt;
+      if (rec && j == 0) rec->nr_aut = g * tr[j].nsource * dt;
+    }
   }
   if (warm)
     for (int i = 0; i < 6; ++i) st[ICE_FIELDS[i]] = in0[ICE_FIELDS[i]];
   memcpy(out, st, ORC_NPROG * sizeof(double));
 }
 
-void orc_point_cfg(const double *in, double dt, double *out, int warm) { point_core(in, dt, out, warm, NULL); }
+void orc_point_cfg(const double *in, double dt, double *out, int warm) {
+  point_core(in, dt, out, warm, NULL, SP[ORC_R].mu);
+}
+
+/* Triple-moment rain in the warm configuration (Section 2: CASIM is a
+   three-moment scheme): the rain's sixth moment z (m^6 per kg of air) is the
+   third prognostic moment.  The step's rates see the shape parameter
+   diagnosed from the input (orc_rain_mu); z then changes as
+     - accretion, self-collection and evaporation act at that fixed shape:
+       z' = z (q'/q)^2 (n/n'), q', n' the rain without the autoconversion
+       part (the shape measure G = z n / M3^2 unchanged);
+     - autoconversion adds drops of one size D0 = 2 r0: + n_aut D0^6.
+   in[ORC_NFIELDS_3M] -> out[ORC_NPROG_3M] (13 prognostic fields, then z). */
+void orc_point_3m(const double *in, double dt, double *out) {
+  double mu = orc_rain_mu(in[ORC_QR], in[ORC_NR], in[ORC_ZR]);
+  orc_record r;
+  double o[ORC_NPROG];
+  point_core(in, dt, o, 1, &r, mu);
+  memcpy(out, o, sizeof o);
+  double q0 = in[ORC_QR], n0 = in[ORC_NR], z0 = in[ORC_ZR];
+  double q1 = o[ORC_QR] - r.tau_aut, n1 = o[ORC_NR] - r.nr_aut;
+  double z = 0.0;
+  if (q0 > QMIN && n0 > 0.0 && q1 > 0.0 && n1 > 0.0) z = z0 * (q1 / q0) * (q1 / q0) * (n0 / n1);
+  double d0 = 2.0 * RR0, d3 = d0 * d0 * d0;
+  out[ORC_NPROG] = z + r.nr_aut * (d3 * d3);
+}
 
 void orc_rates(const double *st, double dt, double *R) { orc_rates_cfg(st, dt, R, 0); }
 
@@ -462,7 +532,7 @@ void orc_point(const double *in, double dt, double *out) { orc_point_cfg(in, dt,
 void orc_point_aero(const double *in, double dt, double *out) {
   orc_record r;
   double o[ORC_NPROG];
-  point_core(in, dt, o, 1, &r);
+  point_core(in, dt, o, 1, &r, SP[ORC_R].mu);
   memcpy(out, o, sizeof o);
   double ma = in[ORC_MA], mac = in[ORC_MAC], mar = in[ORC_MAR], d;
   if (r.evap > 0.0 && r.qc0 > 0.0) {
@@ -492,18 +562,28 @@ void orc_point_aero(const double *in, double dt, double *out) {
 
 /* ------------------------------------------------------ a12 sedimentation */
 static unsigned sediment_species(double *q, double *n, const double *rho, const double *dz, int nlev, double dt,
-                                 double *precip, int *nsub, int nspecies, double *aer, double *aprecip);
+                                 double *precip, int *nsub, int nspecies, double *aer, double *aprecip,
+                                 double *zr);
 
 unsigned orc_sediment_column(double *q, double *n, const double *rho, const double *dz,
                              int nlev, double dt, double *precip, int *nsub) {
-  return sediment_species(q, n, rho, dz, nlev, dt, precip, nsub, 4, NULL, NULL);
+  return sediment_species(q, n, rho, dz, nlev, dt, precip, nsub, 4, NULL, NULL, NULL);
+}
+
+unsigned orc_sediment_rain_3m(double *q, double *n, double *z, const double *rho, const double *dz, int nlev,
+                              double dt, double *precip, int *nsub) {
+  return sediment_species(q, n, rho, dz, nlev, dt, precip, nsub, 1, NULL, NULL, z);
 }
 
 /* the first nspecies of r, i, s, g (warm configuration: rain only); aer (may
    be NULL): aerosol mass in rain, moved with the rain's mass-weighted speed,
-   its surface flux accumulated in *aprecip */
+   its surface flux accumulated in *aprecip; zr (may be NULL): the rain's
+   sixth moment (triple-moment scheme), moved with the sixth-moment-weighted
+   speed, every rain speed then taken at the shape diagnosed per level and
+   substep */
 static unsigned sediment_species(double *q, double *n, const double *rho, const double *dz, int nlev, double dt,
-                                 double *precip, int *nsub, int nspecies, double *aer, double *aprecip) {
+                                 double *precip, int *nsub, int nspecies, double *aer, double *aprecip,
+                                 double *zr) {
   /* For x in r, i, s, g: F_k = rho_k q_k Vq_k (mass), G_k = rho_k n_k Vn_k
      (number), fluxes downward.  Per substep of length dt/n_sub, with all
      fluxes taken from the substep's starting state:
@@ -518,14 +598,17 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
   double *F = (double *)malloc(sizeof(double) * (size_t)(nlev + 1));
   double *G = (double *)malloc(sizeof(double) * (size_t)(nlev + 1));
   double *A = (double *)malloc(sizeof(double) * (size_t)(nlev + 1));
+  double *H = (double *)malloc(sizeof(double) * (size_t)(nlev + 1));
   for (int m = 0; m < nspecies; ++m) {
     int sp = spx[m];
     double *qq = q + (size_t)m * nlev, *nn = n + (size_t)m * nlev;
+    const int tri = zr != NULL && m == 0;
     double cmax = 0.0;
     for (int k = 0; k < nlev; ++k) {
       if (!(qq[k] > QMIN)) continue;
-      double lam = orc_lambda(sp, qq[k], nn[k]);
-      double c = orc_vq(sp, rho[k], lam) * dt / dz[k];
+      double mu = tri ? orc_rain_mu(qq[k], nn[k], zr[k]) : SP[sp].mu;
+      double lam = orc_lambda_mu(sp, qq[k], nn[k], mu);
+      double c = orc_vq_mu(sp, rho[k], lam, mu) * dt / dz[k];
       if (c > cmax) cmax = c;
     }
     int ns = (int)ceil(cmax / CMAX);
@@ -539,27 +622,36 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
         F[k] = 0.0;
         G[k] = 0.0;
         A[k] = 0.0;
+        H[k] = 0.0;
         if (qq[k] > QMIN) {
-          double lam = orc_lambda(sp, qq[k], nn[k]);
+          double mu = tri ? orc_rain_mu(qq[k], nn[k], zr[k]) : SP[sp].mu;
+          double lam = orc_lambda_mu(sp, qq[k], nn[k], mu);
           /* a level never loses more than it holds within one substep: the
              speed is limited to dz_k / dts (binds only when a later substep's
              speeds exceed the maximum that set n_sub) */
           double vlim = dz[k] / dts;
-          double vq = orc_vq(sp, rho[k], lam), vn = orc_vn(sp, rho[k], lam);
+          double vq = orc_vq_mu(sp, rho[k], lam, mu), vn = orc_vn_mu(sp, rho[k], lam, mu);
           if (vq > vlim) vq = vlim;
           if (vn > vlim) vn = vlim;
           F[k] = rho[k] * qq[k] * vq;
           G[k] = rho[k] * (nn[k] > 0.0 ? nn[k] : 0.0) * vn;
           if (with_aer) A[k] = rho[k] * aer[k] * vq;
+          if (tri) {
+            double vz = orc_vz_mu(sp, rho[k], lam, mu);
+            if (vz > vlim) vz = vlim;
+            H[k] = rho[k] * (zr[k] > 0.0 ? zr[k] : 0.0) * vz;
+          }
         }
       }
       F[nlev] = 0.0;
       G[nlev] = 0.0;
       A[nlev] = 0.0;
+      H[nlev] = 0.0;
       for (int k = 0; k < nlev; ++k) {
         qq[k] += dts * (F[k + 1] - F[k]) / (rho[k] * dz[k]);
         nn[k] += dts * (G[k + 1] - G[k]) / (rho[k] * dz[k]);
         if (with_aer) aer[k] += dts * (A[k + 1] - A[k]) / (rho[k] * dz[k]);
+        if (tri) zr[k] += dts * (H[k + 1] - H[k]) / (rho[k] * dz[k]);
       }
       precip[m] += F[0] * dts;
       if (with_aer) *aprecip += A[0] * dts;
@@ -568,16 +660,18 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
   free(F);
   free(G);
   free(A);
+  free(H);
   return err;
 }
 
 /* ----------------------------------------------------------- full step */
-/* aero: the state has ORC_NFIELDS_AERO fields and precip 5 rows (warm only) */
+/* aero: the state has ORC_NFIELDS_AERO fields and precip 5 rows (warm only);
+   tri: the state has ORC_NFIELDS_3M fields (warm only) */
 static unsigned step_column(double *fld, long pitch, int nlev, int c, const double *dz,
-                            double *precip, int *nsub, double dt, int warm, int aero) {
+                            double *precip, int *nsub, double dt, int warm, int aero, int tri) {
   unsigned err = 0;
   long fs = (long)nlev * pitch; /* field stride */
-  const int nfields = aero ? ORC_NFIELDS_AERO : ORC_NFIELDS;
+  const int nfields = aero ? ORC_NFIELDS_AERO : tri ? ORC_NFIELDS_3M : ORC_NFIELDS;
   double in[ORC_NFIELDS_AERO], out[ORC_NPROG_AERO];
   const int map[ORC_NPROG_AERO] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, ORC_MA, ORC_MAC, ORC_MAR};
   for (int k = 0; k < nlev; ++k) {
@@ -585,18 +679,23 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
     if (aero) {
       orc_point_aero(in, dt, out);
       for (int f = 0; f < ORC_NPROG_AERO; ++f) fld[map[f] * fs + (long)k * pitch + c] = out[f];
+    } else if (tri) {
+      orc_point_3m(in, dt, out);
+      for (int f = 0; f < ORC_NPROG; ++f) fld[f * fs + (long)k * pitch + c] = out[f];
+      fld[ORC_ZR * fs + (long)k * pitch + c] = out[ORC_NPROG];
     } else {
       orc_point_cfg(in, dt, out, warm);
       for (int f = 0; f < ORC_NPROG; ++f) fld[f * fs + (long)k * pitch + c] = out[f];
     }
   }
-  double *buf = (double *)malloc(sizeof(double) * (size_t)(10 * nlev));
-  double *q = buf, *n = buf + 4 * nlev, *rho = buf + 8 * nlev, *aer = buf + 9 * nlev;
+  double *buf = (double *)malloc(sizeof(double) * (size_t)(11 * nlev));
+  double *q = buf, *n = buf + 4 * nlev, *rho = buf + 8 * nlev, *aer = buf + 9 * nlev, *zr = buf + 10 * nlev;
   static const int qf[4] = {ORC_QR, ORC_QI, ORC_QS, ORC_QG};
   static const int nf[4] = {ORC_NR, ORC_NI, ORC_NS, ORC_NG};
   for (int k = 0; k < nlev; ++k) {
     rho[k] = fld[ORC_RHO * fs + (long)k * pitch + c];
     aer[k] = aero ? fld[ORC_MAR * fs + (long)k * pitch + c] : 0.0;
+    zr[k] = tri ? fld[ORC_ZR * fs + (long)k * pitch + c] : 0.0;
     for (int m = 0; m < 4; ++m) {
       q[m * nlev + k] = fld[qf[m] * fs + (long)k * pitch + c];
       n[m * nlev + k] = fld[nf[m] * fs + (long)k * pitch + c];
@@ -606,7 +705,9 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
   int ns[4] = {1, 1, 1, 1};
   const int nsp = warm ? 1 : 4;
   double apr = 0.0;
-  err |= sediment_species(q, n, rho, dz, nlev, dt, pr, ns, nsp, aero ? aer : NULL, &apr);
+  err |= sediment_species(q, n, rho, dz, nlev, dt, pr, ns, nsp, aero ? aer : NULL, &apr, tri ? zr : NULL);
+  if (tri)
+    for (int k = 0; k < nlev; ++k) fld[ORC_ZR * fs + (long)k * pitch + c] = zr[k];
   if (aero) {
     for (int k = 0; k < nlev; ++k) fld[ORC_MAR * fs + (long)k * pitch + c] = aer[k];
     precip[4 * pitch + c] += apr;
@@ -627,6 +728,7 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
     if (aero)
       for (int f = ORC_MA; f <= ORC_MAR; ++f)
         if (!isfinite(fld[f * fs + (long)k * pitch + c])) err |= ORC_ERR_NONFINITE;
+    if (tri && !isfinite(fld[ORC_ZR * fs + (long)k * pitch + c])) err |= ORC_ERR_NONFINITE;
   }
   return err;
 }
@@ -639,7 +741,7 @@ unsigned orc_step_cfg(double *fld, long pitch, int ncols, int nlev, const double
   if (nthreads <= 0) nthreads = omp_get_max_threads();
 #pragma omp parallel for schedule(guided) num_threads(nthreads) reduction(| : err)
 #endif
-  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, nsub, dt, warm, 0);
+  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, nsub, dt, warm, 0, 0);
   (void)nthreads;
   return err;
 }
@@ -652,7 +754,20 @@ unsigned orc_step_aero(double *fld, long pitch, int ncols, int nlev, const doubl
   if (nthreads <= 0) nthreads = omp_get_max_threads();
 #pragma omp parallel for schedule(guided) num_threads(nthreads) reduction(| : err)
 #endif
-  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, NULL, dt, 1, 1);
+  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, NULL, dt, 1, 1, 0);
+  (void)nthreads;
+  return err;
+}
+
+unsigned orc_step_3m(double *fld, long pitch, int ncols, int nlev, const double *dz, double *precip, double dt,
+                     int nthreads) {
+  unsigned err = 0;
+  if (nlev <= 0 || ncols <= 0) return 0;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(guided) num_threads(nthreads) reduction(| : err)
+#endif
+  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, NULL, dt, 1, 0, 1);
   (void)nthreads;
   return err;
 }

@@ -32,6 +32,10 @@ enum {
    rain mar (kg/kg) -- and a fifth precipitation row (aerosol deposited). */
 enum { ORC_MA = ORC_NFIELDS, ORC_MAC, ORC_MAR, ORC_NFIELDS_AERO };
 #define ORC_NPROG_AERO (ORC_NPROG + 3)
+/* Triple-moment rain extension (warm configuration): one more field after
+   the 16 above, the rain's sixth moment z (m^6 per kg of air). */
+enum { ORC_ZR = ORC_NFIELDS, ORC_NFIELDS_3M };
+#define ORC_NPROG_3M (ORC_NPROG + 1)
 
 /* Hydrometeor species index. */
 enum { ORC_C = 0, ORC_R, ORC_I, ORC_S, ORC_G, ORC_NSPECIES };
@@ -91,6 +95,27 @@ unsigned orc_step_cfg(double *fld, long pitch, int ncols, int nlev, const double
    s, g, aerosol).  The first 16 fields and 4 precipitation rows are exactly
    those of orc_step_cfg(..., warm = 1). */
 void   orc_point_aero(const double *in, double dt, double *out);
+/* Gamma-distribution algebra with an explicit shape parameter mu (the
+   functions without _mu use the species' fixed mu); the k-th-moment-weighted
+   fall speeds for k = b (mass), 0 (number), 2b (sixth moment). */
+double orc_lambda_mu(int sp, double q, double n, double mu);
+double orc_moment_mu(int sp, double rho, double q, double lam, double k, double mu);
+double orc_vent_integral_mu(int sp, double rho, double q, double lam, double mu);
+double orc_vq_mu(int sp, double rho, double lam, double mu);
+double orc_vn_mu(int sp, double rho, double lam, double mu);
+double orc_vz_mu(int sp, double rho, double lam, double mu);
+/* Triple-moment warm rain: the shape parameter diagnosed from q, n, z; a
+   point in[ORC_NFIELDS_3M] -> out[ORC_NPROG_3M]; rain sedimentation of q, n,
+   z (all [nlev]) with the per-level shape; a step over
+   fld[ORC_NFIELDS_3M][nlev][pitch] with precip[4][pitch].  The first 16
+   fields evolve as in the warm configuration, except that rain evaporation
+   and the rain fall speeds use the diagnosed shape. */
+double orc_rain_mu(double q, double n, double z);
+void   orc_point_3m(const double *in, double dt, double *out);
+unsigned orc_sediment_rain_3m(double *q, double *n, double *z, const double *rho, const double *dz, int nlev,
+                              double dt, double *precip, int *nsub);
+unsigned orc_step_3m(double *fld, long pitch, int ncols, int nlev, const double *dz, double *precip, double dt,
+                     int nthreads);
 unsigned orc_step_aero(double *fld, long pitch, int ncols, int nlev, const double *dz,
                        double *precip, double dt, int nthreads);
 /* Parameter lookup by name for the tests (returns NaN for an unknown name). */
