@@ -137,6 +137,21 @@ int casim_default_params(casim_params *p);
    entry points reject such a context (CASIM_ERR_ARG). */
 #define CASIM_AEROSOL 2
 
+/* casim_init flag, with CASIM_WARM only (not with CASIM_AEROSOL): triple-
+   moment rain (Section 2: CASIM is a three-moment bulk scheme).  The state
+   has 17 fields -- the 16 above, then zr, the rain's sixth moment (m^6 per kg
+   of air, the radar reflectivity factor per unit mass).  The rain's shape
+   parameter mu is diagnosed at every point from
+     G = zr nr / (qr/a)^2 = (mu+4)(mu+5)(mu+6) / ((mu+1)(mu+2)(mu+3))
+   (mu in [0, 20]; the species' fixed mu where rain is absent); rain
+   evaporation and the rain fall speeds use it, and zr sediments with the
+   sixth-moment-weighted speed.  Accretion, self-collection and evaporation
+   change zr at the diagnosed shape, zr (q'/q)^2 (n/n'); autoconversion adds
+   its new drops of diameter 2 r_r0 as (2 r_r0)^6 each.  Requires the rain
+   mass exponent b = 3.  Supported by casim_step (both precisions) and the
+   checkpoint calls; the other step entry points reject such a context. */
+#define CASIM_THREE_MOMENT 4
+
 /* Create a context on the current CUDA device (Section 3.2: the one-off
    set-up that copies constants and allocates device memory).  `params` may be
    NULL for the defaults; `precision` is a casim_precision; `flags` is 0 or
@@ -352,12 +367,14 @@ const char *casim_last_cuda_error(void);
  * ncols and a hash of the scheme parameters) followed by dz, the fields and
  * the precipitation rows as raw FP64 values in host byte order.  A run of N
  * steps equals, bit for bit, k steps, save, load, N - k steps.
- * nfields is CASIM_NFIELDS, or CASIM_NFIELDS_AEROSOL for the activated-
- * aerosol state (whose precip has CASIM_NPRECIP + 1 rows).  Device pointers;
+ * nfields is CASIM_NFIELDS, CASIM_NFIELDS_3MOM for the triple-moment state,
+ * or CASIM_NFIELDS_AEROSOL for the activated-aerosol state (whose precip has
+ * CASIM_NPRECIP + 1 rows).  Device pointers;
  * both calls wait for `stream`.  params may be NULL (the defaults).
  * casim_state_load rejects (CASIM_ERR_ARG) a file whose dimensions or
  * parameter hash differ from the arguments; file errors give CASIM_ERR_IO. */
 #define CASIM_NFIELDS_AEROSOL 19
+#define CASIM_NFIELDS_3MOM 17
 int casim_state_save(const char *path, const casim_params *params, const casim_state *s, int ncols, int nlev,
                      int nfields, void *stream);
 int casim_state_load(const char *path, const casim_params *params, const casim_state *s, int ncols, int nlev,

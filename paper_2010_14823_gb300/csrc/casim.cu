@@ -39,6 +39,7 @@ struct casim_ctx {
   int precision = CASIM_FP64;
   bool warm = false;   // CASIM_WARM: the warm configuration (liquid water only)
   bool aero = false;   // CASIM_AEROSOL: with activated-aerosol mass (19-field state, 5 precip rows)
+  bool tri = false;    // CASIM_THREE_MOMENT: triple-moment rain (17-field state)
   int device = 0;
   int nsm = 1;
   KParams kp;
@@ -167,6 +168,18 @@ static void derive(const casim_params &p, ConstK<R> &K, double (*l)(double)) {
     S.dep = (R)(4.0 * pi * p.ccap[x]);
     S.mlt = (R)(4.0 * pi * p.ccap[x] * p.Ka / p.Lf);
   }
+  // triple-moment rain (species 1)
+  K.r3_a = (R)p.a[1];
+  K.r3_dv = (R)p.dv[1];
+  K.r3_mu0 = (R)p.mu[1];
+  K.r3_mumax = (R)20.0;
+  K.r3_lgdmax = (R)l(p.dmax[1]);
+  K.r3_lgdmin = (R)l(p.dmin[1]);
+  K.r3_ev1c = (R)(0.78 / p.a[1]);
+  K.r3_ev2c = (R)(0.31 * std::sqrt(p.cv[1]) / p.a[1]);
+  K.r3_cv = (R)p.cv[1];
+  const double d0 = 2.0 * p.r_r0, d3 = d0 * d0 * d0;
+  K.r3_d0_6 = (R)(d3 * d3);
 }
 
 static double ln_(double x) { return std::log(x); }
@@ -188,8 +201,10 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   if (!out) return CASIM_ERR_ARG;
   *out = nullptr;
   if (precision != CASIM_FP64 && precision != CASIM_MIXED) return CASIM_ERR_ARG;
-  if ((flags & ~(CASIM_WARM | CASIM_AEROSOL)) != 0) return CASIM_ERR_ARG;
-  if ((flags & CASIM_AEROSOL) && !(flags & CASIM_WARM)) return CASIM_ERR_ARG;
+  if ((flags & ~(CASIM_WARM | CASIM_AEROSOL | CASIM_THREE_MOMENT)) != 0) return CASIM_ERR_ARG;
+  if ((flags & (CASIM_AEROSOL | CASIM_THREE_MOMENT)) && !(flags & CASIM_WARM)) return CASIM_ERR_ARG;
+  if ((flags & CASIM_AEROSOL) && (flags & CASIM_THREE_MOMENT)) return CASIM_ERR_ARG;
+  if ((flags & CASIM_THREE_MOMENT) && !(params ? params->b[1] == 3.0 : true)) return CASIM_ERR_ARG;
   casim_params p;
   if (params) p = *params;
   else casim_default_params(&p);
@@ -198,6 +213,7 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   ctx->precision = precision;
   ctx->warm = (flags & CASIM_WARM) != 0;
   ctx->aero = (flags & CASIM_AEROSOL) != 0;
+  ctx->tri = (flags & CASIM_THREE_MOMENT) != 0;
   derive<double>(p, ctx->kp.d, ln_);
   derive<float>(p, ctx->kp.f, log2_);
   ctx->kp.c_max = p.c_max;
@@ -249,6 +265,10 @@ static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, 
     if (tend) return CASIM_ERR_ARG;
     if (ctx->precision == CASIM_MIXED) k_step<PolicyMixWarmAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
     else k_step<PolicyF64WarmAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+  } else if (ctx->tri) {
+    if (tend) return CASIM_ERR_ARG;
+    if (ctx->precision == CASIM_MIXED) k_step<PolicyMixWarm3, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+    else k_step<PolicyF64Warm3, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
   } else if (ctx->precision == CASIM_MIXED && !ctx->warm) {
     if (tend) k_step<PolicyMix, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
     else k_step<PolicyMix, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
@@ -270,7 +290,7 @@ static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, 
 extern "C" int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, double *tend,
                                    void *stream) {
   NvtxRange nvtx_range_("casim_step_tendency");
-  if (!ctx || ctx->aero || !tend) return CASIM_ERR_ARG;
+  if (!ctx || ctx->aero || ctx->tri || !tend) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
   const size_t span = (size_t)CASIM_NFIELDS * nlev * s->pitch;
@@ -335,7 +355,7 @@ static cudaError_t copy_chunk(double *dev_fld, double *dev_precip, int W, const 
 extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, int nlev, double dt,
                                void *stream) {
   NvtxRange nvtx_range_("casim_step_host");
-  if (!ctx || ctx->aero) return CASIM_ERR_ARG;
+  if (!ctx || ctx->aero || ctx->tri) return CASIM_ERR_ARG;
   if (!h || ncols < 0 || nlev < 1 || nlev > kMaxLev || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
   if (ncols == 0) return CASIM_OK;
   if (!h->fld || !h->dz || !h->precip || h->pitch < ncols || h->pitch % 32 != 0) return CASIM_ERR_ARG;
@@ -1418,7 +1438,8 @@ uint64_t params_hash(const casim_params *params) {
 int ckpt_check(const casim_state *s, int ncols, int nlev, int nfields) {
   if (!s || !s->fld || !s->dz || !s->precip || ncols < 0 || nlev < 1 || nlev > kMaxLev) return CASIM_ERR_ARG;
   if (s->pitch < ncols || s->pitch % 32 != 0) return CASIM_ERR_ARG;
-  if (nfields != CASIM_NFIELDS && nfields != CASIM_NFIELDS_AEROSOL) return CASIM_ERR_ARG;
+  if (nfields != CASIM_NFIELDS && nfields != CASIM_NFIELDS_AEROSOL && nfields != CASIM_NFIELDS_3MOM)
+    return CASIM_ERR_ARG;
   return CASIM_OK;
 }
 }  // namespace

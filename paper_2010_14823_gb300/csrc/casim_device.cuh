@@ -64,6 +64,11 @@ struct ConstK {
   // air
   R mu_air, inv_dv, lgrho0, twopi;
   SpeciesK<R> sp[5];
+  // triple-moment rain: what the shape-dependent rain constants are built from
+  R r3_a, r3_dv, r3_mu0, r3_mumax;  // a (M3 = q / a), fall-speed exponent d, fixed and largest shape
+  R r3_lgdmax, r3_lgdmin;           // log of the mean-diameter bounds (policy base)
+  R r3_ev1c, r3_ev2c, r3_cv;        // 0.78 / a, 0.31 sqrt(cv) / a, cv
+  R r3_d0_6;                        // (2 r0)^6: sixth moment of one new drop
 };
 
 struct KParams {
@@ -145,6 +150,7 @@ struct PolicyF64 {
   static constexpr bool kMixed = false;
   static constexpr bool kWarm = false;
   static constexpr bool kAero = false;
+  static constexpr bool kTri = false;
   static constexpr int kMinBlocks = 3;   // resident blocks of kBlock per SM the step kernel is built for
   static __device__ __forceinline__ const ConstK<double> &K(const KParams &p) { return p.d; }
   static __device__ __forceinline__ R toR(double x) { return x; }
@@ -156,6 +162,7 @@ struct PolicyF64 {
   static __device__ __forceinline__ R sqrt(R x) { return ::sqrt(x); }
   static __device__ __forceinline__ R cbrt(R x) { return ::cbrt(x); }
   static __device__ __forceinline__ R erfc(R x) { return ::erfc(x); }
+  static __device__ __forceinline__ R lgam(R x) { return ::lgamma(x); }
   static __device__ __forceinline__ R div(R a, R b) { return a / b; }
   static __device__ __forceinline__ R mn(R a, R b) { return a < b ? a : b; }
   static __device__ __forceinline__ R mx(R a, R b) { return a > b ? a : b; }
@@ -166,6 +173,7 @@ struct PolicyMix {
   static constexpr bool kMixed = true;
   static constexpr bool kWarm = false;
   static constexpr bool kAero = false;
+  static constexpr bool kTri = false;
   static constexpr int kMinBlocks = 5;   // measured: 4 / 5 / 6 -> 2.95 / 2.73 / 3.06 ms per 512x512x150 step
   static __device__ __forceinline__ const ConstK<float> &K(const KParams &p) { return p.f; }
   static __device__ __forceinline__ R toR(double x) { return d2f(x); }
@@ -177,6 +185,7 @@ struct PolicyMix {
   static __device__ __forceinline__ R sqrt(R x) { return sqrta(x); }
   static __device__ __forceinline__ R cbrt(R x) { return ex2a(lg2a(x) * 0.333333343267f); }
   static __device__ __forceinline__ R erfc(R x) { return erfcf(x); }
+  static __device__ __forceinline__ R lgam(R x) { return lgammaf(x); }
   static __device__ __forceinline__ R div(R a, R b) { return __fdividef(a, b); }
   static __device__ __forceinline__ R mn(R a, R b) { return fminf(a, b); }
   static __device__ __forceinline__ R mx(R a, R b) { return fmaxf(a, b); }
@@ -186,6 +195,7 @@ struct PolicyMix {
 struct Pt {
   double T, qv, qc, qr, qi, qs, qg, nc, nr, ni, ns, ng, na, p, rho, w;
   double ma, mac, mar;   // activated-aerosol mass (free, in cloud, in rain): aerosol-mass policies only
+  double zr;             // the rain's sixth moment: triple-moment policies only
 };
 
 // Working values of a point in the compute precision (after adjustment and
@@ -194,6 +204,7 @@ template <class R>
 struct W {
   double Td;   // FP64 temperature (FP64 form only: ice saturation as the oracle writes it)
   R T, tc, p, rho, qv, qc, qr, qx[3], nc, nr, nx[3];
+  R mu_r;      // rain shape parameter (triple-moment policies)
   unsigned hmax;   // mixed form: largest |high word| of the FP64 inputs read (non-finite check)
 };
 
@@ -211,6 +222,75 @@ template <class R>
 struct Gt {
   R rc, rr, rx[3], nucm, depp[3], sub[3], nmlt[3];
   R aut, acc, scc, scr, evr, nuc, dep[3], mlt[3], rs, rg;
+};
+
+// Triple-moment rain: the shape parameter from (q, n, z) and the rain
+// constants at that shape (rain has b = 3, so the gamma-function ratios of
+// integer offset are products and three lgamma values suffice).
+template <class M>
+struct Rain3 {
+  using R = typename M::R;
+  struct Sh {
+    R lglamfac, lglo, lghi;   // as SpeciesK
+    R ev1, ev2;               // ventilation coefficients
+    R vq, vn, vz;             // mass-, number- and sixth-moment-weighted speed coefficients
+  };
+  static __device__ __forceinline__ R clampmu(const ConstK<R> &K, R mu) {
+    return mu < (R)0 ? (R)0 : (mu > K.r3_mumax ? K.r3_mumax : mu);
+  }
+  // G = z n / (q/a)^2 = (mu+4)(mu+5)(mu+6)/((mu+1)(mu+2)(mu+3)): start from the
+  // root of G^(1/3) = (mu+5)/(mu+2), then four Newton steps on ln G - ln G_obs
+  static __device__ __forceinline__ R mu(const ConstK<R> &K, R q, R n, R z) {
+    if (!(q > K.qmin) || !(n > (R)0) || !(z > (R)0)) return K.r3_mu0;
+    const R m3 = M::div(q, K.r3_a);
+    const R gobs = M::div(M::div(z * n, m3), m3);
+    const R lg = M::ln(gobs);
+    const R g = M::cbrt(gobs);
+    R m = g > (R)1 ? clampmu(K, M::div((R)5 - (R)2 * g, g - (R)1)) : K.r3_mumax;
+#pragma unroll 1
+    for (int it = 0; it < 4; ++it) {
+      const R f = M::ln(M::div((m + (R)4) * (m + (R)5) * (m + (R)6), (m + (R)1) * (m + (R)2) * (m + (R)3))) - lg;
+      const R fp = M::div((R)1, m + (R)4) + M::div((R)1, m + (R)5) + M::div((R)1, m + (R)6) -
+                   M::div((R)1, m + (R)1) - M::div((R)1, m + (R)2) - M::div((R)1, m + (R)3);
+      m = clampmu(K, m - M::div(f, fp));
+    }
+    return m;
+  }
+  static __device__ __forceinline__ void consts(const ConstK<R> &K, R mu, Sh &h) {
+    const R d = K.r3_dv;
+    const R p1 = mu + (R)1, p2 = mu + (R)2, p3 = mu + (R)3;
+    const R q3 = p1 * p2 * p3;   // Gamma(mu+4) / Gamma(mu+1)
+    h.lglamfac = M::lg(K.r3_a * q3);
+    const R lp1 = M::lg(p1);
+    h.lglo = lp1 - K.r3_lgdmax;
+    h.lghi = lp1 - K.r3_lgdmin;
+    h.ev1 = M::div(K.r3_ev1c, p2 * p3);
+    const R lg1 = M::lgam(p1);
+    const R rd = M::exp(M::lgam(p1 + d) - lg1);                              // Gamma(mu+1+d)/Gamma(mu+1)
+    const R rv = M::exp(M::lgam(mu + (R)0.5 * (d + (R)5)) - lg1);            // Gamma(mu+(d+5)/2)/Gamma(mu+1)
+    h.ev2 = M::div(K.r3_ev2c * rv, q3);
+    h.vn = K.r3_cv * rd;
+    h.vq = M::div(h.vn * (p1 + d) * (p2 + d) * (p3 + d), q3);
+    h.vz = M::div(h.vq * (mu + (R)4 + d) * (mu + (R)5 + d) * (mu + (R)6 + d), (mu + (R)4) * (mu + (R)5) * (mu + (R)6));
+  }
+  static __device__ __forceinline__ R lglam(const Sh &h, const SpeciesK<R> &X, R lgq, R n) {
+    const R lgn = M::lg(M::mx(n, (R)0));
+    R l = (h.lglamfac + lgn - lgq) * X.invb;
+    l = M::mx(l, h.lglo);
+    return M::mn(l, h.lghi);
+  }
+  // rain fall speeds at shape mu (mass, number, sixth moment), capped
+  static __device__ __forceinline__ void fall_speeds(const ConstK<R> &K, R guard, R q, R lgq, R n, R z, R dfac,
+                                                     R &vq, R &vn, R &vz) {
+    const SpeciesK<R> &X = K.sp[1];
+    Sh h;
+    consts(K, mu(K, q, n, z), h);
+    const R l = lglam(h, X, lgq, n);
+    const R pw = M::ex(X.exv * l);
+    vq = M::mn(M::mn(h.vq * dfac * pw, X.vmax), guard);
+    vn = M::mn(M::mn(h.vn * dfac * pw, X.vmax), guard);
+    vz = M::mn(M::mn(h.vz * dfac * pw, X.vmax), guard);
+  }
 };
 
 template <class M>
@@ -298,8 +378,16 @@ struct Phys {
       r.scr = K.kr * rho * M::mx(nr, (R)0) * qr;
       if (Sw < (R)1) {
         const SpeciesK<R> &X = K.sp[1];
-        const R l = lglam(X, lgqr, nr);
-        const R iv = rho * qr * (X.ev1 * M::ex(X.ex1 * l) + V0 * X.ev2 * M::ex(X.ex2 * l));
+        R iv;
+        if constexpr (M::kTri) {
+          typename Rain3<M>::Sh h;
+          Rain3<M>::consts(K, w.mu_r, h);
+          const R l = Rain3<M>::lglam(h, X, lgqr, nr);
+          iv = rho * qr * (h.ev1 * M::ex(X.ex1 * l) + V0 * h.ev2 * M::ex(X.ex2 * l));
+        } else {
+          const R l = lglam(X, lgqr, nr);
+          iv = rho * qr * (X.ev1 * M::ex(X.ex1 * l) + V0 * X.ev2 * M::ex(X.ex2 * l));
+        }
         const R Aw = K.awc * iT2, Bw = M::div(K.rv_dv * T, esl);
         r.evr = M::div(K.twopi * ((R)1 - Sw) * iv, rho * (Aw + Bw));
       }
@@ -470,12 +558,13 @@ struct F64T {
     const double na1 = s.na;
     activate(K, s);
     const double dn_act = na1 - s.na;
-    const double qc_post = s.qc, qr_post = s.qr;
-    double tau_cr = 0.0, tau_rv = 0.0;
+    const double qc_post = s.qc, qr_post = s.qr, nr_post = s.nr;
+    double tau_cr = 0.0, tau_rv = 0.0, tau_aut = 0.0, nr_aut = 0.0;
     W<double> w;
     w.Td = s.T; w.T = s.T; w.tc = s.T - K.T0; w.p = s.p; w.rho = s.rho;
     w.qv = s.qv; w.qc = s.qc; w.qr = s.qr; w.qx[0] = s.qi; w.qx[1] = s.qs; w.qx[2] = s.qg;
     w.nc = s.nc; w.nr = s.nr; w.nx[0] = s.ni; w.nx[1] = s.ns; w.nx[2] = s.ng;
+    if constexpr (M::kTri) w.mu_r = Rain3<M>::mu(K, s.qr, s.nr, s.zr);
     Rt<double> r;
     P::rates(K, w, dt, r);
     Gt<double> g;
@@ -483,9 +572,9 @@ struct F64T {
     double qxd[3] = {s.qi, s.qs, s.qg};
     double nxd[3] = {s.ni, s.ns, s.ng};
     double tau;
-    if (r.aut > 0) { tau = g.aut * r.aut * dt; s.qc -= tau; s.qr += tau; tau_cr += tau; }
+    if (r.aut > 0) { tau = g.aut * r.aut * dt; s.qc -= tau; s.qr += tau; tau_cr += tau; tau_aut = tau; }
     if (r.aut * g.rc > 0) s.nc -= g.aut * (r.aut * g.rc) * dt;
-    if (r.aut * K.inv_mr0 > 0) s.nr += g.aut * (r.aut * K.inv_mr0) * dt;
+    if (r.aut * K.inv_mr0 > 0) { nr_aut = g.aut * (r.aut * K.inv_mr0) * dt; s.nr += nr_aut; }
     if (r.acc > 0) { tau = g.acc * r.acc * dt; s.qc -= tau; s.qr += tau; tau_cr += tau; }
     if (r.acc * g.rc > 0) s.nc -= g.acc * (r.acc * g.rc) * dt;
     if (r.scc > 0) s.nc -= g.scc * r.scc * dt;
@@ -514,6 +603,15 @@ struct F64T {
     }
     s.qi = qxd[0]; s.qs = qxd[1]; s.qg = qxd[2];
     s.ni = nxd[0]; s.ns = nxd[1]; s.ng = nxd[2];
+    if constexpr (M::kTri) {
+      // the rain's sixth moment: accretion, self-collection and evaporation
+      // at the diagnosed shape, autoconversion as drops of one size
+      const double q1 = s.qr - tau_aut, n1 = s.nr - nr_aut;
+      double z = 0.0;
+      if (qr_post > K.qmin && nr_post > 0.0 && q1 > 0.0 && n1 > 0.0)
+        z = s.zr * (q1 / qr_post) * (q1 / qr_post) * (nr_post / n1);
+      s.zr = z + nr_aut * K.r3_d0_6;
+    }
     if constexpr (M::kAero) {
       // aerosol mass moves with the water (in the order: adjustment,
       // activation, cloud -> rain, rain -> vapour)
@@ -559,6 +657,7 @@ struct MixInc {
   // and rain -> free; *_all: the whole pool moves
   float a_ev, a_act, a_cr, a_rv;
   bool a_ev_all, a_cr_all, a_rv_all;
+  float r_aut, n_aut;   // triple-moment policies: rain mass and drops made by autoconversion
 };
 
 template <class M>
@@ -629,6 +728,7 @@ struct MixT {
     o.evap_all = false;
     o.dT = 0.f;
     const float qc0 = w.qc;
+    if constexpr (M::kTri) w.mu_r = Rain3<M>::mu(K, w.qr, w.nr, d2f(s.zr));
     if constexpr (M::kAero) {
       o.a_ev = o.a_act = o.a_cr = o.a_rv = 0.f;
       o.a_ev_all = o.a_cr_all = o.a_rv_all = false;
@@ -716,6 +816,10 @@ struct MixT {
     o.cr = (g.aut * r.aut + g.acc * r.acc) * dtr;
     o.cg = (g.rs * r.rim[0] + g.rg * r.rim[1]) * dtr;
     o.rv = g.evr * r.evr * dtr;
+    if constexpr (M::kTri) {
+      o.r_aut = g.aut * r.aut * dtr;
+      o.n_aut = g.aut * r.aut * K.inv_mr0 * dtr;
+    }
     if constexpr (M::kAero) {
       if (o.cr > 0.f && w.qc > 0.f) {
         o.a_cr_all = o.cr >= w.qc;
@@ -769,6 +873,16 @@ struct MixT {
     if constexpr (M::kAero) apply_aero(s, o);
   }
 
+  // the rain's sixth moment after the processes (q0, n0: the rain they saw):
+  // accretion, self-collection and evaporation at the diagnosed shape,
+  // autoconversion as drops of one size
+  static __device__ __forceinline__ void apply_z(const ConstK<float> &K, Pt &s, float q0, float n0, const MixInc &o) {
+    const float q1 = q0 + o.cr - o.r_aut - o.rv, n1 = n0 + o.dn[1] - o.n_aut;
+    float f = 0.f;
+    if (q0 > K.qmin && n0 > 0.f && q1 > 0.f && n1 > 0.f) f = __fdividef(q1, q0) * __fdividef(q1, q0) * __fdividef(n0, n1);
+    s.zr = s.zr * f2d(f) + f2d(o.n_aut * K.r3_d0_6);
+  }
+
   // aerosol masses: each amount is one FP32 product of the source's mass and
   // the moved fraction, taken from the source (never more than it holds) and
   // given to the destination
@@ -811,9 +925,20 @@ struct PolicyF64WarmAero : PolicyF64Warm {
 struct PolicyMixWarmAero : PolicyMixWarm {
   static constexpr bool kAero = true;
 };
+// The warm configuration with triple-moment rain (Section 2: CASIM is a
+// three-moment scheme): field 16 of the state is the rain's sixth moment z
+// (m^6 per kg of air); the rain's shape parameter is diagnosed from (q, n, z)
+// wherever rain evaporation or sedimentation needs the rain's size
+// distribution.
+struct PolicyF64Warm3 : PolicyF64Warm {
+  static constexpr bool kTri = true;
+};
+struct PolicyMixWarm3 : PolicyMixWarm {
+  static constexpr bool kTri = true;
+};
 
 // ---------------------------------------------------------------- kernels
-template <bool kWarm = false, bool kAero = false>
+template <bool kWarm = false, bool kAero = false, bool kTri = false>
 __device__ __forceinline__ void load_pt(const KArgs &a, int k, int c, Pt &s) {
   const double *b = a.fld + (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
@@ -834,6 +959,7 @@ __device__ __forceinline__ void load_pt(const KArgs &a, int k, int c, Pt &s) {
   if constexpr (kAero) {
     s.ma = b[16 * fs]; s.mac = b[17 * fs]; s.mar = b[18 * fs];
   }
+  if constexpr (kTri) s.zr = b[16 * fs];
 }
 
 // any loaded value non-finite (integer pipe: max of the exponent fields)
@@ -857,8 +983,9 @@ __device__ __forceinline__ unsigned store_pt(const KArgs &a, int k, int c, const
          nonfinite(s.ns) | nonfinite(s.ng) | nonfinite(s.na);
 }
 
-// the warm configuration's fields only (and the aerosol masses)
-template <bool kAero = false>
+// the warm configuration's fields only (and the aerosol masses, or the
+// rain's sixth moment)
+template <bool kAero = false, bool kTri = false>
 __device__ __forceinline__ unsigned store_pt_warm(const KArgs &a, int k, int c, const Pt &s) {
   double *b = a.fld + (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
@@ -869,6 +996,10 @@ __device__ __forceinline__ unsigned store_pt_warm(const KArgs &a, int k, int c, 
   if constexpr (kAero) {
     b[16 * fs] = s.ma; b[17 * fs] = s.mac; b[18 * fs] = s.mar;
     e |= nonfinite(s.ma) | nonfinite(s.mac) | nonfinite(s.mar);
+  }
+  if constexpr (kTri) {
+    b[16 * fs] = s.zr;
+    e |= nonfinite(s.zr);
   }
   return e;
 }
@@ -949,6 +1080,7 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
   const double *rhop = a.fld + 14 * fs;
   double *state = kTend ? tend : a.fld;   // the processed state (tendency mode: scratch)
   constexpr int kSed = M::kWarm ? 1 : 4;   // sedimenting species: r (warm) or r, i, s, g
+  double *zp = a.fld + 16 * fs;   // the rain's sixth moment (triple-moment policies)
   for (int x = 0; x < kSed; ++x) {
     double *qp = state + (3 + x) * fs;
     double *np = state + (8 + x) * fs;
@@ -960,7 +1092,12 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
       const R rho = M::toR(__ldg(rhop + o));
       const R dfac = M::ex((R)0.4 * (K.lgrho0 - M::lg(rho)));
       R vq, vn;
-      Ph::fall_speeds(K, (R)1e30, M::lg(q), M::toR(np[o]), dfac, x, vq, vn);
+      if (M::kTri && x == 0) {
+        R vz;
+        Rain3<M>::fall_speeds(K, (R)1e30, q, M::lg(q), M::toR(np[o]), M::toR(zp[o]), dfac, vq, vn, vz);
+      } else {
+        Ph::fall_speeds(K, (R)1e30, M::lg(q), M::toR(np[o]), dfac, x, vq, vn);
+      }
       cmax = M::mx(cmax, M::div(vq * M::toR(a.dt), M::toR(sdz[k])));
     }
     int ns = (int)ceil((double)M::div(cmax, M::toR(P.c_max)));
@@ -970,30 +1107,48 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
     // the rain's aerosol mass moves with the rain (aerosol-mass policies)
     const bool aer = M::kAero && x == 0;
     double *ap = a.fld + 18 * fs;
+    const bool tri = M::kTri && x == 0;
     for (int st = 0; st < ns; ++st) {
-      R Fu = 0, Gu = 0, Au = 0;
+      R Fu = 0, Gu = 0, Au = 0, Hu = 0;
       for (int k = a.nlev - 1; k >= 0; --k) {
         const size_t o = (size_t)k * a.pitch + c;
         double q = qp[o], n = np[o];
         const double rhod = __ldg(rhop + o);
         const R qR = M::toR(q), rho = M::toR(rhod);
-        R F = 0, G = 0, A = 0;
-        double am = 0.0;
+        R F = 0, G = 0, A = 0, H = 0;
+        double am = 0.0, zm = 0.0;
         if (aer) am = ap[o];
+        if (tri) zm = zp[o];
         if (qR > K.qmin) {
           const R dfac = M::ex((R)0.4 * (K.lgrho0 - M::lg(rho)));
-          R vq, vn;
-          Ph::fall_speeds(K, M::toR(sdz[k] / dts), M::lg(qR), M::toR(n), dfac, x, vq, vn);
+          R vq, vn, vz = 0;
+          if (tri) {
+            Rain3<M>::fall_speeds(K, M::toR(sdz[k] / dts), qR, M::lg(qR), M::toR(n), M::toR(zm), dfac, vq, vn, vz);
+          } else {
+            Ph::fall_speeds(K, M::toR(sdz[k] / dts), M::lg(qR), M::toR(n), dfac, x, vq, vn);
+          }
           if constexpr (!M::kMixed) {
             F = rhod * q * vq;
             G = rhod * (n > 0.0 ? n : 0.0) * vn;
             if (aer) A = rhod * am * vq;
+            if (tri) H = rhod * (zm > 0.0 ? zm : 0.0) * vz;
           } else {
             F = rho * qR * vq;
             G = rho * M::mx(M::toR(n), (R)0) * vn;
             if (aer) A = rho * M::toR(am) * vq;
+            if (tri) H = rho * M::mx(M::toR(zm), (R)0) * vz;
           }
         }
+        if (tri && (H != (R)0 || Hu != (R)0)) {
+          if constexpr (!M::kMixed) {
+            zm += dts * (Hu - H) / (rhod * sdz[k]);
+          } else {
+            zm += M::toD((Hu - H) * M::div(M::toR(dts), rho * M::toR(sdz[k])));
+          }
+          zp[o] = zm;
+          eflag |= nonfinite(zm);
+        }
+        Hu = H;
         if (aer && (A != (R)0 || Au != (R)0)) {
           if constexpr (!M::kMixed) {
             am += dts * (Au - A) / (rhod * sdz[k]);
@@ -1045,11 +1200,11 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
   // carried downward fluxes F_{k+1}, G_{k+1} (kg m^-2 s^-1, m^-2 s^-1), and
   // the rain's aerosol-mass flux (aerosol-mass policies)
   R Fq[4] = {0, 0, 0, 0}, Fn[4] = {0, 0, 0, 0};
-  R Fa = 0;
+  R Fa = 0, Fz = 0;   // rain aerosol mass, rain sixth moment
 
   for (int k = a.nlev - 1; k >= 0; --k) {
     Pt s;
-    load_pt<M::kWarm, M::kAero>(a, k, c, s);
+    load_pt<M::kWarm, M::kAero, M::kTri>(a, k, c, s);
     bool touched;
     if constexpr (!M::kMixed) {
       eflag |= nonfinite_in(s);
@@ -1063,13 +1218,28 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
         for (int x = 0; x < kSed; ++x) {
           double &q = qref(s, x);
           double &n = nref(s, x);
-          double F = 0, G = 0, A = 0;
+          double F = 0, G = 0, A = 0, H = 0;
           if (q > K.qmin) {
             double vq, vn;
-            Ph::fall_speeds(K, sdzdt[k], ::log(q), n, dfac, x, vq, vn);
+            if (M::kTri && x == 0) {
+              double vz;
+              Rain3<M>::fall_speeds(K, sdzdt[k], q, ::log(q), n, s.zr, dfac, vq, vn, vz);
+              H = s.rho * (s.zr > 0.0 ? s.zr : 0.0) * vz;
+            } else {
+              Ph::fall_speeds(K, sdzdt[k], ::log(q), n, dfac, x, vq, vn);
+            }
             F = s.rho * q * vq;
             G = s.rho * (n > 0.0 ? n : 0.0) * vn;
             if (M::kAero && x == 0) A = s.rho * s.mar * vq;
+          }
+          if constexpr (M::kTri) {
+            if (x == 0) {
+              if (H != 0.0 || Fz != 0.0) {
+                s.zr += a.dt * (Fz - H) / (s.rho * dzk);
+                touched = true;
+              }
+              Fz = H;
+            }
           }
           if (F != 0.0 || Fq[x] != 0.0 || G != 0.0 || Fn[x] != 0.0) {
             q += a.dt * (Fq[x] - F) / (s.rho * dzk);
@@ -1099,6 +1269,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       if (act) {
         MixT<M>::process(K, s, a.dt, w, es0, qs0, o, a.surr ? a.surr + (size_t)k * a.pitch + c : nullptr);
         MixT<M>::apply_masses(s, o);
+        if constexpr (M::kTri) MixT<M>::apply_z(K, s, w.qr, w.nr, o);
         if (o.dn[0] != 0.f) s.nc += f2d(o.dn[0]);
 #pragma unroll
         for (int x = 0; x < 4; ++x) dn[x] = o.dn[1 + x];
@@ -1131,14 +1302,30 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
           const float guard = d2f(sdzdt[k]);
 #pragma unroll
           for (int x = 0; x < kSed; ++x) {
-            float F = 0.f, G = 0.f, A = 0.f;
+            float F = 0.f, G = 0.f, A = 0.f, H = 0.f;
             if (qpost[x] > K.qmin) {
               const float n = act ? npost[x] : d2f(nref(s, x));
               float vq, vn;
-              Ph::fall_speeds(K, guard, lg2a(qpost[x]), n, dfac, x, vq, vn);
+              if (M::kTri && x == 0) {
+                float vz;
+                const float zp = d2f(s.zr);
+                Rain3<M>::fall_speeds(K, guard, qpost[x], lg2a(qpost[x]), n, zp, dfac, vq, vn, vz);
+                H = rho * fmaxf(zp, 0.f) * vz;
+              } else {
+                Ph::fall_speeds(K, guard, lg2a(qpost[x]), n, dfac, x, vq, vn);
+              }
               F = rho * qpost[x] * vq;
               G = rho * fmaxf(n, 0.f) * vn;
               if (M::kAero && x == 0) A = rho * d2f(s.mar) * vq;
+            }
+            if constexpr (M::kTri) {
+              if (x == 0) {
+                if (H != 0.f || Fz != 0.f) {
+                  s.zr += f2d((Fz - H) * sc);
+                  touched = true;
+                }
+                Fz = H;
+              }
             }
             if constexpr (M::kAero) {
               if (x == 0) {
@@ -1170,7 +1357,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
     if constexpr (kTend) {
       eflag |= store_tend<M::kWarm>(a, tend, k, c, s, fast);
     } else if constexpr (M::kWarm) {
-      if (touched) eflag |= store_pt_warm<M::kAero>(a, k, c, s);
+      if (touched) eflag |= store_pt_warm<M::kAero, M::kTri>(a, k, c, s);
     } else {
       if (touched) eflag |= store_pt(a, k, c, s);
     }

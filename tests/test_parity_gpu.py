@@ -507,15 +507,142 @@ def test_aerosol_context_rules():
 
 
 
+# ------------------------------------------------------------------ triple-moment rain (warm)
+ZR = 16
+
+
+def _gamma_g(mu):
+    """z n / (q/a)^2 of a gamma distribution of shape mu."""
+    return (mu + 4) * (mu + 5) * (mu + 6) / ((mu + 1) * (mu + 2) * (mu + 3))
+
+
+def _tri_state(ncols, nlev, seed, mu=None, pitch=None):
+    """Deep-convective state with the rain's sixth moment of a gamma
+    distribution of shape mu (default: shapes uniform in [0, 8])."""
+    dz = synth.dz_stretched(nlev)
+    base = synth.make_state("deep_convective", ncols, nlev, dz, seed=seed, pitch=pitch)
+    fld = np.zeros((17,) + base.shape[1:])
+    fld[:16] = base
+    rng = np.random.default_rng(seed)
+    qr, nr = base[F["qr"]], base[F["nr"]]
+    shape = np.full(qr.shape, mu) if mu is not None else rng.uniform(0.0, 8.0, qr.shape)
+    ok = (qr > 1e-14) & (nr > 0)
+    fld[ZR][ok] = _gamma_g(shape[ok]) * (qr[ok] / O.param("a_r")) ** 2 / nr[ok]
+    return np.ascontiguousarray(fld), dz
+
+
+def _run_oracle_3m(fld, dz, ncols, dt, nsteps):
+    ref = fld.copy()
+    pref = np.zeros((4, fld.shape[2]))
+    for _ in range(nsteps):
+        _, err = O.step_3m(ref, ncols, dz, dt, precip=pref)
+        assert err == 0
+    return ref, pref
+
+
+@pytest.mark.parametrize("dt", [1.0, 30.0])
+def test_three_moment_fp64_matches_oracle(dt):
+    """FP64 form with triple-moment rain: the 13 prognostic fields, z and the
+    precipitation within 1e-11 of the oracle (z with an absolute floor of
+    1e-16 of the domain's largest z, the floor the masses have relative to
+    their typical size); ice fields untouched."""
+    ncols, nlev = 97, 150
+    nsteps = 3 if dt == 1.0 else 1
+    fld, dz = _tri_state(ncols, nlev, seed=61)
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, nsteps=nsteps, flags=casim.CASIM_WARM | casim.CASIM_THREE_MOMENT)
+    ref, pref = _run_oracle_3m(fld, dz, ncols, dt, nsteps)
+    assert_fp64_close(out, pr, ref, pref, ncols, rtol=1e-11)
+    a, b = out[ZR, :, :ncols], ref[ZR, :, :ncols]
+    floor = 1e-16 * fld[ZR].max()
+    assert (np.abs(a - b) <= 1e-11 * np.abs(b) + floor).all(), float(np.abs(a - b).max())
+    assert not np.array_equal(out[ZR], fld[ZR])
+    for f in ICE:
+        assert np.array_equal(out[f], fld[f])
+    assert np.all(pr[1:] == 0.0) and pr[0, :ncols].max() > 0.0
+
+
+def test_three_moment_reduces_to_warm_at_the_two_moment_shape():
+    """Cloud-free, subsaturated air (no autoconversion, the only source of a
+    shape change) with z at the two-moment rain's shape: the 16 fields agree
+    with the two-moment warm step's to rounding."""
+    ncols, nlev = 64, 150
+    fld, dz = _tri_state(ncols, nlev, seed=62, mu=O.param("mu_r"))
+    for k in range(nlev):
+        for c in range(ncols):
+            qs = O.qsat(O.es_liq(fld[F["T"], k, c]), fld[F["p"], k, c])
+            fld[F["qv"], k, c] = min(fld[F["qv"], k, c], 0.97 * qs)
+    fld[F["qc"]] = 0.0
+    fld[F["nc"]] = 0.0
+    out, pr, _ = run_gpu(fld, dz, ncols, 1.0, flags=casim.CASIM_WARM | casim.CASIM_THREE_MOMENT)
+    two, p2, _ = run_gpu(np.ascontiguousarray(fld[:16]), dz, ncols, 1.0, flags=casim.CASIM_WARM)
+    assert_fp64_close(out, pr, two, p2, ncols, rtol=1e-12)
+
+
+def test_three_moment_mixed_within_derived_bound():
+    """Mixed form: the 13 fields within the mixed bound; z within
+    1e-3 |its change| + 1e-4 |z| of the oracle.  Derivation: the shape comes
+    from an FP32 log of G (relative error ~3e-7), and dG/dmu falls to
+    |d ln G / d mu| ~ 0.016 at mu = 20, so mu carries up to ~2e-5; the
+    speeds depend on mu through FP32 log-gamma differences (~1e-5), so the
+    fluxes of z (each at most z itself at Courant number <= 1) carry ~1e-5
+    relative; the process factor (q'/q)^2 (n/n') is formed in FP32 from
+    FP32 increments (~1e-5 of the change), which is a relative error of the
+    change of z."""
+    ncols, nlev = 512, 150
+    fld, dz = _tri_state(ncols, nlev, seed=63)
+    out, pr, _ = run_gpu(fld, dz, ncols, 1.0, precision=casim.CASIM_MIXED,
+                         flags=casim.CASIM_WARM | casim.CASIM_THREE_MOMENT)
+    ref, pref = _run_oracle_3m(fld, dz, ncols, 1.0, 1)
+    for f in range(13):
+        a, b, i = out[f, :, :ncols], ref[f, :, :ncols], fld[f, :, :ncols]
+        bound = mixed_bound(b, i, f, ref[1, :, :ncols])
+        assert (np.abs(a - b) <= bound).all(), (synth.FIELDS[f], float((np.abs(a - b) / bound).max()))
+    a, b, i = out[ZR, :, :ncols], ref[ZR, :, :ncols], fld[ZR, :, :ncols]
+    bound = 1e-3 * np.abs(b - i) + 1e-4 * np.abs(b) + 1e-16 * fld[ZR].max()
+    assert (np.abs(a - b) <= bound).all(), float((np.abs(a - b) / bound).max())
+    assert (out[ZR, :, :ncols] >= 0).all()
+    for f in ICE:
+        assert np.array_equal(out[f], fld[f])
+
+
+def test_three_moment_context_rules():
+    import torch
+    for flags in (casim.CASIM_THREE_MOMENT, casim.CASIM_WARM | casim.CASIM_THREE_MOMENT | casim.CASIM_AEROSOL):
+        with pytest.raises(RuntimeError):
+            casim.casim_init(precision=casim.CASIM_MIXED, flags=flags)
+    p = casim.casim_default_params()
+    p.b[1] = 2.9
+    with pytest.raises(RuntimeError):                   # the shape algebra needs b = 3
+        casim.casim_init(params=p, precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM | casim.CASIM_THREE_MOMENT)
+    fld, dz = _tri_state(64, 40, seed=64)
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM | casim.CASIM_THREE_MOMENT)
+    try:
+        d = casim.Domain(fld, dz, 64)
+        tend = torch.zeros((14, 40, d.pitch), dtype=torch.float64, device="cuda")
+        with pytest.raises(RuntimeError):
+            casim.casim_step_tendency(ctx, d.state, 64, 40, 1.0, tend)
+        with pytest.raises(RuntimeError):
+            casim.casim_batch_create(ctx, [d.state], [64], [40])
+        h = fld.copy()
+        with pytest.raises(RuntimeError):
+            casim.casim_step_host(ctx, casim.make_state(h, d.pitch, np.ascontiguousarray(dz),
+                                                        np.zeros((4, d.pitch))), 64, 40, 1.0)
+    finally:
+        casim.casim_free(ctx)
+
+
 # ------------------------------------------------------------------ checkpoint / resume
-@pytest.mark.parametrize("aerosol", [False, True])
-def test_checkpoint_resume_is_bitwise(tmp_path, aerosol):
+@pytest.mark.parametrize("state", ["standard", "aerosol", "three_moment"])
+def test_checkpoint_resume_is_bitwise(tmp_path, state):
     """N steps equal k steps, save, load into fresh device memory, N - k steps,
     bit for bit; a checkpoint of other sizes or parameters is refused."""
     ncols, nlev = 97, 150
-    if aerosol:
+    if state == "aerosol":
         fld, dz = _aero_state(ncols, nlev, seed=71)
         flags, nf = casim.CASIM_WARM | casim.CASIM_AEROSOL, 19
+    elif state == "three_moment":
+        fld, dz = _tri_state(ncols, nlev, seed=71)
+        flags, nf = casim.CASIM_WARM | casim.CASIM_THREE_MOMENT, 17
     else:
         dz = synth.dz_stretched(nlev)
         fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=71)
