@@ -376,23 +376,39 @@ def bench_warm(args, rank, world, local):
     aero[16] = 3e-9
     aero[17] = 1e-5 * fld0[2]
     aero[18] = 1e-5 * fld0[3]
-    adom = casim.Domain(aero, dz, ncols)
+
+    def time_ext(ext, flags):
+        d = casim.Domain(ext, dz, ncols)
+        ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=flags)
+        for _ in range(args.warmup):
+            casim.casim_step(ctx, d.state, ncols, nlev, dt, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sync()
+        e0.record(stream)
+        for _ in range(args.steps):
+            casim.casim_step(ctx, d.state, ncols, nlev, dt, stream)
+        e1.record(stream)
+        sync()
+        rc, fl = casim.casim_get_error(ctx, stream)
+        assert rc == 0, (rc, fl)
+        casim.casim_free(ctx)
+        return e0.elapsed_time(e1) / args.steps
+
+    aero_ms = time_ext(aero, casim.CASIM_WARM | casim.CASIM_AEROSOL)
     del aero
-    ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM | casim.CASIM_AEROSOL)
-    for _ in range(args.warmup):
-        casim.casim_step(ctx, adom.state, ncols, nlev, dt, stream)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sync()
-    e0.record(stream)
-    for _ in range(args.steps):
-        casim.casim_step(ctx, adom.state, ncols, nlev, dt, stream)
-    e1.record(stream)
-    sync()
-    rc, fl = casim.casim_get_error(ctx, stream)
-    assert rc == 0, (rc, fl)
-    casim.casim_free(ctx)
-    aero_ms = e0.elapsed_time(e1) / args.steps
-    del adom
+    # triple-moment rain: 17 fields, the rain's sixth moment that of a gamma
+    # distribution of shape uniform in [0, 8] at every rainy point
+    tri = torch.zeros((17, nlev, dom.pitch), dtype=torch.float64, device=dom.fld.device)
+    tri[:16] = fld0
+    g = torch.Generator(device=dom.fld.device).manual_seed(1239)
+    mu = 8.0 * torch.rand((nlev, dom.pitch), generator=g, dtype=torch.float64, device=dom.fld.device)
+    gmu = (mu + 4) * (mu + 5) * (mu + 6) / ((mu + 1) * (mu + 2) * (mu + 3))
+    qr, nr = fld0[3], fld0[8]
+    rainy = (qr > 1e-14) & (nr > 0)
+    tri[16] = torch.where(rainy, gmu * (qr / casim.casim_default_params().a[1]) ** 2 / nr.clamp_min(1e-300), 0.0)
+    del mu, gmu, rainy
+    tri_ms = time_ext(tri, casim.CASIM_WARM | casim.CASIM_THREE_MOMENT)
+    del tri
     peak = _peaks().get("hbm_gbs")
     alg = 80.0 * npts + 56.0 * changed
     achieved = alg / (warm_per * 1e-3) / 1e9
@@ -408,6 +424,8 @@ def bench_warm(args, rank, world, local):
                            "warm_over_cold": cold_ms / warm_ms,
                            "warm_fp64_value": v(w64_ms), "cold_fp64_value": v(c64_ms),
                            "warm_aerosol_mixed_value": v(aero_ms), "warm_aerosol_mixed_ms_per_step": aero_ms,
+                           "warm_three_moment_mixed_value": v(tri_ms),
+                           "warm_three_moment_mixed_ms_per_step": tri_ms,
                            "changed_points_frac": changed / npts},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak if peak else None, "traffic": None,
