@@ -31,6 +31,26 @@ UNIT = "grid-point updates/s"
 WORKLOAD = "deep_512x512x150"
 
 
+# DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one ncu
+# capture of a 65 536-column x 150-level launch (dram__bytes_read.sum +
+# dram__bytes_write.sum = 2.2168 GB for 9.83 M points); reads are 16 fields per
+# point and writes follow the changed points, so the traffic scales with the
+# points processed.  Valid only for the kernel source it was taken on.
+MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.50,
+                    "source": "paper_2010_14823_gb300/csrc/casim_device.cuh",
+                    "sha256": "ba60d0deb14b6bfffe4e90b829651e608c4fa7f049226ca4b2f6f8e8096c8886"}
+
+
+def _measured_traffic(npts: int):
+    """Traffic per launch scaled from the capture, or None if the kernel source changed since."""
+    import hashlib
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), MEASURED_TRAFFIC["source"])
+    with open(path, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != MEASURED_TRAFFIC["sha256"]:
+            return None
+    return MEASURED_TRAFFIC["bytes_per_point"] * npts
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -658,7 +678,8 @@ def main():
     kern_ms = float(np.mean(mix_per))
     achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if peak else None, "traffic": None,
+                "frac": achieved / peak if peak else None,
+                "traffic": _measured_traffic(npts) if args.workload.startswith("deep") else None,
                 "kernel": "k_step<PolicyMix>", "algorithmic_bytes_per_launch": alg_bytes,
                 "changed_points_frac": changed / npts, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"}
 
