@@ -284,6 +284,27 @@ def bench_surrogate(args, rank, world, local):
     for j, name in enumerate(("aut", "acc", "scc", "scr")):
         v = rel[inbox & (ms[:, j] > 0), j]
         rate_err[name] = {"median": float(np.median(v)), "p99": float(np.percentile(v, 99)), "n": int(v.size)}
+    # the network alone, through casim_mlp_forward on device rows: 8 M
+    # standard-normal standardised inputs (the cost does not depend on the
+    # values), 2 warm-up calls, 5 timed; includes the FP32 -> BF16 input pass
+    nnet = 8_000_000
+    gnet = torch.Generator(device="cuda").manual_seed(1240)
+    Xnet = torch.randn((nnet, 12), generator=gnet, device="cuda", dtype=torch.float32)
+    Ynet = torch.empty((nnet, 4), device="cuda", dtype=torch.float32)
+    for _ in range(2):
+        casim.casim_mlp_forward(m, Xnet, Ynet, stream)
+    n0 = torch.cuda.Event(enable_timing=True)
+    n1 = torch.cuda.Event(enable_timing=True)
+    n0.record(stream)
+    for _ in range(5):
+        casim.casim_mlp_forward(m, Xnet, Ynet, stream)
+    n1.record(stream)
+    torch.cuda.synchronize()
+    net_ms = n0.elapsed_time(n1) / 5
+    del Xnet, Ynet
+    net_flop = 270336.0 * nnet
+    net_tflops = net_flop / (net_ms * 1e-3) / 1e12
+    bf16_peak = _peaks().get("bf16_tflops")
     # 100 steps: plain mixed vs surrogate from the same start, surface precipitation judged by the plain run
     nsteps = args.surr_steps
     plain, surr = casim.Domain(fld, dz, ncols), casim.Domain(fld, dz, ncols)
@@ -296,11 +317,14 @@ def bench_surrogate(args, rank, world, local):
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / nsteps
     served = 0
+    sampler = ClockSampler(local)
+    sampler.start()
     e0.record(stream)
     for _ in range(nsteps):
         served += casim.casim_step_surrogate(ctx, m, surr.state, ncols, nlev, dt, stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks = sampler.stop()
     surr_ms = e0.elapsed_time(e1) / nsteps
     rc, fl = casim.casim_get_error(ctx, stream)
     assert rc == 0, (rc, fl)
@@ -322,7 +346,13 @@ def bench_surrogate(args, rank, world, local):
                            "surrogate_ms_per_step": surr_ms, "precip_total_rel_error": abs(tot_s - tot_p) / tot_p,
                            "precip_column_rel_error": {"median": float(np.median(col_rel)),
                                                        "p99": float(np.percentile(col_rel, 99))}},
-                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": None}
+                "roofline": {"bound": "tensor", "achieved": net_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                             "frac": net_tflops / bf16_peak if bf16_peak else None, "traffic": None,
+                             "kernel": "k_mlp_umma (network alone via casim_mlp_forward, 8 M rows, with its "
+                                       "FP32 -> BF16 input pass)",
+                             "algorithmic_flop_per_launch": net_flop, "ms_per_launch": net_ms,
+                             "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst cuBLAS GEMM)"},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks}
         print(json.dumps(line), flush=True)
 
 

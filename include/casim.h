@@ -294,6 +294,14 @@ int casim_mlp_set_engine(casim_mlp *mlp, int engine);
 /* Standardised inputs Xn[n][12] -> outputs Y[n][4] (host arrays; synchronous;
    runs the selected engine). */
 int casim_mlp_forward_host(casim_mlp *mlp, const float *Xn, int n, float *Y);
+/* The same on DEVICE arrays: Xn[n][12] and Y[n][4], FP32 row-major, caller-
+   owned; 1 <= n <= 2^27.  Launches on `stream` (the engine's input
+   conversion, then the network), then synchronises that stream to read the
+   kernel's bounded-wait flag: returns CASIM_ERR_CUDA if a wait gave up
+   (outputs then undefined).  The tcgen05 engine keeps a BF16 input buffer of
+   n x 32 bytes, grown on demand and freed by casim_mlp_free; the mma.sync
+   engine uses the training workspace.  Y must not overlap Xn. */
+int casim_mlp_forward(casim_mlp *mlp, const float *Xn, long long n, float *Y, void *stream);
 /* Loss sum_i sum_j M (Y - Tn)^2 / sum M and its gradient (host arrays of
    n x 12, n x 4, n x 4, and param_count floats; synchronous). */
 int casim_mlp_loss_grad_host(casim_mlp *mlp, const float *Xn, const float *Tn, const float *M, int n, double *loss,

@@ -141,6 +141,8 @@ def lib():
         L.casim_mlp_get_params.restype = i
         L.casim_mlp_forward_host.argtypes = [vp, pf, i, pf]
         L.casim_mlp_forward_host.restype = i
+        L.casim_mlp_forward.argtypes = [vp, vp, ctypes.c_longlong, vp, vp]
+        L.casim_mlp_forward.restype = i
         L.casim_mlp_loss_grad_host.argtypes = [vp, pf, pf, pf, i, ctypes.POINTER(d), pf]
         L.casim_mlp_loss_grad_host.restype = i
         L.casim_mlp_data.argtypes = [vp, ps, i, i, d, vp, vp, vp, vp, ll, ctypes.POINTER(ll), vp]
@@ -395,6 +397,16 @@ def casim_mlp_forward_host(mlp, Xn: np.ndarray) -> np.ndarray:
     Y = np.zeros((X.shape[0], MLP_NOUT), dtype=np.float32)
     _check(lib().casim_mlp_forward_host(mlp, _fp(X), X.shape[0], _fp(Y)), "casim_mlp_forward_host")
     return Y
+
+
+def casim_mlp_forward(mlp, Xn, Y, stream=None):
+    """Xn: device float32 tensor [n][12] (standardised inputs); Y: device
+    float32 tensor [n][4], written.  Synchronises the stream."""
+    import torch
+    assert Xn.is_cuda and Y.is_cuda and Xn.dtype == torch.float32 and Y.dtype == torch.float32
+    assert Xn.is_contiguous() and Y.is_contiguous() and Xn.shape[1] == MLP_NIN and Y.shape == (Xn.shape[0], MLP_NOUT)
+    _check(lib().casim_mlp_forward(mlp, Xn.data_ptr(), Xn.shape[0], Y.data_ptr(), _stream(stream)),
+           "casim_mlp_forward")
 
 
 def casim_mlp_loss_grad_host(mlp, Xn, Tn, M):

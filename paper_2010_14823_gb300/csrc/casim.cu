@@ -921,6 +921,9 @@ struct casim_mlp {
   long long *rowpt = nullptr;
   float4 *surr = nullptr;
   unsigned long long *rowctr = nullptr;
+  // device-array inference: BF16 inputs [cap_f][16]
+  long long cap_f = 0;
+  __nv_bfloat16 *fxb = nullptr;
 };
 
 template <class T>
@@ -1072,7 +1075,7 @@ static int umma_max_clusters() {
 // forward pass of n rows of BF16 inputs on the tcgen05 kernel: rates at the
 // rows' points (rowpt) or standardised outputs in m->y (rowpt null)
 static cudaError_t mlp_forward_umma(casim_mlp *m, const __nv_bfloat16 *xb, long long n, const long long *rowpt,
-                                    float4 *surr, unsigned *err, int nsm, cudaStream_t st) {
+                                    float4 *surr, unsigned *err, int nsm, cudaStream_t st, float *y = nullptr) {
   UmmaArgs u;
   u.xb = xb;
   u.rows = n;
@@ -1081,7 +1084,7 @@ static cudaError_t mlp_forward_umma(casim_mlp *m, const __nv_bfloat16 *xb, long 
   u.theta = m->theta;
   u.norm = m->norm;
   u.surr = surr;
-  u.y = m->y;
+  u.y = y ? y : m->y;
   u.err = err;
   const long long tiles = (n + 127) / 128;
   if (tiles == 0) return cudaSuccess;
@@ -1099,7 +1102,7 @@ extern "C" void casim_mlp_free(casim_mlp *m) {
   cudaDeviceSynchronize();
   mlp_free_batch(m);
   void *ps[] = {m->theta, m->grad, m->m1, m->m2, m->wbuf, m->norm, m->box, m->cnt, m->loss,
-                m->xb, m->rowpt, m->surr, m->rowctr, m->img, m->wsplit, m->d_err};
+                m->xb, m->rowpt, m->surr, m->rowctr, m->img, m->wsplit, m->d_err, m->fxb};
   for (void *p : ps) cudaFree(p);
   delete m;
 }
@@ -1190,6 +1193,10 @@ extern "C" int casim_mlp_set_engine(casim_mlp *m, int engine) {
   return CASIM_OK;
 }
 
+// largest row count of one casim_mlp_forward call (its BF16 input buffer is
+// n x 32 bytes; the input kernel's grid stays below 2^31 threads)
+constexpr long long kMlpForwardMaxRows = 1LL << 27;
+
 extern "C" int casim_mlp_forward_host(casim_mlp *m, const float *Xn, int n, float *Y) {
   NvtxRange nvtx_range_("casim_mlp_forward_host");
   if (!m || !Xn || !Y || n < 1) return CASIM_ERR_ARG;
@@ -1214,6 +1221,44 @@ extern "C" int casim_mlp_forward_host(casim_mlp *m, const float *Xn, int n, floa
     return CASIM_ERR_CUDA;
   }
   CUDA_TRY(cudaMemcpy(Y, m->y, (size_t)n * kNout * sizeof(float), cudaMemcpyDeviceToHost));
+  return CASIM_OK;
+}
+
+extern "C" int casim_mlp_forward(casim_mlp *m, const float *Xn, long long n, float *Y, void *stream) {
+  NvtxRange nvtx_range_("casim_mlp_forward");
+  if (!m || !Xn || !Y || n < 1 || n > kMlpForwardMaxRows) return CASIM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const unsigned gin = (unsigned)((n * kNinPad + 255) / 256);
+  if (m->engine == 1) {
+    if (n > m->cap_f) {
+      cudaFree(m->fxb);
+      m->fxb = nullptr;
+      m->cap_f = 0;
+      cudaError_t e = dalloc(&m->fxb, (size_t)n * kNinPad);
+      if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CASIM_ERR_OOM : cuda_fail(e, "cudaMalloc");
+      m->cap_f = n;
+    }
+    k_mlp_inputs<<<gin, 256, 0, st>>>(Xn, (int)n, m->fxb);
+    int dev = 0, nsm = 1;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(mlp_forward_umma(m, m->fxb, n, nullptr, nullptr, m->d_err, nsm, st, Y));
+  } else {
+    int rc = mlp_batch_ws(m, (int)n);
+    if (rc != CASIM_OK) return rc;
+    k_mlp_inputs<<<gin, 256, 0, st>>>(Xn, (int)n, m->h0);
+    mlp_forward(m, (int)n, false, st);
+    CUDA_TRY(cudaMemcpyAsync(Y, m->y, (size_t)n * kNout * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  }
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(st));
+  unsigned herr = 0;
+  CUDA_TRY(cudaMemcpy(&herr, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (herr) {
+    cudaMemset(m->d_err, 0, sizeof(unsigned));
+    std::snprintf(g_last_error, sizeof(g_last_error), "casim_mlp_forward: a bounded wait gave up");
+    return CASIM_ERR_CUDA;
+  }
   return CASIM_OK;
 }
 

@@ -72,6 +72,15 @@ def test_forward_many_tiles_per_cta(net):
     assert np.isfinite(Y1).all()
     assert np.abs(Y1[idx] - Yo).max() <= 5e-3 * scale
     assert np.abs(Y1 - Y0).max() <= 1e-2 * scale
+    # the device-array entry point runs the same kernels: bit for bit
+    import torch
+    Xd = torch.from_numpy(X.astype(np.float32)).cuda()
+    for eng, Yh in ((1, Y1), (0, Y0)):
+        casim.casim_mlp_set_engine(net, eng)
+        Yd = torch.full((n, 4), float("nan"), dtype=torch.float32, device="cuda")
+        casim.casim_mlp_forward(net, Xd, Yd)
+        assert np.array_equal(Yd.cpu().numpy().astype(np.float64), Yh)
+    casim.casim_mlp_set_engine(net, 1)
 
 
 def test_gradient_matches_oracle(net):
