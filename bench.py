@@ -33,12 +33,12 @@ WORKLOAD = "deep_512x512x150"
 
 # DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one ncu
 # capture of a 65 536-column x 150-level launch (dram__bytes_read.sum +
-# dram__bytes_write.sum = 2.2168 GB for 9.83 M points); reads are 16 fields per
+# dram__bytes_write.sum = 2.2198 GB for 9.83 M points); reads are 16 fields per
 # point and writes follow the changed points, so the traffic scales with the
 # points processed.  Valid only for the kernel source it was taken on.
-MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.50,
+MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.81,
                     "source": "paper_2010_14823_gb300/csrc/casim_device.cuh",
-                    "sha256": "ba60d0deb14b6bfffe4e90b829651e608c4fa7f049226ca4b2f6f8e8096c8886"}
+                    "sha256": "619e73a0e3b0be5e46e8dac338f45e7a831cf649a84f31d28e6e1b9ad6f527d9"}
 
 
 def _measured_traffic(npts: int):
