@@ -112,6 +112,23 @@ __device__ __forceinline__ float d2f(double x) {
   return __uint_as_float(r | s);
 }
 
+// d2f rounded to nearest (ties away from zero), for the factor dt / (rho dz)
+// that turns a flux divergence into a change of mixing ratio: a truncated
+// factor is biased high by ~2^-24 at every level, which would show as a
+// systematic loss of column water of that size times the surface flux.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned s = hi & 0x80000000u;
+  const unsigned a = hi & 0x7fffffffu;
+  // 8-bit exponent and 23-bit mantissa, plus the first dropped bit (a carry
+  // out of the mantissa correctly bumps the exponent)
+  unsigned r = __funnelshift_l(lo, a - 0x38000000u, 3) + ((lo >> 28) & 1u);
+  r = a < 0x38100000u ? 0u : r;
+  r = a >= 0x47f00000u ? 0x7fc00000u : r;
+  return __uint_as_float(r | s);
+}
+
 __device__ __forceinline__ double f2d(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned s = u & 0x80000000u;
@@ -157,6 +174,7 @@ struct PolicyF64 {
   static constexpr int kMinBlocks = 3;   // resident blocks of kBlock per SM the step kernel is built for
   static __device__ __forceinline__ const ConstK<double> &K(const KParams &p) { return p.d; }
   static __device__ __forceinline__ R toR(double x) { return x; }
+  static __device__ __forceinline__ R toRn(double x) { return x; }
   static __device__ __forceinline__ double toD(R x) { return x; }
   static __device__ __forceinline__ R exp(R x) { return ::exp(x); }
   static __device__ __forceinline__ R lg(R x) { return ::log(x); }   // log in the constants' base
@@ -181,6 +199,7 @@ struct PolicyMix {
   static constexpr int kMinBlocks = 5;   // measured: 4 / 5 / 6 -> 2.95 / 2.73 / 3.06 ms per 512x512x150 step
   static __device__ __forceinline__ const ConstK<float> &K(const KParams &p) { return p.f; }
   static __device__ __forceinline__ R toR(double x) { return d2f(x); }
+  static __device__ __forceinline__ R toRn(double x) { return d2f_rn(x); }
   static __device__ __forceinline__ double toD(R x) { return f2d(x); }
   static __device__ __forceinline__ R exp(R x) { return ex2a(x * 1.44269504088896341f); }
   static __device__ __forceinline__ R lg(R x) { return lg2a(x); }
@@ -1205,7 +1224,7 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
           if constexpr (!M::kMixed) {
             zm += dts * (Hu - H) / (rhod * sdz[k]);
           } else {
-            zm += M::toD((Hu - H) * M::div(M::toR(dts), rho * M::toR(sdz[k])));
+            zm += M::toD((Hu - H) * M::div(M::toRn(dts), M::toRn(rhod) * M::toRn(sdz[k])));
           }
           zp[o] = zm;
           eflag |= nonfinite(zm);
@@ -1215,7 +1234,7 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
           if constexpr (!M::kMixed) {
             am += dts * (Au - A) / (rhod * sdz[k]);
           } else {
-            am += M::toD((Au - A) * M::div(M::toR(dts), rho * M::toR(sdz[k])));
+            am += M::toD((Au - A) * M::div(M::toRn(dts), M::toRn(rhod) * M::toRn(sdz[k])));
           }
           ap[o] = am;
           eflag |= nonfinite(am);
@@ -1226,7 +1245,7 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
             q += dts * (Fu - F) / (rhod * sdz[k]);
             n += dts * (Gu - G) / (rhod * sdz[k]);
           } else {
-            const R sc = M::div(M::toR(dts), rho * M::toR(sdz[k]));
+            const R sc = M::div(M::toRn(dts), M::toRn(rhod) * M::toRn(sdz[k]));
             q += M::toD((Fu - F) * sc);
             n += M::toD((Gu - G) * sc);
           }
@@ -1361,7 +1380,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
           if (!act) w.hmax = max(w.hmax, hiabs(s.rho));
           const float rho = act ? w.rho : d2f(s.rho);
           const float dfac = ex2a(0.4f * (K.lgrho0 - lg2a(rho)));
-          const float sc = __fdividef(d2f(a.dt), rho * d2f(sdz[k]));
+          const float sc = __fdividef(d2f_rn(a.dt), d2f_rn(s.rho) * d2f_rn(sdz[k]));
           const float guard = d2f(sdzdt[k]);
 #pragma unroll
           for (int x = 0; x < kSed; ++x) {
