@@ -152,16 +152,23 @@ int casim_default_params(casim_params *p);
    checkpoint calls; the other step entry points reject such a context. */
 #define CASIM_THREE_MOMENT 4
 
+/* Largest level count of a column (the step keeps a column's dz in shared
+   memory). */
+#define CASIM_MAX_LEV 1024
+
 /* Create a context on the current CUDA device (Section 3.2: the one-off
    set-up that copies constants and allocates device memory).  `params` may be
-   NULL for the defaults; `precision` is a casim_precision; `flags` is 0 or
-   CASIM_WARM.  Allocates a small device error word.  On failure *ctx is set
-   to NULL. */
+   NULL for the defaults; `precision` is a casim_precision; `flags` is 0,
+   CASIM_WARM, CASIM_WARM | CASIM_AEROSOL or CASIM_WARM | CASIM_THREE_MOMENT
+   (CASIM_ERR_ARG otherwise).  Allocates a small device error word.  On
+   failure *ctx is set to NULL. */
 int casim_init(casim_ctx **ctx, const casim_params *params, int precision, int flags);
 
 /* Advance every column of one domain by one timestep dt, in place
    (Section 3.2: the per-timestep call running the whole scheme on the GPU).
-   ncols >= 0 (0 is a no-op), 1 <= nlev, dt > 0.  Updates the 13 prognostic
+   ncols >= 0 (0 is a no-op), 1 <= nlev <= CASIM_MAX_LEV, dt > 0 (else
+   CASIM_ERR_ARG before any launch; the same limits hold for every entry point
+   that takes ncols and nlev).  Updates the 13 prognostic
    fields and adds the step's surface precipitation to s->precip.  Reads
    s->dz on the device.  Asynchronous on `stream`. */
 int casim_step(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream);

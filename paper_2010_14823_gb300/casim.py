@@ -23,6 +23,7 @@ CASIM_AEROSOL = 2       # casim_init flag (with CASIM_WARM): activated-aerosol m
 CASIM_THREE_MOMENT = 4  # casim_init flag (with CASIM_WARM): triple-moment rain, 17 fields
 NFIELDS_AERO = 19
 NFIELDS_3MOM = 17
+CASIM_MAX_LEV = 1024   # largest level count of a column
 NFIELDS = 16
 NPROG = 13
 NPRECIP = 4

@@ -233,6 +233,8 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   return CASIM_OK;
 }
 
+static_assert(kMaxLev == CASIM_MAX_LEV, "the header's level limit is the kernels' shared dz array");
+
 static int check_state(const casim_state *s, int ncols, int nlev, double dt) {
   if (!s || ncols < 0 || nlev < 1 || nlev > kMaxLev || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
   if (ncols == 0) return CASIM_OK;

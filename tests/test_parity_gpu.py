@@ -102,6 +102,57 @@ def test_stratus_256x256x100_sampled_columns_fp64():
     assert_fp64_close(out[:, :, cols], pr[:, cols], ref, pr_ref, 32, rtol=1e-11)
 
 
+@pytest.fixture(scope="module")
+def deep_full():
+    """The benchmark's workload: deep convection 512x512 columns x 150 levels."""
+    return synth.workload("deep_512x512x150")
+
+
+@pytest.mark.parametrize("precision", [casim.CASIM_FP64, casim.CASIM_MIXED])
+def test_deep_512x512x150_sampled_columns(deep_full, precision):
+    """The benchmark's full-size workload in its launch configuration (one
+    casim_step over all 262 144 columns): 64 seeded random columns and the
+    last column against the oracle, FP64 within 1e-11, mixed within the
+    derived bound."""
+    fld, dz, ncols, nlev, dt, _ = deep_full
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, precision=precision)
+    cols = np.concatenate([np.sort(np.random.default_rng(77).choice(ncols - 1, 64, replace=False)), [ncols - 1]])
+    sub = np.zeros((fld.shape[0], nlev, 96))
+    sub[:, :, :cols.size] = fld[:, :, cols]
+    ref, pr_ref = run_oracle(sub, dz, cols.size, dt)
+    got = np.zeros_like(sub)
+    got[:, :, :cols.size] = out[:, :, cols]
+    gpr = np.zeros((4, 96))
+    gpr[:, :cols.size] = pr[:, cols]
+    if precision == casim.CASIM_FP64:
+        assert_fp64_close(got, gpr, ref, pr_ref, cols.size, rtol=1e-11)
+    else:
+        n = cols.size
+        for f in range(13):
+            a_, b_, i_ = got[f, :, :n], ref[f, :, :n], sub[f, :, :n]
+            bound = mixed_bound(b_, i_, f, ref[1, :, :n])
+            assert (np.abs(a_ - b_) <= bound).all(), (synth.FIELDS[f], float((np.abs(a_ - b_) / bound).max()))
+
+
+def test_maximum_level_count():
+    """1024 levels (the largest column the step takes) against the oracle;
+    1025 is refused before any launch."""
+    ncols, nlev = 40, 1024
+    dz = np.full(nlev, 20.0)
+    fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=21)
+    out, pr, _ = run_gpu(fld, dz, ncols, 1.0)
+    ref, pr_ref = run_oracle(fld, dz, ncols, 1.0)
+    assert_fp64_close(out, pr, ref, pr_ref, ncols, rtol=1e-11)
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED)
+    try:
+        dz2 = np.full(nlev + 1, 20.0)
+        d = casim.Domain(np.zeros((16, nlev + 1, 64)), dz2, ncols)
+        with pytest.raises(RuntimeError):
+            casim.casim_step(ctx, d.state, ncols, nlev + 1, 1.0)
+    finally:
+        casim.casim_free(ctx)
+
+
 def test_clear_columns_are_bitwise_unchanged():
     dz = synth.dz_uniform(40)
     rc = synth.Recipe(cloud_frac=0.0, T_sfc=300.0, rh_clear=(0.5, 0.8))
