@@ -33,22 +33,52 @@ WORKLOAD = "deep_512x512x150"
 
 # DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one ncu
 # capture of a 65 536-column x 150-level launch (dram__bytes_read.sum +
-# dram__bytes_write.sum = 2.2198 GB for 9.83 M points); reads are 16 fields per
+# dram__bytes_write.sum = 2.2192 GB for 9.83 M points); reads are 16 fields per
 # point and writes follow the changed points, so the traffic scales with the
 # points processed.  Valid only for the kernel source it was taken on.
-MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.81,
+MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.75,
                     "source": "paper_2010_14823_gb300/csrc/casim_device.cuh",
-                    "sha256": "619e73a0e3b0be5e46e8dac338f45e7a831cf649a84f31d28e6e1b9ad6f527d9"}
+                    "sha256": "2930932c646f44484af7ccd504dbb2282bf47040b68d8b8bb99885e6841646ce"}
+
+
+# FP64 arithmetic instructions of k_step<PolicyF64> per point on the same
+# state, from one ncu capture of a 16 384-column x 150-level launch
+# (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum =
+# 1168.2 M + 296.4 M + 381.0 M for 2.458 M points); the FP64 pipe was 72.7 %
+# busy.  Valid only for the kernel source it was taken on.
+MEASURED_FP64_OPS = {"kernel": "k_step<PolicyF64>", "inst_per_point": 750.99,
+                     "dfma": 475.34, "dadd": 120.62, "dmul": 155.03, "fp64_pipe_active": 0.727,
+                     "sha256": "2930932c646f44484af7ccd504dbb2282bf47040b68d8b8bb99885e6841646ce"}
+
+
+def _kernel_source_sha() -> str:
+    import hashlib
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), MEASURED_TRAFFIC["source"])
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
 
 
 def _measured_traffic(npts: int):
     """Traffic per launch scaled from the capture, or None if the kernel source changed since."""
-    import hashlib
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), MEASURED_TRAFFIC["source"])
-    with open(path, "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != MEASURED_TRAFFIC["sha256"]:
-            return None
+    if _kernel_source_sha() != MEASURED_TRAFFIC["sha256"]:
+        return None
     return MEASURED_TRAFFIC["bytes_per_point"] * npts
+
+
+def _fp64_roofline(npts: int, fp_ms: float):
+    """The FP64 form against the FP64 pipe: counted FP64 arithmetic
+    instructions per second over the DFMA rate measured now (probe of
+    include/casim_peaks.h); None if the kernel source changed since the count."""
+    if _kernel_source_sha() != MEASURED_FP64_OPS["sha256"]:
+        return None
+    from paper_2010_14823_gb300 import peaks
+    peak = peaks.peak_rate("dfma", 1 << 12)
+    achieved = MEASURED_FP64_OPS["inst_per_point"] * npts / (fp_ms * 1e-3)
+    return {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "FP64 instructions/s",
+            "frac": achieved / peak, "kernel": "k_step<PolicyF64>",
+            "inst_per_point": MEASURED_FP64_OPS["inst_per_point"],
+            "fp64_pipe_active_ncu": MEASURED_FP64_OPS["fp64_pipe_active"],
+            "peak_source": "measured now: DFMA chains on every SM (casim_peak_rate)"}
 
 
 def _peaks():
@@ -129,7 +159,7 @@ def cpu_oracle_rate(recipe_fld, dz, ncols_total, dt, target_s=10.0, max_cols=Non
         oracle.step(sub, cols, dz, dt, nthreads=nthreads)
         el = time.perf_counter() - t0
         if el >= target_s * 0.5 or cols >= ncols_total or (max_cols and cols >= max_cols):
-            return cols * nlev / el, nthreads, f"{cols} columns x {nlev} levels, 1 step, {el:.1f} s", el
+            return cols * nlev / el, nthreads, f"{cols} columns x {nlev} levels, 1 step, {el:.3f} s", el
         cols = int(cols * min(16.0, max(2.0, target_s / max(el, 1e-3))))
 
 
@@ -356,6 +386,28 @@ def bench_surrogate(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def bench_peaks(args, rank, world, local):
+    """Instruction-throughput probes of this GPU (include/casim_peaks.h): FP32
+    and FP64 fused multiply-adds and the special-function unit's ex2, lg2, rcp
+    and tanh, each over 8 independent chains per thread on every SM; rates
+    per second and per SM per clock (at the median SM clock sampled during
+    the probes)."""
+    import torch
+    from paper_2010_14823_gb300 import peaks
+    torch.cuda.set_device(local)
+    iters = {"ffma": 1 << 18, "dfma": 1 << 12, "ex2": 1 << 16, "lg2": 1 << 15, "rcp": 1 << 15, "tanh": 1 << 15}
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    sampler = ClockSampler(local)
+    sampler.start()
+    rates = {k: peaks.peak_rate(k, n) for k, n in iters.items()}
+    clocks = sampler.stop()
+    mhz = clocks.get("sm_mhz") if isinstance(clocks, dict) else None
+    per = {k: (v / (nsm * mhz * 1e6) if mhz else None) for k, v in rates.items()}
+    if rank == 0:
+        print(json.dumps({"workload": "peaks", "unit": "operations/s (one FMA = one operation)", "sms": nsm,
+                          "rates": rates, "per_sm_per_clock": per, "iters": iters, "clocks": clocks}), flush=True)
+
+
 def bench_warm(args, rank, world, local):
     """The warm configuration (liquid water only) against the cold one on the
     same 512x512x150 stratus state, mixed and FP64 forms.  `value` is the warm
@@ -566,6 +618,8 @@ def main():
         return bench_batch(args, rank, world, local)
     if args.workload == "surrogate":
         return bench_surrogate(args, rank, world, local)
+    if args.workload == "peaks":
+        return bench_peaks(args, rank, world, local)
     if args.workload == "warm_vs_cold":
         return bench_warm(args, rank, world, local)
     from paper_2010_14823_gb300 import shard
@@ -726,6 +780,8 @@ def main():
         if fp64_value is not None:
             cfg.update({"fp64_value": fp64_value, "fp64_ms_per_step": fp_ms / args.fp64_steps,
                         "speedup_mixed_vs_fp64": value / fp64_value})
+            if args.workload.startswith("deep"):
+                cfg["fp64_roofline"] = _fp64_roofline(npts, fp_ms / args.fp64_steps)
         if accuracy is not None:
             cfg["mixed_vs_fp64"] = accuracy
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

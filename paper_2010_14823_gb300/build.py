@@ -12,6 +12,10 @@ LIB = os.path.join(HERE, "libcasim.so")
 SOURCES = [os.path.join(CSRC, "casim.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
+# instruction-throughput probes (measurement support, its own library)
+PEAKS_LIB = os.path.join(HERE, "libcasim_peaks.so")
+PEAKS_SOURCES = [os.path.join(CSRC, "casim_peaks.cu")]
+PEAKS_DEPS = PEAKS_SOURCES + [os.path.join(INCLUDE, "casim_peaks.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared", "-I" + INCLUDE, "-ldl"]
@@ -24,15 +28,22 @@ def nvcc() -> str:
     return "nvcc"
 
 
+def _stale(lib: str, deps: list[str]) -> bool:
+    return not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(p) for p in deps)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libcasim.so if it is missing or older than its sources."""
-    if not force and os.path.exists(LIB):
-        newest = max(os.path.getmtime(p) for p in DEPS)
-        if os.path.getmtime(LIB) >= newest:
-            return LIB
-    cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", LIB + ".tmp"] + SOURCES
-    subprocess.run(cmd, check=True)
-    os.replace(LIB + ".tmp", LIB)
+    """Compile libcasim.so and libcasim_peaks.so (concurrently) where missing
+    or older than their sources."""
+    jobs = []
+    for lib, srcs, deps in ((LIB, SOURCES, DEPS), (PEAKS_LIB, PEAKS_SOURCES, PEAKS_DEPS)):
+        if force or _stale(lib, deps):
+            cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", lib + ".tmp"] + srcs
+            jobs.append((lib, subprocess.Popen(cmd)))
+    for lib, p in jobs:
+        if p.wait() != 0:
+            raise subprocess.CalledProcessError(p.returncode, "nvcc " + os.path.basename(lib))
+        os.replace(lib + ".tmp", lib)
     return LIB
 
 

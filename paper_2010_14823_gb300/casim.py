@@ -164,11 +164,11 @@ def lib():
     return _lib
 
 
-def declared_functions() -> list[str]:
-    """Names of the functions declared in include/*.h."""
+def declared_functions(header: str | None = None) -> list[str]:
+    """Names of the functions declared in include/*.h (or in one header)."""
     names = []
     for f in sorted(os.listdir(INCLUDE)):
-        if f.endswith(".h"):
+        if f.endswith(".h") and (header is None or f == header):
             text = open(os.path.join(INCLUDE, f)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
             names += re.findall(r"^[A-Za-z_][\w \*]*?\b(casim_\w+)\s*\(", text, flags=re.M)

@@ -1,5 +1,6 @@
 """The C-ABI library builds, loads and exports every declared entry point (no GPU needed)."""
 import ctypes
+import os
 
 import pytest
 
@@ -15,10 +16,25 @@ def L():
 
 
 def test_every_declared_symbol_is_exported(L):
-    names = casim.declared_functions()
+    names = casim.declared_functions("casim.h")
     assert len(names) >= 10
     for n in names:
         assert hasattr(L, n), n
+    from paper_2010_14823_gb300 import peaks
+    pn = casim.declared_functions("casim_peaks.h")
+    assert pn == ["casim_peak_rate"]
+    for n in pn:
+        assert hasattr(peaks.lib(), n), n
+    headers = sorted(f for f in os.listdir(casim.INCLUDE) if f.endswith(".h"))
+    assert headers == ["casim.h", "casim_peaks.h"]
+
+
+def test_peak_probe_argument_errors(L):
+    from paper_2010_14823_gb300 import peaks
+    r = ctypes.c_double(0.0)
+    assert peaks.lib().casim_peak_rate(99, 10, None, ctypes.byref(r)) == -1
+    assert peaks.lib().casim_peak_rate(0, 0, None, ctypes.byref(r)) == -1
+    assert peaks.lib().casim_peak_rate(0, 10, None, None) == -1
 
 
 def test_abi_version(L):
