@@ -140,11 +140,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(recipe_fld, dz, ncols_total, dt, target_s=10.0, max_cols=None):
-    """Time the FP64 oracle (as it stands) on host cores over a bounded sample
-    of columns of the same workload; returns (points/s, cores, sample text)."""
+def cpu_oracle_rate(recipe_fld, dz, ncols_total, dt, target_s=10.0, max_cols=None, nthreads=None):
+    """Time the FP64 oracle (as it stands) on host cores (all, or nthreads)
+    over a bounded sample of columns of the same workload; returns (points/s,
+    threads, sample text, seconds)."""
     import oracle
-    nthreads = os.cpu_count() or 1
+    nthreads = nthreads or os.cpu_count() or 1
     fld, nlev = recipe_fld, recipe_fld.shape[1]
     cols = 256
     while True:
@@ -770,7 +771,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, cores, sample, _ = cpu_oracle_rate(base_fld, dz, ncols, dt, target_s=12.0)
-        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        r1, _, sample1, _ = cpu_oracle_rate(base_fld, dz, ncols, dt, target_s=3.0, nthreads=1)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread_value": r1, "single_thread_sample": sample1}
 
     if rank == 0:
         cfg = {"workload": args.workload, "ncols": ncols, "nlev": nlev, "dt_s": dt,
