@@ -24,6 +24,8 @@ NFIELDS_AERO = 19      # + free aerosol mass, aerosol mass in cloud, in rain
 NPROG_AERO = 16
 NFIELDS_3M = 17        # + the rain's sixth moment
 NPROG_3M = 14
+NFIELDS_3MC = 20       # cold configuration: + the sixth moments of r, i, s, g
+NPROG_3MC = 17
 NPROC = 14
 SPECIES = {"c": 0, "r": 1, "i": 2, "s": 3, "g": 4}
 PROCS = ("aut", "acc", "scc", "scr", "evr", "nuc", "depi", "deps", "depg",
@@ -107,6 +109,14 @@ def lib():
         L.orc_sediment_rain_3m.argtypes = [pd, pd, pd, pd, pd, i, d, pd, ctypes.POINTER(ctypes.c_int)]
         L.orc_step_3m.restype = u
         L.orc_step_3m.argtypes = [pd, ctypes.c_long, i, i, pd, pd, d, i]
+        L.orc_shape_mu.restype = d
+        L.orc_shape_mu.argtypes = [i, d, d, d]
+        L.orc_point_3m_cold.restype = None
+        L.orc_point_3m_cold.argtypes = [pd, d, pd]
+        L.orc_sediment_3m.restype = u
+        L.orc_sediment_3m.argtypes = [pd, pd, pd, pd, pd, i, d, pd, ctypes.POINTER(ctypes.c_int)]
+        L.orc_step_3m_cold.restype = u
+        L.orc_step_3m_cold.argtypes = [pd, ctypes.c_long, i, i, pd, pd, d, i]
         L.orc_point_aero.restype = None
         L.orc_point_aero.argtypes = [pd, d, pd]
         L.orc_step_aero.restype = u
@@ -331,4 +341,45 @@ def step_3m(fld: np.ndarray, ncols: int, dz: np.ndarray, dt: float, precip: np.n
     if precip is None:
         precip = np.zeros((4, pitch))
     err = lib().orc_step_3m(_dp(fld), pitch, ncols, nlev, _dp(dz), _dp(precip), dt, nthreads)
+    return precip, err
+
+
+# --------------------------------------- triple-moment, cold configuration
+def shape_mu(sp: str, q: float, n: float, z: float) -> float:
+    """Shape parameter of species sp diagnosed from q, n and its sixth moment z."""
+    return lib().orc_shape_mu(SPECIES[sp], q, n, z)
+
+
+def point_3m_cold(state: np.ndarray, dt: float) -> np.ndarray:
+    """Cold point with triple-moment r, i, s, g: state[20] -> [13 prognostic, z_r, z_i, z_s, z_g]."""
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    assert st.shape == (NFIELDS_3MC,)
+    out = np.zeros(NPROG_3MC)
+    lib().orc_point_3m_cold(_dp(st), dt, _dp(out))
+    return out
+
+
+def sediment_3m(q, n, z, rho, dz, dt: float):
+    """Sedimentation of q, n, z [4][nlev] (r, i, s, g; copied); returns (q, n, z, precip[4], nsub[4], err)."""
+    q, n, z = (np.array(x, dtype=np.float64, order="C") for x in (q, n, z))
+    assert q.shape[0] == 4 and n.shape == q.shape and z.shape == q.shape
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    pr = np.zeros(4)
+    ns = np.zeros(4, dtype=np.int32)
+    err = lib().orc_sediment_3m(_dp(q), _dp(n), _dp(z), _dp(rho), _dp(dz), rho.shape[0], dt, _dp(pr),
+                                ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return q, n, z, pr, ns, err
+
+
+def step_3m_cold(fld: np.ndarray, ncols: int, dz: np.ndarray, dt: float, precip: np.ndarray | None = None,
+                 nthreads: int = 0):
+    """Cold step with triple-moment r, i, s, g, in place on fld [20][nlev][pitch];
+    precip [4][pitch] accumulated.  Returns (precip, err)."""
+    assert fld.dtype == np.float64 and fld.flags["C_CONTIGUOUS"] and fld.shape[0] == NFIELDS_3MC
+    nlev, pitch = fld.shape[1], fld.shape[2]
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    if precip is None:
+        precip = np.zeros((4, pitch))
+    err = lib().orc_step_3m_cold(_dp(fld), pitch, ncols, nlev, _dp(dz), _dp(precip), dt, nthreads)
     return precip, err

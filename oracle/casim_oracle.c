@@ -235,16 +235,17 @@ double orc_vent_integral(int sp, double rho, double q, double lam) {
 double orc_vq(int sp, double rho, double lam) { return orc_vq_mu(sp, rho, lam, SP[sp].mu); }
 double orc_vn(int sp, double rho, double lam) { return orc_vn_mu(sp, rho, lam, SP[sp].mu); }
 
-/* Triple-moment rain: the shape parameter from q, n and the sixth moment z
-   (m^6 per kg of air).  With m = a D^3, M3 = q / a per kg and
+/* Triple-moment species: the shape parameter from q, n and the sixth moment
+   z (m^6 per kg of air).  With m = a D^3 (every species here has b = 3),
+   M3 = q / a per kg and
      G = z n / M3^2 = (mu+4)(mu+5)(mu+6) / ((mu+1)(mu+2)(mu+3)),
    decreasing from 20 at mu = 0 to 1 as mu -> inf.  Start from the root of
    G^(1/3) = (mu+5)/(mu+2), then four Newton steps on ln G(mu) - ln G_obs,
-   every iterate clamped to [0, MU3_MAX].  Rain absent, or n or z not
+   every iterate clamped to [0, MU3_MAX].  Species absent, or n or z not
    positive: the species' fixed mu. */
-double orc_rain_mu(double q, double n, double z) {
-  if (!(q > QMIN) || !(n > 0.0) || !(z > 0.0)) return SP[ORC_R].mu;
-  double m3 = q / SP[ORC_R].a;
+double orc_shape_mu(int sp, double q, double n, double z) {
+  if (!(q > QMIN) || !(n > 0.0) || !(z > 0.0)) return SP[sp].mu;
+  double m3 = q / SP[sp].a;
   double lg = log(z * n / (m3 * m3));
   double g = cbrt(z * n / (m3 * m3));
   double mu = g > 1.0 ? (5.0 - 2.0 * g) / (g - 1.0) : MU3_MAX;
@@ -261,14 +262,17 @@ double orc_rain_mu(double q, double n, double z) {
   return mu;
 }
 
+double orc_rain_mu(double q, double n, double z) { return orc_shape_mu(ORC_R, q, n, z); }
+
 /* --------------------------------------------------------- a4..a9 rates */
-static void rates_core(const double *st, double dt, double *R, int warm, double mu_r);
+static void rates_core(const double *st, double dt, double *R, int warm, const double *mu4);
 
-void orc_rates_cfg(const double *st, double dt, double *R, int warm) { rates_core(st, dt, R, warm, SP[ORC_R].mu); }
+void orc_rates_cfg(const double *st, double dt, double *R, int warm) { rates_core(st, dt, R, warm, NULL); }
 
-/* mu_r: the rain shape parameter (the species' own, or the triple-moment
-   scheme's diagnosed one) */
-static void rates_core(const double *st, double dt, double *R, int warm, double mu_r) {
+/* mu4: the shape parameters of r, i, s, g (the triple-moment scheme's
+   diagnosed ones), or NULL for the species' own */
+static void rates_core(const double *st, double dt, double *R, int warm, const double *mu4) {
+  const double mu_r = mu4 ? mu4[0] : SP[ORC_R].mu;
   /* Rates in kg kg^-1 s^-1 (masses) except SCC, SCR (number kg^-1 s^-1) and
      NUC (new crystals kg^-1 s^-1).  All are >= 0 except DEPx, which is
      positive for deposition and negative for sublimation.  MLTx is the
@@ -323,18 +327,19 @@ static void rates_core(const double *st, double dt, double *R, int warm, double 
     int sp = spx[m];
     double q = st[qx[m]];
     if (!(q > QMIN)) continue;
-    double lam = orc_lambda(sp, q, st[nx[m]]);
+    const double mu = mu4 ? mu4[1 + m] : SP[sp].mu;
+    double lam = orc_lambda_mu(sp, q, st[nx[m]], mu);
     if (T < T0) {
-      double iv = orc_vent_integral(sp, rho, q, lam);
+      double iv = orc_vent_integral_mu(sp, rho, q, lam, mu);
       R[depj[m]] = 4.0 * PI * SP[sp].ccap * (Si - 1.0) * iv / (rho * (Ai + Bi));
       if (sp != ORC_I && hc) {
         /* collection of cloud: (pi/4) E q_c int D^2 V(D) n(D) dD */
         double vfac = SP[sp].cv * pow(RHO0 / rho, 0.4);
-        double r = 0.25 * PI * E_RIM * qc * vfac * orc_moment(sp, rho, q, lam, 2.0 + SP[sp].dv);
+        double r = 0.25 * PI * E_RIM * qc * vfac * orc_moment_mu(sp, rho, q, lam, 2.0 + SP[sp].dv, mu);
         R[sp == ORC_S ? ORC_RIMS : ORC_RIMG] = r;
       }
     } else if (T > T0) {
-      double iv = orc_vent_integral(sp, rho, q, lam);
+      double iv = orc_vent_integral_mu(sp, rho, q, lam, mu);
       R[mltj[m]] = 4.0 * PI * SP[sp].ccap * KA * (T - T0) * iv / (rho * LF);
     }
   }
@@ -382,9 +387,11 @@ typedef struct {
   double qc_post, qr_post;  /* cloud and rain after activation (what the rates see) */
   double tau_cr, tau_rv;    /* cloud -> rain (autoconversion + accretion), rain -> vapour */
   double tau_aut, nr_aut;   /* autoconversion: rain mass, new drops */
+  double nuc_q, nuc_n;      /* ice nucleation: mass and crystals made */
+  double melt_q[3], melt_n[3];  /* melting of i, s, g into rain: mass and particles */
 } orc_record;
 
-static void point_core(const double *in0, double dt, double *out, int warm, orc_record *rec, double mu_r) {
+static void point_core(const double *in0, double dt, double *out, int warm, orc_record *rec, const double *mu4) {
   /* warm: the ice fields are not part of the warm state; they are treated as
      absent and passed through unchanged */
   double in[ORC_NFIELDS];
@@ -404,11 +411,13 @@ static void point_core(const double *in0, double dt, double *out, int warm, orc_
     rec->qc_post = st[ORC_QC];
     rec->qr_post = st[ORC_QR];
     rec->tau_cr = rec->tau_rv = rec->tau_aut = rec->nr_aut = 0.0;
+    rec->nuc_q = rec->nuc_n = 0.0;
+    for (int m = 0; m < 3; ++m) rec->melt_q[m] = rec->melt_n[m] = 0.0;
   }
 
   /* a4..a9 from the post-activation state */
   double R[ORC_NPROC];
-  rates_core(st, dt, R, warm, mu_r);
+  rates_core(st, dt, R, warm, mu4);
 
   double qc = st[ORC_QC], qr = st[ORC_QR];
   orc_transfer tr[ORC_NPROC];
@@ -472,11 +481,15 @@ static void point_core(const double *in0, double dt, double *out, int warm, orc_
       if (rec && (j == 0 || j == 1)) rec->tau_cr += tau;   /* autoconversion, accretion */
       if (rec && j == 0) rec->tau_aut = tau;
       if (rec && j == 4) rec->tau_rv += tau;               /* rain evaporation */
+      if (rec && j == 5) rec->nuc_q = tau;                 /* nucleation */
+      if (rec && j >= nt - 3) rec->melt_q[j - (nt - 3)] = tau;   /* melting of i, s, g */
     }
     if (tr[j].nsink > 0.0) st[tr[j].nsrc] -= g * tr[j].nsink * dt;
     if (tr[j].ndst >= 0 && tr[j].nsource > 0.0) {
       st[tr[j].ndst] += g * tr[j].nsource * dt;
       if (rec && j == 0) rec->nr_aut = g * tr[j].nsource * dt;
+      if (rec && j == 5) rec->nuc_n = g * tr[j].nsource * dt;
+      if (rec && j >= nt - 3) rec->melt_n[j - (nt - 3)] = g * tr[j].nsource * dt;
     }
   }
   if (warm)
@@ -485,7 +498,7 @@ static void point_core(const double *in0, double dt, double *out, int warm, orc_
 }
 
 void orc_point_cfg(const double *in, double dt, double *out, int warm) {
-  point_core(in, dt, out, warm, NULL, SP[ORC_R].mu);
+  point_core(in, dt, out, warm, NULL, NULL);
 }
 
 /* Triple-moment rain in the warm configuration (Section 2: CASIM is a
@@ -498,10 +511,10 @@ void orc_point_cfg(const double *in, double dt, double *out, int warm) {
      - autoconversion adds drops of one size D0 = 2 r0: + n_aut D0^6.
    in[ORC_NFIELDS_3M] -> out[ORC_NPROG_3M] (13 prognostic fields, then z). */
 void orc_point_3m(const double *in, double dt, double *out) {
-  double mu = orc_rain_mu(in[ORC_QR], in[ORC_NR], in[ORC_ZR]);
+  double mu4[4] = {orc_rain_mu(in[ORC_QR], in[ORC_NR], in[ORC_ZR]), SP[ORC_I].mu, SP[ORC_S].mu, SP[ORC_G].mu};
   orc_record r;
   double o[ORC_NPROG];
-  point_core(in, dt, o, 1, &r, mu);
+  point_core(in, dt, o, 1, &r, mu4);
   memcpy(out, o, sizeof o);
   double q0 = in[ORC_QR], n0 = in[ORC_NR], z0 = in[ORC_ZR];
   double q1 = o[ORC_QR] - r.tau_aut, n1 = o[ORC_NR] - r.nr_aut;
@@ -509,6 +522,63 @@ void orc_point_3m(const double *in, double dt, double *out) {
   if (q0 > QMIN && n0 > 0.0 && q1 > 0.0 && n1 > 0.0) z = z0 * (q1 / q0) * (q1 / q0) * (n0 / n1);
   double d0 = 2.0 * RR0, d3 = d0 * d0 * d0;
   out[ORC_NPROG] = z + r.nr_aut * (d3 * d3);
+}
+
+/* the fixed-shape part of a sixth moment after the processes: z (q1/q0)^2
+   (n0/n1), q0, n0 what the rates saw, q1, n1 the result without the source
+   terms (zero where any of them is not positive) */
+static double z_kept(double z0, double q0, double n0, double q1, double n1) {
+  if (q0 > QMIN && n0 > 0.0 && q1 > 0.0 && n1 > 0.0) return z0 * (q1 / q0) * (q1 / q0) * (n0 / n1);
+  return 0.0;
+}
+
+/* Triple-moment scheme in the cold configuration: every sedimenting species
+   x in r, i, s, g carries its sixth moment z_x (fields ORC_ZR..ORC_ZG), each
+   rate sees the shape diagnosed per species from the input, and
+     - processes that keep a species' shape (accretion, self-collection,
+       evaporation, deposition, sublimation, riming, loss by melting) scale
+       its z as z (q'/q)^2 (n/n');
+     - sources add the sixth moment of what they add (moments of superposed
+       populations add): autoconversion n_aut (2 r0)^6 to rain; nucleation
+       n_nuc (m_i0 / a_i)^2 to ice; melting of species m gives rain the
+       melted fraction of its sixth moment in rain diameters, (a_m / a_r)^2
+       (tau_m / q_m) z_m, a particle of mass m having (m / a_r)^2.
+   in[ORC_NFIELDS_3MC] -> out[ORC_NPROG_3MC] (13 prognostic fields, then
+   z_r, z_i, z_s, z_g). */
+void orc_point_3m_cold(const double *in, double dt, double *out) {
+  static const int sp[4] = {ORC_R, ORC_I, ORC_S, ORC_G};
+  static const int qf[4] = {ORC_QR, ORC_QI, ORC_QS, ORC_QG};
+  static const int nf[4] = {ORC_NR, ORC_NI, ORC_NS, ORC_NG};
+  double mu4[4];
+  for (int x = 0; x < 4; ++x) mu4[x] = orc_shape_mu(sp[x], in[qf[x]], in[nf[x]], in[ORC_ZR + x]);
+  orc_record r;
+  double o[ORC_NPROG];
+  point_core(in, dt, o, 0, &r, mu4);
+  memcpy(out, o, sizeof o);
+  /* rain: the adjustment and activation leave it unchanged, so the rates saw the input */
+  double q1 = o[ORC_QR] - r.tau_aut, n1 = o[ORC_NR] - r.nr_aut, zsrc = 0.0;
+  for (int m = 0; m < 3; ++m) {
+    q1 -= r.melt_q[m];
+    n1 -= r.melt_n[m];
+    const double q0m = in[qf[1 + m]];
+    if (r.melt_q[m] > 0.0 && q0m > QMIN) {
+      const double ar = SP[sp[1 + m]].a / SP[ORC_R].a;
+      zsrc += ar * ar * (r.melt_q[m] / q0m) * in[ORC_ZR + 1 + m];
+    }
+  }
+  const double d0 = 2.0 * RR0, d3 = d0 * d0 * d0;
+  out[ORC_NPROG] = z_kept(in[ORC_ZR], in[ORC_QR], in[ORC_NR], q1, n1) + r.nr_aut * (d3 * d3) + zsrc;
+  /* ice species */
+  for (int m = 0; m < 3; ++m) {
+    double q1m = o[qf[1 + m]], n1m = o[nf[1 + m]], src = 0.0;
+    if (m == 0) {
+      q1m -= r.nuc_q;
+      n1m -= r.nuc_n;
+      const double di = MI0 / SP[ORC_I].a;
+      src = r.nuc_n * di * di;
+    }
+    out[ORC_NPROG + 1 + m] = z_kept(in[ORC_ZR + 1 + m], in[qf[1 + m]], in[nf[1 + m]], q1m, n1m) + src;
+  }
 }
 
 void orc_rates(const double *st, double dt, double *R) { orc_rates_cfg(st, dt, R, 0); }
@@ -532,7 +602,7 @@ void orc_point(const double *in, double dt, double *out) { orc_point_cfg(in, dt,
 void orc_point_aero(const double *in, double dt, double *out) {
   orc_record r;
   double o[ORC_NPROG];
-  point_core(in, dt, o, 1, &r, SP[ORC_R].mu);
+  point_core(in, dt, o, 1, &r, NULL);
   memcpy(out, o, sizeof o);
   double ma = in[ORC_MA], mac = in[ORC_MAC], mar = in[ORC_MAR], d;
   if (r.evap > 0.0 && r.qc0 > 0.0) {
@@ -575,12 +645,17 @@ unsigned orc_sediment_rain_3m(double *q, double *n, double *z, const double *rho
   return sediment_species(q, n, rho, dz, nlev, dt, precip, nsub, 1, NULL, NULL, z);
 }
 
+unsigned orc_sediment_3m(double *q, double *n, double *z, const double *rho, const double *dz, int nlev, double dt,
+                         double *precip, int *nsub) {
+  return sediment_species(q, n, rho, dz, nlev, dt, precip, nsub, 4, NULL, NULL, z);
+}
+
 /* the first nspecies of r, i, s, g (warm configuration: rain only); aer (may
    be NULL): aerosol mass in rain, moved with the rain's mass-weighted speed,
-   its surface flux accumulated in *aprecip; zr (may be NULL): the rain's
-   sixth moment (triple-moment scheme), moved with the sixth-moment-weighted
-   speed, every rain speed then taken at the shape diagnosed per level and
-   substep */
+   its surface flux accumulated in *aprecip; zr (may be NULL): the species'
+   sixth moments (triple-moment scheme; nspecies arrays of nlev), each moved
+   with its sixth-moment-weighted speed, every speed of the species then
+   taken at the shape diagnosed per level and substep */
 static unsigned sediment_species(double *q, double *n, const double *rho, const double *dz, int nlev, double dt,
                                  double *precip, int *nsub, int nspecies, double *aer, double *aprecip,
                                  double *zr) {
@@ -602,11 +677,12 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
   for (int m = 0; m < nspecies; ++m) {
     int sp = spx[m];
     double *qq = q + (size_t)m * nlev, *nn = n + (size_t)m * nlev;
-    const int tri = zr != NULL && m == 0;
+    const int tri = zr != NULL;
+    double *zz = tri ? zr + (size_t)m * nlev : NULL;
     double cmax = 0.0;
     for (int k = 0; k < nlev; ++k) {
       if (!(qq[k] > QMIN)) continue;
-      double mu = tri ? orc_rain_mu(qq[k], nn[k], zr[k]) : SP[sp].mu;
+      double mu = tri ? orc_shape_mu(sp, qq[k], nn[k], zz[k]) : SP[sp].mu;
       double lam = orc_lambda_mu(sp, qq[k], nn[k], mu);
       double c = orc_vq_mu(sp, rho[k], lam, mu) * dt / dz[k];
       if (c > cmax) cmax = c;
@@ -624,7 +700,7 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
         A[k] = 0.0;
         H[k] = 0.0;
         if (qq[k] > QMIN) {
-          double mu = tri ? orc_rain_mu(qq[k], nn[k], zr[k]) : SP[sp].mu;
+          double mu = tri ? orc_shape_mu(sp, qq[k], nn[k], zz[k]) : SP[sp].mu;
           double lam = orc_lambda_mu(sp, qq[k], nn[k], mu);
           /* a level never loses more than it holds within one substep: the
              speed is limited to dz_k / dts (binds only when a later substep's
@@ -639,7 +715,7 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
           if (tri) {
             double vz = orc_vz_mu(sp, rho[k], lam, mu);
             if (vz > vlim) vz = vlim;
-            H[k] = rho[k] * (zr[k] > 0.0 ? zr[k] : 0.0) * vz;
+            H[k] = rho[k] * (zz[k] > 0.0 ? zz[k] : 0.0) * vz;
           }
         }
       }
@@ -651,7 +727,7 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
         qq[k] += dts * (F[k + 1] - F[k]) / (rho[k] * dz[k]);
         nn[k] += dts * (G[k + 1] - G[k]) / (rho[k] * dz[k]);
         if (with_aer) aer[k] += dts * (A[k + 1] - A[k]) / (rho[k] * dz[k]);
-        if (tri) zr[k] += dts * (H[k + 1] - H[k]) / (rho[k] * dz[k]);
+        if (tri) zz[k] += dts * (H[k + 1] - H[k]) / (rho[k] * dz[k]);
       }
       precip[m] += F[0] * dts;
       if (with_aer) *aprecip += A[0] * dts;
@@ -666,13 +742,14 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
 
 /* ----------------------------------------------------------- full step */
 /* aero: the state has ORC_NFIELDS_AERO fields and precip 5 rows (warm only);
-   tri: the state has ORC_NFIELDS_3M fields (warm only) */
+   tri: the state has ORC_NFIELDS_3M fields (warm) or ORC_NFIELDS_3MC (cold) */
 static unsigned step_column(double *fld, long pitch, int nlev, int c, const double *dz,
                             double *precip, int *nsub, double dt, int warm, int aero, int tri) {
   unsigned err = 0;
   long fs = (long)nlev * pitch; /* field stride */
-  const int nfields = aero ? ORC_NFIELDS_AERO : tri ? ORC_NFIELDS_3M : ORC_NFIELDS;
-  double in[ORC_NFIELDS_AERO], out[ORC_NPROG_AERO];
+  const int nfields = aero ? ORC_NFIELDS_AERO : tri ? (warm ? ORC_NFIELDS_3M : ORC_NFIELDS_3MC) : ORC_NFIELDS;
+  const int nz = tri ? (warm ? 1 : 4) : 0;   /* sixth moments carried */
+  double in[ORC_NFIELDS_3MC], out[ORC_NPROG_3MC];
   const int map[ORC_NPROG_AERO] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, ORC_MA, ORC_MAC, ORC_MAR};
   for (int k = 0; k < nlev; ++k) {
     for (int f = 0; f < nfields; ++f) in[f] = fld[f * fs + (long)k * pitch + c];
@@ -680,22 +757,23 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
       orc_point_aero(in, dt, out);
       for (int f = 0; f < ORC_NPROG_AERO; ++f) fld[map[f] * fs + (long)k * pitch + c] = out[f];
     } else if (tri) {
-      orc_point_3m(in, dt, out);
+      if (warm) orc_point_3m(in, dt, out);
+      else orc_point_3m_cold(in, dt, out);
       for (int f = 0; f < ORC_NPROG; ++f) fld[f * fs + (long)k * pitch + c] = out[f];
-      fld[ORC_ZR * fs + (long)k * pitch + c] = out[ORC_NPROG];
+      for (int x = 0; x < nz; ++x) fld[(ORC_ZR + x) * fs + (long)k * pitch + c] = out[ORC_NPROG + x];
     } else {
       orc_point_cfg(in, dt, out, warm);
       for (int f = 0; f < ORC_NPROG; ++f) fld[f * fs + (long)k * pitch + c] = out[f];
     }
   }
-  double *buf = (double *)malloc(sizeof(double) * (size_t)(11 * nlev));
+  double *buf = (double *)malloc(sizeof(double) * (size_t)(14 * nlev));
   double *q = buf, *n = buf + 4 * nlev, *rho = buf + 8 * nlev, *aer = buf + 9 * nlev, *zr = buf + 10 * nlev;
   static const int qf[4] = {ORC_QR, ORC_QI, ORC_QS, ORC_QG};
   static const int nf[4] = {ORC_NR, ORC_NI, ORC_NS, ORC_NG};
   for (int k = 0; k < nlev; ++k) {
     rho[k] = fld[ORC_RHO * fs + (long)k * pitch + c];
     aer[k] = aero ? fld[ORC_MAR * fs + (long)k * pitch + c] : 0.0;
-    zr[k] = tri ? fld[ORC_ZR * fs + (long)k * pitch + c] : 0.0;
+    for (int x = 0; x < nz; ++x) zr[x * nlev + k] = fld[(ORC_ZR + x) * fs + (long)k * pitch + c];
     for (int m = 0; m < 4; ++m) {
       q[m * nlev + k] = fld[qf[m] * fs + (long)k * pitch + c];
       n[m * nlev + k] = fld[nf[m] * fs + (long)k * pitch + c];
@@ -706,8 +784,8 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
   const int nsp = warm ? 1 : 4;
   double apr = 0.0;
   err |= sediment_species(q, n, rho, dz, nlev, dt, pr, ns, nsp, aero ? aer : NULL, &apr, tri ? zr : NULL);
-  if (tri)
-    for (int k = 0; k < nlev; ++k) fld[ORC_ZR * fs + (long)k * pitch + c] = zr[k];
+  for (int x = 0; x < nz; ++x)
+    for (int k = 0; k < nlev; ++k) fld[(ORC_ZR + x) * fs + (long)k * pitch + c] = zr[x * nlev + k];
   if (aero) {
     for (int k = 0; k < nlev; ++k) fld[ORC_MAR * fs + (long)k * pitch + c] = aer[k];
     precip[4 * pitch + c] += apr;
@@ -728,7 +806,8 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
     if (aero)
       for (int f = ORC_MA; f <= ORC_MAR; ++f)
         if (!isfinite(fld[f * fs + (long)k * pitch + c])) err |= ORC_ERR_NONFINITE;
-    if (tri && !isfinite(fld[ORC_ZR * fs + (long)k * pitch + c])) err |= ORC_ERR_NONFINITE;
+    for (int x = 0; x < nz; ++x)
+      if (!isfinite(fld[(ORC_ZR + x) * fs + (long)k * pitch + c])) err |= ORC_ERR_NONFINITE;
   }
   return err;
 }
@@ -768,6 +847,19 @@ unsigned orc_step_3m(double *fld, long pitch, int ncols, int nlev, const double 
 #pragma omp parallel for schedule(guided) num_threads(nthreads) reduction(| : err)
 #endif
   for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, NULL, dt, 1, 0, 1);
+  (void)nthreads;
+  return err;
+}
+
+unsigned orc_step_3m_cold(double *fld, long pitch, int ncols, int nlev, const double *dz, double *precip,
+                          double dt, int nthreads) {
+  unsigned err = 0;
+  if (nlev <= 0 || ncols <= 0) return 0;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(guided) num_threads(nthreads) reduction(| : err)
+#endif
+  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, NULL, dt, 0, 0, 1);
   (void)nthreads;
   return err;
 }

@@ -32,10 +32,13 @@ enum {
    rain mar (kg/kg) -- and a fifth precipitation row (aerosol deposited). */
 enum { ORC_MA = ORC_NFIELDS, ORC_MAC, ORC_MAR, ORC_NFIELDS_AERO };
 #define ORC_NPROG_AERO (ORC_NPROG + 3)
-/* Triple-moment rain extension (warm configuration): one more field after
-   the 16 above, the rain's sixth moment z (m^6 per kg of air). */
+/* Triple-moment extension: the sixth moments z (m^6 per kg of air) after the
+   16 fields above -- rain only in the warm configuration (17 fields), rain,
+   ice, snow and graupel in the cold one (20 fields). */
 enum { ORC_ZR = ORC_NFIELDS, ORC_NFIELDS_3M };
+enum { ORC_ZI = ORC_NFIELDS_3M, ORC_ZS, ORC_ZG, ORC_NFIELDS_3MC };
 #define ORC_NPROG_3M (ORC_NPROG + 1)
+#define ORC_NPROG_3MC (ORC_NPROG + 4)
 
 /* Hydrometeor species index. */
 enum { ORC_C = 0, ORC_R, ORC_I, ORC_S, ORC_G, ORC_NSPECIES };
@@ -111,6 +114,18 @@ double orc_vz_mu(int sp, double rho, double lam, double mu);
    fields evolve as in the warm configuration, except that rain evaporation
    and the rain fall speeds use the diagnosed shape. */
 double orc_rain_mu(double q, double n, double z);
+/* the same for any species (all have mass exponent b = 3) */
+double orc_shape_mu(int sp, double q, double n, double z);
+/* The cold configuration with triple-moment r, i, s, g: a point
+   in[ORC_NFIELDS_3MC] -> out[ORC_NPROG_3MC]; sedimentation of q, n, z for the
+   four species ([4][nlev] each); a step over fld[ORC_NFIELDS_3MC][nlev][pitch]
+   with precip[4][pitch].  Every rate and fall speed of a species takes its
+   diagnosed shape. */
+void   orc_point_3m_cold(const double *in, double dt, double *out);
+unsigned orc_sediment_3m(double *q, double *n, double *z, const double *rho, const double *dz, int nlev, double dt,
+                         double *precip, int *nsub);
+unsigned orc_step_3m_cold(double *fld, long pitch, int ncols, int nlev, const double *dz, double *precip,
+                          double dt, int nthreads);
 void   orc_point_3m(const double *in, double dt, double *out);
 unsigned orc_sediment_rain_3m(double *q, double *n, double *z, const double *rho, const double *dz, int nlev,
                               double dt, double *precip, int *nsub);

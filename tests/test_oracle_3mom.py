@@ -172,3 +172,173 @@ def test_column_water_budget_with_random_shapes():
     w1 = sum((out[F[x], :, :32] * rho * dz[:, None]).sum(0) for x in liq)
     assert np.allclose(w1 + pr[0, :32], w0, rtol=1e-12, atol=0)
     assert (out[ZR, :, :32] >= 0).all()
+
+
+# ------------------------------------------------ cold configuration: r, i, s, g
+ZC = {"r": 16, "i": 17, "s": 18, "g": 19}
+QF = {"r": F["qr"], "i": F["qi"], "s": F["qs"], "g": F["qg"]}
+NF = {"r": F["nr"], "i": F["ni"], "s": F["ns"], "g": F["ng"]}
+
+
+def _z_at(sp, q, n, mu):
+    return G(mu) * (q / O.param(f"a_{sp}")) ** 2 / n
+
+
+def _cold_state(ncols, nlev, seed, fixed_shape=False):
+    dz = synth.dz_stretched(nlev)
+    base = synth.make_state("deep_convective", ncols, nlev, dz, seed=seed)
+    fld = np.zeros((20,) + base.shape[1:])
+    fld[:16] = base
+    rng = np.random.default_rng(seed)
+    for sp in "risg":
+        q, n = base[QF[sp]], base[NF[sp]]
+        mu = np.full(q.shape, O.param(f"mu_{sp}")) if fixed_shape else rng.uniform(0.0, 8.0, q.shape)
+        ok = (q > 1e-14) & (n > 0)
+        fld[ZC[sp]][ok] = _z_at(sp, q[ok], n[ok], mu[ok])
+    return np.ascontiguousarray(fld), dz
+
+
+def _point(T, p, **kw):
+    st = np.zeros(20)
+    st[F["T"]], st[F["p"]], st[F["rho"]] = T, p, p / (287.04 * T)
+    for k, v in kw.items():
+        st[ZC[k[1]] if k.startswith("z") else F[k]] = v
+    return st
+
+
+def test_melting_gives_rain_the_melting_species_shape():
+    """Snow melting into no rain: the rain made is the melted part of the
+    snow's population, so its shape (G = z n / (q/a)^2) is the snow's; the
+    snow loses mass and number in proportion and keeps its shape."""
+    T, p = 276.0, 9.0e4
+    qs = O.qsat(O.es_liq(T), p)
+    for mu in (0.5, 3.0, 9.0):
+        q, n = 2e-4, 5e3
+        st = _point(T, p, qv=0.9 * qs, qs=q, ns=n, zs=_z_at("s", q, n, mu), na=1e8)
+        out = O.point_3m_cold(st, 5.0)
+        assert 0.0 < out[F["qr"]] < q and out[F["nr"]] > 0
+        assert abs(O.shape_mu("r", out[F["qr"]], out[F["nr"]], out[13]) - mu) < 1e-9
+        assert abs(O.shape_mu("s", out[F["qs"]], out[F["ns"]], out[15]) - mu) < 1e-9
+        # the sixth moment is conserved in particle-mass units: (m / a_r)^2 summed
+        a_r, a_s = O.param("a_r"), O.param("a_s")
+        assert np.isclose(out[13] + (a_s / a_r) ** 2 * out[15], (a_s / a_r) ** 2 * st[ZC["s"]], rtol=1e-12)
+
+
+def test_nucleation_makes_monodisperse_ice():
+    T, p = 255.0, 5.0e4
+    qsi, qsl = O.qsat(O.es_ice(T), p), O.qsat(O.es_liq(T), p)
+    st = _point(T, p, qv=0.5 * (qsi + qsl), na=1e8)
+    out = O.point_3m_cold(st, 1.0)
+    q, n, z = out[F["qi"]], out[F["ni"]], out[14]
+    assert q > 0 and n > 0
+    assert np.isclose(z * n / (q / O.param("a_i")) ** 2, 1.0, rtol=1e-9)
+    assert np.isclose(z, n * (O.param("m_i0") / O.param("a_i")) ** 2, rtol=1e-12)
+
+
+def test_deposition_keeps_every_ice_species_shape():
+    T, p = 270.0, 7.0e4                      # warmer than nucleation, supersaturated over ice only
+    qsi, qsl = O.qsat(O.es_ice(T), p), O.qsat(O.es_liq(T), p)
+    kw = {"qv": 0.5 * (qsi + qsl), "na": 1e8}
+    mus = {"i": 1.5, "s": 4.0, "g": 7.0}
+    for sp, (q, n) in {"i": (1e-5, 1e5), "s": (1e-4, 1e4), "g": (3e-4, 2e3)}.items():
+        kw["q" + sp], kw["n" + sp], kw["z" + sp] = q, n, _z_at(sp, q, n, mus[sp])
+    st = _point(T, p, **kw)
+    out = O.point_3m_cold(st, 2.0)
+    for sp, off in (("i", 14), ("s", 15), ("g", 16)):
+        assert out[QF[sp]] > st[QF[sp]]                      # grew
+        assert abs(O.shape_mu(sp, out[QF[sp]], out[NF[sp]], out[off]) - mus[sp]) < 1e-9
+
+
+def test_cold_reduces_to_two_moment_where_no_shape_can_change():
+    """No cloud (no autoconversion, no riming), subsaturated over ice and over
+    water (no nucleation, no deposition growth that matters), no ice species
+    where T > T0 (no melting): with z at the species' fixed shapes the 16
+    fields are those of the two-moment cold step."""
+    fld, dz = _cold_state(40, 150, seed=83, fixed_shape=True)
+    T0 = O.param("T0")
+    for k in range(fld.shape[1]):
+        for c in range(40):
+            T, p = fld[F["T"], k, c], fld[F["p"], k, c]
+            qs = min(O.qsat(O.es_liq(T), p), O.qsat(O.es_ice(T), p))
+            fld[F["qv"], k, c] = min(fld[F["qv"], k, c], 0.97 * qs)
+            if T > T0:
+                for sp in "isg":
+                    fld[QF[sp], k, c] = fld[NF[sp], k, c] = fld[ZC[sp], k, c] = 0.0
+    fld[F["qc"]] = 0.0
+    fld[F["nc"]] = 0.0
+    a = fld.copy()
+    pa, ea = O.step_3m_cold(a, 40, dz, 1.0)
+    b = np.ascontiguousarray(fld[:16].copy())
+    pb, _, eb = O.step(b, 40, dz, 1.0)
+    assert ea == 0 and eb == 0
+    assert not np.array_equal(a[F["qg"]], fld[F["qg"]])
+    for f in range(13):
+        assert np.allclose(a[f, :, :40], b[f, :, :40], rtol=1e-11, atol=1e-30), synth.FIELDS[f]
+    assert np.allclose(pa[:, :40], pb[:, :40], rtol=1e-11, atol=0)
+
+
+def test_cold_equals_warm_on_an_ice_free_warm_state():
+    """No ice anywhere and warmer than the nucleation threshold: the cold
+    triple-moment step is the warm one bit for bit (rain fields and z_r)."""
+    fld, dz, ncols, nlev, dt, _ = synth.workload("stratus_16x16x50")
+    top = int(np.argmax(fld[F["T"], :, :ncols].min(axis=1) < O.param("T_nuc") + 1.0))
+    sub = np.ascontiguousarray(fld[:, :top, :])
+    for sp in "isg":
+        sub[QF[sp]] = sub[NF[sp]] = 0.0
+    rng = np.random.default_rng(84)
+    qr, nr = sub[F["qr"]], sub[F["nr"]]
+    zr = np.zeros(qr.shape)
+    ok = (qr > 1e-14) & (nr > 0)
+    zr[ok] = G(rng.uniform(0.0, 6.0, qr.shape)[ok]) * (qr[ok] / A_R) ** 2 / nr[ok]
+    warm = np.zeros((17,) + sub.shape[1:])
+    warm[:16], warm[16] = sub, zr
+    cold = np.zeros((20,) + sub.shape[1:])
+    cold[:16], cold[16] = sub, zr
+    warm, cold = np.ascontiguousarray(warm), np.ascontiguousarray(cold)
+    dzs = np.ascontiguousarray(dz[:top])
+    pw, ew = O.step_3m(warm, ncols, dzs, dt)
+    pc, ec = O.step_3m_cold(cold, ncols, dzs, dt)
+    assert ew == 0 and ec == 0
+    assert not np.array_equal(warm[F["qr"]], sub[F["qr"]])
+    assert np.array_equal(warm, cold[:17]) and np.array_equal(pw, pc)
+    assert np.all(cold[17:] == 0.0)
+
+
+def test_every_species_sixth_moment_falls_with_its_own_speed():
+    """One substep from a single occupied level, Courant number 1/2: the level
+    keeps 1 - v dt/dz of its mass and of its sixth moment, with v the
+    mass- and the sixth-moment-weighted speeds at the diagnosed shape (each
+    pinned by quadrature); the sixth moment falls faster (size sorting)."""
+    nlev = 8
+    for x, sp in enumerate("risg"):
+        dz = np.full(nlev, 50.0)
+        rho = np.full(nlev, 1.0)
+        q, n, z = np.zeros((4, nlev)), np.zeros((4, nlev)), np.zeros((4, nlev))
+        q[x, 5], n[x, 5] = 2e-4, 2e3
+        z[x, 5] = _z_at(sp, q[x, 5], n[x, 5], 2.5)
+        mu = O.shape_mu(sp, q[x, 5], n[x, 5], z[x, 5])
+        lam = O.lam_mu(sp, q[x, 5], n[x, 5], mu)
+        vq, vz = O.vq_mu(sp, 1.0, lam, mu), O.vz_mu(sp, 1.0, lam, mu)
+        assert vz > vq, sp
+        dt = 0.5 * dz[0] / vq
+        q1, n1, z1, pr, ns, err = O.sediment_3m(q, n, z, rho, dz, dt)
+        assert err == 0 and ns[x] == 1
+        cq, cz = vq * dt / dz[0], min(vz, dz[0] / dt) * dt / dz[0]
+        assert np.isclose(q1[x, 5], q[x, 5] * (1 - cq), rtol=1e-12) and np.isclose(q1[x, 4], q[x, 5] * cq, rtol=1e-12)
+        assert np.isclose(z1[x, 5], z[x, 5] * (1 - cz), rtol=1e-12) and np.isclose(z1[x, 4], z[x, 5] * cz, rtol=1e-12)
+        others = [y for y in range(4) if y != x]
+        assert not q1[others].any() and not z1[others].any()
+
+
+def test_cold_column_water_budget_with_random_shapes():
+    fld, dz = _cold_state(32, 150, seed=85)
+    out = fld.copy()
+    pr, err = O.step_3m_cold(out, 32, dz, 1.0)
+    assert err == 0
+    rho = fld[F["rho"], :, :32]
+    names = ("qv", "qc", "qr", "qi", "qs", "qg")
+    w0 = sum((fld[F[x], :, :32] * rho * dz[:, None]).sum(0) for x in names)
+    w1 = sum((out[F[x], :, :32] * rho * dz[:, None]).sum(0) for x in names)
+    assert np.allclose(w1 + pr[:, :32].sum(0), w0, rtol=1e-12, atol=0)
+    assert (out[16:, :, :32] >= 0).all()
+    assert (out[16:, :, :32] > 0).any(axis=(1, 2)).all()
