@@ -137,19 +137,24 @@ int casim_default_params(casim_params *p);
    entry points reject such a context (CASIM_ERR_ARG). */
 #define CASIM_AEROSOL 2
 
-/* casim_init flag, with CASIM_WARM only (not with CASIM_AEROSOL): triple-
-   moment rain (Section 2: CASIM is a three-moment bulk scheme).  The state
-   has 17 fields -- the 16 above, then zr, the rain's sixth moment (m^6 per kg
-   of air, the radar reflectivity factor per unit mass).  The rain's shape
-   parameter mu is diagnosed at every point from
-     G = zr nr / (qr/a)^2 = (mu+4)(mu+5)(mu+6) / ((mu+1)(mu+2)(mu+3))
-   (mu in [0, 20]; the species' fixed mu where rain is absent); rain
-   evaporation and the rain fall speeds use it, and zr sediments with the
-   sixth-moment-weighted speed.  Accretion, self-collection and evaporation
-   change zr at the diagnosed shape, zr (q'/q)^2 (n/n'); autoconversion adds
-   its new drops of diameter 2 r_r0 as (2 r_r0)^6 each.  Requires the rain
-   mass exponent b = 3.  Supported by casim_step (both precisions) and the
-   checkpoint calls; the other step entry points reject such a context. */
+/* casim_init flag (not with CASIM_AEROSOL): the triple-moment scheme
+   (Section 2: CASIM is a three-moment bulk scheme).  Each sedimenting species
+   x carries its sixth moment z_x (m^6 per kg of air; for rain the radar
+   reflectivity factor per unit mass): with CASIM_WARM rain only, a 17-field
+   state (the 16 above, then zr); without it r, i, s, g, a 20-field state
+   (then zr, zi, zs, zg).  A species' shape parameter mu is diagnosed at every
+   point from
+     G = z n / (q/a)^2 = (mu+4)(mu+5)(mu+6) / ((mu+1)(mu+2)(mu+3))
+   (mu in [0, 20]; the species' fixed mu where it is absent); its rates
+   (evaporation, deposition, riming, melting) and fall speeds use that shape,
+   and z sediments with the sixth-moment-weighted speed.  Processes that keep
+   a species' shape change z as z (q'/q)^2 (n/n'); sources add the sixth
+   moment of what they bring: autoconversion (2 r_r0)^6 per new drop,
+   nucleation (m_i0 / a_i)^2 per new crystal, and melting of species m the
+   melted fraction of z_m in rain diameters, (a_m / a_r)^2 (melted / q_m) z_m.
+   Requires mass exponent b = 3 for those species.  Supported by casim_step
+   (both precisions) and the checkpoint calls; the other step entry points
+   reject such a context. */
 #define CASIM_THREE_MOMENT 4
 
 /* Largest level count of a column (the step keeps a column's dz in shared
@@ -159,8 +164,8 @@ int casim_default_params(casim_params *p);
 /* Create a context on the current CUDA device (Section 3.2: the one-off
    set-up that copies constants and allocates device memory).  `params` may be
    NULL for the defaults; `precision` is a casim_precision; `flags` is 0,
-   CASIM_WARM, CASIM_WARM | CASIM_AEROSOL or CASIM_WARM | CASIM_THREE_MOMENT
-   (CASIM_ERR_ARG otherwise).  Allocates a small device error word.  On
+   CASIM_WARM, CASIM_WARM | CASIM_AEROSOL, CASIM_THREE_MOMENT or CASIM_WARM |
+   CASIM_THREE_MOMENT (CASIM_ERR_ARG otherwise).  Allocates a small device error word.  On
    failure *ctx is set to NULL. */
 int casim_init(casim_ctx **ctx, const casim_params *params, int precision, int flags);
 
@@ -382,7 +387,8 @@ const char *casim_last_cuda_error(void);
  * ncols and a hash of the scheme parameters) followed by dz, the fields and
  * the precipitation rows as raw FP64 values in host byte order.  A run of N
  * steps equals, bit for bit, k steps, save, load, N - k steps.
- * nfields is CASIM_NFIELDS, CASIM_NFIELDS_3MOM for the triple-moment state,
+ * nfields is CASIM_NFIELDS, CASIM_NFIELDS_3MOM or CASIM_NFIELDS_3MOM_COLD for
+ * the triple-moment states (warm, cold),
  * or CASIM_NFIELDS_AEROSOL for the activated-aerosol state (whose precip has
  * CASIM_NPRECIP + 1 rows).  Device pointers;
  * both calls wait for `stream`.  params may be NULL (the defaults).
@@ -390,6 +396,7 @@ const char *casim_last_cuda_error(void);
  * parameter hash differ from the arguments; file errors give CASIM_ERR_IO. */
 #define CASIM_NFIELDS_AEROSOL 19
 #define CASIM_NFIELDS_3MOM 17
+#define CASIM_NFIELDS_3MOM_COLD 20
 int casim_state_save(const char *path, const casim_params *params, const casim_state *s, int ncols, int nlev,
                      int nfields, void *stream);
 int casim_state_load(const char *path, const casim_params *params, const casim_state *s, int ncols, int nlev,

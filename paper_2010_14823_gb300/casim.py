@@ -20,9 +20,10 @@ CASIM_FP64 = 0
 CASIM_MIXED = 1
 CASIM_WARM = 1          # casim_init flag: the warm configuration
 CASIM_AEROSOL = 2       # casim_init flag (with CASIM_WARM): activated-aerosol mass, 19 fields, 5 precip rows
-CASIM_THREE_MOMENT = 4  # casim_init flag (with CASIM_WARM): triple-moment rain, 17 fields
+CASIM_THREE_MOMENT = 4  # casim_init flag: triple-moment rain (with CASIM_WARM, 17 fields) or r, i, s, g (20 fields)
 NFIELDS_AERO = 19
 NFIELDS_3MOM = 17
+NFIELDS_3MOM_COLD = 20
 CASIM_MAX_LEV = 1024   # largest level count of a column
 NFIELDS = 16
 NPROG = 13
@@ -332,7 +333,7 @@ class Domain:
         state, whose precip then has 5 rows."""
         import torch
         nf, nlev, pitch = fld.shape
-        assert nf in (NFIELDS, NFIELDS_3MOM, NFIELDS_AERO) and pitch % 32 == 0 and pitch >= ncols
+        assert nf in (NFIELDS, NFIELDS_3MOM, NFIELDS_AERO, NFIELDS_3MOM_COLD) and pitch % 32 == 0 and pitch >= ncols
         self.ncols, self.nlev, self.pitch = ncols, nlev, pitch
         if isinstance(fld, torch.Tensor):
             assert fld.dtype == torch.float64

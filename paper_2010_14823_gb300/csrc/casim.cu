@@ -168,18 +168,26 @@ static void derive(const casim_params &p, ConstK<R> &K, double (*l)(double)) {
     S.dep = (R)(4.0 * pi * p.ccap[x]);
     S.mlt = (R)(4.0 * pi * p.ccap[x] * p.Ka / p.Lf);
   }
-  // triple-moment rain (species 1)
-  K.r3_a = (R)p.a[1];
-  K.r3_dv = (R)p.dv[1];
-  K.r3_mu0 = (R)p.mu[1];
-  K.r3_mumax = (R)20.0;
-  K.r3_lgdmax = (R)l(p.dmax[1]);
-  K.r3_lgdmin = (R)l(p.dmin[1]);
-  K.r3_ev1c = (R)(0.78 / p.a[1]);
-  K.r3_ev2c = (R)(0.31 * std::sqrt(p.cv[1]) / p.a[1]);
-  K.r3_cv = (R)p.cv[1];
+  // triple-moment species r, i, s, g (species 1..4)
+  for (int x = 0; x < 4; ++x) {
+    const int sp = 1 + x;
+    K.s3_a[x] = (R)p.a[sp];
+    K.s3_dv[x] = (R)p.dv[sp];
+    K.s3_mu0[x] = (R)p.mu[sp];
+    K.s3_lgdmax[x] = (R)l(p.dmax[sp]);
+    K.s3_lgdmin[x] = (R)l(p.dmin[sp]);
+    K.s3_ev1c[x] = (R)(0.78 / p.a[sp]);
+    K.s3_ev2c[x] = (R)(0.31 * std::sqrt(p.cv[sp]) / p.a[sp]);
+    K.s3_cv[x] = (R)p.cv[sp];
+    K.s3_rimc[x] = (R)(0.25 * pi * p.e_rim * p.cv[sp] / p.a[sp]);
+    const double ar = p.a[sp] / p.a[1];
+    K.s3_ar2[x] = (R)(ar * ar);
+  }
+  K.s3_mumax = (R)20.0;
   const double d0 = 2.0 * p.r_r0, d3 = d0 * d0 * d0;
-  K.r3_d0_6 = (R)(d3 * d3);
+  K.s3_d0_6 = (R)(d3 * d3);
+  const double di = p.m_i0 / p.a[2];
+  K.s3_di_6 = (R)(di * di);
 }
 
 static double ln_(double x) { return std::log(x); }
@@ -202,9 +210,14 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   *out = nullptr;
   if (precision != CASIM_FP64 && precision != CASIM_MIXED) return CASIM_ERR_ARG;
   if ((flags & ~(CASIM_WARM | CASIM_AEROSOL | CASIM_THREE_MOMENT)) != 0) return CASIM_ERR_ARG;
-  if ((flags & (CASIM_AEROSOL | CASIM_THREE_MOMENT)) && !(flags & CASIM_WARM)) return CASIM_ERR_ARG;
+  if ((flags & CASIM_AEROSOL) && !(flags & CASIM_WARM)) return CASIM_ERR_ARG;
   if ((flags & CASIM_AEROSOL) && (flags & CASIM_THREE_MOMENT)) return CASIM_ERR_ARG;
-  if ((flags & CASIM_THREE_MOMENT) && !(params ? params->b[1] == 3.0 : true)) return CASIM_ERR_ARG;
+  if ((flags & CASIM_THREE_MOMENT) && params) {
+    // the shape identity needs b = 3 for every species that carries z
+    const int last = (flags & CASIM_WARM) ? 1 : 4;
+    for (int x = 1; x <= last; ++x)
+      if (params->b[x] != 3.0) return CASIM_ERR_ARG;
+  }
   casim_params p;
   if (params) p = *params;
   else casim_default_params(&p);
@@ -267,10 +280,14 @@ static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, 
     if (tend) return CASIM_ERR_ARG;
     if (ctx->precision == CASIM_MIXED) k_step<PolicyMixWarmAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
     else k_step<PolicyF64WarmAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-  } else if (ctx->tri) {
+  } else if (ctx->tri && ctx->warm) {
     if (tend) return CASIM_ERR_ARG;
     if (ctx->precision == CASIM_MIXED) k_step<PolicyMixWarm3, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
     else k_step<PolicyF64Warm3, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+  } else if (ctx->tri) {
+    if (tend) return CASIM_ERR_ARG;
+    if (ctx->precision == CASIM_MIXED) k_step<PolicyMix3, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+    else k_step<PolicyF643, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
   } else if (ctx->precision == CASIM_MIXED && !ctx->warm) {
     if (tend) k_step<PolicyMix, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
     else k_step<PolicyMix, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
@@ -520,7 +537,7 @@ extern "C" int casim_batch_create(casim_ctx *ctx, const casim_state *domains, co
                                   int ndom, casim_batch **out) {
   if (!out) return CASIM_ERR_ARG;
   *out = nullptr;
-  if (!ctx || ctx->warm || ndom < 1 || !domains || !ncols || !nlev) return CASIM_ERR_ARG;
+  if (!ctx || ctx->warm || ctx->tri || ndom < 1 || !domains || !ncols || !nlev) return CASIM_ERR_ARG;
   casim_batch *b = new casim_batch();
   b->ctx = ctx;
   b->ndom = ndom;
@@ -1284,7 +1301,7 @@ extern "C" int casim_mlp_loss_grad_host(casim_mlp *m, const float *Xn, const flo
 extern "C" int casim_mlp_data(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, float *X,
                               float *Y, float *M, long long *pts, long long cap, long long *rows, void *stream) {
   NvtxRange nvtx_range_("casim_mlp_data");
-  if (!ctx || ctx->warm || !X || !Y || !M || cap < 0 || !rows) return CASIM_ERR_ARG;
+  if (!ctx || ctx->warm || ctx->tri || !X || !Y || !M || cap < 0 || !rows) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK) return rc;
   *rows = 0;
@@ -1398,7 +1415,7 @@ extern "C" int casim_mlp_set_norm(casim_mlp *m, const float *stats) {
 extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_state *s, int ncols, int nlev,
                                     double dt, void *stream, long long *served) {
   NvtxRange nvtx_range_("casim_step_surrogate");
-  if (!ctx || ctx->warm || !m || !m->fitted || ctx->precision != CASIM_MIXED) return CASIM_ERR_ARG;
+  if (!ctx || ctx->warm || ctx->tri || !m || !m->fitted || ctx->precision != CASIM_MIXED) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1485,7 +1502,8 @@ uint64_t params_hash(const casim_params *params) {
 int ckpt_check(const casim_state *s, int ncols, int nlev, int nfields) {
   if (!s || !s->fld || !s->dz || !s->precip || ncols < 0 || nlev < 1 || nlev > kMaxLev) return CASIM_ERR_ARG;
   if (s->pitch < ncols || s->pitch % 32 != 0) return CASIM_ERR_ARG;
-  if (nfields != CASIM_NFIELDS && nfields != CASIM_NFIELDS_AEROSOL && nfields != CASIM_NFIELDS_3MOM)
+  if (nfields != CASIM_NFIELDS && nfields != CASIM_NFIELDS_AEROSOL && nfields != CASIM_NFIELDS_3MOM &&
+      nfields != CASIM_NFIELDS_3MOM_COLD)
     return CASIM_ERR_ARG;
   return CASIM_OK;
 }

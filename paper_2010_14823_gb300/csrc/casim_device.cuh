@@ -65,11 +65,15 @@ struct ConstK {
   // air
   R mu_air, inv_dv, lgrho0, twopi;
   SpeciesK<R> sp[5];
-  // triple-moment rain: what the shape-dependent rain constants are built from
-  R r3_a, r3_dv, r3_mu0, r3_mumax;  // a (M3 = q / a), fall-speed exponent d, fixed and largest shape
-  R r3_lgdmax, r3_lgdmin;           // log of the mean-diameter bounds (policy base)
-  R r3_ev1c, r3_ev2c, r3_cv;        // 0.78 / a, 0.31 sqrt(cv) / a, cv
-  R r3_d0_6;                        // (2 r0)^6: sixth moment of one new drop
+  // triple-moment species r, i, s, g (index 0..3, species 1..4): what their
+  // shape-dependent constants are built from
+  R s3_a[4], s3_dv[4], s3_mu0[4];    // a (M3 = q / a), fall-speed exponent d, fixed shape
+  R s3_lgdmax[4], s3_lgdmin[4];      // log of the mean-diameter bounds (policy base)
+  R s3_ev1c[4], s3_ev2c[4], s3_cv[4], s3_rimc[4];   // 0.78 / a, 0.31 sqrt(cv) / a, cv, (pi/4) E cv / a
+  R s3_ar2[4];                       // (a_x / a_r)^2: a particle's sixth moment in rain diameters
+  R s3_mumax;                        // largest shape
+  R s3_d0_6;                         // (2 r0)^6: sixth moment of one new drop
+  R s3_di_6;                         // (m_i0 / a_i)^2: of one new crystal
 };
 
 struct KParams {
@@ -236,7 +240,22 @@ struct Pt {
   double T, qv, qc, qr, qi, qs, qg, nc, nr, ni, ns, ng, na, p, rho, w;
   double ma, mac, mar;   // activated-aerosol mass (free, in cloud, in rain): aerosol-mass policies only
   double zr;             // the rain's sixth moment: triple-moment policies only
+  double zi, zs, zg;     // those of ice, snow, graupel: cold triple-moment policies only
 };
+
+// sixth moment of sedimenting species x (r, i, s, g)
+__device__ __forceinline__ double &zref(Pt &s, int x) {
+  return x == 0 ? s.zr : x == 1 ? s.zi : x == 2 ? s.zs : s.zg;
+}
+__device__ __forceinline__ double zval(const Pt &s, int x) {
+  return x == 0 ? s.zr : x == 1 ? s.zi : x == 2 ? s.zs : s.zg;
+}
+
+// number of sixth moments a policy carries: rain only (warm), r, i, s, g (cold)
+template <class M>
+__host__ __device__ constexpr int nz3() {
+  return M::kTri ? (M::kWarm ? 1 : 4) : 0;
+}
 
 // Working values of a point in the compute precision (after adjustment and
 // activation, as the rates see them).
@@ -244,7 +263,7 @@ template <class R>
 struct W {
   double Td;   // FP64 temperature (FP64 form only: ice saturation as the oracle writes it)
   R T, tc, p, rho, qv, qc, qr, qx[3], nc, nr, nx[3];
-  R mu_r;      // rain shape parameter (triple-moment policies)
+  R mu3[4];    // shape parameters of r, i, s, g (triple-moment policies)
   unsigned hmax;   // mixed form: largest |high word| of the FP64 inputs read (non-finite check)
 };
 
@@ -264,11 +283,12 @@ struct Gt {
   R aut, acc, scc, scr, evr, nuc, dep[3], mlt[3], rs, rg;
 };
 
-// Triple-moment rain: the shape parameter from (q, n, z) and the rain
-// constants at that shape (rain has b = 3, so the gamma-function ratios of
-// integer offset are products and two ratios of non-integer offset remain).
+// Triple-moment species (x = 0..3: r, i, s, g): the shape parameter from
+// (q, n, z) and the species constants at that shape (every species has b = 3,
+// so the gamma-function ratios of integer offset are products and the ratios
+// of non-integer offset are Gamma(x + s) / Gamma(x) evaluations).
 template <class M>
-struct Rain3 {
+struct Shape3 {
   using R = typename M::R;
   struct Sh {
     R lglamfac, lglo, lghi;   // as SpeciesK
@@ -276,19 +296,19 @@ struct Rain3 {
     R vq, vn, vz;             // mass-, number- and sixth-moment-weighted speed coefficients
   };
   static __device__ __forceinline__ R clampmu(const ConstK<R> &K, R mu) {
-    return mu < (R)0 ? (R)0 : (mu > K.r3_mumax ? K.r3_mumax : mu);
+    return mu < (R)0 ? (R)0 : (mu > K.s3_mumax ? K.s3_mumax : mu);
   }
   // G = z n / (q/a)^2 = P/Q, P = (mu+4)(mu+5)(mu+6), Q = (mu+1)(mu+2)(mu+3): start
   // from the root of G^(1/3) = (mu+5)/(mu+2), then four Newton steps on
   // f = ln(P/Q) - ln G_obs, whose slope P'/P - Q'/Q = (P'Q - Q'P)/(PQ) has
   // P'Q - Q'P = -3 (3 mu^4 + 42 mu^3 + 207 mu^2 + 420 mu + 292)
-  static __device__ __forceinline__ R mu(const ConstK<R> &K, R q, R n, R z) {
-    if (!(q > K.qmin) || !(n > (R)0) || !(z > (R)0)) return K.r3_mu0;
-    const R m3 = M::div(q, K.r3_a);
+  static __device__ __forceinline__ R mu(const ConstK<R> &K, int x, R q, R n, R z) {
+    if (!(q > K.qmin) || !(n > (R)0) || !(z > (R)0)) return K.s3_mu0[x];
+    const R m3 = M::div(q, K.s3_a[x]);
     const R gobs = M::div(M::div(z * n, m3), m3);
     const R lg = M::ln(gobs);
     const R g = M::cbrt(gobs);
-    R m = g > (R)1 ? clampmu(K, M::div((R)5 - (R)2 * g, g - (R)1)) : K.r3_mumax;
+    R m = g > (R)1 ? clampmu(K, M::div((R)5 - (R)2 * g, g - (R)1)) : K.s3_mumax;
     // FP64: four steps, as the definition; FP32: three (from this start the
     // third step leaves |ln G - ln G_obs| < 3e-8 for every shape in [0, 20],
     // below the FP32 rounding of ln G, so a fourth changes nothing)
@@ -303,21 +323,26 @@ struct Rain3 {
     }
     return m;
   }
-  static __device__ __forceinline__ void consts(const ConstK<R> &K, R mu, Sh &h) {
-    const R d = K.r3_dv;
+  static __device__ __forceinline__ void consts(const ConstK<R> &K, int x, R mu, Sh &h) {
+    const R d = K.s3_dv[x];
     const R p1 = mu + (R)1, p2 = mu + (R)2, p3 = mu + (R)3;
     const R q3 = p1 * p2 * p3;   // Gamma(mu+4) / Gamma(mu+1)
-    h.lglamfac = M::lg(K.r3_a * q3);
+    h.lglamfac = M::lg(K.s3_a[x] * q3);
     const R lp1 = M::lg(p1);
-    h.lglo = lp1 - K.r3_lgdmax;
-    h.lghi = lp1 - K.r3_lgdmin;
-    h.ev1 = M::div(K.r3_ev1c, p2 * p3);
+    h.lglo = lp1 - K.s3_lgdmax[x];
+    h.lghi = lp1 - K.s3_lgdmin[x];
+    h.ev1 = M::div(K.s3_ev1c[x], p2 * p3);
     const R rd = M::gratio(p1, d);                        // Gamma(mu+1+d)/Gamma(mu+1)
     const R rv = M::gratio(p1, (R)0.5 * (d + (R)3));      // Gamma(mu+(d+5)/2)/Gamma(mu+1)
-    h.ev2 = M::div(K.r3_ev2c * rv, q3);
-    h.vn = K.r3_cv * rd;
+    h.ev2 = M::div(K.s3_ev2c[x] * rv, q3);
+    h.vn = K.s3_cv[x] * rd;
     h.vq = M::div(h.vn * (p1 + d) * (p2 + d) * (p3 + d), q3);
     h.vz = M::div(h.vq * (mu + (R)4 + d) * (mu + (R)5 + d) * (mu + (R)6 + d), (mu + (R)4) * (mu + (R)5) * (mu + (R)6));
+  }
+  // riming coefficient (pi/4) E cv Gamma(mu+d+3) / Gamma(mu+4) / a
+  static __device__ __forceinline__ R rim(const ConstK<R> &K, int x, R mu) {
+    const R p1 = mu + (R)1;
+    return M::div(K.s3_rimc[x] * M::gratio(p1, K.s3_dv[x] + (R)2), p1 * (mu + (R)2) * (mu + (R)3));
   }
   static __device__ __forceinline__ R lglam(const Sh &h, const SpeciesK<R> &X, R lgq, R n) {
     const R lgn = M::lg(M::mx(n, (R)0));
@@ -325,12 +350,12 @@ struct Rain3 {
     l = M::mx(l, h.lglo);
     return M::mn(l, h.lghi);
   }
-  // rain fall speeds at shape mu (mass, number, sixth moment), capped
-  static __device__ __forceinline__ void fall_speeds(const ConstK<R> &K, R guard, R q, R lgq, R n, R z, R dfac,
-                                                     R &vq, R &vn, R &vz) {
-    const SpeciesK<R> &X = K.sp[1];
+  // fall speeds of species x at its diagnosed shape (mass, number, sixth moment), capped
+  static __device__ __forceinline__ void fall_speeds(const ConstK<R> &K, int x, R guard, R q, R lgq, R n, R z,
+                                                     R dfac, R &vq, R &vn, R &vz) {
+    const SpeciesK<R> &X = K.sp[1 + x];
     Sh h;
-    consts(K, mu(K, q, n, z), h);
+    consts(K, x, mu(K, x, q, n, z), h);
     const R l = lglam(h, X, lgq, n);
     const R pw = M::ex(X.exv * l);
     vq = M::mn(M::mn(h.vq * dfac * pw, X.vmax), guard);
@@ -426,9 +451,9 @@ struct Phys {
         const SpeciesK<R> &X = K.sp[1];
         R iv;
         if constexpr (M::kTri) {
-          typename Rain3<M>::Sh h;
-          Rain3<M>::consts(K, w.mu_r, h);
-          const R l = Rain3<M>::lglam(h, X, lgqr, nr);
+          typename Shape3<M>::Sh h;
+          Shape3<M>::consts(K, 0, w.mu3[0], h);
+          const R l = Shape3<M>::lglam(h, X, lgqr, nr);
           iv = rho * qr * (h.ev1 * M::ex(X.ex1 * l) + V0 * h.ev2 * M::ex(X.ex2 * l));
         } else {
           const R l = lglam(X, lgqr, nr);
@@ -453,10 +478,21 @@ struct Phys {
       for (int m = 0; m < 3; ++m) {
         if (!(w.qx[m] > K.qmin)) continue;
         const SpeciesK<R> &X = K.sp[2 + m];
-        const R l = lglam(X, M::lg(w.qx[m]), w.nx[m]);
-        const R iv = rho * w.qx[m] * (X.ev1 * M::ex(X.ex1 * l) + V0 * X.ev2 * M::ex(X.ex2 * l));
-        r.dep[m] = X.dep * dfa * iv;
-        if (m > 0 && hc) r.rim[m - 1] = X.rim * qc * dfac * rho * w.qx[m] * M::ex(X.exr * l);
+        if constexpr (M::kTri) {
+          // at the species' diagnosed shape
+          typename Shape3<M>::Sh h;
+          Shape3<M>::consts(K, 1 + m, w.mu3[1 + m], h);
+          const R l = Shape3<M>::lglam(h, X, M::lg(w.qx[m]), w.nx[m]);
+          const R iv = rho * w.qx[m] * (h.ev1 * M::ex(X.ex1 * l) + V0 * h.ev2 * M::ex(X.ex2 * l));
+          r.dep[m] = X.dep * dfa * iv;
+          if (m > 0 && hc)
+            r.rim[m - 1] = Shape3<M>::rim(K, 1 + m, w.mu3[1 + m]) * qc * dfac * rho * w.qx[m] * M::ex(X.exr * l);
+        } else {
+          const R l = lglam(X, M::lg(w.qx[m]), w.nx[m]);
+          const R iv = rho * w.qx[m] * (X.ev1 * M::ex(X.ex1 * l) + V0 * X.ev2 * M::ex(X.ex2 * l));
+          r.dep[m] = X.dep * dfa * iv;
+          if (m > 0 && hc) r.rim[m - 1] = X.rim * qc * dfac * rho * w.qx[m] * M::ex(X.exr * l);
+        }
       }
     }
     if (!M::kWarm && warm) {
@@ -464,8 +500,16 @@ struct Phys {
       for (int m = 0; m < 3; ++m) {
         if (!(w.qx[m] > K.qmin)) continue;
         const SpeciesK<R> &X = K.sp[2 + m];
-        const R l = lglam(X, M::lg(w.qx[m]), w.nx[m]);
-        const R iv = rho * w.qx[m] * (X.ev1 * M::ex(X.ex1 * l) + V0 * X.ev2 * M::ex(X.ex2 * l));
+        R iv;
+        if constexpr (M::kTri) {
+          typename Shape3<M>::Sh h;
+          Shape3<M>::consts(K, 1 + m, w.mu3[1 + m], h);
+          const R l = Shape3<M>::lglam(h, X, M::lg(w.qx[m]), w.nx[m]);
+          iv = rho * w.qx[m] * (h.ev1 * M::ex(X.ex1 * l) + V0 * h.ev2 * M::ex(X.ex2 * l));
+        } else {
+          const R l = lglam(X, M::lg(w.qx[m]), w.nx[m]);
+          iv = rho * w.qx[m] * (X.ev1 * M::ex(X.ex1 * l) + V0 * X.ev2 * M::ex(X.ex2 * l));
+        }
         r.mlt[m] = M::div(X.mlt * tc * iv, rho);
       }
     }
@@ -605,12 +649,20 @@ struct F64T {
     activate(K, s);
     const double dn_act = na1 - s.na;
     const double qc_post = s.qc, qr_post = s.qr, nr_post = s.nr;
+    const double qx0[3] = {s.qi, s.qs, s.qg}, nx0[3] = {s.ni, s.ns, s.ng};
     double tau_cr = 0.0, tau_rv = 0.0, tau_aut = 0.0, nr_aut = 0.0;
+    double nuc_q = 0.0, nuc_n = 0.0, melt_q[3] = {0.0, 0.0, 0.0}, melt_n[3] = {0.0, 0.0, 0.0};
     W<double> w;
     w.Td = s.T; w.T = s.T; w.tc = s.T - K.T0; w.p = s.p; w.rho = s.rho;
     w.qv = s.qv; w.qc = s.qc; w.qr = s.qr; w.qx[0] = s.qi; w.qx[1] = s.qs; w.qx[2] = s.qg;
     w.nc = s.nc; w.nr = s.nr; w.nx[0] = s.ni; w.nx[1] = s.ns; w.nx[2] = s.ng;
-    if constexpr (M::kTri) w.mu_r = Rain3<M>::mu(K, s.qr, s.nr, s.zr);
+    if constexpr (M::kTri) {
+#pragma unroll
+      for (int x = 0; x < nz3<M>(); ++x) {
+        const double q = x == 0 ? s.qr : qx0[x - 1], n = x == 0 ? s.nr : nx0[x - 1];
+        w.mu3[x] = Shape3<M>::mu(K, x, q, n, zref(s, x));
+      }
+    }
     Rt<double> r;
     P::rates(K, w, dt, r);
     Gt<double> g;
@@ -627,8 +679,8 @@ struct F64T {
     if (r.scr > 0) s.nr -= g.scr * r.scr * dt;
     if (r.evr > 0) { tau = g.evr * r.evr * dt; s.qr -= tau; s.qv += tau; s.T += tau * (-K.lv) / K.cp; tau_rv = tau; }
     if (r.evr * g.rr > 0) s.nr -= g.evr * (r.evr * g.rr) * dt;
-    if (g.nucm > 0) { tau = g.nuc * g.nucm * dt; s.qv -= tau; qxd[0] += tau; s.T += tau * K.ls / K.cp; }
-    if (r.nucn > 0) nxd[0] += g.nuc * r.nucn * dt;
+    if (g.nucm > 0) { tau = g.nuc * g.nucm * dt; s.qv -= tau; qxd[0] += tau; s.T += tau * K.ls / K.cp; nuc_q = tau; }
+    if (r.nucn > 0) { nuc_n = g.nuc * r.nucn * dt; nxd[0] += nuc_n; }
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       if (r.dep[m] >= 0) {
@@ -644,19 +696,39 @@ struct F64T {
     if (r.rim[1] * g.rc > 0) s.nc -= g.rg * (r.rim[1] * g.rc) * dt;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      if (r.mlt[m] > 0) { tau = g.mlt[m] * r.mlt[m] * dt; qxd[m] -= tau; s.qr += tau; s.T += tau * (-K.lf) / K.cp; }
-      if (g.nmlt[m] > 0) { nxd[m] -= g.mlt[m] * g.nmlt[m] * dt; s.nr += g.mlt[m] * g.nmlt[m] * dt; }
+      if (r.mlt[m] > 0) {
+        tau = g.mlt[m] * r.mlt[m] * dt; qxd[m] -= tau; s.qr += tau; s.T += tau * (-K.lf) / K.cp; melt_q[m] = tau;
+      }
+      if (g.nmlt[m] > 0) {
+        melt_n[m] = g.mlt[m] * g.nmlt[m] * dt; nxd[m] -= melt_n[m]; s.nr += melt_n[m];
+      }
     }
     s.qi = qxd[0]; s.qs = qxd[1]; s.qg = qxd[2];
     s.ni = nxd[0]; s.ns = nxd[1]; s.ng = nxd[2];
     if constexpr (M::kTri) {
-      // the rain's sixth moment: accretion, self-collection and evaporation
-      // at the diagnosed shape, autoconversion as drops of one size
-      const double q1 = s.qr - tau_aut, n1 = s.nr - nr_aut;
-      double z = 0.0;
-      if (qr_post > K.qmin && nr_post > 0.0 && q1 > 0.0 && n1 > 0.0)
-        z = s.zr * (q1 / qr_post) * (q1 / qr_post) * (nr_post / n1);
-      s.zr = z + nr_aut * K.r3_d0_6;
+      // sixth moments: the processes that keep a species' shape scale z by
+      // (q'/q)^2 (n/n'), q', n' the result without the sources; sources add
+      // what they bring (autoconversion: drops of one size; melting of i, s,
+      // g: the melted fraction of their sixth moment, in rain diameters;
+      // nucleation: crystals of one size)
+      auto kept = [&](double z0, double q0, double n0, double q1, double n1) {
+        return (q0 > K.qmin && n0 > 0.0 && q1 > 0.0 && n1 > 0.0) ? z0 * (q1 / q0) * (q1 / q0) * (n0 / n1) : 0.0;
+      };
+      double q1 = s.qr - tau_aut, n1 = s.nr - nr_aut, zsrc = 0.0;
+      if constexpr (!M::kWarm) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          q1 -= melt_q[m];
+          n1 -= melt_n[m];
+          if (melt_q[m] > 0.0 && qx0[m] > K.qmin) zsrc += K.s3_ar2[1 + m] * (melt_q[m] / qx0[m]) * zref(s, 1 + m);
+        }
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          const double qm = qxd[m] - (m == 0 ? nuc_q : 0.0), nm = nxd[m] - (m == 0 ? nuc_n : 0.0);
+          zref(s, 1 + m) = kept(zref(s, 1 + m), qx0[m], nx0[m], qm, nm) + (m == 0 ? nuc_n * K.s3_di_6 : 0.0);
+        }
+      }
+      s.zr = kept(s.zr, qr_post, nr_post, q1, n1) + nr_aut * K.s3_d0_6 + zsrc;
     }
     if constexpr (M::kAero) {
       // aerosol mass moves with the water (in the order: adjustment,
@@ -730,6 +802,8 @@ struct MixInc {
   float a_ev, a_act, a_cr, a_rv;
   bool a_ev_all, a_cr_all, a_rv_all;
   float r_aut, n_aut;   // triple-moment policies: rain mass and drops made by autoconversion
+  float q_nuc, n_nuc;   // cold triple-moment policies: ice mass and crystals made by nucleation
+  float n_melt[3];      // and particles of i, s, g melted into rain
 };
 
 template <class M>
@@ -800,7 +874,13 @@ struct MixT {
     o.evap_all = false;
     o.dT = 0.f;
     const float qc0 = w.qc;
-    if constexpr (M::kTri) w.mu_r = Rain3<M>::mu(K, w.qr, w.nr, d2f(s.zr));
+    if constexpr (M::kTri) {
+      w.mu3[0] = Shape3<M>::mu(K, 0, w.qr, w.nr, d2f(s.zr));
+      if constexpr (!M::kWarm) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) w.mu3[1 + m] = Shape3<M>::mu(K, 1 + m, w.qx[m], w.nx[m], d2f(zval(s, 1 + m)));
+      }
+    }
     if constexpr (M::kAero) {
       o.a_ev = o.a_act = o.a_cr = o.a_rv = 0.f;
       o.a_ev_all = o.a_cr_all = o.a_rv_all = false;
@@ -891,6 +971,12 @@ struct MixT {
     if constexpr (M::kTri) {
       o.r_aut = g.aut * r.aut * dtr;
       o.n_aut = g.aut * r.aut * K.inv_mr0 * dtr;
+      if constexpr (!M::kWarm) {
+        o.q_nuc = g.nuc * g.nucm * dtr;
+        o.n_nuc = g.nuc * r.nucn * dtr;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) o.n_melt[m] = g.mlt[m] * g.nmlt[m] * dtr;
+      }
     }
     if constexpr (M::kAero) {
       if (o.cr > 0.f && w.qc > 0.f) {
@@ -954,14 +1040,34 @@ struct MixT {
     if constexpr (M::kAero) apply_aero(s, o);
   }
 
-  // the rain's sixth moment after the processes (q0, n0: the rain they saw):
-  // accretion, self-collection and evaporation at the diagnosed shape,
-  // autoconversion as drops of one size
-  static __device__ __forceinline__ void apply_z(const ConstK<float> &K, Pt &s, float q0, float n0, const MixInc &o) {
-    const float q1 = q0 + o.cr - o.r_aut - o.rv, n1 = n0 + o.dn[1] - o.n_aut;
-    float f = 0.f;
-    if (q0 > K.qmin && n0 > 0.f && q1 > 0.f && n1 > 0.f) f = __fdividef(q1, q0) * __fdividef(q1, q0) * __fdividef(n0, n1);
-    s.zr = s.zr * f2d(f) + f2d(o.n_aut * K.r3_d0_6);
+  // the sixth moments after the processes (w: the point the rates saw):
+  // processes that keep a species' shape scale z by (q'/q)^2 (n/n'), q', n'
+  // without the sources; sources add what they bring (autoconversion: drops
+  // of one size; melting of i, s, g: the melted fraction of their sixth
+  // moment, in rain diameters; nucleation: crystals of one size)
+  static __device__ __forceinline__ float kept(const ConstK<float> &K, float q0, float n0, float q1, float n1) {
+    return (q0 > K.qmin && n0 > 0.f && q1 > 0.f && n1 > 0.f)
+               ? __fdividef(q1, q0) * __fdividef(q1, q0) * __fdividef(n0, n1) : 0.f;
+  }
+  static __device__ __forceinline__ void apply_z(const ConstK<float> &K, Pt &s, const W<float> &w, const MixInc &o) {
+    const float q1 = w.qr + o.cr - o.r_aut - o.rv;
+    float n1 = w.nr + o.dn[1] - o.n_aut, src = o.n_aut * K.s3_d0_6;
+    if constexpr (!M::kWarm) {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        n1 -= o.n_melt[m];
+        if (o.xr[m] > 0.f && w.qx[m] > K.qmin)
+          src += K.s3_ar2[1 + m] * __fdividef(o.xr[m], w.qx[m]) * d2f(zref(s, 1 + m));
+      }
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const float qm = w.qx[m] + o.vx[m] - o.xr[m] + (m == 2 ? o.cg : 0.f) - (m == 0 ? o.q_nuc : 0.f);
+        const float nm = w.nx[m] + o.dn[2 + m] - (m == 0 ? o.n_nuc : 0.f);
+        double &z = zref(s, 1 + m);
+        z = z * f2d(kept(K, w.qx[m], w.nx[m], qm, nm)) + (m == 0 ? f2d(o.n_nuc * K.s3_di_6) : 0.0);
+      }
+    }
+    s.zr = s.zr * f2d(kept(K, w.qr, w.nr, q1, n1)) + f2d(src);
   }
 
   // aerosol masses: each amount is one FP32 product of the source's mass and
@@ -1017,6 +1123,15 @@ struct PolicyF64Warm3 : PolicyF64Warm {
 struct PolicyMixWarm3 : PolicyMixWarm {
   static constexpr bool kTri = true;
 };
+// The cold configuration with triple-moment r, i, s, g: fields 16..19 are
+// their sixth moments.
+struct PolicyF643 : PolicyF64 {
+  static constexpr bool kTri = true;
+};
+struct PolicyMix3 : PolicyMix {
+  static constexpr bool kTri = true;
+  static constexpr int kMinBlocks = 4;
+};
 
 // ---------------------------------------------------------------- kernels
 template <bool kWarm = false, bool kAero = false, bool kTri = false>
@@ -1040,7 +1155,12 @@ __device__ __forceinline__ void load_pt(const KArgs &a, int k, int c, Pt &s) {
   if constexpr (kAero) {
     s.ma = b[16 * fs]; s.mac = b[17 * fs]; s.mar = b[18 * fs];
   }
-  if constexpr (kTri) s.zr = b[16 * fs];
+  if constexpr (kTri) {
+    s.zr = b[16 * fs];
+    if constexpr (!kWarm) {
+      s.zi = b[17 * fs]; s.zs = b[18 * fs]; s.zg = b[19 * fs];
+    }
+  }
 }
 
 // any loaded value non-finite (integer pipe: max of the exponent fields)
@@ -1161,10 +1281,12 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
   const double *rhop = a.fld + 14 * fs;
   double *state = kTend ? tend : a.fld;   // the processed state (tendency mode: scratch)
   constexpr int kSed = M::kWarm ? 1 : 4;   // sedimenting species: r (warm) or r, i, s, g
-  double *zp = a.fld + 16 * fs;   // the rain's sixth moment (triple-moment policies)
   for (int x = 0; x < kSed; ++x) {
     double *qp = state + (3 + x) * fs;
     double *np = state + (8 + x) * fs;
+    // the species' sixth moment (triple-moment policies: rain, or r, i, s, g)
+    const bool tri = x < nz3<M>();
+    double *zp = a.fld + (16 + x) * fs;
     R cmax = 0;
     for (int k = 0; k < a.nlev; ++k) {
       const size_t o = (size_t)k * a.pitch + c;
@@ -1173,9 +1295,9 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
       const R rho = M::toR(__ldg(rhop + o));
       const R dfac = M::ex((R)0.4 * (K.lgrho0 - M::lg(rho)));
       R vq, vn;
-      if (M::kTri && x == 0) {
+      if (tri) {
         R vz;
-        Rain3<M>::fall_speeds(K, (R)1e30, q, M::lg(q), M::toR(np[o]), M::toR(zp[o]), dfac, vq, vn, vz);
+        Shape3<M>::fall_speeds(K, x, (R)1e30, q, M::lg(q), M::toR(np[o]), M::toR(zp[o]), dfac, vq, vn, vz);
       } else {
         Ph::fall_speeds(K, (R)1e30, M::lg(q), M::toR(np[o]), dfac, x, vq, vn);
       }
@@ -1188,7 +1310,6 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
     // the rain's aerosol mass moves with the rain (aerosol-mass policies)
     const bool aer = M::kAero && x == 0;
     double *ap = a.fld + 18 * fs;
-    const bool tri = M::kTri && x == 0;
     for (int st = 0; st < ns; ++st) {
       R Fu = 0, Gu = 0, Au = 0, Hu = 0;
       for (int k = a.nlev - 1; k >= 0; --k) {
@@ -1204,7 +1325,7 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
           const R dfac = M::ex((R)0.4 * (K.lgrho0 - M::lg(rho)));
           R vq, vn, vz = 0;
           if (tri) {
-            Rain3<M>::fall_speeds(K, M::toR(sdz[k] / dts), qR, M::lg(qR), M::toR(n), M::toR(zm), dfac, vq, vn, vz);
+            Shape3<M>::fall_speeds(K, x, M::toR(sdz[k] / dts), qR, M::lg(qR), M::toR(n), M::toR(zm), dfac, vq, vn, vz);
           } else {
             Ph::fall_speeds(K, M::toR(sdz[k] / dts), M::lg(qR), M::toR(n), dfac, x, vq, vn);
           }
@@ -1281,7 +1402,8 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
   // carried downward fluxes F_{k+1}, G_{k+1} (kg m^-2 s^-1, m^-2 s^-1), and
   // the rain's aerosol-mass flux (aerosol-mass policies)
   R Fq[4] = {0, 0, 0, 0}, Fn[4] = {0, 0, 0, 0};
-  R Fa = 0, Fz = 0;   // rain aerosol mass, rain sixth moment
+  R Fa = 0;                     // rain aerosol mass
+  R Fz[4] = {0, 0, 0, 0};       // sixth moments of r, i, s, g (triple-moment policies)
 
   for (int k = a.nlev - 1; k >= 0; --k) {
     Pt s;
@@ -1302,10 +1424,11 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
           double F = 0, G = 0, A = 0, H = 0;
           if (q > K.qmin) {
             double vq, vn;
-            if (M::kTri && x == 0) {
+            if (x < nz3<M>()) {
               double vz;
-              Rain3<M>::fall_speeds(K, sdzdt[k], q, ::log(q), n, s.zr, dfac, vq, vn, vz);
-              H = s.rho * (s.zr > 0.0 ? s.zr : 0.0) * vz;
+              const double z = zref(s, x);
+              Shape3<M>::fall_speeds(K, x, sdzdt[k], q, ::log(q), n, z, dfac, vq, vn, vz);
+              H = s.rho * (z > 0.0 ? z : 0.0) * vz;
             } else {
               Ph::fall_speeds(K, sdzdt[k], ::log(q), n, dfac, x, vq, vn);
             }
@@ -1313,14 +1436,12 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
             G = s.rho * (n > 0.0 ? n : 0.0) * vn;
             if (M::kAero && x == 0) A = s.rho * s.mar * vq;
           }
-          if constexpr (M::kTri) {
-            if (x == 0) {
-              if (H != 0.0 || Fz != 0.0) {
-                s.zr += a.dt * (Fz - H) / (s.rho * dzk);
-                touched = true;
-              }
-              Fz = H;
+          if (x < nz3<M>()) {
+            if (H != 0.0 || Fz[x] != 0.0) {
+              zref(s, x) += a.dt * (Fz[x] - H) / (s.rho * dzk);
+              touched = true;
             }
+            Fz[x] = H;
           }
           if (F != 0.0 || Fq[x] != 0.0 || G != 0.0 || Fn[x] != 0.0) {
             q += a.dt * (Fq[x] - F) / (s.rho * dzk);
@@ -1351,7 +1472,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       if (act) {
         MixT<M>::process(K, s, a.dt, w, es0, qs0, o, a.surr ? a.surr + (size_t)k * a.pitch + c : nullptr);
         MixT<M>::apply_masses(s, o, macc);
-        if constexpr (M::kTri) MixT<M>::apply_z(K, s, w.qr, w.nr, o);
+        if constexpr (M::kTri) MixT<M>::apply_z(K, s, w, o);
         if (o.dn[0] != 0.f) s.nc += f2d(o.dn[0]);
 #pragma unroll
         for (int x = 0; x < 4; ++x) dn[x] = o.dn[1 + x];
@@ -1388,10 +1509,10 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
             if (qpost[x] > K.qmin) {
               const float n = act ? npost[x] : d2f(nref(s, x));
               float vq, vn;
-              if (M::kTri && x == 0) {
+              if (x < nz3<M>()) {
                 float vz;
-                const float zp = d2f(s.zr);
-                Rain3<M>::fall_speeds(K, guard, qpost[x], lg2a(qpost[x]), n, zp, dfac, vq, vn, vz);
+                const float zp = d2f(zref(s, x));
+                Shape3<M>::fall_speeds(K, x, guard, qpost[x], lg2a(qpost[x]), n, zp, dfac, vq, vn, vz);
                 H = rho * fmaxf(zp, 0.f) * vz;
               } else {
                 Ph::fall_speeds(K, guard, lg2a(qpost[x]), n, dfac, x, vq, vn);
@@ -1400,14 +1521,12 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
               G = rho * fmaxf(n, 0.f) * vn;
               if (M::kAero && x == 0) A = rho * d2f(s.mar) * vq;
             }
-            if constexpr (M::kTri) {
-              if (x == 0) {
-                if (H != 0.f || Fz != 0.f) {
-                  s.zr += f2d((Fz - H) * sc);
-                  touched = true;
-                }
-                Fz = H;
+            if (x < nz3<M>()) {
+              if (H != 0.f || Fz[x] != 0.f) {
+                zref(s, x) += f2d((Fz[x] - H) * sc);
+                touched = true;
               }
+              Fz[x] = H;
             }
             if constexpr (M::kAero) {
               if (x == 0) {
@@ -1442,7 +1561,19 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
     } else if constexpr (M::kWarm) {
       if (touched) eflag |= store_pt_warm<M::kAero, M::kTri>(a, k, c, s);
     } else {
-      if (touched) eflag |= store_pt(a, k, c, s);
+      if (touched) {
+        eflag |= store_pt(a, k, c, s);
+        if constexpr (M::kTri) {
+          // the sixth moments of r, i, s, g
+          double *b = a.fld + (size_t)k * a.pitch + c;
+          const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            b[(16 + x) * fs] = zval(s, x);
+            eflag |= nonfinite(zval(s, x));
+          }
+        }
+      }
     }
   }
   if (fast) {

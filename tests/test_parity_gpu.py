@@ -661,9 +661,16 @@ def test_three_moment_mixed_within_derived_bound():
 
 def test_three_moment_context_rules():
     import torch
-    for flags in (casim.CASIM_THREE_MOMENT, casim.CASIM_WARM | casim.CASIM_THREE_MOMENT | casim.CASIM_AEROSOL):
+    for flags in (casim.CASIM_THREE_MOMENT | casim.CASIM_AEROSOL,
+                  casim.CASIM_WARM | casim.CASIM_THREE_MOMENT | casim.CASIM_AEROSOL):
         with pytest.raises(RuntimeError):
             casim.casim_init(precision=casim.CASIM_MIXED, flags=flags)
+    p = casim.casim_default_params()
+    p.b[3] = 2.9                                        # snow: carries z only in the cold configuration
+    casim.casim_free(casim.casim_init(params=p, precision=casim.CASIM_MIXED,
+                                      flags=casim.CASIM_WARM | casim.CASIM_THREE_MOMENT))
+    with pytest.raises(RuntimeError):
+        casim.casim_init(params=p, precision=casim.CASIM_MIXED, flags=casim.CASIM_THREE_MOMENT)
     p = casim.casim_default_params()
     p.b[1] = 2.9
     with pytest.raises(RuntimeError):                   # the shape algebra needs b = 3
@@ -685,8 +692,77 @@ def test_three_moment_context_rules():
         casim.casim_free(ctx)
 
 
+# ---------------------------------------------- triple-moment r, i, s, g (cold configuration)
+ZC = {"r": 16, "i": 17, "s": 18, "g": 19}
+QF = {"r": F["qr"], "i": F["qi"], "s": F["qs"], "g": F["qg"]}
+NF = {"r": F["nr"], "i": F["ni"], "s": F["ns"], "g": F["ng"]}
+
+
+def _tri_cold_state(ncols, nlev, seed):
+    """Deep-convective state with each species' sixth moment of a gamma
+    distribution of shape uniform in [0, 8]."""
+    dz = synth.dz_stretched(nlev)
+    base = synth.make_state("deep_convective", ncols, nlev, dz, seed=seed)
+    fld = np.zeros((20,) + base.shape[1:])
+    fld[:16] = base
+    rng = np.random.default_rng(seed)
+    for sp in "risg":
+        q, n = base[QF[sp]], base[NF[sp]]
+        shape = rng.uniform(0.0, 8.0, q.shape)
+        ok = (q > 1e-14) & (n > 0)
+        fld[ZC[sp]][ok] = _gamma_g(shape[ok]) * (q[ok] / O.param(f"a_{sp}")) ** 2 / n[ok]
+    return np.ascontiguousarray(fld), dz
+
+
+def _run_oracle_3m_cold(fld, dz, ncols, dt, nsteps):
+    ref = fld.copy()
+    pref = np.zeros((4, fld.shape[2]))
+    for _ in range(nsteps):
+        _, err = O.step_3m_cold(ref, ncols, dz, dt, precip=pref)
+        assert err == 0
+    return ref, pref
+
+
+@pytest.mark.parametrize("dt", [1.0, 30.0])
+def test_three_moment_cold_fp64_matches_oracle(dt):
+    """FP64 form, triple-moment r, i, s, g: the 13 prognostic fields, the four
+    sixth moments and the precipitation within 1e-11 of the oracle (each z
+    with an absolute floor of 1e-16 of the domain's largest z of the species)."""
+    ncols, nlev = 97, 150
+    nsteps = 3 if dt == 1.0 else 1
+    fld, dz = _tri_cold_state(ncols, nlev, seed=65)
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, nsteps=nsteps, flags=casim.CASIM_THREE_MOMENT)
+    ref, pref = _run_oracle_3m_cold(fld, dz, ncols, dt, nsteps)
+    assert_fp64_close(out, pr, ref, pref, ncols, rtol=1e-11)
+    for sp, f in ZC.items():
+        a, b = out[f, :, :ncols], ref[f, :, :ncols]
+        floor = 1e-16 * fld[f].max()
+        assert (np.abs(a - b) <= 1e-11 * np.abs(b) + floor).all(), (sp, float(np.abs(a - b).max()))
+        assert not np.array_equal(out[f], fld[f]), sp
+
+
+def test_three_moment_cold_mixed_within_derived_bound():
+    """Mixed form, triple-moment r, i, s, g: the 13 fields within the mixed
+    bound; each z within 1e-3 |its change| + 1e-4 |z| (the derivation of the
+    rain case holds for every species: FP32 shapes, FP32 log-gamma-free
+    coefficients, FP32 process factors and sources)."""
+    ncols, nlev = 512, 150
+    fld, dz = _tri_cold_state(ncols, nlev, seed=66)
+    out, pr, _ = run_gpu(fld, dz, ncols, 1.0, precision=casim.CASIM_MIXED, flags=casim.CASIM_THREE_MOMENT)
+    ref, pref = _run_oracle_3m_cold(fld, dz, ncols, 1.0, 1)
+    for f in range(13):
+        a, b, i = out[f, :, :ncols], ref[f, :, :ncols], fld[f, :, :ncols]
+        bound = mixed_bound(b, i, f, ref[1, :, :ncols])
+        assert (np.abs(a - b) <= bound).all(), (synth.FIELDS[f], float((np.abs(a - b) / bound).max()))
+    for sp, f in ZC.items():
+        a, b, i = out[f, :, :ncols], ref[f, :, :ncols], fld[f, :, :ncols]
+        bound = 1e-3 * np.abs(b - i) + 1e-4 * np.abs(b) + 1e-16 * fld[f].max()
+        assert (np.abs(a - b) <= bound).all(), (sp, float((np.abs(a - b) / bound).max()))
+        assert (a >= 0).all(), sp
+
+
 # ------------------------------------------------------------------ checkpoint / resume
-@pytest.mark.parametrize("state", ["standard", "aerosol", "three_moment"])
+@pytest.mark.parametrize("state", ["standard", "aerosol", "three_moment", "three_moment_cold"])
 def test_checkpoint_resume_is_bitwise(tmp_path, state):
     """N steps equal k steps, save, load into fresh device memory, N - k steps,
     bit for bit; a checkpoint of other sizes or parameters is refused."""
@@ -697,6 +773,9 @@ def test_checkpoint_resume_is_bitwise(tmp_path, state):
     elif state == "three_moment":
         fld, dz = _tri_state(ncols, nlev, seed=71)
         flags, nf = casim.CASIM_WARM | casim.CASIM_THREE_MOMENT, 17
+    elif state == "three_moment_cold":
+        fld, dz = _tri_cold_state(ncols, nlev, seed=71)
+        flags, nf = casim.CASIM_THREE_MOMENT, 20
     else:
         dz = synth.dz_stretched(nlev)
         fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=71)
