@@ -353,9 +353,14 @@ struct Shape3 {
   // fall speeds of species x at its diagnosed shape (mass, number, sixth moment), capped
   static __device__ __forceinline__ void fall_speeds(const ConstK<R> &K, int x, R guard, R q, R lgq, R n, R z,
                                                      R dfac, R &vq, R &vn, R &vz) {
+    fall_speeds_mu(K, x, guard, lgq, n, mu(K, x, q, n, z), dfac, vq, vn, vz);
+  }
+  // the same at a known shape
+  static __device__ __forceinline__ void fall_speeds_mu(const ConstK<R> &K, int x, R guard, R lgq, R n, R mu,
+                                                        R dfac, R &vq, R &vn, R &vz) {
     const SpeciesK<R> &X = K.sp[1 + x];
     Sh h;
-    consts(K, x, mu(K, x, q, n, z), h);
+    consts(K, x, mu, h);
     const R l = lglam(h, X, lgq, n);
     const R pw = M::ex(X.exv * l);
     vq = M::mn(M::mn(h.vq * dfac * pw, X.vmax), guard);
@@ -641,7 +646,11 @@ struct F64T {
   }
 
   // a2..a10 on one active point; transfers applied one by one in list order
-  static __device__ __forceinline__ void process(const ConstK<double> &K, Pt &s, double dt, double es0, double qs0) {
+  // mu3, keep3 (triple-moment policies): the shapes the rates used, and a bit
+  // per species whose sixth moment was only rescaled (no source), so that its
+  // shape is unchanged by the processes
+  static __device__ __forceinline__ void process(const ConstK<double> &K, Pt &s, double dt, double es0, double qs0,
+                                                 double *mu3 = nullptr, unsigned *keep3 = nullptr) {
     const double qc0 = s.qc;
     satadj(K, s, es0, qs0);
     const double evap = qc0 > s.qc ? qc0 - s.qc : 0.0;
@@ -711,24 +720,37 @@ struct F64T {
       // what they bring (autoconversion: drops of one size; melting of i, s,
       // g: the melted fraction of their sixth moment, in rain diameters;
       // nucleation: crystals of one size)
+      unsigned keep = 0;
       auto kept = [&](double z0, double q0, double n0, double q1, double n1) {
         return (q0 > K.qmin && n0 > 0.0 && q1 > 0.0 && n1 > 0.0) ? z0 * (q1 / q0) * (q1 / q0) * (n0 / n1) : 0.0;
       };
+      auto scaled = [&](double q0, double n0, double q1, double n1) {
+        return q0 > K.qmin && n0 > 0.0 && q1 > 0.0 && n1 > 0.0;
+      };
       double q1 = s.qr - tau_aut, n1 = s.nr - nr_aut, zsrc = 0.0;
+      bool rsrc = nr_aut > 0.0 || tau_aut > 0.0;
       if constexpr (!M::kWarm) {
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
           q1 -= melt_q[m];
           n1 -= melt_n[m];
+          rsrc = rsrc || melt_q[m] > 0.0 || melt_n[m] > 0.0;
           if (melt_q[m] > 0.0 && qx0[m] > K.qmin) zsrc += K.s3_ar2[1 + m] * (melt_q[m] / qx0[m]) * zref(s, 1 + m);
         }
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
           const double qm = qxd[m] - (m == 0 ? nuc_q : 0.0), nm = nxd[m] - (m == 0 ? nuc_n : 0.0);
+          if (scaled(qx0[m], nx0[m], qm, nm) && !(m == 0 && (nuc_q > 0.0 || nuc_n > 0.0))) keep |= 2u << m;
           zref(s, 1 + m) = kept(zref(s, 1 + m), qx0[m], nx0[m], qm, nm) + (m == 0 ? nuc_n * K.s3_di_6 : 0.0);
         }
       }
+      if (scaled(qr_post, nr_post, q1, n1) && !rsrc) keep |= 1u;
       s.zr = kept(s.zr, qr_post, nr_post, q1, n1) + nr_aut * K.s3_d0_6 + zsrc;
+      if (keep3) *keep3 = keep;
+      if (mu3) {
+#pragma unroll
+        for (int x = 0; x < nz3<M>(); ++x) mu3[x] = w.mu3[x];
+      }
     }
     if constexpr (M::kAero) {
       // aerosol mass moves with the water (in the order: adjustment,
@@ -1049,13 +1071,22 @@ struct MixT {
     return (q0 > K.qmin && n0 > 0.f && q1 > 0.f && n1 > 0.f)
                ? __fdividef(q1, q0) * __fdividef(q1, q0) * __fdividef(n0, n1) : 0.f;
   }
-  static __device__ __forceinline__ void apply_z(const ConstK<float> &K, Pt &s, const W<float> &w, const MixInc &o) {
+  // returns a bit per species whose z was only rescaled (no source): its
+  // shape is unchanged by the processes
+  static __device__ __forceinline__ unsigned apply_z(const ConstK<float> &K, Pt &s, const W<float> &w,
+                                                     const MixInc &o) {
+    auto scaled = [&](float q0, float n0, float q1, float n1) {
+      return q0 > K.qmin && n0 > 0.f && q1 > 0.f && n1 > 0.f;
+    };
+    unsigned keep = 0;
     const float q1 = w.qr + o.cr - o.r_aut - o.rv;
     float n1 = w.nr + o.dn[1] - o.n_aut, src = o.n_aut * K.s3_d0_6;
+    bool rsrc = o.r_aut > 0.f || o.n_aut > 0.f;
     if constexpr (!M::kWarm) {
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         n1 -= o.n_melt[m];
+        rsrc = rsrc || o.xr[m] > 0.f || o.n_melt[m] > 0.f;
         if (o.xr[m] > 0.f && w.qx[m] > K.qmin)
           src += K.s3_ar2[1 + m] * __fdividef(o.xr[m], w.qx[m]) * d2f(zref(s, 1 + m));
       }
@@ -1063,11 +1094,14 @@ struct MixT {
       for (int m = 0; m < 3; ++m) {
         const float qm = w.qx[m] + o.vx[m] - o.xr[m] + (m == 2 ? o.cg : 0.f) - (m == 0 ? o.q_nuc : 0.f);
         const float nm = w.nx[m] + o.dn[2 + m] - (m == 0 ? o.n_nuc : 0.f);
+        if (scaled(w.qx[m], w.nx[m], qm, nm) && !(m == 0 && (o.q_nuc > 0.f || o.n_nuc > 0.f))) keep |= 2u << m;
         double &z = zref(s, 1 + m);
         z = z * f2d(kept(K, w.qx[m], w.nx[m], qm, nm)) + (m == 0 ? f2d(o.n_nuc * K.s3_di_6) : 0.0);
       }
     }
+    if (scaled(w.qr, w.nr, q1, n1) && !rsrc) keep |= 1u;
     s.zr = s.zr * f2d(kept(K, w.qr, w.nr, q1, n1)) + f2d(src);
+    return keep;
   }
 
   // aerosol masses: each amount is one FP32 product of the source's mass and
@@ -1413,7 +1447,9 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       eflag |= nonfinite_in(s);
       double es0, qs0;
       touched = F64T<M>::active(K, s, es0, qs0);
-      if (touched) F64T<M>::process(K, s, a.dt, es0, qs0);
+      double mu3[4];
+      unsigned keep3 = 0;   // species whose shape the processes left unchanged (triple-moment policies)
+      if (touched) F64T<M>::process(K, s, a.dt, es0, qs0, mu3, &keep3);
       if (fast) {
         const double dzk = sdz[k];
         const double dfac = ::exp(0.4 * (K.lgrho0 - ::log(s.rho)));
@@ -1427,7 +1463,8 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
             if (x < nz3<M>()) {
               double vz;
               const double z = zref(s, x);
-              Shape3<M>::fall_speeds(K, x, sdzdt[k], q, ::log(q), n, z, dfac, vq, vn, vz);
+              const double mus = ((keep3 >> x) & 1u) ? mu3[x] : Shape3<M>::mu(K, x, q, n, z);
+              Shape3<M>::fall_speeds_mu(K, x, sdzdt[k], ::log(q), n, mus, dfac, vq, vn, vz);
               H = s.rho * (z > 0.0 ? z : 0.0) * vz;
             } else {
               Ph::fall_speeds(K, sdzdt[k], ::log(q), n, dfac, x, vq, vn);
@@ -1467,12 +1504,13 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       const bool act = MixT<M>::active(K, s, P.T0, w, es0, qs0);
       MixInc o;
       MassAcc macc;
+      unsigned keep3 = 0;   // species whose shape the processes left unchanged (triple-moment policies)
       float dn[4] = {0.f, 0.f, 0.f, 0.f};   // number increments of r, i, s, g
       float qpost[4], npost[4];
       if (act) {
         MixT<M>::process(K, s, a.dt, w, es0, qs0, o, a.surr ? a.surr + (size_t)k * a.pitch + c : nullptr);
         MixT<M>::apply_masses(s, o, macc);
-        if constexpr (M::kTri) MixT<M>::apply_z(K, s, w, o);
+        if constexpr (M::kTri) keep3 = MixT<M>::apply_z(K, s, w, o);
         if (o.dn[0] != 0.f) s.nc += f2d(o.dn[0]);
 #pragma unroll
         for (int x = 0; x < 4; ++x) dn[x] = o.dn[1 + x];
@@ -1512,7 +1550,8 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
               if (x < nz3<M>()) {
                 float vz;
                 const float zp = d2f(zref(s, x));
-                Shape3<M>::fall_speeds(K, x, guard, qpost[x], lg2a(qpost[x]), n, zp, dfac, vq, vn, vz);
+                const float mus = ((keep3 >> x) & 1u) ? w.mu3[x] : Shape3<M>::mu(K, x, qpost[x], n, zp);
+                Shape3<M>::fall_speeds_mu(K, x, guard, lg2a(qpost[x]), n, mus, dfac, vq, vn, vz);
                 H = rho * fmaxf(zp, 0.f) * vz;
               } else {
                 Ph::fall_speeds(K, guard, lg2a(qpost[x]), n, dfac, x, vq, vn);

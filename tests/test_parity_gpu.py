@@ -761,6 +761,52 @@ def test_three_moment_cold_mixed_within_derived_bound():
         assert (a >= 0).all(), sp
 
 
+# ------------------------------------- the warm/cold benchmark's state at full size
+@pytest.fixture(scope="module")
+def stratus_full():
+    """The configurations' benchmark state: stratus 512x512 columns x 150 levels."""
+    return synth.workload("stratus_512x512x150")
+
+
+@pytest.mark.parametrize("config", ["warm", "cold_three_moment"])
+def test_stratus_512x512x150_sampled_columns(stratus_full, config):
+    """Full size, one launch over all 262 144 columns, mixed form: 64 seeded
+    random columns and the last one against the oracle (warm configuration;
+    cold configuration with triple-moment r, i, s, g)."""
+    fld16, dz, ncols, nlev, dt, _ = stratus_full
+    cols = np.concatenate([np.sort(np.random.default_rng(78).choice(ncols - 1, 64, replace=False)), [ncols - 1]])
+    n = cols.size
+    if config == "warm":
+        fld, flags = fld16, casim.CASIM_WARM
+    else:
+        fld = np.zeros((20,) + fld16.shape[1:])
+        fld[:16] = fld16
+        rng = np.random.default_rng(79)
+        for sp in "risg":
+            q, nn = fld16[QF[sp]], fld16[NF[sp]]
+            ok = (q > 1e-14) & (nn > 0)
+            shape = rng.uniform(0.0, 8.0, int(ok.sum()))
+            fld[ZC[sp]][ok] = _gamma_g(shape) * (q[ok] / O.param(f"a_{sp}")) ** 2 / nn[ok]
+        flags = casim.CASIM_THREE_MOMENT
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, precision=casim.CASIM_MIXED, flags=flags)
+    sub = np.zeros((fld.shape[0], nlev, 96))
+    sub[:, :, :n] = fld[:, :, cols]
+    if config == "warm":
+        ref, _ = run_oracle(sub, dz, n, dt, warm=True)
+    else:
+        ref, _ = _run_oracle_3m_cold(sub, dz, n, dt, 1)
+    got = out[:, :, cols]
+    for f in range(13):
+        a_, b_, i_ = got[f], ref[f, :, :n], sub[f, :, :n]
+        bound = mixed_bound(b_, i_, f, ref[1, :, :n])
+        assert (np.abs(a_ - b_) <= bound).all(), (synth.FIELDS[f], float((np.abs(a_ - b_) / bound).max()))
+    if config != "warm":
+        for sp, f in ZC.items():
+            a_, b_, i_ = got[f], ref[f, :, :n], sub[f, :, :n]
+            bound = 1e-3 * np.abs(b_ - i_) + 1e-4 * np.abs(b_) + 1e-16 * fld[f].max()
+            assert (np.abs(a_ - b_) <= bound).all(), (sp, float((np.abs(a_ - b_) / bound).max()))
+
+
 # ------------------------------------------------------------------ checkpoint / resume
 @pytest.mark.parametrize("state", ["standard", "aerosol", "three_moment", "three_moment_cold"])
 def test_checkpoint_resume_is_bitwise(tmp_path, state):
