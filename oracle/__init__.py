@@ -25,6 +25,8 @@ NPROG_AERO = 16
 NFIELDS_3M = 17        # + the rain's sixth moment
 NPROG_3M = 14
 NFIELDS_3MC = 20       # cold configuration: + the sixth moments of r, i, s, g
+NFIELDS_AEROC = 22     # cold configuration: + aerosol mass free, in c, r, i, s, g
+NPROG_AEROC = 19
 NPROG_3MC = 17
 NPROC = 14
 SPECIES = {"c": 0, "r": 1, "i": 2, "s": 3, "g": 4}
@@ -115,6 +117,10 @@ def lib():
         L.orc_point_3m_cold.argtypes = [pd, d, pd]
         L.orc_sediment_3m.restype = u
         L.orc_sediment_3m.argtypes = [pd, pd, pd, pd, pd, i, d, pd, ctypes.POINTER(ctypes.c_int)]
+        L.orc_point_aero_cold.restype = None
+        L.orc_point_aero_cold.argtypes = [pd, d, pd]
+        L.orc_step_aero_cold.restype = u
+        L.orc_step_aero_cold.argtypes = [pd, ctypes.c_long, i, i, pd, pd, d, i]
         L.orc_step_3m_cold.restype = u
         L.orc_step_3m_cold.argtypes = [pd, ctypes.c_long, i, i, pd, pd, d, i]
         L.orc_point_aero.restype = None
@@ -382,4 +388,28 @@ def step_3m_cold(fld: np.ndarray, ncols: int, dz: np.ndarray, dt: float, precip:
     if precip is None:
         precip = np.zeros((4, pitch))
     err = lib().orc_step_3m_cold(_dp(fld), pitch, ncols, nlev, _dp(dz), _dp(precip), dt, nthreads)
+    return precip, err
+
+
+# ------------------------------------- activated-aerosol mass, cold configuration
+def point_aero_cold(state: np.ndarray, dt: float) -> np.ndarray:
+    """Cold point with aerosol mass: state[22] -> [13 prognostic, ma, mac, mar, mai, mas, mag]."""
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    assert st.shape == (NFIELDS_AEROC,)
+    out = np.zeros(NPROG_AEROC)
+    lib().orc_point_aero_cold(_dp(st), dt, _dp(out))
+    return out
+
+
+def step_aero_cold(fld: np.ndarray, ncols: int, dz: np.ndarray, dt: float, precip: np.ndarray | None = None,
+                   nthreads: int = 0):
+    """Cold step with aerosol mass, in place on fld [22][nlev][pitch]; precip
+    [5][pitch] (r, i, s, g, aerosol) accumulated.  Returns (precip, err)."""
+    assert fld.dtype == np.float64 and fld.flags["C_CONTIGUOUS"] and fld.shape[0] == NFIELDS_AEROC
+    nlev, pitch = fld.shape[1], fld.shape[2]
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    if precip is None:
+        precip = np.zeros((5, pitch))
+    assert precip.shape == (5, pitch) and precip.dtype == np.float64 and precip.flags["C_CONTIGUOUS"]
+    err = lib().orc_step_aero_cold(_dp(fld), pitch, ncols, nlev, _dp(dz), _dp(precip), dt, nthreads)
     return precip, err

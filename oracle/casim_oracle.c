@@ -388,6 +388,8 @@ typedef struct {
   double tau_cr, tau_rv;    /* cloud -> rain (autoconversion + accretion), rain -> vapour */
   double tau_aut, nr_aut;   /* autoconversion: rain mass, new drops */
   double nuc_q, nuc_n;      /* ice nucleation: mass and crystals made */
+  double tau_rim;           /* cloud -> graupel by riming (snow and graupel collecting cloud) */
+  double sub_q[3];          /* sublimation of i, s, g: mass returned to vapour */
   double melt_q[3], melt_n[3];  /* melting of i, s, g into rain: mass and particles */
 } orc_record;
 
@@ -411,8 +413,8 @@ static void point_core(const double *in0, double dt, double *out, int warm, orc_
     rec->qc_post = st[ORC_QC];
     rec->qr_post = st[ORC_QR];
     rec->tau_cr = rec->tau_rv = rec->tau_aut = rec->nr_aut = 0.0;
-    rec->nuc_q = rec->nuc_n = 0.0;
-    for (int m = 0; m < 3; ++m) rec->melt_q[m] = rec->melt_n[m] = 0.0;
+    rec->nuc_q = rec->nuc_n = rec->tau_rim = 0.0;
+    for (int m = 0; m < 3; ++m) rec->melt_q[m] = rec->melt_n[m] = rec->sub_q[m] = 0.0;
   }
 
   /* a4..a9 from the post-activation state */
@@ -482,6 +484,8 @@ static void point_core(const double *in0, double dt, double *out, int warm, orc_
       if (rec && j == 0) rec->tau_aut = tau;
       if (rec && j == 4) rec->tau_rv += tau;               /* rain evaporation */
       if (rec && j == 5) rec->nuc_q = tau;                 /* nucleation */
+      if (rec && j >= 6 && j <= 8 && tr[j].mdst == ORC_QV) rec->sub_q[j - 6] = tau;   /* sublimation */
+      if (rec && (j == 9 || j == 10)) rec->tau_rim += tau; /* riming by snow and graupel */
       if (rec && j >= nt - 3) rec->melt_q[j - (nt - 3)] = tau;   /* melting of i, s, g */
     }
     if (tr[j].nsink > 0.0) st[tr[j].nsrc] -= g * tr[j].nsink * dt;
@@ -630,6 +634,70 @@ void orc_point_aero(const double *in, double dt, double *out) {
   out[ORC_NPROG + 2] = mar;
 }
 
+/* Activated-aerosol mass in the cold configuration: six mass mixing ratios,
+   free aerosol ma and aerosol in cloud mac, rain mar, ice mai, snow mas,
+   graupel mag.  Beyond the warm configuration's moves (the adjustment returns
+   evaporated cloud's share to ma; activation takes ma dn/na; rain
+   evaporation returns mar in proportion):
+     cloud sinks: autoconversion and accretion carry mac to rain, riming by
+        snow and graupel carries it to graupel (rimed mass goes to graupel),
+        together as the fraction (tau_cr + tau_rim) / q_c of the
+        post-activation cloud, split in proportion to the water;
+     ice species m: sublimation returns its aerosol to ma, melting gives it
+        to rain, together as the fraction (sub_m + melt_m) / q_m, split in
+        proportion (after rain evaporation, so aerosol melted into rain this
+        step is not evaporated with it);
+     nucleated crystals carry no aerosol mass (the ice nuclei are not a
+        tracked population); deposition and self-collection move none.
+   Each species' aerosol sediments with that species' mass-weighted speed.
+   in[ORC_NFIELDS_AEROC] -> out[ORC_NPROG_AEROC]. */
+void orc_point_aero_cold(const double *in, double dt, double *out) {
+  static const int qf[3] = {ORC_QI, ORC_QS, ORC_QG};
+  orc_record r;
+  double o[ORC_NPROG];
+  point_core(in, dt, o, 0, &r, NULL);
+  memcpy(out, o, sizeof o);
+  double ma = in[ORC_MA], mac = in[ORC_MAC], mar = in[ORC_MAR], d;
+  double mx[3] = {in[ORC_MAI], in[ORC_MAS], in[ORC_MAG]};
+  if (r.evap > 0.0 && r.qc0 > 0.0) {
+    d = r.evap >= r.qc0 ? mac : mac * (r.evap / r.qc0);
+    mac -= d;
+    ma += d;
+  }
+  if (r.dn_act > 0.0 && r.na0 > 0.0) {
+    d = ma * (r.dn_act / r.na0);
+    ma -= d;
+    mac += d;
+  }
+  const double cs = r.tau_cr + r.tau_rim;
+  if (cs > 0.0 && r.qc_post > 0.0) {
+    d = cs >= r.qc_post ? mac : mac * (cs / r.qc_post);
+    mac -= d;
+    const double dg = d * (r.tau_rim / cs);
+    mx[2] += dg;
+    mar += d - dg;
+  }
+  if (r.tau_rv > 0.0 && r.qr_post > 0.0) {
+    d = r.tau_rv >= r.qr_post ? mar : mar * (r.tau_rv / r.qr_post);
+    mar -= d;
+    ma += d;
+  }
+  for (int m = 0; m < 3; ++m) {
+    const double q0 = in[qf[m]], sk = r.sub_q[m] + r.melt_q[m];
+    if (sk > 0.0 && q0 > 0.0) {
+      d = sk >= q0 ? mx[m] : mx[m] * (sk / q0);
+      mx[m] -= d;
+      const double dm = d * (r.melt_q[m] / sk);
+      mar += dm;
+      ma += d - dm;
+    }
+  }
+  out[ORC_NPROG + 0] = ma;
+  out[ORC_NPROG + 1] = mac;
+  out[ORC_NPROG + 2] = mar;
+  for (int m = 0; m < 3; ++m) out[ORC_NPROG + 3 + m] = mx[m];
+}
+
 /* ------------------------------------------------------ a12 sedimentation */
 static unsigned sediment_species(double *q, double *n, const double *rho, const double *dz, int nlev, double dt,
                                  double *precip, int *nsub, int nspecies, double *aer, double *aprecip,
@@ -651,8 +719,9 @@ unsigned orc_sediment_3m(double *q, double *n, double *z, const double *rho, con
 }
 
 /* the first nspecies of r, i, s, g (warm configuration: rain only); aer (may
-   be NULL): aerosol mass in rain, moved with the rain's mass-weighted speed,
-   its surface flux accumulated in *aprecip; zr (may be NULL): the species'
+   be NULL): aerosol mass in the species (nspecies arrays of nlev), each moved
+   with its species' mass-weighted speed, the surface fluxes accumulated in
+   *aprecip; zr (may be NULL): the species'
    sixth moments (triple-moment scheme; nspecies arrays of nlev), each moved
    with its sixth-moment-weighted speed, every speed of the species then
    taken at the shape diagnosed per level and substep */
@@ -693,7 +762,8 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
     if (nsub) nsub[m] = ns;
     double dts = dt / ns;
     for (int s = 0; s < ns; ++s) {
-      const int with_aer = aer != NULL && m == 0;
+      const int with_aer = aer != NULL;
+      double *am = with_aer ? aer + (size_t)m * nlev : NULL;
       for (int k = 0; k < nlev; ++k) {
         F[k] = 0.0;
         G[k] = 0.0;
@@ -711,7 +781,7 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
           if (vn > vlim) vn = vlim;
           F[k] = rho[k] * qq[k] * vq;
           G[k] = rho[k] * (nn[k] > 0.0 ? nn[k] : 0.0) * vn;
-          if (with_aer) A[k] = rho[k] * aer[k] * vq;
+          if (with_aer) A[k] = rho[k] * am[k] * vq;
           if (tri) {
             double vz = orc_vz_mu(sp, rho[k], lam, mu);
             if (vz > vlim) vz = vlim;
@@ -726,7 +796,7 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
       for (int k = 0; k < nlev; ++k) {
         qq[k] += dts * (F[k + 1] - F[k]) / (rho[k] * dz[k]);
         nn[k] += dts * (G[k + 1] - G[k]) / (rho[k] * dz[k]);
-        if (with_aer) aer[k] += dts * (A[k + 1] - A[k]) / (rho[k] * dz[k]);
+        if (with_aer) am[k] += dts * (A[k + 1] - A[k]) / (rho[k] * dz[k]);
         if (tri) zz[k] += dts * (H[k + 1] - H[k]) / (rho[k] * dz[k]);
       }
       precip[m] += F[0] * dts;
@@ -741,21 +811,27 @@ static unsigned sediment_species(double *q, double *n, const double *rho, const 
 }
 
 /* ----------------------------------------------------------- full step */
-/* aero: the state has ORC_NFIELDS_AERO fields and precip 5 rows (warm only);
+/* aero: the state has ORC_NFIELDS_AERO (warm) or ORC_NFIELDS_AEROC (cold)
+   fields and precip 5 rows;
    tri: the state has ORC_NFIELDS_3M fields (warm) or ORC_NFIELDS_3MC (cold) */
 static unsigned step_column(double *fld, long pitch, int nlev, int c, const double *dz,
                             double *precip, int *nsub, double dt, int warm, int aero, int tri) {
   unsigned err = 0;
   long fs = (long)nlev * pitch; /* field stride */
-  const int nfields = aero ? ORC_NFIELDS_AERO : tri ? (warm ? ORC_NFIELDS_3M : ORC_NFIELDS_3MC) : ORC_NFIELDS;
-  const int nz = tri ? (warm ? 1 : 4) : 0;   /* sixth moments carried */
-  double in[ORC_NFIELDS_3MC], out[ORC_NPROG_3MC];
-  const int map[ORC_NPROG_AERO] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, ORC_MA, ORC_MAC, ORC_MAR};
+  const int nfields = aero ? (warm ? ORC_NFIELDS_AERO : ORC_NFIELDS_AEROC)
+                            : tri ? (warm ? ORC_NFIELDS_3M : ORC_NFIELDS_3MC) : ORC_NFIELDS;
+  const int nz = tri ? (warm ? 1 : 4) : 0;        /* sixth moments carried */
+  const int na = aero ? (warm ? 1 : 4) : 0;       /* species carrying aerosol mass */
+  double in[ORC_NFIELDS_AEROC], out[ORC_NPROG_AEROC];
+  const int map[ORC_NPROG_AEROC] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12,
+                                    ORC_MA, ORC_MAC, ORC_MAR, ORC_MAI, ORC_MAS, ORC_MAG};
   for (int k = 0; k < nlev; ++k) {
     for (int f = 0; f < nfields; ++f) in[f] = fld[f * fs + (long)k * pitch + c];
     if (aero) {
-      orc_point_aero(in, dt, out);
-      for (int f = 0; f < ORC_NPROG_AERO; ++f) fld[map[f] * fs + (long)k * pitch + c] = out[f];
+      if (warm) orc_point_aero(in, dt, out);
+      else orc_point_aero_cold(in, dt, out);
+      const int nout = warm ? ORC_NPROG_AERO : ORC_NPROG_AEROC;
+      for (int f = 0; f < nout; ++f) fld[map[f] * fs + (long)k * pitch + c] = out[f];
     } else if (tri) {
       if (warm) orc_point_3m(in, dt, out);
       else orc_point_3m_cold(in, dt, out);
@@ -766,13 +842,13 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
       for (int f = 0; f < ORC_NPROG; ++f) fld[f * fs + (long)k * pitch + c] = out[f];
     }
   }
-  double *buf = (double *)malloc(sizeof(double) * (size_t)(14 * nlev));
-  double *q = buf, *n = buf + 4 * nlev, *rho = buf + 8 * nlev, *aer = buf + 9 * nlev, *zr = buf + 10 * nlev;
+  double *buf = (double *)malloc(sizeof(double) * (size_t)(17 * nlev));
+  double *q = buf, *n = buf + 4 * nlev, *rho = buf + 8 * nlev, *aer = buf + 9 * nlev, *zr = buf + 13 * nlev;
   static const int qf[4] = {ORC_QR, ORC_QI, ORC_QS, ORC_QG};
   static const int nf[4] = {ORC_NR, ORC_NI, ORC_NS, ORC_NG};
   for (int k = 0; k < nlev; ++k) {
     rho[k] = fld[ORC_RHO * fs + (long)k * pitch + c];
-    aer[k] = aero ? fld[ORC_MAR * fs + (long)k * pitch + c] : 0.0;
+    for (int x = 0; x < na; ++x) aer[x * nlev + k] = fld[(ORC_MAR + x) * fs + (long)k * pitch + c];
     for (int x = 0; x < nz; ++x) zr[x * nlev + k] = fld[(ORC_ZR + x) * fs + (long)k * pitch + c];
     for (int m = 0; m < 4; ++m) {
       q[m * nlev + k] = fld[qf[m] * fs + (long)k * pitch + c];
@@ -787,7 +863,8 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
   for (int x = 0; x < nz; ++x)
     for (int k = 0; k < nlev; ++k) fld[(ORC_ZR + x) * fs + (long)k * pitch + c] = zr[x * nlev + k];
   if (aero) {
-    for (int k = 0; k < nlev; ++k) fld[ORC_MAR * fs + (long)k * pitch + c] = aer[k];
+    for (int x = 0; x < na; ++x)
+      for (int k = 0; k < nlev; ++k) fld[(ORC_MAR + x) * fs + (long)k * pitch + c] = aer[x * nlev + k];
     precip[4 * pitch + c] += apr;
   }
   for (int k = 0; k < nlev; ++k)
@@ -804,7 +881,7 @@ static unsigned step_column(double *fld, long pitch, int nlev, int c, const doub
     for (int f = 0; f < ORC_NPROG; ++f)
       if (!isfinite(fld[f * fs + (long)k * pitch + c])) err |= ORC_ERR_NONFINITE;
     if (aero)
-      for (int f = ORC_MA; f <= ORC_MAR; ++f)
+      for (int f = ORC_MA; f < ORC_MAR + na; ++f)
         if (!isfinite(fld[f * fs + (long)k * pitch + c])) err |= ORC_ERR_NONFINITE;
     for (int x = 0; x < nz; ++x)
       if (!isfinite(fld[(ORC_ZR + x) * fs + (long)k * pitch + c])) err |= ORC_ERR_NONFINITE;
@@ -847,6 +924,19 @@ unsigned orc_step_3m(double *fld, long pitch, int ncols, int nlev, const double 
 #pragma omp parallel for schedule(guided) num_threads(nthreads) reduction(| : err)
 #endif
   for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, NULL, dt, 1, 0, 1);
+  (void)nthreads;
+  return err;
+}
+
+unsigned orc_step_aero_cold(double *fld, long pitch, int ncols, int nlev, const double *dz, double *precip,
+                            double dt, int nthreads) {
+  unsigned err = 0;
+  if (nlev <= 0 || ncols <= 0) return 0;
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(guided) num_threads(nthreads) reduction(| : err)
+#endif
+  for (int c = 0; c < ncols; ++c) err |= step_column(fld, pitch, nlev, c, dz, precip, NULL, dt, 0, 1, 0);
   (void)nthreads;
   return err;
 }

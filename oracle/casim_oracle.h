@@ -32,6 +32,10 @@ enum {
    rain mar (kg/kg) -- and a fifth precipitation row (aerosol deposited). */
 enum { ORC_MA = ORC_NFIELDS, ORC_MAC, ORC_MAR, ORC_NFIELDS_AERO };
 #define ORC_NPROG_AERO (ORC_NPROG + 3)
+/* Cold configuration: three more after those -- aerosol mass in ice mai,
+   snow mas and graupel mag (the aerosol of r, i, s, g is fields 18..21). */
+enum { ORC_MAI = ORC_NFIELDS_AERO, ORC_MAS, ORC_MAG, ORC_NFIELDS_AEROC };
+#define ORC_NPROG_AEROC (ORC_NPROG + 6)
 /* Triple-moment extension: the sixth moments z (m^6 per kg of air) after the
    16 fields above -- rain only in the warm configuration (17 fields), rain,
    ice, snow and graupel in the cold one (20 fields). */
@@ -133,6 +137,14 @@ unsigned orc_step_3m(double *fld, long pitch, int ncols, int nlev, const double 
                      int nthreads);
 unsigned orc_step_aero(double *fld, long pitch, int ncols, int nlev, const double *dz,
                        double *precip, double dt, int nthreads);
+/* The cold configuration with activated-aerosol mass in cloud, rain and the
+   ice species: in[ORC_NFIELDS_AEROC] -> out[ORC_NPROG_AEROC] (13 prognostic
+   fields, then ma, mac, mar, mai, mas, mag); a step over
+   fld[ORC_NFIELDS_AEROC][nlev][pitch] with precip[5][pitch].  The first 16
+   fields and 4 precipitation rows are exactly those of orc_step. */
+void   orc_point_aero_cold(const double *in, double dt, double *out);
+unsigned orc_step_aero_cold(double *fld, long pitch, int ncols, int nlev, const double *dz,
+                            double *precip, double dt, int nthreads);
 /* Parameter lookup by name for the tests (returns NaN for an unknown name). */
 double orc_param(const char *name);
 int    orc_max_threads(void);
