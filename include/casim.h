@@ -121,20 +121,26 @@ int casim_default_params(casim_params *p);
    surrogate entry points reject a warm context (CASIM_ERR_ARG). */
 #define CASIM_WARM 1
 
-/* casim_init flag, with CASIM_WARM only: activated-aerosol mass (Section 2:
-   CASIM carries the mass of activated aerosol in the cloud and returns it
-   to the air when the water evaporates).  The state then has 19 fields --
-   the 16 above, then ma (free aerosol mass), mac (aerosol mass in cloud
-   droplets), mar (aerosol mass in rain), kg/kg -- and precip 5 rows, the
-   fifth the aerosol mass deposited by rain (kg m^-2).  Aerosol mass moves
-   with the water: the cloud the adjustment evaporates returns its share of
-   mac to ma; activated droplets take the free aerosol's mean particle mass
-   ma * dn / na; autoconversion and accretion carry mac to rain in proportion
-   to the cloud water they move; rain evaporation returns mar to ma in
-   proportion; mar sediments with the rain's mass-weighted fall speed.  The
-   other 16 fields and 4 precipitation rows evolve exactly as in the warm
-   configuration.  Supported by casim_step (both precisions); the other step
-   entry points reject such a context (CASIM_ERR_ARG). */
+/* casim_init flag (not with CASIM_THREE_MOMENT): activated-aerosol mass
+   (Section 2: CASIM carries the mass of activated aerosol in the cloud and
+   returns it to the air when the water evaporates).  With CASIM_WARM the
+   state has 19 fields -- the 16 above, then ma (free aerosol mass), mac
+   (aerosol mass in cloud droplets), mar (aerosol mass in rain), kg/kg;
+   without it 22 fields -- then also mai, mas, mag (aerosol mass in ice,
+   snow, graupel).  precip then has 5 rows, the fifth the aerosol mass
+   deposited at the surface (kg m^-2).  Aerosol mass moves with the water:
+   the cloud the adjustment evaporates returns its share of mac to ma;
+   activated droplets take the free aerosol's mean particle mass
+   ma * dn / na; autoconversion and accretion carry mac to rain, and (cold)
+   riming by snow and graupel carries it to graupel, in proportion to the
+   cloud water they move; rain evaporation returns mar to ma in proportion;
+   (cold) sublimation returns, and melting passes on to rain, an ice
+   species' aerosol in proportion to the mass it loses; nucleated crystals
+   carry none; each species' aerosol sediments with its mass-weighted fall
+   speed.  The other 16 fields and 4 precipitation rows evolve exactly as
+   without aerosol mass.  Supported by casim_step (both precisions) and the
+   checkpoint calls; the other step entry points reject such a context
+   (CASIM_ERR_ARG). */
 #define CASIM_AEROSOL 2
 
 /* casim_init flag (not with CASIM_AEROSOL): the triple-moment scheme
@@ -163,9 +169,9 @@ int casim_default_params(casim_params *p);
 
 /* Create a context on the current CUDA device (Section 3.2: the one-off
    set-up that copies constants and allocates device memory).  `params` may be
-   NULL for the defaults; `precision` is a casim_precision; `flags` is 0,
-   CASIM_WARM, CASIM_WARM | CASIM_AEROSOL, CASIM_THREE_MOMENT or CASIM_WARM |
-   CASIM_THREE_MOMENT (CASIM_ERR_ARG otherwise).  Allocates a small device error word.  On
+   NULL for the defaults; `precision` is a casim_precision; `flags` is 0 or
+   CASIM_WARM, optionally with one of CASIM_AEROSOL or CASIM_THREE_MOMENT
+   (CASIM_ERR_ARG otherwise).  Allocates a small device error word.  On
    failure *ctx is set to NULL. */
 int casim_init(casim_ctx **ctx, const casim_params *params, int precision, int flags);
 
@@ -388,7 +394,8 @@ const char *casim_last_cuda_error(void);
  * the precipitation rows as raw FP64 values in host byte order.  A run of N
  * steps equals, bit for bit, k steps, save, load, N - k steps.
  * nfields is CASIM_NFIELDS, CASIM_NFIELDS_3MOM or CASIM_NFIELDS_3MOM_COLD for
- * the triple-moment states (warm, cold),
+ * the triple-moment states (warm, cold), CASIM_NFIELDS_AEROSOL_COLD for the
+ * cold activated-aerosol state (whose precip has CASIM_NPRECIP + 1 rows),
  * or CASIM_NFIELDS_AEROSOL for the activated-aerosol state (whose precip has
  * CASIM_NPRECIP + 1 rows).  Device pointers;
  * both calls wait for `stream`.  params may be NULL (the defaults).
@@ -397,6 +404,7 @@ const char *casim_last_cuda_error(void);
 #define CASIM_NFIELDS_AEROSOL 19
 #define CASIM_NFIELDS_3MOM 17
 #define CASIM_NFIELDS_3MOM_COLD 20
+#define CASIM_NFIELDS_AEROSOL_COLD 22
 int casim_state_save(const char *path, const casim_params *params, const casim_state *s, int ncols, int nlev,
                      int nfields, void *stream);
 int casim_state_load(const char *path, const casim_params *params, const casim_state *s, int ncols, int nlev,

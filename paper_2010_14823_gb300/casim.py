@@ -19,11 +19,12 @@ from .build import LIB, INCLUDE
 CASIM_FP64 = 0
 CASIM_MIXED = 1
 CASIM_WARM = 1          # casim_init flag: the warm configuration
-CASIM_AEROSOL = 2       # casim_init flag (with CASIM_WARM): activated-aerosol mass, 19 fields, 5 precip rows
+CASIM_AEROSOL = 2       # casim_init flag: activated-aerosol mass (with CASIM_WARM 19 fields, else 22), 5 precip rows
 CASIM_THREE_MOMENT = 4  # casim_init flag: triple-moment rain (with CASIM_WARM, 17 fields) or r, i, s, g (20 fields)
 NFIELDS_AERO = 19
 NFIELDS_3MOM = 17
 NFIELDS_3MOM_COLD = 20
+NFIELDS_AERO_COLD = 22
 CASIM_MAX_LEV = 1024   # largest level count of a column
 NFIELDS = 16
 NPROG = 13
@@ -333,7 +334,8 @@ class Domain:
         state, whose precip then has 5 rows."""
         import torch
         nf, nlev, pitch = fld.shape
-        assert nf in (NFIELDS, NFIELDS_3MOM, NFIELDS_AERO, NFIELDS_3MOM_COLD) and pitch % 32 == 0 and pitch >= ncols
+        assert nf in (NFIELDS, NFIELDS_3MOM, NFIELDS_AERO, NFIELDS_3MOM_COLD, NFIELDS_AERO_COLD)
+        assert pitch % 32 == 0 and pitch >= ncols
         self.ncols, self.nlev, self.pitch = ncols, nlev, pitch
         if isinstance(fld, torch.Tensor):
             assert fld.dtype == torch.float64
@@ -342,7 +344,8 @@ class Domain:
             self.fld = torch.from_numpy(np.ascontiguousarray(fld)).to(device)
         assert self.fld.data_ptr() % 256 == 0
         self.dz = torch.from_numpy(np.ascontiguousarray(dz, dtype=np.float64)).to(device)
-        self.precip = torch.zeros((NPRECIP + (nf == NFIELDS_AERO), pitch), dtype=torch.float64, device=device)
+        nrows = NPRECIP + (nf in (NFIELDS_AERO, NFIELDS_AERO_COLD))
+        self.precip = torch.zeros((nrows, pitch), dtype=torch.float64, device=device)
         self.state = make_state(self.fld, pitch, self.dz, self.precip)
 
     def numpy(self):

@@ -210,7 +210,6 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   *out = nullptr;
   if (precision != CASIM_FP64 && precision != CASIM_MIXED) return CASIM_ERR_ARG;
   if ((flags & ~(CASIM_WARM | CASIM_AEROSOL | CASIM_THREE_MOMENT)) != 0) return CASIM_ERR_ARG;
-  if ((flags & CASIM_AEROSOL) && !(flags & CASIM_WARM)) return CASIM_ERR_ARG;
   if ((flags & CASIM_AEROSOL) && (flags & CASIM_THREE_MOMENT)) return CASIM_ERR_ARG;
   if ((flags & CASIM_THREE_MOMENT) && params) {
     // the shape identity needs b = 3 for every species that carries z
@@ -276,10 +275,14 @@ static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, 
   const dim3 grid((unsigned)((ncols + kBlock - 1) / kBlock));
   cudaStream_t st = (cudaStream_t)stream;
   const KParams &kp = ctx->kp;
-  if (ctx->aero) {
+  if (ctx->aero && ctx->warm) {
     if (tend) return CASIM_ERR_ARG;
     if (ctx->precision == CASIM_MIXED) k_step<PolicyMixWarmAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
     else k_step<PolicyF64WarmAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+  } else if (ctx->aero) {
+    if (tend) return CASIM_ERR_ARG;
+    if (ctx->precision == CASIM_MIXED) k_step<PolicyMixAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+    else k_step<PolicyF64Aero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
   } else if (ctx->tri && ctx->warm) {
     if (tend) return CASIM_ERR_ARG;
     if (ctx->precision == CASIM_MIXED) k_step<PolicyMixWarm3, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
@@ -537,7 +540,7 @@ extern "C" int casim_batch_create(casim_ctx *ctx, const casim_state *domains, co
                                   int ndom, casim_batch **out) {
   if (!out) return CASIM_ERR_ARG;
   *out = nullptr;
-  if (!ctx || ctx->warm || ctx->tri || ndom < 1 || !domains || !ncols || !nlev) return CASIM_ERR_ARG;
+  if (!ctx || ctx->warm || ctx->tri || ctx->aero || ndom < 1 || !domains || !ncols || !nlev) return CASIM_ERR_ARG;
   casim_batch *b = new casim_batch();
   b->ctx = ctx;
   b->ndom = ndom;
@@ -1301,7 +1304,7 @@ extern "C" int casim_mlp_loss_grad_host(casim_mlp *m, const float *Xn, const flo
 extern "C" int casim_mlp_data(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, float *X,
                               float *Y, float *M, long long *pts, long long cap, long long *rows, void *stream) {
   NvtxRange nvtx_range_("casim_mlp_data");
-  if (!ctx || ctx->warm || ctx->tri || !X || !Y || !M || cap < 0 || !rows) return CASIM_ERR_ARG;
+  if (!ctx || ctx->warm || ctx->tri || ctx->aero || !X || !Y || !M || cap < 0 || !rows) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK) return rc;
   *rows = 0;
@@ -1415,7 +1418,7 @@ extern "C" int casim_mlp_set_norm(casim_mlp *m, const float *stats) {
 extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_state *s, int ncols, int nlev,
                                     double dt, void *stream, long long *served) {
   NvtxRange nvtx_range_("casim_step_surrogate");
-  if (!ctx || ctx->warm || ctx->tri || !m || !m->fitted || ctx->precision != CASIM_MIXED) return CASIM_ERR_ARG;
+  if (!ctx || ctx->warm || ctx->tri || ctx->aero || !m || !m->fitted || ctx->precision != CASIM_MIXED) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -1503,7 +1506,7 @@ int ckpt_check(const casim_state *s, int ncols, int nlev, int nfields) {
   if (!s || !s->fld || !s->dz || !s->precip || ncols < 0 || nlev < 1 || nlev > kMaxLev) return CASIM_ERR_ARG;
   if (s->pitch < ncols || s->pitch % 32 != 0) return CASIM_ERR_ARG;
   if (nfields != CASIM_NFIELDS && nfields != CASIM_NFIELDS_AEROSOL && nfields != CASIM_NFIELDS_3MOM &&
-      nfields != CASIM_NFIELDS_3MOM_COLD)
+      nfields != CASIM_NFIELDS_3MOM_COLD && nfields != CASIM_NFIELDS_AEROSOL_COLD)
     return CASIM_ERR_ARG;
   return CASIM_OK;
 }
@@ -1519,7 +1522,7 @@ extern "C" int casim_state_save(const char *path, const casim_params *params, co
   std::memcpy(h.tag, "CASIMSV1", 8);
   h.abi = CASIM_ABI_VERSION;
   h.nfields = nfields;
-  h.nprecip = CASIM_NPRECIP + (nfields == CASIM_NFIELDS_AEROSOL);
+  h.nprecip = CASIM_NPRECIP + (nfields == CASIM_NFIELDS_AEROSOL || nfields == CASIM_NFIELDS_AEROSOL_COLD);
   h.nlev = nlev;
   h.pitch = s->pitch;
   h.ncols = ncols;
@@ -1551,7 +1554,8 @@ extern "C" int casim_state_load(const char *path, const casim_params *params, co
     return CASIM_ERR_IO;
   }
   if (std::memcmp(h.tag, "CASIMSV1", 8) != 0 || h.abi != CASIM_ABI_VERSION || h.nfields != nfields ||
-      h.nprecip != CASIM_NPRECIP + (nfields == CASIM_NFIELDS_AEROSOL) || h.nlev != nlev || h.pitch != s->pitch ||
+      h.nprecip != CASIM_NPRECIP + (nfields == CASIM_NFIELDS_AEROSOL || nfields == CASIM_NFIELDS_AEROSOL_COLD) ||
+      h.nlev != nlev || h.pitch != s->pitch ||
       h.ncols != ncols || h.params_hash != params_hash(params)) {
     std::fclose(f);
     return CASIM_ERR_ARG;

@@ -239,6 +239,7 @@ struct PolicyMix {
 struct Pt {
   double T, qv, qc, qr, qi, qs, qg, nc, nr, ni, ns, ng, na, p, rho, w;
   double ma, mac, mar;   // activated-aerosol mass (free, in cloud, in rain): aerosol-mass policies only
+  double mai, mas, mag;  // in ice, snow, graupel: cold aerosol-mass policies only
   double zr;             // the rain's sixth moment: triple-moment policies only
   double zi, zs, zg;     // those of ice, snow, graupel: cold triple-moment policies only
 };
@@ -251,10 +252,21 @@ __device__ __forceinline__ double zval(const Pt &s, int x) {
   return x == 0 ? s.zr : x == 1 ? s.zi : x == 2 ? s.zs : s.zg;
 }
 
+// aerosol mass carried by sedimenting species x (r, i, s, g)
+__device__ __forceinline__ double &maref(Pt &s, int x) {
+  return x == 0 ? s.mar : x == 1 ? s.mai : x == 2 ? s.mas : s.mag;
+}
+
 // number of sixth moments a policy carries: rain only (warm), r, i, s, g (cold)
 template <class M>
 __host__ __device__ constexpr int nz3() {
   return M::kTri ? (M::kWarm ? 1 : 4) : 0;
+}
+
+// number of sedimenting species that carry aerosol mass: rain only (warm), r, i, s, g (cold)
+template <class M>
+__host__ __device__ constexpr int na3() {
+  return M::kAero ? (M::kWarm ? 1 : 4) : 0;
 }
 
 // Working values of a point in the compute precision (after adjustment and
@@ -661,6 +673,7 @@ struct F64T {
     const double qx0[3] = {s.qi, s.qs, s.qg}, nx0[3] = {s.ni, s.ns, s.ng};
     double tau_cr = 0.0, tau_rv = 0.0, tau_aut = 0.0, nr_aut = 0.0;
     double nuc_q = 0.0, nuc_n = 0.0, melt_q[3] = {0.0, 0.0, 0.0}, melt_n[3] = {0.0, 0.0, 0.0};
+    double tau_rim = 0.0, sub_q[3] = {0.0, 0.0, 0.0};
     W<double> w;
     w.Td = s.T; w.T = s.T; w.tc = s.T - K.T0; w.p = s.p; w.rho = s.rho;
     w.qv = s.qv; w.qc = s.qc; w.qr = s.qr; w.qx[0] = s.qi; w.qx[1] = s.qs; w.qx[2] = s.qg;
@@ -695,13 +708,13 @@ struct F64T {
       if (r.dep[m] >= 0) {
         if (g.depp[m] > 0) { tau = g.dep[m] * g.depp[m] * dt; s.qv -= tau; qxd[m] += tau; s.T += tau * K.ls / K.cp; }
       } else {
-        tau = g.dep[m] * g.sub[m] * dt; qxd[m] -= tau; s.qv += tau; s.T += tau * (-K.ls) / K.cp;
+        tau = g.dep[m] * g.sub[m] * dt; qxd[m] -= tau; s.qv += tau; s.T += tau * (-K.ls) / K.cp; sub_q[m] = tau;
         if (g.sub[m] * g.rx[m] > 0) nxd[m] -= g.dep[m] * (g.sub[m] * g.rx[m]) * dt;
       }
     }
-    if (r.rim[0] > 0) { tau = g.rs * r.rim[0] * dt; s.qc -= tau; qxd[2] += tau; s.T += tau * K.lf / K.cp; }
+    if (r.rim[0] > 0) { tau = g.rs * r.rim[0] * dt; s.qc -= tau; qxd[2] += tau; s.T += tau * K.lf / K.cp; tau_rim += tau; }
     if (r.rim[0] * g.rc > 0) s.nc -= g.rs * (r.rim[0] * g.rc) * dt;
-    if (r.rim[1] > 0) { tau = g.rg * r.rim[1] * dt; s.qc -= tau; qxd[2] += tau; s.T += tau * K.lf / K.cp; }
+    if (r.rim[1] > 0) { tau = g.rg * r.rim[1] * dt; s.qc -= tau; qxd[2] += tau; s.T += tau * K.lf / K.cp; tau_rim += tau; }
     if (r.rim[1] * g.rc > 0) s.nc -= g.rg * (r.rim[1] * g.rc) * dt;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -766,15 +779,44 @@ struct F64T {
         s.ma -= d;
         s.mac += d;
       }
-      if (tau_cr > 0.0 && qc_post > 0.0) {
-        d = tau_cr >= qc_post ? s.mac : s.mac * (tau_cr / qc_post);
-        s.mac -= d;
-        s.mar += d;
+      if constexpr (M::kWarm) {
+        if (tau_cr > 0.0 && qc_post > 0.0) {
+          d = tau_cr >= qc_post ? s.mac : s.mac * (tau_cr / qc_post);
+          s.mac -= d;
+          s.mar += d;
+        }
+      } else {
+        // cloud sinks: to rain (autoconversion, accretion) and to graupel
+        // (riming), as one fraction of the cloud split in proportion
+        const double cs = tau_cr + tau_rim;
+        if (cs > 0.0 && qc_post > 0.0) {
+          d = cs >= qc_post ? s.mac : s.mac * (cs / qc_post);
+          s.mac -= d;
+          const double dg = d * (tau_rim / cs);
+          s.mag += dg;
+          s.mar += d - dg;
+        }
       }
       if (tau_rv > 0.0 && qr_post > 0.0) {
         d = tau_rv >= qr_post ? s.mar : s.mar * (tau_rv / qr_post);
         s.mar -= d;
         s.ma += d;
+      }
+      if constexpr (!M::kWarm) {
+        // ice species: sublimation returns, melting passes on to rain, their
+        // aerosol as one fraction of the species split in proportion
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          const double sk = sub_q[m] + melt_q[m];
+          if (sk > 0.0 && qx0[m] > 0.0) {
+            double &mx = maref(s, 1 + m);
+            d = sk >= qx0[m] ? mx : mx * (sk / qx0[m]);
+            mx -= d;
+            const double dm = d * (melt_q[m] / sk);
+            s.mar += dm;
+            s.ma += d - dm;
+          }
+        }
       }
     }
   }
@@ -823,6 +865,12 @@ struct MixInc {
   // and rain -> free; *_all: the whole pool moves
   float a_ev, a_act, a_cr, a_rv;
   bool a_ev_all, a_cr_all, a_rv_all;
+  // cold aerosol-mass policies: a_cr is the cloud's whole sink (to rain and,
+  // by riming, to graupel) and a_rim the graupel's share of it; a_x: the
+  // fraction of ice species' aerosol leaving it (sublimation, melting),
+  // a_melt the share of that going to rain
+  float a_rim, a_x[3], a_melt[3];
+  bool a_x_all[3];
   float r_aut, n_aut;   // triple-moment policies: rain mass and drops made by autoconversion
   float q_nuc, n_nuc;   // cold triple-moment policies: ice mass and crystals made by nucleation
   float n_melt[3];      // and particles of i, s, g melted into rain
@@ -906,6 +954,14 @@ struct MixT {
     if constexpr (M::kAero) {
       o.a_ev = o.a_act = o.a_cr = o.a_rv = 0.f;
       o.a_ev_all = o.a_cr_all = o.a_rv_all = false;
+      if constexpr (!M::kWarm) {
+        o.a_rim = 0.f;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          o.a_x[m] = o.a_melt[m] = 0.f;
+          o.a_x_all[m] = false;
+        }
+      }
     }
     // a2: Newton on the temperature increment; qv - qs(T + dT) is the FP64
     // difference at dT = 0 plus the FP32 change of qs
@@ -1001,9 +1057,18 @@ struct MixT {
       }
     }
     if constexpr (M::kAero) {
-      if (o.cr > 0.f && w.qc > 0.f) {
-        o.a_cr_all = o.cr >= w.qc;
-        o.a_cr = __fdividef(o.cr, w.qc);
+      if constexpr (M::kWarm) {
+        if (o.cr > 0.f && w.qc > 0.f) {
+          o.a_cr_all = o.cr >= w.qc;
+          o.a_cr = __fdividef(o.cr, w.qc);
+        }
+      } else {
+        const float cs = o.cr + o.cg;
+        if (cs > 0.f && w.qc > 0.f) {
+          o.a_cr_all = cs >= w.qc;
+          o.a_cr = __fdividef(cs, w.qc);
+          o.a_rim = fminf(__fdividef(o.cg, cs), 1.f);
+        }
       }
       if (o.rv > 0.f && w.qr > 0.f) {
         o.a_rv_all = o.rv >= w.qr;
@@ -1015,6 +1080,18 @@ struct MixT {
     o.vx[2] = g.dep[2] * r.dep[2] * dtr;
 #pragma unroll
     for (int m = 0; m < 3; ++m) o.xr[m] = g.mlt[m] * r.mlt[m] * dtr;
+    if constexpr (M::kAero && !M::kWarm) {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const float sub = r.dep[m] < 0.f ? -o.vx[m] : 0.f;
+        const float sk = sub + o.xr[m];
+        if (sk > 0.f && w.qx[m] > 0.f) {
+          o.a_x_all[m] = sk >= w.qx[m];
+          o.a_x[m] = __fdividef(sk, w.qx[m]);
+          o.a_melt[m] = fminf(__fdividef(o.xr[m], sk), 1.f);
+        }
+      }
+    }
     o.dn[0] = dnc_act - (g.aut * r.aut * g.rc + g.acc * r.acc * g.rc + g.scc * r.scc + g.rs * r.rim[0] * g.rc +
                          g.rg * r.rim[1] * g.rc) * dtr;
     o.dn[1] = (g.aut * r.aut * K.inv_mr0 - g.scr * r.scr - g.evr * r.evr * g.rr + g.mlt[0] * g.nmlt[0] +
@@ -1114,10 +1191,27 @@ struct MixT {
       from -= d;
       to += d;
     };
+    // a move whose amount is split between two destinations (share to the first)
+    auto split = [](double &from, double &to1, double &to2, float frac, bool all, float share) {
+      if (!all && !(frac > 0.f)) return;
+      const double d = all ? from : fmin(f2d(d2f(from) * frac), from);
+      const double d1 = f2d(d2f(d) * share);
+      from -= d;
+      to1 += d1;
+      to2 += d - d1;
+    };
     move(s.mac, s.ma, o.a_ev, o.a_ev_all);
     move(s.ma, s.mac, o.a_act, false);
-    move(s.mac, s.mar, o.a_cr, o.a_cr_all);
+    if constexpr (M::kWarm) {
+      move(s.mac, s.mar, o.a_cr, o.a_cr_all);
+    } else {
+      split(s.mac, s.mag, s.mar, o.a_cr, o.a_cr_all, o.a_rim);
+    }
     move(s.mar, s.ma, o.a_rv, o.a_rv_all);
+    if constexpr (!M::kWarm) {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) split(maref(s, 1 + m), s.mar, s.ma, o.a_x[m], o.a_x_all[m], o.a_melt[m]);
+    }
   }
 };
 
@@ -1162,6 +1256,15 @@ struct PolicyMixWarm3 : PolicyMixWarm {
 struct PolicyF643 : PolicyF64 {
   static constexpr bool kTri = true;
 };
+// The cold configuration with activated-aerosol mass in cloud, rain and the
+// ice species: fields 16..21 are ma, mac, mar, mai, mas, mag.
+struct PolicyF64Aero : PolicyF64 {
+  static constexpr bool kAero = true;
+};
+struct PolicyMixAero : PolicyMix {
+  static constexpr bool kAero = true;
+  static constexpr int kMinBlocks = 4;
+};
 struct PolicyMix3 : PolicyMix {
   static constexpr bool kTri = true;
   static constexpr int kMinBlocks = 4;
@@ -1188,6 +1291,9 @@ __device__ __forceinline__ void load_pt(const KArgs &a, int k, int c, Pt &s) {
   s.p = __ldg(b + 13 * fs); s.rho = __ldg(b + 14 * fs); s.w = __ldg(b + 15 * fs);
   if constexpr (kAero) {
     s.ma = b[16 * fs]; s.mac = b[17 * fs]; s.mar = b[18 * fs];
+    if constexpr (!kWarm) {
+      s.mai = b[19 * fs]; s.mas = b[20 * fs]; s.mag = b[21 * fs];
+    }
   }
   if constexpr (kTri) {
     s.zr = b[16 * fs];
@@ -1342,8 +1448,8 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
     if (ns > 64) { ns = 64; eflag |= 2u; }
     const double dts = a.dt / ns;
     // the rain's aerosol mass moves with the rain (aerosol-mass policies)
-    const bool aer = M::kAero && x == 0;
-    double *ap = a.fld + 18 * fs;
+    const bool aer = x < na3<M>();
+    double *ap = a.fld + (18 + x) * fs;
     for (int st = 0; st < ns; ++st) {
       R Fu = 0, Gu = 0, Au = 0, Hu = 0;
       for (int k = a.nlev - 1; k >= 0; --k) {
@@ -1436,7 +1542,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
   // carried downward fluxes F_{k+1}, G_{k+1} (kg m^-2 s^-1, m^-2 s^-1), and
   // the rain's aerosol-mass flux (aerosol-mass policies)
   R Fq[4] = {0, 0, 0, 0}, Fn[4] = {0, 0, 0, 0};
-  R Fa = 0;                     // rain aerosol mass
+  R Fa[4] = {0, 0, 0, 0};       // aerosol mass in r, i, s, g (aerosol-mass policies)
   R Fz[4] = {0, 0, 0, 0};       // sixth moments of r, i, s, g (triple-moment policies)
 
   for (int k = a.nlev - 1; k >= 0; --k) {
@@ -1471,7 +1577,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
             }
             F = s.rho * q * vq;
             G = s.rho * (n > 0.0 ? n : 0.0) * vn;
-            if (M::kAero && x == 0) A = s.rho * s.mar * vq;
+            if (x < na3<M>()) A = s.rho * maref(s, x) * vq;
           }
           if (x < nz3<M>()) {
             if (H != 0.0 || Fz[x] != 0.0) {
@@ -1485,14 +1591,12 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
             n += a.dt * (Fn[x] - G) / (s.rho * dzk);
             touched = true;
           }
-          if constexpr (M::kAero) {
-            if (x == 0) {
-              if (A != 0.0 || Fa != 0.0) {
-                s.mar += a.dt * (Fa - A) / (s.rho * dzk);
-                touched = true;
-              }
-              Fa = A;
+          if (x < na3<M>()) {
+            if (A != 0.0 || Fa[x] != 0.0) {
+              maref(s, x) += a.dt * (Fa[x] - A) / (s.rho * dzk);
+              touched = true;
             }
+            Fa[x] = A;
           }
           Fq[x] = F;
           Fn[x] = G;
@@ -1558,7 +1662,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
               }
               F = rho * qpost[x] * vq;
               G = rho * fmaxf(n, 0.f) * vn;
-              if (M::kAero && x == 0) A = rho * d2f(s.mar) * vq;
+              if (x < na3<M>()) A = rho * d2f(maref(s, x)) * vq;
             }
             if (x < nz3<M>()) {
               if (H != 0.f || Fz[x] != 0.f) {
@@ -1567,14 +1671,12 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
               }
               Fz[x] = H;
             }
-            if constexpr (M::kAero) {
-              if (x == 0) {
-                if (A != 0.f || Fa != 0.f) {
-                  s.mar += f2d((Fa - A) * sc);
-                  touched = true;
-                }
-                Fa = A;
+            if (x < na3<M>()) {
+              if (A != 0.f || Fa[x] != 0.f) {
+                maref(s, x) += f2d((Fa[x] - A) * sc);
+                touched = true;
               }
+              Fa[x] = A;
             }
             if (F != 0.f || Fq[x] != 0.f) {
               macc.add(x == 0 ? MassAcc::kR : MassAcc::kI + x - 1, (Fq[x] - F) * sc);
@@ -1612,13 +1714,28 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
             eflag |= nonfinite(zval(s, x));
           }
         }
+        if constexpr (M::kAero) {
+          // the aerosol masses: free, in cloud, in r, i, s, g
+          double *b = a.fld + (size_t)k * a.pitch + c;
+          const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
+          const double v[6] = {s.ma, s.mac, s.mar, s.mai, s.mas, s.mag};
+#pragma unroll
+          for (int i = 0; i < 6; ++i) {
+            b[(16 + i) * fs] = v[i];
+            eflag |= nonfinite(v[i]);
+          }
+        }
       }
     }
   }
   if (fast) {
 #pragma unroll
     for (int x = 0; x < kSed; ++x) prec[x] = M::toD(Fq[x]) * a.dt;
-    if constexpr (M::kAero) prec[4] = M::toD(Fa) * a.dt;
+    if constexpr (M::kAero) {
+      prec[4] = 0.0;
+#pragma unroll
+      for (int x = 0; x < na3<M>(); ++x) prec[4] += M::toD(Fa[x]) * a.dt;
+    }
   } else {
     eflag |= sediment_substeps<M, kTend>(a, P, sdz, c, prec, tend);
     if constexpr (kTend) {

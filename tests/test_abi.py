@@ -54,7 +54,8 @@ def test_default_params_match_the_oracle(L):
 def test_argument_errors_without_touching_the_device(L):
     ctx = ctypes.c_void_p()
     assert L.casim_init(ctypes.byref(ctx), None, 7, 0) == -1          # bad precision
-    assert L.casim_init(ctypes.byref(ctx), None, 0, 2) == -1          # unknown flag
+    assert L.casim_init(ctypes.byref(ctx), None, 0, 8) == -1          # unknown flag
+    assert L.casim_init(ctypes.byref(ctx), None, 0, 2 | 4) == -1      # aerosol mass with triple moment
     assert not ctx.value
     st = casim.casim_state(None, 32, None, None)
     assert L.casim_step(None, ctypes.byref(st), 1, 1, 1.0, None) == -1

@@ -545,8 +545,10 @@ def test_aerosol_mixed_within_bound_and_budget():
 
 def test_aerosol_context_rules():
     import torch
-    with pytest.raises(RuntimeError):                    # needs the warm configuration
-        casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_AEROSOL)
+    for flags in (casim.CASIM_AEROSOL | casim.CASIM_THREE_MOMENT,
+                  casim.CASIM_WARM | casim.CASIM_AEROSOL | casim.CASIM_THREE_MOMENT):
+        with pytest.raises(RuntimeError):
+            casim.casim_init(precision=casim.CASIM_MIXED, flags=flags)
     fld, dz = _aero_state(64, 40, seed=53)
     ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM | casim.CASIM_AEROSOL)
     try:
@@ -559,6 +561,81 @@ def test_aerosol_context_rules():
     finally:
         casim.casim_free(ctx)
 
+
+
+# ------------------------------------- activated-aerosol mass, cold configuration
+MAI, MAS, MAG = 19, 20, 21
+
+
+def _aero_cold_state(ncols, nlev, seed):
+    dz = synth.dz_stretched(nlev)
+    base = synth.make_state("deep_convective", ncols, nlev, dz, seed=seed)
+    fld = np.zeros((22,) + base.shape[1:])
+    fld[:16] = base
+    rng = np.random.default_rng(seed)
+    fld[MA] = rng.uniform(1e-9, 5e-9, base.shape[1:])
+    for f, q in ((MAC, "qc"), (MAR, "qr"), (MAI, "qi"), (MAS, "qs"), (MAG, "qg")):
+        fld[f] = fld[F[q]] * rng.uniform(1e-5, 1e-4, base.shape[1:])
+    return np.ascontiguousarray(fld), dz
+
+
+def _run_oracle_aero_cold(fld, dz, ncols, dt, nsteps):
+    ref = fld.copy()
+    pref = np.zeros((5, fld.shape[2]))
+    for _ in range(nsteps):
+        _, err = O.step_aero_cold(ref, ncols, dz, dt, precip=pref)
+        assert err == 0
+    return ref, pref
+
+
+@pytest.mark.parametrize("dt", [1.0, 30.0])
+def test_aerosol_cold_fp64_matches_oracle(dt):
+    """FP64 form, aerosol mass in cloud, rain and the ice species: the 13
+    prognostic fields and 4 precipitation rows within 1e-11 of the oracle,
+    the six aerosol masses within 1e-11 of the point's total aerosol, the
+    deposited row likewise; the standard fields are the cold step's bit for
+    bit (the extension is additive)."""
+    ncols, nlev = 97, 150
+    nsteps = 3 if dt == 1.0 else 1
+    fld, dz = _aero_cold_state(ncols, nlev, seed=54)
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, nsteps=nsteps, flags=casim.CASIM_AEROSOL)
+    ref, pref = _run_oracle_aero_cold(fld, dz, ncols, dt, nsteps)
+    assert_fp64_close(out, pr[:4], ref, pref[:4], ncols, rtol=1e-11)
+    scale = fld[MA:MAG + 1, :, :ncols].sum(axis=0)
+    for f in range(MA, MAG + 1):
+        a, b = out[f, :, :ncols], ref[f, :, :ncols]
+        assert (np.abs(a - b) <= 1e-11 * np.maximum(np.abs(b), scale) + 1e-26).all(), (f, float(np.abs(a - b).max()))
+    assert np.allclose(pr[4, :ncols], pref[4, :ncols], rtol=1e-11, atol=1e-26)
+    assert pref[4, :ncols].max() > 0.0
+    std, pstd, _ = run_gpu(np.ascontiguousarray(fld[:16]), dz, ncols, dt, nsteps=nsteps)
+    assert np.array_equal(out[:16], std) and np.array_equal(pr[:4], pstd)
+
+
+def test_aerosol_cold_mixed_within_bound_and_budget():
+    """Mixed form: the 13 fields within the mixed bound; each aerosol mass
+    within 1e-4 of the point's total aerosol (every amount moved is one FP32
+    product of a pool and a fraction of FP32 rates, ~1e-5 relative, and no
+    move exceeds the total); the column's total aerosol plus the deposited row
+    conserved to 2^-22 of the aerosol moved by sedimentation (one FP32 amount
+    per level and species) plus FP64 rounding."""
+    ncols, nlev = 512, 150
+    fld, dz = _aero_cold_state(ncols, nlev, seed=55)
+    out, pr, _ = run_gpu(fld, dz, ncols, 1.0, precision=casim.CASIM_MIXED, flags=casim.CASIM_AEROSOL)
+    ref, pref = _run_oracle_aero_cold(fld, dz, ncols, 1.0, 1)
+    for f in range(13):
+        a, b, i = out[f, :, :ncols], ref[f, :, :ncols], fld[f, :, :ncols]
+        assert (np.abs(a - b) <= mixed_bound(b, i, f, ref[1, :, :ncols])).all(), synth.FIELDS[f]
+    scale = fld[MA:MAG + 1, :, :ncols].sum(axis=0)
+    for f in range(MA, MAG + 1):
+        a, b = out[f, :, :ncols], ref[f, :, :ncols]
+        bound = 1e-4 * scale + 1e-22
+        assert (np.abs(a - b) <= bound).all(), (f, float((np.abs(a - b) / bound).max()))
+    assert (out[MA:MAG + 1, :, :ncols] >= 0).all()
+    w = fld[F["rho"], :, :ncols] * dz[:, None]
+    m0 = (fld[MA:MAG + 1, :, :ncols] * w).sum(axis=(0, 1))
+    m1 = (out[MA:MAG + 1, :, :ncols] * w).sum(axis=(0, 1))
+    moved = (np.abs(out[MAR:MAG + 1] - fld[MAR:MAG + 1])[:, :, :ncols] * w).sum(axis=(0, 1)) + pr[4, :ncols]
+    assert (np.abs(m1 + pr[4, :ncols] - m0) <= 2.0 ** -22 * moved + 1e-15 * m0).all()
 
 
 # ------------------------------------------------------------------ triple-moment rain (warm)
@@ -808,7 +885,7 @@ def test_stratus_512x512x150_sampled_columns(stratus_full, config):
 
 
 # ------------------------------------------------------------------ checkpoint / resume
-@pytest.mark.parametrize("state", ["standard", "aerosol", "three_moment", "three_moment_cold"])
+@pytest.mark.parametrize("state", ["standard", "aerosol", "three_moment", "three_moment_cold", "aerosol_cold"])
 def test_checkpoint_resume_is_bitwise(tmp_path, state):
     """N steps equal k steps, save, load into fresh device memory, N - k steps,
     bit for bit; a checkpoint of other sizes or parameters is refused."""
@@ -822,6 +899,9 @@ def test_checkpoint_resume_is_bitwise(tmp_path, state):
     elif state == "three_moment_cold":
         fld, dz = _tri_cold_state(ncols, nlev, seed=71)
         flags, nf = casim.CASIM_THREE_MOMENT, 20
+    elif state == "aerosol_cold":
+        fld, dz = _aero_cold_state(ncols, nlev, seed=71)
+        flags, nf = casim.CASIM_AEROSOL, 22
     else:
         dz = synth.dz_stretched(nlev)
         fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=71)
