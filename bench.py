@@ -499,6 +499,15 @@ def bench_warm(args, rank, world, local):
 
     aero_ms = time_ext(aero, casim.CASIM_WARM | casim.CASIM_AEROSOL)
     del aero
+    # the cold chain with aerosol mass also in ice, snow and graupel (22
+    # fields, each at 1e-5 of its species' water)
+    aero = torch.zeros((22, nlev, dom.pitch), dtype=torch.float64, device=dom.fld.device)
+    aero[:16] = fld0
+    aero[16] = 3e-9
+    for f, q in ((17, 2), (18, 3), (19, 4), (20, 5), (21, 6)):
+        aero[f] = 1e-5 * fld0[q]
+    aero_cold_ms = time_ext(aero, casim.CASIM_AEROSOL)
+    del aero
     # triple-moment rain: 17 fields, the rain's sixth moment that of a gamma
     # distribution of shape uniform in [0, 8] at every rainy point
     tri = torch.zeros((17, nlev, dom.pitch), dtype=torch.float64, device=dom.fld.device)
@@ -541,6 +550,8 @@ def bench_warm(args, rank, world, local):
                            "warm_over_cold": cold_ms / warm_ms,
                            "warm_fp64_value": v(w64_ms), "cold_fp64_value": v(c64_ms),
                            "warm_aerosol_mixed_value": v(aero_ms), "warm_aerosol_mixed_ms_per_step": aero_ms,
+                           "cold_aerosol_mixed_value": v(aero_cold_ms),
+                           "cold_aerosol_mixed_ms_per_step": aero_cold_ms,
                            "warm_three_moment_mixed_value": v(tri_ms),
                            "warm_three_moment_mixed_ms_per_step": tri_ms,
                            "cold_three_moment_mixed_value": v(tri_cold_ms),

@@ -845,16 +845,24 @@ def stratus_full():
     return synth.workload("stratus_512x512x150")
 
 
-@pytest.mark.parametrize("config", ["warm", "cold_three_moment"])
+@pytest.mark.parametrize("config", ["warm", "cold_three_moment", "cold_aerosol"])
 def test_stratus_512x512x150_sampled_columns(stratus_full, config):
     """Full size, one launch over all 262 144 columns, mixed form: 64 seeded
     random columns and the last one against the oracle (warm configuration;
-    cold configuration with triple-moment r, i, s, g)."""
+    cold configuration with triple-moment r, i, s, g; cold configuration
+    with aerosol mass)."""
     fld16, dz, ncols, nlev, dt, _ = stratus_full
     cols = np.concatenate([np.sort(np.random.default_rng(78).choice(ncols - 1, 64, replace=False)), [ncols - 1]])
     n = cols.size
     if config == "warm":
         fld, flags = fld16, casim.CASIM_WARM
+    elif config == "cold_aerosol":
+        fld = np.zeros((22,) + fld16.shape[1:])
+        fld[:16] = fld16
+        fld[MA] = 3e-9
+        for f, q in ((MAC, "qc"), (MAR, "qr"), (MAI, "qi"), (MAS, "qs"), (MAG, "qg")):
+            fld[f] = 1e-5 * fld16[F[q]]
+        flags = casim.CASIM_AEROSOL
     else:
         fld = np.zeros((20,) + fld16.shape[1:])
         fld[:16] = fld16
@@ -870,6 +878,8 @@ def test_stratus_512x512x150_sampled_columns(stratus_full, config):
     sub[:, :, :n] = fld[:, :, cols]
     if config == "warm":
         ref, _ = run_oracle(sub, dz, n, dt, warm=True)
+    elif config == "cold_aerosol":
+        ref, _ = _run_oracle_aero_cold(sub, dz, n, dt, 1)
     else:
         ref, _ = _run_oracle_3m_cold(sub, dz, n, dt, 1)
     got = out[:, :, cols]
@@ -877,7 +887,11 @@ def test_stratus_512x512x150_sampled_columns(stratus_full, config):
         a_, b_, i_ = got[f], ref[f, :, :n], sub[f, :, :n]
         bound = mixed_bound(b_, i_, f, ref[1, :, :n])
         assert (np.abs(a_ - b_) <= bound).all(), (synth.FIELDS[f], float((np.abs(a_ - b_) / bound).max()))
-    if config != "warm":
+    if config == "cold_aerosol":
+        scale = sub[MA:MAG + 1, :, :n].sum(axis=0)
+        for f in range(MA, MAG + 1):
+            assert (np.abs(got[f] - ref[f, :, :n]) <= 1e-4 * scale + 1e-22).all(), f
+    elif config != "warm":
         for sp, f in ZC.items():
             a_, b_, i_ = got[f], ref[f, :, :n], sub[f, :, :n]
             bound = 1e-3 * np.abs(b_ - i_) + 1e-4 * np.abs(b_) + 1e-16 * fld[f].max()
