@@ -138,9 +138,9 @@ int casim_default_params(casim_params *p);
    species' aerosol in proportion to the mass it loses; nucleated crystals
    carry none; each species' aerosol sediments with its mass-weighted fall
    speed.  The other 16 fields and 4 precipitation rows evolve exactly as
-   without aerosol mass.  Supported by casim_step (both precisions) and the
-   checkpoint calls; the other step entry points reject such a context
-   (CASIM_ERR_ARG). */
+   without aerosol mass.  Supported by casim_step, casim_step_tendency,
+   casim_step_host (both precisions) and the checkpoint calls; the batched and
+   surrogate entry points reject such a context (CASIM_ERR_ARG). */
 #define CASIM_AEROSOL 2
 
 /* casim_init flag (not with CASIM_AEROSOL): the triple-moment scheme
@@ -159,8 +159,9 @@ int casim_default_params(casim_params *p);
    nucleation (m_i0 / a_i)^2 per new crystal, and melting of species m the
    melted fraction of z_m in rain diameters, (a_m / a_r)^2 (melted / q_m) z_m.
    Requires mass exponent b = 3 for those species.  Supported by casim_step
-   (both precisions) and the checkpoint calls; the other step entry points
-   reject such a context. */
+   (both precisions), casim_step_tendency, casim_step_host and the
+   checkpoint calls; the batched and surrogate entry points reject such a
+   context. */
 #define CASIM_THREE_MOMENT 4
 
 /* Largest level count of a column (the step keeps a column's dz in shared
@@ -188,9 +189,12 @@ int casim_step(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double
    source term per field for the parent model to add (Section 3.2: results go
    into source-term arguments for each q field; Section 3.1: source terms are
    copied back and integrated on the host).  The same step as casim_step, but
-   s->fld is left unchanged and tend (device, [13][nlev][s->pitch], owned by
-   the caller, not overlapping s->fld) receives (x_after - x_before) / dt of
-   the 13 prognostic fields at every point of the first ncols columns, where
+   s->fld is left unchanged and tend (device, [nfields - 3][nlev][s->pitch]
+   for the context's state of nfields fields -- 13 rows for the standard
+   state -- owned by the caller, not overlapping s->fld) receives
+   (x_after - x_before) / dt of the 13 prognostic fields (rows 0..12) and of
+   the configuration's fields after the inputs p, rho, w (field 16 + i in
+   row 13 + i) at every point of the first ncols columns, where
    x_after is what casim_step would store (so x_before + tend * dt reproduces
    it to the rounding of the subtraction and division).  s->precip
    accumulates the step's surface precipitation as in casim_step.
@@ -201,10 +205,11 @@ int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int ncols, int nle
 
 /* Same step for a domain held in HOST memory (any host allocation; pinned
    memory copies faster and overlaps).  A domain of more than 65 536 columns
-   is processed in column chunks of 65 536 (fewer if 16 fields x nlev of them
-   exceed 2 GB) on three internal streams of the context, so one chunk's copy
-   in (16 fields and precip), another's step and a third's copy out (13
-   prognostic fields and precip) run at once (the paper's per-step transfers,
+   is processed in column chunks of 65 536 (fewer if the state's fields x nlev
+   of them exceed 2 GB) on three internal streams of the context, so one
+   chunk's copy in (every field of the context's state, and precip), another's
+   step and a third's copy out (the prognostic fields -- all but p, rho, w --
+   and precip) run at once (the paper's per-step transfers,
    Section 3.3, overlapped with the kernel); a smaller domain is copied whole
    on `stream`.  Starts after the work already queued on `stream` and returns
    when every copy back has landed.  Results equal casim_step's on the same

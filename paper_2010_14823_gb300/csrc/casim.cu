@@ -271,39 +271,36 @@ static KArgs make_args(const casim_ctx *ctx, const casim_state *s, int ncols, in
 }
 
 // tend null: the in-place step; else the source-term mode
+// fields and precipitation rows of a context's state
+static int ctx_nfields(const casim_ctx *ctx) {
+  if (ctx->aero) return ctx->warm ? CASIM_NFIELDS_AEROSOL : CASIM_NFIELDS_AEROSOL_COLD;
+  if (ctx->tri) return ctx->warm ? CASIM_NFIELDS_3MOM : CASIM_NFIELDS_3MOM_COLD;
+  return CASIM_NFIELDS;
+}
+static int ctx_nprecip(const casim_ctx *ctx) { return CASIM_NPRECIP + (ctx->aero ? 1 : 0); }
+
+// one configuration's kernels: the in-place step, or (tend) the source-term mode
+template <class PMix, class PF64>
+static void launch_pair(const casim_ctx *ctx, dim3 grid, cudaStream_t st, const KArgs &a, double *tend) {
+  const KParams &kp = ctx->kp;
+  if (ctx->precision == CASIM_MIXED) {
+    if (tend) k_step<PMix, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
+    else k_step<PMix, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+  } else {
+    if (tend) k_step<PF64, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
+    else k_step<PF64, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+  }
+}
+
 static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, void *stream) {
   const dim3 grid((unsigned)((ncols + kBlock - 1) / kBlock));
   cudaStream_t st = (cudaStream_t)stream;
-  const KParams &kp = ctx->kp;
-  if (ctx->aero && ctx->warm) {
-    if (tend) return CASIM_ERR_ARG;
-    if (ctx->precision == CASIM_MIXED) k_step<PolicyMixWarmAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-    else k_step<PolicyF64WarmAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-  } else if (ctx->aero) {
-    if (tend) return CASIM_ERR_ARG;
-    if (ctx->precision == CASIM_MIXED) k_step<PolicyMixAero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-    else k_step<PolicyF64Aero, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-  } else if (ctx->tri && ctx->warm) {
-    if (tend) return CASIM_ERR_ARG;
-    if (ctx->precision == CASIM_MIXED) k_step<PolicyMixWarm3, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-    else k_step<PolicyF64Warm3, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-  } else if (ctx->tri) {
-    if (tend) return CASIM_ERR_ARG;
-    if (ctx->precision == CASIM_MIXED) k_step<PolicyMix3, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-    else k_step<PolicyF643, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-  } else if (ctx->precision == CASIM_MIXED && !ctx->warm) {
-    if (tend) k_step<PolicyMix, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
-    else k_step<PolicyMix, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-  } else if (ctx->precision == CASIM_MIXED) {
-    if (tend) k_step<PolicyMixWarm, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
-    else k_step<PolicyMixWarm, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-  } else if (!ctx->warm) {
-    if (tend) k_step<PolicyF64, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
-    else k_step<PolicyF64, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-  } else {
-    if (tend) k_step<PolicyF64Warm, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
-    else k_step<PolicyF64Warm, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
-  }
+  if (ctx->aero && ctx->warm) launch_pair<PolicyMixWarmAero, PolicyF64WarmAero>(ctx, grid, st, a, tend);
+  else if (ctx->aero) launch_pair<PolicyMixAero, PolicyF64Aero>(ctx, grid, st, a, tend);
+  else if (ctx->tri && ctx->warm) launch_pair<PolicyMixWarm3, PolicyF64Warm3>(ctx, grid, st, a, tend);
+  else if (ctx->tri) launch_pair<PolicyMix3, PolicyF643>(ctx, grid, st, a, tend);
+  else if (ctx->warm) launch_pair<PolicyMixWarm, PolicyF64Warm>(ctx, grid, st, a, tend);
+  else launch_pair<PolicyMix, PolicyF64>(ctx, grid, st, a, tend);
   ctx->launches++;
   CUDA_TRY(cudaGetLastError());
   return CASIM_OK;
@@ -312,11 +309,12 @@ static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, 
 extern "C" int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, double *tend,
                                    void *stream) {
   NvtxRange nvtx_range_("casim_step_tendency");
-  if (!ctx || ctx->aero || ctx->tri || !tend) return CASIM_ERR_ARG;
+  if (!ctx || !tend) return CASIM_ERR_ARG;
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
-  const size_t span = (size_t)CASIM_NFIELDS * nlev * s->pitch;
-  const size_t tspan = (size_t)CASIM_NPROG * nlev * s->pitch;
+  const int NF = ctx_nfields(ctx);
+  const size_t span = (size_t)NF * nlev * s->pitch;
+  const size_t tspan = (size_t)(NF - 3) * nlev * s->pitch;   // no rows for the inputs p, rho, w
   if (reinterpret_cast<uintptr_t>(tend) % alignof(double) != 0 ||
       (tend < s->fld + span && s->fld < tend + tspan))   // must not overlap the state
     return CASIM_ERR_ARG;
@@ -356,40 +354,57 @@ constexpr size_t kHostChunkBytes = 2ull << 30;
 
 // one column chunk [c0, c0 + wc) of a host state: fields (3-D strided copy:
 // wc columns x nlev levels x nfields) and precip (2-D copy)
-static cudaError_t copy_chunk(double *dev_fld, double *dev_precip, int W, const casim_state *h, int c0, int wc,
-                              int nlev, int nfields, cudaMemcpyKind kind, cudaStream_t st) {
+// fields [f0, f0 + nf) of one column chunk between the host state and a
+// device chunk of width W (one 3-D copy)
+static cudaError_t copy_fields(double *dev_fld, int W, const casim_state *h, int c0, int wc, int nlev, int f0,
+                               int nf, cudaMemcpyKind kind, cudaStream_t st) {
   cudaMemcpy3DParms p = {};
   const bool up = kind == cudaMemcpyHostToDevice;
-  cudaPitchedPtr hp = make_cudaPitchedPtr(h->fld + c0, (size_t)h->pitch * sizeof(double), (size_t)wc, (size_t)nlev);
-  cudaPitchedPtr dp = make_cudaPitchedPtr(dev_fld, (size_t)W * sizeof(double), (size_t)wc, (size_t)nlev);
+  const size_t hs = (size_t)nlev * h->pitch, ds = (size_t)nlev * W;   // field strides
+  cudaPitchedPtr hp = make_cudaPitchedPtr(h->fld + f0 * hs + c0, (size_t)h->pitch * sizeof(double), (size_t)wc,
+                                          (size_t)nlev);
+  cudaPitchedPtr dp = make_cudaPitchedPtr(dev_fld + f0 * ds, (size_t)W * sizeof(double), (size_t)wc, (size_t)nlev);
   p.srcPtr = up ? hp : dp;
   p.dstPtr = up ? dp : hp;
-  p.extent = make_cudaExtent((size_t)wc * sizeof(double), (size_t)nlev, (size_t)nfields);
+  p.extent = make_cudaExtent((size_t)wc * sizeof(double), (size_t)nlev, (size_t)nf);
   p.kind = kind;
-  cudaError_t e = cudaMemcpy3DAsync(&p, st);
+  return cudaMemcpy3DAsync(&p, st);
+}
+
+// one column chunk: up, every field; down, the prognostic ones (0..12 and
+// the configuration's fields after the inputs p, rho, w); and the precip rows
+static cudaError_t copy_chunk(double *dev_fld, double *dev_precip, int W, const casim_state *h, int c0, int wc,
+                              int nlev, int nfields, int nprecip, cudaMemcpyKind kind, cudaStream_t st) {
+  const bool up = kind == cudaMemcpyHostToDevice;
+  cudaError_t e = copy_fields(dev_fld, W, h, c0, wc, nlev, 0, up ? nfields : CASIM_NPROG, kind, st);
+  if (e == cudaSuccess && !up && nfields > CASIM_NFIELDS)
+    e = copy_fields(dev_fld, W, h, c0, wc, nlev, CASIM_NFIELDS, nfields - CASIM_NFIELDS, kind, st);
   if (e != cudaSuccess) return e;
   double *hpr = h->precip + c0;
   const size_t hpitch = (size_t)h->pitch * sizeof(double), dpitch = (size_t)W * sizeof(double);
-  return up ? cudaMemcpy2DAsync(dev_precip, dpitch, hpr, hpitch, (size_t)wc * sizeof(double), CASIM_NPRECIP, kind, st)
-            : cudaMemcpy2DAsync(hpr, hpitch, dev_precip, dpitch, (size_t)wc * sizeof(double), CASIM_NPRECIP, kind, st);
+  return up ? cudaMemcpy2DAsync(dev_precip, dpitch, hpr, hpitch, (size_t)wc * sizeof(double), nprecip, kind, st)
+            : cudaMemcpy2DAsync(hpr, hpitch, dev_precip, dpitch, (size_t)wc * sizeof(double), nprecip, kind, st);
 }
+
+
 
 extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, int nlev, double dt,
                                void *stream) {
   NvtxRange nvtx_range_("casim_step_host");
-  if (!ctx || ctx->aero || ctx->tri) return CASIM_ERR_ARG;
+  if (!ctx) return CASIM_ERR_ARG;
   if (!h || ncols < 0 || nlev < 1 || nlev > kMaxLev || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
   if (ncols == 0) return CASIM_OK;
   if (!h->fld || !h->dz || !h->precip || h->pitch < ncols || h->pitch % 32 != 0) return CASIM_ERR_ARG;
+  const int NF = ctx_nfields(ctx), NP = ctx_nprecip(ctx);
   // chunk width: a multiple of 32 columns with long contiguous rows, within the byte cap
-  const size_t col_bytes = (size_t)CASIM_NFIELDS * nlev * sizeof(double);
+  const size_t col_bytes = (size_t)NF * nlev * sizeof(double);
   const int wcap = (int)std::max<size_t>(32, kHostChunkBytes / col_bytes / 32 * 32);
   const int W = (int)std::min<size_t>(kHostMinRowBytes / sizeof(double), (size_t)wcap);
   const int nchunk = (ncols + W - 1) / W;
   int rc;
   if (nchunk == 1) {
     // one chunk: contiguous copies of the whole state at the host pitch
-    const size_t nf = (size_t)CASIM_NFIELDS * nlev * h->pitch, np = (size_t)CASIM_NPRECIP * h->pitch;
+    const size_t nf = (size_t)NF * nlev * h->pitch, np = (size_t)NP * h->pitch;
     if ((rc = grow(&ctx->h2d_fld[0], &ctx->cap_fld[0], nf)) != CASIM_OK) return rc;
     if ((rc = grow(&ctx->h2d_precip[0], &ctx->cap_precip[0], np)) != CASIM_OK) return rc;
     if ((rc = grow(&ctx->h2d_dz, &ctx->cap_dz, (size_t)nlev)) != CASIM_OK) return rc;
@@ -403,16 +418,19 @@ extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, 
     d.dz = ctx->h2d_dz;
     d.precip = ctx->h2d_precip[0];
     if ((rc = casim_step(ctx, &d, ncols, nlev, dt, stream)) != CASIM_OK) return rc;
-    const size_t nprog = (size_t)CASIM_NPROG * nlev * h->pitch;
+    const size_t fsz = (size_t)nlev * h->pitch, nprog = (size_t)CASIM_NPROG * fsz;
     CUDA_TRY(cudaMemcpyAsync(h->fld, ctx->h2d_fld[0], nprog * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (NF > CASIM_NFIELDS)   // the configuration's prognostic fields after the inputs
+      CUDA_TRY(cudaMemcpyAsync(h->fld + CASIM_NFIELDS * fsz, ctx->h2d_fld[0] + CASIM_NFIELDS * fsz,
+                               (size_t)(NF - CASIM_NFIELDS) * fsz * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(h->precip, ctx->h2d_precip[0], np * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     return CASIM_OK;
   }
   const int S = std::min(casim_ctx::kStages, nchunk);
   for (int s = 0; s < S; ++s) {
-    if ((rc = grow(&ctx->h2d_fld[s], &ctx->cap_fld[s], (size_t)CASIM_NFIELDS * nlev * W)) != CASIM_OK) return rc;
-    if ((rc = grow(&ctx->h2d_precip[s], &ctx->cap_precip[s], (size_t)CASIM_NPRECIP * W)) != CASIM_OK) return rc;
+    if ((rc = grow(&ctx->h2d_fld[s], &ctx->cap_fld[s], (size_t)NF * nlev * W)) != CASIM_OK) return rc;
+    if ((rc = grow(&ctx->h2d_precip[s], &ctx->cap_precip[s], (size_t)NP * W)) != CASIM_OK) return rc;
     if (!ctx->hst[s]) CUDA_TRY(cudaStreamCreateWithFlags(&ctx->hst[s], cudaStreamNonBlocking));
   }
   if ((rc = grow(&ctx->h2d_dz, &ctx->cap_dz, (size_t)nlev)) != CASIM_OK) return rc;
@@ -431,7 +449,7 @@ extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, 
   for (int i = 0; i < nchunk && e == cudaSuccess && rc == CASIM_OK; ++i) {
     const int s = i % S;
     const int c0 = i * W, wc = std::min(W, ncols - c0);
-    e = copy_chunk(ctx->h2d_fld[s], ctx->h2d_precip[s], W, h, c0, wc, nlev, CASIM_NFIELDS, cudaMemcpyHostToDevice,
+    e = copy_chunk(ctx->h2d_fld[s], ctx->h2d_precip[s], W, h, c0, wc, nlev, NF, NP, cudaMemcpyHostToDevice,
                    ctx->hst[s]);
     if (e != cudaSuccess) break;
     casim_state d;
@@ -441,7 +459,7 @@ extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, 
     d.precip = ctx->h2d_precip[s];
     rc = casim_step(ctx, &d, wc, nlev, dt, ctx->hst[s]);
     if (rc != CASIM_OK) break;
-    e = copy_chunk(ctx->h2d_fld[s], ctx->h2d_precip[s], W, h, c0, wc, nlev, CASIM_NPROG, cudaMemcpyDeviceToHost,
+    e = copy_chunk(ctx->h2d_fld[s], ctx->h2d_precip[s], W, h, c0, wc, nlev, NF, NP, cudaMemcpyDeviceToHost,
                    ctx->hst[s]);
   }
   for (int s = 0; s < S; ++s) {

@@ -1350,8 +1350,24 @@ __device__ __forceinline__ unsigned store_pt_warm(const KArgs &a, int k, int c, 
 // from the state, still in cache); in the multi-substep path the new values
 // go to tend as scratch for the substep sweeps and are converted afterwards.
 // (warm configuration: zero source terms for the ice fields)
-template <bool kWarm>
+// prognostic fields a policy carries after the inputs p, rho, w (fields 16..):
+// aerosol masses, or sixth moments; tendency row 13 + i holds field 16 + i
+template <class M>
+__host__ __device__ constexpr int nextra() {
+  return M::kAero ? (M::kWarm ? 3 : 6) : nz3<M>();
+}
+template <class M>
+__device__ __forceinline__ double extra(const Pt &s, int i) {
+  if constexpr (M::kAero) {
+    return i == 0 ? s.ma : i == 1 ? s.mac : i == 2 ? s.mar : i == 3 ? s.mai : i == 4 ? s.mas : s.mag;
+  } else {
+    return zval(s, i);
+  }
+}
+
+template <class M>
 __device__ __forceinline__ unsigned store_tend(const KArgs &a, double *tend, int k, int c, const Pt &s, bool fast) {
+  constexpr bool kWarm = M::kWarm;
   const size_t o = (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
   const double v[13] = {s.T, s.qv, s.qc, s.qr, s.qi, s.qs, s.qg, s.nc, s.nr, s.ni, s.ns, s.ng, s.na};
@@ -1364,7 +1380,14 @@ __device__ __forceinline__ unsigned store_tend(const KArgs &a, double *tend, int
       tend[f * fs + o] = fast ? (v[f] - a.fld[f * fs + o]) / a.dt : v[f];
     }
   }
-  return nonfinite(s.T) | nonfinite(s.qv) | nonfinite(s.qc) | nonfinite(s.qr) | nonfinite(s.qi) |
+  unsigned ex = 0;
+#pragma unroll
+  for (int e = 0; e < nextra<M>(); ++e) {
+    const double v = extra<M>(s, e);
+    tend[(13 + e) * fs + o] = fast ? (v - a.fld[(16 + e) * fs + o]) / a.dt : v;
+    ex |= nonfinite(v);
+  }
+  return ex | nonfinite(s.T) | nonfinite(s.qv) | nonfinite(s.qc) | nonfinite(s.qr) | nonfinite(s.qi) |
          nonfinite(s.qs) | nonfinite(s.qg) | nonfinite(s.nc) | nonfinite(s.nr) | nonfinite(s.ni) |
          nonfinite(s.ns) | nonfinite(s.ng) | nonfinite(s.na);
 }
@@ -1426,7 +1449,8 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
     double *np = state + (8 + x) * fs;
     // the species' sixth moment (triple-moment policies: rain, or r, i, s, g)
     const bool tri = x < nz3<M>();
-    double *zp = a.fld + (16 + x) * fs;
+    // fields after the inputs: in tendency mode their rows of tend (field f at row f - 3)
+    double *zp = kTend ? tend + (13 + x) * fs : a.fld + (16 + x) * fs;
     R cmax = 0;
     for (int k = 0; k < a.nlev; ++k) {
       const size_t o = (size_t)k * a.pitch + c;
@@ -1449,7 +1473,7 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
     const double dts = a.dt / ns;
     // the rain's aerosol mass moves with the rain (aerosol-mass policies)
     const bool aer = x < na3<M>();
-    double *ap = a.fld + (18 + x) * fs;
+    double *ap = kTend ? tend + (15 + x) * fs : a.fld + (18 + x) * fs;
     for (int st = 0; st < ns; ++st) {
       R Fu = 0, Gu = 0, Au = 0, Hu = 0;
       for (int k = a.nlev - 1; k >= 0; --k) {
@@ -1698,7 +1722,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       eflag |= w.hmax >= 0x7ff00000u;
     }
     if constexpr (kTend) {
-      eflag |= store_tend<M::kWarm>(a, tend, k, c, s, fast);
+      eflag |= store_tend<M>(a, tend, k, c, s, fast);
     } else if constexpr (M::kWarm) {
       if (touched) eflag |= store_pt_warm<M::kAero, M::kTri>(a, k, c, s);
     } else {
@@ -1748,6 +1772,9 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
           const bool ice = (f >= 4 && f <= 6) || (f >= 9 && f <= 11);
           if (!(M::kWarm && ice)) tend[f * fs + o] = (tend[f * fs + o] - a.fld[f * fs + o]) / a.dt;
         }
+#pragma unroll
+        for (int e = 0; e < nextra<M>(); ++e)
+          tend[(13 + e) * fs + o] = (tend[(13 + e) * fs + o] - a.fld[(16 + e) * fs + o]) / a.dt;
       }
     }
   }

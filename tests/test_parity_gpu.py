@@ -553,11 +553,10 @@ def test_aerosol_context_rules():
     ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM | casim.CASIM_AEROSOL)
     try:
         d = casim.Domain(fld, dz, 64)
-        tend = torch.zeros((16, 40, d.pitch), dtype=torch.float64, device="cuda")
-        with pytest.raises(RuntimeError):
-            casim.casim_step_tendency(ctx, d.state, 64, 40, 1.0, tend)
-        with pytest.raises(RuntimeError):
+        with pytest.raises(RuntimeError):                 # the batched entry points have no aerosol variant
             casim.casim_batch_create(ctx, [d.state], [64], [40])
+        with pytest.raises(RuntimeError):                 # tend overlapping the state
+            casim.casim_step_tendency(ctx, d.state, 64, 40, 1.0, d.fld[1:])
     finally:
         casim.casim_free(ctx)
 
@@ -756,15 +755,8 @@ def test_three_moment_context_rules():
     ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_WARM | casim.CASIM_THREE_MOMENT)
     try:
         d = casim.Domain(fld, dz, 64)
-        tend = torch.zeros((14, 40, d.pitch), dtype=torch.float64, device="cuda")
-        with pytest.raises(RuntimeError):
-            casim.casim_step_tendency(ctx, d.state, 64, 40, 1.0, tend)
-        with pytest.raises(RuntimeError):
+        with pytest.raises(RuntimeError):                 # the batched entry points have no triple-moment variant
             casim.casim_batch_create(ctx, [d.state], [64], [40])
-        h = fld.copy()
-        with pytest.raises(RuntimeError):
-            casim.casim_step_host(ctx, casim.make_state(h, d.pitch, np.ascontiguousarray(dz),
-                                                        np.zeros((4, d.pitch))), 64, 40, 1.0)
     finally:
         casim.casim_free(ctx)
 
@@ -896,6 +888,71 @@ def test_stratus_512x512x150_sampled_columns(stratus_full, config):
             a_, b_, i_ = got[f], ref[f, :, :n], sub[f, :, :n]
             bound = 1e-3 * np.abs(b_ - i_) + 1e-4 * np.abs(b_) + 1e-16 * fld[f].max()
             assert (np.abs(a_ - b_) <= bound).all(), (sp, float((np.abs(a_ - b_) / bound).max()))
+
+
+# ------------------------- source-term and host entry points, every configuration
+EXT_CONFIGS = {
+    "warm_aerosol": (lambda n, l, seed: _aero_state(n, l, seed), lambda: casim.CASIM_WARM | casim.CASIM_AEROSOL),
+    "cold_aerosol": (lambda n, l, seed: _aero_cold_state(n, l, seed), lambda: casim.CASIM_AEROSOL),
+    "warm_three_moment": (lambda n, l, seed: _tri_state(n, l, seed),
+                          lambda: casim.CASIM_WARM | casim.CASIM_THREE_MOMENT),
+    "cold_three_moment": (lambda n, l, seed: _tri_cold_state(n, l, seed), lambda: casim.CASIM_THREE_MOMENT),
+}
+
+
+@pytest.mark.parametrize("config", list(EXT_CONFIGS))
+@pytest.mark.parametrize("precision", [casim.CASIM_FP64, casim.CASIM_MIXED])
+@pytest.mark.parametrize("dt", [1.0, 30.0])
+def test_extended_tendency_and_host_entry_points(config, precision, dt):
+    """The aerosol-mass and triple-moment configurations through the
+    source-term mode (state untouched; tend rows 0..12 and 13.. for the fields
+    after the inputs, each (x_after - x_before) / dt of the in-place step, bit
+    for bit) and the host-buffer entry point (whole-domain and chunked paths,
+    bit for bit); dt = 30 s takes the multi-substep sedimentation path."""
+    import torch
+    make, flags = EXT_CONFIGS[config]
+    ncols, nlev = 200, 60
+    fld, dz = make(ncols, nlev, 91)
+    nf, pitch = fld.shape[0], fld.shape[2]
+    out, pr, _ = run_gpu(fld, dz, ncols, dt, precision=precision, flags=flags())
+    ctx = casim.casim_init(precision=precision, flags=flags())
+    try:
+        d = casim.Domain(fld, dz, ncols)
+        tend = torch.full((nf - 3, nlev, pitch), float("nan"), dtype=torch.float64, device="cuda")
+        casim.casim_step_tendency(ctx, d.state, ncols, nlev, dt, tend)
+        rc, fl = casim.casim_get_error(ctx)
+        assert rc == 0, (rc, fl)
+        f2, p2 = d.numpy()
+        assert np.array_equal(f2, fld) and np.array_equal(p2, pr)
+        rows = list(range(13)) + list(range(16, nf))
+        t = tend.cpu().numpy()[:, :, :ncols]
+        assert np.array_equal(t, (out[rows, :, :ncols] - fld[rows, :, :ncols]) / dt)
+        # host entry point: one chunk, then many (a wide domain copied column-chunk-wise)
+        h = np.ascontiguousarray(fld.copy())
+        hpr = np.zeros(pr.shape)
+        casim.casim_step_host(ctx, casim.make_state(h, pitch, np.ascontiguousarray(dz), hpr), ncols, nlev, dt)
+        assert np.array_equal(h, out) and np.array_equal(hpr, pr)
+    finally:
+        casim.casim_free(ctx)
+
+
+def test_extended_host_entry_point_in_chunks():
+    """More columns than one host chunk (65 536): the chunked pipeline moves
+    every field of the extended state, bit for bit against the device step."""
+    for config in ("cold_aerosol", "cold_three_moment"):
+        make, flags = EXT_CONFIGS[config]
+        ncols, nlev = 70_000, 12
+        fld, dz = make(ncols, nlev, 92)
+        out, pr, _ = run_gpu(fld, dz, ncols, 1.0, precision=casim.CASIM_MIXED, flags=flags())
+        ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=flags())
+        try:
+            h = np.ascontiguousarray(fld.copy())
+            hpr = np.zeros(pr.shape)
+            casim.casim_step_host(ctx, casim.make_state(h, fld.shape[2], np.ascontiguousarray(dz), hpr),
+                                  ncols, nlev, 1.0)
+            assert np.array_equal(h, out) and np.array_equal(hpr, pr), config
+        finally:
+            casim.casim_free(ctx)
 
 
 # ------------------------------------------------------------------ checkpoint / resume
