@@ -225,6 +225,15 @@ int casim_step_host(casim_ctx *ctx, const casim_state *host, int ncols, int nlev
    Asynchronous on `stream`. */
 int casim_budget(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double *out, void *stream);
 
+/* Failure detection without a fault: run the bounded wait every
+   tensor-core kernel uses on a barrier that nothing completes, with a limit
+   of limit_ns (1 ns .. 2 s, the kernels' own limit; CASIM_ERR_ARG outside),
+   so that it gives up; the kernel records that in the context's error word
+   (casim_get_error then returns CASIM_ERR_TIMEOUT with CASIM_EFLAG_TIMEOUT)
+   and the context stays usable.  Synchronises `stream`; *elapsed_ns
+   receives how long the wait lasted on the device. */
+int casim_wait_selftest(casim_ctx *ctx, long long limit_ns, long long *elapsed_ns, void *stream);
+
 /* Wait for `stream`, read and clear the device error word.  *flags receives the
    CASIM_EFLAG_* bits (may be NULL).  Returns CASIM_OK, CASIM_ERR_NONFINITE or
    CASIM_ERR_CFL (the first set, in that order of precedence, after CASIM_ERR_TIMEOUT),

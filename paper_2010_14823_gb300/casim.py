@@ -100,6 +100,8 @@ def lib():
             getattr(L, name).restype = i
         L.casim_budget.restype = i
         L.casim_get_error.argtypes = [vp, ctypes.POINTER(u), vp]
+        L.casim_wait_selftest.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong), vp]
+        L.casim_wait_selftest.restype = i
         L.casim_get_error.restype = i
         L.casim_launch_count.argtypes = [vp]
         L.casim_launch_count.restype = ctypes.c_longlong
@@ -227,6 +229,14 @@ def casim_step_tendency(ctx, state: casim_state, ncols: int, nlev: int, dt: floa
     """Source-term mode: state unchanged, tend [13][nlev][pitch] (device) = (x_after - x_before) / dt."""
     _check(lib().casim_step_tendency(ctx, ctypes.byref(state), ncols, nlev, dt, _ptr(tend), _stream(stream)),
            "casim_step_tendency")
+
+
+def casim_wait_selftest(ctx, limit_ns: int, stream=None) -> int:
+    """Run the kernels' bounded wait on a barrier nothing completes; returns
+    how long it waited (ns).  The give-up is left in the error word."""
+    el = ctypes.c_longlong(0)
+    _check(lib().casim_wait_selftest(ctx, limit_ns, ctypes.byref(el), _stream(stream)), "casim_wait_selftest")
+    return el.value
 
 
 def casim_step_host(ctx, state: casim_state, ncols: int, nlev: int, dt: float, stream=None):

@@ -497,6 +497,24 @@ extern "C" int casim_get_error(casim_ctx *ctx, unsigned *flags, void *stream) {
 }
 
 
+extern "C" int casim_wait_selftest(casim_ctx *ctx, long long limit_ns, long long *elapsed_ns, void *stream) {
+  NvtxRange nvtx_range_("casim_wait_selftest");
+  if (!ctx || limit_ns < 1 || limit_ns > (long long)kWaitLimitNs || !elapsed_ns) return CASIM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long *d_el = nullptr;
+  CUDA_TRY(cudaMalloc(&d_el, sizeof(unsigned long long)));
+  k_wait_selftest<<<1, 32, 0, st>>>((uint64_t)limit_ns, ctx->d_err, d_el);
+  ctx->launches++;
+  cudaError_t e = cudaGetLastError();
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d_el, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(d_el);
+  if (e != cudaSuccess) return cuda_fail(e, "casim_wait_selftest");
+  *elapsed_ns = (long long)h;
+  return CASIM_OK;
+}
+
 // ------------------------------------------------------------------ batches
 struct casim_batch {
   casim_ctx *ctx = nullptr;

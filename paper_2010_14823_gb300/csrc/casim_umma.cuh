@@ -158,13 +158,35 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, unsigned
 }
 // bounded wait that also gives up early once `abort` is set by another thread
 __device__ __forceinline__ bool bar_wait_or_abort(uint32_t bar, uint32_t parity, unsigned spins,
-                                                  const volatile int *abort) {
+                                                  const volatile int *abort, uint64_t limit_ns = kWaitLimitNs) {
   const uint64_t t0 = global_ns();
   for (unsigned i = 0; i < spins; ++i) {
     if (bar_try(bar, parity)) return true;
-    if ((i & 63u) == 63u && (*abort || global_ns() - t0 > kWaitLimitNs)) return false;
+    if ((i & 63u) == 63u && (*abort || global_ns() - t0 > limit_ns)) return false;
   }
   return false;
+}
+
+// The bounded wait on its own: one thread waits on an mbarrier that nothing
+// arrives at (phase 0 never completes) through the waits' own code, gives up
+// after limit_ns, and records that in the error word as the kernels do.  No
+// copy, MMA or tensor memory is involved, so there is nothing to drain.
+__global__ void k_wait_selftest(uint64_t limit_ns, unsigned *err, unsigned long long *elapsed) {
+  __shared__ alignas(8) unsigned long long s_bar;
+  __shared__ int s_abort;
+  const uint32_t bar = smem_addr(&s_bar);
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    bar_init(bar, 1);
+    bar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint64_t t0 = global_ns();
+    const bool ok = bar_wait_or_abort(bar, 0u, 0xffffffffu, &s_abort, limit_ns);
+    *elapsed = global_ns() - t0;
+    if (!ok) atomicOr(err, 4u);
+  }
 }
 // 1-D bulk copy global -> shared, completing on the mbarrier (16-byte aligned, size a multiple of 16)
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {

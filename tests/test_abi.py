@@ -61,6 +61,8 @@ def test_argument_errors_without_touching_the_device(L):
     assert L.casim_step(None, ctypes.byref(st), 1, 1, 1.0, None) == -1
     assert L.casim_get_error(None, None, None) == -1
     assert L.casim_launch_count(None) == -1
+    el = ctypes.c_longlong(0)
+    assert L.casim_wait_selftest(None, 1000, ctypes.byref(el), None) == -1
     L.casim_free(None)
     bad = casim.casim_default_params()
     bad.q_min = -1.0

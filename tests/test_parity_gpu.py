@@ -1005,3 +1005,32 @@ def test_checkpoint_resume_is_bitwise(tmp_path, state):
             casim.casim_state_load(str(tmp_path / "missing"), b.state, ncols, nlev, nf)
     finally:
         casim.casim_free(ctx)
+
+
+# ------------------------------------------------------------------ failure detection
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """The tensor-core kernels' bounded wait, run on a barrier nothing
+    completes, gives up after its limit and reports it through the error
+    word (no fault, no hang); the same context then steps normally."""
+    fld, dz, ncols, nlev, dt, _ = synth.workload("stratus_16x16x50")
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED)
+    try:
+        el = casim.casim_wait_selftest(ctx, 20_000_000)
+        assert 20_000_000 <= el < 1_000_000_000, el
+        rc, flags = casim.casim_get_error(ctx)
+        assert rc == -6 and flags & casim.EFLAG_TIMEOUT, (rc, flags)
+        assert casim.casim_get_error(ctx)[0] == 0                 # read and cleared
+        d = casim.Domain(fld, dz, ncols)
+        casim.casim_step(ctx, d.state, ncols, nlev, dt)
+        assert casim.casim_get_error(ctx)[0] == 0
+        out, pr = d.numpy()
+    finally:
+        casim.casim_free(ctx)
+    ref, pref, _ = run_gpu(fld, dz, ncols, dt, precision=casim.CASIM_MIXED)
+    assert np.array_equal(out, ref) and np.array_equal(pr, pref)
+    with pytest.raises(RuntimeError):
+        ctx = casim.casim_init(precision=casim.CASIM_MIXED)
+        try:
+            casim.casim_wait_selftest(ctx, 3_000_000_000)            # beyond the kernels' own limit
+        finally:
+            casim.casim_free(ctx)
