@@ -396,7 +396,8 @@ def bench_peaks(args, rank, world, local):
     import torch
     from paper_2010_14823_gb300 import peaks
     torch.cuda.set_device(local)
-    iters = {"ffma": 1 << 18, "dfma": 1 << 12, "ex2": 1 << 16, "lg2": 1 << 15, "rcp": 1 << 15, "tanh": 1 << 15}
+    iters = {"ffma": 1 << 18, "dfma": 1 << 12, "ex2": 1 << 16, "lg2": 1 << 15, "rcp": 1 << 15, "tanh": 1 << 15,
+             "tanh_bf16x2": 1 << 15}
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     sampler = ClockSampler(local)
     sampler.start()

@@ -10,7 +10,8 @@
  * kernel of (SM count x 8) blocks x 256 threads in which every thread runs 8
  * independent chains of `iters` dependent operations of one kind, after one
  * untimed launch, and writes the operations per second to *rate.  A fused
- * multiply-add counts as one operation (two FLOPs).  The chains are kept on a
+ * multiply-add counts as one operation (two FLOPs); a packed bf16x2
+ * instruction as two.  The chains are kept on a
  * bounded orbit (x -> f(x) with a constant offset where needed; the offset's
  * addition runs on another pipe and is not counted), and each thread writes
  * its result so that no chain is removed by the compiler.
@@ -32,7 +33,8 @@ extern "C" {
 #define CASIM_PEAK_LG2 3    /* lg2.approx.ftz.f32: x = log2(x) + 2 */
 #define CASIM_PEAK_RCP 4    /* rcp.approx.ftz.f32: x = 1/x + 1 */
 #define CASIM_PEAK_TANH 5   /* tanh.approx.f32: x = tanh(x) + 0.5 */
-#define CASIM_PEAK_NKINDS 6
+#define CASIM_PEAK_TANH2 6  /* tanh.approx.bf16x2 on packed pairs: two operations per instruction */
+#define CASIM_PEAK_NKINDS 7
 
 #define CASIM_PEAK_ERR_ARG (-1)
 #define CASIM_PEAK_ERR_CUDA (-2)

@@ -1,6 +1,7 @@
 // Instruction-throughput probes (see include/casim_peaks.h): each thread runs
 // 8 independent chains of one operation, so that every scheduler always has
 // independent work for the unit under test.
+#include <cstdint>
 #include <cuda_runtime.h>
 
 #include "casim_peaks.h"
@@ -31,11 +32,30 @@ __device__ __forceinline__ float tanha(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// packed pair: x -> tanh(x) + 0.5 on both halves (bf16x2 add)
+__device__ __forceinline__ uint32_t tanh2(uint32_t x) {
+  uint32_t y;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
+  asm("add.rn.bf16x2 %0, %1, %2;" : "=r"(y) : "r"(y), "r"(0x3f003f00u));
+  return y;
+}
 
 template <int K>
 __global__ void __launch_bounds__(kThreads) k_peak(long long iters, double *out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if constexpr (K == CASIM_PEAK_DFMA) {
+  if constexpr (K == CASIM_PEAK_TANH2) {
+    uint32_t x[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) x[i] = 0x3f203f30u + (uint32_t)i;   // pairs near 0.62
+    for (long long n = 0; n < iters; ++n) {
+#pragma unroll
+      for (int i = 0; i < kChains; ++i) x[i] = tanh2(x[i]);
+    }
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) s ^= x[i];
+    out[t] = (double)s;
+  } else if constexpr (K == CASIM_PEAK_DFMA) {
     double x[kChains];
 #pragma unroll
     for (int i = 0; i < kChains; ++i) x[i] = 0.5 + 0.01 * i + 1e-7 * (t & 63);
@@ -82,6 +102,7 @@ cudaError_t launch_kind(int kind, int blocks, long long iters, double *out, cuda
     case CASIM_PEAK_EX2: return launch<CASIM_PEAK_EX2>(blocks, iters, out, st);
     case CASIM_PEAK_LG2: return launch<CASIM_PEAK_LG2>(blocks, iters, out, st);
     case CASIM_PEAK_RCP: return launch<CASIM_PEAK_RCP>(blocks, iters, out, st);
+    case CASIM_PEAK_TANH2: return launch<CASIM_PEAK_TANH2>(blocks, iters, out, st);
     default: return launch<CASIM_PEAK_TANH>(blocks, iters, out, st);
   }
 }
@@ -111,6 +132,7 @@ extern "C" int casim_peak_rate(int kind, long long iters, void *stream, double *
   if (e1) cudaEventDestroy(e1);
   if (out) cudaFree(out);
   if (e != cudaSuccess || !(ms > 0.f)) return CASIM_PEAK_ERR_CUDA;
-  *rate = 3.0 * (double)blocks * kThreads * kChains * (double)iters / (ms * 1e-3);
+  const double per = kind == CASIM_PEAK_TANH2 ? 2.0 : 1.0;   // operations per instruction
+  *rate = 3.0 * per * (double)blocks * kThreads * kChains * (double)iters / (ms * 1e-3);
   return 0;
 }

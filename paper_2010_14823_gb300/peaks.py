@@ -7,7 +7,7 @@ import os
 
 from .build import PEAKS_LIB
 
-KINDS = {"ffma": 0, "dfma": 1, "ex2": 2, "lg2": 3, "rcp": 4, "tanh": 5}
+KINDS = {"ffma": 0, "dfma": 1, "ex2": 2, "lg2": 3, "rcp": 4, "tanh": 5, "tanh_bf16x2": 6}
 _lib = None
 
 
