@@ -51,6 +51,47 @@ MEASURED_FP64_OPS = {"kernel": "k_step<PolicyF64>", "inst_per_point": 750.99,
                      "sha256": "4b1951cbc97854bc5c74cf9bcefc73fa8135a7b4793b87b98ecdba27e6da06ff"}
 
 
+def _host_link_gbs(torch, stream, nbytes: int = 1 << 30):
+    """The host link as this run sees it: 1 GB pinned <-> device copies timed with CUDA
+    events (one warm-up each), host to device alone, device to host alone, and both at
+    once on two streams (GB/s counting both directions).  The host memory and link of
+    the box may be shared with other jobs, so the end-to-end rate is read against this."""
+    n = nbytes // 8
+    h_in = torch.ones(n, dtype=torch.float64).pin_memory()
+    h_out = torch.empty(n, dtype=torch.float64).pin_memory()
+    d_a = torch.empty(n, dtype=torch.float64, device="cuda")
+    d_b = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s2 = torch.cuda.Stream()
+
+    def timed(fn, nb):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return nb / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+    def both():
+        start = torch.cuda.Event()
+        start.record(stream)
+        s2.wait_event(start)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_b, non_blocking=True)
+        d_a.copy_(h_in, non_blocking=True)
+        done = torch.cuda.Event()
+        done.record(s2)
+        stream.wait_event(done)
+
+    with torch.cuda.stream(stream):
+        r = {"h2d": timed(lambda: d_a.copy_(h_in, non_blocking=True), nbytes),
+             "d2h": timed(lambda: h_out.copy_(d_b, non_blocking=True), nbytes),
+             "both": timed(both, 2 * nbytes)}
+    del h_in, h_out, d_a, d_b
+    return r
+
+
 def _kernel_source_sha() -> str:
     import hashlib
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), MEASURED_TRAFFIC["source"])
@@ -760,6 +801,7 @@ def main():
 
     # end to end through the host entry point: pinned host state, copies inside the timed region
     e2e = None
+    link = _host_link_gbs(torch, stream) if args.e2e_steps > 0 else None
     if args.e2e_steps > 0:
         pitch = dom.pitch
         hfld = torch.from_numpy(base_fld).pin_memory()
@@ -779,7 +821,10 @@ def main():
         d2h = 13 * nlev * pitch * 8 + hpr.numel() * 8
         e2e = {"value": world * npts * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-               "path": "casim_step_host: pinned host state; H2D + step + D2H per step, 65 536-column chunks pipelined over 3 streams"}
+               "path": "casim_step_host: pinned host state; H2D + step + D2H per step, 65 536-column chunks pipelined over 3 streams",
+               "host_link_gbs": link,
+               "copy_gbs": (h2d + d2h) * args.e2e_steps / e2e_s / 1e9,
+               "link_frac": (h2d + d2h) * args.e2e_steps / e2e_s / 1e9 / link["both"] if link else None}
 
     accuracy = None
     if args.acc_steps > 0 and {"mixed", "fp64"} <= forms:
