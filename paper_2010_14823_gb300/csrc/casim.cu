@@ -647,10 +647,19 @@ static BatchArgs batch_args(const casim_batch *b, double dt) {
   return a;
 }
 
+// the mixed form's batch kernel for a block size: blocks of up to 128 threads
+// take the instantiation with the single-domain step's register budget
+// (96 registers, 5 blocks of 128 per SM), wider blocks the 128-register one
+template <class M>
+static auto batch_kernel(int block) {
+  if constexpr (M::kMixed) return block <= kBatchNarrowBlock ? k_step_batch<M, true> : k_step_batch<M, false>;
+  else return k_step_batch<M, false>;
+}
+
 template <class M>
 static int persistent_grid(const casim_batch *b) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch<M>, b->block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<M>(b->block), b->block, 0);
   return std::max(1, per_sm) * b->ctx->nsm;
 }
 
@@ -671,10 +680,10 @@ static int enqueue_batch_step(casim_batch *b, double dt, cudaStream_t st) {
   if (b->persistent) CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
   if (ctx->precision == CASIM_MIXED) {
     const int grid = b->persistent ? std::min(b->nitems, persistent_grid<PolicyMix>(b)) : b->nitems;
-    k_step_batch<PolicyMix><<<grid, b->block, 0, st>>>(a, ctx->kp);
+    batch_kernel<PolicyMix>(b->block)<<<grid, b->block, 0, st>>>(a, ctx->kp);
   } else {
     const int grid = b->persistent ? std::min(b->nitems, persistent_grid<PolicyF64>(b)) : b->nitems;
-    k_step_batch<PolicyF64><<<grid, b->block, 0, st>>>(a, ctx->kp);
+    batch_kernel<PolicyF64>(b->block)<<<grid, b->block, 0, st>>>(a, ctx->kp);
   }
   ctx->launches++;
   CUDA_TRY(cudaGetLastError());
@@ -930,12 +939,12 @@ extern "C" int casim_step_noalloc(const casim_params *params, int precision, con
   int per_sm = 1;
   if (precision == CASIM_MIXED) {
     k_compact<PolicyMix><<<ntiles, kTile, 0, st>>>(a, sc->tiles, ntiles, kp);
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch<PolicyMix>, kTile, 0));
-    k_step_batch<PolicyMix><<<std::min(ntiles, std::max(1, per_sm) * nsm), kTile, 0, st>>>(a, kp);
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<PolicyMix>(kTile), kTile, 0));
+    batch_kernel<PolicyMix>(kTile)<<<std::min(ntiles, std::max(1, per_sm) * nsm), kTile, 0, st>>>(a, kp);
   } else {
     k_compact<PolicyF64><<<ntiles, kTile, 0, st>>>(a, sc->tiles, ntiles, kp);
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch<PolicyF64>, kTile, 0));
-    k_step_batch<PolicyF64><<<std::min(ntiles, std::max(1, per_sm) * nsm), kTile, 0, st>>>(a, kp);
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<PolicyF64>(kTile), kTile, 0));
+    batch_kernel<PolicyF64>(kTile)<<<std::min(ntiles, std::max(1, per_sm) * nsm), kTile, 0, st>>>(a, kp);
   }
   CUDA_TRY(cudaGetLastError());
   if (flags) {

@@ -18,6 +18,7 @@
 namespace casim_dev {
 
 constexpr int kBatchMaxBlock = 256;
+constexpr int kBatchNarrowBlock = 128;
 constexpr int kTile = 128;   // columns per block of the compaction pass
 
 struct DomDesc {
@@ -102,8 +103,13 @@ __global__ void __launch_bounds__(kTile) k_compact(const BatchArgs b, const Item
   }
 }
 
-template <class M>
-__global__ void __launch_bounds__(kBatchMaxBlock, M::kMixed ? 2 : 1) k_step_batch(const BatchArgs b, const KParams P) {
+// kNarrow: built for blocks of at most kBatchNarrowBlock threads with the
+// policy's register budget (the single-domain step's blocks per SM); else for
+// blocks up to kBatchMaxBlock
+template <class M, bool kNarrow = false>
+__global__ void __launch_bounds__(kNarrow ? kBatchNarrowBlock : kBatchMaxBlock,
+                                  kNarrow ? M::kMinBlocks : (M::kMixed ? 2 : 1))
+    k_step_batch(const BatchArgs b, const KParams P) {
   __shared__ double s_dz[kMaxLev];
   __shared__ double s_dzdt[kMaxLev];
   __shared__ int s_item;
@@ -153,8 +159,9 @@ __global__ void __launch_bounds__(kBatchMaxBlock, M::kMixed ? 2 : 1) k_step_batc
         eflag |= run_column<M>(a, P, s_dz, s_dzdt, fast, c);
       }
     }
-    // shared memory (item, dz) is reused by the next iteration
-    __syncthreads();
+    // shared memory (item, dz) is reused by the next item; with one item per
+    // block there is none, and the warps leave as they finish
+    if (b.persistent) __syncthreads();
   }
   if (eflag) atomicOr(b.err, eflag);
 }
