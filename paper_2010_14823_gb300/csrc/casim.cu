@@ -647,13 +647,12 @@ static BatchArgs batch_args(const casim_batch *b, double dt) {
   return a;
 }
 
-// the mixed form's batch kernel for a block size: blocks of up to 128 threads
-// take the instantiation with the single-domain step's register budget
-// (96 registers, 5 blocks of 128 per SM), wider blocks the 128-register one
+// the batch kernel for a block size: blocks of up to 128 threads take the
+// instantiation with the single-domain step's register budget (mixed: 5
+// blocks of 128 per SM, FP64: 3), wider blocks the one built for 256
 template <class M>
 static auto batch_kernel(int block) {
-  if constexpr (M::kMixed) return block <= kBatchNarrowBlock ? k_step_batch<M, true> : k_step_batch<M, false>;
-  else return k_step_batch<M, false>;
+  return block <= kBatchNarrowBlock ? k_step_batch<M, true> : k_step_batch<M, false>;
 }
 
 template <class M>
