@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 F = synth.FIDX
 RTOL64 = 1e-12
 ATOL = np.array([1e-10] + [1e-20] * 6 + [1e-6] * 6)   # T, 6 masses, 6 numbers (incl. n_a)
+QMIN = casim.casim_default_params().q_min              # a species is present above this
 
 
 def run_gpu(fld, dz, ncols, dt, nsteps=1, precision=casim.CASIM_FP64, check_err=True, flags=0):
@@ -51,6 +52,12 @@ def assert_fp64_close(out, pr, ref, pr_ref, ncols, rtol=RTOL64):
                                np.argwhere(bad)[:3].tolist())
     e = np.abs(pr[:, :ncols] - pr_ref[:, :ncols])
     assert np.all(e <= rtol * np.abs(pr_ref[:, :ncols]) + 1e-20), float(e.max())
+    # branch flips: presence decisions (q > q_min) taken differently by the
+    # GPU and the oracle, per hydrometeor mass
+    flips = {synth.FIELDS[f]: int(((out[f, :, :ncols] > QMIN) != (ref[f, :, :ncols] > QMIN)).sum())
+             for f in range(2, 7)}
+    print("presence-decision flips, GPU FP64 vs oracle:", flips)
+    assert not any(flips.values()), flips
 
 
 def test_stratus_16x16x50_fp64():
