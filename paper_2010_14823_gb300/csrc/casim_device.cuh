@@ -1222,7 +1222,9 @@ using Mix = MixT<PolicyMix>;
 // ice process runs and only rain sediments.
 struct PolicyF64Warm : PolicyF64 {
   static constexpr bool kWarm = true;
-  static constexpr int kMinBlocks = 4;
+  // measured on 512x512x150 stratus: 4 / 5 / 6 -> 52.3-54.3 / 49.0 / 50.4 ms per step (96
+  // registers and no spills at 5, also in the aerosol and triple-moment warm forms)
+  static constexpr int kMinBlocks = 5;
 };
 struct PolicyMixWarm : PolicyMix {
   static constexpr bool kWarm = true;
