@@ -33,12 +33,12 @@ WORKLOAD = "deep_512x512x150"
 
 # DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one ncu
 # capture of a 65 536-column x 150-level launch (dram__bytes_read.sum +
-# dram__bytes_write.sum = 2.2186 GB for 9.83 M points); reads are 16 fields per
+# dram__bytes_write.sum = 2.2195 GB for 9.83 M points); reads are 16 fields per
 # point and writes follow the changed points, so the traffic scales with the
 # points processed.  Valid only for the kernel source it was taken on.
-MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.69,
+MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.78,
                     "source": "paper_2010_14823_gb300/csrc/casim_device.cuh",
-                    "sha256": "e0a41679f3da62c38722f8bff72b8750ea0faa67c50b4709e5fb8dec85149fd4"}
+                    "sha256": "21b439d3df2993a275ecc6f5c6d9399cc277290105e455b1a058f7ffcfee5a4c"}
 
 
 # FP64 arithmetic instructions of k_step<PolicyF64> per point on the same
@@ -48,7 +48,7 @@ MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.69,
 # busy.  Valid only for the kernel source it was taken on.
 MEASURED_FP64_OPS = {"kernel": "k_step<PolicyF64>", "inst_per_point": 750.99,
                      "dfma": 475.34, "dadd": 120.62, "dmul": 155.03, "fp64_pipe_active": 0.723,
-                     "sha256": "e0a41679f3da62c38722f8bff72b8750ea0faa67c50b4709e5fb8dec85149fd4"}
+                     "sha256": "21b439d3df2993a275ecc6f5c6d9399cc277290105e455b1a058f7ffcfee5a4c"}
 
 
 def _host_link_gbs(torch, stream, nbytes: int = 1 << 30):
