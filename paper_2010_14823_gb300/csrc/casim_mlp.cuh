@@ -456,15 +456,28 @@ __global__ void __launch_bounds__(256) k_mlp_features(const KArgs a, const KPara
       }
     }
   }
-  // warp-aggregated append of the rows
+  // block-aggregated append of the rows: one atomic on the row counter per
+  // block (a counter that every warp hits serialises in L2), the warps'
+  // offsets from a prefix sum of their counts; rows come in no set order
+  // (each carries its point)
+  __shared__ unsigned s_off[256 / 32];
+  __shared__ unsigned long long s_base;
   const unsigned ball = __ballot_sync(0xffffffffu, warm);
-  if (!ball) return;
-  const int lane = threadIdx.x & 31;
-  unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(fa.rows, (unsigned long long)__popc(ball));
-  base = __shfl_sync(0xffffffffu, base, 0);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) s_off[wid] = __popc(ball);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tot = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      const unsigned t = s_off[i];
+      s_off[i] = tot;
+      tot += t;
+    }
+    s_base = tot ? atomicAdd(fa.rows, (unsigned long long)tot) : 0ull;
+  }
+  __syncthreads();
   if (!warm) return;
-  const long long row = (long long)base + __popc(ball & ((1u << lane) - 1u));
+  const long long row = (long long)(s_base + s_off[wid]) + __popc(ball & ((1u << lane) - 1u));
   if (row >= fa.cap) return;   // the caller sees rows > cap and reports it
   if (fa.mode == 0) {
     if (fa.rowpt) fa.rowpt[row] = pt;
