@@ -334,6 +334,42 @@ def test_rate_regimes():
     assert abs(O.rates(s4, 1.0)["aut"] / (1350 * 5e-4 ** 2.47 * 100.0 ** -1.79) - 1) < 1e-12
 
 
+def test_self_collection_scaling_and_number_only():
+    """Seifert-Beheng self-collection: the cloud-number loss goes as the
+    square of the cloud water and does not depend on the droplet number, the
+    rain-number loss as n_r q_r, both linearly with the air density, and
+    neither exists without its species.  The process moves no mass: in
+    saturated warm air holding only rain (no adjustment, no evaporation, no
+    cloud processes), a point update changes the rain number alone, by dt
+    times the rate."""
+    rho = 1.1
+    cloud = dict(qc=1e-4, nc=1e8 / rho, rho=rho)
+    scc = lambda **kw: O.rates(_state(**{**cloud, **kw}), 1.0)["scc"]
+    c0 = scc()
+    assert c0 > 0.0
+    assert abs(scc(qc=2e-4) / c0 - 4.0) < 1e-13
+    assert scc(nc=3e8 / rho) == c0
+    assert abs(scc(rho=2 * rho) / c0 - 2.0) < 1e-13
+    assert scc(qc=0.5 * P("q_min")) == 0.0
+    rain = dict(qr=1e-4, nr=1e3, rho=rho)
+    scr = lambda **kw: O.rates(_state(**{**rain, **kw}), 1.0)["scr"]
+    r0 = scr()
+    assert r0 > 0.0
+    assert abs(scr(nr=2e3) / r0 - 2.0) < 1e-13
+    assert abs(scr(qr=3e-4) / r0 - 3.0) < 1e-13
+    assert abs(scr(rho=2 * rho) / r0 - 2.0) < 1e-13
+    assert scr(qr=0.5 * P("q_min")) == 0.0
+    T, p, dt = 285.0, 9e4, 1.0
+    st = _state(T=T, p=p, rho=rho, qv=O.qsat(O.es_liq(T), p), qr=1e-4, nr=1e3)
+    R = O.rates(st, dt)
+    assert R["evr"] == 0.0 and R["aut"] == 0.0 and R["acc"] == 0.0
+    out = O.point(st, dt)
+    for name in ("T", "qv", "qc", "qr", "qi", "qs", "qg", "nc", "ni", "ns", "ng"):
+        assert out[F[name]] == st[F[name]], name
+    assert abs(out[F["nr"]] - (st[F["nr"]] - dt * R["scr"])) <= 4 * np.spacing(st[F["nr"]])
+    assert out[F["nr"]] < st[F["nr"]]
+
+
 # ------------------------------------------------------------ a10 limiter
 def _liq(s):
     return s[F["qc"]] + s[F["qr"]]
