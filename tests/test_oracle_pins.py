@@ -370,6 +370,39 @@ def test_self_collection_scaling_and_number_only():
     assert out[F["nr"]] < st[F["nr"]]
 
 
+def test_ice_nucleation_closed_form_and_bookkeeping():
+    """Meyers et al. (1992) ice nucleation below T_nuc: the crystal number
+    grows as exp(c (S_i - 1)) with the ice supersaturation, the crystals
+    already present are subtracted, the difference is made within the step
+    (rate ~ 1/dt) and counted per kg of air (~ 1/rho); each new crystal has
+    mass m_i0, taken from the vapour, with the heat of sublimation."""
+    T, p, rho = P("T_nuc") - 5.0, 6e4, 0.8
+    qsi = O.qsat(O.es_ice(T), p)
+    assert qsi < O.qsat(O.es_liq(T), p)
+    nuc = lambda Si, ni=0.0, dt=1.0, r=rho: O.rates(_state(T=T, p=p, rho=r, qv=Si * qsi, ni=ni), dt)["nuc"]
+    r1, r2 = nuc(1.02), nuc(1.07)
+    assert r1 > 0.0
+    assert abs(r2 / r1 / math.exp(P("mey_c") * 0.05) - 1.0) < 1e-12
+    n_in = r1 * 1.0                      # crystals per kg made in a 1 s step from none
+    assert abs(nuc(1.02, ni=0.25 * n_in) / r1 - 0.75) < 1e-12
+    assert nuc(1.02, ni=n_in * (1 + 1e-9)) == 0.0
+    assert abs(nuc(1.02, dt=4.0) / r1 - 0.25) < 1e-12
+    assert abs(nuc(1.02, r=2 * rho) / r1 - 0.5) < 1e-12
+    # point update: vapour -> ice only through nucleation (no ice to grow on,
+    # liquid subsaturated, no cloud or rain)
+    dt = 1.0
+    st = _state(T=T, p=p, rho=rho, qv=1.05 * qsi)
+    R = O.rates(st, dt)
+    out = O.point(st, dt)
+    dn = out[F["ni"]] - st[F["ni"]]
+    dq = out[F["qi"]] - st[F["qi"]]
+    assert abs(dn / (dt * R["nuc"]) - 1.0) < 1e-12
+    assert abs(dq / (P("m_i0") * dn) - 1.0) < 1e-12
+    assert abs((out[F["qv"]] - st[F["qv"]]) + dq) <= 8 * np.spacing(st[F["qv"]])
+    # cp dT = (Lv + Lf) dq up to the rounding of the new temperature (dT is ~1e-6 K)
+    assert abs(P("cp") * (out[F["T"]] - T) - (P("Lv") + P("Lf")) * dq) <= 4 * P("cp") * np.spacing(T)
+
+
 # ------------------------------------------------------------ a10 limiter
 def _liq(s):
     return s[F["qc"]] + s[F["qr"]]
