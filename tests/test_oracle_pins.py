@@ -403,6 +403,28 @@ def test_ice_nucleation_closed_form_and_bookkeeping():
     assert abs(P("cp") * (out[F["T"]] - T) - (P("Lv") + P("Lf")) * dq) <= 4 * P("cp") * np.spacing(T)
 
 
+@pytest.mark.parametrize("sp", ["i", "s", "g"])
+def test_melting_moves_mass_number_and_heat(sp):
+    """Melting above 0 C, isolated (saturated air holding one ice species and
+    nothing else: no evaporation, deposition or collection): the melted mass
+    goes to rain, the species' number moves to rain in proportion to its mass
+    (the mean mass is kept), and the heat of fusion comes from the air."""
+    T, p, rho, dt = 275.0, 9e4, 1.1, 1.0
+    q, n = 1e-4, 1e4
+    st = _state(T=T, p=p, rho=rho, qv=O.qsat(O.es_liq(T), p), **{"q" + sp: q, "n" + sp: n})
+    R = O.rates(st, dt)
+    assert {k for k, v in R.items() if v != 0.0} == {"mlt" + sp}
+    out = O.point(st, dt)
+    dq = out[F["q" + sp]] - q
+    dn = out[F["n" + sp]] - n
+    assert abs(dq / (-dt * R["mlt" + sp]) - 1.0) < 1e-12
+    assert abs(out[F["qr"]] + dq) <= 4 * np.spacing(q)
+    assert abs(dn / (dq * n / q) - 1.0) < 1e-12
+    assert abs(out[F["nr"]] + dn) <= 4 * np.spacing(n)
+    assert out[F["qv"]] == st[F["qv"]]
+    assert abs(P("cp") * (out[F["T"]] - T) - P("Lf") * dq) <= 4 * P("cp") * np.spacing(T)
+
+
 # ------------------------------------------------------------ a10 limiter
 def _liq(s):
     return s[F["qc"]] + s[F["qr"]]
