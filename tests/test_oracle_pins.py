@@ -425,6 +425,24 @@ def test_melting_moves_mass_number_and_heat(sp):
     assert abs(P("cp") * (out[F["T"]] - T) - P("Lf") * dq) <= 4 * P("cp") * np.spacing(T)
 
 
+def test_rain_evaporation_moves_mass_number_and_heat():
+    """Rain evaporating in subsaturated warm air with no cloud: the vapour
+    gains the evaporated mass, the rain number falls in proportion to the
+    mass (plus rain self-collection, the one other process acting), and the
+    heat of vaporisation comes from the air."""
+    T, p, rho, dt = 288.0, 9e4, 1.08, 1.0
+    q, n = 2e-4, 2e3
+    st = _state(T=T, p=p, rho=rho, qv=0.7 * O.qsat(O.es_liq(T), p), qr=q, nr=n)
+    R = O.rates(st, dt)
+    assert {k for k, v in R.items() if v != 0.0} == {"evr", "scr"}
+    out = O.point(st, dt)
+    dq = out[F["qr"]] - q
+    assert abs(dq / (-dt * R["evr"]) - 1.0) < 1e-12
+    assert abs(out[F["qv"]] - st[F["qv"]] + dq) <= 4 * np.spacing(st[F["qv"]])
+    assert abs((out[F["nr"]] - n) / (dq * n / q - dt * R["scr"]) - 1.0) < 1e-12
+    assert abs(P("cp") * (out[F["T"]] - T) - P("Lv") * dq) <= 4 * P("cp") * np.spacing(T)
+
+
 # ------------------------------------------------------------ a10 limiter
 def _liq(s):
     return s[F["qc"]] + s[F["qr"]]
