@@ -443,6 +443,33 @@ def test_rain_evaporation_moves_mass_number_and_heat():
     assert abs(P("cp") * (out[F["T"]] - T) - P("Lv") * dq) <= 4 * P("cp") * np.spacing(T)
 
 
+@pytest.mark.parametrize("sp", ["i", "s", "g"])
+@pytest.mark.parametrize("regime", ["growth", "sublimation"])
+def test_deposition_moves_mass_number_and_heat(sp, regime):
+    """Vapour deposition on one ice species, isolated (270 K: below 0 C,
+    above the nucleation threshold; no liquid): growth keeps the crystal
+    number; sublimation removes crystals in proportion to the mass; the
+    vapour balances the ice mass and the heat of sublimation the air."""
+    T, p, rho, dt = 270.0, 8e4, 1.0, 1.0
+    q, n = 1e-4, 1e4
+    qsi, qsl = O.qsat(O.es_ice(T), p), O.qsat(O.es_liq(T), p)
+    assert T > P("T_nuc") and qsi < qsl
+    qv = 0.5 * (qsi + qsl) if regime == "growth" else 0.8 * qsi
+    st = _state(T=T, p=p, rho=rho, qv=qv, **{"q" + sp: q, "n" + sp: n})
+    R = O.rates(st, dt)
+    assert {k for k, v in R.items() if v != 0.0} == {"dep" + sp}
+    assert (R["dep" + sp] > 0.0) == (regime == "growth")
+    out = O.point(st, dt)
+    dq = out[F["q" + sp]] - q
+    assert abs(dq / (dt * R["dep" + sp]) - 1.0) < 1e-12
+    assert abs(out[F["qv"]] - qv + dq) <= 4 * np.spacing(qv)
+    if regime == "growth":
+        assert out[F["n" + sp]] == n
+    else:
+        assert abs((out[F["n" + sp]] - n) / (dq * n / q) - 1.0) < 1e-12
+    assert abs(P("cp") * (out[F["T"]] - T) - (P("Lv") + P("Lf")) * dq) <= 4 * P("cp") * np.spacing(T)
+
+
 # ------------------------------------------------------------ a10 limiter
 def _liq(s):
     return s[F["qc"]] + s[F["qr"]]
