@@ -75,3 +75,45 @@ def test_param_count_and_layout():
     assert np.array_equal(mlp.flatten(mlp.unflatten(theta)), theta)
     W1, b1 = mlp.unflatten(theta)[0]
     assert W1[0, 1] == 1 and W1[1, 0] == 256 and b1[0] == 12 * 256
+
+
+def test_surrogate_targets_and_masks_follow_the_scheme():
+    """The surrogate's targets are the natural logs of the scheme oracle's four
+    warm-rain rates, defined exactly where the scheme computes each (cloud:
+    autoconversion and cloud self-collection; cloud and rain: accretion;
+    rain: rain self-collection), and its features recover the state they
+    came from."""
+    import oracle as O
+    from oracle import surrogate as OS
+    from paper_2010_14823_gb300 import synth
+    F = synth.FIDX
+
+    def state(**kw):
+        st = np.zeros(16)
+        base = dict(T=285.0, qv=8e-3, p=9e4, rho=1.1, na=1e8, w=0.3)
+        base.update(kw)
+        for k, v in base.items():
+            st[F[k]] = v
+        return st
+
+    cases = {(1, 0, 1, 0): dict(qc=3e-4, nc=1e8),
+             (0, 0, 0, 1): dict(qr=1e-4, nr=1e3),
+             (1, 1, 1, 1): dict(qc=3e-4, nc=1e8, qr=1e-4, nr=1e3)}
+    for mask, kw in cases.items():
+        st = state(**kw)
+        y, m = OS.targets(st, 1.0)
+        assert tuple(int(v) for v in m) == mask
+        r = O.rates(st, 1.0)
+        for j, name in enumerate(("aut", "acc", "scc", "scr")):
+            if m[j]:
+                assert abs(np.exp(y[j]) / r[name] - 1.0) < 1e-14
+            else:
+                assert y[j] == 0.0
+        f = OS.features(st)
+        assert OS.warm(st)
+        for j, name in ((0, "qc"), (1, "qr"), (2, "nc"), (3, "nr")):
+            if st[F[name]] > 0:
+                assert abs(np.exp(f[j]) / st[F[name]] - 1.0) < 1e-14
+        assert f[5] == st[F["T"]] - 273.15 and f[8] == st[F["w"]]
+        assert (f[10], f[11]) == (float(st[F["qc"]] > 1e-14), float(st[F["qr"]] > 1e-14))
+    assert not OS.warm(state())
