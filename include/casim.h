@@ -390,7 +390,11 @@ void casim_mlp_free(casim_mlp *mlp);
  *  - params may be NULL (defaults).  If flags is non-NULL the call waits for
  *    `stream`, stores the CASIM_EFLAG_* bits of this step in *flags and
  *    returns CASIM_ERR_NONFINITE / CASIM_ERR_CFL when they are set; if NULL it
- *    returns after enqueuing. */
+ *    returns after enqueuing, and the step's error bits are never reported:
+ *    the next call clears them before it runs.  A caller that must learn of
+ *    non-finite values or the substep cap passes flags.
+ *  - Host threads may make their first call on a device concurrently (the
+ *    address lookup is thread-safe); their GPU work must still be ordered. */
 #define CASIM_NOALLOC_MAX_COLS (1 << 20)
 int casim_step_noalloc(const casim_params *params, int precision, const casim_state *s, int ncols, int nlev,
                        double dt, void *stream, unsigned *flags);

@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -863,17 +864,22 @@ __global__ void k_noalloc_dzmin(NoallocScratch *sc) {
 static NoallocScratch *noalloc_scratch_ptr(int dev, int *rc) {
   // set-up once per device, with that device current; host code must not
   // take the address of the __device__ array directly (that would be the
-  // host-side stand-in, not device memory)
-  static NoallocScratch *ptrs[64] = {nullptr};
+  // host-side stand-in, not device memory).  Host threads making their first
+  // call on one device at the same time may both look the address up; they
+  // find the same value, and the atomic entries make the concurrent stores
+  // and loads well defined.
+  static std::atomic<NoallocScratch *> ptrs[64];
   if (dev < 0 || dev >= 64) { *rc = CASIM_ERR_ARG; return nullptr; }
-  if (!ptrs[dev]) {
+  NoallocScratch *cached = ptrs[dev].load(std::memory_order_acquire);
+  if (!cached) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) { *rc = cuda_fail(e, "cudaGetSymbolAddress"); return nullptr; }
-    ptrs[dev] = static_cast<NoallocScratch *>(p);
+    cached = static_cast<NoallocScratch *>(p);
+    ptrs[dev].store(cached, std::memory_order_release);
   }
   *rc = CASIM_OK;
-  return ptrs[dev];
+  return cached;
 }
 
 extern "C" int casim_step_noalloc(const casim_params *params, int precision, const casim_state *s, int ncols,
@@ -967,8 +973,6 @@ struct casim_mlp {
   float *wsplit = nullptr;        // split-K partial weight gradients [kSplitMax][256][256]
   unsigned *d_err = nullptr;
   int engine = 1;                 // 1: tcgen05 inference, 0: mma.sync
-  int umma_cluster = 1;           // CTAs per cluster of the tcgen05 kernel (shared weight stream)
-  int umma_max_clusters = 0;      // co-resident clusters of that size (persistent grid)
   float *norm = nullptr;   // [12 mean][12 sd][4 mean][4 sd]
   float *box = nullptr;    // [12 lo][12 hi]
   bool fitted = false;
@@ -1099,45 +1103,6 @@ static void mlp_cast(casim_mlp *m, cudaStream_t st) {
   k_mlp_images<<<(kNh * kNh + 255) / 256, 256, 0, st>>>(m->theta, m->img);
 }
 
-template <int C>
-static cudaError_t launch_umma_cluster(const UmmaArgs &u, int clusters, cudaStream_t st) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(clusters * C));
-  cfg.blockDim = dim3(kUmmaThreads);
-  cfg.dynamicSmemBytes = kUmmaSmem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = C;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_mlp_umma<C>, u);
-}
-
-// co-resident clusters of C CTAs of the tcgen05 kernel (0: none fit)
-template <int C>
-static int umma_max_clusters() {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(C);
-  cfg.blockDim = dim3(kUmmaThreads);
-  cfg.dynamicSmemBytes = kUmmaSmem;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = C;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_mlp_umma<C>, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return n;
-}
-
 // forward pass of n rows of BF16 inputs on the tcgen05 kernel: rates at the
 // rows' points (rowpt) or standardised outputs in m->y (rowpt null)
 static cudaError_t mlp_forward_umma(casim_mlp *m, const __nv_bfloat16 *xb, long long n, const long long *rowpt,
@@ -1154,12 +1119,8 @@ static cudaError_t mlp_forward_umma(casim_mlp *m, const __nv_bfloat16 *xb, long 
   u.err = err;
   const long long tiles = (n + 127) / 128;
   if (tiles == 0) return cudaSuccess;
-  if (m->umma_cluster == 2) {
-    const int clusters = (int)std::min<long long>((tiles + 1) / 2, m->umma_max_clusters);
-    return launch_umma_cluster<2>(u, clusters, st);
-  }
   const int grid = (int)std::min<long long>(tiles, nsm);
-  k_mlp_umma<1><<<grid, kUmmaThreads, kUmmaSmem, st>>>(u);
+  k_mlp_umma<<<grid, kUmmaThreads, kUmmaSmem, st>>>(u);
   return cudaGetLastError();
 }
 
@@ -1203,16 +1164,7 @@ extern "C" int casim_mlp_create(casim_mlp **out, unsigned long long seed) {
   if (e == cudaSuccess) e = dalloc(&m->wsplit, (size_t)kSplitMax * kNh * kNh);
   if (e == cudaSuccess) e = dalloc(&m->d_err, 1);
   if (e == cudaSuccess) e = cudaMemset(m->d_err, 0, sizeof(unsigned));
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_umma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_umma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
-  if (e == cudaSuccess) {
-    // pairs of CTAs share the weight stream when enough pairs fit at once
-    int dev = 0, nsm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    m->umma_max_clusters = umma_max_clusters<2>();
-    m->umma_cluster = 2 * m->umma_max_clusters >= (nsm * 3) / 4 ? 2 : 1;
-  }
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
   if (e == cudaSuccess) e = cudaMemcpy(m->theta, th.data(), kNParam * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->m1, 0, kNParam * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->m2, 0, kNParam * sizeof(float));

@@ -578,7 +578,7 @@ constexpr uint32_t kTmA0 = 0, kTmA1 = 256, kTmFeat = 504;
 constexpr int kUmmaSmem = 1024 + kSmRing + kUmmaStages * kImgChunk;
 static_assert(kUmmaSmem + 4096 <= 232448, "shared memory of the tensor-core kernel");
 
-// Persistent, one CTA (18 warps) per SM, clusters of C CTAs, 128-row tiles.
+// Persistent, one CTA (18 warps) per SM, 128-row tiles.
 //
 // Tensor memory holds two 256-column FP32 accumulators used by alternate
 // layers (layer 1 -> A0, 2 -> A1, 3 -> A0, 4 -> A1), so the MMAs of layer
@@ -597,19 +597,12 @@ static_assert(kUmmaSmem + 4096 <= 232448, "shared memory of the tensor-core kern
 //    after the last slab it commits the accumulator to acc;
 //  * producer warp (one thread): streams the 8 weight chunks of layers 2-3
 //    per tile through the ring (full/free barriers).
-// The C CTAs of a cluster walk tile groups together (CTA r takes tile C*g+r
-// of group g; a tile past the end computes on zero rows and stores nothing),
-// so they consume the same chunk sequence: CTA r copies the chunks i with
-// i % C == r into the ring of every CTA of the cluster (multicast), and every
-// CTA's MMA thread commits each consumed chunk to the free barrier of every
-// CTA, so a stage is refilled only when all C CTAs are done with it.  Weight
-// traffic from L2 is 256 KB per C tiles.  N = 256 MMAs read each A slab once
+// Weight traffic from L2 is 256 KB per tile.  N = 256 MMAs read each A slab once
 // (N = 128 halves would read it twice): shared-memory operand bandwidth, not
 // the tensor pipe, bounds these MMAs.
 // Every wait is bounded and gives up once any thread of the CTA has set the
 // abort flag; before the tensor memory is released and the CTA leaves, all
 // MMAs, copies and arrivals from or to this CTA have completed.
-template <int C>
 __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) {
   extern __shared__ __align__(16) unsigned char sraw[];
   unsigned char *sm = sraw + ((1024 - (smem_addr(sraw) & 1023)) & 1023);
@@ -619,11 +612,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long ntiles = (u.rows + 127) / 128;
-  const long long ngroups = (ntiles + C - 1) / C;
-  const int rank = C > 1 ? (int)cluster_ctarank() : 0;
-  const long long cluster = blockIdx.x / C, nclusters = gridDim.x / C;
-  const long long my_groups = cluster < ngroups ? (ngroups - 1 - cluster) / nclusters + 1 : 0;
-  const uint16_t all = (uint16_t)((1u << C) - 1u);
+  const long long cta = blockIdx.x, ncta = gridDim.x;
+  const long long my_tiles = cta < ntiles ? (ntiles - 1 - cta) / ncta + 1 : 0;
   const uint32_t sb = smem_addr(sm);
   volatile int *abort = &s_abort;
   enum { B_W = 0, B_FEAT = 1, B_ACC = 2, B_ACT = 3, B_FULL = 7, B_FREE = 7 + kUmmaStages, B_DRAIN = 7 + 2 * kUmmaStages };
@@ -651,7 +641,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
     for (int s = 0; s < 4; ++s) bar_init(bar(B_ACT + s), kUmmaEpiWarps);
     for (int s = 0; s < kUmmaStages; ++s) {
       bar_init(bar(B_FULL + s), 1);
-      bar_init(bar(B_FREE + s), C);
+      bar_init(bar(B_FREE + s), 1);
     }
     bar_init(bar(B_DRAIN), 1);
     bar_fence_init();
@@ -660,8 +650,6 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  // the peers' barriers exist before any copy or commit reaches them
-  if constexpr (C > 1) cluster_sync_all();
   const uint32_t taddr = s_tmem;
 
   if (warp == kUmmaProdWarp) {
@@ -670,9 +658,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
       bulk_load(sb + kSmW1, u.img, kImgW1, bar(B_W));
       bulk_load(sb + kSmW4, u.img + kImgW1 + kImgChunks * kImgChunk, kImgW4, bar(B_W));
       // load i goes to stage i % S as that stage's (i / S)-th fill; from the
-      // second fill on it waits until all C CTAs' MMAs of the previous fill
-      // have completed
-      const long long nch = my_groups * kImgChunks;
+      // second fill on it waits until the MMAs of the previous fill have
+      // completed
+      const long long nch = my_tiles * kImgChunks;
       long long i = 0;
       for (; i < nch; ++i) {
         const int st = (int)(i % kUmmaStages);
@@ -684,14 +672,10 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
         bar_expect_tx(bar(B_FULL + st), kImgChunk);
         const uint32_t dst = sb + kSmRing + (uint32_t)st * kImgChunk;
         const unsigned char *src = u.img + kImgW1 + (uint32_t)(i % kImgChunks) * kImgChunk;
-        if constexpr (C > 1) {
-          if ((int)(i % C) == rank) bulk_load_multicast(dst, src, kImgChunk, bar(B_FULL + st), all);
-        } else {
-          bulk_load(dst, src, kImgChunk, bar(B_FULL + st));
-        }
+        bulk_load(dst, src, kImgChunk, bar(B_FULL + st));
       }
       // drain: the copies into this CTA have landed (last fill of each
-      // stage), and so have all C CTAs' commits of those fills
+      // stage), and so have the commits of those fills
       bar_wait(bar(B_W), 0, kUmmaSpins);
       for (int st = 0; st < kUmmaStages && st < i; ++st) {
         const long long fills = (i - st + kUmmaStages - 1) / kUmmaStages;
@@ -706,7 +690,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
       bool ok = bar_wait_or_abort(bar(B_W), 0, kUmmaSpins, abort);
       int nfeat = 0, nact = 0;
       long long chunk = 0;
-      for (long long it = 0; ok && it < my_groups; ++it) {
+      for (long long it = 0; ok && it < my_tiles; ++it) {
         ok = bar_wait_or_abort(bar(B_FEAT), (uint32_t)(nfeat++ & 1), kUmmaSpins, abort);
         if (!ok) break;
         tc_fence_after();
@@ -729,8 +713,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
             for (int sub = 0; sub < 4; ++sub)
               umma_bf16_ts(dacc, ain + 64u * (uint32_t)s + 16u * (uint32_t)sub, umma_desc_sw128(wst + 32u * (uint32_t)sub),
                            id256, (s | sub) ? 1u : 0u);
-            if constexpr (C > 1) umma_commit_multicast(bar(B_FREE + st), all);
-            else umma_commit(bar(B_FREE + st));
+            umma_commit(bar(B_FREE + st));
             ++chunk;
           }
           if (ok) umma_commit(bar(B_ACC));
@@ -766,16 +749,16 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
     auto load_features = [&](long long g) {
       f0 = make_uint4(0, 0, 0, 0);
       f1 = f0;
-      const long long r = (g * C + rank) * 128 + row;
-      if (g < ngroups && r < u.rows) {
+      const long long r = g * 128 + row;
+      if (g < ntiles && r < u.rows) {
         const uint4 *src = reinterpret_cast<const uint4 *>(u.xb + r * kNinPad);
         f0 = src[0];
         f1 = src[1];
       }
     };
-    if (j == 0) load_features(cluster);
-    for (long long g = cluster; ok && g < ngroups; g += nclusters) {
-      const long long r0 = (g * C + rank) * 128;
+    if (j == 0) load_features(cta);
+    for (long long g = cta; ok && g < ntiles; g += ncta) {
+      const long long r0 = g * 128;
       // every epilogue warp arrives: the next tile's layer-1 MMA (which
       // overwrites A0) waits until all of them have seen the previous
       // tile's last accumulator phase; the features go to tensor memory
@@ -788,7 +771,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
       }
       __syncwarp();
       if (lane == 0) bar_arrive(bar(B_FEAT));
-      if (j == 0) load_features(g + nclusters);
+      if (j == 0) load_features(g + ncta);
       for (int l = 0; l < 3; ++l) {
         ok = bar_wait_or_abort(bar(B_ACC), (uint32_t)(nacc++ & 1), kUmmaSpins, abort);
         if (!ok) break;
@@ -842,8 +825,6 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
   __syncthreads();
   tc_fence_after();
   if (warp == kUmmaMmaWarp) tmem_dealloc(taddr, 512);
-  // no CTA leaves while a peer may still copy or arrive into it
-  if constexpr (C > 1) cluster_sync_all();
 }
 
 }  // namespace casim_dev
