@@ -30,6 +30,11 @@ def test_reference_arm_prints_the_contract_line():
     assert d["higher_is_better"] is True and d["scaling"] in ("weak", "strong")
     assert d["vs_baseline"] is None and d["data"] == "synthetic" and d["dtype"] == "f64"
     assert d["config"]["workload"] == bench.WORKLOAD
+    # the line reports what was timed: the sample's columns, K steps of it
+    c = d["config"]
+    assert c["ncols"] % 32 == 0 and 0 < c["ncols"] <= c["sample_of_ncols"]
+    assert d["ms_per_step"] * d["steps"] == pytest.approx(c["timed_s"] * 1e3, rel=1e-9)
+    assert d["value"] == pytest.approx(c["ncols"] * c["nlev"] / (d["ms_per_step"] * 1e-3), rel=1e-9)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]
