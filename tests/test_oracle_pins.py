@@ -329,9 +329,49 @@ def test_rate_regimes():
     r1, r2, r3 = (O.rates(s, 1.0)["aut"] for s in (s1, s2, s3))
     assert abs(r2 / r1 - 2 ** P("kk_aut_qc")) < 1e-12
     assert abs(r3 / r1 - 2 ** P("kk_aut_nc")) < 1e-12
-    # 100 cm^-3 and 0.5 g/kg: the value KK2000 gives in its own units
-    s4 = _state(qc=5e-4, nc=1e8 / rho, rho=rho)
-    assert abs(O.rates(s4, 1.0)["aut"] / (1350 * 5e-4 ** 2.47 * 100.0 ** -1.79) - 1) < 1e-12
+
+
+def test_kk2000_point_values_worked_by_hand():
+    """Khairoutdinov & Kogan (2000) in their own units (q in kg/kg, N_c in
+    cm^-3, rates in kg kg^-1 s^-1), evaluated by hand in logarithms (seven
+    digits each) at q_c = 0.5 g/kg, N_c = 100 cm^-3, q_r = 0.1 g/kg:
+      autoconversion 1350 q_c^2.47 N_c^-1.79:
+        ln 1350 = 7.2078599, ln 5e-4 = -7.6009025, ln 100 = 4.6051702
+        7.2078599 + 2.47 (-7.6009025) - 1.79 (4.6051702)
+          = 7.2078599 - 18.7742292 - 8.2432547 = -19.8096240
+        exp(-19.8096240) = e^-20 e^0.1903760 = 2.0611536e-9 x 1.2097 = 2.4934e-9
+      accretion 67 (q_c q_r)^1.15:
+        ln 67 = 4.2046926, ln 5e-8 = -16.8112428
+        4.2046926 + 1.15 (-16.8112428) = 4.2046926 - 19.3329292 = -15.1282366
+        exp(-15.1282366) = e^-15 e^-0.1282366 = 3.0590232e-7 x 0.879646 = 2.6909e-7
+    The droplet number is given per kg of air: 100 cm^-3 at rho = 1.1 kg m^-3
+    is 1e8 / 1.1 per kg."""
+    rho = 1.1
+    R = O.rates(_state(qc=5e-4, nc=1e8 / rho, qr=1e-4, nr=1e4, rho=rho), 1.0)
+    assert abs(R["aut"] / 2.4934e-9 - 1.0) < 5e-5
+    assert abs(R["acc"] / 2.6909e-7 - 1.0) < 5e-5
+
+
+def test_accretion_scaling_and_presence():
+    """KK2000 accretion is a power of the product q_c q_r: doubling either
+    water content multiplies it by 2^1.15 (a law with the exponent on one
+    factor only would give 2 for the other), it does not depend on either
+    number concentration or on the air density, and it is zero unless both
+    cloud and rain are present (above q_min)."""
+    rho = 1.1
+    base = dict(qc=3e-4, nc=1.5e8, qr=2e-4, nr=5e3, rho=rho)
+    acc = lambda **kw: O.rates(_state(**{**base, **kw}), 1.0)["acc"]
+    a0 = acc()
+    assert a0 > 0.0
+    assert abs(acc(qc=6e-4) / a0 - 2.0 ** 1.15) < 1e-13
+    assert abs(acc(qr=4e-4) / a0 - 2.0 ** 1.15) < 1e-13
+    assert abs(acc(qc=6e-4, qr=1e-4) / a0 - 1.0) < 1e-13
+    assert acc(nc=4e8) == a0 and acc(nr=9e4) == a0
+    assert acc(rho=0.6) == a0
+    q_min = P("q_min")
+    assert acc(qc=q_min) == 0.0 and acc(qr=q_min) == 0.0
+    assert acc(qc=0.5 * q_min) == 0.0 and acc(qr=0.5 * q_min) == 0.0
+    assert acc(qc=2 * q_min) > 0.0 and acc(qr=2 * q_min) > 0.0
 
 
 def test_self_collection_scaling_and_number_only():
