@@ -33,12 +33,12 @@ WORKLOAD = "deep_512x512x150"
 
 # DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one ncu
 # capture of a 65 536-column x 150-level launch (dram__bytes_read.sum +
-# dram__bytes_write.sum = 2.2195 GB for 9.83 M points); reads are 16 fields per
+# dram__bytes_write.sum = 2.2197 GB for 9.83 M points); reads are 16 fields per
 # point and writes follow the changed points, so the traffic scales with the
 # points processed.  Valid only for the kernel source it was taken on.
-MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.78,
+MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.80,
                     "source": "paper_2010_14823_gb300/csrc/casim_device.cuh",
-                    "sha256": "21b439d3df2993a275ecc6f5c6d9399cc277290105e455b1a058f7ffcfee5a4c"}
+                    "sha256": "8a311e4612e8c54fb4eafa703ca5f74ca863cd918f7f5255a4f9f9956e3ebf64"}
 
 
 # FP64 arithmetic instructions of k_step<PolicyF64> per point on the same

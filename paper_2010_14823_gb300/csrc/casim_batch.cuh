@@ -112,7 +112,10 @@ __global__ void __launch_bounds__(kNarrow ? kBatchNarrowBlock : kBatchMaxBlock,
     k_step_batch(const BatchArgs b, const KParams P) {
   __shared__ double s_dz[kMaxLev];
   __shared__ double s_dzdt[kMaxLev];
+  __shared__ float s_dtdz_f[kMaxLev];
+  __shared__ float s_dzdt_f[kMaxLev];
   __shared__ int s_item;
+  const LevelTab lt{s_dz, s_dzdt, s_dtdz_f, s_dzdt_f};
   const int B = blockDim.x;
   const int tid = threadIdx.x;
   unsigned eflag = 0;
@@ -132,11 +135,7 @@ __global__ void __launch_bounds__(kNarrow ? kBatchNarrowBlock : kBatchMaxBlock,
     const int n = b.compact ? b.count[item.dom] : d.ncols;
     if (item.chunk * B < n) {
       if (item.dom != prev_dom) {
-        for (int k = tid; k < d.nlev; k += B) {
-          const double v = d.dz[k];
-          s_dz[k] = v;
-          s_dzdt[k] = v / b.dt;
-        }
+        for (int k = tid; k < d.nlev; k += B) level_tab(s_dz, s_dzdt, s_dtdz_f, s_dzdt_f, k, d.dz[k], b.dt);
         __syncthreads();
         prev_dom = item.dom;
       }
@@ -156,7 +155,7 @@ __global__ void __launch_bounds__(kNarrow ? kBatchNarrowBlock : kBatchMaxBlock,
         a.nlev = d.nlev;
         a.dt = b.dt;
         a.surr = nullptr;
-        eflag |= run_column<M>(a, P, s_dz, s_dzdt, fast, c);
+        eflag |= run_column<M>(a, P, lt, fast, c);
       }
     }
     // shared memory (item, dz) is reused by the next item; with one item per

@@ -201,12 +201,17 @@ def test_training_reduces_loss_and_surrogate_step():
 
 
 def test_what_the_trained_network_gains_over_the_scheme():
-    """The network is judged by the scheme it replaces.  Training buys
-    accuracy (held-out rate error far below an untrained network's); the
-    surrogate step then follows the plain step closely over many steps.  It
-    buys no speed: the scheme's closed-form rates cost a few MUFU operations
-    per point, the network ~2.7e5 FLOP, so the surrogate step is slower --
-    the measured ratio is reported, not asserted as a gain."""
+    """What the trained network gains over the scheme it replaces, asserted
+    on both sides of the ledger and judged by the scheme itself:
+      * accuracy against the scheme: the held-out median error of each of the
+        four rates is below 15 %, and training bought it (each at most a
+        quarter of an untrained network's, which is ~100 %); over 20 steps the
+        surrogate step's surface precipitation stays within 1 % of the plain
+        step's;
+      * speed: none.  The scheme's closed-form rates cost a few MUFU
+        operations per point, the network ~2.7e5 FLOP plus a feature pass, so
+        the surrogate step is slower than the plain step; the test asserts
+        that finding (surrogate time > plain time) rather than a gain."""
     import time
     ctx = casim.casim_init(precision=casim.CASIM_MIXED)
     trained, untrained = casim.casim_mlp_create(seed=8), casim.casim_mlp_create(seed=8)
@@ -246,7 +251,7 @@ def test_what_the_trained_network_gains_over_the_scheme():
 
         et, eu = rel_err(trained), rel_err(untrained)
         print("held-out median relative rate error: trained", et, "untrained", eu)
-        assert np.all(et < 0.15) and np.all(et < 0.1 * eu)
+        assert np.all(et < 0.15) and np.all(et < 0.25 * eu)
         # 20 steps: surrogate vs plain from the same state, judged by the plain step
         f2 = d.numpy()[0]
         plain, surr = casim.Domain(f2, dz, ncols), casim.Domain(f2, dz, ncols)
@@ -266,6 +271,7 @@ def test_what_the_trained_network_gains_over_the_scheme():
         print("20-step precipitation: plain %.6e surrogate %.6e (rel %.2e); time per step plain %.3f ms, "
               "surrogate %.3f ms" % (pp, ps, abs(ps - pp) / pp, (t1 - t0) * 50, (t2 - t1) * 50))
         assert abs(ps - pp) <= 1e-2 * pp
+        assert t2 - t1 > t1 - t0, "the surrogate step was measured faster than the closed-form scheme"
     finally:
         casim.casim_mlp_free(trained)
         casim.casim_mlp_free(untrained)
