@@ -290,6 +290,25 @@ int casim_batch_tune_steps(int steps);
 int casim_batch_graph(casim_ctx *ctx, casim_batch *batch, double dt, int nsteps, void *stream);
 int casim_batch_graph_launch(casim_batch *batch, void *stream);
 
+/* One call per timestep for many domains (Section 3.2: the host makes one
+   call per timestep, which runs the whole scheme for every column; here the
+   columns of ndom domains of different sizes go in one launch).  Arguments
+   as for casim_batch_create, plus dt (> 0, s) and `stream`.  Results are,
+   bit for bit, those of casim_step on each domain.
+   The context keeps the batch object of the last domain list it was given
+   and reuses it while the same list comes back (same state pointers, pitches,
+   ncols, nlev); a different list replaces it.  Building a batch reads every
+   domain's dz and synchronises the device, so the first call with a list is
+   not asynchronous; later calls with that list are (one or two launches on
+   `stream`).  As for casim_batch_create, dz must not change while its list
+   is in use; the launch configuration is the batch default (block 128,
+   compaction, persistent grid); tune a batch object with casim_batch_tune
+   where that matters.  The cached batch is released by casim_free.
+   Errors: CASIM_ERR_ARG for invalid arguments or a context with CASIM_WARM,
+   CASIM_AEROSOL or CASIM_THREE_MOMENT; CASIM_ERR_OOM; CASIM_ERR_CUDA. */
+int casim_step_batched(casim_ctx *ctx, const casim_state *domains, const int *ncols, const int *nlev, int ndom,
+                       double dt, void *stream);
+
 /* Total columns of the batch (sum of ncols). */
 long long casim_batch_columns(const casim_batch *batch);
 

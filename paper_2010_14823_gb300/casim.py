@@ -116,6 +116,8 @@ def lib():
         L.casim_batch_create.restype = i
         L.casim_batch_step.argtypes = [vp, vp, d, vp]
         L.casim_batch_step.restype = i
+        L.casim_step_batched.argtypes = [vp, ps, pi, pi, i, d, vp]
+        L.casim_step_batched.restype = i
         L.casim_batch_config.argtypes = [vp, i, i, i]
         L.casim_batch_config.restype = i
         L.casim_batch_get_config.argtypes = [vp, pi, pi, pi]
@@ -295,6 +297,15 @@ def casim_batch_create(ctx, states, ncols, nlev):
 
 def casim_batch_step(ctx, batch, dt: float, stream=None):
     _check(lib().casim_batch_step(ctx, batch, dt, _stream(stream)), "casim_batch_step")
+
+
+def casim_step_batched(ctx, states, ncols, nlev, dt: float, stream=None):
+    """One step of many domains (the context keeps the batch of the last list)."""
+    n = len(states)
+    arr = (casim_state * n)(*states)
+    nc = (ctypes.c_int * n)(*ncols)
+    nl = (ctypes.c_int * n)(*nlev)
+    _check(lib().casim_step_batched(ctx, arr, nc, nl, n, dt, _stream(stream)), "casim_step_batched")
 
 
 def casim_batch_config(batch, block: int, compact: int, persistent: int):

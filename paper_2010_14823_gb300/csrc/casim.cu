@@ -53,6 +53,11 @@ struct casim_ctx {
   size_t cap_fld[kStages] = {}, cap_precip[kStages] = {}, cap_dz = 0;
   cudaStream_t hst[kStages] = {};
   cudaEvent_t hev_start = nullptr, hev_dz = nullptr;
+  // casim_step_batched: the batch of the last domain list it was given, and
+  // that list (a different list replaces the batch)
+  casim_batch *sb = nullptr;
+  std::vector<casim_state> sb_dom;
+  std::vector<int> sb_ncols, sb_nlev;
 };
 
 static thread_local char g_last_error[256] = "";
@@ -807,6 +812,37 @@ extern "C" int casim_batch_graph_launch(casim_batch *b, void *stream) {
 }
 
 extern "C" long long casim_batch_columns(const casim_batch *b) { return b ? b->total_cols : -1; }
+
+// One call per timestep for many domains (the paper's one call per step that
+// runs the whole scheme over every column, Section 3.2, with several domains
+// in one launch).  The batch object is built on the first call and kept in
+// the context while the same domain list comes back.
+extern "C" int casim_step_batched(casim_ctx *ctx, const casim_state *domains, const int *ncols, const int *nlev,
+                                  int ndom, double dt, void *stream) {
+  NvtxRange nvtx_range_("casim_step_batched");
+  if (!ctx || ndom < 1 || !domains || !ncols || !nlev || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
+  bool same = ctx->sb && (int)ctx->sb_dom.size() == ndom;
+  for (int i = 0; same && i < ndom; ++i) {
+    const casim_state &a = ctx->sb_dom[i], &b = domains[i];
+    same = a.fld == b.fld && a.pitch == b.pitch && a.dz == b.dz && a.precip == b.precip &&
+           ctx->sb_ncols[i] == ncols[i] && ctx->sb_nlev[i] == nlev[i];
+  }
+  if (!same) {
+    casim_batch_free(ctx->sb);
+    ctx->sb = nullptr;
+    ctx->sb_dom.clear();
+    ctx->sb_ncols.clear();
+    ctx->sb_nlev.clear();
+    casim_batch *b = nullptr;
+    const int rc = casim_batch_create(ctx, domains, ncols, nlev, ndom, &b);
+    if (rc != CASIM_OK) return rc;
+    ctx->sb = b;
+    ctx->sb_dom.assign(domains, domains + ndom);
+    ctx->sb_ncols.assign(ncols, ncols + ndom);
+    ctx->sb_nlev.assign(nlev, nlev + ndom);
+  }
+  return casim_batch_step(ctx, ctx->sb, dt, stream);
+}
 
 
 // ------------------------------------------------------- allocation-free step
@@ -1573,6 +1609,7 @@ extern "C" int casim_state_load(const char *path, const casim_params *params, co
 extern "C" void casim_free(casim_ctx *ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
+  casim_batch_free(ctx->sb);
   if (ctx->d_err) cudaFree(ctx->d_err);
   for (int s = 0; s < casim_ctx::kStages; ++s) {
     if (ctx->h2d_fld[s]) cudaFree(ctx->h2d_fld[s]);

@@ -137,3 +137,50 @@ def test_batch_argument_errors():
         casim.casim_batch_free(b)
     finally:
         casim.casim_free(ctx)
+
+
+@pytest.mark.parametrize("precision", [casim.CASIM_MIXED, casim.CASIM_FP64])
+def test_step_batched_equals_batch_step_and_follows_the_domain_list(precision):
+    """casim_step_batched (one call per step for a list of domains) gives, bit
+    for bit, what casim_batch_step gives on a batch of the same domains; when
+    the list changes (another subset, in another order) the context's batch
+    is rebuilt and the result is again that of per-domain steps."""
+    doms = domains(seed=29)
+    ref, _ = run_batch(doms, precision, 3)
+    dev = to_device(doms)
+    ctx = casim.casim_init(precision=precision)
+    try:
+        st, nc, nl = [d.state for d in dev], [d.ncols for d in dev], [d.nlev for d in dev]
+        for _ in range(3):
+            casim.casim_step_batched(ctx, st, nc, nl, 1.0)
+        assert casim.casim_get_error(ctx)[0] == 0
+        same([d.numpy() for d in dev], ref)
+        # another list: three of the domains, reversed, one step from fresh states
+        pick = [6, 2, 0]
+        sub = [doms[i] for i in pick]
+        dev2 = to_device(sub)
+        casim.casim_step_batched(ctx, [d.state for d in dev2], [d.ncols for d in dev2], [d.nlev for d in dev2], 1.0)
+        assert casim.casim_get_error(ctx)[0] == 0
+        same([d.numpy() for d in dev2], reference(sub, precision, 1))
+    finally:
+        casim.casim_free(ctx)
+
+
+def test_step_batched_argument_errors():
+    ctx = casim.casim_init()
+    try:
+        d = casim.Domain(*domains()[2][:2], 64)
+        with pytest.raises(casim.CasimError):
+            casim.casim_step_batched(ctx, [], [], [], 1.0)
+        with pytest.raises(casim.CasimError):
+            casim.casim_step_batched(ctx, [d.state], [64], [17], 0.0)
+        with pytest.raises(casim.CasimError):
+            casim.casim_step_batched(ctx, [d.state], [64], [5000], 1.0)
+    finally:
+        casim.casim_free(ctx)
+    warm = casim.casim_init(flags=casim.CASIM_WARM)
+    try:
+        with pytest.raises(casim.CasimError):
+            casim.casim_step_batched(warm, [d.state], [64], [17], 1.0)
+    finally:
+        casim.casim_free(warm)
