@@ -121,7 +121,7 @@ static void derive(const casim_params &p, ConstK<R> &K, double (*l)(double)) {
   const double pi = 3.14159265358979323846;
   const double Ls = p.Lv + p.Lf;
   const double eps = p.Rd / p.Rv;
-  K.T0 = (R)p.T0; K.Tnuc = (R)p.T_nuc; K.qmin = (R)p.q_min;
+  K.T0 = (R)p.T0; K.Tnuc = (R)p.T_nuc; K.qmin = (R)p.q_min; K.tnuc0 = (R)(p.T_nuc - p.T0);
   K.t0_esit = (R)(p.T0 - p.es_it); K.t0_esib = (R)(p.T0 - p.es_ib);
   K.lv_cp = (R)(p.Lv / p.cp); K.cp_lv = (R)(p.cp / p.Lv); K.cp = (R)p.cp; K.inv_cp = (R)(1.0 / p.cp);
   K.lv = (R)p.Lv; K.ls = (R)Ls; K.lf = (R)p.Lf;

@@ -45,6 +45,7 @@ struct SpeciesK {
 template <class R>
 struct ConstK {
   R T0, Tnuc, qmin;
+  R tnuc0;                          // Tnuc - T0, formed in FP64
   R t0_esit, t0_esib;               // T0 - es_it, T0 - es_ib
   R lv_cp, cp_lv, cp, inv_cp, lv, ls, lf;
   R eps, ome;                       // Rd/Rv, 1 - Rd/Rv
@@ -446,7 +447,13 @@ struct Phys {
     const R iT2 = M::div((R)1, T * T);
     const R Sw = M::div(qv, qsl);
     const bool hc = qc > K.qmin, hr = qr > K.qmin;
-    const bool cold = T < K.T0, warm = T > K.T0;
+    // regimes: the FP64 form compares T itself; the mixed form compares
+    // tc = T - T0, which it forms in FP64 before rounding (an FP32 T is
+    // resolved to 3e-5 K only, so a point adjusted to within that of the
+    // freezing or nucleation temperature would take the other regime)
+    const bool cold = M::kMixed ? tc < (R)0 : T < K.T0;
+    const bool warm = M::kMixed ? tc > (R)0 : T > K.T0;
+    const bool nucl = M::kMixed ? tc < K.tnuc0 : T < K.Tnuc;
 
     // air properties shared by the ventilated integrals
     const R lgrho = M::lg(rho);
@@ -489,7 +496,7 @@ struct Phys {
       const R esi = es_ice(K, w.Td, tc);
       const R qsi = qsat(K, esi, p);
       const R Si = M::div(qv, qsi);
-      if (T < K.Tnuc && Si > (R)1) {
+      if (nucl && Si > (R)1) {
         const R nin = K.mey_a * M::exp(K.mey_b + K.mey_c * (Si - (R)1));
         const R dn = M::div(nin, rho) - w.nx[0];
         if (dn > (R)0) r.nucn = M::div(dn, dtr);
@@ -914,7 +921,7 @@ struct MixT {
     bool act = w.qc > qmin || w.qr > qmin || w.qv > qs0;
     if constexpr (!M::kWarm) {
       act = act || w.qx[0] > qmin || w.qx[1] > qmin || w.qx[2] > qmin;
-      if (!act && w.T < K.Tnuc) act = __fdividef(w.qv, P::qsat(K, P::es_ice(K, s.T, w.tc), w.p)) > 1.f;
+      if (!act && w.tc < K.tnuc0) act = __fdividef(w.qv, P::qsat(K, P::es_ice(K, s.T, w.tc), w.p)) > 1.f;
     }
     return act;
   }
