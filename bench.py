@@ -295,10 +295,19 @@ def bench_batch(args, rank, world, local):
 
 
 def bench_surrogate(args, rank, world, local):
+    """The surrogate workload on its own line (see surrogate_run)."""
+    line = surrogate_run(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def surrogate_run(args, rank, world, local):
     """Learned warm-rain rates on deep convection 512x512x150: training data
     from mixed-form runs (the scheme's own rates), training on the GPU,
-    inference through the guarded surrogate step; errors judged by the plain
-    mixed step (rates on held-out points, 100-step surface precipitation)."""
+    inference through the guarded surrogate step of a batch holding the
+    domain (one feature pass, one network launch, one step launch, no host
+    synchronisation); errors judged by the plain mixed step (rates on
+    held-out points, 100-step surface precipitation).  Returns the line."""
     import torch
     from paper_2010_14823_gb300 import casim, shard, synth
     casim.lib()
@@ -388,16 +397,21 @@ def bench_surrogate(args, rank, world, local):
     e1.record(stream)
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / nsteps
-    served = 0
+    # the batched surrogate step: warm-up step (counts the served points), then timed steps
+    b = casim.casim_batch_create(ctx, [surr.state], [ncols], [nlev])
+    served = casim.casim_batch_step_surrogate(ctx, b, m, dt, stream, want_served=True)
+    n0 = casim.casim_launch_count(ctx)
     sampler = ClockSampler(local)
     sampler.start()
     e0.record(stream)
-    for _ in range(nsteps):
-        served += casim.casim_step_surrogate(ctx, m, surr.state, ncols, nlev, dt, stream)
+    for _ in range(nsteps - 1):
+        casim.casim_batch_step_surrogate(ctx, b, m, dt, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    surr_ms = e0.elapsed_time(e1) / nsteps
+    launches = casim.casim_launch_count(ctx) - n0
+    surr_ms = e0.elapsed_time(e1) / max(1, nsteps - 1)
+    casim.casim_batch_free(b)
     rc, fl = casim.casim_get_error(ctx, stream)
     assert rc == 0, (rc, fl)
     pp, ps = plain.precip[:, :ncols].sum(0).cpu().numpy(), surr.precip[:, :ncols].sum(0).cpu().numpy()
@@ -406,15 +420,15 @@ def bench_surrogate(args, rank, world, local):
     col_rel = np.abs(ps[wet] - pp[wet]) / pp[wet]
     casim.casim_mlp_free(m)
     casim.casim_free(ctx)
-    if rank == 0:
-        value = world * npts / (surr_ms * 1e-3)
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": nsteps, "warmup": 0,
+    value = world * npts / (surr_ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": nsteps - 1, "warmup": 1,
                 "ms_per_step": surr_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "bf16 network + f32/f64 step", "data": "synthetic",
                 "config": {"workload": "surrogate_deep_512x512x150", "train_rows": have, "gen_steps": gen_steps,
                            "train_steps": train_steps, "batch": batch, "train_s": train_s,
+                           "path": "casim_batch_step_surrogate: feature pass, network, step; no host sync",
                            "rate_rel_error_heldout": rate_err, "heldout_inbox_frac": float(inbox.mean()),
-                           "served_points_per_step": served / nsteps, "plain_ms_per_step": plain_ms,
+                           "served_points_per_step": served, "plain_ms_per_step": plain_ms,
                            "surrogate_ms_per_step": surr_ms, "precip_total_rel_error": abs(tot_s - tot_p) / tot_p,
                            "precip_column_rel_error": {"median": float(np.median(col_rel)),
                                                        "p99": float(np.percentile(col_rel, 99))}},
@@ -424,8 +438,8 @@ def bench_surrogate(args, rank, world, local):
                                        "FP32 -> BF16 input pass)",
                              "algorithmic_flop_per_launch": net_flop, "ms_per_launch": net_ms,
                              "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst cuBLAS GEMM)"},
-                "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks}
-        print(json.dumps(line), flush=True)
+                "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks}
+    return line
 
 
 def bench_peaks(args, rank, world, local):
@@ -612,31 +626,10 @@ def bench_warm(args, rank, world, local):
 FIELD_NAMES = ("T", "qv", "qc", "qr", "qi", "qs", "qg", "nc", "nr", "ni", "ns", "ng", "na")
 
 
-def mixed_vs_fp64(casim, torch, fld0, dz, ncols, nlev, dt, nsteps, stream):
-    """The mixed form against the FP64 form on the GPU, both advanced nsteps
-    from the same state: per prognostic field the largest and rms absolute
-    difference, and the largest and rms relative difference over points where
-    the FP64 value exceeds a floor (1e-12 kg/kg for masses, 1 /kg for
-    numbers); per form the drift of total water (vapour + condensate in the
-    air + accumulated surface precipitation) per step, relative."""
-    doms, drift = {}, {}
-    for name, prec in (("mixed", casim.CASIM_MIXED), ("fp64", casim.CASIM_FP64)):
-        ctx = casim.casim_init(precision=prec)
-        d = casim.Domain(fld0, dz, ncols)
-        bud = torch.zeros((2, ncols), dtype=torch.float64, device=d.fld.device)
-        casim.casim_budget(ctx, d.state, ncols, nlev, bud, stream)
-        w0 = float(bud[0].sum().item())
-        for _ in range(nsteps):
-            casim.casim_step(ctx, d.state, ncols, nlev, dt, stream)
-        casim.casim_budget(ctx, d.state, ncols, nlev, bud, stream)
-        rc, fl = casim.casim_get_error(ctx, stream)
-        assert rc == 0, (rc, fl)
-        w1 = float(bud[0].sum().item()) + float(d.precip[:, :ncols].sum().item())
-        drift[name] = abs(w1 - w0) / w0 / nsteps
-        casim.casim_free(ctx)
-        doms[name] = d
-    a, b = doms["mixed"].fld[:13, :, :ncols], doms["fp64"].fld[:13, :, :ncols]
-    out = {"steps": nsteps, "water_drift_per_step": drift, "fields": {}}
+def _compare(torch, a, b, x0, pa, pb):
+    """Per-field differences of the mixed state a against the FP64 state b
+    (both [13][nlev][ncols] on the device), x0 the common starting state."""
+    out = {"fields": {}}
     for f, name in enumerate(FIELD_NAMES):
         diff = (a[f] - b[f]).abs()
         rec = {"max_abs": float(diff.max().item()), "rms_abs": float(diff.square().mean().sqrt().item())}
@@ -651,9 +644,55 @@ def mixed_vs_fp64(casim, torch, fld0, dz, ncols, nlev, dt, nsteps, stream):
             # presence decisions (q > q_min) taken differently by the two forms
             rec["presence_flips"] = int(((a[f] > 1e-14) != (b[f] > 1e-14)).sum().item())
         out["fields"][name] = rec
-    pa, pb = doms["mixed"].precip[:, :ncols].sum(0), doms["fp64"].precip[:, :ncols].sum(0)
+    # the scales the scheme conserves: cloud water against total water
+    # (qv + qc: the adjustment moves water between them), the aerosol number
+    # against the aerosol population (n_a + n_c: activation moves number
+    # between them); activation decisions: points where n_a changed in one
+    # form only
+    na, nc, qv, qc = 12, 7, 1, 2
+    out["qc_max_rel_to_total_water"] = float(((a[qc] - b[qc]).abs() / (b[qv] + b[qc])).max().item())
+    out["na_max_rel_to_population"] = float(((a[na] - b[na]).abs() / (b[na] + b[nc]).clamp_min(1.0)).max().item())
+    out["activation_decision_flips"] = int(((a[na] != x0[na]) != (b[na] != x0[na])).sum().item())
     wet = pb > 1e-6 * float(pb.max().item())
     out["precip_column_max_rel"] = float(((pa - pb).abs()[wet] / pb[wet]).max().item()) if wet.any() else 0.0
+    return out
+
+
+def mixed_vs_fp64(casim, torch, fld0, dz, ncols, nlev, dt, nsteps, stream):
+    """The mixed form against the FP64 form on the GPU, both advanced from the
+    same state, compared after one step and after nsteps: per prognostic
+    field the largest and rms absolute difference, and the largest and rms
+    relative difference over points where the FP64 value exceeds a floor
+    (1e-12 kg/kg for masses, 1 /kg for numbers; and a significant floor,
+    1e-6 kg/kg and 1e3 /kg); cloud water relative to total water, aerosol
+    number relative to the aerosol population, activation decisions taken
+    differently; per form the drift of total water (vapour + condensate in
+    the air + accumulated surface precipitation) per step, relative."""
+    doms, drift, one = {}, {}, {}
+    for name, prec in (("mixed", casim.CASIM_MIXED), ("fp64", casim.CASIM_FP64)):
+        ctx = casim.casim_init(precision=prec)
+        d = casim.Domain(fld0, dz, ncols)
+        bud = torch.zeros((2, ncols), dtype=torch.float64, device=d.fld.device)
+        casim.casim_budget(ctx, d.state, ncols, nlev, bud, stream)
+        w0 = float(bud[0].sum().item())
+        for i in range(nsteps):
+            casim.casim_step(ctx, d.state, ncols, nlev, dt, stream)
+            if i == 0:
+                one[name] = (d.fld[:13, :, :ncols].clone(), d.precip[:, :ncols].sum(0))
+        casim.casim_budget(ctx, d.state, ncols, nlev, bud, stream)
+        rc, fl = casim.casim_get_error(ctx, stream)
+        assert rc == 0, (rc, fl)
+        w1 = float(bud[0].sum().item()) + float(d.precip[:, :ncols].sum().item())
+        drift[name] = abs(w1 - w0) / w0 / nsteps
+        casim.casim_free(ctx)
+        doms[name] = d
+    x0 = fld0[:13, :, :ncols]
+    out = {"steps": nsteps, "water_drift_per_step": drift}
+    out["after_one_step"] = _compare(torch, one["mixed"][0], one["fp64"][0], x0, one["mixed"][1], one["fp64"][1])
+    del one
+    last = _compare(torch, doms["mixed"].fld[:13, :, :ncols], doms["fp64"].fld[:13, :, :ncols], x0,
+                    doms["mixed"].precip[:, :ncols].sum(0), doms["fp64"].precip[:, :ncols].sum(0))
+    out.update(last)
     del doms
     torch.cuda.empty_cache()
     return out
@@ -728,6 +767,8 @@ def main():
     ap.add_argument("--surr-steps", type=int, default=100, help="surrogate: steps compared with the plain step")
     ap.add_argument("--gen-steps", type=int, default=10, help="surrogate: states the training rows come from")
     ap.add_argument("--train-steps", type=int, default=4000, help="surrogate: Adam steps")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="leave the surrogate run (training + 100 steps) out of the main line's config")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -880,6 +921,23 @@ def main():
         cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                "single_thread_value": r1, "single_thread_sample": sample1}
 
+    surrogate = None
+    if not args.no_surrogate and args.workload.startswith("deep") and "mixed" in forms:
+        # the learned warm-rain rates on the same workload (their own seed):
+        # training, then the batched surrogate step against the plain step
+        del dom, fld0
+        torch.cuda.empty_cache()
+        sl = surrogate_run(args, rank, world, local)
+        c = sl["config"]
+        surrogate = {"workload": c["workload"], "value": sl["value"], "ms_per_step": sl["ms_per_step"],
+                     "plain_ms_per_step": c["plain_ms_per_step"], "path": c["path"],
+                     "served_points_per_step": c["served_points_per_step"], "train_rows": c["train_rows"],
+                     "train_steps": c["train_steps"], "train_s": c["train_s"],
+                     "rate_rel_error_heldout": c["rate_rel_error_heldout"],
+                     "precip_total_rel_error": c["precip_total_rel_error"],
+                     "precip_column_rel_error": c["precip_column_rel_error"], "network_roofline": sl["roofline"],
+                     "gpu_launches": sl["gpu_launches"]}
+
     if rank == 0:
         cfg = {"workload": args.workload, "ncols": ncols, "nlev": nlev, "dt_s": dt,
                "form": "mixed FP32 rates / FP64 state and transfers" if "mixed" in forms else "FP64",
@@ -892,6 +950,8 @@ def main():
                 cfg["fp64_roofline"] = _fp64_roofline(npts, fp_ms / args.fp64_steps)
         if accuracy is not None:
             cfg["mixed_vs_fp64"] = accuracy
+        if surrogate is not None:
+            cfg["surrogate"] = surrogate
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": mix_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,

@@ -340,7 +340,11 @@ long long casim_mlp_param_count(void);
 /* FP32 master parameters, host arrays of casim_mlp_param_count() floats. */
 int casim_mlp_set_params(casim_mlp *mlp, const float *host, long long n);
 int casim_mlp_get_params(const casim_mlp *mlp, float *host, long long n);
-/* Inference engine: 1 (default) = tcgen05/TMEM kernel, 0 = mma.sync GEMMs. */
+/* Engine: 1 (default) = the tensor-core (tcgen05/TMEM) kernels -- inference
+   and the training GEMMs (forward, data and weight gradients); 0 = the
+   mma.sync GEMMs for both.  casim_mlp_fit and casim_mlp_loss_grad_host
+   return CASIM_ERR_TIMEOUT if a bounded wait of a tensor-core kernel gave
+   up (the error is cleared). */
 int casim_mlp_set_engine(casim_mlp *mlp, int engine);
 /* Standardised inputs Xn[n][12] -> outputs Y[n][4] (host arrays; synchronous;
    runs the selected engine). */
@@ -383,6 +387,21 @@ int casim_mlp_set_norm(casim_mlp *mlp, const float *stats);
    points that took the network's rates. */
 int casim_step_surrogate(casim_ctx *ctx, casim_mlp *mlp, const casim_state *s, int ncols, int nlev, double dt,
                          void *stream, long long *served);
+
+/* Every domain of a batch advanced by dt with the surrogate's warm-rain
+   rates where its guard admits the point (as casim_step_surrogate for each
+   domain; the results are, bit for bit, those per-domain calls').  One
+   feature pass over all the batch's points, one network launch over their
+   rows, then the batch's step launch(es) in its configuration.  The
+   context must be CASIM_MIXED and the batch's; the network fitted.
+   Allocates the network's scratch on first use for the batch's point count
+   (sum of nlev * pitch).  On the tensor-core engine (the default) the
+   network reads the row count on the device, so the call only enqueues
+   work; if `served` is non-NULL it waits for `stream` and stores the number
+   of points that took the network's rates.  (No paper counterpart: the
+   paper has no learned part.) */
+int casim_batch_step_surrogate(casim_ctx *ctx, casim_batch *batch, casim_mlp *mlp, double dt, void *stream,
+                               long long *served);
 void casim_mlp_free(casim_mlp *mlp);
 
 /* ----------------------------------------------------------------------------

@@ -162,6 +162,8 @@ def lib():
         L.casim_mlp_set_norm.restype = i
         L.casim_step_surrogate.argtypes = [vp, vp, ps, i, i, d, vp, ctypes.POINTER(ll)]
         L.casim_step_surrogate.restype = i
+        L.casim_batch_step_surrogate.argtypes = [vp, vp, vp, d, vp, ctypes.POINTER(ll)]
+        L.casim_batch_step_surrogate.restype = i
         L.casim_mlp_set_engine.argtypes = [vp, i]
         L.casim_mlp_set_engine.restype = i
         L.casim_mlp_free.argtypes = [vp]
@@ -479,6 +481,16 @@ def casim_step_surrogate(ctx, mlp, state: casim_state, ncols: int, nlev: int, dt
     _check(lib().casim_step_surrogate(ctx, mlp, ctypes.byref(state), ncols, nlev, dt, _stream(stream),
                                       ctypes.byref(served)), "casim_step_surrogate")
     return served.value
+
+
+def casim_batch_step_surrogate(ctx, batch, mlp, dt: float, stream=None, want_served: bool = False) -> int | None:
+    """One surrogate step of every domain of a batch; with want_served the call
+    waits for the stream and returns the points that took the network's rates."""
+    served = ctypes.c_longlong(0)
+    _check(lib().casim_batch_step_surrogate(ctx, batch, mlp, dt, _stream(stream),
+                                            ctypes.byref(served) if want_served else None),
+           "casim_batch_step_surrogate")
+    return served.value if want_served else None
 
 
 def casim_mlp_free(mlp):

@@ -534,6 +534,7 @@ struct casim_batch {
   Item *d_items = nullptr;
   int nitems = 0, items_block = 0, items_cap = 0;
   long long total_cols = 0;
+  long long total_pts = 0;        // sum of nlev pitch over the non-empty domains (per-point arrays)
   int block = 128, compact = 1, persistent = 1;
   cudaGraphExec_t gexec = nullptr;
   int graph_steps = 0;
@@ -587,7 +588,7 @@ extern "C" int casim_batch_create(casim_ctx *ctx, const casim_state *domains, co
   b->ctx = ctx;
   b->ndom = ndom;
   b->dom.resize(ndom);
-  long long off = 0;
+  long long off = 0, pts = 0;
   std::vector<double> hdz;
   for (int i = 0; i < ndom; ++i) {
     const casim_state &s = domains[i];
@@ -601,8 +602,10 @@ extern "C" int casim_batch_create(casim_ctx *ctx, const casim_state *domains, co
     d.ncols = ncols[i];
     d.nlev = nlev[i];
     d.list_off = off;
+    d.pt_off = pts;
     d.dzmin = 1e300;
     if (ncols[i] > 0) {
+      pts += (long long)nlev[i] * s.pitch;
       hdz.resize(nlev[i]);
       cudaError_t e = cudaMemcpy(hdz.data(), s.dz, nlev[i] * sizeof(double), cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) { delete b; return cuda_fail(e, "casim_batch_create: dz"); }
@@ -614,6 +617,7 @@ extern "C" int casim_batch_create(casim_ctx *ctx, const casim_state *domains, co
     off += ncols[i];
   }
   b->total_cols = off;
+  b->total_pts = pts;
   b->order.resize(ndom);
   for (int i = 0; i < ndom; ++i) b->order[i] = i;
   std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return b->dom[x].nlev > b->dom[y].nlev; });
@@ -650,6 +654,7 @@ static BatchArgs batch_args(const casim_batch *b, double dt) {
   a.dt = dt;
   a.compact = b->compact;
   a.persistent = b->persistent;
+  a.surr = nullptr;
   return a;
 }
 
@@ -668,11 +673,13 @@ static int persistent_grid(const casim_batch *b) {
   return std::max(1, per_sm) * b->ctx->nsm;
 }
 
-// enqueue one step of every domain (no validation; used by step and capture)
-static int enqueue_batch_step(casim_batch *b, double dt, cudaStream_t st) {
+// enqueue one step of every domain (no validation; used by step and capture);
+// surr: the surrogate's per-point rates of the batch (mixed form), or null
+static int enqueue_batch_step(casim_batch *b, double dt, cudaStream_t st, const float4 *surr = nullptr) {
   casim_ctx *ctx = b->ctx;
   if (b->nitems == 0) return CASIM_OK;
-  const BatchArgs a = batch_args(b, dt);
+  BatchArgs a = batch_args(b, dt);
+  a.surr = surr;
   if (b->compact) {
     CUDA_TRY(cudaMemsetAsync(b->d_count, 0, b->ndom * sizeof(int), st));
     if (ctx->precision == CASIM_MIXED)
@@ -960,6 +967,7 @@ extern "C" int casim_step_noalloc(const casim_params *params, int precision, con
   d.nlev = nlev;
   d.dzmin = 0.0;   // replaced on the device by k_noalloc_dzmin
   d.list_off = 0;
+  d.pt_off = 0;
   const int ntiles = (ncols + kTile - 1) / kTile;
   cudaStream_t st = (cudaStream_t)stream;
   k_noalloc_setup<<<(ntiles + 255) / 256, 256, 0, st>>>(sc, d, ntiles);
@@ -977,6 +985,7 @@ extern "C" int casim_step_noalloc(const casim_params *params, int precision, con
   a.dt = dt;
   a.compact = 1;
   a.persistent = 1;
+  a.surr = nullptr;
   int per_sm = 1;
   if (precision == CASIM_MIXED) {
     k_compact<PolicyMix><<<ntiles, kTile, 0, st>>>(a, sc->tiles, ntiles, kp);
@@ -1077,36 +1086,59 @@ static int mlp_batch_ws(casim_mlp *m, int n) {
   return CASIM_OK;
 }
 
+// the tcgen05 GEMM takes operands that are K-major or MN-major with
+// 16-byte aligned rows (strides in multiples of 8 elements)
+static bool tc_operands_ok(long long sr, long long sk) {
+  return (sk == 1 && sr % 8 == 0) || (sr == 1 && sk % 8 == 0);
+}
+
+// one training GEMM: on the tensor-core engine (engine 1) the tcgen05 kernel,
+// else (or for operands it does not take) the mma.sync kernel
 template <class Epi>
-static void gemm(const __nv_bfloat16 *A, long long sam, long long sak, const __nv_bfloat16 *B, long long sbn,
-                 long long sbk, int M, int N, int K, const Epi &epi, cudaStream_t st) {
+static void launch_gemm(const casim_mlp *m, const GemmArgs &g, const Epi &epi, int nsplit, cudaStream_t st);
+
+template <class Epi>
+static void gemm(const casim_mlp *m, const __nv_bfloat16 *A, long long sam, long long sak, const __nv_bfloat16 *B,
+                 long long sbn, long long sbk, int M, int N, int K, const Epi &epi, cudaStream_t st) {
   GemmArgs g{A, sam, sak, B, sbn, sbk, M, N, K, K};
-  const dim3 grid((N + kGBN - 1) / kGBN, (M + kGBM - 1) / kGBM);
-  k_gemm<Epi><<<grid, 128, 0, st>>>(g, epi);
+  launch_gemm(m, g, epi, 1, st);
 }
 
 // weight gradient out[m][n] (ld N) = sum_k A(m, k) B(n, k) over a long K (the
-// batch): K split into chunks of kSplitK rows, partial tiles summed in order
-constexpr int kSplitK = 512, kSplitMax = 64;
+// batch): K split into chunks (kSplitK rows on the mma.sync engine; on the
+// tensor-core engine 256, enough chunks to give every SM a tile), partial
+// tiles summed in order
+constexpr int kSplitK = 512, kSplitKTc = 256, kSplitMax = 64;
 static void gemm_wgrad(casim_mlp *m, const __nv_bfloat16 *A, long long sam, long long sak, const __nv_bfloat16 *B,
                        long long sbn, long long sbk, int M, int N, int K, float *out, cudaStream_t st) {
-  const int kchunk = std::max(kSplitK, (K + kSplitMax - 1) / kSplitMax + kGBK - 1) / kGBK * kGBK;
+  const int split = m->engine == 1 ? kSplitKTc : kSplitK;
+  const int kchunk = std::max(split, (K + kSplitMax - 1) / kSplitMax + kGBK - 1) / kGBK * kGBK;
   const int nsplit = (K + kchunk - 1) / kchunk;
   GemmArgs g{A, sam, sak, B, sbn, sbk, M, N, K, kchunk};
-  const dim3 grid((N + kGBN - 1) / kGBN, (M + kGBM - 1) / kGBM, nsplit);
   const long long len = (long long)M * N;
-  k_gemm<EpiPartial><<<grid, 128, 0, st>>>(g, EpiPartial{m->wsplit, N, len});
+  launch_gemm(m, g, EpiPartial{m->wsplit, N, len}, nsplit, st);
   k_splitk_sum<<<(unsigned)((len + 255) / 256), 256, 0, st>>>(m->wsplit, nsplit, len, out);
+}
+
+template <class Epi>
+static void launch_gemm(const casim_mlp *m, const GemmArgs &g, const Epi &epi, int nsplit, cudaStream_t st) {
+  if (m->engine == 1 && tc_operands_ok(g.sam, g.sak) && tc_operands_ok(g.sbn, g.sbk)) {
+    const dim3 grid((g.N + kTcBN - 1) / kTcBN, (g.M + kTcBM - 1) / kTcBM, nsplit);
+    k_gemm_tc<Epi><<<grid, 128, kTcSmem, st>>>(g, epi, m->d_err);
+  } else {
+    const dim3 grid((g.N + kGBN - 1) / kGBN, (g.M + kGBM - 1) / kGBM, nsplit);
+    k_gemm<Epi><<<grid, 128, 0, st>>>(g, epi);
+  }
 }
 
 // forward pass of n rows whose BF16 inputs are in m->h0; keep_act stores the
 // FP32 activations the backward pass needs
 static void mlp_forward(casim_mlp *m, int n, bool keep_act, cudaStream_t st) {
-  gemm(m->h0, kNinPad, 1, m->wb.w1t, kNinPad, 1, n, kNh, kNinPad,
+  gemm(m, m->h0, kNinPad, 1, m->wb.w1t, kNinPad, 1, n, kNh, kNinPad,
        EpiHidden{m->theta + kOffB1, keep_act ? m->a1 : nullptr, m->h1, kNh}, st);
-  gemm(m->h1, kNh, 1, m->wb.w2t, kNh, 1, n, kNh, kNh, EpiHidden{m->theta + kOffB2, keep_act ? m->a2 : nullptr, m->h2, kNh}, st);
-  gemm(m->h2, kNh, 1, m->wb.w3t, kNh, 1, n, kNh, kNh, EpiHidden{m->theta + kOffB3, keep_act ? m->a3 : nullptr, m->h3, kNh}, st);
-  gemm(m->h3, kNh, 1, m->wb.w4t, kNh, 1, n, kNout, kNh, EpiOut{m->theta + kOffB4, m->y, kNout}, st);
+  gemm(m, m->h1, kNh, 1, m->wb.w2t, kNh, 1, n, kNh, kNh, EpiHidden{m->theta + kOffB2, keep_act ? m->a2 : nullptr, m->h2, kNh}, st);
+  gemm(m, m->h2, kNh, 1, m->wb.w3t, kNh, 1, n, kNh, kNh, EpiHidden{m->theta + kOffB3, keep_act ? m->a3 : nullptr, m->h3, kNh}, st);
+  gemm(m, m->h3, kNh, 1, m->wb.w4t, kNh, 1, n, kNout, kNh, EpiOut{m->theta + kOffB4, m->y, kNout}, st);
 }
 
 // loss and gradient of n rows (inputs in h0, targets Tn, masks Mb)
@@ -1117,21 +1149,27 @@ static void mlp_backward(casim_mlp *m, int n, cudaStream_t st) {
   const long long tot = (long long)n * kNoutPad;
   k_mlp_loss<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(m->y, m->Tn, m->Mb, n, m->cnt, m->loss, m->dz4, m->dzb4);
   const dim3 cs(32, kColsumY);
+  // bias gradients: column sums over row chunks (into wsplit's tail), then in order
+  float *cpart = m->wsplit + (size_t)(kSplitMax - 1) * kNh * kNh;
+  auto colsum = [&](const float *dz, int cols, float *g) {
+    k_colsum<<<dim3((cols + 31) / 32, kColsumChunks), cs, 0, st>>>(dz, n, cols, cols, cpart);
+    k_colsum_fin<<<1, 256, 0, st>>>(cpart, kColsumChunks, cols, g);
+  };
   // layer 4
   gemm_wgrad(m, m->h3, 1, kNh, m->dzb4, 1, kNoutPad, kNh, kNout, n, m->grad + kOffW4, st);
-  k_colsum<<<1, cs, 0, st>>>(m->dz4, n, kNout, kNout, m->grad + kOffB4);
-  gemm(m->dzb4, kNoutPad, 1, m->wb.w4k, kNoutPad, 1, n, kNh, kNoutPad, EpiBackTanh{m->a3, m->dz3, m->dzb3, kNh}, st);
+  colsum(m->dz4, kNout, m->grad + kOffB4);
+  gemm(m, m->dzb4, kNoutPad, 1, m->wb.w4k, kNoutPad, 1, n, kNh, kNoutPad, EpiBackTanh{m->a3, m->dz3, m->dzb3, kNh}, st);
   // layer 3
   gemm_wgrad(m, m->h2, 1, kNh, m->dzb3, 1, kNh, kNh, kNh, n, m->grad + kOffW3, st);
-  k_colsum<<<kNh / 32, cs, 0, st>>>(m->dz3, n, kNh, kNh, m->grad + kOffB3);
-  gemm(m->dzb3, kNh, 1, m->wb.w3k, kNh, 1, n, kNh, kNh, EpiBackTanh{m->a2, m->dz2, m->dzb2, kNh}, st);
+  colsum(m->dz3, kNh, m->grad + kOffB3);
+  gemm(m, m->dzb3, kNh, 1, m->wb.w3k, kNh, 1, n, kNh, kNh, EpiBackTanh{m->a2, m->dz2, m->dzb2, kNh}, st);
   // layer 2
   gemm_wgrad(m, m->h1, 1, kNh, m->dzb2, 1, kNh, kNh, kNh, n, m->grad + kOffW2, st);
-  k_colsum<<<kNh / 32, cs, 0, st>>>(m->dz2, n, kNh, kNh, m->grad + kOffB2);
-  gemm(m->dzb2, kNh, 1, m->wb.w2k, kNh, 1, n, kNh, kNh, EpiBackTanh{m->a1, m->dz1, m->dzb1, kNh}, st);
+  colsum(m->dz2, kNh, m->grad + kOffB2);
+  gemm(m, m->dzb2, kNh, 1, m->wb.w2k, kNh, 1, n, kNh, kNh, EpiBackTanh{m->a1, m->dz1, m->dzb1, kNh}, st);
   // layer 1
   gemm_wgrad(m, m->h0, 1, kNinPad, m->dzb1, 1, kNh, kNin, kNh, n, m->grad + kOffW1, st);
-  k_colsum<<<kNh / 32, cs, 0, st>>>(m->dz1, n, kNh, kNh, m->grad + kOffB1);
+  colsum(m->dz1, kNh, m->grad + kOffB1);
 }
 
 static void mlp_cast(casim_mlp *m, cudaStream_t st) {
@@ -1141,11 +1179,15 @@ static void mlp_cast(casim_mlp *m, cudaStream_t st) {
 
 // forward pass of n rows of BF16 inputs on the tcgen05 kernel: rates at the
 // rows' points (rowpt) or standardised outputs in m->y (rowpt null)
+// rows_dev: if set, the row count is read on the device (written by the
+// feature pass before it on the stream) and n is its upper bound
 static cudaError_t mlp_forward_umma(casim_mlp *m, const __nv_bfloat16 *xb, long long n, const long long *rowpt,
-                                    float4 *surr, unsigned *err, int nsm, cudaStream_t st, float *y = nullptr) {
+                                    float4 *surr, unsigned *err, int nsm, cudaStream_t st, float *y = nullptr,
+                                    const unsigned long long *rows_dev = nullptr) {
   UmmaArgs u;
   u.xb = xb;
   u.rows = n;
+  u.rows_dev = rows_dev;
   u.rowpt = rowpt;
   u.img = m->img;
   u.theta = m->theta;
@@ -1201,6 +1243,10 @@ extern "C" int casim_mlp_create(casim_mlp **out, unsigned long long seed) {
   if (e == cudaSuccess) e = dalloc(&m->d_err, 1);
   if (e == cudaSuccess) e = cudaMemset(m->d_err, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mlp_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, kUmmaSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tc<EpiHidden>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tc<EpiOut>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tc<EpiBackTanh>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gemm_tc<EpiPartial>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
   if (e == cudaSuccess) e = cudaMemcpy(m->theta, th.data(), kNParam * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(m->m1, 0, kNParam * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(m->m2, 0, kNParam * sizeof(float));
@@ -1238,6 +1284,19 @@ extern "C" int casim_mlp_set_params(casim_mlp *m, const float *host, long long n
 extern "C" int casim_mlp_get_params(const casim_mlp *m, float *host, long long n) {
   if (!m || !host || n != kNParam) return CASIM_ERR_ARG;
   CUDA_TRY(cudaMemcpy(host, m->theta, kNParam * sizeof(float), cudaMemcpyDeviceToHost));
+  return CASIM_OK;
+}
+
+// after the device has finished the network's work: a bounded wait of a
+// tensor-core kernel that gave up (error bit 4) is reported, and cleared
+static int mlp_wait_report(casim_mlp *m, const char *where) {
+  unsigned herr = 0;
+  CUDA_TRY(cudaMemcpy(&herr, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (herr) {
+    cudaMemset(m->d_err, 0, sizeof(unsigned));
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: a bounded wait of a tensor-core kernel gave up", where);
+    return CASIM_ERR_TIMEOUT;
+  }
   return CASIM_OK;
 }
 
@@ -1330,7 +1389,7 @@ extern "C" int casim_mlp_loss_grad_host(casim_mlp *m, const float *Xn, const flo
   CUDA_TRY(cudaGetLastError());
   if (loss) CUDA_TRY(cudaMemcpy(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost));
   if (grad) CUDA_TRY(cudaMemcpy(grad, m->grad, kNParam * sizeof(float), cudaMemcpyDeviceToHost));
-  return CASIM_OK;
+  return mlp_wait_report(m, "casim_mlp_loss_grad_host");
 }
 
 extern "C" int casim_mlp_data(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, float *X,
@@ -1429,7 +1488,7 @@ extern "C" int casim_mlp_fit(casim_mlp *m, const float *X, const float *Y, const
   }
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaStreamSynchronize(st));
-  return CASIM_OK;
+  return mlp_wait_report(m, "casim_mlp_fit");
 }
 
 extern "C" int casim_mlp_get_norm(const casim_mlp *m, float *stats) {
@@ -1447,6 +1506,25 @@ extern "C" int casim_mlp_set_norm(casim_mlp *m, const float *stats) {
   return CASIM_OK;
 }
 
+// the surrogate step's scratch for np points: BF16 features and the point
+// of each row (a row per point at most), the rates at every point
+static int surrogate_scratch(casim_mlp *m, long long np) {
+  if (np <= m->cap_pts) return CASIM_OK;
+  cudaFree(m->xb);
+  cudaFree(m->rowpt);
+  cudaFree(m->surr);
+  m->xb = nullptr;
+  m->rowpt = nullptr;
+  m->surr = nullptr;
+  m->cap_pts = m->cap_rows = 0;
+  cudaError_t e = dalloc(&m->xb, (size_t)np * kNinPad);
+  if (e == cudaSuccess) e = dalloc(&m->rowpt, (size_t)np);
+  if (e == cudaSuccess) e = dalloc(&m->surr, (size_t)np);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CASIM_ERR_OOM : cuda_fail(e, "cudaMalloc");
+  m->cap_pts = m->cap_rows = np;
+  return CASIM_OK;
+}
+
 extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_state *s, int ncols, int nlev,
                                     double dt, void *stream, long long *served) {
   NvtxRange nvtx_range_("casim_step_surrogate");
@@ -1455,20 +1533,7 @@ extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_st
   if (rc != CASIM_OK || ncols == 0) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const long long np = (long long)nlev * s->pitch;
-  if (np > m->cap_pts) {
-    cudaFree(m->xb);
-    cudaFree(m->rowpt);
-    cudaFree(m->surr);
-    m->xb = nullptr;
-    m->rowpt = nullptr;
-    m->surr = nullptr;
-    m->cap_pts = m->cap_rows = 0;
-    cudaError_t e = dalloc(&m->xb, (size_t)np * kNinPad);
-    if (e == cudaSuccess) e = dalloc(&m->rowpt, (size_t)np);
-    if (e == cudaSuccess) e = dalloc(&m->surr, (size_t)np);
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CASIM_ERR_OOM : cuda_fail(e, "cudaMalloc");
-    m->cap_pts = m->cap_rows = np;
-  }
+  if ((rc = surrogate_scratch(m, np)) != CASIM_OK) return rc;
   // 1. features of every warm point inside the box; NaN rates outside it
   CUDA_TRY(cudaMemsetAsync(m->rowctr, 0, sizeof(unsigned long long), st));
   FeatArgs fa{};
@@ -1511,6 +1576,74 @@ extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_st
   ctx->launches++;
   CUDA_TRY(cudaGetLastError());
   if (served) *served = rows;
+  return CASIM_OK;
+}
+
+// Every domain of a batch with the surrogate's warm-rain rates: one feature
+// pass over all the batch's points, one network launch over their rows and
+// the batch's step launch(es) reading the network's rates where it gave them.
+// On the tensor-core engine the network reads the row count on the device,
+// so nothing waits for the host unless `served` is asked for.
+extern "C" int casim_batch_step_surrogate(casim_ctx *ctx, casim_batch *b, casim_mlp *m, double dt, void *stream,
+                                          long long *served) {
+  NvtxRange nvtx_range_("casim_batch_step_surrogate");
+  if (!ctx || !b || b->ctx != ctx || ctx->precision != CASIM_MIXED || !m || !m->fitted || !(dt > 0.0) ||
+      !std::isfinite(dt))
+    return CASIM_ERR_ARG;
+  if (served) *served = 0;
+  if (b->total_pts == 0) return CASIM_OK;
+  int rc = surrogate_scratch(m, b->total_pts);
+  if (rc != CASIM_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  // 1. features of every warm point inside the box, in one pass over all domains
+  CUDA_TRY(cudaMemsetAsync(m->rowctr, 0, sizeof(unsigned long long), st));
+  FeatArgs fa{};
+  fa.mode = 1;
+  fa.cap = m->cap_rows;
+  fa.rows = m->rowctr;
+  fa.xb = m->xb;
+  fa.rowpt = m->rowpt;
+  fa.surr = m->surr;
+  fa.norm = m->norm;
+  fa.box = m->box;
+  k_mlp_features_batch<<<(unsigned)((b->total_pts + 255) / 256), 256, 0, st>>>(b->d_dom, b->ndom, b->total_pts, dt,
+                                                                               ctx->kp, fa);
+  ctx->launches++;
+  CUDA_TRY(cudaGetLastError());
+  // 2. the network on the rows
+  long long rows = -1;
+  if (m->engine == 1) {
+    CUDA_TRY(mlp_forward_umma(m, m->xb, m->cap_rows, m->rowpt, m->surr, ctx->d_err, ctx->nsm, st, nullptr,
+                              m->rowctr));
+    ctx->launches++;
+  } else {
+    unsigned long long hrows = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hrows, m->rowctr, sizeof(hrows), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    rows = std::min((long long)hrows, m->cap_rows);
+    const int chunk = 1 << 17;
+    if ((rc = mlp_batch_ws(m, (int)std::min<long long>(chunk, std::max<long long>(rows, 1)))) != CASIM_OK) return rc;
+    for (long long r0 = 0; r0 < rows; r0 += m->cap_b) {
+      const int n = (int)std::min<long long>(m->cap_b, rows - r0);
+      __nv_bfloat16 *save = m->h0;
+      m->h0 = m->xb + r0 * kNinPad;
+      mlp_forward(m, n, false, st);
+      m->h0 = save;
+      k_mlp_scatter<<<(n + 255) / 256, 256, 0, st>>>(m->y, n, m->rowpt + r0, m->norm, m->surr);
+      ctx->launches += 5;
+    }
+  }
+  // 3. the batch's step, taking the network's rates where given
+  if ((rc = enqueue_batch_step(b, dt, st, m->surr)) != CASIM_OK) return rc;
+  if (served) {
+    if (rows < 0) {
+      unsigned long long hrows = 0;
+      CUDA_TRY(cudaMemcpyAsync(&hrows, m->rowctr, sizeof(hrows), cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
+      rows = std::min((long long)hrows, m->cap_rows);
+    }
+    *served = rows;
+  }
   return CASIM_OK;
 }
 

@@ -29,6 +29,7 @@ struct DomDesc {
   int ncols, nlev;
   double dzmin;    // smallest layer thickness of the domain
   long long list_off;
+  long long pt_off;   // first point of the domain in a batch-wide per-point array (surrogate rates)
 };
 
 struct Item {
@@ -46,6 +47,7 @@ struct BatchArgs {
   double dt;
   int compact;
   int persistent;
+  const float4 *surr;   // surrogate warm-rain rates of every point of the batch (pt_off per domain), or null
 };
 
 template <class M>
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(kNarrow ? kBatchNarrowBlock : kBatchMaxBlock,
         a.ncols = d.ncols;
         a.nlev = d.nlev;
         a.dt = b.dt;
-        a.surr = nullptr;
+        a.surr = b.surr ? b.surr + d.pt_off : nullptr;
         eflag |= run_column<M>(a, P, lt, fast, c);
       }
     }

@@ -8,6 +8,7 @@
 #include <cuda_bf16.h>
 
 #include "casim_device.cuh"
+#include "casim_batch.cuh"
 
 namespace casim_dev {
 
@@ -114,9 +115,15 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g, const Epi epi) {
       }
 }
 
+// Epilogues receive (m, n, acc) for m < M, n < N.  One with kLoad = true
+// also reads a value per element (load(m, n)); the tensor-core GEMM issues
+// those reads for a block of rows before it applies the epilogue
+// (apply(m, n, acc, loaded)), so their latencies overlap.
+
 // hidden layer: a = tanh(acc + b); keeps a (FP32, for the backward pass) and
 // its BF16 copy (the next layer's input)
 struct EpiHidden {
+  static constexpr bool kLoad = false;
   const float *bias;
   float *a;              // [M][ld] or null
   __nv_bfloat16 *h;      // [M][ld]
@@ -130,6 +137,7 @@ struct EpiHidden {
 
 // output layer: y = acc + b
 struct EpiOut {
+  static constexpr bool kLoad = false;
   const float *bias;
   float *y;              // [M][ld]
   int ld;
@@ -138,6 +146,7 @@ struct EpiOut {
 
 // weight gradient: g[m][n] = acc
 struct EpiStore {
+  static constexpr bool kLoad = false;
   float *c;
   int ld;
   __device__ __forceinline__ void operator()(int m, int n, float acc) const { c[(long long)m * ld + n] = acc; }
@@ -145,6 +154,7 @@ struct EpiStore {
 
 // split-K partial sums: ws[z][m][n] for block z
 struct EpiPartial {
+  static constexpr bool kLoad = false;
   float *ws;
   int ld;
   long long zstride;
@@ -165,17 +175,19 @@ __global__ void k_splitk_sum(const float *ws, int nsplit, long long len, float *
 // data gradient through tanh: dz = acc (1 - a^2); FP32 for the bias sums,
 // BF16 for the next GEMMs
 struct EpiBackTanh {
+  static constexpr bool kLoad = true;
   const float *a;        // [M][ld] activations of the layer below
   float *dz;
   __nv_bfloat16 *dzb;
   int ld;
-  __device__ __forceinline__ void operator()(int m, int n, float acc) const {
+  __device__ __forceinline__ float load(int m, int n) const { return __ldg(a + (long long)m * ld + n); }
+  __device__ __forceinline__ void apply(int m, int n, float acc, float av) const {
     const long long i = (long long)m * ld + n;
-    const float av = a[i];
     const float v = acc * (1.f - av * av);
     dz[i] = v;
     dzb[i] = __float2bfloat16(v);
   }
+  __device__ __forceinline__ void operator()(int m, int n, float acc) const { apply(m, n, acc, load(m, n)); }
 };
 
 // ---------------------------------------------------------- elementwise kernels
@@ -251,23 +263,33 @@ __global__ void k_sum(const float *x, long long n, float *out) {
   if ((threadIdx.x & 31) == 0) atomicAdd(out, part);
 }
 
-// bias gradient: column sums of dz [n][ld] (first `cols` columns) into g.
-// Block (32, 32): lane x is a column (coalesced rows), y a row phase; the 32
-// phase sums are added in a fixed order.
-constexpr int kColsumY = 32;
-__global__ void __launch_bounds__(32 * kColsumY) k_colsum(const float *dz, int n, int ld, int cols, float *g) {
+// bias gradient: column sums of dz [n][ld] (first `cols` columns).  Block
+// (32, 32) of grid (column blocks, row chunks): lane x is a column
+// (coalesced rows), y a row phase within chunk blockIdx.y; the 32 phase sums
+// are added in a fixed order into part[chunk][c]; k_colsum_fin adds the
+// chunks in order into g (deterministic).
+constexpr int kColsumY = 32, kColsumChunks = 16;
+__global__ void __launch_bounds__(32 * kColsumY) k_colsum(const float *dz, int n, int ld, int cols, float *part_out) {
   __shared__ float s_part[kColsumY][33];
   const int c = blockIdx.x * 32 + threadIdx.x;
+  const int per = (n + gridDim.y - 1) / gridDim.y, r0 = blockIdx.y * per, r1 = min(n, r0 + per);
   float part = 0.f;
   if (c < cols)
-    for (int r = threadIdx.y; r < n; r += kColsumY) part += dz[(long long)r * ld + c];
+    for (int r = r0 + threadIdx.y; r < r1; r += kColsumY) part += dz[(long long)r * ld + c];
   s_part[threadIdx.y][threadIdx.x] = part;
   __syncthreads();
   if (threadIdx.y == 0 && c < cols) {
     float s = 0.f;
     for (int y = 0; y < kColsumY; ++y) s += s_part[y][threadIdx.x];
-    g[c] = s;
+    part_out[(long long)blockIdx.y * cols + c] = s;
   }
+}
+__global__ void k_colsum_fin(const float *part, int chunks, int cols, float *g) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float s = 0.f;
+  for (int y = 0; y < chunks; ++y) s += part[(long long)y * cols + c];
+  g[c] = s;
 }
 
 // Adam on the flat FP32 parameters
@@ -402,15 +424,14 @@ struct FeatArgs {
   const float *box;       // mode 1: [12 lo][12 hi]
 };
 
-// One thread per point of a domain: adjustment and activation as the mixed
-// step does them, then the point's features (and, for training data, the
-// scheme's four log-rates).
-__global__ void __launch_bounds__(256) k_mlp_features(const KArgs a, const KParams P, const FeatArgs fa) {
+// The features of one point (index pt of its domain's [nlev][pitch] grid;
+// gpt: its index in the rates array, which is pt for one domain): adjustment
+// and activation as the mixed step does them, then the point's features (and,
+// for training data, the scheme's four log-rates).  warm: the point gets a row.
+__device__ __forceinline__ void feature_point(const KArgs &a, const KParams &P, const FeatArgs &fa, long long pt,
+                                              long long gpt, bool &warm, float f[kNin], float y[kNout],
+                                              float mk[kNout]) {
   const long long np = (long long)a.nlev * a.pitch;
-  const long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  bool warm = false;
-  float f[kNin];
-  float y[kNout] = {0, 0, 0, 0}, mk[kNout] = {0, 0, 0, 0};
   if (pt < np) {
     const int c = (int)(pt % a.pitch);
     if (c < a.ncols) {
@@ -448,7 +469,7 @@ __global__ void __launch_bounds__(256) k_mlp_features(const KArgs a, const KPara
 #pragma unroll
             for (int j = 0; j < kNin; ++j) inbox &= f[j] >= fa.box[j] && f[j] <= fa.box[kNin + j];
             if (!inbox) {
-              fa.surr[pt] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+              fa.surr[gpt] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
               warm = false;
             }
           }
@@ -456,10 +477,14 @@ __global__ void __launch_bounds__(256) k_mlp_features(const KArgs a, const KPara
       }
     }
   }
-  // block-aggregated append of the rows: one atomic on the row counter per
-  // block (a counter that every warp hits serialises in L2), the warps'
-  // offsets from a prefix sum of their counts; rows come in no set order
-  // (each carries its point)
+}
+
+// Block-aggregated append of the rows: one atomic on the row counter per
+// block (a counter that every warp hits serialises in L2), the warps' offsets
+// from a prefix sum of their counts; rows come in no set order (each carries
+// its point, gpt).  Every thread of the block calls it.
+__device__ __forceinline__ void feature_append(const FeatArgs &fa, bool warm, long long gpt, const float f[kNin],
+                                               const float y[kNout], const float mk[kNout]) {
   __shared__ unsigned s_off[256 / 32];
   __shared__ unsigned long long s_base;
   const unsigned ball = __ballot_sync(0xffffffffu, warm);
@@ -480,7 +505,7 @@ __global__ void __launch_bounds__(256) k_mlp_features(const KArgs a, const KPara
   const long long row = (long long)(s_base + s_off[wid]) + __popc(ball & ((1u << lane) - 1u));
   if (row >= fa.cap) return;   // the caller sees rows > cap and reports it
   if (fa.mode == 0) {
-    if (fa.rowpt) fa.rowpt[row] = pt;
+    if (fa.rowpt) fa.rowpt[row] = gpt;
 #pragma unroll
     for (int j = 0; j < kNin; ++j) fa.X[row * kNin + j] = f[j];
 #pragma unroll
@@ -496,8 +521,50 @@ __global__ void __launch_bounds__(256) k_mlp_features(const KArgs a, const KPara
     uint4 *dst = reinterpret_cast<uint4 *>(fa.xb + row * kNinPad);
     dst[0] = reinterpret_cast<const uint4 *>(hb)[0];
     dst[1] = reinterpret_cast<const uint4 *>(hb)[1];
-    fa.rowpt[row] = pt;
+    fa.rowpt[row] = gpt;
   }
+}
+
+// One thread per point of a domain.
+__global__ void __launch_bounds__(256) k_mlp_features(const KArgs a, const KParams P, const FeatArgs fa) {
+  const long long pt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  bool warm = false;
+  float f[kNin];
+  float y[kNout] = {0, 0, 0, 0}, mk[kNout] = {0, 0, 0, 0};
+  feature_point(a, P, fa, pt, pt, warm, f, y, mk);
+  feature_append(fa, warm, pt, f, y, mk);
+}
+
+// One thread per point of every domain of a batch: the points of domain d
+// are [dom[d].pt_off, dom[d].pt_off + nlev pitch) of the batch's rates array
+// (a binary search over the domains' offsets finds a thread's domain).
+__global__ void __launch_bounds__(256) k_mlp_features_batch(const DomDesc *dom, int ndom, long long total,
+                                                            double dt, const KParams P, const FeatArgs fa) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  bool warm = false;
+  float f[kNin];
+  float y[kNout] = {0, 0, 0, 0}, mk[kNout] = {0, 0, 0, 0};
+  if (g < total) {
+    int lo = 0, hi = ndom - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (dom[mid].pt_off <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    const DomDesc d = dom[lo];
+    KArgs a;
+    a.fld = d.fld;
+    a.pitch = d.pitch;
+    a.dz = d.dz;
+    a.precip = d.precip;
+    a.err = nullptr;
+    a.ncols = d.ncols;
+    a.nlev = d.nlev;
+    a.dt = dt;
+    a.surr = nullptr;
+    feature_point(a, P, fa, g - d.pt_off, g, warm, f, y, mk);
+  }
+  feature_append(fa, warm, g, f, y, mk);
 }
 
 // network outputs (standardised log-rates) -> rates at the rows' points
@@ -552,7 +619,8 @@ __global__ void k_mlp_images(const float *theta, unsigned char *img) {
 
 struct UmmaArgs {
   const __nv_bfloat16 *xb;     // [rows][16] standardised features
-  long long rows;
+  long long rows;              // rows, or the capacity when rows_dev is set
+  const unsigned long long *rows_dev;   // if set: the row count, read on the device (at most rows)
   const long long *rowpt;      // point of each row (null: write Y rows instead)
   const unsigned char *img;    // weight images
   const float *theta;          // biases are read from the flat parameters
@@ -611,7 +679,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
   __shared__ __align__(8) unsigned long long s_bar[24];
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long ntiles = (u.rows + 127) / 128;
+  const long long nrows = u.rows_dev ? min((long long)*u.rows_dev, u.rows) : u.rows;
+  const long long ntiles = (nrows + 127) / 128;
   const long long cta = blockIdx.x, ncta = gridDim.x;
   const long long my_tiles = cta < ntiles ? (ntiles - 1 - cta) / ncta + 1 : 0;
   const uint32_t sb = smem_addr(sm);
@@ -750,7 +819,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
       f0 = make_uint4(0, 0, 0, 0);
       f1 = f0;
       const long long r = g * 128 + row;
-      if (g < ntiles && r < u.rows) {
+      if (g < ntiles && r < nrows) {
         const uint4 *src = reinterpret_cast<const uint4 *>(u.xb + r * kNinPad);
         f0 = src[0];
         f1 = src[1];
@@ -804,7 +873,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
         float v[16];
         tmem_ld16(tl + kTmA1, v);
         tc_fence_before();
-        if (r0 + row < u.rows) {
+        if (r0 + row < nrows) {
           float y[kNout];
 #pragma unroll
           for (int i = 0; i < kNout; ++i) y[i] = v[i] + s_bias[3 * kNh + i];
@@ -825,6 +894,241 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
   __syncthreads();
   tc_fence_after();
   if (warp == kUmmaMmaWarp) tmem_dealloc(taddr, 512);
+}
+
+
+// ------------------------------------------------ tcgen05 training GEMM
+// The training GEMMs of the network on the fifth-generation tensor cores:
+// C[m][n] = sum_k A(m, k) B(n, k), operands BF16 with the strides of
+// GemmArgs, FP32 accumulators in tensor memory, the same fused epilogues as
+// k_gemm.  Each operand is K-major (unit stride along k: the forward pass and
+// the data gradients) or MN-major (unit stride along m or n: the weight
+// gradients, whose k runs over the batch); both are staged in shared memory
+// as the K-major 128-byte-swizzled slabs the MMA reads (sw128_offset), an
+// MN-major tile being transposed in registers on the way (8 x 8 blocks).
+//
+// One CTA of 4 warps per 128 x 128 output tile (split K over blockIdx.z as
+// for k_gemm); K advances in slabs of 64 through two shared-memory buffers:
+// all threads load slab s + 1 into registers while the MMAs of slab s run,
+// then wait (bounded) for the MMAs that last read the buffer before storing
+// into it.  One thread issues the MMAs (M = 128, N = the tile's columns
+// rounded up to 16, K = 16 each) and commits each slab to its buffer's
+// mbarrier.  Epilogue: warp w reads tensor-memory lanes 32w.. (its rows),
+// 32 columns at a time, and passes the 32 x 32 block through shared memory
+// (the operand buffers, free once the last MMA completed) so that the
+// epilogue's loads and stores run along n, coalesced.  A wait that gives up
+// sets error bit 4, waits again for the MMAs it issued and releases the
+// tensor memory.
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 64;
+constexpr uint32_t kTcTile = kTcBM * kTcBK * 2;              // one operand slab: 16 KB
+constexpr int kTcSmem = 1024 + 4 * (int)kTcTile;              // A and B, two buffers, 1024-byte alignment
+constexpr unsigned kTcSpins = 1u << 24;
+
+// One thread's share of an operand slab: rows r0..r0+127 of the operand
+// (row index m or n), k in [k0, k0 + 64) of [.., ke), zeros outside it.
+// K-major (unit stride along k): 8 chunks of 8 k, consecutive threads along a
+// row.  MN-major (unit stride along the rows): one 8 (rows) x 8 (k) block,
+// as 8 chunks of 8 rows at one k, transposed into 8 chunks of 8 k at one row
+// when stored.  tc_fetch issues the global loads, tc_put writes the slab in
+// the swizzled K-major layout, so both operands' loads are in flight
+// together.
+struct TcFrag {
+  uint4 v[8];
+};
+
+__device__ __forceinline__ void tc_fetch(TcFrag &fr, const __nv_bfloat16 *P, long long srow, long long sk, int nrows,
+                                         int r0, int k0, int ke, int tid) {
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  if (sk == 1) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = tid + 128 * j, r = i >> 3, ch = i & 7;
+      const int row = r0 + r, k = k0 + 8 * ch;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (row < nrows && k < ke) {
+        const __nv_bfloat16 *src = P + (long long)row * srow + k;
+        if (k + 8 <= ke) {
+          v = __ldg(reinterpret_cast<const uint4 *>(src));
+        } else {
+          __align__(16) __nv_bfloat16 e[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) e[t] = k + t < ke ? src[t] : zero;
+          v = *reinterpret_cast<const uint4 *>(e);
+        }
+      }
+      fr.v[j] = v;
+    }
+  } else {
+    const int rg = tid & 15, kg = tid >> 4;
+    const int row = r0 + 8 * rg;
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const int k = k0 + 8 * kg + kk;
+      uint4 u = make_uint4(0, 0, 0, 0);
+      if (k < ke && row < nrows) {
+        const __nv_bfloat16 *src = P + (long long)k * sk + row;
+        if (row + 8 <= nrows) {
+          u = __ldg(reinterpret_cast<const uint4 *>(src));
+        } else {
+          __align__(16) __nv_bfloat16 e[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) e[t] = row + t < nrows ? src[t] : zero;
+          u = *reinterpret_cast<const uint4 *>(e);
+        }
+      }
+      fr.v[kk] = u;
+    }
+  }
+}
+
+__device__ __forceinline__ void tc_put(unsigned char *dst, const TcFrag &fr, long long sk, int tid) {
+  if (sk == 1) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = tid + 128 * j, r = i >> 3, ch = i & 7;
+      *reinterpret_cast<uint4 *>(dst + sw128_offset(kTcBM, r, 8 * ch)) = fr.v[j];
+    }
+  } else {
+    const int rg = tid & 15, kg = tid >> 4;
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(fr.v);   // w[4 kk + j]: rows 2j, 2j + 1 at k kk
+#pragma unroll
+    for (int mm = 0; mm < 8; ++mm) {
+      const unsigned sel = (mm & 1) ? 0x7632u : 0x5410u;   // high or low halves of the two words
+      const int j = mm >> 1;
+      uint4 o;
+      o.x = __byte_perm(w[0 * 4 + j], w[1 * 4 + j], sel);
+      o.y = __byte_perm(w[2 * 4 + j], w[3 * 4 + j], sel);
+      o.z = __byte_perm(w[4 * 4 + j], w[5 * 4 + j], sel);
+      o.w = __byte_perm(w[6 * 4 + j], w[7 * 4 + j], sel);
+      *reinterpret_cast<uint4 *>(dst + sw128_offset(kTcBM, 8 * rg + mm, 8 * kg)) = o;
+    }
+  }
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g, const Epi epi, unsigned *err) {
+  extern __shared__ __align__(16) unsigned char sraw[];
+  unsigned char *sm = sraw + ((1024 - (smem_addr(sraw) & 1023)) & 1023);
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) unsigned long long s_bar[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * kTcBN;
+  const int kb = blockIdx.z * g.kchunk, ke = min(g.K, kb + g.kchunk);
+  const int nst = ke > kb ? (ke - kb + kTcBK - 1) / kTcBK : 0;
+  const int ncols = min(kTcBN, ((g.N - n0) + 15) / 16 * 16);   // MMA N: the tile's columns, multiple of 16
+  const uint32_t idesc = umma_idesc_bf16(kTcBM, ncols);
+  unsigned char *bufA[2] = {sm, sm + 2 * kTcTile};
+  unsigned char *bufB[2] = {sm + kTcTile, sm + 3 * kTcTile};
+  const uint32_t bar0 = smem_addr(&s_bar[0]);
+  if (warp == 0) {
+    tmem_alloc(smem_addr(&s_tmem), kTcBN);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    bar_init(bar0, 1);
+    bar_init(bar0 + 8, 1);
+    bar_fence_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = s_tmem;
+  bool ok = true;
+  TcFrag fa, fb;
+  if (nst > 0) {
+    tc_fetch(fa, g.A, g.sam, g.sak, g.M, m0, kb, ke, tid);
+    tc_fetch(fb, g.B, g.sbn, g.sbk, g.N, n0, kb, ke, tid);
+    tc_put(bufA[0], fa, g.sak, tid);
+    tc_put(bufB[0], fb, g.sbk, tid);
+  }
+  fence_async_smem();
+  __syncthreads();
+  for (int s = 0; s < nst; ++s) {
+    const int buf = s & 1, k0 = kb + s * kTcBK;
+    if (tid == 0) {
+      tc_fence_after();
+      const int nsub = (min(kTcBK, ke - k0) + 15) / 16;
+      const uint32_t a = smem_addr(bufA[buf]), b = smem_addr(bufB[buf]);
+      for (int sub = 0; sub < nsub; ++sub)
+        umma_bf16(taddr, umma_desc_sw128(a + 32u * (uint32_t)sub), umma_desc_sw128(b + 32u * (uint32_t)sub), idesc,
+                  (s | sub) ? 1u : 0u);
+      umma_commit(bar0 + 8u * (uint32_t)buf);
+    }
+    if (s + 1 < nst) {
+      const int nb = buf ^ 1;
+      tc_fetch(fa, g.A, g.sam, g.sak, g.M, m0, k0 + kTcBK, ke, tid);
+      tc_fetch(fb, g.B, g.sbn, g.sbk, g.N, n0, k0 + kTcBK, ke, tid);
+      // the MMAs of slab s - 1 read buffer nb: wait for their commit
+      if (s >= 1 && ok) ok = bar_wait(bar0 + 8u * (uint32_t)nb, (uint32_t)(((s - 1) >> 1) & 1), kTcSpins);
+      if (ok) {
+        tc_put(bufA[nb], fa, g.sak, tid);
+        tc_put(bufB[nb], fb, g.sbk, tid);
+      }
+      fence_async_smem();
+    }
+    __syncthreads();
+  }
+  // the last slab's commit completes after every MMA of the tile
+  if (nst > 0) {
+    const int last = nst - 1;
+    if (!bar_wait(bar0 + 8u * (uint32_t)(last & 1), (uint32_t)((last >> 1) & 1), kTcSpins)) ok = false;
+  }
+  tc_fence_after();
+  if (!__all_sync(0xffffffffu, ok)) ok = false;
+  if (ok) {
+    float *blk = reinterpret_cast<float *>(sm) + warp * (32 * 33);
+    for (int c0 = 0; c0 < ncols; c0 += 32) {
+      float v[32];
+      if (nst > 0) {
+        tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < 32; ++i) blk[lane * 33 + i] = v[i];   // row lane, column i
+      __syncwarp();
+      const int n = n0 + c0 + lane;
+      if (c0 + lane < ncols && n < g.N) {
+        if constexpr (Epi::kLoad) {
+          // 16 rows at a time: their reads first, then the epilogue
+#pragma unroll
+          for (int h = 0; h < 32; h += 16) {
+            float ld[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+              const int m = m0 + 32 * warp + h + r;
+              ld[r] = m < g.M ? epi.load(m, n) : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+              const int m = m0 + 32 * warp + h + r;
+              if (m < g.M) epi.apply(m, n, blk[(h + r) * 33 + lane], ld[r]);
+            }
+          }
+        } else {
+#pragma unroll 8
+          for (int r = 0; r < 32; ++r) {
+            const int m = m0 + 32 * warp + r;
+            if (m < g.M) epi(m, n, blk[r * 33 + lane]);
+          }
+        }
+      }
+    }
+  } else if (lane == 0) {
+    atomicOr(err, 4u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (!ok && tid == 0 && nst > 0) {
+    // drain: every MMA this CTA issued has completed before its tensor
+    // memory is released (bounded as every wait)
+    const int last = nst - 1;
+    bar_wait(bar0 + 8u * (uint32_t)(last & 1), (uint32_t)((last >> 1) & 1), kTcSpins);
+  }
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(taddr, kTcBN);
 }
 
 }  // namespace casim_dev

@@ -200,6 +200,52 @@ def test_training_reduces_loss_and_surrogate_step():
         casim.casim_free(ctx)
 
 
+@pytest.mark.parametrize("engine", [1, 0])
+def test_batched_surrogate_step_equals_per_domain_surrogate_steps(engine):
+    """The surrogate over a batch of uneven domains (one feature pass, one
+    network launch, one step launch) gives, bit for bit, what
+    casim_step_surrogate gives on each domain, over two steps and in two
+    launch configurations of the batch; the points served add up.  Each
+    row's rates depend on that row alone, so the order in which the feature
+    pass appends rows does not matter."""
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED)
+    m = casim.casim_mlp_create(seed=12)
+    try:
+        casim.casim_mlp_set_engine(m, engine)
+        _, _, _, X, Y, M, rows = _data(ctx, ncols=1024, nlev=150, seed=43)
+        casim.casim_mlp_fit(m, X, Y, M, rows, steps=200, batch=4096, lr=1e-3, seed=4, history=False)
+        specs = [("deep_convective", 700, 150), ("stratus", 97, 60), ("deep_convective", 0, 30),
+                 ("deep_convective", 333, 101), ("stratus_broken", 64, 17)]
+        doms = []
+        for i, (rc, nc, nl) in enumerate(specs):
+            dz = synth.dz_stretched(nl)
+            doms.append((synth.make_state(rc, nc, nl, dz, seed=70 + i), dz, nc, nl))
+        ref = [casim.Domain(f, dz, nc) for f, dz, nc, nl in doms]
+        served_ref = []
+        for _ in range(2):
+            served_ref.append(sum(casim.casim_step_surrogate(ctx, m, d.state, d.ncols, d.nlev, 1.0)
+                                  for d in ref if d.ncols))
+        assert casim.casim_get_error(ctx)[0] == 0 and served_ref[0] > 0
+        for config in ((128, 1, 1), (64, 0, 0)):
+            got = [casim.Domain(f, dz, nc) for f, dz, nc, nl in doms]
+            b = casim.casim_batch_create(ctx, [d.state for d in got], [d.ncols for d in got], [d.nlev for d in got])
+            try:
+                casim.casim_batch_config(b, *config)
+                served = casim.casim_batch_step_surrogate(ctx, b, m, 1.0, want_served=True)
+                casim.casim_batch_step_surrogate(ctx, b, m, 1.0)    # asynchronous form
+                torch.cuda.synchronize()
+            finally:
+                casim.casim_batch_free(b)
+            assert casim.casim_get_error(ctx)[0] == 0
+            assert served == served_ref[0]
+            for dg, dr in zip(got, ref):
+                (a, pa), (r, pr) = dg.numpy(), dr.numpy()
+                assert np.array_equal(a, r) and np.array_equal(pa, pr), config
+    finally:
+        casim.casim_mlp_free(m)
+        casim.casim_free(ctx)
+
+
 def test_what_the_trained_network_gains_over_the_scheme():
     """What the trained network gains over the scheme it replaces, asserted
     on both sides of the ledger and judged by the scheme itself:
