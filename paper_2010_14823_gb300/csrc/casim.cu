@@ -239,6 +239,11 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   for (int x = 0; x < 5; ++x) ctx->kp.vmax[x] = p.vmax[x];
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  // the staged mixed step's dynamic shared memory exceeds the default 48 KB
+  // for columns of more than ~640 levels
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step<PolicyMix, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)step_smem_bytes<PolicyMix, false>(kMaxLev));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
@@ -290,11 +295,11 @@ template <class PMix, class PF64>
 static void launch_pair(const casim_ctx *ctx, dim3 grid, cudaStream_t st, const KArgs &a, double *tend) {
   const KParams &kp = ctx->kp;
   if (ctx->precision == CASIM_MIXED) {
-    if (tend) k_step<PMix, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
-    else k_step<PMix, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+    if (tend) k_step<PMix, true><<<grid, kBlock, step_smem_bytes<PMix, true>(a.nlev), st>>>(a, kp, tend);
+    else k_step<PMix, false><<<grid, kBlock, step_smem_bytes<PMix, false>(a.nlev), st>>>(a, kp, nullptr);
   } else {
-    if (tend) k_step<PF64, true><<<grid, kBlock, 0, st>>>(a, kp, tend);
-    else k_step<PF64, false><<<grid, kBlock, 0, st>>>(a, kp, nullptr);
+    if (tend) k_step<PF64, true><<<grid, kBlock, step_smem_bytes<PF64, true>(a.nlev), st>>>(a, kp, tend);
+    else k_step<PF64, false><<<grid, kBlock, step_smem_bytes<PF64, false>(a.nlev), st>>>(a, kp, nullptr);
   }
 }
 
@@ -1572,7 +1577,7 @@ extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_st
   // 3. the step, taking the network's rates where given
   a.surr = m->surr;
   const dim3 grid((unsigned)((ncols + kBlock - 1) / kBlock));
-  k_step<PolicyMix, false><<<grid, kBlock, 0, st>>>(a, ctx->kp, nullptr);
+  k_step<PolicyMix, false><<<grid, kBlock, step_smem_bytes<PolicyMix, false>(nlev), st>>>(a, ctx->kp, nullptr);
   ctx->launches++;
   CUDA_TRY(cudaGetLastError());
   if (served) *served = rows;

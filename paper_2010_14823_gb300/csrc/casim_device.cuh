@@ -1439,22 +1439,53 @@ __device__ __forceinline__ void level_tab(double *dz, double *dzdt, float *dtdz_
   dzdt_f[k] = d2f(v / dt);
 }
 
-// Block prologue: the level tables into shared memory, and whether every
-// species' capped speed keeps within one level per step.
-struct Smem {
-  double dz[kMaxLev];
-  double dzdt[kMaxLev];
-  float dtdz_f[kMaxLev];
-  float dzdt_f[kMaxLev];
-  double red[kBlock / 32];
-  int fast;
+// The step kernel's dynamic shared memory: the prefetch stage (standard
+// mixed step: two levels of the block's 16 fields, 32 KB), then the level
+// tables of this domain's nlev levels (dz, dz/dt, dt/dz and dz/dt in FP32),
+// then the block's reduction slots.
+template <class M, bool kTend>
+__host__ __device__ constexpr bool step_staged() {
+  return M::kMixed && !M::kWarm && !M::kAero && !M::kTri && !kTend;
+}
+constexpr int kStageFields = 16;
+constexpr size_t kStageBytes = 2 * kStageFields * kBlock * sizeof(double);
+template <class M, bool kTend>
+__host__ __device__ constexpr size_t step_smem_bytes(int nlev) {
+  return (step_staged<M, kTend>() ? kStageBytes : 0) + (size_t)nlev * 24 + (kBlock / 32) * 8 + 16;
+}
+
+struct StepSmem {
+  double *stage;   // [2][16][kBlock] or null
+  LevelTab lt;
+  double *red;
+  int *fast;
 };
 
-__device__ __forceinline__ bool prologue(const KArgs &a, const KParams &P, Smem &sm) {
+template <class M, bool kTend>
+__device__ __forceinline__ StepSmem step_smem(unsigned char *base, int nlev) {
+  StepSmem m;
+  unsigned char *p = base;
+  m.stage = nullptr;
+  if constexpr (step_staged<M, kTend>()) {
+    m.stage = reinterpret_cast<double *>(p);
+    p += kStageBytes;
+  }
+  double *dz = reinterpret_cast<double *>(p), *dzdt = dz + nlev;
+  float *dtdz_f = reinterpret_cast<float *>(dzdt + nlev), *dzdt_f = dtdz_f + nlev;
+  m.lt = LevelTab{dz, dzdt, dtdz_f, dzdt_f};
+  m.red = reinterpret_cast<double *>(dzdt_f + nlev);   // 24 nlev bytes in: 8-byte aligned
+  m.fast = reinterpret_cast<int *>(m.red + kBlock / 32);
+  return m;
+}
+
+// Block prologue: the level tables into shared memory, and whether every
+// species' capped speed keeps within one level per step.
+__device__ __forceinline__ bool prologue(const KArgs &a, const KParams &P, const StepSmem &sm) {
   double dzmin = 1e300;
   for (int k = threadIdx.x; k < a.nlev; k += blockDim.x) {
     const double v = a.dz[k];
-    level_tab(sm.dz, sm.dzdt, sm.dtdz_f, sm.dzdt_f, k, v, a.dt);
+    level_tab(const_cast<double *>(sm.lt.dz), const_cast<double *>(sm.lt.dzdt), const_cast<float *>(sm.lt.dtdz_f),
+              const_cast<float *>(sm.lt.dzdt_f), k, v, a.dt);
     dzmin = fmin(dzmin, v);
   }
   for (int o = 16; o > 0; o >>= 1) dzmin = fmin(dzmin, __shfl_xor_sync(0xffffffffu, dzmin, o));
@@ -1465,11 +1496,20 @@ __device__ __forceinline__ bool prologue(const KArgs &a, const KParams &P, Smem 
     for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmin(m, sm.red[i]);
     int fast = 1;
     for (int x = 1; x < 5; ++x) fast &= ((P.vmax[x] * a.dt) / m) / P.c_max <= 1.0;
-    sm.fast = fast;
+    *sm.fast = fast;
   }
   __syncthreads();
-  return sm.fast != 0;
+  return *sm.fast != 0;
 }
+
+// 8-byte asynchronous copy global -> shared (this thread's own slot)
+__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Multi-substep sedimentation of one column after the processes (used when a
 // capped speed could exceed one level per step): per species, n_sub from the
@@ -1595,10 +1635,22 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
 // sweep of the processes (one read and one write of the state).  Otherwise
 // the processes are applied first and each species is sedimented with its
 // own substep count in further sweeps over the column.
-template <class M, bool kTend = false>
+// stg (kStage): this thread's slots of the prefetch stage (slot f of buffer
+// b at stg[(b * 16 + f) * kBlock]): level k - 1's 16 fields are copied there
+// by cp.async while level k is processed, so the sweep seldom waits on a load
+// (each thread reads only the slots it filled itself: no block barrier)
+template <class M, bool kTend = false, bool kStage = false>
 __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P, const LevelTab &lt, bool fast, int c,
-                                               double *tend = nullptr) {
+                                               double *tend = nullptr, double *stg = nullptr) {
   const double *sdz = lt.dz, *sdzdt = lt.dzdt;
+  if constexpr (kStage) {
+    static_assert(!M::kWarm && !M::kAero && !M::kTri, "the stage holds the 16 standard fields");
+    const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
+    const double *src = a.fld + (size_t)(a.nlev - 1) * a.pitch + c;
+#pragma unroll
+    for (int f = 0; f < kStageFields; ++f) cp_async8(stg + f * kBlock, src + f * fs);
+    cp_async_commit();
+  }
   using R = typename M::R;
   using Ph = Phys<M>;
   const ConstK<R> &K = M::K(P);
@@ -1613,7 +1665,28 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
 
   for (int k = a.nlev - 1; k >= 0; --k) {
     Pt s;
-    load_pt<M::kWarm, M::kAero, M::kTri>(a, k, c, s);
+    if constexpr (kStage) {
+      const int b = (a.nlev - 1 - k) & 1;
+      const double *cur = stg + b * kStageFields * kBlock;
+      if (k > 0) {
+        double *nxt = stg + (b ^ 1) * kStageFields * kBlock;
+        const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
+        const double *src = a.fld + (size_t)(k - 1) * a.pitch + c;
+#pragma unroll
+        for (int f = 0; f < kStageFields; ++f) cp_async8(nxt + f * kBlock, src + f * fs);
+        cp_async_commit();
+        cp_async_wait<1>();   // this level's copies (the older group) have landed
+      } else {
+        cp_async_wait<0>();
+      }
+      s.T = cur[0 * kBlock]; s.qv = cur[1 * kBlock]; s.qc = cur[2 * kBlock]; s.qr = cur[3 * kBlock];
+      s.qi = cur[4 * kBlock]; s.qs = cur[5 * kBlock]; s.qg = cur[6 * kBlock];
+      s.nc = cur[7 * kBlock]; s.nr = cur[8 * kBlock]; s.ni = cur[9 * kBlock]; s.ns = cur[10 * kBlock];
+      s.ng = cur[11 * kBlock]; s.na = cur[12 * kBlock];
+      s.p = cur[13 * kBlock]; s.rho = cur[14 * kBlock]; s.w = cur[15 * kBlock];
+    } else {
+      load_pt<M::kWarm, M::kAero, M::kTri>(a, k, c, s);
+    }
     bool touched;
     if constexpr (!M::kMixed) {
       eflag |= nonfinite_in(s);
@@ -1833,14 +1906,17 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
 }
 
 // kTend: tendency mode (tend receives the source terms, a.fld unchanged)
+// dynamic shared memory: step_smem_bytes<M, kTend>(a.nlev)
 template <class M, bool kTend>
 __global__ void __launch_bounds__(kBlock, M::kMinBlocks) k_step(const KArgs a, const KParams P, double *tend) {
-  __shared__ Smem sm;
+  extern __shared__ __align__(16) unsigned char step_dyn[];
+  const StepSmem sm = step_smem<M, kTend>(step_dyn, a.nlev);
   const bool fast = prologue(a, P, sm);
   const int c = blockIdx.x * kBlock + threadIdx.x;
   if (c >= a.ncols) return;
-  const LevelTab lt{sm.dz, sm.dzdt, sm.dtdz_f, sm.dzdt_f};
-  const unsigned eflag = run_column<M, kTend>(a, P, lt, fast, c, tend);
+  constexpr bool kStage = step_staged<M, kTend>();
+  const unsigned eflag =
+      run_column<M, kTend, kStage>(a, P, sm.lt, fast, c, tend, kStage ? sm.stage + threadIdx.x : nullptr);
   if (eflag) atomicOr(a.err, eflag);
 }
 
