@@ -33,22 +33,22 @@ WORKLOAD = "deep_512x512x150"
 
 # DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one ncu
 # capture of a 65 536-column x 150-level launch (dram__bytes_read.sum +
-# dram__bytes_write.sum = 2.2197 GB for 9.83 M points); reads are 16 fields per
+# dram__bytes_write.sum = 2.2204 GB for 9.83 M points); reads are 16 fields per
 # point and writes follow the changed points, so the traffic scales with the
 # points processed.  Valid only for the kernel source it was taken on.
-MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.80,
+MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.87,
                     "source": "paper_2010_14823_gb300/csrc/casim_device.cuh",
-                    "sha256": "8a311e4612e8c54fb4eafa703ca5f74ca863cd918f7f5255a4f9f9956e3ebf64"}
+                    "sha256": "e9a0895dad591d40b25711a591fc21c0bbdc4e48065d1cc819831ba52ae4927c"}
 
 
 # FP64 arithmetic instructions of k_step<PolicyF64> per point on the same
 # state, from one ncu capture of a 16 384-column x 150-level launch
 # (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum =
-# 1168.2 M + 296.4 M + 381.0 M for 2.458 M points); the FP64 pipe was 72.3 %
+# 1168.3 M + 296.4 M + 381.0 M for 2.458 M points); the FP64 pipe was 72.7 %
 # busy.  Valid only for the kernel source it was taken on.
-MEASURED_FP64_OPS = {"kernel": "k_step<PolicyF64>", "inst_per_point": 750.99,
-                     "dfma": 475.34, "dadd": 120.62, "dmul": 155.03, "fp64_pipe_active": 0.723,
-                     "sha256": "21b439d3df2993a275ecc6f5c6d9399cc277290105e455b1a058f7ffcfee5a4c"}
+MEASURED_FP64_OPS = {"kernel": "k_step<PolicyF64>", "inst_per_point": 751.07,
+                     "dfma": 475.40, "dadd": 120.63, "dmul": 155.04, "fp64_pipe_active": 0.727,
+                     "sha256": "e9a0895dad591d40b25711a591fc21c0bbdc4e48065d1cc819831ba52ae4927c"}
 
 
 def _host_link_gbs(torch, stream, nbytes: int = 1 << 30):
