@@ -244,6 +244,13 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_step<PolicyMix, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)step_smem_bytes<PolicyMix, false>(kMaxLev));
+  // and the batched step's (256-thread blocks: a 64 KB stage)
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step_batch<PolicyMix, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batch_smem_bytes<PolicyMix>(kBatchNarrowBlock, kMaxLev));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step_batch<PolicyMix, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)batch_smem_bytes<PolicyMix>(kBatchMaxBlock, kMaxLev));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
@@ -540,6 +547,7 @@ struct casim_batch {
   int nitems = 0, items_block = 0, items_cap = 0;
   long long total_cols = 0;
   long long total_pts = 0;        // sum of nlev pitch over the non-empty domains (per-point arrays)
+  int maxlev = 1;                 // most levels of any domain
   int block = 128, compact = 1, persistent = 1;
   cudaGraphExec_t gexec = nullptr;
   int graph_steps = 0;
@@ -623,6 +631,7 @@ extern "C" int casim_batch_create(casim_ctx *ctx, const casim_state *domains, co
   }
   b->total_cols = off;
   b->total_pts = pts;
+  for (int i = 0; i < ndom; ++i) b->maxlev = std::max(b->maxlev, nlev[i]);
   b->order.resize(ndom);
   for (int i = 0; i < ndom; ++i) b->order[i] = i;
   std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return b->dom[x].nlev > b->dom[y].nlev; });
@@ -660,6 +669,7 @@ static BatchArgs batch_args(const casim_batch *b, double dt) {
   a.compact = b->compact;
   a.persistent = b->persistent;
   a.surr = nullptr;
+  a.maxlev = b->maxlev;
   return a;
 }
 
@@ -674,7 +684,8 @@ static auto batch_kernel(int block) {
 template <class M>
 static int persistent_grid(const casim_batch *b) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<M>(b->block), b->block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<M>(b->block), b->block,
+                                                batch_smem_bytes<M>(b->block, b->maxlev));
   return std::max(1, per_sm) * b->ctx->nsm;
 }
 
@@ -697,10 +708,10 @@ static int enqueue_batch_step(casim_batch *b, double dt, cudaStream_t st, const 
   if (b->persistent) CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
   if (ctx->precision == CASIM_MIXED) {
     const int grid = b->persistent ? std::min(b->nitems, persistent_grid<PolicyMix>(b)) : b->nitems;
-    batch_kernel<PolicyMix>(b->block)<<<grid, b->block, 0, st>>>(a, ctx->kp);
+    batch_kernel<PolicyMix>(b->block)<<<grid, b->block, batch_smem_bytes<PolicyMix>(b->block, b->maxlev), st>>>(a, ctx->kp);
   } else {
     const int grid = b->persistent ? std::min(b->nitems, persistent_grid<PolicyF64>(b)) : b->nitems;
-    batch_kernel<PolicyF64>(b->block)<<<grid, b->block, 0, st>>>(a, ctx->kp);
+    batch_kernel<PolicyF64>(b->block)<<<grid, b->block, batch_smem_bytes<PolicyF64>(b->block, b->maxlev), st>>>(a, ctx->kp);
   }
   ctx->launches++;
   CUDA_TRY(cudaGetLastError());
@@ -991,15 +1002,18 @@ extern "C" int casim_step_noalloc(const casim_params *params, int precision, con
   a.compact = 1;
   a.persistent = 1;
   a.surr = nullptr;
+  a.maxlev = nlev;
   int per_sm = 1;
   if (precision == CASIM_MIXED) {
     k_compact<PolicyMix><<<ntiles, kTile, 0, st>>>(a, sc->tiles, ntiles, kp);
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<PolicyMix>(kTile), kTile, 0));
-    batch_kernel<PolicyMix>(kTile)<<<std::min(ntiles, std::max(1, per_sm) * nsm), kTile, 0, st>>>(a, kp);
+    const size_t smem = batch_smem_bytes<PolicyMix>(kTile, nlev);
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<PolicyMix>(kTile), kTile, smem));
+    batch_kernel<PolicyMix>(kTile)<<<std::min(ntiles, std::max(1, per_sm) * nsm), kTile, smem, st>>>(a, kp);
   } else {
     k_compact<PolicyF64><<<ntiles, kTile, 0, st>>>(a, sc->tiles, ntiles, kp);
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<PolicyF64>(kTile), kTile, 0));
-    batch_kernel<PolicyF64>(kTile)<<<std::min(ntiles, std::max(1, per_sm) * nsm), kTile, 0, st>>>(a, kp);
+    const size_t smem = batch_smem_bytes<PolicyF64>(kTile, nlev);
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<PolicyF64>(kTile), kTile, smem));
+    batch_kernel<PolicyF64>(kTile)<<<std::min(ntiles, std::max(1, per_sm) * nsm), kTile, smem, st>>>(a, kp);
   }
   CUDA_TRY(cudaGetLastError());
   if (flags) {

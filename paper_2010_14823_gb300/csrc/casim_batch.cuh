@@ -48,7 +48,15 @@ struct BatchArgs {
   int compact;
   int persistent;
   const float4 *surr;   // surrogate warm-rain rates of every point of the batch (pt_off per domain), or null
+  int maxlev;           // most levels of any domain (the level tables' size)
 };
+
+// dynamic shared memory of the batched step: the mixed step's prefetch stage
+// (two levels of 16 fields per thread) and the level tables of maxlev levels
+template <class M>
+__host__ __device__ constexpr size_t batch_smem_bytes(int block, int maxlev) {
+  return (step_staged<M, false>() ? 2 * (size_t)kStageFields * block * sizeof(double) : 0) + (size_t)maxlev * 24;
+}
 
 template <class M>
 __device__ __forceinline__ bool point_needs_step(const KParams &P, const DomDesc &d, int k, int c) {
@@ -112,13 +120,15 @@ template <class M, bool kNarrow = false>
 __global__ void __launch_bounds__(kNarrow ? kBatchNarrowBlock : kBatchMaxBlock,
                                   kNarrow ? M::kMinBlocks : (M::kMixed ? 2 : 1))
     k_step_batch(const BatchArgs b, const KParams P) {
-  __shared__ double s_dz[kMaxLev];
-  __shared__ double s_dzdt[kMaxLev];
-  __shared__ float s_dtdz_f[kMaxLev];
-  __shared__ float s_dzdt_f[kMaxLev];
+  extern __shared__ __align__(16) unsigned char batch_dyn[];
   __shared__ int s_item;
-  const LevelTab lt{s_dz, s_dzdt, s_dtdz_f, s_dzdt_f};
   const int B = blockDim.x;
+  constexpr bool kStage = step_staged<M, false>();
+  double *stage = kStage ? reinterpret_cast<double *>(batch_dyn) : nullptr;
+  double *s_dz = reinterpret_cast<double *>(batch_dyn + (kStage ? 2 * (size_t)kStageFields * B * sizeof(double) : 0));
+  double *s_dzdt = s_dz + b.maxlev;
+  float *s_dtdz_f = reinterpret_cast<float *>(s_dzdt + b.maxlev), *s_dzdt_f = s_dtdz_f + b.maxlev;
+  const LevelTab lt{s_dz, s_dzdt, s_dtdz_f, s_dzdt_f};
   const int tid = threadIdx.x;
   unsigned eflag = 0;
   int prev_dom = -1;
@@ -157,7 +167,7 @@ __global__ void __launch_bounds__(kNarrow ? kBatchNarrowBlock : kBatchMaxBlock,
         a.nlev = d.nlev;
         a.dt = b.dt;
         a.surr = b.surr ? b.surr + d.pt_off : nullptr;
-        eflag |= run_column<M>(a, P, lt, fast, c);
+        eflag |= run_column<M, false, kStage>(a, P, lt, fast, c, nullptr, kStage ? stage + tid : nullptr, B);
       }
     }
     // shared memory (item, dz) is reused by the next item; with one item per

@@ -1636,19 +1636,20 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
 // the processes are applied first and each species is sedimented with its
 // own substep count in further sweeps over the column.
 // stg (kStage): this thread's slots of the prefetch stage (slot f of buffer
-// b at stg[(b * 16 + f) * kBlock]): level k - 1's 16 fields are copied there
-// by cp.async while level k is processed, so the sweep seldom waits on a load
-// (each thread reads only the slots it filled itself: no block barrier)
+// b at stg[(b * 16 + f) * ss], ss the block's thread count): level k - 1's 16
+// fields are copied there by cp.async while level k is processed, so the
+// sweep seldom waits on a load (each thread reads only the slots it filled
+// itself: no block barrier)
 template <class M, bool kTend = false, bool kStage = false>
 __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P, const LevelTab &lt, bool fast, int c,
-                                               double *tend = nullptr, double *stg = nullptr) {
+                                               double *tend = nullptr, double *stg = nullptr, int ss = kBlock) {
   const double *sdz = lt.dz, *sdzdt = lt.dzdt;
   if constexpr (kStage) {
     static_assert(!M::kWarm && !M::kAero && !M::kTri, "the stage holds the 16 standard fields");
     const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
     const double *src = a.fld + (size_t)(a.nlev - 1) * a.pitch + c;
 #pragma unroll
-    for (int f = 0; f < kStageFields; ++f) cp_async8(stg + f * kBlock, src + f * fs);
+    for (int f = 0; f < kStageFields; ++f) cp_async8(stg + f * ss, src + f * fs);
     cp_async_commit();
   }
   using R = typename M::R;
@@ -1667,23 +1668,23 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
     Pt s;
     if constexpr (kStage) {
       const int b = (a.nlev - 1 - k) & 1;
-      const double *cur = stg + b * kStageFields * kBlock;
+      const double *cur = stg + b * kStageFields * ss;
       if (k > 0) {
-        double *nxt = stg + (b ^ 1) * kStageFields * kBlock;
+        double *nxt = stg + (b ^ 1) * kStageFields * ss;
         const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
         const double *src = a.fld + (size_t)(k - 1) * a.pitch + c;
 #pragma unroll
-        for (int f = 0; f < kStageFields; ++f) cp_async8(nxt + f * kBlock, src + f * fs);
+        for (int f = 0; f < kStageFields; ++f) cp_async8(nxt + f * ss, src + f * fs);
         cp_async_commit();
         cp_async_wait<1>();   // this level's copies (the older group) have landed
       } else {
         cp_async_wait<0>();
       }
-      s.T = cur[0 * kBlock]; s.qv = cur[1 * kBlock]; s.qc = cur[2 * kBlock]; s.qr = cur[3 * kBlock];
-      s.qi = cur[4 * kBlock]; s.qs = cur[5 * kBlock]; s.qg = cur[6 * kBlock];
-      s.nc = cur[7 * kBlock]; s.nr = cur[8 * kBlock]; s.ni = cur[9 * kBlock]; s.ns = cur[10 * kBlock];
-      s.ng = cur[11 * kBlock]; s.na = cur[12 * kBlock];
-      s.p = cur[13 * kBlock]; s.rho = cur[14 * kBlock]; s.w = cur[15 * kBlock];
+      s.T = cur[0 * ss]; s.qv = cur[1 * ss]; s.qc = cur[2 * ss]; s.qr = cur[3 * ss];
+      s.qi = cur[4 * ss]; s.qs = cur[5 * ss]; s.qg = cur[6 * ss];
+      s.nc = cur[7 * ss]; s.nr = cur[8 * ss]; s.ni = cur[9 * ss]; s.ns = cur[10 * ss];
+      s.ng = cur[11 * ss]; s.na = cur[12 * ss];
+      s.p = cur[13 * ss]; s.rho = cur[14 * ss]; s.w = cur[15 * ss];
     } else {
       load_pt<M::kWarm, M::kAero, M::kTri>(a, k, c, s);
     }
