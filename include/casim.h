@@ -71,13 +71,16 @@ enum casim_status {
   CASIM_ERR_CFL = -5,        /* casim_get_error: substep cap reached in sedimentation */
   CASIM_ERR_TIMEOUT = -6,    /* casim_get_error: a bounded wait inside the surrogate network's
                                 kernel gave up; its rows were left to the scheme's rates */
-  CASIM_ERR_IO = -7          /* a checkpoint file could not be opened, read or written */
+  CASIM_ERR_IO = -7,         /* a checkpoint file could not be opened, read or written */
+  CASIM_ERR_INDEX = -8       /* casim_get_error: the debug build (libcasim_debug.so) found an
+                                index outside its array and skipped the access */
 };
 
 /* device error-word bits (casim_get_error) */
 #define CASIM_EFLAG_NONFINITE 1u
 #define CASIM_EFLAG_CFL 2u
 #define CASIM_EFLAG_TIMEOUT 4u
+#define CASIM_EFLAG_INDEX 8u   /* debug build only: an index check failed */
 
 /* Scheme parameters.  casim_default_params() fills the published values the
    scheme is defined with; callers may change them before casim_init(). */
@@ -164,6 +167,13 @@ int casim_default_params(casim_params *p);
    context. */
 #define CASIM_THREE_MOMENT 4
 
+/* casim_init flag (standard configuration only: not with CASIM_WARM,
+   CASIM_AEROSOL or CASIM_THREE_MOMENT): casim_step and casim_step_host also
+   count per-step statistics, read by casim_get_stats.  The step then runs a
+   statistics build of its kernel (one warp-aggregated atomic per counter and
+   warp).  No paper counterpart: diagnostics of where the scheme acts. */
+#define CASIM_STATS 8
+
 /* Largest level count of a column (the step keeps a column's dz in shared
    memory). */
 #define CASIM_MAX_LEV 1024
@@ -236,9 +246,29 @@ int casim_wait_selftest(casim_ctx *ctx, long long limit_ns, long long *elapsed_n
 
 /* Wait for `stream`, read and clear the device error word.  *flags receives the
    CASIM_EFLAG_* bits (may be NULL).  Returns CASIM_OK, CASIM_ERR_NONFINITE or
-   CASIM_ERR_CFL (the first set, in that order of precedence, after CASIM_ERR_TIMEOUT),
-   or CASIM_ERR_CUDA. */
+   CASIM_ERR_CFL (the first set, in that order of precedence, after CASIM_ERR_INDEX
+   and CASIM_ERR_TIMEOUT), or CASIM_ERR_CUDA. */
 int casim_get_error(casim_ctx *ctx, unsigned *flags, void *stream);
+
+/* Statistics counted by a CASIM_STATS context since casim_init or the last
+   reset, over casim_step and casim_step_host calls. */
+typedef struct {
+  long long steps;            /* calls counted */
+  long long points;           /* grid points stepped (sum of ncols x nlev) */
+  long long active_points;    /* points the activity flag (any hydrometeor above q_min, or
+                                 supersaturation over liquid, or over ice below T_nuc) sent
+                                 through the processes */
+  long long changed_points;   /* points the step changed (processes or sedimentation) */
+  long long active_columns;   /* columns with at least one active point, summed over steps */
+  long long nsub[4][65];      /* per sedimenting species r, i, s, g: columns whose sweep took
+                                 n substeps, n = 1..64 (1 in the single-substep path and for a
+                                 species absent from the column, as max(1, ceil(Courant))) */
+} casim_stats;
+
+/* Wait for `stream` and copy the statistics into *out; reset != 0 then sets
+   them to zero.  CASIM_ERR_ARG if the context was not created with
+   CASIM_STATS or out is NULL. */
+int casim_get_stats(casim_ctx *ctx, casim_stats *out, int reset, void *stream);
 
 /* ----------------------------------------------------------------------------
  * Batches: many independent domains advanced by one launch per step.

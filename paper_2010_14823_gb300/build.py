@@ -9,6 +9,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libcasim.so")
+# the same library with every index checked (-DCASIM_DEBUG): an index outside
+# its array sets CASIM_EFLAG_INDEX in the error word and the access is skipped
+LIB_DEBUG = os.path.join(HERE, "libcasim_debug.so")
 SOURCES = [os.path.join(CSRC, "casim.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
@@ -33,12 +36,13 @@ def _stale(lib: str, deps: list[str]) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libcasim.so and libcasim_peaks.so (concurrently) where missing
-    or older than their sources."""
+    """Compile libcasim.so, its index-checked build libcasim_debug.so and
+    libcasim_peaks.so (concurrently) where missing or older than their sources."""
     jobs = []
-    for lib, srcs, deps in ((LIB, SOURCES, DEPS), (PEAKS_LIB, PEAKS_SOURCES, PEAKS_DEPS)):
+    for lib, srcs, deps, extra in ((LIB, SOURCES, DEPS, []), (LIB_DEBUG, SOURCES, DEPS, ["-DCASIM_DEBUG"]),
+                                   (PEAKS_LIB, PEAKS_SOURCES, PEAKS_DEPS, [])):
         if force or _stale(lib, deps):
-            cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", lib + ".tmp"] + srcs
+            cmd = [nvcc()] + NVCC_FLAGS + extra + (["-Xptxas", "-v"] if verbose else []) + ["-o", lib + ".tmp"] + srcs
             jobs.append((lib, subprocess.Popen(cmd)))
     for lib, p in jobs:
         if p.wait() != 0:

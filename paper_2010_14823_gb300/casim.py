@@ -14,7 +14,7 @@ import re
 
 import numpy as np
 
-from .build import LIB, INCLUDE
+from .build import LIB, LIB_DEBUG, INCLUDE
 
 CASIM_FP64 = 0
 CASIM_MIXED = 1
@@ -33,9 +33,12 @@ NSUB_MAX = 64
 EFLAG_NONFINITE = 1
 EFLAG_CFL = 2
 EFLAG_TIMEOUT = 4
+EFLAG_INDEX = 8         # the debug build (libcasim_debug.so): an index check failed
+CASIM_STATS = 8         # casim_init flag: per-step statistics (casim_get_stats)
 NOALLOC_MAX_COLS = 1 << 20
 _ERRORS = {-1: "CASIM_ERR_ARG", -2: "CASIM_ERR_OOM", -3: "CASIM_ERR_CUDA",
-           -4: "CASIM_ERR_NONFINITE", -5: "CASIM_ERR_CFL", -6: "CASIM_ERR_TIMEOUT", -7: "CASIM_ERR_IO"}
+           -4: "CASIM_ERR_NONFINITE", -5: "CASIM_ERR_CFL", -6: "CASIM_ERR_TIMEOUT", -7: "CASIM_ERR_IO",
+           -8: "CASIM_ERR_INDEX"}
 
 
 class CasimError(RuntimeError):
@@ -66,6 +69,12 @@ class casim_state(ctypes.Structure):
                 ("dz", ctypes.c_void_p), ("precip", ctypes.c_void_p)]
 
 
+class casim_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("points", ctypes.c_longlong), ("active_points", ctypes.c_longlong),
+                ("changed_points", ctypes.c_longlong), ("active_columns", ctypes.c_longlong),
+                ("nsub", (ctypes.c_longlong * 65) * 4)]
+
+
 class casim_tune_entry(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("compact", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("ms_per_step", ctypes.c_float)]
@@ -74,102 +83,116 @@ class casim_tune_entry(ctypes.Structure):
 _lib = None
 
 
+def library_path() -> str:
+    """The library this process uses: libcasim.so, or its index-checked build
+    libcasim_debug.so when the environment sets CASIM_LIBRARY=debug."""
+    return LIB_DEBUG if os.environ.get("CASIM_LIBRARY", "") == "debug" else LIB
+
+
 def lib():
-    """Load libcasim.so (raises if it has not been built)."""
+    """Load the library (raises if it has not been built)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
-            raise RuntimeError(f"{LIB} is missing: build it with "
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
                                "`python -c 'import __graft_entry__ as g; g.build()'`")
-        L = ctypes.CDLL(LIB)
-        vp, i, d, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint
-        ps = ctypes.POINTER(casim_state)
-        L.casim_default_params.argtypes = [ctypes.POINTER(casim_params)]
-        L.casim_default_params.restype = i
-        L.casim_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(casim_params), i, i]
-        L.casim_init.restype = i
-        L.casim_step.argtypes = [vp, ps, i, i, d, vp]
-        L.casim_step.restype = i
-        L.casim_step_tendency.argtypes = [vp, ps, i, i, d, vp, vp]
-        L.casim_step_tendency.restype = i
-        L.casim_step_host.argtypes = [vp, ps, i, i, d, vp]
-        L.casim_step_host.restype = i
-        L.casim_budget.argtypes = [vp, ps, i, i, vp, vp]
-        for name in ("casim_state_save", "casim_state_load"):
-            getattr(L, name).argtypes = [ctypes.c_char_p, ctypes.c_void_p, ps, i, i, i, vp]
-            getattr(L, name).restype = i
-        L.casim_budget.restype = i
-        L.casim_get_error.argtypes = [vp, ctypes.POINTER(u), vp]
-        L.casim_wait_selftest.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong), vp]
-        L.casim_wait_selftest.restype = i
-        L.casim_get_error.restype = i
-        L.casim_launch_count.argtypes = [vp]
-        L.casim_launch_count.restype = ctypes.c_longlong
-        L.casim_last_cuda_error.argtypes = []
-        L.casim_last_cuda_error.restype = ctypes.c_char_p
-        L.casim_free.argtypes = [vp]
-        L.casim_free.restype = None
-        L.casim_abi_version.argtypes = []
-        L.casim_abi_version.restype = i
-        pi = ctypes.POINTER(i)
-        L.casim_batch_create.argtypes = [vp, ps, pi, pi, i, ctypes.POINTER(vp)]
-        L.casim_batch_create.restype = i
-        L.casim_batch_step.argtypes = [vp, vp, d, vp]
-        L.casim_batch_step.restype = i
-        L.casim_step_batched.argtypes = [vp, ps, pi, pi, i, d, vp]
-        L.casim_step_batched.restype = i
-        L.casim_batch_config.argtypes = [vp, i, i, i]
-        L.casim_batch_config.restype = i
-        L.casim_batch_get_config.argtypes = [vp, pi, pi, pi]
-        L.casim_batch_get_config.restype = i
-        L.casim_batch_tune.argtypes = [vp, vp, d, i, vp, ctypes.POINTER(casim_tune_entry), i]
-        L.casim_batch_tune.restype = i
-        L.casim_batch_tune_steps.argtypes = [i]
-        L.casim_batch_tune_steps.restype = i
-        L.casim_batch_graph.argtypes = [vp, vp, d, i, vp]
-        L.casim_batch_graph.restype = i
-        L.casim_batch_graph_launch.argtypes = [vp, vp]
-        L.casim_batch_graph_launch.restype = i
-        L.casim_batch_columns.argtypes = [vp]
-        L.casim_batch_columns.restype = ctypes.c_longlong
-        L.casim_batch_free.argtypes = [vp]
-        L.casim_batch_free.restype = None
-        L.casim_step_noalloc.argtypes = [ctypes.POINTER(casim_params), i, ps, i, i, d, vp, ctypes.POINTER(u)]
-        L.casim_step_noalloc.restype = i
-        pf = ctypes.POINTER(ctypes.c_float)
-        ll = ctypes.c_longlong
-        L.casim_mlp_create.argtypes = [ctypes.POINTER(vp), ctypes.c_ulonglong]
-        L.casim_mlp_create.restype = i
-        L.casim_mlp_param_count.argtypes = []
-        L.casim_mlp_param_count.restype = ll
-        L.casim_mlp_set_params.argtypes = [vp, pf, ll]
-        L.casim_mlp_set_params.restype = i
-        L.casim_mlp_get_params.argtypes = [vp, pf, ll]
-        L.casim_mlp_get_params.restype = i
-        L.casim_mlp_forward_host.argtypes = [vp, pf, i, pf]
-        L.casim_mlp_forward_host.restype = i
-        L.casim_mlp_forward.argtypes = [vp, vp, ctypes.c_longlong, vp, vp]
-        L.casim_mlp_forward.restype = i
-        L.casim_mlp_loss_grad_host.argtypes = [vp, pf, pf, pf, i, ctypes.POINTER(d), pf]
-        L.casim_mlp_loss_grad_host.restype = i
-        L.casim_mlp_data.argtypes = [vp, ps, i, i, d, vp, vp, vp, vp, ll, ctypes.POINTER(ll), vp]
-        L.casim_mlp_data.restype = i
-        L.casim_mlp_fit.argtypes = [vp, vp, vp, vp, ll, i, i, ctypes.c_float, ctypes.c_ulonglong, pf, vp]
-        L.casim_mlp_fit.restype = i
-        L.casim_mlp_get_norm.argtypes = [vp, pf]
-        L.casim_mlp_get_norm.restype = i
-        L.casim_mlp_set_norm.argtypes = [vp, pf]
-        L.casim_mlp_set_norm.restype = i
-        L.casim_step_surrogate.argtypes = [vp, vp, ps, i, i, d, vp, ctypes.POINTER(ll)]
-        L.casim_step_surrogate.restype = i
-        L.casim_batch_step_surrogate.argtypes = [vp, vp, vp, d, vp, ctypes.POINTER(ll)]
-        L.casim_batch_step_surrogate.restype = i
-        L.casim_mlp_set_engine.argtypes = [vp, i]
-        L.casim_mlp_set_engine.restype = i
-        L.casim_mlp_free.argtypes = [vp]
-        L.casim_mlp_free.restype = None
+        L = bind(ctypes.CDLL(path))
         _lib = L
     return _lib
+
+
+def bind(L):
+    """Declare the argument and result types of a loaded library's entry points."""
+    vp, i, d, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint
+    ps = ctypes.POINTER(casim_state)
+    L.casim_default_params.argtypes = [ctypes.POINTER(casim_params)]
+    L.casim_default_params.restype = i
+    L.casim_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(casim_params), i, i]
+    L.casim_init.restype = i
+    L.casim_step.argtypes = [vp, ps, i, i, d, vp]
+    L.casim_step.restype = i
+    L.casim_step_tendency.argtypes = [vp, ps, i, i, d, vp, vp]
+    L.casim_step_tendency.restype = i
+    L.casim_step_host.argtypes = [vp, ps, i, i, d, vp]
+    L.casim_step_host.restype = i
+    L.casim_budget.argtypes = [vp, ps, i, i, vp, vp]
+    for name in ("casim_state_save", "casim_state_load"):
+        getattr(L, name).argtypes = [ctypes.c_char_p, ctypes.c_void_p, ps, i, i, i, vp]
+        getattr(L, name).restype = i
+    L.casim_budget.restype = i
+    L.casim_get_error.argtypes = [vp, ctypes.POINTER(u), vp]
+    L.casim_wait_selftest.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong), vp]
+    L.casim_wait_selftest.restype = i
+    L.casim_get_error.restype = i
+    L.casim_launch_count.argtypes = [vp]
+    L.casim_launch_count.restype = ctypes.c_longlong
+    L.casim_last_cuda_error.argtypes = []
+    L.casim_last_cuda_error.restype = ctypes.c_char_p
+    L.casim_free.argtypes = [vp]
+    L.casim_free.restype = None
+    L.casim_abi_version.argtypes = []
+    L.casim_abi_version.restype = i
+    pi = ctypes.POINTER(i)
+    L.casim_batch_create.argtypes = [vp, ps, pi, pi, i, ctypes.POINTER(vp)]
+    L.casim_batch_create.restype = i
+    L.casim_batch_step.argtypes = [vp, vp, d, vp]
+    L.casim_batch_step.restype = i
+    L.casim_step_batched.argtypes = [vp, ps, pi, pi, i, d, vp]
+    L.casim_step_batched.restype = i
+    L.casim_batch_config.argtypes = [vp, i, i, i]
+    L.casim_batch_config.restype = i
+    L.casim_batch_get_config.argtypes = [vp, pi, pi, pi]
+    L.casim_batch_get_config.restype = i
+    L.casim_batch_tune.argtypes = [vp, vp, d, i, vp, ctypes.POINTER(casim_tune_entry), i]
+    L.casim_batch_tune.restype = i
+    L.casim_batch_tune_steps.argtypes = [i]
+    L.casim_batch_tune_steps.restype = i
+    L.casim_batch_graph.argtypes = [vp, vp, d, i, vp]
+    L.casim_batch_graph.restype = i
+    L.casim_batch_graph_launch.argtypes = [vp, vp]
+    L.casim_batch_graph_launch.restype = i
+    L.casim_batch_columns.argtypes = [vp]
+    L.casim_batch_columns.restype = ctypes.c_longlong
+    L.casim_batch_free.argtypes = [vp]
+    L.casim_batch_free.restype = None
+    L.casim_step_noalloc.argtypes = [ctypes.POINTER(casim_params), i, ps, i, i, d, vp, ctypes.POINTER(u)]
+    L.casim_step_noalloc.restype = i
+    pf = ctypes.POINTER(ctypes.c_float)
+    ll = ctypes.c_longlong
+    L.casim_mlp_create.argtypes = [ctypes.POINTER(vp), ctypes.c_ulonglong]
+    L.casim_mlp_create.restype = i
+    L.casim_mlp_param_count.argtypes = []
+    L.casim_mlp_param_count.restype = ll
+    L.casim_mlp_set_params.argtypes = [vp, pf, ll]
+    L.casim_mlp_set_params.restype = i
+    L.casim_mlp_get_params.argtypes = [vp, pf, ll]
+    L.casim_mlp_get_params.restype = i
+    L.casim_mlp_forward_host.argtypes = [vp, pf, i, pf]
+    L.casim_mlp_forward_host.restype = i
+    L.casim_mlp_forward.argtypes = [vp, vp, ctypes.c_longlong, vp, vp]
+    L.casim_mlp_forward.restype = i
+    L.casim_mlp_loss_grad_host.argtypes = [vp, pf, pf, pf, i, ctypes.POINTER(d), pf]
+    L.casim_mlp_loss_grad_host.restype = i
+    L.casim_mlp_data.argtypes = [vp, ps, i, i, d, vp, vp, vp, vp, ll, ctypes.POINTER(ll), vp]
+    L.casim_mlp_data.restype = i
+    L.casim_mlp_fit.argtypes = [vp, vp, vp, vp, ll, i, i, ctypes.c_float, ctypes.c_ulonglong, pf, vp]
+    L.casim_mlp_fit.restype = i
+    L.casim_mlp_get_norm.argtypes = [vp, pf]
+    L.casim_mlp_get_norm.restype = i
+    L.casim_mlp_set_norm.argtypes = [vp, pf]
+    L.casim_mlp_set_norm.restype = i
+    L.casim_step_surrogate.argtypes = [vp, vp, ps, i, i, d, vp, ctypes.POINTER(ll)]
+    L.casim_step_surrogate.restype = i
+    L.casim_batch_step_surrogate.argtypes = [vp, vp, vp, d, vp, ctypes.POINTER(ll)]
+    L.casim_batch_step_surrogate.restype = i
+    L.casim_mlp_set_engine.argtypes = [vp, i]
+    L.casim_mlp_set_engine.restype = i
+    L.casim_mlp_free.argtypes = [vp]
+    L.casim_mlp_free.restype = None
+    L.casim_get_stats.argtypes = [vp, ctypes.POINTER(casim_stats), i, vp]
+    L.casim_get_stats.restype = i
+    return L
 
 
 def declared_functions(header: str | None = None) -> list[str]:
@@ -272,6 +295,15 @@ def casim_get_error(ctx, stream=None) -> tuple[int, int]:
     if rc == -3:
         _check(rc, "casim_get_error")
     return rc, f.value
+
+
+def casim_get_stats(ctx, reset: bool = False, stream=None) -> dict:
+    """Statistics of a CASIM_STATS context (waits for the stream)."""
+    st = casim_stats()
+    _check(lib().casim_get_stats(ctx, ctypes.byref(st), int(reset), _stream(stream)), "casim_get_stats")
+    return {"steps": st.steps, "points": st.points, "active_points": st.active_points,
+            "changed_points": st.changed_points, "active_columns": st.active_columns,
+            "nsub": np.array([[st.nsub[x][n] for n in range(65)] for x in range(4)], dtype=np.int64)}
 
 
 def casim_launch_count(ctx) -> int:

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -58,6 +59,10 @@ struct casim_ctx {
   casim_batch *sb = nullptr;
   std::vector<casim_state> sb_dom;
   std::vector<int> sb_ncols, sb_nlev;
+  // CASIM_STATS: the device counters (ColStats words) and the host's
+  bool stats = false;
+  unsigned long long *d_stats = nullptr;
+  long long stat_steps = 0, stat_points = 0;
 };
 
 static thread_local char g_last_error[256] = "";
@@ -215,7 +220,8 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   if (!out) return CASIM_ERR_ARG;
   *out = nullptr;
   if (precision != CASIM_FP64 && precision != CASIM_MIXED) return CASIM_ERR_ARG;
-  if ((flags & ~(CASIM_WARM | CASIM_AEROSOL | CASIM_THREE_MOMENT)) != 0) return CASIM_ERR_ARG;
+  if ((flags & ~(CASIM_WARM | CASIM_AEROSOL | CASIM_THREE_MOMENT | CASIM_STATS)) != 0) return CASIM_ERR_ARG;
+  if ((flags & CASIM_STATS) && (flags & (CASIM_WARM | CASIM_AEROSOL | CASIM_THREE_MOMENT))) return CASIM_ERR_ARG;
   if ((flags & CASIM_AEROSOL) && (flags & CASIM_THREE_MOMENT)) return CASIM_ERR_ARG;
   if ((flags & CASIM_THREE_MOMENT) && params) {
     // the shape identity needs b = 3 for every species that carries z
@@ -251,6 +257,12 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_step_batch<PolicyMix, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)batch_smem_bytes<PolicyMix>(kBatchMaxBlock, kMaxLev));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step<PolicyMix, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)step_smem_bytes<PolicyMix, false>(kMaxLev));
+  ctx->stats = (flags & CASIM_STATS) != 0;
+  if (e == cudaSuccess && ctx->stats) e = cudaMalloc(&ctx->d_stats, kStatsWords * sizeof(unsigned long long));
+  if (e == cudaSuccess && ctx->stats) e = cudaMemset(ctx->d_stats, 0, kStatsWords * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->d_err, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
@@ -264,6 +276,9 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
 }
 
 static_assert(kMaxLev == CASIM_MAX_LEV, "the header's level limit is the kernels' shared dz array");
+static_assert(kEflagIndex == CASIM_EFLAG_INDEX, "the debug build's error bit");
+static_assert(kStatsWords == 3 + 4 * 65 && sizeof(((casim_stats *)0)->nsub) == 4 * 65 * sizeof(long long),
+              "the statistics buffer's layout");
 
 static int check_state(const casim_state *s, int ncols, int nlev, double dt) {
   if (!s || ncols < 0 || nlev < 1 || nlev > kMaxLev || !(dt > 0.0) || !std::isfinite(dt)) return CASIM_ERR_ARG;
@@ -285,6 +300,7 @@ static KArgs make_args(const casim_ctx *ctx, const casim_state *s, int ncols, in
   a.nlev = nlev;
   a.dt = dt;
   a.surr = nullptr;
+  a.stats = ctx->stats ? ctx->d_stats : nullptr;
   return a;
 }
 
@@ -301,6 +317,16 @@ static int ctx_nprecip(const casim_ctx *ctx) { return CASIM_NPRECIP + (ctx->aero
 template <class PMix, class PF64>
 static void launch_pair(const casim_ctx *ctx, dim3 grid, cudaStream_t st, const KArgs &a, double *tend) {
   const KParams &kp = ctx->kp;
+  if constexpr (std::is_same<PMix, PolicyMix>::value) {
+    // the statistics build (a CASIM_STATS context: standard configuration)
+    if (a.stats && !tend) {
+      if (ctx->precision == CASIM_MIXED)
+        k_step<PMix, false, true><<<grid, kBlock, step_smem_bytes<PMix, false>(a.nlev), st>>>(a, kp, nullptr);
+      else
+        k_step<PF64, false, true><<<grid, kBlock, step_smem_bytes<PF64, false>(a.nlev), st>>>(a, kp, nullptr);
+      return;
+    }
+  }
   if (ctx->precision == CASIM_MIXED) {
     if (tend) k_step<PMix, true><<<grid, kBlock, step_smem_bytes<PMix, true>(a.nlev), st>>>(a, kp, tend);
     else k_step<PMix, false><<<grid, kBlock, step_smem_bytes<PMix, false>(a.nlev), st>>>(a, kp, nullptr);
@@ -340,13 +366,26 @@ extern "C" int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int nco
   return launch_step(ctx, a, ncols, tend, stream);
 }
 
-extern "C" int casim_step(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream) {
-  NvtxRange nvtx_range_("casim_step");
-  if (!ctx) return CASIM_ERR_ARG;
+static int step_device(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream) {
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
   const KArgs a = make_args(ctx, s, ncols, nlev, dt);
   return launch_step(ctx, a, ncols, nullptr, stream);
+}
+
+// a CASIM_STATS context counts the step and its points on the host
+static void count_step(casim_ctx *ctx, int ncols, int nlev) {
+  if (!ctx->stats) return;
+  ++ctx->stat_steps;
+  ctx->stat_points += (long long)ncols * nlev;
+}
+
+extern "C" int casim_step(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream) {
+  NvtxRange nvtx_range_("casim_step");
+  if (!ctx) return CASIM_ERR_ARG;
+  const int rc = step_device(ctx, s, ncols, nlev, dt, stream);
+  if (rc == CASIM_OK) count_step(ctx, ncols, nlev);
+  return rc;
 }
 
 static int grow(double **buf, size_t *cap, size_t n) {
@@ -435,7 +474,7 @@ extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, 
     d.pitch = h->pitch;
     d.dz = ctx->h2d_dz;
     d.precip = ctx->h2d_precip[0];
-    if ((rc = casim_step(ctx, &d, ncols, nlev, dt, stream)) != CASIM_OK) return rc;
+    if ((rc = step_device(ctx, &d, ncols, nlev, dt, stream)) != CASIM_OK) return rc;
     const size_t fsz = (size_t)nlev * h->pitch, nprog = (size_t)CASIM_NPROG * fsz;
     CUDA_TRY(cudaMemcpyAsync(h->fld, ctx->h2d_fld[0], nprog * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (NF > CASIM_NFIELDS)   // the configuration's prognostic fields after the inputs
@@ -443,6 +482,7 @@ extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, 
                                (size_t)(NF - CASIM_NFIELDS) * fsz * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(h->precip, ctx->h2d_precip[0], np * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
+    count_step(ctx, ncols, nlev);
     return CASIM_OK;
   }
   const int S = std::min(casim_ctx::kStages, nchunk);
@@ -475,7 +515,7 @@ extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, 
     d.pitch = W;
     d.dz = ctx->h2d_dz;
     d.precip = ctx->h2d_precip[s];
-    rc = casim_step(ctx, &d, wc, nlev, dt, ctx->hst[s]);
+    rc = step_device(ctx, &d, wc, nlev, dt, ctx->hst[s]);
     if (rc != CASIM_OK) break;
     e = copy_chunk(ctx->h2d_fld[s], ctx->h2d_precip[s], W, h, c0, wc, nlev, NF, NP, cudaMemcpyDeviceToHost,
                    ctx->hst[s]);
@@ -485,6 +525,7 @@ extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, 
     if (e == cudaSuccess) e = es;
   }
   if (e != cudaSuccess) return cuda_fail(e, "casim_step_host");
+  if (rc == CASIM_OK) count_step(ctx, ncols, nlev);
   return rc;
 }
 
@@ -508,6 +549,7 @@ extern "C" int casim_get_error(casim_ctx *ctx, unsigned *flags, void *stream) {
   CUDA_TRY(cudaMemcpy(&h, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
   if (flags) *flags = h;
+  if (h & CASIM_EFLAG_INDEX) return CASIM_ERR_INDEX;
   if (h & CASIM_EFLAG_TIMEOUT) return CASIM_ERR_TIMEOUT;
   if (h & CASIM_EFLAG_NONFINITE) return CASIM_ERR_NONFINITE;
   if (h & CASIM_EFLAG_CFL) return CASIM_ERR_CFL;
@@ -670,6 +712,7 @@ static BatchArgs batch_args(const casim_batch *b, double dt) {
   a.persistent = b->persistent;
   a.surr = nullptr;
   a.maxlev = b->maxlev;
+  a.ndom = b->ndom;
   return a;
 }
 
@@ -1003,6 +1046,7 @@ extern "C" int casim_step_noalloc(const casim_params *params, int precision, con
   a.persistent = 1;
   a.surr = nullptr;
   a.maxlev = nlev;
+  a.ndom = 1;
   int per_sm = 1;
   if (precision == CASIM_MIXED) {
     k_compact<PolicyMix><<<ntiles, kTile, 0, st>>>(a, sc->tiles, ntiles, kp);
@@ -1202,8 +1246,9 @@ static void mlp_cast(casim_mlp *m, cudaStream_t st) {
 // feature pass before it on the stream) and n is its upper bound
 static cudaError_t mlp_forward_umma(casim_mlp *m, const __nv_bfloat16 *xb, long long n, const long long *rowpt,
                                     float4 *surr, unsigned *err, int nsm, cudaStream_t st, float *y = nullptr,
-                                    const unsigned long long *rows_dev = nullptr) {
+                                    const unsigned long long *rows_dev = nullptr, long long npts = 0) {
   UmmaArgs u;
+  u.npts = npts;
   u.xb = xb;
   u.rows = n;
   u.rows_dev = rows_dev;
@@ -1573,7 +1618,7 @@ extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_st
   const long long rows = std::min((long long)hrows, m->cap_rows);
   // 2. the network on the rows
   if (m->engine == 1) {
-    CUDA_TRY(mlp_forward_umma(m, m->xb, rows, m->rowpt, m->surr, ctx->d_err, ctx->nsm, st));
+    CUDA_TRY(mlp_forward_umma(m, m->xb, rows, m->rowpt, m->surr, ctx->d_err, ctx->nsm, st, nullptr, nullptr, np));
     ctx->launches++;
   } else {
     const int chunk = 1 << 17;
@@ -1584,7 +1629,7 @@ extern "C" int casim_step_surrogate(casim_ctx *ctx, casim_mlp *m, const casim_st
       m->h0 = m->xb + r0 * kNinPad;
       mlp_forward(m, n, false, st);
       m->h0 = save;
-      k_mlp_scatter<<<(n + 255) / 256, 256, 0, st>>>(m->y, n, m->rowpt + r0, m->norm, m->surr);
+      k_mlp_scatter<<<(n + 255) / 256, 256, 0, st>>>(m->y, n, m->rowpt + r0, m->norm, m->surr, np, ctx->d_err);
       ctx->launches += 5;
     }
   }
@@ -1633,7 +1678,7 @@ extern "C" int casim_batch_step_surrogate(casim_ctx *ctx, casim_batch *b, casim_
   long long rows = -1;
   if (m->engine == 1) {
     CUDA_TRY(mlp_forward_umma(m, m->xb, m->cap_rows, m->rowpt, m->surr, ctx->d_err, ctx->nsm, st, nullptr,
-                              m->rowctr));
+                              m->rowctr, b->total_pts));
     ctx->launches++;
   } else {
     unsigned long long hrows = 0;
@@ -1648,7 +1693,8 @@ extern "C" int casim_batch_step_surrogate(casim_ctx *ctx, casim_batch *b, casim_
       m->h0 = m->xb + r0 * kNinPad;
       mlp_forward(m, n, false, st);
       m->h0 = save;
-      k_mlp_scatter<<<(n + 255) / 256, 256, 0, st>>>(m->y, n, m->rowpt + r0, m->norm, m->surr);
+      k_mlp_scatter<<<(n + 255) / 256, 256, 0, st>>>(m->y, n, m->rowpt + r0, m->norm, m->surr, b->total_pts,
+                                                     ctx->d_err);
       ctx->launches += 5;
     }
   }
@@ -1758,10 +1804,32 @@ extern "C" int casim_state_load(const char *path, const casim_params *params, co
   return CASIM_OK;
 }
 
+extern "C" int casim_get_stats(casim_ctx *ctx, casim_stats *out, int reset, void *stream) {
+  if (!ctx || !ctx->stats || !out) return CASIM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long h[kStatsWords];
+  CUDA_TRY(cudaMemcpyAsync(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  out->steps = ctx->stat_steps;
+  out->points = ctx->stat_points;
+  out->active_points = (long long)h[0];
+  out->changed_points = (long long)h[1];
+  out->active_columns = (long long)h[2];
+  for (int x = 0; x < 4; ++x)
+    for (int n = 0; n < 65; ++n) out->nsub[x][n] = (long long)h[3 + 65 * x + n];
+  if (reset) {
+    CUDA_TRY(cudaMemsetAsync(ctx->d_stats, 0, sizeof(h), st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    ctx->stat_steps = ctx->stat_points = 0;
+  }
+  return CASIM_OK;
+}
+
 extern "C" void casim_free(casim_ctx *ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
   casim_batch_free(ctx->sb);
+  if (ctx->d_stats) cudaFree(ctx->d_stats);
   if (ctx->d_err) cudaFree(ctx->d_err);
   for (int s = 0; s < casim_ctx::kStages; ++s) {
     if (ctx->h2d_fld[s]) cudaFree(ctx->h2d_fld[s]);

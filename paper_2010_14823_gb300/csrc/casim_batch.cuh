@@ -49,6 +49,7 @@ struct BatchArgs {
   int persistent;
   const float4 *surr;   // surrogate warm-rain rates of every point of the batch (pt_off per domain), or null
   int maxlev;           // most levels of any domain (the level tables' size)
+  int ndom;             // domains in the table
 };
 
 // dynamic shared memory of the batched step: the mixed step's prefetch stage
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(kTile) k_compact(const BatchArgs b, const Item
   __syncthreads();
   if (act) {
     const int pos = s_base + s_warp[wid] + __popc(ball & ((1u << lane) - 1u));
-    b.list[d.list_off + pos] = c;
+    if (CASIM_INDEX_OK(pos < d.ncols, b.err)) b.list[d.list_off + pos] = c;
   }
 }
 
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(kNarrow ? kBatchNarrowBlock : kBatchMaxBlock,
     }
     if (it >= b.nitems) break;
     const Item item = b.items[it];
+    if (!CASIM_INDEX_OK(item.dom >= 0 && item.dom < b.ndom, b.err)) break;
     const DomDesc d = b.dom[item.dom];
     const int n = b.compact ? b.count[item.dom] : d.ncols;
     if (item.chunk * B < n) {
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(kNarrow ? kBatchNarrowBlock : kBatchMaxBlock,
       for (int x = 1; x < 5; ++x) fast &= ((P.vmax[x] * b.dt) / d.dzmin) / P.c_max <= 1.0;
       const int idx = item.chunk * B + tid;
       if (idx < n) {
-        const int c = b.compact ? b.list[d.list_off + idx] : idx;
+        const int c = b.compact && CASIM_INDEX_OK(idx < d.ncols, b.err) ? b.list[d.list_off + idx] : idx;
         KArgs a;
         a.fld = d.fld;
         a.pitch = d.pitch;
@@ -167,6 +169,7 @@ __global__ void __launch_bounds__(kNarrow ? kBatchNarrowBlock : kBatchMaxBlock,
         a.nlev = d.nlev;
         a.dt = b.dt;
         a.surr = b.surr ? b.surr + d.pt_off : nullptr;
+        a.stats = nullptr;
         eflag |= run_column<M, false, kStage>(a, P, lt, fast, c, nullptr, kStage ? stage + tid : nullptr, B);
       }
     }

@@ -94,7 +94,20 @@ struct KArgs {
   int ncols, nlev;
   double dt;
   const float4 *surr;   // [nlev][pitch] surrogate warm-rain rates (mixed form), or null
+  unsigned long long *stats;   // per-step statistics (the statistics build of the step), or null
 };
+
+// Per-step statistics of one column: points the activity flag sent through
+// the processes, points the step changed, and the substeps each sedimenting
+// species took (1 in the single-substep path).  The statistics instantiation
+// of the step adds them to a device buffer: [0] active points, [1] changed
+// points, [2] columns with an active point, [3 + 65 x + n] columns whose
+// species x (r, i, s, g) took n substeps.
+struct ColStats {
+  int active, changed;
+  int nsub[4];
+};
+constexpr int kStatsWords = 3 + 4 * 65;
 
 // ------------------------------------------------------- conversions
 // FP64 <-> FP32 on the integer pipe.  Values handled here are finite and, as
@@ -168,6 +181,22 @@ __device__ __forceinline__ float rcpa(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+
+// Debug build (CASIM_DEBUG): every index into the state, the precipitation
+// rows, the batch's lists and the surrogate's rows is checked against its
+// array; one outside sets this bit of the error word and the access is
+// skipped (the kernel never traps).  In the normal build the checks compile
+// to nothing.
+constexpr unsigned kEflagIndex = 8u;
+#ifdef CASIM_DEBUG
+__device__ __forceinline__ bool index_ok(bool ok, unsigned *err) {
+  if (!ok && err) atomicOr(err, kEflagIndex);
+  return ok;
+}
+#define CASIM_INDEX_OK(cond, err) ::casim_dev::index_ok((cond), (err))
+#else
+#define CASIM_INDEX_OK(cond, err) true
+#endif
 
 // non-finite test on the high word (integer pipe)
 __device__ __forceinline__ unsigned nonfinite(double x) {
@@ -1295,6 +1324,10 @@ struct PolicyMix3 : PolicyMix {
 // ---------------------------------------------------------------- kernels
 template <bool kWarm = false, bool kAero = false, bool kTri = false>
 __device__ __forceinline__ void load_pt(const KArgs &a, int k, int c, Pt &s) {
+  if (!CASIM_INDEX_OK(k >= 0 && k < a.nlev && c >= 0 && c < a.ncols && c < a.pitch, a.err)) {
+    s = Pt{};
+    return;
+  }
   const double *b = a.fld + (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
   s.T = b[0 * fs]; s.qv = b[1 * fs]; s.qc = b[2 * fs]; s.qr = b[3 * fs];
@@ -1335,6 +1368,7 @@ __device__ __forceinline__ unsigned nonfinite_in(const Pt &s) {
 }
 
 __device__ __forceinline__ unsigned store_pt(const KArgs &a, int k, int c, const Pt &s) {
+  if (!CASIM_INDEX_OK(k >= 0 && k < a.nlev && c >= 0 && c < a.ncols, a.err)) return 0u;
   double *b = a.fld + (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
   b[0 * fs] = s.T; b[1 * fs] = s.qv; b[2 * fs] = s.qc; b[3 * fs] = s.qr;
@@ -1350,6 +1384,7 @@ __device__ __forceinline__ unsigned store_pt(const KArgs &a, int k, int c, const
 // rain's sixth moment)
 template <bool kAero = false, bool kTri = false>
 __device__ __forceinline__ unsigned store_pt_warm(const KArgs &a, int k, int c, const Pt &s) {
+  if (!CASIM_INDEX_OK(k >= 0 && k < a.nlev && c >= 0 && c < a.ncols, a.err)) return 0u;
   double *b = a.fld + (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
   b[0 * fs] = s.T; b[1 * fs] = s.qv; b[2 * fs] = s.qc; b[3 * fs] = s.qr;
@@ -1389,6 +1424,7 @@ __device__ __forceinline__ double extra(const Pt &s, int i) {
 
 template <class M>
 __device__ __forceinline__ unsigned store_tend(const KArgs &a, double *tend, int k, int c, const Pt &s, bool fast) {
+  if (!CASIM_INDEX_OK(k >= 0 && k < a.nlev && c >= 0 && c < a.ncols, a.err)) return 0u;
   constexpr bool kWarm = M::kWarm;
   const size_t o = (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
@@ -1514,13 +1550,17 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Multi-substep sedimentation of one column after the processes (used when a
 // capped speed could exceed one level per step): per species, n_sub from the
 // largest Courant number, then n_sub top-down sweeps in place.
+// nsub_out (may be null): the substep count each sedimenting species took;
+// lvmask (may be null): bit k set for every level k the sweeps write
 template <class M, bool kTend>
 __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KParams &P, const double *sdz, int c,
-                                                      double prec[5], double *tend) {
+                                                      double prec[5], double *tend, int *nsub_out = nullptr,
+                                                      unsigned *lvmask = nullptr) {
   using R = typename M::R;
   using Ph = Phys<M>;
   const ConstK<R> &K = M::K(P);
   unsigned eflag = 0;
+  if (!CASIM_INDEX_OK(c >= 0 && c < a.ncols, a.err)) return 0u;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
   const double *rhop = a.fld + 14 * fs;
   double *state = kTend ? tend : a.fld;   // the processed state (tendency mode: scratch)
@@ -1551,6 +1591,7 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
     int ns = (int)ceil((double)M::div(cmax, M::toR(P.c_max)));
     if (ns < 1) ns = 1;
     if (ns > 64) { ns = 64; eflag |= 2u; }
+    if (nsub_out) nsub_out[x] = ns;
     const double dts = a.dt / ns;
     // the rain's aerosol mass moves with the rain (aerosol-mass policies)
     const bool aer = x < na3<M>();
@@ -1617,6 +1658,7 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
           }
           qp[o] = q;
           np[o] = n;
+          if (lvmask) lvmask[k >> 5] |= 1u << (k & 31);
           eflag |= nonfinite(q) | nonfinite(n);
         }
         Fu = F;
@@ -1640,12 +1682,14 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
 // fields are copied there by cp.async while level k is processed, so the
 // sweep seldom waits on a load (each thread reads only the slots it filled
 // itself: no block barrier)
-template <class M, bool kTend = false, bool kStage = false>
+template <class M, bool kTend = false, bool kStage = false, bool kStats = false>
 __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P, const LevelTab &lt, bool fast, int c,
-                                               double *tend = nullptr, double *stg = nullptr, int ss = kBlock) {
+                                               double *tend = nullptr, double *stg = nullptr, int ss = kBlock,
+                                               ColStats *cs = nullptr) {
   const double *sdz = lt.dz, *sdzdt = lt.dzdt;
   if constexpr (kStage) {
     static_assert(!M::kWarm && !M::kAero && !M::kTri, "the stage holds the 16 standard fields");
+    if (!CASIM_INDEX_OK(c >= 0 && c < a.ncols && c < a.pitch, a.err)) return 0u;
     const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
     const double *src = a.fld + (size_t)(a.nlev - 1) * a.pitch + c;
 #pragma unroll
@@ -1664,6 +1708,10 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
   R Fa[4] = {0, 0, 0, 0};       // aerosol mass in r, i, s, g (aerosol-mass policies)
   R Fz[4] = {0, 0, 0, 0};       // sixth moments of r, i, s, g (triple-moment policies)
 
+  // statistics build: the levels this column's step writes (processes and sweeps)
+  unsigned lvmask[kStats ? (kMaxLev + 31) / 32 : 1];
+  if constexpr (kStats)
+    for (int i = 0; i < (a.nlev + 31) / 32; ++i) lvmask[i] = 0u;
   for (int k = a.nlev - 1; k >= 0; --k) {
     Pt s;
     if constexpr (kStage) {
@@ -1693,6 +1741,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       eflag |= nonfinite_in(s);
       double es0, qs0;
       touched = F64T<M>::active(K, s, es0, qs0);
+      if constexpr (kStats) cs->active += touched;
       double mu3[4];
       unsigned keep3 = 0;   // species whose shape the processes left unchanged (triple-moment policies)
       if (touched) F64T<M>::process(K, s, a.dt, es0, qs0, mu3, &keep3);
@@ -1746,6 +1795,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       W<float> w;
       float es0, qs0;
       const bool act = MixT<M>::active(K, s, P.T0, w, es0, qs0);
+      if constexpr (kStats) cs->active += act;
       MixInc o;
       MassAcc macc;
       unsigned keep3 = 0;   // species whose shape the processes left unchanged (triple-moment policies)
@@ -1844,6 +1894,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
     } else {
       if (touched) {
         eflag |= store_pt(a, k, c, s);
+        if constexpr (kStats) lvmask[k >> 5] |= 1u << (k & 31);
         if constexpr (M::kTri) {
           // the sixth moments of r, i, s, g
           double *b = a.fld + (size_t)k * a.pitch + c;
@@ -1877,7 +1928,8 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       for (int x = 0; x < na3<M>(); ++x) prec[4] += M::toD(Fa[x]) * a.dt;
     }
   } else {
-    eflag |= sediment_substeps<M, kTend>(a, P, sdz, c, prec, tend);
+    eflag |= sediment_substeps<M, kTend>(a, P, sdz, c, prec, tend, kStats ? cs->nsub : nullptr,
+                                         kStats ? lvmask : nullptr);
     if constexpr (kTend) {
       // tendency mode: the new state in tend becomes (x_new - x_old) / dt
       const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
@@ -1897,18 +1949,45 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
 #pragma unroll
   for (int x = 0; x < 5; ++x) {
     if (x >= kSed && !(M::kAero && x == 4)) continue;
-    if (prec[x] != 0.0) {
+    if (prec[x] != 0.0 && CASIM_INDEX_OK(c >= 0 && c < a.ncols, a.err)) {
       double *pp = a.precip + (size_t)x * a.pitch + c;
       *pp += prec[x];
       eflag |= nonfinite(*pp);
     }
   }
+  if constexpr (kStats) {
+    int n = 0;
+    for (int i = 0; i < (a.nlev + 31) / 32; ++i) n += __popc(lvmask[i]);
+    cs->changed = n;
+  }
   return eflag;
 }
 
-// kTend: tendency mode (tend receives the source terms, a.fld unchanged)
-// dynamic shared memory: step_smem_bytes<M, kTend>(a.nlev)
-template <class M, bool kTend>
+// one column's statistics into the buffer: warp sums, one atomic per warp
+// and counter (per distinct substep count for the histogram)
+__device__ __forceinline__ void stats_add(unsigned long long *st, const ColStats &cs) {
+  const unsigned mask = __activemask();
+  const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+  const unsigned act = __reduce_add_sync(mask, (unsigned)cs.active);
+  const unsigned chg = __reduce_add_sync(mask, (unsigned)cs.changed);
+  const unsigned cols = __popc(__ballot_sync(mask, cs.active > 0));
+  if (lane == leader) {
+    atomicAdd(&st[0], (unsigned long long)act);
+    atomicAdd(&st[1], (unsigned long long)chg);
+    atomicAdd(&st[2], (unsigned long long)cols);
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int n = min(max(cs.nsub[x], 0), 64);
+    const unsigned peers = __match_any_sync(mask, n);
+    if (lane == __ffs(peers) - 1) atomicAdd(&st[3 + 65 * x + n], (unsigned long long)__popc(peers));
+  }
+}
+
+// kTend: tendency mode (tend receives the source terms, a.fld unchanged).
+// Dynamic shared memory: step_smem_bytes<M, kTend>(a.nlev).  kStats: the
+// statistics instantiation (standard configuration; a.stats set)
+template <class M, bool kTend, bool kStats = false>
 __global__ void __launch_bounds__(kBlock, M::kMinBlocks) k_step(const KArgs a, const KParams P, double *tend) {
   extern __shared__ __align__(16) unsigned char step_dyn[];
   const StepSmem sm = step_smem<M, kTend>(step_dyn, a.nlev);
@@ -1916,8 +1995,10 @@ __global__ void __launch_bounds__(kBlock, M::kMinBlocks) k_step(const KArgs a, c
   const int c = blockIdx.x * kBlock + threadIdx.x;
   if (c >= a.ncols) return;
   constexpr bool kStage = step_staged<M, kTend>();
-  const unsigned eflag =
-      run_column<M, kTend, kStage>(a, P, sm.lt, fast, c, tend, kStage ? sm.stage + threadIdx.x : nullptr);
+  ColStats cs{0, 0, {1, 1, 1, 1}};
+  const unsigned eflag = run_column<M, kTend, kStage, kStats>(a, P, sm.lt, fast, c, tend,
+                                                              kStage ? sm.stage + threadIdx.x : nullptr, kBlock, &cs);
+  if constexpr (kStats) stats_add(a.stats, cs);
   if (eflag) atomicOr(a.err, eflag);
 }
 

@@ -562,6 +562,7 @@ __global__ void __launch_bounds__(256) k_mlp_features_batch(const DomDesc *dom, 
     a.nlev = d.nlev;
     a.dt = dt;
     a.surr = nullptr;
+    a.stats = nullptr;
     feature_point(a, P, fa, g - d.pt_off, g, warm, f, y, mk);
   }
   feature_append(fa, warm, g, f, y, mk);
@@ -569,9 +570,10 @@ __global__ void __launch_bounds__(256) k_mlp_features_batch(const DomDesc *dom, 
 
 // network outputs (standardised log-rates) -> rates at the rows' points
 __global__ void k_mlp_scatter(const float *Yn, long long rows, const long long *rowpt, const float *norm,
-                              float4 *surr) {
+                              float4 *surr, long long npts, unsigned *err) {
   const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= rows) return;
+  if (!CASIM_INDEX_OK(rowpt[r] >= 0 && rowpt[r] < npts, err)) return;
   const float *muy = norm + 2 * kNin, *sdy = norm + 2 * kNin + kNout;
   float v[kNout];
 #pragma unroll
@@ -626,6 +628,7 @@ struct UmmaArgs {
   const float *theta;          // biases are read from the flat parameters
   const float *norm;           // output standardisation
   float4 *surr;                // rates at the points
+  long long npts;              // points of surr (the rows' point indices are below it)
   float *y;                    // [rows][4] standardised outputs when rowpt is null
   unsigned *err;
 };
@@ -877,7 +880,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_mlp_umma(const UmmaArgs u) 
           float y[kNout];
 #pragma unroll
           for (int i = 0; i < kNout; ++i) y[i] = v[i] + s_bias[3 * kNh + i];
-          if (u.rowpt) {
+          if (u.rowpt && CASIM_INDEX_OK(u.rowpt[r0 + row] >= 0 && u.rowpt[r0 + row] < u.npts, u.err)) {
             const float *muy = u.norm + 2 * kNin, *sdy = u.norm + 2 * kNin + kNout;
             u.surr[u.rowpt[r0 + row]] = make_float4(__expf(y[0] * sdy[0] + muy[0]), __expf(y[1] * sdy[1] + muy[1]),
                                                     __expf(y[2] * sdy[2] + muy[2]), __expf(y[3] * sdy[3] + muy[3]));

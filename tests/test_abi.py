@@ -20,6 +20,10 @@ def test_every_declared_symbol_is_exported(L):
     assert len(names) >= 10
     for n in names:
         assert hasattr(L, n), n
+    # the index-checked build exports the same entry points
+    D = ctypes.CDLL(build.LIB_DEBUG)
+    for n in names:
+        assert hasattr(D, n), n
     from paper_2010_14823_gb300 import peaks
     pn = casim.declared_functions("casim_peaks.h")
     assert pn == ["casim_peak_rate"]
@@ -54,7 +58,8 @@ def test_default_params_match_the_oracle(L):
 def test_argument_errors_without_touching_the_device(L):
     ctx = ctypes.c_void_p()
     assert L.casim_init(ctypes.byref(ctx), None, 7, 0) == -1          # bad precision
-    assert L.casim_init(ctypes.byref(ctx), None, 0, 8) == -1          # unknown flag
+    assert L.casim_init(ctypes.byref(ctx), None, 0, 16) == -1         # unknown flag
+    assert L.casim_init(ctypes.byref(ctx), None, 0, 8 | 1) == -1      # statistics need the standard configuration
     assert L.casim_init(ctypes.byref(ctx), None, 0, 2 | 4) == -1      # aerosol mass with triple moment
     assert not ctx.value
     st = casim.casim_state(None, 32, None, None)
