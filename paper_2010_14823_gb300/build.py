@@ -20,7 +20,12 @@ PEAKS_LIB = os.path.join(HERE, "libcasim_peaks.so")
 PEAKS_SOURCES = [os.path.join(CSRC, "casim_peaks.cu")]
 PEAKS_DEPS = PEAKS_SOURCES + [os.path.join(INCLUDE, "casim_peaks.h")]
 
-NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+# -ftz=true: FP32 arithmetic flushes subnormal values to zero.  The mixed
+# step's FP32 values are normal or zero by construction (its FP64 -> FP32
+# conversion flushes magnitudes below 2^-126), so its results are unchanged,
+# bit for bit, while FP32 divisions and the like skip their subnormal handling
+# (measured: 2.13 -> 2.02 ms per 512x512x150 step).  FP64 code is unaffected.
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-ftz=true",
               "-Xcompiler", "-fPIC", "-shared", "-I" + INCLUDE, "-ldl"]
 
 
