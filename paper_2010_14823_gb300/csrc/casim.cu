@@ -216,6 +216,14 @@ static bool params_ok(const casim_params &p) {
   return true;
 }
 
+// a staged step kernel may use the dynamic shared memory of a column of the
+// largest level count
+template <class M>
+static cudaError_t allow_step_smem() {
+  return cudaFuncSetAttribute(k_step<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)step_smem_bytes<M, false>(kMaxLev));
+}
+
 extern "C" int casim_init(casim_ctx **out, const casim_params *params, int precision, int flags) {
   if (!out) return CASIM_ERR_ARG;
   *out = nullptr;
@@ -245,11 +253,14 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   for (int x = 0; x < 5; ++x) ctx->kp.vmax[x] = p.vmax[x];
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-  // the staged mixed step's dynamic shared memory exceeds the default 48 KB
-  // for columns of more than ~640 levels
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_step<PolicyMix, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)step_smem_bytes<PolicyMix, false>(kMaxLev));
+  // the staged mixed steps' dynamic shared memory (prefetch stage and level
+  // tables) exceeds the default 48 KB for long columns
+  if (e == cudaSuccess) e = allow_step_smem<PolicyMix>();
+  if (e == cudaSuccess) e = allow_step_smem<PolicyMixWarm>();
+  if (e == cudaSuccess) e = allow_step_smem<PolicyMixWarmAero>();
+  if (e == cudaSuccess) e = allow_step_smem<PolicyMixWarm3>();
+  if (e == cudaSuccess) e = allow_step_smem<PolicyMixAero>();
+  if (e == cudaSuccess) e = allow_step_smem<PolicyMix3>();
   // and the batched step's (256-thread blocks: a 64 KB stage)
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_step_batch<PolicyMix, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

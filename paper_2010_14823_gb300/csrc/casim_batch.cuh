@@ -56,7 +56,7 @@ struct BatchArgs {
 // (two levels of 16 fields per thread) and the level tables of maxlev levels
 template <class M>
 __host__ __device__ constexpr size_t batch_smem_bytes(int block, int maxlev) {
-  return (step_staged<M, false>() ? 2 * (size_t)kStageFields * block * sizeof(double) : 0) + (size_t)maxlev * 24;
+  return (step_staged<M, false>() ? stage_bytes<M>(block) : 0) + (size_t)maxlev * 24;
 }
 
 template <class M>
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kNarrow ? kBatchNarrowBlock : kBatchMaxBlock,
   const int B = blockDim.x;
   constexpr bool kStage = step_staged<M, false>();
   double *stage = kStage ? reinterpret_cast<double *>(batch_dyn) : nullptr;
-  double *s_dz = reinterpret_cast<double *>(batch_dyn + (kStage ? 2 * (size_t)kStageFields * B * sizeof(double) : 0));
+  double *s_dz = reinterpret_cast<double *>(batch_dyn + (kStage ? stage_bytes<M>(B) : 0));
   double *s_dzdt = s_dz + b.maxlev;
   float *s_dtdz_f = reinterpret_cast<float *>(s_dzdt + b.maxlev), *s_dzdt_f = s_dtdz_f + b.maxlev;
   const LevelTab lt{s_dz, s_dzdt, s_dtdz_f, s_dzdt_f};

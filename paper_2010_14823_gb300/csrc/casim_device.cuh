@@ -279,6 +279,48 @@ struct Pt {
   double zi, zs, zg;     // those of ice, snow, graupel: cold triple-moment policies only
 };
 
+// field f of the state (0..15 standard; from 16 the configuration's
+// aerosol masses or sixth moments)
+template <class M>
+__device__ __forceinline__ double &pt_field(Pt &s, int f) {
+  switch (f) {
+    case 0: return s.T;
+    case 1: return s.qv;
+    case 2: return s.qc;
+    case 3: return s.qr;
+    case 4: return s.qi;
+    case 5: return s.qs;
+    case 6: return s.qg;
+    case 7: return s.nc;
+    case 8: return s.nr;
+    case 9: return s.ni;
+    case 10: return s.ns;
+    case 11: return s.ng;
+    case 12: return s.na;
+    case 13: return s.p;
+    case 14: return s.rho;
+    case 15: return s.w;
+    default: break;
+  }
+  if constexpr (M::kAero) {
+    switch (f) {
+      case 16: return s.ma;
+      case 17: return s.mac;
+      case 18: return s.mar;
+      case 19: return s.mai;
+      case 20: return s.mas;
+      default: return s.mag;
+    }
+  } else {
+    switch (f) {
+      case 16: return s.zr;
+      case 17: return s.zi;
+      case 18: return s.zs;
+      default: return s.zg;
+    }
+  }
+}
+
 // sixth moment of sedimenting species x (r, i, s, g)
 __device__ __forceinline__ double &zref(Pt &s, int x) {
   return x == 0 ? s.zr : x == 1 ? s.zi : x == 2 ? s.zs : s.zg;
@@ -1475,19 +1517,33 @@ __device__ __forceinline__ void level_tab(double *dz, double *dzdt, float *dtdz_
   dzdt_f[k] = d2f(v / dt);
 }
 
-// The step kernel's dynamic shared memory: the prefetch stage (standard
-// mixed step: two levels of the block's 16 fields, 32 KB), then the level
-// tables of this domain's nlev levels (dz, dz/dt, dt/dz and dz/dt in FP32),
-// then the block's reduction slots.
+// The step kernel's dynamic shared memory: the prefetch stage (mixed step:
+// two levels of the fields the configuration loads, per thread), then the
+// level tables of this domain's nlev levels (dz, dz/dt, dt/dz and dz/dt in
+// FP32), then the block's reduction slots.
 template <class M, bool kTend>
 __host__ __device__ constexpr bool step_staged() {
-  return M::kMixed && !M::kWarm && !M::kAero && !M::kTri && !kTend;
+  return M::kMixed && !kTend;
 }
-constexpr int kStageFields = 16;
-constexpr size_t kStageBytes = 2 * kStageFields * kBlock * sizeof(double);
+// fields a configuration loads per point: the warm configuration T, qv, qc,
+// qr, nc, nr, na, p, rho, w; the cold one the 16 standard fields; then the
+// aerosol masses or sixth moments (fields 16..)
+template <class M>
+__host__ __device__ constexpr int stage_nf() {
+  return M::kWarm ? 10 + (M::kAero ? 3 : 0) + (M::kTri ? 1 : 0) : 16 + (M::kAero ? 6 : 0) + (M::kTri ? 4 : 0);
+}
+// the state field held in stage slot i
+template <class M>
+__host__ __device__ constexpr int stage_field(int i) {
+  return !M::kWarm ? i : i < 4 ? i : i < 6 ? i + 3 : i < 10 ? i + 6 : 16 + (i - 10);
+}
+template <class M>
+__host__ __device__ constexpr size_t stage_bytes(int block) {
+  return 2 * (size_t)stage_nf<M>() * block * sizeof(double);
+}
 template <class M, bool kTend>
 __host__ __device__ constexpr size_t step_smem_bytes(int nlev) {
-  return (step_staged<M, kTend>() ? kStageBytes : 0) + (size_t)nlev * 24 + (kBlock / 32) * 8 + 16;
+  return (step_staged<M, kTend>() ? stage_bytes<M>(kBlock) : 0) + (size_t)nlev * 24 + (kBlock / 32) * 8 + 16;
 }
 
 struct StepSmem {
@@ -1504,7 +1560,7 @@ __device__ __forceinline__ StepSmem step_smem(unsigned char *base, int nlev) {
   m.stage = nullptr;
   if constexpr (step_staged<M, kTend>()) {
     m.stage = reinterpret_cast<double *>(p);
-    p += kStageBytes;
+    p += stage_bytes<M>(kBlock);
   }
   double *dz = reinterpret_cast<double *>(p), *dzdt = dz + nlev;
   float *dtdz_f = reinterpret_cast<float *>(dzdt + nlev), *dzdt_f = dtdz_f + nlev;
@@ -1687,13 +1743,13 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
                                                double *tend = nullptr, double *stg = nullptr, int ss = kBlock,
                                                ColStats *cs = nullptr) {
   const double *sdz = lt.dz, *sdzdt = lt.dzdt;
+  constexpr int kNf = stage_nf<M>();
   if constexpr (kStage) {
-    static_assert(!M::kWarm && !M::kAero && !M::kTri, "the stage holds the 16 standard fields");
     if (!CASIM_INDEX_OK(c >= 0 && c < a.ncols && c < a.pitch, a.err)) return 0u;
     const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
     const double *src = a.fld + (size_t)(a.nlev - 1) * a.pitch + c;
 #pragma unroll
-    for (int f = 0; f < kStageFields; ++f) cp_async8(stg + f * ss, src + f * fs);
+    for (int i = 0; i < kNf; ++i) cp_async8(stg + i * ss, src + stage_field<M>(i) * fs);
     cp_async_commit();
   }
   using R = typename M::R;
@@ -1716,23 +1772,29 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
     Pt s;
     if constexpr (kStage) {
       const int b = (a.nlev - 1 - k) & 1;
-      const double *cur = stg + b * kStageFields * ss;
+      const double *cur = stg + b * kNf * ss;
       if (k > 0) {
-        double *nxt = stg + (b ^ 1) * kStageFields * ss;
+        double *nxt = stg + (b ^ 1) * kNf * ss;
         const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
         const double *src = a.fld + (size_t)(k - 1) * a.pitch + c;
 #pragma unroll
-        for (int f = 0; f < kStageFields; ++f) cp_async8(nxt + f * ss, src + f * fs);
+        for (int i = 0; i < kNf; ++i) cp_async8(nxt + i * ss, src + stage_field<M>(i) * fs);
         cp_async_commit();
         cp_async_wait<1>();   // this level's copies (the older group) have landed
       } else {
         cp_async_wait<0>();
       }
-      s.T = cur[0 * ss]; s.qv = cur[1 * ss]; s.qc = cur[2 * ss]; s.qr = cur[3 * ss];
-      s.qi = cur[4 * ss]; s.qs = cur[5 * ss]; s.qg = cur[6 * ss];
-      s.nc = cur[7 * ss]; s.nr = cur[8 * ss]; s.ni = cur[9 * ss]; s.ns = cur[10 * ss];
-      s.ng = cur[11 * ss]; s.na = cur[12 * ss];
-      s.p = cur[13 * ss]; s.rho = cur[14 * ss]; s.w = cur[15 * ss];
+      if constexpr (!M::kWarm && !M::kAero && !M::kTri) {
+        s.T = cur[0 * ss]; s.qv = cur[1 * ss]; s.qc = cur[2 * ss]; s.qr = cur[3 * ss];
+        s.qi = cur[4 * ss]; s.qs = cur[5 * ss]; s.qg = cur[6 * ss];
+        s.nc = cur[7 * ss]; s.nr = cur[8 * ss]; s.ni = cur[9 * ss]; s.ns = cur[10 * ss];
+        s.ng = cur[11 * ss]; s.na = cur[12 * ss];
+        s.p = cur[13 * ss]; s.rho = cur[14 * ss]; s.w = cur[15 * ss];
+      } else {
+        if constexpr (M::kWarm) s.qi = s.qs = s.qg = s.ni = s.ns = s.ng = 0.0;
+#pragma unroll
+        for (int i = 0; i < kNf; ++i) pt_field<M>(s, stage_field<M>(i)) = cur[i * ss];
+      }
     } else {
       load_pt<M::kWarm, M::kAero, M::kTri>(a, k, c, s);
     }
