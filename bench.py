@@ -33,22 +33,22 @@ WORKLOAD = "deep_512x512x150"
 
 # DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one ncu
 # capture of a 65 536-column x 150-level launch (dram__bytes_read.sum +
-# dram__bytes_write.sum = 2.2204 GB for 9.83 M points); reads are 16 fields per
+# dram__bytes_write.sum = 2.2139 GB for 9.83 M points); reads are 16 fields per
 # point and writes follow the changed points, so the traffic scales with the
 # points processed.  Valid only for the kernel source it was taken on.
-MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.87,
+MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.21,
                     "source": "paper_2010_14823_gb300/csrc/casim_device.cuh",
-                    "sha256": "e9a0895dad591d40b25711a591fc21c0bbdc4e48065d1cc819831ba52ae4927c"}
+                    "sha256": "8587d796bf1a0d15485b253313ed31139f20665174628d58db8724d710bbe1e3"}
 
 
 # FP64 arithmetic instructions of k_step<PolicyF64> per point on the same
 # state, from one ncu capture of a 16 384-column x 150-level launch
 # (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum =
-# 1168.3 M + 296.4 M + 381.0 M for 2.458 M points); the FP64 pipe was 72.7 %
+# 1168.3 M + 296.4 M + 381.0 M for 2.458 M points); the FP64 pipe was 72.6 %
 # busy.  Valid only for the kernel source it was taken on.
 MEASURED_FP64_OPS = {"kernel": "k_step<PolicyF64>", "inst_per_point": 751.07,
-                     "dfma": 475.40, "dadd": 120.63, "dmul": 155.04, "fp64_pipe_active": 0.727,
-                     "sha256": "e9a0895dad591d40b25711a591fc21c0bbdc4e48065d1cc819831ba52ae4927c"}
+                     "dfma": 475.40, "dadd": 120.63, "dmul": 155.04, "fp64_pipe_active": 0.726,
+                     "sha256": "8587d796bf1a0d15485b253313ed31139f20665174628d58db8724d710bbe1e3"}
 
 
 def _host_link_gbs(torch, stream, nbytes: int = 1 << 30):
