@@ -33,22 +33,22 @@ WORKLOAD = "deep_512x512x150"
 
 # DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one ncu
 # capture of a 65 536-column x 150-level launch (dram__bytes_read.sum +
-# dram__bytes_write.sum = 2.2139 GB for 9.83 M points); reads are 16 fields per
+# dram__bytes_write.sum = 2.2137 GB for 9.83 M points); reads are 16 fields per
 # point and writes follow the changed points, so the traffic scales with the
 # points processed.  Valid only for the kernel source it was taken on.
-MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.21,
+MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.19,
                     "source": "paper_2010_14823_gb300/csrc/casim_device.cuh",
-                    "sha256": "8587d796bf1a0d15485b253313ed31139f20665174628d58db8724d710bbe1e3"}
+                    "sha256": "3f2ae49c032a084a7892be6d8a11ef396214fef04c6aadf23a4babfb283f9b84"}
 
 
 # FP64 arithmetic instructions of k_step<PolicyF64> per point on the same
 # state, from one ncu capture of a 16 384-column x 150-level launch
 # (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum =
-# 1168.3 M + 296.4 M + 381.0 M for 2.458 M points); the FP64 pipe was 72.6 %
+# 1168.3 M + 296.4 M + 381.0 M for 2.458 M points); the FP64 pipe was 72.3 %
 # busy.  Valid only for the kernel source it was taken on.
 MEASURED_FP64_OPS = {"kernel": "k_step<PolicyF64>", "inst_per_point": 751.07,
-                     "dfma": 475.40, "dadd": 120.63, "dmul": 155.04, "fp64_pipe_active": 0.726,
-                     "sha256": "8587d796bf1a0d15485b253313ed31139f20665174628d58db8724d710bbe1e3"}
+                     "dfma": 475.40, "dadd": 120.63, "dmul": 155.04, "fp64_pipe_active": 0.723,
+                     "sha256": "3f2ae49c032a084a7892be6d8a11ef396214fef04c6aadf23a4babfb283f9b84"}
 
 
 def _host_link_gbs(torch, stream, nbytes: int = 1 << 30):
@@ -850,7 +850,11 @@ def main():
     casim.casim_step(ctx, dom.state, ncols, nlev, dt, stream)
     torch.cuda.synchronize()
     changed = int((dom.fld[:13] != before).any(dim=0)[:, :ncols].sum().item())
-    del before
+    # the in-place host step's stores: per field, level and warp (32 columns)
+    # the whole 256-byte row where any value's bits changed
+    flips = dom.fld[:13].view(torch.int64) != before.view(torch.int64)
+    line_rows = int(flips.view(13, nlev, dom.pitch // 32, 32).any(dim=-1).sum().item())
+    del before, flips
     casim.casim_free(ctx)
 
     value = fp64_value = None
@@ -890,11 +894,16 @@ def main():
         barrier()
         e2e_s = max_over_ranks(time.perf_counter() - t0)
         casim.casim_free(ctx)
-        h2d = hfld.numel() * 8 + hdz.numel() * 8 + hpr.numel() * 8
-        d2h = 13 * nlev * pitch * 8 + hpr.numel() * 8
+        # bytes over the host link: every input of the ncols columns, dz and the
+        # precipitation rows in; the changed fields' whole warp rows (as the
+        # first step wrote them) and the precipitation rows out
+        h2d = 16 * nlev * ncols * 8 + hdz.numel() * 8 + 4 * ncols * 8
+        d2h = line_rows * 256 + 4 * ncols * 8
         e2e = {"value": world * npts * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-               "path": "casim_step_host: pinned host state; H2D + step + D2H per step, 65 536-column chunks pipelined over 3 streams",
+               "path": "casim_step_host on pinned host state: the step kernel loads every input over the host "
+                       "link and stores, per field and warp, whole rows where a value changed, in place; "
+                       "equal to the device step bit for bit",
                "host_link_gbs": link,
                "copy_gbs": (h2d + d2h) * args.e2e_steps / e2e_s / 1e9,
                "link_frac": (h2d + d2h) * args.e2e_steps / e2e_s / 1e9 / link["both"] if link else None}

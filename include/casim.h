@@ -213,19 +213,25 @@ int casim_step(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double
 int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, double *tend,
                         void *stream);
 
-/* Same step for a domain held in HOST memory (any host allocation; pinned
-   memory copies faster and overlaps).  A domain of more than 65 536 columns
-   is processed in column chunks of 65 536 (fewer if the state's fields x nlev
-   of them exceed 2 GB) on three internal streams of the context, so one
-   chunk's copy in (every field of the context's state, and precip), another's
-   step and a third's copy out (the prognostic fields -- all but p, rho, w --
-   and precip) run at once (the paper's per-step transfers,
-   Section 3.3, overlapped with the kernel); a smaller domain is copied whole
-   on `stream`.  Starts after the work already queued on `stream` and returns
-   when every copy back has landed.  Results equal casim_step's on the same
-   state, bit for bit.  The state layout is the device one, with host
-   pointers.  Device buffers grow to the largest size seen and are freed by
-   casim_free. */
+/* Same step for a domain held in HOST memory (the paper's per-step
+   transfers, Section 3.3).  The state layout is the device one, with host
+   pointers.  Two paths, chosen per call:
+   - fields and precip each one mapped pinned range (cudaHostAlloc, or
+     cudaHostRegister'ed memory the device can address) and host->fld
+     256-byte aligned: the step kernel loads and stores the host state in
+     place over the host link on `stream` (each input crosses once, only the
+     points the step changes are written back; dz is copied to the device);
+   - otherwise (pageable or misaligned memory): copies.  A domain of more than
+     65 536 columns is processed in column chunks of 65 536 (fewer if the
+     state's fields x nlev of them exceed 2 GB) on three internal streams of
+     the context, so one chunk's copy in (every field of the context's state,
+     and precip), another's step and a third's copy out (the prognostic fields
+     -- all but p, rho, w -- and precip) run at once; a smaller domain is
+     copied whole on `stream`.
+   Starts after the work already queued on `stream` and returns when the host
+   state holds the result.  Results equal casim_step's on the same state, bit
+   for bit, on either path.  Device buffers grow to the largest size seen and
+   are freed by casim_free. */
 int casim_step_host(casim_ctx *ctx, const casim_state *host, int ncols, int nlev, double dt,
                     void *stream);
 

@@ -220,8 +220,12 @@ static bool params_ok(const casim_params &p) {
 // largest level count
 template <class M>
 static cudaError_t allow_step_smem() {
-  return cudaFuncSetAttribute(k_step<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)step_smem_bytes<M, false>(kMaxLev));
+  cudaError_t e = cudaFuncSetAttribute(k_step<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)step_smem_bytes<M, false>(kMaxLev));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step<M, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)step_smem_bytes<M, false>(kMaxLev));
+  return e;
 }
 
 extern "C" int casim_init(casim_ctx **out, const casim_params *params, int precision, int flags) {
@@ -324,9 +328,11 @@ static int ctx_nfields(const casim_ctx *ctx) {
 }
 static int ctx_nprecip(const casim_ctx *ctx) { return CASIM_NPRECIP + (ctx->aero ? 1 : 0); }
 
-// one configuration's kernels: the in-place step, or (tend) the source-term mode
+// one configuration's kernels: the in-place step, or (tend) the source-term
+// mode; line: the state is mapped host memory (the mixed step's whole-line
+// stores)
 template <class PMix, class PF64>
-static void launch_pair(const casim_ctx *ctx, dim3 grid, cudaStream_t st, const KArgs &a, double *tend) {
+static void launch_pair(const casim_ctx *ctx, dim3 grid, cudaStream_t st, const KArgs &a, double *tend, bool line) {
   const KParams &kp = ctx->kp;
   if constexpr (std::is_same<PMix, PolicyMix>::value) {
     // the statistics build (a CASIM_STATS context: standard configuration)
@@ -340,6 +346,8 @@ static void launch_pair(const casim_ctx *ctx, dim3 grid, cudaStream_t st, const 
   }
   if (ctx->precision == CASIM_MIXED) {
     if (tend) k_step<PMix, true><<<grid, kBlock, step_smem_bytes<PMix, true>(a.nlev), st>>>(a, kp, tend);
+    else if (line)
+      k_step<PMix, false, false, true><<<grid, kBlock, step_smem_bytes<PMix, false>(a.nlev), st>>>(a, kp, nullptr);
     else k_step<PMix, false><<<grid, kBlock, step_smem_bytes<PMix, false>(a.nlev), st>>>(a, kp, nullptr);
   } else {
     if (tend) k_step<PF64, true><<<grid, kBlock, step_smem_bytes<PF64, true>(a.nlev), st>>>(a, kp, tend);
@@ -347,15 +355,15 @@ static void launch_pair(const casim_ctx *ctx, dim3 grid, cudaStream_t st, const 
   }
 }
 
-static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, void *stream) {
+static int launch_step(casim_ctx *ctx, const KArgs &a, int ncols, double *tend, void *stream, bool line = false) {
   const dim3 grid((unsigned)((ncols + kBlock - 1) / kBlock));
   cudaStream_t st = (cudaStream_t)stream;
-  if (ctx->aero && ctx->warm) launch_pair<PolicyMixWarmAero, PolicyF64WarmAero>(ctx, grid, st, a, tend);
-  else if (ctx->aero) launch_pair<PolicyMixAero, PolicyF64Aero>(ctx, grid, st, a, tend);
-  else if (ctx->tri && ctx->warm) launch_pair<PolicyMixWarm3, PolicyF64Warm3>(ctx, grid, st, a, tend);
-  else if (ctx->tri) launch_pair<PolicyMix3, PolicyF643>(ctx, grid, st, a, tend);
-  else if (ctx->warm) launch_pair<PolicyMixWarm, PolicyF64Warm>(ctx, grid, st, a, tend);
-  else launch_pair<PolicyMix, PolicyF64>(ctx, grid, st, a, tend);
+  if (ctx->aero && ctx->warm) launch_pair<PolicyMixWarmAero, PolicyF64WarmAero>(ctx, grid, st, a, tend, line);
+  else if (ctx->aero) launch_pair<PolicyMixAero, PolicyF64Aero>(ctx, grid, st, a, tend, line);
+  else if (ctx->tri && ctx->warm) launch_pair<PolicyMixWarm3, PolicyF64Warm3>(ctx, grid, st, a, tend, line);
+  else if (ctx->tri) launch_pair<PolicyMix3, PolicyF643>(ctx, grid, st, a, tend, line);
+  else if (ctx->warm) launch_pair<PolicyMixWarm, PolicyF64Warm>(ctx, grid, st, a, tend, line);
+  else launch_pair<PolicyMix, PolicyF64>(ctx, grid, st, a, tend, line);
   ctx->launches++;
   CUDA_TRY(cudaGetLastError());
   return CASIM_OK;
@@ -377,11 +385,13 @@ extern "C" int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int nco
   return launch_step(ctx, a, ncols, tend, stream);
 }
 
-static int step_device(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream) {
+// line: the state is mapped host memory
+static int step_device(casim_ctx *ctx, const casim_state *s, int ncols, int nlev, double dt, void *stream,
+                       bool line = false) {
   int rc = check_state(s, ncols, nlev, dt);
   if (rc != CASIM_OK || ncols == 0) return rc;
   const KArgs a = make_args(ctx, s, ncols, nlev, dt);
-  return launch_step(ctx, a, ncols, nullptr, stream);
+  return launch_step(ctx, a, ncols, nullptr, stream, line);
 }
 
 // a CASIM_STATS context counts the step and its points on the host
@@ -456,6 +466,27 @@ static cudaError_t copy_chunk(double *dev_fld, double *dev_precip, int W, const 
 
 
 
+// The device address of the host range [p, p + bytes) when the whole range
+// is mapped pinned memory that kernels may load and store (a cudaHostAlloc
+// allocation or a cudaHostRegister range, which this device reaches over the
+// host link): both ends are host memory with device addresses the same
+// distance apart as the host ones.  nullptr for pageable memory.
+static void *mapped_host(const void *p, size_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  const char *b = static_cast<const char *>(p);
+  cudaPointerAttributes a0, a1;
+  if (cudaPointerGetAttributes(&a0, b) != cudaSuccess || cudaPointerGetAttributes(&a1, b + bytes - 1) != cudaSuccess) {
+    (void)cudaGetLastError();   // the query's own error, not a sticky one
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+    return nullptr;
+  if (static_cast<const char *>(a1.devicePointer) - static_cast<const char *>(a0.devicePointer) !=
+      static_cast<ptrdiff_t>(bytes - 1))
+    return nullptr;
+  return a0.devicePointer;
+}
+
 extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, int nlev, double dt,
                                void *stream) {
   NvtxRange nvtx_range_("casim_step_host");
@@ -464,12 +495,33 @@ extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, 
   if (ncols == 0) return CASIM_OK;
   if (!h->fld || !h->dz || !h->precip || h->pitch < ncols || h->pitch % 32 != 0) return CASIM_ERR_ARG;
   const int NF = ctx_nfields(ctx), NP = ctx_nprecip(ctx);
+  int rc;
+  // mapped pinned state: the step kernel loads and stores it in place over the
+  // host link (every input crosses once, only the points the step changes come
+  // back; its prefetch keeps a level of loads in flight), no staging copies
+  // (the device state's 256-byte alignment; otherwise the copies below)
+  void *mfld = mapped_host(h->fld, (size_t)NF * nlev * h->pitch * sizeof(double));
+  if (reinterpret_cast<uintptr_t>(mfld) % 256 != 0) mfld = nullptr;
+  void *mpr = mfld ? mapped_host(h->precip, (size_t)NP * h->pitch * sizeof(double)) : nullptr;
+  if (mfld && mpr) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = grow(&ctx->h2d_dz, &ctx->cap_dz, (size_t)nlev)) != CASIM_OK) return rc;
+    CUDA_TRY(cudaMemcpyAsync(ctx->h2d_dz, h->dz, (size_t)nlev * sizeof(double), cudaMemcpyHostToDevice, st));
+    casim_state d;
+    d.fld = static_cast<double *>(mfld);
+    d.pitch = h->pitch;
+    d.dz = ctx->h2d_dz;
+    d.precip = static_cast<double *>(mpr);
+    if ((rc = step_device(ctx, &d, ncols, nlev, dt, stream, true)) != CASIM_OK) return rc;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    count_step(ctx, ncols, nlev);
+    return CASIM_OK;
+  }
   // chunk width: a multiple of 32 columns with long contiguous rows, within the byte cap
   const size_t col_bytes = (size_t)NF * nlev * sizeof(double);
   const int wcap = (int)std::max<size_t>(32, kHostChunkBytes / col_bytes / 32 * 32);
   const int W = (int)std::min<size_t>(kHostMinRowBytes / sizeof(double), (size_t)wcap);
   const int nchunk = (ncols + W - 1) / W;
-  int rc;
   if (nchunk == 1) {
     // one chunk: contiguous copies of the whole state at the host pitch
     const size_t nf = (size_t)NF * nlev * h->pitch, np = (size_t)NP * h->pitch;

@@ -1738,10 +1738,19 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
 // fields are copied there by cp.async while level k is processed, so the
 // sweep seldom waits on a load (each thread reads only the slots it filled
 // itself: no block barrier)
-template <class M, bool kTend = false, bool kStage = false, bool kStats = false>
+// kLine (the state lies in mapped host memory, reached over the host link):
+// when any lane of a warp stores a level, every lane of it does -- the lanes
+// whose point is unchanged write back the values they read, taken again from
+// this level's stage slots -- so each field's row crosses the link as whole
+// lines (a write of part of a line there costs about as much as a whole one:
+// reading 16 fields and writing 13 at a random 76 % of the points of a
+// 512x512x150 state measured 37.0 ms, at every point 26.4 ms).  The stored
+// bits and the error flags are those of the in-place step.
+template <class M, bool kTend = false, bool kStage = false, bool kStats = false, bool kLine = false>
 __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P, const LevelTab &lt, bool fast, int c,
                                                double *tend = nullptr, double *stg = nullptr, int ss = kBlock,
                                                ColStats *cs = nullptr) {
+  static_assert(!kLine || (kStage && !kTend && !kStats), "whole-line stores re-read the stage");
   const double *sdz = lt.dz, *sdzdt = lt.dzdt;
   constexpr int kNf = stage_nf<M>();
   if constexpr (kStage) {
@@ -1963,6 +1972,25 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
     }
     if constexpr (kTend) {
       eflag |= store_tend<M>(a, tend, k, c, s, fast);
+    } else if constexpr (kLine) {
+      const unsigned wm = __activemask();
+      if (__any_sync(wm, touched)) {
+        // per field: the warp stores the whole row where any lane's value
+        // changed bits (the stage holds the value read); every lane takes
+        // part in every vote
+        const bool ok = CASIM_INDEX_OK(k >= 0 && k < a.nlev && c >= 0 && c < a.ncols, a.err);
+        double *b = a.fld + (size_t)k * a.pitch + c;
+        const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
+#pragma unroll
+        for (int i = 0; i < kNf; ++i) {
+          const int f = stage_field<M>(i);
+          if (f >= 13 && f < 16) continue;   // the inputs p, rho, w
+          const double o = cur[i * ss];
+          const double v = touched ? pt_field<M>(s, f) : o;
+          if (__any_sync(wm, __double_as_longlong(v) != __double_as_longlong(o)) && ok) b[f * fs] = v;
+          if (touched) eflag |= nonfinite(v);
+        }
+      }
     } else if constexpr (M::kWarm) {
       if (touched) eflag |= store_pt_warm<M::kAero, M::kTri>(a, k, c, s);
     } else {
@@ -2060,8 +2088,9 @@ __device__ __forceinline__ void stats_add(unsigned long long *st, const ColStats
 
 // kTend: tendency mode (tend receives the source terms, a.fld unchanged).
 // Dynamic shared memory: step_smem_bytes<M, kTend>(a.nlev).  kStats: the
-// statistics instantiation (standard configuration; a.stats set)
-template <class M, bool kTend, bool kStats = false>
+// statistics instantiation (standard configuration; a.stats set).  kLine:
+// whole-line stores for a state in mapped host memory (staged policies)
+template <class M, bool kTend, bool kStats = false, bool kLine = false>
 __global__ void __launch_bounds__(kBlock, M::kMinBlocks) k_step(const KArgs a, const KParams P, double *tend) {
   extern __shared__ __align__(16) unsigned char step_dyn[];
   const StepSmem sm = step_smem<M, kTend>(step_dyn, a.nlev);
@@ -2070,8 +2099,9 @@ __global__ void __launch_bounds__(kBlock, M::kMinBlocks) k_step(const KArgs a, c
   if (c >= a.ncols) return;
   constexpr bool kStage = step_staged<M, kTend>();
   ColStats cs{0, 0, {1, 1, 1, 1}};
-  const unsigned eflag = run_column<M, kTend, kStage, kStats>(a, P, sm.lt, fast, c, tend,
-                                                              kStage ? sm.stage + threadIdx.x : nullptr, kBlock, &cs);
+  const unsigned eflag = run_column<M, kTend, kStage, kStats, kLine>(a, P, sm.lt, fast, c, tend,
+                                                                     kStage ? sm.stage + threadIdx.x : nullptr,
+                                                                     kBlock, &cs);
   if constexpr (kStats) stats_add(a.stats, cs);
   if (eflag) atomicOr(a.err, eflag);
 }

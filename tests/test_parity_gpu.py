@@ -235,12 +235,26 @@ def test_cfl_cap_sets_error_flag():
     assert rc == -5 and flags & casim.EFLAG_CFL
 
 
+def _host_buffers(fld, npr, pinned):
+    """Host copies of a state for casim_step_host: numpy (pageable: the copy
+    path) or pinned torch tensors viewed as numpy (mapped: the in-place path)."""
+    import torch
+    h = np.ascontiguousarray(fld.copy())
+    hpr = np.zeros((npr, fld.shape[2]))
+    if pinned:
+        th, tpr = torch.from_numpy(h).pin_memory(), torch.from_numpy(hpr).pin_memory()
+        return th.numpy(), tpr.numpy(), (th, tpr)
+    return h, hpr, None
+
+
+@pytest.mark.parametrize("pinned", [False, True], ids=["pageable", "pinned"])
 @pytest.mark.parametrize("case", ["stratus_16x16x50", "deep_1000_of_1056", "deep_mixed_140000_of_140032x6"])
-def test_host_entry_point_matches_device_entry_point(case):
-    """The host-buffer step gives the device step's result bit for bit: one
-    chunk copied whole (pitch = ncols, and pitch > ncols); three column chunks
-    of 65 536, 65 536 and 8 928 pipelined over the internal streams, pitch >
-    ncols, mixed form."""
+def test_host_entry_point_matches_device_entry_point(case, pinned):
+    """The host-buffer step gives the device step's result bit for bit.
+    Pageable host memory: one chunk copied whole (pitch = ncols, and pitch >
+    ncols); three column chunks of 65 536, 65 536 and 8 928 pipelined over the
+    internal streams, pitch > ncols, mixed form.  Pinned host memory: the step
+    kernel loads and stores the host state in place."""
     precision = casim.CASIM_FP64
     if case == "stratus_16x16x50":
         fld, dz, ncols, nlev, dt, _ = synth.workload(case)
@@ -254,15 +268,51 @@ def test_host_entry_point_matches_device_entry_point(case):
     out, pr, _ = run_gpu(fld, dz, ncols, dt, precision=precision)
     ctx = casim.casim_init(precision=precision)
     try:
-        h = np.ascontiguousarray(fld.copy())
+        h, hpr, _keep = _host_buffers(fld, 4, pinned)
         hdz = np.ascontiguousarray(dz)
-        hpr = np.zeros((4, fld.shape[2]))
         st = casim.make_state(h, fld.shape[2], hdz, hpr)
         casim.casim_step_host(ctx, st, ncols, nlev, dt, stream=0)
         rc, flags = casim.casim_get_error(ctx)
         assert rc == 0, (rc, flags)
         assert np.array_equal(h, out)
         assert np.array_equal(hpr, pr)
+    finally:
+        casim.casim_free(ctx)
+
+
+@pytest.mark.parametrize("precision", [casim.CASIM_FP64, casim.CASIM_MIXED])
+def test_pinned_host_state_in_place_and_misaligned(precision):
+    """Pinned host state stepped in place over the host link: dt = 30 s (the
+    multi-substep sedimentation sweeps re-read the host state) and three steps
+    in a row equal three device steps bit for bit; a pinned state whose fields
+    start off the 256-byte alignment goes through the copies and agrees too."""
+    import torch
+    nlev, ncols, pitch, dt = 150, 1000, 1024, 30.0
+    dz = synth.dz_stretched(nlev)
+    fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=23, pitch=pitch)
+    d = casim.Domain(fld, dz, ncols)
+    ctx = casim.casim_init(precision=precision)
+    try:
+        for _ in range(3):
+            casim.casim_step(ctx, d.state, ncols, nlev, dt)
+        assert casim.casim_get_error(ctx)[0] == 0
+        out, pr = d.numpy()
+        h, hpr, _keep = _host_buffers(fld, 4, True)
+        st = casim.make_state(h, pitch, np.ascontiguousarray(dz), hpr)
+        for _ in range(3):
+            casim.casim_step_host(ctx, st, ncols, nlev, dt)
+        assert casim.casim_get_error(ctx)[0] == 0
+        assert np.array_equal(h, out) and np.array_equal(hpr, pr)
+        # the same state 8 bytes into a pinned buffer
+        big = torch.zeros(fld.size + 1, dtype=torch.float64).pin_memory()
+        hb = big.numpy()[1:].reshape(fld.shape)
+        hb[...] = fld
+        assert hb.ctypes.data % 256 == 8
+        hpr[...] = 0.0
+        out1, pr1, _ = run_gpu(fld, dz, ncols, dt, precision=precision)
+        casim.casim_step_host(ctx, casim.make_state(hb, pitch, np.ascontiguousarray(dz), hpr), ncols, nlev, dt)
+        assert casim.casim_get_error(ctx)[0] == 0
+        assert np.array_equal(hb, out1) and np.array_equal(hpr, pr1)
     finally:
         casim.casim_free(ctx)
 
@@ -474,10 +524,10 @@ def test_warm_tendency_and_host_entry_points(dt):
         t = tend.cpu().numpy()[:, :, :ncols]
         assert np.array_equal(t, (out[:13, :, :ncols] - fld[:13, :, :ncols]) / dt)
         assert np.all(t[ICE] == 0.0)
-        h = np.ascontiguousarray(fld.copy())
-        hpr = np.zeros((4, pitch))
-        casim.casim_step_host(ctx, casim.make_state(h, pitch, np.ascontiguousarray(dz), hpr), ncols, nlev, dt)
-        assert np.array_equal(h, out) and np.array_equal(hpr, pr)
+        for pinned in (False, True):   # the copies; the in-place step over the host link
+            h, hpr, _keep = _host_buffers(fld, 4, pinned)
+            casim.casim_step_host(ctx, casim.make_state(h, pitch, np.ascontiguousarray(dz), hpr), ncols, nlev, dt)
+            assert np.array_equal(h, out) and np.array_equal(hpr, pr), pinned
         # entry points without a warm variant refuse a warm context
         with pytest.raises(RuntimeError):
             casim.casim_batch_create(ctx, [d.state], [ncols], [nlev])
@@ -965,11 +1015,11 @@ def test_extended_tendency_and_host_entry_points(config, precision, dt):
         rows = list(range(13)) + list(range(16, nf))
         t = tend.cpu().numpy()[:, :, :ncols]
         assert np.array_equal(t, (out[rows, :, :ncols] - fld[rows, :, :ncols]) / dt)
-        # host entry point: one chunk, then many (a wide domain copied column-chunk-wise)
-        h = np.ascontiguousarray(fld.copy())
-        hpr = np.zeros(pr.shape)
-        casim.casim_step_host(ctx, casim.make_state(h, pitch, np.ascontiguousarray(dz), hpr), ncols, nlev, dt)
-        assert np.array_equal(h, out) and np.array_equal(hpr, pr)
+        # host entry point: pageable (copied whole) and pinned (stepped in place)
+        for pinned in (False, True):
+            h, hpr, _keep = _host_buffers(fld, pr.shape[0], pinned)
+            casim.casim_step_host(ctx, casim.make_state(h, pitch, np.ascontiguousarray(dz), hpr), ncols, nlev, dt)
+            assert np.array_equal(h, out) and np.array_equal(hpr, pr), pinned
     finally:
         casim.casim_free(ctx)
 
