@@ -3,7 +3,8 @@
 // The library owns no state memory: the caller passes device pointers (for
 // instance PyTorch tensors) and a stream.  A context carries the derived
 // scheme constants, the precision form, a device error word and, for
-// casim_step_host only, staging buffers.  Mirrors the paper's host protocol
+// casim_step_host only, staging buffers (its copy path for pageable host
+// memory; pinned host state is stepped in place).  Mirrors the paper's host protocol
 // (Section 3.2): one-off set-up, one asynchronous call per timestep running
 // the whole scheme for every column, tear-down.
 #include <cmath>
@@ -48,7 +49,7 @@ struct casim_ctx {
   unsigned *d_err = nullptr;
   long long launches = 0;
   // staging for casim_step_host: per pipeline stage a chunk of the state and
-  // of precip, its own stream; dz once
+  // of precip, its own stream (the copy path); dz once (both paths)
   static constexpr int kStages = 3;
   double *h2d_fld[kStages] = {}, *h2d_precip[kStages] = {}, *h2d_dz = nullptr;
   size_t cap_fld[kStages] = {}, cap_precip[kStages] = {}, cap_dz = 0;
