@@ -216,9 +216,13 @@ int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int ncols, int nle
 /* Same step for a domain held in HOST memory (the paper's per-step
    transfers, Section 3.3).  The state layout is the device one, with host
    pointers.  Two paths, chosen per call:
-   - fields and precip each one mapped pinned range (cudaHostAlloc, or
-     cudaHostRegister'ed memory the device can address) and host->fld
-     256-byte aligned: the step kernel loads and stores the host state in
+   - fields and precip each in pinned host memory mapped into the device's
+     address space (cudaHostAlloc / cudaMallocHost, as torch's pin_memory()
+     allocates, or a cudaHostRegister range) and host->fld 256-byte aligned,
+     on a device that cannot register host memory read-only
+     (cudaDevAttrHostRegisterReadOnlySupported = 0, as on GB300; where it can,
+     a registered range cannot be told apart from a writable one and this path
+     is not taken): the step kernel loads and stores the host state in
      place over the host link on `stream` (each input crosses once, only the
      points the step changes are written back; dz is copied to the device);
    - otherwise (pageable or misaligned memory): copies.  A domain of more than

@@ -45,6 +45,7 @@ struct casim_ctx {
   bool tri = false;    // CASIM_THREE_MOMENT: triple-moment rain (17-field state)
   int device = 0;
   int nsm = 1;
+  int host_ro = 1;   // the device supports read-only registration of host memory (assumed until queried)
   KParams kp;
   unsigned *d_err = nullptr;
   long long launches = 0;
@@ -258,6 +259,7 @@ extern "C" int casim_init(casim_ctx **out, const casim_params *params, int preci
   for (int x = 0; x < 5; ++x) ctx->kp.vmax[x] = p.vmax[x];
   cudaError_t e = cudaGetDevice(&ctx->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->host_ro, cudaDevAttrHostRegisterReadOnlySupported, ctx->device);
   // the staged mixed steps' dynamic shared memory (prefetch stage and level
   // tables) exceeds the default 48 KB for long columns
   if (e == cudaSuccess) e = allow_step_smem<PolicyMix>();
@@ -468,10 +470,12 @@ static cudaError_t copy_chunk(double *dev_fld, double *dev_precip, int W, const 
 
 
 // The device address of the host range [p, p + bytes) when the whole range
-// is mapped pinned memory that kernels may load and store (a cudaHostAlloc
-// allocation or a cudaHostRegister range, which this device reaches over the
-// host link): both ends are host memory with device addresses the same
-// distance apart as the host ones.  nullptr for pageable memory.
+// is pinned host memory mapped into the device's address space (a
+// cudaHostAlloc / cudaMallocHost allocation or a cudaHostRegister range),
+// which this device reaches over the host link: both ends are host memory
+// with device addresses the same distance apart as the host ones.  nullptr
+// for pageable memory.  (Whether the device may also store to it is the
+// caller's concern: see host_ro.)
 static void *mapped_host(const void *p, size_t bytes) {
   if (!p || bytes == 0) return nullptr;
   const char *b = static_cast<const char *>(p);
@@ -500,8 +504,10 @@ extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, 
   // mapped pinned state: the step kernel loads and stores it in place over the
   // host link (every input crosses once, only the points the step changes come
   // back; its prefetch keeps a level of loads in flight), no staging copies
-  // (the device state's 256-byte alignment; otherwise the copies below)
-  void *mfld = mapped_host(h->fld, (size_t)NF * nlev * h->pitch * sizeof(double));
+  // (the device state's 256-byte alignment; otherwise the copies below).  On
+  // a device that can register host memory read-only, a registered range
+  // cannot be told apart from a writable one, so there only the copies run.
+  void *mfld = ctx->host_ro == 0 ? mapped_host(h->fld, (size_t)NF * nlev * h->pitch * sizeof(double)) : nullptr;
   if (reinterpret_cast<uintptr_t>(mfld) % 256 != 0) mfld = nullptr;
   void *mpr = mfld ? mapped_host(h->precip, (size_t)NP * h->pitch * sizeof(double)) : nullptr;
   if (mfld && mpr) {

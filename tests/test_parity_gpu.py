@@ -271,13 +271,65 @@ def test_host_entry_point_matches_device_entry_point(case, pinned):
         h, hpr, _keep = _host_buffers(fld, 4, pinned)
         hdz = np.ascontiguousarray(dz)
         st = casim.make_state(h, fld.shape[2], hdz, hpr)
+        n0 = casim.casim_launch_count(ctx)
         casim.casim_step_host(ctx, st, ncols, nlev, dt, stream=0)
         rc, flags = casim.casim_get_error(ctx)
         assert rc == 0, (rc, flags)
+        if ncols > 65536 and _readonly_host_registration() == 0:
+            # in place: one launch; copies: one per 65 536-column chunk
+            assert casim.casim_launch_count(ctx) - n0 == (1 if pinned else 3)
         assert np.array_equal(h, out)
         assert np.array_equal(hpr, pr)
     finally:
         casim.casim_free(ctx)
+
+
+def _readonly_host_registration():
+    """cudaDevAttrHostRegisterReadOnlySupported of device 0, from the CUDA
+    runtime library (None if it cannot be loaded)."""
+    import ctypes
+    for name in ("libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            rt = ctypes.CDLL(name)
+        except OSError:
+            continue
+        v = ctypes.c_int(-1)
+        if rt.cudaDeviceGetAttribute(ctypes.byref(v), 113, 0) == 0:
+            return v.value
+    return None
+
+
+def test_registered_host_memory():
+    """Host memory pinned by cudaHostRegister: stepped in place (one launch
+    for 140 000 columns) on a device that cannot register host memory
+    read-only, as GB300, else moved by the copies (three chunk launches);
+    bit for bit the device step's result either way."""
+    import torch
+    ncols, pitch, nlev = 140000, 140032, 6
+    dz = synth.dz_stretched(nlev)
+    fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=21, pitch=pitch)
+    out, pr, _ = run_gpu(fld, dz, ncols, 1.0, precision=casim.CASIM_MIXED)
+    nf, npr = fld.size, 4 * pitch
+    raw = np.zeros(nf + npr + 64)
+    off = (-raw.ctypes.data % 256) // 8
+    buf = raw[off:off + nf + npr]   # the fields 256-byte aligned, then precip
+    h = buf[:nf].reshape(fld.shape)
+    h[...] = fld
+    hpr = buf[nf:].reshape(4, pitch)
+    cr = torch.cuda.cudart()
+    assert int(cr.cudaHostRegister(buf.ctypes.data, buf.nbytes, 0)) == 0
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED)
+    try:
+        n0 = casim.casim_launch_count(ctx)
+        casim.casim_step_host(ctx, casim.make_state(h, pitch, np.ascontiguousarray(dz), hpr), ncols, nlev, 1.0)
+        ro = _readonly_host_registration()
+        if ro is not None:
+            assert casim.casim_launch_count(ctx) - n0 == (3 if ro else 1)
+        assert casim.casim_get_error(ctx)[0] == 0
+        assert np.array_equal(h, out) and np.array_equal(hpr, pr)
+    finally:
+        casim.casim_free(ctx)
+        cr.cudaHostUnregister(buf.ctypes.data)
 
 
 @pytest.mark.parametrize("precision", [casim.CASIM_FP64, casim.CASIM_MIXED])
