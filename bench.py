@@ -31,12 +31,14 @@ UNIT = "grid-point updates/s"
 WORKLOAD = "deep_512x512x150"
 
 
-# DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one ncu
-# capture of a 65 536-column x 150-level launch (dram__bytes_read.sum +
-# dram__bytes_write.sum = 2.2137 GB for 9.83 M points); reads are 16 fields per
-# point and writes follow the changed points, so the traffic scales with the
-# points processed.  Valid only for the kernel source it was taken on.
-MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_point": 225.19,
+# DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one
+# single-pass ncu capture of the full 262 144-column x 150-level launch
+# (dram__bytes_read.sum + dram__bytes_write.sum = 5.0596 + 3.9830 GB for
+# 39.32 M points); at another column count it is scaled per point (reads are
+# 16 fields per point and writes follow the changed points).  Valid only for
+# the kernel source it was taken on.
+MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_launch": 9042611456, "points": 39321600,
+                    "bytes_per_point": 229.97,
                     "source": "paper_2010_14823_gb300/csrc/casim_device.cuh",
                     "sha256": "3f2ae49c032a084a7892be6d8a11ef396214fef04c6aadf23a4babfb283f9b84"}
 
@@ -103,6 +105,8 @@ def _measured_traffic(npts: int):
     """Traffic per launch scaled from the capture, or None if the kernel source changed since."""
     if _kernel_source_sha() != MEASURED_TRAFFIC["sha256"]:
         return None
+    if npts == MEASURED_TRAFFIC["points"]:
+        return float(MEASURED_TRAFFIC["bytes_per_launch"])
     return MEASURED_TRAFFIC["bytes_per_point"] * npts
 
 

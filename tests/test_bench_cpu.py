@@ -48,7 +48,9 @@ def test_measured_counters_follow_the_kernel_source(monkeypatch):
     npts = 39_321_600
     monkeypatch.setitem(bench.MEASURED_TRAFFIC, "sha256", sha)
     monkeypatch.setitem(bench.MEASURED_FP64_OPS, "sha256", sha)
-    assert bench._measured_traffic(npts) == pytest.approx(bench.MEASURED_TRAFFIC["bytes_per_point"] * npts)
+    # the captured launch's own bytes at its size, per point elsewhere
+    assert bench._measured_traffic(npts) == bench.MEASURED_TRAFFIC["bytes_per_launch"]
+    assert bench._measured_traffic(npts // 4) == pytest.approx(bench.MEASURED_TRAFFIC["bytes_per_point"] * npts // 4)
     # the DFMA rate is probed on the GPU at run time; here a fixed stand-in
     from paper_2010_14823_gb300 import peaks
     monkeypatch.setattr(peaks, "peak_rate", lambda kind, iters: 0.5e12)
