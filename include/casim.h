@@ -223,8 +223,9 @@ int casim_step_tendency(casim_ctx *ctx, const casim_state *s, int ncols, int nle
      (cudaDevAttrHostRegisterReadOnlySupported = 0, as on GB300; where it can,
      a registered range cannot be told apart from a writable one and this path
      is not taken): the step kernel loads and stores the host state in
-     place over the host link on `stream` (each input crosses once, only the
-     points the step changes are written back; dz is copied to the device);
+     place over the host link on `stream` (each input crosses once; written
+     back are only the rows of 32 columns of the fields the step changed
+     somewhere in them; dz is copied to the device);
    - otherwise (pageable or misaligned memory): copies.  A domain of more than
      65 536 columns is processed in column chunks of 65 536 (fewer if the
      state's fields x nlev of them exceed 2 GB) on three internal streams of

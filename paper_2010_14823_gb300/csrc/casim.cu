@@ -502,8 +502,9 @@ extern "C" int casim_step_host(casim_ctx *ctx, const casim_state *h, int ncols, 
   const int NF = ctx_nfields(ctx), NP = ctx_nprecip(ctx);
   int rc;
   // mapped pinned state: the step kernel loads and stores it in place over the
-  // host link (every input crosses once, only the points the step changes come
-  // back; its prefetch keeps a level of loads in flight), no staging copies
+  // host link (every input crosses once; back come only the 32-column rows of
+  // the fields the step changed somewhere in them; its prefetch keeps a level
+  // of loads in flight), no staging copies
   // (the device state's 256-byte alignment; otherwise the copies below).  On
   // a device that can register host memory read-only, a registered range
   // cannot be told apart from a writable one, so there only the copies run.

@@ -235,7 +235,7 @@ struct PolicyMix {
   static constexpr bool kWarm = false;
   static constexpr bool kAero = false;
   static constexpr bool kTri = false;
-  static constexpr int kMinBlocks = 5;   // measured: 4 / 5 / 6 -> 2.95 / 2.73 / 3.06 ms per 512x512x150 step
+  static constexpr int kMinBlocks = 5;   // measured: 4 / 5 / 6 -> 2.07 / 1.94 / 1.99 ms per 512x512x150 step
   static __device__ __forceinline__ const ConstK<float> &K(const KParams &p) { return p.f; }
   static __device__ __forceinline__ R toR(double x) { return d2f(x); }
   static __device__ __forceinline__ R toRn(double x) { return d2f_rn(x); }
@@ -1739,13 +1739,14 @@ __device__ __forceinline__ unsigned sediment_substeps(const KArgs &a, const KPar
 // sweep seldom waits on a load (each thread reads only the slots it filled
 // itself: no block barrier)
 // kLine (the state lies in mapped host memory, reached over the host link):
-// when any lane of a warp stores a level, every lane of it does -- the lanes
-// whose point is unchanged write back the values they read, taken again from
-// this level's stage slots -- so each field's row crosses the link as whole
-// lines (a write of part of a line there costs about as much as a whole one:
-// reading 16 fields and writing 13 at a random 76 % of the points of a
-// 512x512x150 state measured 37.0 ms, at every point 26.4 ms).  The stored
-// bits and the error flags are those of the in-place step.
+// per level and field, when any lane of a warp changed that field's bits,
+// every lane stores it -- a lane whose value is unchanged writes back the
+// value it read, taken again from this level's stage slots -- so each stored
+// row (32 columns x 8 bytes) crosses the link as whole lines (a write of part
+// of a line there costs about as much as a whole one: reading 16 fields and
+// writing 13 at a random 76 % of the points of a 512x512x150 state measured
+// 37.0 ms, at every point 26.4 ms).  The stored bits and the error flags are
+// those of the in-place step.
 template <class M, bool kTend = false, bool kStage = false, bool kStats = false, bool kLine = false>
 __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P, const LevelTab &lt, bool fast, int c,
                                                double *tend = nullptr, double *stg = nullptr, int ss = kBlock,
