@@ -140,6 +140,34 @@ def test_stats_count_planted_cloud_exactly(precision):
         casim.casim_free(ctx)
 
 
+def test_stats_host_step_on_pinned_state():
+    """A statistics context's host step on pinned host state (stepped in
+    place by the statistics kernel over the host link): the planted cloud
+    counted exactly, one step of every point, results equal to the device
+    step's bit for bit."""
+    import torch
+    ncols, nlev = 200, 60
+    dz = np.full(nlev, 50.0)
+    fld, pts = _dry_state(ncols, nlev, seed=9)
+    ctx = casim.casim_init(precision=casim.CASIM_MIXED, flags=casim.CASIM_STATS)
+    try:
+        d = casim.Domain(fld, dz, ncols)
+        casim.casim_step(ctx, d.state, ncols, nlev, 1.0)
+        out, pr = d.numpy()
+        casim.casim_get_stats(ctx, reset=True)
+        th = torch.from_numpy(fld.copy()).pin_memory()
+        tpr = torch.zeros((4, fld.shape[2]), dtype=torch.float64).pin_memory()
+        h, hpr = th.numpy(), tpr.numpy()
+        casim.casim_step_host(ctx, casim.make_state(h, fld.shape[2], np.ascontiguousarray(dz), hpr), ncols, nlev, 1.0)
+        st = casim.casim_get_stats(ctx)
+        assert casim.casim_get_error(ctx)[0] == 0
+        assert np.array_equal(h, out) and np.array_equal(hpr, pr)
+        assert st["steps"] == 1 and st["points"] == ncols * nlev
+        assert st["active_points"] == len(pts) and st["changed_points"] == len(pts)
+    finally:
+        casim.casim_free(ctx)
+
+
 @pytest.mark.parametrize("dt", [1.0, 30.0])
 def test_stats_substep_histogram_matches_oracle_and_results_unchanged(dt):
     """FP64 form on a deep-convective state; dt = 30 s takes the multi-substep
