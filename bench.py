@@ -33,24 +33,24 @@ WORKLOAD = "deep_512x512x150"
 
 # DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one
 # single-pass ncu capture of the full 262 144-column x 150-level launch
-# (dram__bytes_read.sum + dram__bytes_write.sum = 5.0591 + 3.9829 GB for
+# (dram__bytes_read.sum + dram__bytes_write.sum = 5.0597 + 3.9829 GB for
 # 39.32 M points); at another column count it is scaled per point (reads are
 # 16 fields per point and writes follow the changed points).  Valid only for
 # the kernel source it was taken on.
-MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_launch": 9041975040, "points": 39321600,
-                    "bytes_per_point": 229.95,
+MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_launch": 9042586624, "points": 39321600,
+                    "bytes_per_point": 229.97,
                     "source": "paper_2010_14823_gb300/csrc/casim_device.cuh",
-                    "sha256": "3e29c37b049dee54ad6f5d93179f05f4b2a274497ddb1ae9ff1fe6b2cec97f7e"}
+                    "sha256": "7a9a453d74983d7765f2a802c15053bf0c614a250003c30cd93fdc40629aeb2c"}
 
 
 # FP64 arithmetic instructions of k_step<PolicyF64> per point on the same
 # state, from one ncu capture of a 16 384-column x 150-level launch
 # (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum =
-# 1168.3 M + 296.4 M + 381.0 M for 2.458 M points); the FP64 pipe was 72.4 %
+# 1168.3 M + 296.4 M + 381.0 M for 2.458 M points); the FP64 pipe was 73.0 %
 # busy.  Valid only for the kernel source it was taken on.
 MEASURED_FP64_OPS = {"kernel": "k_step<PolicyF64>", "inst_per_point": 751.07,
-                     "dfma": 475.40, "dadd": 120.63, "dmul": 155.04, "fp64_pipe_active": 0.724,
-                     "sha256": "3e29c37b049dee54ad6f5d93179f05f4b2a274497ddb1ae9ff1fe6b2cec97f7e"}
+                     "dfma": 475.40, "dadd": 120.63, "dmul": 155.04, "fp64_pipe_active": 0.730,
+                     "sha256": "7a9a453d74983d7765f2a802c15053bf0c614a250003c30cd93fdc40629aeb2c"}
 
 
 def _host_link_gbs(torch, stream, nbytes: int = 1 << 30):
@@ -469,6 +469,74 @@ def bench_peaks(args, rank, world, local):
                           "rates": rates, "per_sm_per_clock": per, "iters": iters, "clocks": clocks}), flush=True)
 
 
+def bench_tendency(args, rank, world, local):
+    """The source-term mode on deep convection 512x512x150: the state is left
+    unchanged and (x_after - x_before) / dt of the 13 prognostic fields goes to
+    a separate array at every point, the parent model's interface.  `value` is
+    the mixed form; the roofline counts 16 fields read and 13 source terms
+    written per point (every point's, zero where nothing changes)."""
+    import torch
+    from paper_2010_14823_gb300 import casim, synth, shard
+    casim.lib()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    fld, dz, ncols, nlev, dt, _ = synth.workload(WORKLOAD, ncols=args.ncols, seed=shard.rank_seed(1236, rank))
+    npts = ncols * nlev
+    stream = torch.cuda.current_stream()
+    dom = casim.Domain(fld, dz, ncols)
+    tend = torch.empty((13, nlev, dom.pitch), dtype=torch.float64, device=dom.fld.device)
+
+    def sync():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def run(precision, steps, warmup):
+        ctx = casim.casim_init(precision=precision)
+        for _ in range(warmup):
+            casim.casim_step_tendency(ctx, dom.state, ncols, nlev, dt, tend, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sync()
+        n0 = casim.casim_launch_count(ctx)
+        e0.record(stream)
+        for _ in range(steps):
+            casim.casim_step_tendency(ctx, dom.state, ncols, nlev, dt, tend, stream)
+        e1.record(stream)
+        sync()
+        rc, fl = casim.casim_get_error(ctx, stream)
+        assert rc == 0, (rc, fl)
+        launches = casim.casim_launch_count(ctx) - n0
+        casim.casim_free(ctx)
+        return shard.max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / steps, launches
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    mix_ms, launches = run(casim.CASIM_MIXED, args.steps, args.warmup)
+    clocks = sampler.stop()
+    fp_ms, _ = run(casim.CASIM_FP64, args.fp64_steps, 1)
+    peak = _peaks().get("hbm_gbs")
+    alg = (128.0 + 104.0) * npts
+    achieved = alg / (mix_ms * 1e-3) / 1e9
+    if rank == 0:
+        v = lambda ms: world * npts / (ms * 1e-3)
+        line = {"metric": METRIC, "value": v(mix_ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": mix_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD + " source-term mode", "ncols": ncols, "nlev": nlev, "dt_s": dt,
+                           "path": "casim_step_tendency: state unchanged, 13 source-term rows written",
+                           "l2": "state 5 GB and source terms 4 GB > L2, no flush needed",
+                           "fp64_value": v(fp_ms), "fp64_ms_per_step": fp_ms},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak if peak else None, "traffic": None,
+                             "kernel": "k_step<PolicyMix, tendency>", "algorithmic_bytes_per_launch": alg,
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+
+
 def bench_warm(args, rank, world, local):
     """The warm configuration (liquid water only) against the cold one on the
     same 512x512x150 stratus state, mixed and FP64 forms.  `value` is the warm
@@ -788,6 +856,8 @@ def main():
         return bench_peaks(args, rank, world, local)
     if args.workload == "warm_vs_cold":
         return bench_warm(args, rank, world, local)
+    if args.workload == "tendency":
+        return bench_tendency(args, rank, world, local)
     from paper_2010_14823_gb300 import shard
     base_fld, dz, ncols, nlev, dt, _ = synth.workload(args.workload, ncols=args.ncols,
                                                       seed=shard.rank_seed(1236, rank))

@@ -218,8 +218,8 @@ static bool params_ok(const casim_params &p) {
   return true;
 }
 
-// a staged step kernel may use the dynamic shared memory of a column of the
-// largest level count
+// a staged step kernel (in place, its whole-line-store form, source-term
+// mode) may use the dynamic shared memory of a column of the largest level count
 template <class M>
 static cudaError_t allow_step_smem() {
   cudaError_t e = cudaFuncSetAttribute(k_step<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -227,6 +227,9 @@ static cudaError_t allow_step_smem() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_step<M, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)step_smem_bytes<M, false>(kMaxLev));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_step<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)step_smem_bytes<M, true>(kMaxLev));
   return e;
 }
 

@@ -1464,12 +1464,49 @@ __device__ __forceinline__ double extra(const Pt &s, int i) {
   }
 }
 
+// x / dt for the source terms, correctly rounded as the division is, from the
+// reciprocal inv = 1/dt rounded once: for a dt that is a power of two the
+// quotient is x * inv exactly; otherwise Markstein's correction (Markstein
+// 1990: q = x inv, the remainder x - q dt exactly by a fused multiply-add,
+// then q + remainder * inv) yields the correctly rounded quotient whenever it
+// is a normal number away from the ends of the exponent range, and the rest
+// (zero, which keeps its sign, and quotients near those ends) take the
+// division itself.  One division per thread instead of one per source term:
+// an FP64 division costs about ten SM cycles on this part.
+struct DtDiv {
+  double dt, inv;
+  bool pow2;
+  __device__ explicit DtDiv(double d) : dt(d), inv(1.0 / d) {
+    pow2 = (__double_as_longlong(d) & 0x000FFFFFFFFFFFFFll) == 0;   // a positive normal dt: 2^e exactly
+  }
+  __device__ __forceinline__ double operator()(double x) const {
+    if (pow2) return x * inv;
+    if (x == 0.0) return x;
+    const double q = x * inv;
+    const double q1 = fma(fma(-q, dt, x), inv, q);
+    const double m = fabs(q1);
+    return (m > 0x1p-1000 && m < 0x1p+1000) ? q1 : x / dt;
+  }
+};
+
+// the prefetch stage's slot that holds state field f (a field the configuration
+// loads: all 16 and those after the inputs; the warm configuration leaves out
+// the ice fields)
 template <class M>
-__device__ __forceinline__ unsigned store_tend(const KArgs &a, double *tend, int k, int c, const Pt &s, bool fast) {
+__host__ __device__ constexpr int stage_slot(int f) {
+  return !M::kWarm ? f : f < 4 ? f : f < 9 ? f - 3 : f < 16 ? f - 6 : 10 + (f - 16);
+}
+
+template <class M>
+// cur, ss (the staged mixed forms): the point's stage slots, which hold the
+// values read, so x_before comes from there rather than from the state again
+__device__ __forceinline__ unsigned store_tend(const KArgs &a, double *tend, int k, int c, const Pt &s, bool fast,
+                                               const DtDiv &per_dt, const double *cur = nullptr, int ss = 0) {
   if (!CASIM_INDEX_OK(k >= 0 && k < a.nlev && c >= 0 && c < a.ncols, a.err)) return 0u;
   constexpr bool kWarm = M::kWarm;
   const size_t o = (size_t)k * a.pitch + c;
   const size_t fs = (size_t)a.nlev * (size_t)a.pitch;
+  auto before = [&](int f) { return cur ? cur[stage_slot<M>(f) * ss] : a.fld[f * fs + o]; };
   const double v[13] = {s.T, s.qv, s.qc, s.qr, s.qi, s.qs, s.qg, s.nc, s.nr, s.ni, s.ns, s.ng, s.na};
 #pragma unroll
   for (int f = 0; f < 13; ++f) {
@@ -1477,14 +1514,14 @@ __device__ __forceinline__ unsigned store_tend(const KArgs &a, double *tend, int
     if (kWarm && ice) {
       tend[f * fs + o] = 0.0;   // zero source term (the conversion pass skips these)
     } else {
-      tend[f * fs + o] = fast ? (v[f] - a.fld[f * fs + o]) / a.dt : v[f];
+      tend[f * fs + o] = fast ? per_dt(v[f] - before(f)) : v[f];
     }
   }
   unsigned ex = 0;
 #pragma unroll
   for (int e = 0; e < nextra<M>(); ++e) {
     const double v = extra<M>(s, e);
-    tend[(13 + e) * fs + o] = fast ? (v - a.fld[(16 + e) * fs + o]) / a.dt : v;
+    tend[(13 + e) * fs + o] = fast ? per_dt(v - before(16 + e)) : v;
     ex |= nonfinite(v);
   }
   return ex | nonfinite(s.T) | nonfinite(s.qv) | nonfinite(s.qc) | nonfinite(s.qr) | nonfinite(s.qi) |
@@ -1523,7 +1560,7 @@ __device__ __forceinline__ void level_tab(double *dz, double *dzdt, float *dtdz_
 // FP32), then the block's reduction slots.
 template <class M, bool kTend>
 __host__ __device__ constexpr bool step_staged() {
-  return M::kMixed && !kTend;
+  return M::kMixed;
 }
 // fields a configuration loads per point: the warm configuration T, qv, qc,
 // qr, nc, nr, na, p, rho, w; the cold one the 16 standard fields; then the
@@ -1766,6 +1803,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
   using Ph = Phys<M>;
   const ConstK<R> &K = M::K(P);
   unsigned eflag = 0;
+  const DtDiv per_dt(kTend ? a.dt : 1.0);   // the source terms' division by dt (tendency mode)
   constexpr int kSed = M::kWarm ? 1 : 4;   // sedimenting species: r (warm) or r, i, s, g
   double prec[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // r, i, s, g (and aerosol in rain)
   // carried downward fluxes F_{k+1}, G_{k+1} (kg m^-2 s^-1, m^-2 s^-1), and
@@ -1972,7 +2010,7 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       eflag |= w.hmax >= kF32RangeHi;
     }
     if constexpr (kTend) {
-      eflag |= store_tend<M>(a, tend, k, c, s, fast);
+      eflag |= store_tend<M>(a, tend, k, c, s, fast, per_dt, kStage ? cur : nullptr, ss);
     } else if constexpr (kLine) {
       const unsigned wm = __activemask();
       if (__any_sync(wm, touched)) {
@@ -2041,11 +2079,11 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
 #pragma unroll
         for (int f = 0; f < 13; ++f) {
           const bool ice = (f >= 4 && f <= 6) || (f >= 9 && f <= 11);
-          if (!(M::kWarm && ice)) tend[f * fs + o] = (tend[f * fs + o] - a.fld[f * fs + o]) / a.dt;
+          if (!(M::kWarm && ice)) tend[f * fs + o] = per_dt(tend[f * fs + o] - a.fld[f * fs + o]);
         }
 #pragma unroll
         for (int e = 0; e < nextra<M>(); ++e)
-          tend[(13 + e) * fs + o] = (tend[(13 + e) * fs + o] - a.fld[(16 + e) * fs + o]) / a.dt;
+          tend[(13 + e) * fs + o] = per_dt(tend[(13 + e) * fs + o] - a.fld[(16 + e) * fs + o]);
       }
     }
   }

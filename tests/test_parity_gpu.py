@@ -370,6 +370,35 @@ def test_pinned_host_state_in_place_and_misaligned(precision):
 
 
 @pytest.mark.parametrize("precision", [casim.CASIM_FP64, casim.CASIM_MIXED])
+@pytest.mark.parametrize("dt", [0.1, 1.0 / 3.0, 2.0, 7.3, 0.25, 11.0])
+def test_tendency_division_by_dt_is_correctly_rounded(precision, dt):
+    """The source terms divide by dt through one reciprocal per launch (exact
+    for a power-of-two dt, Markstein's correction otherwise): on every point
+    of a deep-convective state, at time steps that are and are not powers of
+    two, tend equals numpy's correctly rounded (x_after - x_before) / dt bit
+    for bit."""
+    import torch
+    nlev = 120
+    dz = synth.dz_stretched(nlev)
+    ncols, pitch = 256, 256
+    fld = synth.make_state("deep_convective", ncols, nlev, dz, seed=41, pitch=pitch)
+    out, _, _ = run_gpu(fld, dz, ncols, dt, precision=precision)
+    ctx = casim.casim_init(precision=precision)
+    try:
+        d = casim.Domain(fld, dz, ncols)
+        tend = torch.full((13, nlev, pitch), float("nan"), dtype=torch.float64, device="cuda")
+        casim.casim_step_tendency(ctx, d.state, ncols, nlev, dt, tend)
+        assert casim.casim_get_error(ctx)[0] == 0
+        diff = out[:13, :, :ncols] - fld[:13, :, :ncols]
+        t = tend.cpu().numpy()[:, :, :ncols]
+        assert np.count_nonzero(diff) > 10000   # many quotients that are not zero
+        assert np.array_equal(t, diff / dt)
+        assert np.array_equal(np.signbit(t), np.signbit(diff / dt))
+    finally:
+        casim.casim_free(ctx)
+
+
+@pytest.mark.parametrize("precision", [casim.CASIM_FP64, casim.CASIM_MIXED])
 @pytest.mark.parametrize("dt", [1.0, 30.0])
 def test_tendency_mode_equals_in_place_step(precision, dt):
     """Source-term mode: the state is untouched and tend is (x_after - x_before)
