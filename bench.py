@@ -33,24 +33,24 @@ WORKLOAD = "deep_512x512x150"
 
 # DRAM traffic of k_step<PolicyMix> on the deep-convection state, from one
 # single-pass ncu capture of the full 262 144-column x 150-level launch
-# (dram__bytes_read.sum + dram__bytes_write.sum = 5.0597 + 3.9829 GB for
+# (dram__bytes_read.sum + dram__bytes_write.sum = 5.0588 + 3.9828 GB for
 # 39.32 M points); at another column count it is scaled per point (reads are
 # 16 fields per point and writes follow the changed points).  Valid only for
 # the kernel source it was taken on.
-MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_launch": 9042586624, "points": 39321600,
-                    "bytes_per_point": 229.97,
+MEASURED_TRAFFIC = {"kernel": "k_step<PolicyMix>", "bytes_per_launch": 9041585152, "points": 39321600,
+                    "bytes_per_point": 229.94,
                     "source": "paper_2010_14823_gb300/csrc/casim_device.cuh",
-                    "sha256": "7a9a453d74983d7765f2a802c15053bf0c614a250003c30cd93fdc40629aeb2c"}
+                    "sha256": "b040dec6cc7b6d47b6f675add1fcc1f4f5979e38b72bbe9ddb8b957d05c32d1c"}
 
 
 # FP64 arithmetic instructions of k_step<PolicyF64> per point on the same
 # state, from one ncu capture of a 16 384-column x 150-level launch
 # (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum =
-# 1168.3 M + 296.4 M + 381.0 M for 2.458 M points); the FP64 pipe was 73.0 %
+# 1168.3 M + 296.4 M + 381.0 M for 2.458 M points); the FP64 pipe was 72.9 %
 # busy.  Valid only for the kernel source it was taken on.
 MEASURED_FP64_OPS = {"kernel": "k_step<PolicyF64>", "inst_per_point": 751.07,
-                     "dfma": 475.40, "dadd": 120.63, "dmul": 155.04, "fp64_pipe_active": 0.730,
-                     "sha256": "7a9a453d74983d7765f2a802c15053bf0c614a250003c30cd93fdc40629aeb2c"}
+                     "dfma": 475.40, "dadd": 120.63, "dmul": 155.04, "fp64_pipe_active": 0.729,
+                     "sha256": "b040dec6cc7b6d47b6f675add1fcc1f4f5979e38b72bbe9ddb8b957d05c32d1c"}
 
 
 def _host_link_gbs(torch, stream, nbytes: int = 1 << 30):

@@ -514,7 +514,26 @@ void orc_point_cfg(const double *in, double dt, double *out, int warm) {
        part (the shape measure G = z n / M3^2 unchanged);
      - autoconversion adds drops of one size D0 = 2 r0: + n_aut D0^6.
    in[ORC_NFIELDS_3M] -> out[ORC_NPROG_3M] (13 prognostic fields, then z). */
+/* a1, the activity flag: a point is active when it holds a hydrometeor
+   (q > q_min), is supersaturated over liquid, or (cold configuration) is
+   colder than T_nuc and supersaturated over ice; the chain leaves every
+   other point unchanged.  The fixed-shape rule for a sixth moment (z_kept:
+   none left where the species is absent) acts at active points only, so an
+   inactive point keeps its sixth moments too. */
+static int point_active(const double *in, int warm) {
+  if (in[ORC_QC] > QMIN || in[ORC_QR] > QMIN) return 1;
+  if (in[ORC_QV] > orc_qsat(orc_es_liq(in[ORC_T]), in[ORC_P])) return 1;
+  if (warm) return 0;
+  if (in[ORC_QI] > QMIN || in[ORC_QS] > QMIN || in[ORC_QG] > QMIN) return 1;
+  return in[ORC_T] < TNUC && in[ORC_QV] / orc_qsat(orc_es_ice(in[ORC_T]), in[ORC_P]) > 1.0;
+}
+
 void orc_point_3m(const double *in, double dt, double *out) {
+  if (!point_active(in, 1)) {
+    memcpy(out, in, ORC_NPROG * sizeof(double));
+    out[ORC_NPROG] = in[ORC_ZR];
+    return;
+  }
   double mu4[4] = {orc_rain_mu(in[ORC_QR], in[ORC_NR], in[ORC_ZR]), SP[ORC_I].mu, SP[ORC_S].mu, SP[ORC_G].mu};
   orc_record r;
   double o[ORC_NPROG];
@@ -550,6 +569,11 @@ static double z_kept(double z0, double q0, double n0, double q1, double n1) {
    in[ORC_NFIELDS_3MC] -> out[ORC_NPROG_3MC] (13 prognostic fields, then
    z_r, z_i, z_s, z_g). */
 void orc_point_3m_cold(const double *in, double dt, double *out) {
+  if (!point_active(in, 0)) {
+    memcpy(out, in, ORC_NPROG * sizeof(double));
+    for (int x = 0; x < 4; ++x) out[ORC_NPROG + x] = in[ORC_ZR + x];
+    return;
+  }
   static const int sp[4] = {ORC_R, ORC_I, ORC_S, ORC_G};
   static const int qf[4] = {ORC_QR, ORC_QI, ORC_QS, ORC_QG};
   static const int nf[4] = {ORC_NR, ORC_NI, ORC_NS, ORC_NG};

@@ -1850,6 +1850,10 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
     bool touched;
     if constexpr (!M::kMixed) {
       eflag |= nonfinite_in(s);
+      // the aerosol masses or sixth moments too: an inactive point is not stored,
+      // so its values are checked as they are read
+#pragma unroll
+      for (int e = 0; e < nextra<M>(); ++e) eflag |= nonfinite(extra<M>(s, e));
       double es0, qs0;
       touched = F64T<M>::active(K, s, es0, qs0);
       if constexpr (kStats) cs->active += touched;
@@ -1906,6 +1910,10 @@ __device__ __forceinline__ unsigned run_column(const KArgs &a, const KParams &P,
       W<float> w;
       float es0, qs0;
       const bool act = MixT<M>::active(K, s, P.T0, w, es0, qs0);
+      // the aerosol masses or sixth moments join the magnitude scan (an
+      // inactive point is not stored, so its values are checked as read)
+#pragma unroll
+      for (int e = 0; e < nextra<M>(); ++e) w.hmax = max(w.hmax, hiabs(extra<M>(s, e)));
       if constexpr (kStats) cs->active += act;
       MixInc o;
       MassAcc macc;

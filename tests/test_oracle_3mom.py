@@ -342,3 +342,31 @@ def test_cold_column_water_budget_with_random_shapes():
     assert np.allclose(w1 + pr[:, :32].sum(0), w0, rtol=1e-12, atol=0)
     assert (out[16:, :, :32] >= 0).all()
     assert (out[16:, :, :32] > 0).any(axis=(1, 2)).all()
+
+
+def test_an_inactive_point_keeps_its_sixth_moments():
+    """A point the chain leaves unchanged (no hydrometeor, subsaturated over
+    liquid and, when cold, over ice or warmer than T_nuc) keeps every field,
+    its sixth moments included, even where they describe no species; an
+    active point with rain absent has none left (the fixed-shape rule)."""
+    p = 9e4
+    for T in (290.0, 260.0):
+        es = O.es_liq(T) if T > 273.15 else min(O.es_liq(T), O.es_ice(T))
+        qv = 0.8 * O.qsat(es, p)
+        warm = np.zeros(17)
+        warm[F["T"]], warm[F["p"]], warm[F["rho"]], warm[F["qv"]], warm[F["na"]] = T, p, 1.1, qv, 1e8
+        warm[ZR] = 3e-12
+        out = O.point_3m(warm, 1.0)
+        assert np.array_equal(out[:13], warm[:13]) and out[13] == warm[ZR]
+        cold = np.zeros(20)
+        cold[:16] = warm[:16]
+        cold[16:20] = [3e-12, 1e-14, 2e-13, 5e-12]
+        out = O.point_3m_cold(cold, 1.0)
+        assert np.array_equal(out[:13], cold[:13]) and np.array_equal(out[13:], cold[16:20])
+    # the same warm point made active by a little cloud: the absent rain's z is dropped
+    act = np.zeros(17)
+    act[F["T"]], act[F["p"]], act[F["rho"]], act[F["na"]] = 290.0, p, 1.1, 1e8
+    act[F["qv"]] = 0.8 * O.qsat(O.es_liq(290.0), p)
+    act[F["qc"]], act[F["nc"]], act[ZR] = 1e-5, 5e7, 3e-12
+    out = O.point_3m(act, 1.0)
+    assert out[13] == 0.0

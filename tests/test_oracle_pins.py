@@ -154,6 +154,43 @@ def test_activation_limits_and_monotonicity():
     assert 5e-4 < O.arg_smax(1e8, 1.0, T, p) < 2e-2
 
 
+def test_activation_counts_existing_droplets_and_moves_aerosol_number():
+    """Activation raises the cloud-droplet number to the number the updraft
+    activates (Abdul-Razzak and Ghan, pinned above) out of the whole
+    population n_a + n_c, never lowers it, and takes the new droplets from
+    the free aerosol: with no droplets the cloud number becomes the activated
+    number; with at least that many already nothing activates; in between the
+    cloud number is topped up to it.  n_a + n_c is conserved throughout."""
+    T, p, rho, w = 283.0, 9.0e4, 1.1, 1.5
+    base = np.zeros(16)
+    base[F["T"]], base[F["p"]], base[F["rho"]], base[F["w"]] = T, p, rho, w
+    base[F["qv"]] = 1.005 * O.qsat(O.es_liq(T), p)      # saturated: the adjustment makes cloud
+    base[F["qc"]] = 2e-4
+    pop = 1.5e8                                         # n_a + n_c per kg
+    cases = []
+    for nc in (0.0, 0.2 * pop, 0.6 * pop, 0.999 * pop):
+        st = base.copy()
+        st[F["nc"]], st[F["na"]] = nc, pop - nc
+        out = O.adjust_activate(st)
+        assert out[F["qc"]] > P("q_min")
+        nact = O.arg_nact(rho * pop, w, out[F["T"]], p) / rho   # activated per kg
+        cases.append((nc, nact, out[F["nc"]], out[F["na"]]))
+        assert out[F["nc"]] + out[F["na"]] == pytest.approx(pop, rel=1e-14)
+        if nc >= nact:
+            assert out[F["nc"]] == nc and out[F["na"]] == pop - nc       # nothing activates
+        else:
+            assert out[F["nc"]] == pytest.approx(min(nact, pop), rel=1e-12)
+    # the cases cover both sides of the activated number
+    assert any(nc < nact for nc, nact, _, _ in cases) and any(nc >= nact for nc, nact, _, _ in cases)
+    # a very strong updraft activates nearly the whole population: the free
+    # aerosol is nearly used up but never negative (no droplet is created
+    # beyond n_a + n_c)
+    st = base.copy()
+    st[F["w"]], st[F["nc"]], st[F["na"]] = 1e4, 0.0, pop
+    out = O.adjust_activate(st)
+    assert 0.0 <= out[F["na"]] < 1e-2 * pop and out[F["nc"]] <= pop * (1 + 1e-14)
+
+
 # -------------------------------------------------- gamma-distribution algebra
 def _psd_quad(sp, q, lam, rho, fn):
     """int fn(D) n(D) dD with n(D) = N0 D^mu e^(-lam D), N0 set by the mass
@@ -581,6 +618,37 @@ def test_inactive_point_is_bitwise_unchanged():
     st = _state(T=290.0, qv=0.9 * _qs(290.0, p), p=p, w=1.5)
     out = O.point(st, 1.0)
     assert np.array_equal(out, st[:13])
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -float("inf")])
+def test_a_non_finite_value_in_any_field_is_reported(bad):
+    """The step reports a non-finite value (error bit) wherever it sits: in
+    each of the 13 prognostic fields of the standard state, and in each field
+    a configuration adds after the inputs (aerosol masses, sixth moments),
+    planted one at a time at an inactive point (clear, dry air) of an
+    otherwise clean domain; the clean domain reports nothing."""
+    nlev, ncols = 12, 4
+    dz = np.full(nlev, 100.0)
+    T, p = 290.0, 9e4
+
+    def clean(nf):
+        fld = np.zeros((nf, nlev, ncols))
+        fld[F["T"]], fld[F["p"]], fld[F["rho"]] = T, p, 1.08
+        fld[F["qv"]] = 0.5 * O.qsat(O.es_liq(T), p)
+        fld[F["na"]] = 1e8
+        return fld
+
+    steps = [(O.NFIELDS, lambda f: O.step(f, ncols, dz, 1.0)[2], list(range(13))),
+             (O.NFIELDS_AERO, lambda f: O.step_aero(f, ncols, dz, 1.0)[1], [16, 17, 18]),
+             (O.NFIELDS_AEROC, lambda f: O.step_aero_cold(f, ncols, dz, 1.0)[1], list(range(16, 22))),
+             (O.NFIELDS_3M, lambda f: O.step_3m(f, ncols, dz, 1.0)[1], [16]),
+             (O.NFIELDS_3MC, lambda f: O.step_3m_cold(f, ncols, dz, 1.0)[1], list(range(16, 20)))]
+    for nf, run, fields in steps:
+        assert run(clean(nf)) == 0
+        for f in fields:
+            fld = clean(nf)
+            fld[f, 7, 2] = bad
+            assert run(fld) & O.ERR_NONFINITE, (nf, f)
 
 
 # ---------------------------------------------------------- a12 sedimentation

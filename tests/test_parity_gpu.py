@@ -1105,6 +1105,51 @@ def test_extended_tendency_and_host_entry_points(config, precision, dt):
         casim.casim_free(ctx)
 
 
+EXT_ORACLE = {
+    "warm_aerosol": (19, lambda f, n, dz: O.step_aero(f, n, dz, 1.0)[1]),
+    "cold_aerosol": (22, lambda f, n, dz: O.step_aero_cold(f, n, dz, 1.0)[1]),
+    "warm_three_moment": (17, lambda f, n, dz: O.step_3m(f, n, dz, 1.0)[1]),
+    "cold_three_moment": (20, lambda f, n, dz: O.step_3m_cold(f, n, dz, 1.0)[1]),
+}
+
+
+def _clear_ext_state(nf, ncols, nlev, seed):
+    """Dry, subsaturated air with no hydrometeor (every point inactive),
+    carrying nonzero aerosol masses or sixth moments that describe nothing."""
+    rng = np.random.default_rng(seed)
+    fld = np.zeros((nf, nlev, ncols))
+    T, p = 285.0, 9e4
+    fld[F["T"]] = T + rng.uniform(-1, 1, (nlev, ncols))
+    fld[F["p"]], fld[F["rho"]] = p, 1.1
+    fld[F["qv"]] = 0.6 * O.qsat(O.es_liq(T - 1), p)
+    fld[F["na"]] = 1e8
+    fld[16:] = 10.0 ** rng.uniform(-14, -9, (nf - 16, nlev, ncols))
+    return fld
+
+
+@pytest.mark.parametrize("config", list(EXT_ORACLE))
+@pytest.mark.parametrize("precision", [casim.CASIM_FP64, casim.CASIM_MIXED])
+def test_extended_fields_at_inactive_points(config, precision):
+    """Inactive points keep every field, the aerosol masses and sixth moments
+    included, as the oracle has them; a non-finite value in any of those
+    fields at an inactive point sets the non-finite error bit."""
+    nf, ostep = EXT_ORACLE[config]
+    _, flags = EXT_CONFIGS[config]
+    ncols, nlev = 64, 20
+    dz = np.full(nlev, 100.0)
+    fld = _clear_ext_state(nf, ncols, nlev, seed=7)
+    out, pr, _ = run_gpu(fld, dz, ncols, 1.0, precision=precision, flags=flags())
+    ref = fld.copy()
+    assert ostep(ref, ncols, dz) == 0
+    assert np.array_equal(ref, fld)          # the oracle leaves the clear domain as it is
+    assert np.array_equal(out, ref) and not pr.any()
+    for f in range(16, nf):
+        bad = fld.copy()
+        bad[f, 11, 37] = float("nan")
+        _, _, (rc, fl) = run_gpu(bad, dz, ncols, 1.0, precision=precision, flags=flags(), check_err=False)
+        assert rc == -4 and fl & casim.EFLAG_NONFINITE, (config, f)
+
+
 def test_extended_host_entry_point_in_chunks():
     """More columns than one host chunk (65 536): the chunked pipeline moves
     every field of the extended state, bit for bit against the device step."""
