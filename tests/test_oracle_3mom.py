@@ -57,20 +57,20 @@ def test_gamma_algebra_at_any_shape_matches_quadrature(mu):
     nd = lambda D: N0 * D ** mu * np.exp(-lam * D)   # noqa: E731
     up = 60.0 / lam
     M = lambda k: quad(lambda D: D ** k * nd(D), 0, up, limit=400, epsabs=0)[0]   # noqa: E731
-    assert np.isclose(a * M(3.0), rho * q, rtol=1e-8)
-    assert np.isclose(M(0.0), rho * n, rtol=1e-8)
+    assert np.isclose(a * M(3.0), rho * q, rtol=1e-8, atol=0.0)
+    assert np.isclose(M(0.0), rho * n, rtol=1e-8, atol=0.0)
     for k in (1.0, 1.75, 6.0):
-        assert np.isclose(O.moment_mu("r", rho, q, lam, k, mu), M(k), rtol=1e-8)
+        assert np.isclose(O.moment_mu("r", rho, q, lam, k, mu), M(k), rtol=1e-8, atol=0.0)
     cv, dv, rho0 = O.param("cv_r"), O.param("dv_r"), O.param("rho0")
     fac = cv * (rho0 / rho) ** 0.4
     for k, fn in ((3.0, O.vq_mu), (0.0, O.vn_mu), (6.0, O.vz_mu)):
         w = quad(lambda D: fac * D ** dv * D ** k * nd(D), 0, up, limit=400, epsabs=0)[0] / M(k)
-        assert np.isclose(fn("r", rho, lam, mu), min(w, O.param("vmax_r")), rtol=1e-8)
+        assert np.isclose(fn("r", rho, lam, mu), min(w, O.param("vmax_r")), rtol=1e-8, atol=0.0)
     nu = O.param("mu_air") / rho
     sc = nu / O.param("Dv")
     vent = quad(lambda D: D * (0.78 + 0.31 * sc ** (1 / 3) * np.sqrt(fac * D ** dv * D / nu)) * nd(D), 0, up,
                 limit=400, epsabs=0)[0]
-    assert np.isclose(O.vent_integral_mu("r", rho, q, lam, mu), vent, rtol=1e-8)
+    assert np.isclose(O.vent_integral_mu("r", rho, q, lam, mu), vent, rtol=1e-8, atol=0.0)
 
 
 def _rain_state(ncols, nlev, seed, mu=None):
@@ -113,17 +113,18 @@ def test_reduces_to_two_moment_where_the_shape_cannot_change():
     assert np.allclose(pa[:, :40], pb[:, :40], rtol=1e-12, atol=0)
 
 
-def test_autoconversion_makes_monodisperse_rain():
+@pytest.mark.parametrize("dt", [1.0, 3.0])
+def test_autoconversion_makes_monodisperse_rain(dt):
     st = np.zeros(17)
     T, p = 285.0, 9.0e4
     qs = O.qsat(O.es_liq(T), p)
     st[F["T"]], st[F["p"]], st[F["rho"]] = T, p, p / (287.04 * T)
     st[F["qv"]], st[F["qc"]], st[F["nc"]], st[F["na"]] = qs, 1e-3, 5e7, 1e8
-    out = O.point_3m(st, 1.0)
+    out = O.point_3m(st, dt)
     q, n, z = out[F["qr"]], out[F["nr"]], out[13]
     assert q > 0 and n > 0
-    assert np.isclose(z, n * D0 ** 6, rtol=1e-12)
-    assert np.isclose(z * n / (q / A_R) ** 2, 1.0, rtol=1e-9)
+    assert np.isclose(z, n * D0 ** 6, rtol=1e-12, atol=0.0)
+    assert np.isclose(z * n / (q / A_R) ** 2, 1.0, rtol=1e-9, atol=0.0)
 
 
 def test_rain_keeps_its_shape_through_evaporation_and_self_collection():
@@ -158,7 +159,7 @@ def test_sixth_moment_shifts_one_level_at_courant_one():
     assert err == 0 and ns == 1
     assert np.array_equal(q1, np.roll(q, -1))
     assert np.allclose(z1, np.roll(z, -1), rtol=1e-15, atol=1e-15 * z[5])   # to one rounding
-    assert 0.0 < n1[5] < n[5] and np.isclose(n1.sum(), n.sum())   # the number falls slower
+    assert 0.0 < n1[5] < n[5] and np.isclose(n1.sum(), n.sum(), rtol=1e-12, atol=0.0)   # the number falls slower
 
 
 def test_column_water_budget_with_random_shapes():
@@ -221,18 +222,46 @@ def test_melting_gives_rain_the_melting_species_shape():
         assert abs(O.shape_mu("s", out[F["qs"]], out[F["ns"]], out[15]) - mu) < 1e-9
         # the sixth moment is conserved in particle-mass units: (m / a_r)^2 summed
         a_r, a_s = O.param("a_r"), O.param("a_s")
-        assert np.isclose(out[13] + (a_s / a_r) ** 2 * out[15], (a_s / a_r) ** 2 * st[ZC["s"]], rtol=1e-12)
+        assert np.isclose(out[13] + (a_s / a_r) ** 2 * out[15], (a_s / a_r) ** 2 * st[ZC["s"]], rtol=1e-12, atol=0.0)
 
 
-def test_nucleation_makes_monodisperse_ice():
+def test_melting_snow_adds_its_sixth_moment_to_existing_rain():
+    """Snow melting into rain already present, in air saturated over water
+    (no evaporation, no cloud): the rain after the step is the superposition
+    of its own population, whose shape (G) self-collection does not change,
+    and the melted part of the snow, one drop per melted particle carrying
+    (a_s / a_r)^2 times the melted fraction of the snow's sixth moment.
+    Masses and numbers of the two parts come from the snow's losses; moments
+    of superposed populations add."""
+    T, p = 276.0, 9.0e4
+    qsl = O.qsat(O.es_liq(T), p)
+    a_r, a_s = O.param("a_r"), O.param("a_s")
+    for dt in (1.0, 5.0):
+        for mu_r, mu_s in ((1.0, 4.0), (6.0, 0.5)):
+            qr0, nr0, qs0, ns0 = 3e-4, 2e3, 2e-4, 5e3
+            st = _point(T, p, qv=qsl, qr=qr0, nr=nr0, zr=_z_at("r", qr0, nr0, mu_r),
+                        qs=qs0, ns=ns0, zs=_z_at("s", qs0, ns0, mu_s), na=1e8)
+            out = O.point_3m_cold(st, dt)
+            q_m, n_m = qs0 - out[F["qs"]], ns0 - out[F["ns"]]      # the melted part
+            assert 0.0 < q_m < qs0 and 0.0 < n_m < ns0
+            assert np.isclose(out[F["qr"]], qr0 + q_m, rtol=1e-13, atol=0.0)
+            q_own, n_own = out[F["qr"]] - q_m, out[F["nr"]] - n_m  # rain's own population
+            assert n_own < nr0                                      # self-collection acted
+            z_own = G(mu_r) * (q_own / a_r) ** 2 / n_own
+            z_melt = (a_s / a_r) ** 2 * (q_m / qs0) * st[ZC["s"]]
+            assert np.isclose(out[13], z_own + z_melt, rtol=1e-10, atol=0.0), (dt, mu_r, mu_s)
+
+
+@pytest.mark.parametrize("dt", [1.0, 4.0])
+def test_nucleation_makes_monodisperse_ice(dt):
     T, p = 255.0, 5.0e4
     qsi, qsl = O.qsat(O.es_ice(T), p), O.qsat(O.es_liq(T), p)
     st = _point(T, p, qv=0.5 * (qsi + qsl), na=1e8)
-    out = O.point_3m_cold(st, 1.0)
+    out = O.point_3m_cold(st, dt)
     q, n, z = out[F["qi"]], out[F["ni"]], out[14]
     assert q > 0 and n > 0
-    assert np.isclose(z * n / (q / O.param("a_i")) ** 2, 1.0, rtol=1e-9)
-    assert np.isclose(z, n * (O.param("m_i0") / O.param("a_i")) ** 2, rtol=1e-12)
+    assert np.isclose(z * n / (q / O.param("a_i")) ** 2, 1.0, rtol=1e-9, atol=0.0)
+    assert np.isclose(z, n * (O.param("m_i0") / O.param("a_i")) ** 2, rtol=1e-12, atol=0.0)
 
 
 def test_deposition_keeps_every_ice_species_shape():
@@ -324,8 +353,8 @@ def test_every_species_sixth_moment_falls_with_its_own_speed():
         q1, n1, z1, pr, ns, err = O.sediment_3m(q, n, z, rho, dz, dt)
         assert err == 0 and ns[x] == 1
         cq, cz = vq * dt / dz[0], min(vz, dz[0] / dt) * dt / dz[0]
-        assert np.isclose(q1[x, 5], q[x, 5] * (1 - cq), rtol=1e-12) and np.isclose(q1[x, 4], q[x, 5] * cq, rtol=1e-12)
-        assert np.isclose(z1[x, 5], z[x, 5] * (1 - cz), rtol=1e-12) and np.isclose(z1[x, 4], z[x, 5] * cz, rtol=1e-12)
+        assert np.isclose(q1[x, 5], q[x, 5] * (1 - cq), rtol=1e-12, atol=0.0) and np.isclose(q1[x, 4], q[x, 5] * cq, rtol=1e-12, atol=0.0)
+        assert np.isclose(z1[x, 5], z[x, 5] * (1 - cz), rtol=1e-12, atol=0.0) and np.isclose(z1[x, 4], z[x, 5] * cz, rtol=1e-12, atol=0.0)
         others = [y for y in range(4) if y != x]
         assert not q1[others].any() and not z1[others].any()
 

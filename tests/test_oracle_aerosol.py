@@ -93,8 +93,8 @@ def test_activation_takes_the_mean_particle_mass():
     out = O.point_aero(st, 1e-9)                 # dt -> 0: activation only
     dn = st[F["na"]] - out[F["na"]]
     assert dn > 0
-    assert np.isclose(out[14], st[MA] * dn / st[F["na"]], rtol=1e-9)
-    assert np.isclose(out[13] + out[14] + out[15], st[MA], rtol=1e-15)
+    assert np.isclose(out[14], st[MA] * dn / st[F["na"]], rtol=1e-9, atol=0.0)
+    assert np.isclose(out[13] + out[14] + out[15], st[MA], rtol=1e-15, atol=0.0)
 
 
 def test_evaporated_cloud_returns_all_its_aerosol():
@@ -191,8 +191,8 @@ def test_melting_gives_rain_the_melted_share_of_snow_aerosol():
     out = O.point_aero_cold(st, 5.0)
     qs1 = out[F["qs"]]
     assert 0.0 < qs1 < qs0 and out[F["qr"]] > 0.0
-    assert np.isclose(out[13 + 4], mas0 * qs1 / qs0, rtol=1e-12)           # snow keeps its share
-    assert np.isclose(out[13 + 2], mas0 * (1 - qs1 / qs0), rtol=1e-12)     # the rest is in rain
+    assert np.isclose(out[13 + 4], mas0 * qs1 / qs0, rtol=1e-12, atol=0.0)           # snow keeps its share
+    assert np.isclose(out[13 + 2], mas0 * (1 - qs1 / qs0), rtol=1e-12, atol=0.0)     # the rest is in rain
 
 
 def test_sublimation_returns_the_sublimated_share_of_ice_aerosol():
@@ -203,8 +203,8 @@ def test_sublimation_returns_the_sublimated_share_of_ice_aerosol():
     out = O.point_aero_cold(st, 5.0)
     qi1 = out[F["qi"]]
     assert 0.0 < qi1 < qi0
-    assert np.isclose(out[13 + 3], mai0 * qi1 / qi0, rtol=1e-12)
-    assert np.isclose(out[13 + 0], ma0 + mai0 * (1 - qi1 / qi0), rtol=1e-12)
+    assert np.isclose(out[13 + 3], mai0 * qi1 / qi0, rtol=1e-12, atol=0.0)
+    assert np.isclose(out[13 + 0], ma0 + mai0 * (1 - qi1 / qi0), rtol=1e-12, atol=0.0)
 
 
 def test_each_species_aerosol_falls_with_its_mass():

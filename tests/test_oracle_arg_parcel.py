@@ -60,3 +60,29 @@ def test_arg_smax_and_activation_against_a_parcel_integration(N, w, T, p):
     smax, act = parcel(N, w, T, p)
     assert abs(O.arg_smax(N, w, T, p) / smax - 1.0) < 0.20
     assert abs(O.arg_nact(N, w, T, p) / act - 1.0) < 0.10
+
+
+def test_arg_closed_form_worked_by_hand():
+    """The closed form evaluated by hand, term by term, at T = 283 K,
+    p = 900 hPa, w = 0.5 m/s and N = 1e9 m^-3 (about half the mode activates,
+    so both S_max and the activated number are sensitive to every term):
+      e_s (Bolton, t = 9.85 C) = 611.2 exp(17.67 t / (t + 243.5))   = 1214.8994 Pa
+      alpha = g M_w L_v / (c_p R T^2) - g M_a / (R T)               = 5.3946220e-4 m^-1
+      gamma = R T / (e_s M_w) + M_w L_v^2 / (c_p p M_a T)           = 259.36414 m^3 kg^-1
+      F_d = rho_w R T / (e_s D_v M_w)                              = 4.7567841e9
+      F_k = L_v rho_w / (K_a T) (L_v M_w / (R T) - 1)              = 6.6775551e9
+      G = 1 / (F_d + F_k)                                          = 8.7455863e-11 m^2 s^-1
+      A = 2 sigma_w M_w / (rho_w R T)                              = 1.1653395e-9 m
+      S_m = (2 / sqrt(kappa)) (A / (3 r_m))^1.5                     = 1.7535045e-3
+      alpha w / G                                                  = 3.0841969e6 m^-2
+      zeta = (2 A / 3) (alpha w / G)^0.5                           = 1.3643703e-6
+      eta = (alpha w / G)^1.5 / (2 pi rho_w gamma N)               = 3.3237117e-6
+      f_1 = 0.5 exp(2.5 ln^2 sigma), f_2 = 1 + 0.25 ln sigma       = 0.75416636, 1.1013663
+      f_1 (zeta / eta)^1.5 = 0.19834923, f_2 (S_m^2 / (eta + 3 zeta))^0.75 = 0.56902151
+      S_max = S_m / sqrt(0.19834923 + 0.56902151)                  = 2.0017243e-3
+      u = 2 ln(S_m / S_max) / (3 sqrt(2) ln sigma)                 = -0.15392318
+      N_act = (N / 2) erfc(u)                                      = 5.8616087e8 m^-3"""
+    N, w, T, p = 1e9, 0.5, 283.0, 9.0e4
+    assert abs(O.arg_sm(T) / 1.7535045e-3 - 1.0) < 1e-7
+    assert abs(O.arg_smax(N, w, T, p) / 2.0017243e-3 - 1.0) < 1e-7
+    assert abs(O.arg_nact(N, w, T, p) / 5.8616087e8 - 1.0) < 1e-7

@@ -389,6 +389,37 @@ def test_kk2000_point_values_worked_by_hand():
     assert abs(R["acc"] / 2.6909e-7 - 1.0) < 5e-5
 
 
+def test_kk2000_droplet_number_floor():
+    """The droplet concentration entering the KK2000 autoconversion is held
+    at 1 cm^-3 from below: any smaller concentration gives the rate at
+    1 cm^-3, and the -1.79 power law runs from exactly 1 cm^-3 upward (at
+    2 cm^-3 the rate is 2^-1.79 times the rate at 1 cm^-3, and at 1.05 cm^-3
+    already below it)."""
+    rho = 1.1
+    aut = lambda ncm3: O.rates(_state(qc=3e-4, nc=ncm3 * 1e6 / rho, rho=rho), 1.0)["aut"]
+    a1 = aut(1.0)
+    assert a1 > 0.0
+    for low in (0.99, 0.5, 1e-3, 0.0):
+        assert abs(aut(low) / a1 - 1.0) < 1e-14, low
+    assert abs(aut(2.0) / a1 - 2.0 ** -1.79) < 1e-13
+    assert aut(1.05) < a1 * (1.0 - 0.08)        # 1.05^-1.79 = 0.9164
+
+
+def test_self_collection_point_values_worked_by_hand():
+    """Seifert & Beheng self-collection in SI units with the cloud droplet
+    shape nu = 1, evaluated by hand at rho = 1.1 kg m^-3:
+      cloud: per m^3 of air the number falls at k_c (nu+2)/(nu+1) L_c^2 with
+        L_c = rho q_c; per kg of air (divided by rho) at
+        k_c (nu+2)/(nu+1) rho q_c^2 = 9.44e9 x (3/2) x 1.1 x (1e-4)^2
+                                    = 1.416e10 x 1.1e-8 = 155.76 kg^-1 s^-1
+      rain: per m^3 at k_r N_r L_r with N_r = rho n_r, L_r = rho q_r; per kg at
+        k_r rho n_r q_r = 5.78 x 1.1 x 1e3 x 1e-4 = 0.6358 kg^-1 s^-1"""
+    rho = 1.1
+    R = O.rates(_state(qc=1e-4, nc=1e8 / rho, qr=1e-4, nr=1e3, rho=rho), 1.0)
+    assert abs(R["scc"] / 155.76 - 1.0) < 1e-13
+    assert abs(R["scr"] / 0.6358 - 1.0) < 1e-13
+
+
 def test_accretion_scaling_and_presence():
     """KK2000 accretion is a power of the product q_c q_r: doubling either
     water content multiplies it by 2^1.15 (a law with the exponent on one
@@ -626,7 +657,8 @@ def test_a_non_finite_value_in_any_field_is_reported(bad):
     each of the 13 prognostic fields of the standard state, and in each field
     a configuration adds after the inputs (aerosol masses, sixth moments),
     planted one at a time at an inactive point (clear, dry air) of an
-    otherwise clean domain; the clean domain reports nothing."""
+    otherwise clean domain, at an inner point and at the edges of the level
+    and column ranges; the clean domain reports nothing."""
     nlev, ncols = 12, 4
     dz = np.full(nlev, 100.0)
     T, p = 290.0, 9e4
@@ -643,12 +675,15 @@ def test_a_non_finite_value_in_any_field_is_reported(bad):
              (O.NFIELDS_AEROC, lambda f: O.step_aero_cold(f, ncols, dz, 1.0)[1], list(range(16, 22))),
              (O.NFIELDS_3M, lambda f: O.step_3m(f, ncols, dz, 1.0)[1], [16]),
              (O.NFIELDS_3MC, lambda f: O.step_3m_cold(f, ncols, dz, 1.0)[1], list(range(16, 20)))]
+    # an inner point, the last level of an inner column and the first level of the last column
+    where = [(7, 2), (nlev - 1, 1), (0, ncols - 1)]
     for nf, run, fields in steps:
         assert run(clean(nf)) == 0
         for f in fields:
-            fld = clean(nf)
-            fld[f, 7, 2] = bad
-            assert run(fld) & O.ERR_NONFINITE, (nf, f)
+            for k, c in where:
+                fld = clean(nf)
+                fld[f, k, c] = bad
+                assert run(fld) & O.ERR_NONFINITE, (nf, f, k, c)
 
 
 # ---------------------------------------------------------- a12 sedimentation
@@ -759,10 +794,26 @@ def test_step_threads_do_not_change_results():
     assert np.array_equal(a, b)
 
 
+def test_gas_constants_follow_from_the_molar_masses():
+    """The specific gas constants of dry air and of water vapour are the
+    universal gas constant over the molar masses (to the digits given), and
+    their ratio is the familiar 0.622."""
+    R, Ma, Mw = P("Rgas"), P("Ma"), P("Mw")
+    assert R == 8.314 and Ma == 0.028965 and Mw == 0.018015
+    assert abs(P("Rd") * Ma / R - 1.0) < 1e-4
+    assert abs(P("Rv") * Mw / R - 1.0) < 1e-4
+    assert abs(P("Rd") / P("Rv") - 0.622) < 5e-4
+
+
 def test_parameters_are_the_cited_values():
     assert P("kk_aut") == 1350.0 and P("kk_aut_qc") == 2.47 and P("kk_aut_nc") == -1.79
     assert P("kk_acc") == 67.0 and P("kk_acc_exp") == 1.15
     assert P("kc_sb") == 9.44e9 and P("kr_sb") == 5.78
     assert P("mey_a") == 1e3 and P("mey_b") == -0.639 and P("mey_c") == 12.96
     assert P("es_l0") == 611.2 and P("es_la") == 17.67 and P("es_lb") == 243.5
+    assert P("nc_min_cm3") == 1.0 and P("nu_c") == 1.0
+    # the aerosol mode: an accumulation mode of ammonium sulphate (kappa of
+    # Petters & Kreidenweis 2007) and the surface tension of water
+    assert P("arg_rm") == 0.05e-6 and P("arg_sigma") == 1.5 and P("arg_kappa") == 0.61
+    assert P("surft") == 0.0761
     assert math.isnan(P("no_such_parameter"))

@@ -471,7 +471,7 @@ def test_budget_sums():
     m = fld[F["rho"], :, :ncols] * dz[:, None]
     w = (m * sum(fld[F[x], :, :ncols] for x in ("qv", "qc", "qr", "qi", "qs", "qg"))).sum(0)
     n = (m * (fld[F["nc"], :, :ncols] + fld[F["na"], :, :ncols])).sum(0)
-    assert np.allclose(got[0], w, rtol=1e-13) and np.allclose(got[1], n, rtol=1e-13)
+    assert np.allclose(got[0], w, rtol=1e-13, atol=0.0) and np.allclose(got[1], n, rtol=1e-13, atol=0.0)
 
 
 # ------------------------------------------------------------------ mixed
