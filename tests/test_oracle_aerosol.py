@@ -207,6 +207,30 @@ def test_sublimation_returns_the_sublimated_share_of_ice_aerosol():
     assert np.isclose(out[13 + 0], ma0 + mai0 * (1 - qi1 / qi0), rtol=1e-12, atol=0.0)
 
 
+def test_collected_cloud_takes_its_share_of_cloud_aerosol_to_rain_and_graupel():
+    """Cloud water collected at once by rain (accretion) and by graupel
+    (riming), in air saturated over water with no updraft (no adjustment, no
+    activation): the cloud keeps its aerosol per unit water, the rain gains
+    the accreted share and the graupel the rimed share, each in proportion to
+    the water it took, and the total is conserved."""
+    T, p = 263.0, 7.0e4
+    qsl = O.qsat(O.es_liq(T), p)
+    qc0, mac0, mar0, mag0 = 5e-4, 4e-9, 1e-9, 2e-9
+    st = _cold_point(T, p, qv=qsl, qc=qc0, nc=1e8, qr=2e-4, nr=1e3, qg=1e-3, ng=1e3,
+                     na=1e8, ma=1e-9, mac=mac0, mar=mar0, mag=mag0)
+    R = O.rates(st[:16], 2.0)
+    assert R["acc"] > 0.0 and R["rimg"] > 0.0
+    out = O.point_aero_cold(st, 2.0)
+    qc1 = out[F["qc"]]
+    assert 0.0 < qc1 < qc0
+    assert np.isclose(out[13 + 1] / qc1, mac0 / qc0, rtol=1e-9, atol=0.0)
+    to_rain, to_graupel = out[13 + 2] - mar0, out[13 + 5] - mag0
+    assert to_rain > 0.0 and to_graupel > 0.0
+    assert np.isclose(to_rain + to_graupel, mac0 * (1.0 - qc1 / qc0), rtol=1e-9, atol=0.0)
+    assert np.isclose(to_graupel / to_rain, R["rimg"] / (R["aut"] + R["acc"]), rtol=1e-9, atol=0.0)
+    assert np.isclose(out[13:19].sum(), st[16:22].sum(), rtol=1e-14, atol=0.0)
+
+
 def test_each_species_aerosol_falls_with_its_mass():
     """A cold column exactly at ice saturation, without cloud or rain: the
     ice species only sediment (no deposition, nucleation, riming or
