@@ -786,6 +786,31 @@ def test_step_column_budgets_and_independence():
     assert np.array_equal(fld[13:], f0[13:])
 
 
+def test_each_species_precipitation_is_its_own_column_loss():
+    """Ice, snow and graupel (no cloud, no rain) falling through air
+    saturated over ice below the nucleation temperature, so that no process
+    moves water between them: each species' surface precipitation row
+    (r, i, s, g) is that species' column loss, and the rain row stays zero."""
+    nlev, ncols, dt = 10, 3, 10.0
+    dz = np.full(nlev, 100.0)
+    T, p = 250.0, 7.0e4
+    fld = np.zeros((O.NFIELDS, nlev, ncols))
+    fld[F["T"]], fld[F["p"]], fld[F["rho"]] = T, p, p / (P("Rd") * T)
+    fld[F["qv"]] = O.qsat(O.es_ice(T), p)
+    fld[F["na"]] = 1e8
+    for sp, q, n in (("i", 1e-5, 1e5), ("s", 1e-4, 1e4), ("g", 3e-4, 2e3)):
+        fld[F["q" + sp]], fld[F["n" + sp]] = q, n
+    f0 = fld.copy()
+    pr, _, err = O.step(fld, ncols, dz, dt)
+    assert err == 0
+    m = f0[F["rho"]] * dz[:, None]
+    assert np.all(pr[0] == 0.0)
+    for row, sp in ((1, "qi"), (2, "qs"), (3, "qg")):
+        loss = ((f0[F[sp]] - fld[F[sp]]) * m).sum(0)
+        assert np.all(pr[row] > 0.0), sp
+        np.testing.assert_allclose(pr[row], loss, rtol=1e-9, atol=0)
+
+
 def test_step_threads_do_not_change_results():
     fld, dz, nc, nl, dt, _ = synth.workload("stratus_256x256x100", ncols=64, nlev=100)
     a, b = fld.copy(), fld.copy()
