@@ -109,6 +109,24 @@ def test_evaporated_cloud_returns_all_its_aerosol():
     assert out[14] == 0.0 and out[13] == st[MA] + st[MAC]
 
 
+def test_partly_evaporated_cloud_returns_its_share_of_aerosol():
+    """Cloud that the adjustment evaporates in part (subsaturated air, more
+    cloud water than the deficit) returns the evaporated share of its aerosol
+    to the free aerosol and keeps its aerosol per unit water."""
+    T, p = 285.0, 9.0e4
+    qs = O.qsat(O.es_liq(T), p)
+    for frac in (0.96, 0.99):
+        st = np.zeros(19)
+        st[F["T"]], st[F["p"]], st[F["rho"]] = T, p, p / (287.04 * T)
+        st[F["qv"]], st[F["qc"]], st[F["nc"]], st[F["na"]] = frac * qs, 1e-3, 1e8, 1e8
+        st[MA], st[MAC] = 2e-9, 3e-9
+        out = O.point_aero(st, 1.0)
+        assert 0.0 < out[F["qc"]] < 0.98 * st[F["qc"]]
+        assert np.isclose(out[14] / out[F["qc"]], st[MAC] / st[F["qc"]], rtol=1e-9, atol=0.0)
+        assert np.isclose(out[13] - st[MA], st[MAC] - out[14] - out[15], rtol=1e-12, atol=0.0)
+        assert out[13] > st[MA]
+
+
 # ------------------------------------------------ cold configuration (aerosol in ice too)
 MAI, MAS, MAG = 19, 20, 21
 QX = {MAR: F["qr"], MAI: F["qi"], MAS: F["qs"], MAG: F["qg"], MAC: F["qc"]}

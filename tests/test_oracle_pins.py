@@ -420,6 +420,18 @@ def test_self_collection_point_values_worked_by_hand():
     assert abs(R["scr"] / 0.6358 - 1.0) < 1e-13
 
 
+def test_rain_does_not_grow_in_supersaturated_air():
+    """Rain exchanges vapour only by evaporating in subsaturated air: at
+    S_w = 1.05, 1.0 and 1 + 1e-12 its evaporation rate is zero, at
+    S_w = 0.95 positive."""
+    T, p, rho = 285.0, 9.0e4, 1.1
+    qs = O.qsat(O.es_liq(T), p)
+    evr = lambda sw: O.rates(_state(T=T, p=p, rho=rho, qv=sw * qs, qr=2e-4, nr=1e3), 1.0)["evr"]
+    for sw in (1.05, 1.0, 1.0 + 1e-12):
+        assert evr(sw) == 0.0, sw
+    assert evr(0.95) > 0.0
+
+
 def test_accretion_scaling_and_presence():
     """KK2000 accretion is a power of the product q_c q_r: doubling either
     water content multiplies it by 2^1.15 (a law with the exponent on one
@@ -837,6 +849,15 @@ def test_parameters_are_the_cited_values():
     assert P("mey_a") == 1e3 and P("mey_b") == -0.639 and P("mey_c") == 12.96
     assert P("es_l0") == 611.2 and P("es_la") == 17.67 and P("es_lb") == 243.5
     assert P("nc_min_cm3") == 1.0 and P("nu_c") == 1.0
+    # thermodynamic and transport constants (standard values), the fall-speed
+    # reference density, the ice nucleation threshold and crystal mass, the
+    # new-raindrop radius, the presence threshold, the riming efficiency and
+    # the Courant limit per substep
+    assert P("T0") == 273.15 and P("cp") == 1005.0 and P("Lv") == 2.5e6 and P("Lf") == 3.34e5
+    assert P("g") == 9.81 and P("rho_w") == 1000.0 and P("rho0") == 1.2
+    assert P("Ka") == 2.4e-2 and P("Dv") == 2.26e-5 and P("mu_air") == 1.72e-5
+    assert P("T_nuc") == 268.15 and P("m_i0") == 1e-12 and P("r_r0") == 25e-6
+    assert P("q_min") == 1e-14 and P("e_rim") == 1.0 and P("c_max") == 1.0
     # the aerosol mode: an accumulation mode of ammonium sulphate (kappa of
     # Petters & Kreidenweis 2007) and the surface tension of water
     assert P("arg_rm") == 0.05e-6 and P("arg_sigma") == 1.5 and P("arg_kappa") == 0.61
