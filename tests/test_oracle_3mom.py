@@ -273,6 +273,21 @@ def test_nucleation_makes_monodisperse_ice(dt):
     assert np.isclose(z, n * (O.param("m_i0") / O.param("a_i")) ** 2, rtol=1e-12, atol=0.0)
 
 
+@pytest.mark.parametrize("si", [1.005, 1.05])
+def test_nucleation_just_above_ice_saturation(si):
+    """A point holding no hydrometeor, subsaturated over water but
+    supersaturated over ice below the nucleation temperature, is active:
+    ice nucleates there exactly as in the two-moment cold step (the
+    activity rule's ice-supersaturation clause, however small the excess)."""
+    T, p = 255.0, 5.0e4
+    qsi, qsl = O.qsat(O.es_ice(T), p), O.qsat(O.es_liq(T), p)
+    assert si * qsi < qsl
+    st = _point(T, p, qv=si * qsi, na=1e8)
+    out = O.point_3m_cold(st, 1.0)
+    assert out[F["qi"]] > 0.0 and out[F["ni"]] > 0.0
+    assert np.array_equal(out[:13], O.point(st[:16], 1.0))
+
+
 def test_deposition_keeps_every_ice_species_shape():
     T, p = 270.0, 7.0e4                      # warmer than nucleation, supersaturated over ice only
     qsi, qsl = O.qsat(O.es_ice(T), p), O.qsat(O.es_liq(T), p)
