@@ -523,6 +523,18 @@ def test_ice_nucleation_closed_form_and_bookkeeping():
     assert abs(P("cp") * (out[F["T"]] - T) - (P("Lv") + P("Lf")) * dq) <= 4 * P("cp") * np.spacing(T)
 
 
+def test_meyers_nucleation_worked_by_hand():
+    """Meyers et al. (1992) at S_i = 1.1 (ice supersaturation 10 %), by hand:
+      N_in = 1e3 exp(-0.639 + 12.96 x 0.1) m^-3 = 1e3 exp(0.657)
+           = 1e3 x e^0.6 x e^0.057 = 1e3 x 1.8221188 x 1.0586558 = 1928.9967 m^-3
+    made from none within a 1 s step and counted per kg of air at
+    rho = 0.8 kg m^-3: 1928.9967 / 0.8 = 2411.2458 kg^-1 s^-1."""
+    T, p = P("T_nuc") - 5.0, 6e4
+    qsi = O.qsat(O.es_ice(T), p)
+    nuc = O.rates(_state(T=T, p=p, rho=0.8, qv=1.1 * qsi), 1.0)["nuc"]
+    assert abs(nuc / 2411.2458 - 1.0) < 5e-8
+
+
 @pytest.mark.parametrize("sp", ["i", "s", "g"])
 def test_melting_moves_mass_number_and_heat(sp):
     """Melting above 0 C, isolated (saturated air holding one ice species and
