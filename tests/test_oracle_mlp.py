@@ -54,6 +54,56 @@ def test_masked_outputs_do_not_contribute():
     assert l1 == l2 and np.array_equal(g1, g2)
 
 
+def test_loss_is_the_masked_mean_squared_error():
+    """The loss is the mean of the squared errors over the unmasked outputs
+    (numpy's mean of the selected entries): zero with zero gradient where the
+    targets are the network's own outputs, the single squared error where one
+    output is unmasked, and zero where none is."""
+    rng = np.random.default_rng(7)
+    theta = mlp.init_params(3)
+    X = rng.normal(size=(9, 12))
+    Y = mlp.forward(theta, X)[0]
+    T = Y + rng.normal(size=Y.shape)
+    M = (rng.uniform(size=Y.shape) < 0.6).astype(np.float64)
+    loss, _ = mlp.loss_grad(theta, X, T, M)
+    assert abs(loss / np.mean((Y - T)[M > 0] ** 2) - 1.0) < 1e-13
+    loss, g = mlp.loss_grad(theta, X, Y, np.ones_like(Y))
+    assert loss == 0.0 and not np.any(g)
+    one = np.zeros_like(Y)
+    one[4, 2] = 1.0
+    assert abs(mlp.loss_grad(theta, X, T, one)[0] / (Y[4, 2] - T[4, 2]) ** 2 - 1.0) < 1e-13
+    assert mlp.loss_grad(theta, X, T, np.zeros_like(Y))[0] == 0.0
+
+
+def test_init_is_xavier_uniform():
+    """Weights uniform on +-sqrt(6 / (fan_in + fan_out)) (Glorot & Bengio
+    2010): inside the bound, reaching near it, with the uniform law's
+    variance bound^2 / 3; biases zero."""
+    for i, (W, b) in enumerate(mlp.unflatten(mlp.init_params(11))):
+        k, n = mlp.SIZES[i], mlp.SIZES[i + 1]
+        lim = np.sqrt(6.0 / (k + n))
+        assert np.all(np.abs(W) <= lim) and not np.any(b)
+        assert np.max(np.abs(W)) > (0.98 if W.size > 1000 else 0.9) * lim
+        if W.size > 1000:
+            assert abs(W.var() / (lim * lim / 3.0) - 1.0) < 0.03
+
+
+def test_surrogate_features_floor_the_logs():
+    """Absent species and numbers enter the features as the logs of their
+    floors: q_min for the water contents, one particle per kg for cloud
+    droplets and aerosol, 1e-3 per kg for raindrops, 1e-10 for vapour."""
+    from oracle import surrogate as OS
+    from paper_2010_14823_gb300 import synth
+    F = synth.FIDX
+    st = np.zeros(16)
+    st[F["T"]], st[F["p"]], st[F["rho"]] = 280.0, 8e4, 1.0
+    f = OS.features(st)
+    qmin = 1e-14
+    assert f[0] == np.log(qmin) and f[1] == np.log(qmin)
+    assert f[2] == 0.0 and f[9] == 0.0 and f[3] == np.log(1e-3) and f[7] == np.log(1e-10)
+    assert f[4] == 0.0 and f[10] == 0.0 and f[11] == 0.0
+
+
 def test_bf16_rounding_is_round_to_nearest_even():
     # exactly representable values stay, halfway cases go to the even neighbour
     one = np.float32(1.0)
@@ -102,7 +152,7 @@ def test_surrogate_targets_and_masks_follow_the_scheme():
     for mask, kw in cases.items():
         st = state(**kw)
         y, m = OS.targets(st, 1.0)
-        assert tuple(int(v) for v in m) == mask
+        assert tuple(m) == tuple(float(v) for v in mask)          # exactly 0 or 1
         r = O.rates(st, 1.0)
         for j, name in enumerate(("aut", "acc", "scc", "scr")):
             if m[j]:
