@@ -293,9 +293,11 @@ def bench_batch(args, rank, world, local):
                            "l2": "state %.1f GB > L2, no flush needed" % (16 * 8 * sum(d.nlev * d.pitch for d in dev) / 1e9)},
                 "roofline": None, "cpu_baseline": None, "e2e": None,
                 "gpu_launches": launches, "clocks": clocks}
-        print(json.dumps(line), flush=True)
+        if getattr(args, "emit", True):
+            print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return line if rank == 0 else None
 
 
 def bench_surrogate(args, rank, world, local):
@@ -534,7 +536,9 @@ def bench_tendency(args, rank, world, local):
                              "kernel": "k_step<PolicyMix, tendency>", "algorithmic_bytes_per_launch": alg,
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
                 "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks}
-        print(json.dumps(line), flush=True)
+        if getattr(args, "emit", True):
+            print(json.dumps(line), flush=True)
+    return line if rank == 0 else None
 
 
 def bench_warm(args, rank, world, local):
@@ -690,9 +694,11 @@ def bench_warm(args, rank, world, local):
                              "kernel": "k_step<PolicyMixWarm>", "algorithmic_bytes_per_launch": alg,
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)"},
                 "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clocks}
-        print(json.dumps(line), flush=True)
+        if getattr(args, "emit", True):
+            print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+    return line if rank == 0 else None
 
 
 FIELD_NAMES = ("T", "qv", "qc", "qr", "qi", "qs", "qg", "nc", "nr", "ni", "ns", "ng", "na")
@@ -839,6 +845,8 @@ def main():
     ap.add_argument("--surr-steps", type=int, default=100, help="surrogate: steps compared with the plain step")
     ap.add_argument("--gen-steps", type=int, default=10, help="surrogate: states the training rows come from")
     ap.add_argument("--train-steps", type=int, default=4000, help="surrogate: Adam steps")
+    ap.add_argument("--no-more-workloads", action="store_true",
+                    help="default run: skip the short batch64, warm_vs_cold and tendency runs")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="leave the surrogate run (training + 100 steps) out of the main line's config")
     args = ap.parse_args()
@@ -1045,6 +1053,30 @@ def main():
                      "precip_column_rel_error": c["precip_column_rel_error"], "network_roofline": sl["roofline"],
                      "gpu_launches": sl["gpu_launches"]}
 
+    more = None
+    if not args.no_more_workloads and world == 1 and args.workload.startswith("deep") and "mixed" in forms:
+        # the other single-GPU workloads, shortly (20 steps each), each with its
+        # own state: the batch of 64 uneven domains, the warm configuration
+        # against the cold one on stratus, the source-term mode
+        import copy
+        torch.cuda.empty_cache()
+        sub = copy.copy(args)
+        sub.emit, sub.steps, sub.warmup, sub.fp64_steps = False, 20, 3, 1
+        more = {}
+        for key, fn in (("batch64", bench_batch), ("warm_vs_cold", bench_warm), ("tendency", bench_tendency)):
+            ln = fn(sub, rank, world, local)
+            c = ln["config"]
+            more[key] = {"workload": c["workload"], "value": ln["value"], "ms_per_step": ln["ms_per_step"],
+                         "steps": ln["steps"], "fp64_ms_per_step": c.get("fp64_ms_per_step"),
+                         "roofline_frac": ln["roofline"]["frac"] if ln["roofline"] else None,
+                         "gpu_launches": ln["gpu_launches"]}
+            for extra in ("eager_ms_per_step", "tuned", "cold_mixed_ms_per_step", "warm_over_cold",
+                          "warm_aerosol_mixed_ms_per_step", "cold_aerosol_mixed_ms_per_step",
+                          "warm_three_moment_mixed_ms_per_step", "cold_three_moment_mixed_ms_per_step"):
+                if extra in c:
+                    more[key][extra] = c[extra]
+            torch.cuda.empty_cache()
+
     if rank == 0:
         cfg = {"workload": args.workload, "ncols": ncols, "nlev": nlev, "dt_s": dt,
                "form": "mixed FP32 rates / FP64 state and transfers" if "mixed" in forms else "FP64",
@@ -1059,6 +1091,8 @@ def main():
             cfg["mixed_vs_fp64"] = accuracy
         if surrogate is not None:
             cfg["surrogate"] = surrogate
+        if more is not None:
+            cfg["more_workloads"] = more
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": mix_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
