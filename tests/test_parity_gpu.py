@@ -1248,3 +1248,112 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable():
             casim.casim_wait_selftest(ctx, 3_000_000_000)            # beyond the kernels' own limit
         finally:
             casim.casim_free(ctx)
+
+
+# ---------------------------------------- hand-made regimes, one per column
+def _regime_domain(nf, regimes, nlev=12, reps=3):
+    """A domain whose columns hold the given point states at every level
+    (each regime in `reps` neighbouring columns, the temperature nudged by
+    0.01 K per copy), pitch a multiple of 32."""
+    ncols = reps * len(regimes)
+    pitch = (ncols + 31) // 32 * 32
+    fld = np.zeros((nf, nlev, pitch))
+    for i, reg in enumerate(regimes):
+        for r in range(reps):
+            c = reps * i + r
+            for k, v in reg.items():
+                fld[k, :, c] = v
+            fld[F["T"], :, c] += 0.01 * r
+    # padding columns: clear, subsaturated air
+    fld[F["T"], :, ncols:], fld[F["p"], :, ncols:], fld[F["rho"], :, ncols:] = 280.0, 8e4, 1.0
+    return np.ascontiguousarray(fld), np.full(nlev, 100.0), ncols
+
+
+def _pt(T, p, extra=None, **kw):
+    """One point state: T, p, rho = p / (R_d T), the named fields of the
+    standard layout, and `extra` {field index: value} for the fields after
+    the inputs."""
+    st = {F["T"]: T, F["p"]: p, F["rho"]: p / (287.04 * T), F["na"]: 1e8}
+    for k, v in kw.items():
+        st[F[k]] = v
+    st.update(extra or {})
+    return st
+
+
+def _qsl(T, p):
+    return O.qsat(O.es_liq(T), p)
+
+
+def _qsi(T, p):
+    return O.qsat(O.es_ice(T), p)
+
+
+@pytest.mark.parametrize("precision", [casim.CASIM_FP64, casim.CASIM_MIXED])
+@pytest.mark.parametrize("dt", [1.0, 5.0])
+def test_hand_made_regimes(dt, precision):
+    """The regimes the oracle's hand-made pins single out, each in its own
+    columns, against the oracle.  FP64 form: 13 fields and the precipitation
+    rows within 1e-12, aerosol masses within 1e-12 of the point's total
+    aerosol, sixth moments within 1e-12 of the largest.  Mixed form: the 13
+    fields within the derived mixed bound, aerosol masses within 1e-4 of the
+    point's total aerosol, sixth moments within 1e-3 of their change plus 1e-4
+    of their value (the bounds of the configurations' own mixed tests).
+    The regimes:
+    snow, ice and graupel falling at ice saturation (each species' own
+    precipitation row); Meyers nucleation at S_i = 1.1; rain in air
+    supersaturated over water; partial evaporation of cloud holding aerosol;
+    cloud collected at once by rain and graupel, with aerosol; nucleation just
+    above ice saturation and snow melting into existing rain with
+    triple-moment species."""
+    std = [_pt(250.0, 7e4, qv=_qsi(250.0, 7e4), qi=1e-5, ni=1e5, qs=1e-4, ns=1e4, qg=3e-4, ng=2e3),
+           _pt(263.15, 6e4, qv=1.1 * _qsi(263.15, 6e4)),
+           _pt(285.0, 9e4, qv=1.05 * _qsl(285.0, 9e4), qr=2e-4, nr=1e3)]
+    aero_warm = [_pt(285.0, 9e4, qv=0.96 * _qsl(285.0, 9e4), qc=1e-3, nc=1e8, extra={MA: 2e-9, MAC: 3e-9}),
+                 _pt(285.0, 9e4, qv=0.99 * _qsl(285.0, 9e4), qc=1e-3, nc=1e8, qr=2e-4, nr=1e3,
+                     extra={MA: 2e-9, MAC: 3e-9, MAR: 1e-9})]
+    aero_cold = [_pt(263.0, 7e4, qv=_qsl(263.0, 7e4), qc=5e-4, nc=1e8, qr=2e-4, nr=1e3, qg=1e-3, ng=1e3,
+                     extra={MA: 1e-9, MAC: 4e-9, MAR: 1e-9, 21: 2e-9})]
+    a = casim.casim_default_params().a
+
+    def z_at(x, q, n, mu):
+        return _gamma_g(mu) * (q / a[1 + x]) ** 2 / n
+    tri_cold = [_pt(255.0, 5e4, qv=1.005 * _qsi(255.0, 5e4)),
+                _pt(276.0, 9e4, qv=_qsl(276.0, 9e4), qr=3e-4, nr=2e3, qs=2e-4, ns=5e3,
+                    extra={ZC["r"]: z_at(0, 3e-4, 2e3, 1.0), ZC["s"]: z_at(2, 2e-4, 5e3, 4.0)})]
+    cases = [(16, std, 0, lambda f, n, dz: O.step(f, n, dz, dt)),
+             (19, aero_warm, casim.CASIM_WARM | casim.CASIM_AEROSOL, lambda f, n, dz: O.step_aero(f, n, dz, dt)),
+             (22, aero_cold, casim.CASIM_AEROSOL, lambda f, n, dz: O.step_aero_cold(f, n, dz, dt)),
+             (20, tri_cold, casim.CASIM_THREE_MOMENT, lambda f, n, dz: O.step_3m_cold(f, n, dz, dt))]
+    for nf, regimes, flags, ostep in cases:
+        fld, dz, ncols = _regime_domain(nf, regimes)
+        out, pr, _ = run_gpu(fld, dz, ncols, dt, precision=precision, flags=flags)
+        ref = fld.copy()
+        res = ostep(ref, ncols, dz)
+        assert res[-1] == 0
+        pref = res[0]
+        assert not np.array_equal(ref[:13, :, :ncols], fld[:13, :, :ncols])     # the regimes do act
+        if precision == casim.CASIM_MIXED:
+            for f in range(13):
+                a_, b_, i_ = out[f, :, :ncols], ref[f, :, :ncols], fld[f, :, :ncols]
+                bound = mixed_bound(b_, i_, f, ref[1, :, :ncols])
+                assert (np.abs(a_ - b_) <= bound).all(), (nf, synth.FIELDS[f], float((np.abs(a_ - b_) / bound).max()))
+            if nf in (19, 22):
+                scale = fld[MA:nf, :, :ncols].sum(axis=0)
+                assert (np.abs(out[MA:nf, :, :ncols] - ref[MA:nf, :, :ncols]) <= 1e-4 * scale + 1e-22).all(), nf
+            if nf == 20:
+                a_, b_, i_ = out[16:20, :, :ncols], ref[16:20, :, :ncols], fld[16:20, :, :ncols]
+                bound = 1e-3 * np.abs(b_ - i_) + 1e-4 * np.abs(b_) + 1e-16 * np.abs(fld[16:20]).max()
+                assert (np.abs(a_ - b_) <= bound).all(), float((np.abs(a_ - b_) / bound).max())
+            continue
+        assert_fp64_close(out, pr[:4], ref, pref[:4], ncols)
+        if nf in (19, 22):
+            hi = 19 if nf == 19 else 22
+            scale = fld[MA:hi, :, :ncols].sum(axis=0)
+            for f in range(MA, hi):
+                d = np.abs(out[f, :, :ncols] - ref[f, :, :ncols])
+                assert (d <= RTOL64 * np.maximum(np.abs(ref[f, :, :ncols]), scale)).all(), (nf, f, float(d.max()))
+            assert np.all(np.abs(pr[4, :ncols] - pref[4, :ncols]) <= RTOL64 * np.abs(pref[4, :ncols]) + 1e-26)
+        if nf == 20:
+            zmax = np.abs(ref[16:20, :, :ncols]).max()
+            d = np.abs(out[16:20, :, :ncols] - ref[16:20, :, :ncols])
+            assert (d <= RTOL64 * np.abs(ref[16:20, :, :ncols]) + 1e-12 * zmax).all(), float(d.max())
