@@ -73,3 +73,16 @@ def test_argument_errors_without_touching_the_device(L):
     bad.q_min = -1.0
     assert L.casim_init(ctypes.byref(ctx), ctypes.byref(bad), 0, 0) == -1
     assert L.casim_default_params(None) == -1
+
+
+def test_a_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library the binding raises at first use, naming the
+    missing file; there is no fallback path."""
+    from paper_2010_14823_gb300 import casim
+    monkeypatch.setattr(casim, "_lib", None)
+    monkeypatch.setattr(casim, "LIB", str(tmp_path / "libcasim.so"))
+    monkeypatch.delenv("CASIM_LIBRARY", raising=False)
+    with pytest.raises(RuntimeError, match="libcasim.so is missing"):
+        casim.lib()
+    with pytest.raises(RuntimeError, match="is missing"):
+        casim.casim_init()
