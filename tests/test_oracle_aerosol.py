@@ -249,6 +249,22 @@ def test_collected_cloud_takes_its_share_of_cloud_aerosol_to_rain_and_graupel():
     assert np.isclose(out[13:19].sum(), st[16:22].sum(), rtol=1e-14, atol=0.0)
 
 
+def test_cold_partly_evaporated_cloud_returns_its_share_of_aerosol():
+    """The cold configuration's aerosol bookkeeping on the same partial
+    evaporation (warm air, no ice): the cloud keeps its aerosol per unit
+    water and the free aerosol gains the rest."""
+    T, p = 285.0, 9.0e4
+    qsl = O.qsat(O.es_liq(T), p)
+    for frac in (0.96, 0.99):
+        st = _cold_point(T, p, qv=frac * qsl, qc=1e-3, nc=1e8, na=1e8, ma=2e-9, mac=3e-9)
+        out = O.point_aero_cold(st, 1.0)
+        qc1 = out[F["qc"]]
+        assert 0.0 < qc1 < 0.98 * st[F["qc"]]
+        assert np.isclose(out[13 + 1] / qc1, st[MAC] / st[F["qc"]], rtol=1e-9, atol=0.0)
+        assert np.isclose(out[13:19].sum(), st[16:22].sum(), rtol=1e-14, atol=0.0)
+        assert out[13 + 0] > st[MA]
+
+
 def test_each_species_aerosol_falls_with_its_mass():
     """A cold column exactly at ice saturation, without cloud or rain: the
     ice species only sediment (no deposition, nucleation, riming or
